@@ -1,0 +1,888 @@
+/*
+ * Plain FP64 CPU oracle for the multi-resolution SPH fluid-structure method of
+ * Zhang, Rezavand & Hu, "A multi-resolution SPH method for fluid-structure
+ * interactions" (arXiv 1911.13255).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the GPU library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may load it; the product
+ * path never does.  It shares no code with the CUDA library.
+ *
+ * Everything is double precision, single threaded, compiled without FMA
+ * contraction (-ffp-contract=off) so that the in-support test
+ * r^2 = dx*dx + dy*dy (+ dz*dz) < (2h)^2 is bit-reproducible.
+ *
+ * Where the paper is silent or garbled a written reading is used; each is
+ * named R1..R20 in the comments and listed in the design notes:
+ *   R1  support radius 2h; in-support <=> r^2 < 4h^2 in FP64
+ *   R2  solid volumes in all sums are the reference volumes V0 = dp_S^d
+ *   R4  low-dissipation Riemann solver (the paper defers to its ref. [zhang2017])
+ *   R5  g in the momentum equation is an acceleration
+ *   R6  ghost state p^d, v^d with outward normals (solid -> fluid)
+ *   R7  continuity includes solid/wall neighbours through a Riemann interface
+ *   R8  correction matrix B0 with the neighbour volumes V_b
+ *   R9  deformation-rate dF/dt = [sum_b V_b (v_b - v_a) (x) grad0 W_ab] B0_a
+ *   R10 Lame constants from E = 2 mu (1 + nu)
+ *   R11 all pair forces of a coarse step at the fluid mid state
+ *   R12 one density rate per step, used for this step's second half drift
+ *       and the next step's first half drift
+ *   R13 Delta t_S = Delta t_F / K exactly
+ *   R14 time averages as exact means of the discrete solid trajectory
+ *   R15 neighbours rebuilt every coarse step
+ *   R16 density reinitialisation from the number density
+ *   R17 normals n = normalize(F^-T n0)
+ *   R18 inflow buffer + periodic x
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "sph_oracle.h"
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Wendland C2 kernel, h = 1.3 dp (Section 4, "5th-order Wendland"), R1.     */
+/* W(q) = alpha_d (1 - q/2)^4 (1 + 2q) for q = r/h < 2.                      */
+/* ------------------------------------------------------------------------ */
+static double wendland_alpha(int dim, double h)
+{
+    return dim == 2 ? 7.0 / (4.0 * PI * h * h) : 21.0 / (16.0 * PI * h * h * h);
+}
+
+double or_kernel_W(int dim, double r, double h)
+{
+    double q = r / h;
+    if (q >= 2.0) return 0.0;
+    double a = 1.0 - 0.5 * q;
+    return wendland_alpha(dim, h) * a * a * a * a * (1.0 + 2.0 * q);
+}
+
+/* dW/dr = -(5 alpha / h) q (1 - q/2)^3 */
+double or_kernel_dW(int dim, double r, double h)
+{
+    double q = r / h;
+    if (q >= 2.0) return 0.0;
+    double a = 1.0 - 0.5 * q;
+    return -5.0 * wendland_alpha(dim, h) / h * q * a * a * a;
+}
+
+/* Lattice number-density sum sigma0 * dp^d over an infinite square/cubic   */
+/* lattice at spacing dp (self included), R16.                               */
+double or_lattice_sigma0(int dim, double dp, double h)
+{
+    double s = 0.0;
+    int K = (int)ceil(2.0 * h / dp) + 1;
+    if (dim == 2) {
+        for (int i = -K; i <= K; i++)
+            for (int j = -K; j <= K; j++)
+                s += or_kernel_W(2, sqrt((double)(i * i + j * j)) * dp, h);
+    } else {
+        for (int i = -K; i <= K; i++)
+            for (int j = -K; j <= K; j++)
+                for (int k = -K; k <= K; k++)
+                    s += or_kernel_W(3, sqrt((double)(i * i + j * j + k * k)) * dp, h);
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tait equation of state (Eq. eqeos) and its inverse for the ghost density */
+/* (Section 2.2, below Eq. fs-coupling), gamma = 7.                          */
+/* ------------------------------------------------------------------------ */
+double or_eos_p(double rho, double rho0, double c0)
+{
+    return rho0 * c0 * c0 / 7.0 * (pow(rho / rho0, 7.0) - 1.0);
+}
+
+double or_eos_rho(double p, double rho0, double c0)
+{
+    return rho0 * pow(p * 7.0 / (rho0 * c0 * c0) + 1.0, 1.0 / 7.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry helpers                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* d = ri - rj with the minimal image in x when periodic; returns r^2 summed */
+/* in coordinate order without contraction (R1).                            */
+static double delta(const or_params *P, int dim, const double *ri, const double *rj, double *d)
+{
+    for (int k = 0; k < dim; k++) d[k] = ri[k] - rj[k];
+    if (P->periodic_x) {
+        if (d[0] > 0.5 * P->Lx) d[0] -= P->Lx;
+        else if (d[0] < -0.5 * P->Lx) d[0] += P->Lx;
+    }
+    double r2 = d[0] * d[0];
+    for (int k = 1; k < dim; k++) r2 = r2 + d[k] * d[k];
+    return r2;
+}
+
+static double dot(int dim, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int k = 0; k < dim; k++) s += a[k] * b[k];
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour lists (Alg. 1, "particle-neighbour list").                      */
+/* Pairs (a, b) with |r_a - r_b|^2 < rc^2, a from set A and b from set B,    */
+/* each row sorted by b.  Brute force is the definition; the cell-linked    */
+/* list gives the same sets and is what the oracle's step uses.             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t *ptr; /* nA + 1 */
+    int64_t *idx; /* ptr[nA] */
+} csr_t;
+
+static void csr_free(csr_t *c)
+{
+    free(c->ptr);
+    free(c->idx);
+    c->ptr = c->idx = NULL;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static void pairs_brute(const or_params *P, int dim, const double *A, int64_t nA, const double *B,
+                        int64_t nB, double rc, int same, csr_t *out)
+{
+    double rc2 = rc * rc, d[3];
+    out->ptr = (int64_t *)malloc(sizeof(int64_t) * (nA + 1));
+    int64_t cap = 16 * (nA + 1), n = 0;
+    out->idx = (int64_t *)malloc(sizeof(int64_t) * cap);
+    out->ptr[0] = 0;
+    for (int64_t a = 0; a < nA; a++) {
+        for (int64_t b = 0; b < nB; b++) {
+            if (same && a == b) continue;
+            if (delta(P, dim, A + a * dim, B + b * dim, d) < rc2) {
+                if (n == cap) {
+                    cap *= 2;
+                    out->idx = (int64_t *)realloc(out->idx, sizeof(int64_t) * cap);
+                }
+                out->idx[n++] = b;
+            }
+        }
+        out->ptr[a + 1] = n;
+    }
+}
+
+/* Cell-linked list with cells of edge >= rc over the bounding box of A and */
+/* B (in x over the periodic period when periodic).                         */
+static int pairs_cells(const or_params *P, int dim, const double *A, int64_t nA, const double *B,
+                       int64_t nB, double rc, int same, csr_t *out)
+{
+    double lo[3], hi[3], csz[3];
+    int64_t nc[3] = {1, 1, 1};
+    for (int k = 0; k < dim; k++) {
+        lo[k] = 1e300;
+        hi[k] = -1e300;
+    }
+    for (int64_t i = 0; i < nA; i++)
+        for (int k = 0; k < dim; k++) {
+            if (A[i * dim + k] < lo[k]) lo[k] = A[i * dim + k];
+            if (A[i * dim + k] > hi[k]) hi[k] = A[i * dim + k];
+        }
+    for (int64_t i = 0; i < nB; i++)
+        for (int k = 0; k < dim; k++) {
+            if (B[i * dim + k] < lo[k]) lo[k] = B[i * dim + k];
+            if (B[i * dim + k] > hi[k]) hi[k] = B[i * dim + k];
+        }
+    if (nA == 0 || nB == 0) {
+        out->ptr = (int64_t *)calloc(nA + 1, sizeof(int64_t));
+        out->idx = (int64_t *)malloc(sizeof(int64_t));
+        return 0;
+    }
+    /* a blown-up state (non-finite or absurdly spread positions) is an error */
+    double ncell_f = 1.0;
+    for (int k = 0; k < dim; k++) {
+        if (!isfinite(lo[k]) || !isfinite(hi[k])) return -2;
+        ncell_f *= floor((hi[k] - lo[k]) / rc) + 1.0;
+    }
+    if (ncell_f > 4e8) return -2;
+    for (int k = 0; k < dim; k++) {
+        nc[k] = (int64_t)floor((hi[k] - lo[k]) / rc) + 1;
+        csz[k] = rc;
+    }
+    int px = P->periodic_x && floor(P->Lx / rc) >= 3;
+    if (px) {
+        lo[0] = P->x_lo;
+        nc[0] = (int64_t)floor(P->Lx / rc);
+        csz[0] = P->Lx / (double)nc[0];
+    }
+    int64_t ncell = nc[0] * nc[1] * nc[2];
+    int64_t *head = (int64_t *)calloc(ncell + 1, sizeof(int64_t));
+    int64_t *cell_of = (int64_t *)malloc(sizeof(int64_t) * nB);
+    int64_t *sorted = (int64_t *)malloc(sizeof(int64_t) * nB);
+    int64_t c3[3];
+#define CELL_COORDS(p)                                                        \
+    for (int k = 0; k < 3; k++) {                                             \
+        if (k < dim) {                                                        \
+            int64_t ck = (int64_t)floor(((p)[k] - lo[k]) / csz[k]);           \
+            if (ck < 0) ck = 0;                                               \
+            if (ck >= nc[k]) ck = nc[k] - 1;                                  \
+            c3[k] = ck;                                                       \
+        } else                                                                \
+            c3[k] = 0;                                                        \
+    }
+    for (int64_t b = 0; b < nB; b++) {
+        CELL_COORDS(B + b * dim);
+        cell_of[b] = (c3[2] * nc[1] + c3[1]) * nc[0] + c3[0];
+        head[cell_of[b] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; c++) head[c + 1] += head[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (ncell + 1));
+    memcpy(fill, head, sizeof(int64_t) * (ncell + 1));
+    for (int64_t b = 0; b < nB; b++) sorted[fill[cell_of[b]]++] = b;
+    free(fill);
+
+    double rc2 = rc * rc, d[3];
+    out->ptr = (int64_t *)malloc(sizeof(int64_t) * (nA + 1));
+    int64_t cap = 16 * (nA + 1), n = 0;
+    out->idx = (int64_t *)malloc(sizeof(int64_t) * cap);
+    out->ptr[0] = 0;
+    for (int64_t a = 0; a < nA; a++) {
+        CELL_COORDS(A + a * dim);
+        int64_t row0 = n;
+        int dz0 = dim == 3 ? -1 : 0, dz1 = dim == 3 ? 1 : 0;
+        for (int dz = dz0; dz <= dz1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int64_t cx = c3[0] + dx, cy = c3[1] + dy, cz = c3[2] + dz;
+                    if (px) cx = (cx + nc[0]) % nc[0];
+                    if (cx < 0 || cx >= nc[0] || cy < 0 || cy >= nc[1] || cz < 0 || cz >= nc[2]) continue;
+                    int64_t c = (cz * nc[1] + cy) * nc[0] + cx;
+                    for (int64_t s = head[c]; s < head[c + 1]; s++) {
+                        int64_t b = sorted[s];
+                        if (same && a == b) continue;
+                        if (delta(P, dim, A + a * dim, B + b * dim, d) < rc2) {
+                            if (n == cap) {
+                                cap *= 2;
+                                out->idx = (int64_t *)realloc(out->idx, sizeof(int64_t) * cap);
+                            }
+                            out->idx[n++] = b;
+                        }
+                    }
+                }
+        qsort(out->idx + row0, (size_t)(n - row0), sizeof(int64_t), cmp_i64);
+        out->ptr[a + 1] = n;
+    }
+#undef CELL_COORDS
+    free(head);
+    free(cell_of);
+    free(sorted);
+    return 0;
+}
+
+int64_t or_pairs_count(const or_params *P, int dim, const double *A, int64_t nA, const double *B,
+                       int64_t nB, double rc, int same, int brute)
+{
+    csr_t c;
+    if (brute) pairs_brute(P, dim, A, nA, B, nB, rc, same, &c);
+    else if (pairs_cells(P, dim, A, nA, B, nB, rc, same, &c)) return -1;
+    int64_t n = c.ptr[nA];
+    csr_free(&c);
+    return n;
+}
+
+int or_pairs_fill(const or_params *P, int dim, const double *A, int64_t nA, const double *B,
+                  int64_t nB, double rc, int same, int brute, int64_t *ptr, int64_t *idx)
+{
+    csr_t c;
+    if (brute) pairs_brute(P, dim, A, nA, B, nB, rc, same, &c);
+    else if (pairs_cells(P, dim, A, nA, B, nB, rc, same, &c)) return -1;
+    memcpy(ptr, c.ptr, sizeof(int64_t) * (nA + 1));
+    memcpy(idx, c.idx, sizeof(int64_t) * c.ptr[nA]);
+    csr_free(&c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Low-dissipation inter-particle Riemann solver, reading R4 (Section 2.2    */
+/* defers it to the authors' earlier work).  Left state i, right state j,   */
+/* e the unit vector from i to j.  Returns p~ and writes v~.                 */
+/* ------------------------------------------------------------------------ */
+double or_riemann(int dim, const double *e, const double *vL, const double *vR, double pL,
+                  double pR, double rhoL, double rhoR, double c0, double *vstar)
+{
+    double UL = dot(dim, vL, e), UR = dot(dim, vR, e);
+    double rb = 0.5 * (rhoL + rhoR);
+    double Us = 0.5 * (UL + UR) + (pL - pR) / (2.0 * rb * c0);
+    double beta = 3.0 * fmax(UL - UR, 0.0);
+    if (beta > c0) beta = c0;
+    double Ps = 0.5 * (pL + pR) + 0.5 * rb * beta * (UL - UR);
+    if (vstar)
+        for (int k = 0; k < dim; k++)
+            vstar[k] = Us * e[k] + 0.5 * (vL[k] + vR[k]) - 0.5 * (UL + UR) * e[k];
+    return Ps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small dense matrix helpers (row-major d x d)                              */
+/* ------------------------------------------------------------------------ */
+static double det_d(int dim, const double *A)
+{
+    if (dim == 2) return A[0] * A[3] - A[1] * A[2];
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse through the adjugate */
+static void inv_d(int dim, const double *A, double *Ai)
+{
+    double dt = det_d(dim, A);
+    if (dim == 2) {
+        Ai[0] = A[3] / dt;
+        Ai[1] = -A[1] / dt;
+        Ai[2] = -A[2] / dt;
+        Ai[3] = A[0] / dt;
+        return;
+    }
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / dt;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) / dt;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / dt;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) / dt;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / dt;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) / dt;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / dt;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) / dt;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / dt;
+}
+
+static void matmul_d(int dim, const double *A, const double *B, double *C)
+{
+    for (int i = 0; i < dim; i++)
+        for (int j = 0; j < dim; j++) {
+            double s = 0.0;
+            for (int k = 0; k < dim; k++) s += A[i * dim + k] * B[k * dim + j];
+            C[i * dim + j] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Solid constitutive law: neo-Hookean (Eqs. Neo-Hookean-energy, 2rd-PK).    */
+/* S = dW/dE = mu (I - C^-1) + lambda ln J C^-1, C = F^T F; P = F S.         */
+/* ------------------------------------------------------------------------ */
+void or_neo_hookean_P(int dim, const double *F, double mu, double lam, double *Pout)
+{
+    double C[9], Ci[9], S[9];
+    for (int i = 0; i < dim; i++)
+        for (int j = 0; j < dim; j++) {
+            double s = 0.0;
+            for (int k = 0; k < dim; k++) s += F[k * dim + i] * F[k * dim + j];
+            C[i * dim + j] = s;
+        }
+    inv_d(dim, C, Ci);
+    double lnJ = log(det_d(dim, F));
+    for (int i = 0; i < dim; i++)
+        for (int j = 0; j < dim; j++)
+            S[i * dim + j] = mu * ((i == j ? 1.0 : 0.0) - Ci[i * dim + j]) + lam * lnJ * Ci[i * dim + j];
+    matmul_d(dim, F, S, Pout);
+}
+
+/* Lame constants, reading R10 (Eq. relation-modulus with E = 2G(1+nu)) */
+static void lame(double E, double nu, double *mu, double *lam)
+{
+    *mu = E / (2.0 * (1.0 + nu));
+    *lam = 2.0 * (*mu) * nu / (1.0 - 2.0 * nu);
+}
+
+double or_solid_sound_speed(double E, double nu, double rho0)
+{
+    /* c_S = sqrt(K / rho), K = E / (3 (1 - 2 nu))  (Section 2.1) */
+    return sqrt(E / (3.0 * (1.0 - 2.0 * nu)) / rho0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Solid set-up: static reference neighbour list (total Lagrangian), the     */
+/* correction matrix B0 (Eq. correctmatrix with V_b, reading R8), F = I.     */
+/* ------------------------------------------------------------------------ */
+int64_t or_solid_count(const or_params *P, const or_solid *s)
+{
+    int dim = P->dim;
+    double hS = 1.3 * s->dp;
+    or_params Q = *P;
+    Q.periodic_x = 0; /* the body's reference configuration is not wrapped */
+    return or_pairs_count(&Q, dim, s->r0, s->n, s->r0, s->n, 2.0 * hS, 1, 0);
+}
+
+int or_solid_setup(const or_params *P, or_solid *s)
+{
+    int dim = P->dim, dd = dim * dim;
+    double hS = 1.3 * s->dp, V0 = pow(s->dp, dim), d[3];
+    or_params Q = *P;
+    Q.periodic_x = 0;
+    or_pairs_fill(&Q, dim, s->r0, s->n, s->r0, s->n, 2.0 * hS, 1, 0, s->nb_ptr, s->nb_idx);
+    for (int64_t a = 0; a < s->n; a++) {
+        double M[9] = {0};
+        for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
+            int64_t b = s->nb_idx[q];
+            double r2 = delta(&Q, dim, s->r0 + a * dim, s->r0 + b * dim, d); /* d = r0_a - r0_b */
+            double r = sqrt(r2), dW = or_kernel_dW(dim, r, hS);
+            for (int i = 0; i < dim; i++)
+                for (int j = 0; j < dim; j++)
+                    M[i * dim + j] += V0 * (-d[i]) * (dW * d[j] / r); /* (r0_b - r0_a) (x) grad0_a W_ab */
+        }
+        inv_d(dim, M, s->B0 + a * dd);
+        for (int i = 0; i < dd; i++) s->F[a * dd + i] = (i % (dim + 1) == 0) ? 1.0 : 0.0;
+        for (int k = 0; k < dim; k++) {
+            s->r[a * dim + k] = s->r0[a * dim + k];
+            s->nrm[a * dim + k] = s->n0[a * dim + k];
+            if (s->cons[a]) s->v[a * dim + k] = 0.0; /* constrained: r = r0, v = 0 */
+        }
+    }
+    return 0;
+}
+
+/* grad0_a W_ab (reference configuration, h_S), Eq. strongkernel */
+static void grad0(const or_params *Q, int dim, const or_solid *s, int64_t a, int64_t b, double hS,
+                  double *g)
+{
+    double d[3];
+    double r = sqrt(delta(Q, dim, s->r0 + a * dim, s->r0 + b * dim, d));
+    double dW = or_kernel_dW(dim, r, hS);
+    for (int k = 0; k < dim; k++) g[k] = dW * d[k] / r;
+}
+
+/* F from positions: [sum_b V_b (r_b - r_a) (x) grad0_a W_ab] B0_a (the     */
+/* invariant that integrating dF/dt preserves, reading R9).                  */
+int or_solid_F_from_positions(const or_params *P, const or_solid *s, double *Fout)
+{
+    int dim = P->dim, dd = dim * dim;
+    double hS = 1.3 * s->dp, V0 = pow(s->dp, dim), g[3];
+    or_params Q = *P;
+    Q.periodic_x = 0;
+    for (int64_t a = 0; a < s->n; a++) {
+        double M[9] = {0};
+        for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
+            int64_t b = s->nb_idx[q];
+            grad0(&Q, dim, s, a, b, hS, g);
+            for (int i = 0; i < dim; i++)
+                for (int j = 0; j < dim; j++)
+                    M[i * dim + j] += V0 * (s->r[b * dim + i] - s->r[a * dim + i]) * g[j];
+        }
+        matmul_d(dim, M, s->B0 + a * dd, Fout + a * dd);
+    }
+    return 0;
+}
+
+/* dF/dt_a = [sum_b V_b (v_b - v_a) (x) grad0_a W_ab] B0_a   (reading R9) */
+static void solid_Fdot(const or_params *Q, int dim, const or_solid *s, double hS, double V0,
+                       double *Fdot)
+{
+    int dd = dim * dim;
+    double g[3];
+    for (int64_t a = 0; a < s->n; a++) {
+        double M[9] = {0};
+        for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
+            int64_t b = s->nb_idx[q];
+            grad0(Q, dim, s, a, b, hS, g);
+            for (int i = 0; i < dim; i++)
+                for (int j = 0; j < dim; j++)
+                    M[i * dim + j] += V0 * (s->v[b * dim + i] - s->v[a * dim + i]) * g[j];
+        }
+        matmul_d(dim, M, s->B0 + a * dd, Fdot + a * dd);
+    }
+}
+
+/* Solid acceleration, Eq. solid-model-mr (R2, R5):                          */
+/* m_a dv_a/dt = 2 sum_b V_a V_b 1/2 (P_a B0_a + P_b B0_b) grad0_a W_ab      */
+/*               + m_a g + f_a^F                                            */
+int or_solid_accel(const or_params *P, const or_solid *s, const double *F, double *acc)
+{
+    int dim = P->dim, dd = dim * dim;
+    double hS = 1.3 * s->dp, V0 = pow(s->dp, dim), m = s->rho0 * V0, mu, lam, g[3];
+    or_params Q = *P;
+    Q.periodic_x = 0;
+    lame(s->E, s->nu, &mu, &lam);
+    double *PB = (double *)malloc(sizeof(double) * dd * (s->n > 0 ? s->n : 1));
+    for (int64_t a = 0; a < s->n; a++) {
+        double Pk[9];
+        or_neo_hookean_P(dim, F + a * dd, mu, lam, Pk);
+        matmul_d(dim, Pk, s->B0 + a * dd, PB + a * dd);
+    }
+    for (int64_t a = 0; a < s->n; a++) {
+        double f[3] = {0, 0, 0};
+        for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
+            int64_t b = s->nb_idx[q];
+            grad0(&Q, dim, s, a, b, hS, g);
+            for (int i = 0; i < dim; i++) {
+                double t = 0.0;
+                for (int j = 0; j < dim; j++) t += 0.5 * (PB[a * dd + i * dim + j] + PB[b * dd + i * dim + j]) * g[j];
+                f[i] += 2.0 * V0 * V0 * t;
+            }
+        }
+        for (int i = 0; i < dim; i++) acc[a * dim + i] = (f[i] + s->fF[a * dim + i]) / m + P->g[i];
+    }
+    free(PB);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fluid-structure pair (fluid i, solid or wall particle a), Section 2.2     */
+/* with the multi-rate ghost state of Eq. fs-coupling-mr, readings R6, R7.   */
+/* Returns the force on the fluid particle (f^{S:p} + f^{S:v}) in fout,      */
+/* and, when vi2 is non-null, the continuity contribution of the pair        */
+/* evaluated with the fluid velocity vi2.                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double rho0, c0, eta, hF, Vi;
+} fluid_consts;
+
+static void fs_pair(const or_params *P, int dim, const fluid_consts *fc, const double *ri,
+                    const double *vi, double rhoi, double pi, const double *ra, const double *vbar,
+                    const double *abar, const double *na, double Va, double *fout,
+                    const double *vi2, double *drho_out)
+{
+    double d[3], e[3], vd[3];
+    double r = sqrt(delta(P, dim, ri, ra, d)); /* d = r_i - r_a */
+    double dW = or_kernel_dW(dim, r, fc->hF);
+    double gW[3];
+    for (int k = 0; k < dim; k++) {
+        gW[k] = dW * d[k] / r; /* grad_i W(r_ia, h_F) */
+        e[k] = -d[k] / r;      /* unit vector from i to a */
+    }
+    double gma[3];
+    for (int k = 0; k < dim; k++) gma[k] = P->g[k] - abar[k];
+    /* ghost pressure, reading R6: p_d = p_i + rho_i max(0, -(g - a~).n) max(0, r_ia.n) */
+    double pd = pi + rhoi * fmax(0.0, -dot(dim, gma, na)) * fmax(0.0, dot(dim, d, na));
+    double rhod = or_eos_rho(pd, fc->rho0, fc->c0);
+    if (fout) {
+        double pbar = (pi * rhod + pd * rhoi) / (rhoi + rhod);
+        for (int k = 0; k < dim; k++) {
+            vd[k] = 2.0 * vbar[k] - vi[k]; /* ghost velocity, reading R6 */
+            double fp = -2.0 * fc->Vi * Va * pbar * gW[k];
+            double fv = 2.0 * fc->eta * fc->Vi * Va * (vi[k] - vd[k]) / (r + 0.01 * fc->hF) * dW;
+            fout[k] = fp + fv;
+        }
+    }
+    if (vi2) {
+        double vs[3];
+        for (int k = 0; k < dim; k++) vd[k] = 2.0 * vbar[k] - vi2[k];
+        or_riemann(dim, e, vi2, vd, pi, pd, rhoi, rhod, fc->c0, vs);
+        double s = 0.0;
+        for (int k = 0; k < dim; k++) s += (vi2[k] - vs[k]) * gW[k];
+        *drho_out = 2.0 * rhoi * Va * s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inflow profile (Section 4.1), reading R18: U(y) = 6 Ubar y (H - y) / H^2  */
+/* (mean Ubar), Ubar(t) = 0.5 U0 (1 - cos(pi t / t_s)) for t < t_s.          */
+/* ------------------------------------------------------------------------ */
+double or_inflow_u(const or_params *P, double y, double t)
+{
+    double U = P->inflow_U;
+    if (P->inflow_tramp > 0.0 && t < P->inflow_tramp) U = 0.5 * U * (1.0 - cos(PI * t / P->inflow_tramp));
+    if (P->inflow_profile == 1) return U;
+    double H = P->inflow_H, yy = y - P->inflow_y0;
+    if (yy < 0.0) yy = 0.0;
+    if (yy > H) yy = H;
+    return 6.0 * U * yy * (H - yy) / (H * H);
+}
+
+static void wrap_x(const or_params *P, double *x)
+{
+    if (!P->periodic_x) return;
+    if (*x >= P->x_lo + P->Lx) *x -= P->Lx;
+    else if (*x < P->x_lo) *x += P->Lx;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One coarse fluid step with K solid sub-steps (Section 3, Alg. 1), in the  */
+/* order a1..a8 of readings R11-R16:                                         */
+/*  a1 inflow buffer, fluid first half drift of rho and r (Eq. verlet-first-half)
+ *  a2 neighbour lists at the fluid mid state (solid at its start position)
+ *  a3 [every n_reinit steps] density reinitialisation and normal update
+ *  a4 fluid momentum (Eq. fluid-model-mr-mom) + kick (Eq. verlet-first-mediate)
+ *  a5 fluid force on the solid (Eqs. F:p, F:v) from the same pair terms
+ *  a6 fluid continuity (Eq. fluid-model-mr-con) at (r^{n+1/2}, v^{n+1});
+ *     second half drift (Eq. verlet-first-final)
+ *  a7 K solid sub-steps (Eqs. verlet-first-half-solid .. -final-solid)
+ *  a8 time-averaged solid velocity and acceleration (Eq. fs-coupling-mr)
+ * ------------------------------------------------------------------------ */
+int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K,
+            double t, int64_t step_index, or_diag *dg)
+{
+    int dim = P->dim, dd = dim * dim;
+    if (dim != 2 && dim != 3) return -1;
+    if (K < 1) return -1;
+    double hF = 1.3 * f->dp;
+    double rcF = 2.0 * hF;
+    double mF = f->rho0 * pow(f->dp, dim);
+    double VW = pow(w->dp, dim);
+    double VS = pow(s->dp, dim);
+    double hS = 1.3 * s->dp;
+    double zero[3] = {0, 0, 0};
+    memset(dg, 0, sizeof(*dg));
+
+    /* a1: inflow buffer (R18), then first half drift */
+    if (P->inflow_on) {
+        for (int64_t i = 0; i < f->n; i++) {
+            double *ri = f->r + i * dim;
+            if (ri[0] >= P->x_lo && ri[0] < P->x_lo + P->inflow_width) {
+                f->v[i * dim + 0] = or_inflow_u(P, ri[1], t);
+                for (int k = 1; k < dim; k++) f->v[i * dim + k] = 0.0;
+            }
+        }
+    }
+    for (int64_t i = 0; i < f->n; i++) {
+        f->rho[i] = f->rho[i] + 0.5 * dt * f->drho[i];
+        for (int k = 0; k < dim; k++) f->r[i * dim + k] = f->r[i * dim + k] + 0.5 * dt * f->v[i * dim + k];
+        wrap_x(P, &f->r[i * dim]);
+    }
+
+    /* a2: neighbour lists (R15: rebuilt every coarse step) */
+    csr_t FF, FW, FS, SF;
+    if (pairs_cells(P, dim, f->r, f->n, f->r, f->n, rcF, 1, &FF)) return -2;
+    if (pairs_cells(P, dim, f->r, f->n, w->r, w->n, rcF, 0, &FW)) return -2;
+    if (pairs_cells(P, dim, f->r, f->n, s->r, s->n, rcF, 0, &FS)) return -2;
+    if (pairs_cells(P, dim, s->r, s->n, f->r, f->n, rcF, 0, &SF)) return -2;
+    dg->n_ff = FF.ptr[f->n];
+    dg->n_fw = FW.ptr[f->n];
+    dg->n_fs = FS.ptr[f->n];
+    dg->n_sf = SF.ptr[s->n];
+    dg->n_ss = s->n > 0 ? s->nb_ptr[s->n] : 0;
+
+    double d[3];
+    /* a3: density reinitialisation (R16) and normal update (R17) */
+    if (P->n_reinit > 0 && step_index % P->n_reinit == 0) {
+        double sigma0 = or_lattice_sigma0(dim, f->dp, hF); /* lattice number density */
+        double VF = pow(f->dp, dim);
+        for (int64_t i = 0; i < f->n; i++) {
+            double sg = or_kernel_W(dim, 0.0, hF);
+            for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++)
+                sg += or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, f->r + FF.idx[q] * dim, d)), hF);
+            for (int64_t q = FW.ptr[i]; q < FW.ptr[i + 1]; q++)
+                sg += VW / VF * or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, w->r + FW.idx[q] * dim, d)), hF);
+            for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++)
+                sg += VS / VF * or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, s->r + FS.idx[q] * dim, d)), hF);
+            double rr = f->rho0 * sg / sigma0;
+            if (P->free_surface && rr < f->rho0) rr = f->rho0;
+            f->rho[i] = rr;
+        }
+        for (int64_t a = 0; a < s->n; a++) {
+            double Fi[9], n[3] = {0, 0, 0}, nn = 0.0;
+            inv_d(dim, s->F + a * dd, Fi);
+            /* F^-T n0: (F^-T)_{ij} = (F^-1)_{ji} */
+            for (int i = 0; i < dim; i++) {
+                for (int j = 0; j < dim; j++) n[i] += Fi[j * dim + i] * s->n0[a * dim + j];
+                nn += n[i] * n[i];
+            }
+            nn = sqrt(nn);
+            for (int i = 0; i < dim; i++) s->nrm[a * dim + i] = n[i] / nn;
+        }
+    }
+
+    /* pressures at the mid state */
+    double *p = (double *)malloc(sizeof(double) * (f->n > 0 ? f->n : 1));
+    for (int64_t i = 0; i < f->n; i++) p[i] = or_eos_p(f->rho[i], f->rho0, f->c0);
+
+    fluid_consts fc = {f->rho0, f->c0, f->eta, hF, 0.0};
+
+    /* a4: fluid momentum at (r^{n+1/2}, rho^{n+1/2}, v^n), Eq. fluid-model-mr-mom */
+    for (int64_t i = 0; i < f->n; i++) {
+        const double *ri = f->r + i * dim, *vi = f->v + i * dim;
+        double Vi = mF / f->rho[i];
+        double force[3] = {0, 0, 0}, e[3];
+        for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
+            int64_t j = FF.idx[q];
+            double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            double dW = or_kernel_dW(dim, r, hF);
+            double Vj = mF / f->rho[j];
+            for (int k = 0; k < dim; k++) e[k] = -d[k] / r;
+            double ps = or_riemann(dim, e, vi, f->v + j * dim, p[i], p[j], f->rho[i], f->rho[j], f->c0, NULL);
+            for (int k = 0; k < dim; k++) {
+                double gW = dW * d[k] / r;
+                force[k] += -2.0 * Vi * Vj * ps * gW;
+                force[k] += 2.0 * f->eta * Vi * Vj * (vi[k] - f->v[j * dim + k]) / r * dW;
+            }
+        }
+        fc.Vi = Vi;
+        for (int64_t q = FW.ptr[i]; q < FW.ptr[i + 1]; q++) {
+            int64_t a = FW.idx[q];
+            double fo[3];
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], w->r + a * dim, zero, zero, w->nrm + a * dim, VW,
+                    fo, NULL, NULL);
+            for (int k = 0; k < dim; k++) force[k] += fo[k];
+        }
+        for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++) {
+            int64_t a = FS.idx[q];
+            double fo[3];
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], s->r + a * dim, s->vbar + a * dim,
+                    s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
+            for (int k = 0; k < dim; k++) {
+                force[k] += fo[k];
+                dg->mom_fs_fluid[k] += fo[k];
+                dg->abs_fs += fabs(fo[k]);
+            }
+        }
+        for (int k = 0; k < dim; k++) f->dvdt[i * dim + k] = force[k] / mF + P->g[k];
+    }
+
+    /* a5: fluid force on the solid from the same pair terms (Eqs. F:p, F:v) */
+    for (int64_t a = 0; a < s->n; a++) {
+        double fa[3] = {0, 0, 0};
+        for (int64_t q = SF.ptr[a]; q < SF.ptr[a + 1]; q++) {
+            int64_t i = SF.idx[q];
+            double fo[3];
+            fc.Vi = mF / f->rho[i];
+            fs_pair(P, dim, &fc, f->r + i * dim, f->v + i * dim, f->rho[i], p[i], s->r + a * dim,
+                    s->vbar + a * dim, s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
+            for (int k = 0; k < dim; k++) fa[k] -= fo[k];
+        }
+        for (int k = 0; k < dim; k++) {
+            s->fF[a * dim + k] = fa[k];
+            dg->mom_fs_solid[k] += fa[k];
+        }
+    }
+
+    /* kick: v^{n+1} = v^n + dt dv/dt (Eq. verlet-first-mediate) */
+    double vmaxF = 0.0;
+    for (int64_t i = 0; i < f->n; i++) {
+        double v2 = 0.0;
+        for (int k = 0; k < dim; k++) {
+            f->v[i * dim + k] = f->v[i * dim + k] + dt * f->dvdt[i * dim + k];
+            v2 += f->v[i * dim + k] * f->v[i * dim + k];
+        }
+        if (v2 > vmaxF) vmaxF = v2;
+    }
+    dg->vmax_f = sqrt(vmaxF);
+
+    /* a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}), Eq. fluid-model-mr-con + R7 */
+    for (int64_t i = 0; i < f->n; i++) {
+        const double *ri = f->r + i * dim, *vi = f->v + i * dim;
+        double rate = 0.0, e[3], vs[3];
+        for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
+            int64_t j = FF.idx[q];
+            double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            double dW = or_kernel_dW(dim, r, hF);
+            double Vj = mF / f->rho[j];
+            for (int k = 0; k < dim; k++) e[k] = -d[k] / r;
+            or_riemann(dim, e, vi, f->v + j * dim, p[i], p[j], f->rho[i], f->rho[j], f->c0, vs);
+            double sdot = 0.0;
+            for (int k = 0; k < dim; k++) sdot += (vi[k] - vs[k]) * dW * d[k] / r;
+            rate += 2.0 * f->rho[i] * Vj * sdot;
+        }
+        fc.Vi = mF / f->rho[i];
+        for (int64_t q = FW.ptr[i]; q < FW.ptr[i + 1]; q++) {
+            int64_t a = FW.idx[q];
+            double dr;
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], w->r + a * dim, zero, zero, w->nrm + a * dim, VW,
+                    NULL, vi, &dr);
+            rate += dr;
+        }
+        for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++) {
+            int64_t a = FS.idx[q];
+            double dr;
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], s->r + a * dim, s->vbar + a * dim,
+                    s->abar + a * dim, s->nrm + a * dim, VS, NULL, vi, &dr);
+            rate += dr;
+        }
+        f->drho[i] = rate;
+    }
+    /* second half drift (Eq. verlet-first-final) */
+    for (int64_t i = 0; i < f->n; i++) {
+        f->rho[i] = f->rho[i] + 0.5 * dt * f->drho[i];
+        for (int k = 0; k < dim; k++) f->r[i * dim + k] = f->r[i * dim + k] + 0.5 * dt * f->v[i * dim + k];
+        wrap_x(P, &f->r[i * dim]);
+    }
+    free(p);
+    csr_free(&FF);
+    csr_free(&FW);
+    csr_free(&FS);
+    csr_free(&SF);
+
+    /* a7: K solid sub-steps with dt_S = dt / K (R13), f^F held constant */
+    if (s->n > 0) {
+        double dts = dt / (double)K, mu, lam;
+        lame(s->E, s->nu, &mu, &lam);
+        or_params Q = *P;
+        Q.periodic_x = 0;
+        double *rn = (double *)malloc(sizeof(double) * s->n * dim);
+        double *vn = (double *)malloc(sizeof(double) * s->n * dim);
+        double *acc = (double *)malloc(sizeof(double) * s->n * dim);
+        memcpy(rn, s->r, sizeof(double) * s->n * dim);
+        memcpy(vn, s->v, sizeof(double) * s->n * dim);
+        double vmaxS = 0.0, amaxS = 0.0;
+        solid_Fdot(&Q, dim, s, hS, VS, s->Fdot); /* dF/dt(v^0) */
+        for (int kk = 0; kk < K; kk++) {
+            /* first half: F, rho = rho0/J, r (Eq. verlet-first-half-solid) */
+            for (int64_t a = 0; a < s->n; a++) {
+                for (int i = 0; i < dd; i++) s->F[a * dd + i] = s->F[a * dd + i] + 0.5 * dts * s->Fdot[a * dd + i];
+                if (!s->cons[a])
+                    for (int k = 0; k < dim; k++) s->r[a * dim + k] = s->r[a * dim + k] + 0.5 * dts * s->v[a * dim + k];
+            }
+            /* velocity (Eq. verlet-first-mediate-solid) */
+            or_solid_accel(P, s, s->F, acc);
+            for (int64_t a = 0; a < s->n; a++) {
+                if (s->cons[a]) continue;
+                double a2 = 0.0, v2 = 0.0;
+                for (int k = 0; k < dim; k++) {
+                    s->v[a * dim + k] = s->v[a * dim + k] + dts * acc[a * dim + k];
+                    a2 += acc[a * dim + k] * acc[a * dim + k];
+                    v2 += s->v[a * dim + k] * s->v[a * dim + k];
+                }
+                if (a2 > amaxS) amaxS = a2;
+                if (v2 > vmaxS) vmaxS = v2;
+            }
+            /* second half (Eq. verlet-first-final-solid) with dF/dt(v^{k+1}) */
+            solid_Fdot(&Q, dim, s, hS, VS, s->Fdot);
+            for (int64_t a = 0; a < s->n; a++) {
+                for (int i = 0; i < dd; i++) s->F[a * dd + i] = s->F[a * dd + i] + 0.5 * dts * s->Fdot[a * dd + i];
+                if (!s->cons[a])
+                    for (int k = 0; k < dim; k++) s->r[a * dim + k] = s->r[a * dim + k] + 0.5 * dts * s->v[a * dim + k];
+            }
+        }
+        /* a8: time averages, reading R14 */
+        for (int64_t a = 0; a < s->n; a++) {
+            for (int k = 0; k < dim; k++) {
+                s->vbar[a * dim + k] = (s->r[a * dim + k] - rn[a * dim + k]) / dt;
+                s->abar[a * dim + k] = (s->v[a * dim + k] - vn[a * dim + k]) / dt;
+            }
+        }
+        dg->vmax_s = sqrt(vmaxS);
+        dg->amax_s = sqrt(amaxS);
+        free(rn);
+        free(vn);
+        free(acc);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time-step criteria (Section 3.2): acoustic Eq. dt-relax, advection        */
+/* Eq. dtf-advection (h^2/nu, reading of the garbled h^2/eta), solid         */
+/* Eq. dts-advection and kappa = [dt_F / dt_S] + 1.                          */
+/* ------------------------------------------------------------------------ */
+void or_suggest_dt(const or_params *P, const or_fluid *f, const or_solid *s, double vmax_f,
+                   double vmax_s, double amax_s, double *dt_ac, double *dt_ad, double *dt_s)
+{
+    (void)P;
+    double hF = 1.3 * f->dp, hS = 1.3 * s->dp;
+    *dt_ac = 0.6 * hF / (f->c0 + vmax_f);
+    double nu = f->eta / f->rho0;
+    double a1 = vmax_f > 0.0 ? hF / vmax_f : 1e300;
+    double a2 = nu > 0.0 ? hF * hF / nu : 1e300;
+    *dt_ad = 0.25 * (a1 < a2 ? a1 : a2);
+    double cS = s->n > 0 ? or_solid_sound_speed(s->E, s->nu, s->rho0) : 0.0;
+    double b1 = s->n > 0 ? hS / (cS + vmax_s) : 1e300;
+    double b2 = amax_s > 0.0 ? sqrt(hS / amax_s) : 1e300;
+    *dt_s = 0.6 * (b1 < b2 ? b1 : b2);
+}
+
+void or_eos_rho_array(int64_t n, const double *p, double *rho, double rho0, double c0)
+{
+    for (int64_t i = 0; i < n; i++) rho[i] = or_eos_rho(p[i], rho0, c0);
+}
+
+int or_substeps(double dt_f, double dt_s)
+{
+    return (int)floor(dt_f / dt_s) + 1;
+}

@@ -1,0 +1,425 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Every check here is independent of the oracle's own formulas: quadrature,
+finite differences of a stated energy, brute force, a library k-d tree,
+closed forms (Euler-Bernoulli, plane Poiseuille, hydrostatics) and exact
+conservation laws.  No GPU is used.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, spatial
+
+import fsi_cases as fc
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Kernel (Section 4: 5th-order Wendland, h = 1.3 dp; support 2h, reading R1)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_unit_integral(dim):
+    h = 0.37
+    f = (lambda r: 2 * math.pi * r * O.kernel_W(2, r, h)) if dim == 2 else \
+        (lambda r: 4 * math.pi * r * r * O.kernel_W(3, r, h))
+    val, _ = integrate.quad(f, 0.0, 2 * h, epsabs=1e-14, epsrel=1e-13)
+    assert abs(val - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_derivative_matches_finite_difference(dim):
+    h = 0.013
+    for q in (0.1, 0.5, 1.0, 1.37, 1.9):
+        r, eps = q * h, 1e-7 * h
+        fd = (O.kernel_W(dim, r + eps, h) - O.kernel_W(dim, r - eps, h)) / (2 * eps)
+        assert abs(O.kernel_dW(dim, r, h) - fd) < 1e-6 * abs(fd)
+
+
+def test_kernel_compact_support():
+    h = 0.5
+    for dim in (2, 3):
+        assert O.kernel_W(dim, 2 * h, h) == 0.0 and O.kernel_dW(dim, 2 * h, h) == 0.0
+        assert O.kernel_W(dim, 2 * h * (1 - 1e-9), h) < 1e-30
+        assert O.kernel_dW(dim, 0.0, h) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_lattice_partition_of_unity(dim):
+    """Sum_j V_j W_ij on a lattice at h = 1.3 dp is 1 to within 1.1 % and the
+    gradient sum vanishes by symmetry (Section 4, kernel choice)."""
+    dp = 1.0
+    s = O.lattice_sigma0(dim, dp, 1.3 * dp)
+    assert abs(s - 1.0) < 0.011
+    # jittered lattice, interior particle
+    rng = np.random.default_rng(3)
+    n = 9 if dim == 2 else 7
+    pts = fc.lattice((0,) * dim, (n * dp,) * dim, dp)
+    pts = fc.jitter(pts, dp, 1e-3, rng)
+    c = np.argmin(((pts - n * dp / 2) ** 2).sum(1))
+    tot, grad = 0.0, np.zeros(dim)
+    for j in range(len(pts)):
+        d = pts[c] - pts[j]
+        r = math.sqrt((d * d).sum())
+        tot += O.kernel_W(dim, r, 1.3) * dp ** dim
+        if j != c:
+            grad += O.kernel_dW(dim, r, 1.3) * d / r * dp ** dim
+    assert abs(tot - 1.0) < 0.03
+    assert np.abs(grad).max() < 0.05
+
+
+# --------------------------------------------------------------------------
+# Neighbour sets: brute force is the definition (r^2 < (2h)^2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("periodic", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_list_equals_brute_force(dim, periodic):
+    rng = np.random.default_rng(11 + dim + 7 * periodic)
+    n = 1500 if dim == 2 else 1200
+    L = 1.0
+    A = rng.uniform(0, L, size=(n, dim))
+    B = rng.uniform(0, L, size=(n // 2, dim))
+    rc = 0.06 if dim == 2 else 0.12
+    case = fc.Case(name="x", dim=dim, gravity=(0, 0, 0), periodic_x=periodic, x_lo=0.0, Lx=L)
+    for same, X, Y in ((1, A, A), (0, A, B), (0, B, A)):
+        p1, i1 = O.pairs(case, X, Y, rc, same, brute=False)
+        p2, i2 = O.pairs(case, X, Y, rc, same, brute=True)
+        assert np.array_equal(p1, p2) and np.array_equal(i1, i2)
+    # against an independent library k-d tree
+    box = [L] + [1e9] * (dim - 1) if periodic else None
+    Bs = B.copy()
+    tree = spatial.cKDTree(Bs, boxsize=box)
+    p, i = O.pairs(case, A, B, rc, 0)
+    for a in range(0, n, 37):
+        ref = sorted(tree.query_ball_point(A[a], rc))
+        assert list(i[p[a]:p[a + 1]]) == ref
+
+
+def test_neighbor_counts_on_lattice():
+    """20 neighbours in 2-D and 80 in 3-D at h = 1.3 dp, support 2h."""
+    for dim, expect in ((2, 20), (3, 80)):
+        n = 11 if dim == 2 else 9
+        pts = fc.lattice((0,) * dim, (float(n),) * dim, 1.0)
+        c = int(np.argmin(((pts - n / 2) ** 2).sum(1)))
+        case = fc.Case(name="x", dim=dim, gravity=(0, 0, 0))
+        p, i = O.pairs(case, pts[c:c + 1], pts, 2.6, 0)
+        assert p[1] - p[0] == expect + 1  # self included when same=0
+
+
+# --------------------------------------------------------------------------
+# Equation of state (Eq. eqeos) and its inverse
+# --------------------------------------------------------------------------
+
+def test_eos_closed_forms():
+    rho0, c0 = 1000.0, 20.0
+    assert O.eos_p(rho0, rho0, c0) == 0.0
+    eps = 1e-4
+    dpdrho = (O.eos_p(rho0 + eps, rho0, c0) - O.eos_p(rho0 - eps, rho0, c0)) / (2 * eps)
+    assert abs(dpdrho - c0 * c0) < 1e-6 * c0 * c0   # dp/drho = c^2 at rho0
+    for p in (-5e3, -1.0, 0.0, 3.7, 1373.0, 1e5):
+        rr = O.eos_rho(p, rho0, c0)
+        assert abs(O.eos_p(rr, rho0, c0) - p) <= 1e-14 * max(abs(p), rho0 * c0 * c0 / 7)
+
+
+# --------------------------------------------------------------------------
+# Riemann interface (reading R4): reduces to the average for equal states,
+# symmetric under exchange, dissipative in compression
+# --------------------------------------------------------------------------
+
+def test_riemann_properties():
+    rng = np.random.default_rng(5)
+    for dim in (2, 3):
+        for _ in range(20):
+            e = rng.normal(size=dim)
+            e /= np.linalg.norm(e)
+            v = rng.normal(size=dim)
+            p = rng.uniform(-10, 10)
+            ps, vs = O.riemann(e, v, v, p, p, 1.0, 1.0, 10.0)
+            assert abs(ps - p) < 1e-12 and np.allclose(vs, v, atol=1e-12)
+            vL, vR = rng.normal(size=dim), rng.normal(size=dim)
+            pL, pR, rL, rR = rng.uniform(-5, 5), rng.uniform(-5, 5), 1.01, 0.99
+            ps1, vs1 = O.riemann(e, vL, vR, pL, pR, rL, rR, 10.0)
+            ps2, vs2 = O.riemann(-e, vR, vL, pR, pL, rR, rL, 10.0)
+            assert abs(ps1 - ps2) < 1e-12 and np.allclose(vs1, vs2, atol=1e-12)
+    # approaching particles raise the interface pressure, capped by c0
+    e = np.array([1.0, 0.0])
+    ps, _ = O.riemann(e, np.array([1.0, 0]), np.array([-1.0, 0]), 0.0, 0.0, 1.0, 1.0, 10.0)
+    assert ps > 0
+    ps_far, _ = O.riemann(e, np.array([100.0, 0]), np.array([-100.0, 0]), 0.0, 0.0, 1.0, 1.0, 10.0)
+    assert abs(ps_far - 0.5 * 1.0 * 10.0 * 200.0) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Neo-Hookean stress (Eqs. Neo-Hookean-energy, 2rd-PK): P = dW/dF
+# --------------------------------------------------------------------------
+
+def _energy(F, mu, lam):
+    """Strain energy of Eq. Neo-Hookean-energy: mu tr E - mu ln J + lam/2 (ln J)^2."""
+    d = F.shape[0]
+    E = 0.5 * (F.T @ F - np.eye(d))
+    lnJ = math.log(np.linalg.det(F))
+    return mu * np.trace(E) - mu * lnJ + 0.5 * lam * lnJ ** 2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neo_hookean_is_energy_derivative(dim):
+    rng = np.random.default_rng(dim)
+    mu, lam = 3.1, 7.3
+    for _ in range(5):
+        F = np.eye(dim) + 0.2 * rng.normal(size=(dim, dim))
+        if np.linalg.det(F) < 0.3:
+            continue
+        P = O.neo_hookean_P(F, mu, lam)
+        G = np.zeros_like(F)
+        eps = 1e-6
+        for i in range(dim):
+            for j in range(dim):
+                Fp, Fm = F.copy(), F.copy()
+                Fp[i, j] += eps
+                Fm[i, j] -= eps
+                G[i, j] = (_energy(Fp, mu, lam) - _energy(Fm, mu, lam)) / (2 * eps)
+        assert np.abs(P - G).max() < 1e-7 * (mu + lam)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_zero_stress_under_rigid_rotation(dim):
+    """F from positions under a finite rotation equals R; P(R) = 0 (Eq. 2rd-PK)."""
+    case = fc.cantilever() if dim == 2 else fc.tiny_box_3d()
+    s = O.OracleSim(case)
+    if dim == 2:
+        th = 0.7
+        R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    else:
+        R = spatial.transform.Rotation.from_rotvec([0.3, -0.5, 0.8]).as_matrix()
+    s.set_solid_positions(s.s_r0 @ R.T + 0.123)
+    F = s.F_from_positions()
+    assert np.abs(F - R[None]).max() < 1e-12
+    P = O.neo_hookean_P(R, 1.0, 2.0)
+    assert np.abs(P).max() < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_corrected_gradient_reproduces_affine_fields(dim):
+    """With B0 (Eq. correctmatrix, reading R8) F = I on the reference
+    configuration and F = A under r = A r0 + b, boundary particles included."""
+    case = fc.cantilever() if dim == 2 else fc.tiny_box_3d()
+    s = O.OracleSim(case)
+    assert np.abs(s.F_from_positions() - np.eye(dim)[None]).max() < 1e-12
+    rng = np.random.default_rng(1)
+    A = np.eye(dim) + 0.3 * rng.normal(size=(dim, dim))
+    s.set_solid_positions(s.s_r0 @ A.T + 0.5)
+    assert np.abs(s.F_from_positions() - A[None]).max() < 1e-11
+
+
+def test_uniform_stretch_has_no_interior_force():
+    """A uniform deformation gives a uniform stress: zero net force on interior particles."""
+    case = fc.cantilever(L=0.1, t=0.08)
+    s = O.OracleSim(case)
+    F = np.array([[1.05, 0.02], [0.0, 0.97]])
+    acc = s.solid_accel(np.broadcast_to(F, s.s_F.shape).copy())
+    r = s.s_r0
+    m = 4 * 1.3 * case.s_dp   # the particle and all its neighbours have full support
+    interior = (r[:, 0] > -0.02 + m) & (r[:, 0] < 0.1 - m) & (r[:, 1] > m) & (r[:, 1] < 0.08 - m)
+    assert interior.sum() > 10
+    assert np.abs(acc[interior]).max() < 1e-8 * np.abs(acc).max()
+
+
+# --------------------------------------------------------------------------
+# Solid dynamics: dF/dt integration and a cantilever against Euler-Bernoulli
+# --------------------------------------------------------------------------
+
+def test_integrated_F_matches_F_from_positions():
+    """Integrating dF/dt (reading R9) keeps F equal to the position-based F."""
+    case = fc.cantilever(L=0.2, v_tip=0.2)
+    s = O.OracleSim(case)
+    _, _, dts = s.suggest_dt()
+    for _ in range(100):
+        s.step(5 * dts * 0.9, 5)
+    F = s.F_from_positions()
+    assert np.abs(F - s.s_F).max() < 1e-11
+    assert np.abs(s.s_F - np.eye(2)).max() > 1e-4   # it did deform
+
+
+def _cantilever_period(dpS, L=0.2):
+    case = fc.cantilever(L=L, dpS=dpS, v_tip=0.02)
+    s = O.OracleSim(case)
+    _, _, dts = s.suggest_dt()
+    dt = 0.9 * dts
+    ys, ts = [], []
+    while True:
+        s.step(dt, 1)
+        ys.append(s.s_r[case.tip, 1] - s.s_r0[case.tip, 1])
+        ts.append(s.t)
+        y = np.array(ys)
+        down = np.where((y[:-1] > 0) & (y[1:] <= 0))[0]
+        up = np.where((y[:-1] < 0) & (y[1:] >= 0))[0]
+        if len(up) >= 1 and len(down) >= 1:
+            # linear interpolation of the crossings
+            def cross(k):
+                return ts[k] + (ts[k + 1] - ts[k]) * y[k] / (y[k] - y[k + 1])
+            return 2.0 * (cross(up[0]) - cross(down[0]))
+
+
+def test_cantilever_first_mode_vs_euler_bernoulli():
+    """Clamped 2-D plane-strain beam (L = 0.2, t = 0.02, rho = 10, E = 1.4e3,
+    nu = 0.4): the period converges at second order to the Euler-Bernoulli
+    value; the Richardson extrapolation of 4 and 8 layers is within 5 %."""
+    g = _golden("euler_bernoulli.txt")
+    b1 = optimize.brentq(lambda x: 1 + math.cos(x) * math.cosh(x), 1.0, 3.0, xtol=1e-15)
+    assert abs(b1 - g["beta1L"]) < 1e-12
+    L, t, E, nu, rho = 0.2, 0.02, 1.4e3, 0.4, 10.0
+    Ep = E / (1 - nu * nu)
+    f1 = b1 ** 2 / (2 * math.pi) * math.sqrt(Ep * t ** 3 / 12 / (rho * t * L ** 4))
+    T_eb = 1 / f1
+    T4 = _cantilever_period(0.005)
+    T8 = _cantilever_period(0.0025)
+    assert abs(T8 - T_eb) < abs(T4 - T_eb) / 2.5        # converging
+    T_ext = T8 + (T8 - T4) / 3.0
+    assert abs(T_ext / T_eb - 1.0) < 0.05
+
+
+# --------------------------------------------------------------------------
+# Coupling and integrator: antisymmetry and momentum conservation
+# --------------------------------------------------------------------------
+
+def test_fluid_solid_forces_are_antisymmetric():
+    """Sum_i f_i^S + Sum_a f_a^F = 0 (Eqs. S:p, S:v vs F:p, F:v)."""
+    s = O.OracleSim(fc.tiny_box(seed=2))
+    dt, _, dts = s.suggest_dt()
+    for _ in range(3):
+        d = s.step(dt, 3)
+        tot = d["mom_fs_fluid"] + d["mom_fs_solid"]
+        assert d["n_fs"] > 0 and d["n_fs"] == d["n_sf"]
+        assert np.abs(tot).max() <= 1e-13 * d["abs_fs"]
+
+
+def test_total_momentum_conserved_with_substeps():
+    """Free block in a periodic fluid blob, no walls, no gravity, K = 3:
+    position-based Verlet with sum of dt_S = dt_F conserves the total momentum
+    to round-off (Section 3.3)."""
+    case = fc.floating_block(seed=1)
+    s = O.OracleSim(case)
+    mF, mS = case.f_rho0 * case.f_dp ** 2, case.s_rho0 * case.s_dp ** 2
+
+    def mom():
+        return mF * s.f_v.sum(0) + mS * s.s_v.sum(0)
+
+    scale = mF * np.abs(s.f_v).sum() + mS * np.abs(s.s_v).sum()
+    P0 = mom()
+    dt, _, _ = s.suggest_dt()
+    for _ in range(100):
+        s.step(dt, 3)
+    assert np.abs(mom() - P0).max() < 1e-13 * scale
+    assert np.abs(s.s_v).max() > 1e-3   # the block moved
+
+
+def test_time_averages_are_trajectory_means():
+    """v~ dt_F = r^{n+1} - r^n and a~ dt_F = v^{n+1} - v^n (reading R14)."""
+    s = O.OracleSim(fc.tiny_box(seed=4))
+    dt, _, _ = s.suggest_dt()
+    s.step(dt, 2)
+    r0, v0 = s.s_r.copy(), s.s_v.copy()
+    s.step(dt, 4)
+    assert np.abs(s.s_vbar * dt - (s.s_r - r0)).max() < 1e-15
+    assert np.abs(s.s_abar * dt - (s.s_v - v0)).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Ghost state (reading R6): hydrostatic equilibrium and no-slip Poiseuille
+# --------------------------------------------------------------------------
+
+def test_hydrostatic_column_in_equilibrium_at_the_floor():
+    """A water column with hydrostatic density at rest: the near-floor fluid
+    is in equilibrium only if the ghost pressure adds rho g d (reading R6)."""
+    case = fc.hydrostatic_column(W=0.04, H=0.06, dp=0.002)
+    case.n_reinit = 0
+    s = O.OracleSim(case)
+    s.step(1e-12, 1)
+    a, x, y = s.f_dvdt, s.f_r[:, 0], s.f_r[:, 1]
+    hF, g = 1.3 * 0.002, 9.81
+    cols = (x > 2 * hF) & (x < 0.04 - 2 * hF)
+    bottom = cols & (y < 2 * hF)
+    interior = cols & (y > 2 * hF) & (y < 0.06 - 3 * hF)
+    assert abs(a[bottom, 1].mean()) < 0.06 * g
+    assert np.abs(a[interior, 1]).max() < 0.05 * g
+
+
+def _poiseuille_case(steps):
+    dp, H, Lx, nu, Umax = 0.001, 0.02, 0.02, 1e-3, 0.05
+    g = 8 * nu * Umax / H ** 2
+    fr = fc.lattice((0, 0), (Lx, H), dp)
+    wb, nb = fc._wall_layers_y(0, Lx, 0.0, -1, dp, 4, 2)
+    wt, nt = fc._wall_layers_y(0, Lx, H, +1, dp, 4, 2)
+    case = fc.Case(name="poiseuille", dim=2, gravity=(g, 0, 0), periodic_x=1, x_lo=0, Lx=Lx,
+                   f_r=fr, f_v=np.zeros_like(fr), f_p=np.zeros(len(fr)), f_dp=dp, f_rho0=1.0,
+                   f_c0=2.0, f_eta=nu, w_r=np.concatenate([wb, wt]), w_n=np.concatenate([nb, nt]),
+                   w_dp=dp, s_r0=np.zeros((0, 2)), s_v0=np.zeros((0, 2)), s_n0=np.zeros((0, 2)),
+                   s_cons=np.zeros(0, np.uint8), s_dp=dp / 2)
+    s = O.OracleSim(case)
+    dt, _, _ = s.suggest_dt(vmax_f=Umax)
+    for _ in range(steps):
+        s.step(dt, 1)
+    return s, g, nu, H, Umax
+
+
+def test_plane_poiseuille_no_slip():
+    """Body-force driven flow between walls reaches the parabola
+    u = g y (H - y) / (2 nu) (ghost velocity 2 v~ - v_i, reading R6)."""
+    s, g, nu, H, Umax = _poiseuille_case(1000)
+    y, u = s.f_r[:, 1], s.f_v[:, 0]
+    rows = np.round(y / 0.001 - 0.5).astype(int)
+    for k in np.unique(rows):
+        sel = rows == k
+        ue = g * y[sel].mean() * (H - y[sel].mean()) / (2 * nu)
+        assert abs(u[sel].mean() - ue) < 0.025 * Umax
+    assert np.abs(s.f_v[:, 1]).max() < 1e-2 * Umax
+
+
+# --------------------------------------------------------------------------
+# Density reinitialisation (reading R16) and inflow (reading R18)
+# --------------------------------------------------------------------------
+
+def test_density_reinit_recovers_rho0_on_lattice():
+    case = fc.hydrostatic_column(W=0.04, H=0.04, dp=0.002)
+    case.f_p[:] = 0.0
+    case.f_v[:] = 0.0
+    case.gravity = (0.0, 0.0, 0.0)
+    case.free_surface = 0
+    case.n_reinit = 1
+    s = O.OracleSim(case)
+    s.f_rho[:] = 1234.0
+    s.step(1e-12, 1)
+    x, y = s.f_r[:, 0], s.f_r[:, 1]
+    hF = 1.3 * 0.002
+    inner = (x > 2 * hF) & (x < 0.04 - 2 * hF) & (y > 2 * hF) & (y < 0.04 - 2 * hF)
+    assert np.abs(s.f_rho[inner] / 1000.0 - 1.0).max() < 1e-9
+    # at the walls the wall particles complete the support
+    near = (x < 2 * hF) & (y > 2 * hF) & (y < 0.04 - 2 * hF)
+    assert np.abs(s.f_rho[near] / 1000.0 - 1.0).max() < 1e-9
+
+
+def test_inflow_profile_mean_and_ramp():
+    case = fc.channel_flag()
+    P = O.make_params(case)
+    H = case.inflow_H
+    mean, _ = integrate.quad(lambda y: O.lib().or_inflow_u(P, y, 10.0), 0.0, H)
+    assert abs(mean / H - 1.0) < 1e-12
+    assert abs(O.lib().or_inflow_u(P, H / 2, 10.0) - 1.5) < 1e-12
+    P.inflow_tramp = 2.0
+    assert abs(O.lib().or_inflow_u(P, H / 2, 1.0) - 0.75) < 1e-12   # half-way up the ramp
+    assert O.lib().or_inflow_u(P, H / 2, 0.0) == 0.0
