@@ -1,0 +1,206 @@
+/*
+ * sphfsi — GB300 (sm_103a) library for one coarse time step of the
+ * multi-resolution SPH fluid-structure interaction method of Zhang, Rezavand
+ * & Hu, "A multi-resolution SPH method for fluid-structure interactions"
+ * (arXiv 1911.13255).
+ *
+ * One step (sphfsi_step) is, in order (Section 3, Alg. 1):
+ *   a1  inflow buffer and fluid first half drift of rho and r
+ *       (Eq. verlet-first-half)
+ *   a2  cell-linked-list neighbour build (counting sort by cell), fluid grid
+ *       with cell edge >= 2 h_F; solid and wall particles binned in it
+ *   a3  every n_reinit steps: density reinitialisation from the number
+ *       density and solid normal update (Alg. 1, outer loop)
+ *   a4  equation of state (Eq. eqeos), fluid momentum with the Riemann
+ *       pressure and viscous terms at h_F plus the fluid-solid/wall ghost
+ *       forces (Eqs. fluid-model-mr-mom, fs-force-mr-sp, fs-force-mr-sv,
+ *       fs-coupling-mr) and the velocity kick (Eq. verlet-first-mediate)
+ *   a5  fluid force on the solid from the same pair terms (Eqs. F:p, F:v)
+ *   a6  fluid continuity (Eq. fluid-model-mr-con) and second half drift
+ *       (Eq. verlet-first-final)
+ *   a7  K solid sub-steps at h_S, dt_S = dt_F / K: corrected deformation
+ *       gradient, neo-Hookean PK1 stress and force loop, position-based
+ *       Verlet (Eqs. correctmatrix, solid-model-mr, Neo-Hookean-energy,
+ *       verlet-first-half-solid .. verlet-first-final-solid)
+ *   a8  time-averaged solid velocity and acceleration for the next step's
+ *       coupling (Eq. fs-coupling-mr), max-speed reductions for the next
+ *       time step (Eqs. dt-relax, dts-advection), FP64 momentum sums.
+ *
+ * Precision: pair loops in FP32; particle positions, solid displacement,
+ * the time-averaged sums and the momentum reductions in FP64.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success or a negative SPHFSI_E_* code; nothing aborts.
+ *   - Vectors are row-major n x dim, tensors n x dim x dim, in the caller's
+ *     original particle order (the library keeps the permutation).
+ *   - Array arguments may be host pointers or CUDA device pointers (unified
+ *     addressing decides); the caller owns them; the library copies.
+ *   - All work is issued on the stream given to sphfsi_create; getters and
+ *     sphfsi_sync wait for it.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef SPHFSI_H
+#define SPHFSI_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPHFSI_OK 0
+#define SPHFSI_E_INVAL (-1)    /* bad argument or out-of-range size         */
+#define SPHFSI_E_NOMEM (-2)    /* device allocation failed                   */
+#define SPHFSI_E_CUDA (-3)     /* a CUDA runtime call failed                 */
+#define SPHFSI_E_STATE (-4)    /* call out of order (e.g. step before finalize) */
+#define SPHFSI_E_UNSTABLE (-5) /* non-finite state detected on the device    */
+#define SPHFSI_E_TIMEOUT (-6)  /* a bounded device-side wait ran out         */
+#define SPHFSI_E_CAPACITY (-7) /* problem exceeds a documented device limit  */
+
+typedef struct sphfsi_ctx sphfsi_ctx;
+
+/* Global parameters.  gravity is an acceleration (body force per unit
+ * mass).  The fixed cell grid covers [domain_lo, domain_hi]; particles that
+ * leave it are clamped into the border cells (still correct, slower).
+ * periodic_x wraps fluid particles in x over [x_lo, x_lo + Lx); the grid's
+ * x extent is then that period.  free_surface selects the density
+ * reinitialisation rho = max(rho0 sigma / sigma0, rho0).  n_reinit is the
+ * cadence of density reinitialisation and normal update in steps (0 = off). */
+typedef struct {
+    int32_t dim; /* 2 or 3 */
+    int32_t periodic_x;
+    double gravity[3];
+    double x_lo, Lx;
+    int32_t free_surface;
+    int32_t n_reinit;
+    double domain_lo[3], domain_hi[3];
+} sphfsi_params;
+
+/* Velocity-imposing inflow buffer (Section 4.1): fluid particles with
+ * x in [x_lo, x_lo + width) get v = (U(y, t), 0, 0) at the start of a step.
+ * profile 0: U = 6 Ubar (y - y0)(H - (y - y0)) / H^2 (mean Ubar, clamped to
+ * [y0, y0 + H]); profile 1: uniform Ubar.  Ubar(t) = U (1 - cos(pi t /
+ * t_ramp)) / 2 for t < t_ramp, else U. */
+typedef struct {
+    int32_t on, profile;
+    double width, y0, H, U, t_ramp;
+} sphfsi_inflow;
+
+/* Per-context counters and last-step diagnostics. */
+typedef struct {
+    int64_t n_fluid, n_solid, n_wall, n_cells;
+    int64_t step;            /* completed steps                                  */
+    double t;                /* simulated time                                   */
+    double last_dt;          /* dt_F of the last step                            */
+    int32_t last_K;          /* solid sub-steps of the last step                 */
+    int32_t status;          /* device status bits of the last sync (0 = fine)   */
+    int64_t pairs_ff, pairs_fw, pairs_fs, pairs_sf; /* in-support pairs, last step */
+    int64_t pairs_ss;        /* static solid neighbour entries (per loop)        */
+    int64_t pairs_total;     /* all pair interactions since creation             */
+    double vmax_f, vmax_s, amax_s;  /* reductions of the last step               */
+    double mom_fs_fluid[3];  /* sum of fluid-side fluid-solid forces, last step  */
+    double mom_fs_solid[3];  /* sum of solid-side fluid forces, last step        */
+    int32_t solid_path;      /* 1 = cluster-resident sub-steps, 2 = cooperative grid */
+    int32_t kernels_per_step; /* this library's kernel launches per step        */
+} sphfsi_info;
+
+/* Create an empty context bound to a CUDA stream (cudaStream_t, may be 0
+ * for the legacy default stream) on the current device.  *out receives the
+ * context; the caller frees it with sphfsi_destroy. */
+int sphfsi_create(sphfsi_ctx **out, const sphfsi_params *p, void *cuda_stream);
+
+/* Fluid particles (Section 2.1): positions r (n x dim, FP64), velocities v
+ * (n x dim), initial pressure p_init (n; the density follows from the
+ * inverse of Eq. eqeos; NULL means rho = rho0), spacing dp (h_F = 1.3 dp,
+ * mass rho0 dp^dim), reference density rho0, sound speed c0, dynamic
+ * viscosity eta.  Called once, before sphfsi_finalize. */
+int sphfsi_add_fluid(sphfsi_ctx *c, int64_t n, const double *r, const double *v, const double *p_init,
+                     double dp, double rho0, double c0, double eta);
+
+/* Static wall particles (v = 0) with outward unit normals nrm pointing into
+ * the fluid, spacing dp (volume dp^dim).  Optional; once, before finalize. */
+int sphfsi_set_walls(sphfsi_ctx *c, int64_t n, const double *r, const double *nrm, double dp);
+
+/* One elastic body (Section 2.1, total Lagrangian, neo-Hookean): reference
+ * positions r0, initial velocities v0, outward unit normals n0 (solid ->
+ * fluid) in the reference configuration, constrained flags (1 = position
+ * fixed at r0, velocity 0), spacing dp (h_S = 1.3 dp, volume dp^dim),
+ * density rho0, Young's modulus E, Poisson ratio nu.  Optional; once. */
+int sphfsi_add_solid(sphfsi_ctx *c, int64_t n, const double *r0, const double *v0, const double *n0,
+                     const uint8_t *constrained, double dp, double rho0, double E, double nu);
+
+/* Inflow buffer (see sphfsi_inflow).  Optional; before finalize. */
+int sphfsi_set_inflow(sphfsi_ctx *c, const sphfsi_inflow *f);
+
+/* Build the device state: the solid's static reference neighbour list and
+ * correction matrices B0 (Eq. correctmatrix), F = I, the wall bins, the
+ * lattice number density sigma0 for reinitialisation. */
+int sphfsi_finalize(sphfsi_ctx *c);
+
+/* Fix the number of solid sub-steps K per fluid step (K >= 1), or 0 for
+ * the paper's kappa = [dt_F / dt_S] + 1 from the previous step's maxima
+ * (Section 3.2).  SPHFSI_E_INVAL for K < 0. */
+int sphfsi_set_substeps(sphfsi_ctx *c, int32_t K);
+
+/* One coarse step a1..a8.  dt_F > 0 fixes the step; dt_F <= 0 uses the
+ * acoustic criterion 0.6 h_F / (c0 + |v|max) (Eq. dt-relax) from the
+ * previous step's maximum fluid speed.  Asynchronous on the context stream;
+ * errors detected on the device surface at the next sphfsi_sync. */
+int sphfsi_step(sphfsi_ctx *c, double dt_F);
+
+/* nsteps steps replayed from one captured CUDA graph of a step (the first
+ * call captures it); same semantics as nsteps calls of sphfsi_step. */
+int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F);
+
+/* Wait for the stream; return SPHFSI_E_UNSTABLE / SPHFSI_E_TIMEOUT if the
+ * device flagged a non-finite state or a bounded wait ran out. */
+int sphfsi_sync(sphfsi_ctx *c);
+
+/* Fluid state in original order: r (n x dim FP64), v (n x dim FP32),
+ * rho (n FP64: rho0 plus the FP32 deviation the library stores), drho_dt
+ * (n FP32, the last density rate), dvdt (n x dim
+ * FP32, the last step's accelerations, a4).  Any pointer may be NULL. */
+int sphfsi_get_fluid(sphfsi_ctx *c, double *r, float *v, double *rho, float *drho_dt, float *dvdt);
+
+/* Solid state in original order: r (FP64), v (FP32), F (n x dim x dim
+ * FP64: I plus the FP32 displacement gradient the library stores), vbar and abar (FP64, the time averages of the last step), fF (the
+ * fluid force of the last step, FP32), nrm (current normals, FP32). */
+int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar, double *abar, float *fF,
+                     float *nrm);
+
+/* Overwrite the dynamic state (original order, FP64 inputs; NULL keeps a
+ * field).  Used for checkpoint/resume and for parity at a given state. */
+int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, const double *rho,
+                           const double *drho_dt);
+int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, const double *F,
+                           const double *vbar, const double *abar, const double *nrm);
+int sphfsi_set_time(sphfsi_ctx *c, double t, int64_t step);
+
+int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out);
+
+/* Neighbour sets from the device cell list at the current positions with the
+ * FP64 in-support test r^2 < (2 h_F)^2 (dx*dx + dy*dy (+ dz*dz), no FMA).
+ * which: 0 fluid-fluid, 1 fluid-wall, 2 fluid-solid, 3 solid-fluid.
+ * Two-phase: with idx == NULL, *nnz receives the total count and ptr
+ * (n_rows + 1, may be NULL) the row offsets; then call again with idx of
+ * *nnz entries.  Rows in original order, columns sorted ascending. */
+int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx, int64_t *nnz);
+
+/* Per-stage device timing.  With on != 0 every later step records CUDA
+ * events on the context stream at its stage boundaries (also inside the
+ * captured graph of sphfsi_run).  sphfsi_stage_times waits for the stream
+ * and writes the durations in ms of the last step's 8 stages into ms[0..7]:
+ * 0 control + solid binning, 1 fluid drift + binning + sort, 2 density
+ * reinitialisation, 3 momentum (a4), 4 solid-side coupling force (a5),
+ * 5 continuity + drift (a6), 6 solid sub-steps (a7, a8), 7 finish.
+ * Returns the number of stages, SPHFSI_E_INVAL if n < 8, SPHFSI_E_STATE if
+ * profiling is off. */
+int sphfsi_set_profiling(sphfsi_ctx *c, int on);
+int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n);
+
+void sphfsi_destroy(sphfsi_ctx *c);
+const char *sphfsi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

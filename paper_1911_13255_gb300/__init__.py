@@ -1,0 +1,296 @@
+"""GB300-native multi-resolution SPH fluid-structure interaction (arXiv 1911.13255).
+
+Thin ctypes binding over the C-ABI library ``libsphfsi.so`` (include/sphfsi.h).
+Every step of the method runs in the library's CUDA kernels; this module only
+marshals arguments.  There is no CPU fallback: if the library cannot be
+built or loaded, importing :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["lib", "Simulation", "SphError", "library_path"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {lib().sphfsi_strerror(code).decode()} ({code})")
+
+
+class Params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("periodic_x", C.c_int32), ("gravity", C.c_double * 3),
+                ("x_lo", C.c_double), ("Lx", C.c_double), ("free_surface", C.c_int32),
+                ("n_reinit", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3)]
+
+
+class Inflow(C.Structure):
+    _fields_ = [("on", C.c_int32), ("profile", C.c_int32), ("width", C.c_double), ("y0", C.c_double),
+                ("H", C.c_double), ("U", C.c_double), ("t_ramp", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_fluid", C.c_int64), ("n_solid", C.c_int64), ("n_wall", C.c_int64), ("n_cells", C.c_int64),
+                ("step", C.c_int64), ("t", C.c_double), ("last_dt", C.c_double), ("last_K", C.c_int32),
+                ("status", C.c_int32), ("pairs_ff", C.c_int64), ("pairs_fw", C.c_int64),
+                ("pairs_fs", C.c_int64), ("pairs_sf", C.c_int64), ("pairs_ss", C.c_int64),
+                ("pairs_total", C.c_int64), ("vmax_f", C.c_double), ("vmax_s", C.c_double),
+                ("amax_s", C.c_double), ("mom_fs_fluid", C.c_double * 3), ("mom_fs_solid", C.c_double * 3),
+                ("solid_path", C.c_int32), ("kernels_per_step", C.c_int32)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["mom_fs_fluid"] = np.array(self.mom_fs_fluid[:])
+        d["mom_fs_solid"] = np.array(self.mom_fs_solid[:])
+        return d
+
+
+_vp = C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "sphfsi_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Params), _vp]),
+    "sphfsi_add_fluid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "sphfsi_set_walls": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_double]),
+    "sphfsi_add_solid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double,
+                                   C.c_double]),
+    "sphfsi_set_inflow": (C.c_int, [_vp, C.POINTER(Inflow)]),
+    "sphfsi_finalize": (C.c_int, [_vp]),
+    "sphfsi_set_substeps": (C.c_int, [_vp, C.c_int32]),
+    "sphfsi_step": (C.c_int, [_vp, C.c_double]),
+    "sphfsi_run": (C.c_int, [_vp, C.c_int64, C.c_double]),
+    "sphfsi_sync": (C.c_int, [_vp]),
+    "sphfsi_get_fluid": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sphfsi_get_solid": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sphfsi_set_fluid_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sphfsi_set_solid_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sphfsi_set_time": (C.c_int, [_vp, C.c_double, C.c_int64]),
+    "sphfsi_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
+    "sphfsi_debug_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_int64)]),
+    "sphfsi_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "sphfsi_stage_times": (C.c_int, [_vp, _vp, C.c_int]),
+    "sphfsi_destroy": (None, [_vp]),
+    "sphfsi_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if stale) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise SphError(rc, what)
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def _f64(a, shape=None):
+    if hasattr(a, "data_ptr"):   # torch tensor (host, pinned or device): passed through
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous()
+        return a if shape is None else a.reshape(shape)
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a if shape is None else a.reshape(shape)
+
+
+class Simulation:
+    """One FSI problem on the current CUDA device (see include/sphfsi.h)."""
+
+    def __init__(self, dim, gravity=(0, 0, 0), periodic_x=0, x_lo=0.0, Lx=0.0, free_surface=0,
+                 n_reinit=0, domain_lo=(0, 0, 0), domain_hi=(1, 1, 1), stream=None):
+        L = lib()
+        p = Params()
+        p.dim, p.periodic_x, p.x_lo, p.Lx = dim, int(periodic_x), float(x_lo), float(Lx)
+        p.free_surface, p.n_reinit = int(free_surface), int(n_reinit)
+        for k in range(3):
+            p.gravity[k] = float(gravity[k]) if k < len(gravity) else 0.0
+            p.domain_lo[k] = float(domain_lo[k]) if k < len(domain_lo) else 0.0
+            p.domain_hi[k] = float(domain_hi[k]) if k < len(domain_hi) else 1.0
+        if stream is None:
+            st = 0
+        elif isinstance(stream, int):
+            st = stream
+        else:
+            st = stream.cuda_stream
+        self._stream = stream
+        h = _vp()
+        _check(L.sphfsi_create(C.byref(h), C.byref(p), st), "sphfsi_create")
+        self.h = h
+        self.dim = dim
+        self.nf = self.ns = self.nw = 0
+        self._keep = []
+
+    # --- set-up -----------------------------------------------------------
+    def add_fluid(self, r, v, p_init, dp, rho0, c0, eta):
+        r, v = _f64(r), _f64(v)
+        p = None if p_init is None else _f64(p_init)
+        self.nf = len(r)
+        _check(lib().sphfsi_add_fluid(self.h, self.nf, _ptr(r), _ptr(v), _ptr(p), dp, rho0, c0, eta),
+               "sphfsi_add_fluid")
+
+    def set_walls(self, r, nrm, dp):
+        r, nrm = _f64(r), _f64(nrm)
+        self.nw = len(r)
+        _check(lib().sphfsi_set_walls(self.h, self.nw, _ptr(r), _ptr(nrm), dp), "sphfsi_set_walls")
+
+    def add_solid(self, r0, v0, n0, constrained, dp, rho0, E, nu):
+        r0, v0, n0 = _f64(r0), _f64(v0), _f64(n0)
+        cons = np.ascontiguousarray(np.asarray(constrained, np.uint8))
+        self.ns = len(r0)
+        _check(lib().sphfsi_add_solid(self.h, self.ns, _ptr(r0), _ptr(v0), _ptr(n0), _ptr(cons), dp, rho0, E,
+                                      nu), "sphfsi_add_solid")
+
+    def set_inflow(self, on, profile, width, y0, H, U, t_ramp):
+        f = Inflow(int(on), int(profile), float(width), float(y0), float(H), float(U), float(t_ramp))
+        _check(lib().sphfsi_set_inflow(self.h, C.byref(f)), "sphfsi_set_inflow")
+
+    def finalize(self):
+        _check(lib().sphfsi_finalize(self.h), "sphfsi_finalize")
+        return self
+
+    @classmethod
+    def from_case(cls, case, stream=None):
+        """Build from any object with the attributes of a test/bench case."""
+        s = cls(case.dim, case.gravity, case.periodic_x, case.x_lo, case.Lx, case.free_surface,
+                case.n_reinit, case.domain_lo, case.domain_hi, stream=stream)
+        s.add_fluid(case.f_r, case.f_v, case.f_p, case.f_dp, case.f_rho0, case.f_c0, case.f_eta)
+        if case.nw:
+            s.set_walls(case.w_r, case.w_n, case.w_dp)
+        if case.ns:
+            s.add_solid(case.s_r0, case.s_v0, case.s_n0, case.s_cons, case.s_dp, case.s_rho0, case.s_E,
+                        case.s_nu)
+        if case.inflow_on:
+            s.set_inflow(1, case.inflow_profile, case.inflow_width, case.inflow_y0, case.inflow_H,
+                         case.inflow_U, case.inflow_tramp)
+        return s.finalize()
+
+    # --- stepping ---------------------------------------------------------
+    def set_substeps(self, K):
+        _check(lib().sphfsi_set_substeps(self.h, int(K)), "sphfsi_set_substeps")
+
+    def step(self, dt=0.0):
+        _check(lib().sphfsi_step(self.h, float(dt)), "sphfsi_step")
+
+    def run(self, nsteps, dt=0.0):
+        _check(lib().sphfsi_run(self.h, int(nsteps), float(dt)), "sphfsi_run")
+
+    def sync(self):
+        _check(lib().sphfsi_sync(self.h), "sphfsi_sync")
+
+    # --- state ------------------------------------------------------------
+    def get_fluid(self):
+        d, n = self.dim, self.nf
+        r = np.zeros((n, d))
+        v = np.zeros((n, d), np.float32)
+        rho = np.zeros(n)
+        rd = np.zeros(n, np.float32)
+        a = np.zeros((n, d), np.float32)
+        _check(lib().sphfsi_get_fluid(self.h, _ptr(r), _ptr(v), _ptr(rho), _ptr(rd), _ptr(a)),
+               "sphfsi_get_fluid")
+        return dict(r=r, v=v, rho=rho, drho=rd, dvdt=a)
+
+    def get_solid(self):
+        d, n = self.dim, self.ns
+        r = np.zeros((n, d))
+        v = np.zeros((n, d), np.float32)
+        F = np.zeros((n, d, d))
+        vb = np.zeros((n, d))
+        ab = np.zeros((n, d))
+        fF = np.zeros((n, d), np.float32)
+        nrm = np.zeros((n, d), np.float32)
+        _check(lib().sphfsi_get_solid(self.h, _ptr(r), _ptr(v), _ptr(F), _ptr(vb), _ptr(ab), _ptr(fF),
+                                      _ptr(nrm)), "sphfsi_get_solid")
+        return dict(r=r, v=v, F=F, vbar=vb, abar=ab, fF=fF, nrm=nrm)
+
+    def get_solid_positions(self, out):
+        """Solid positions into a caller buffer (numpy host array or CUDA tensor), n x dim FP64."""
+        _check(lib().sphfsi_get_solid(self.h, _ptr(out), None, None, None, None, None, None),
+               "sphfsi_get_solid")
+        return out
+
+    def set_fluid_state(self, r=None, v=None, rho=None, drho=None):
+        args = [None if x is None else _f64(x) for x in (r, v, rho, drho)]
+        _check(lib().sphfsi_set_fluid_state(self.h, *[_ptr(x) for x in args]), "sphfsi_set_fluid_state")
+
+    def set_solid_state(self, r=None, v=None, F=None, vbar=None, abar=None, nrm=None):
+        args = [None if x is None else _f64(x) for x in (r, v, F, vbar, abar, nrm)]
+        _check(lib().sphfsi_set_solid_state(self.h, *[_ptr(x) for x in args]), "sphfsi_set_solid_state")
+
+    def set_time(self, t, step):
+        _check(lib().sphfsi_set_time(self.h, float(t), int(step)), "sphfsi_set_time")
+
+    def info(self):
+        i = Info()
+        _check(lib().sphfsi_get_info(self.h, C.byref(i)), "sphfsi_get_info")
+        return i.as_dict()
+
+    STAGES = ("control+solid_bin", "fluid_bin_sort", "reinit", "momentum", "solid_fluid_force",
+              "continuity", "solid_substeps", "finish")
+
+    def set_profiling(self, on=True):
+        _check(lib().sphfsi_set_profiling(self.h, int(bool(on))), "sphfsi_set_profiling")
+
+    def stage_times(self):
+        """Device ms of the last step's stages (needs set_profiling(True))."""
+        ms = np.zeros(8, np.float32)
+        rc = lib().sphfsi_stage_times(self.h, _ptr(ms), 8)
+        if rc < 0:
+            _check(rc, "sphfsi_stage_times")
+        return dict(zip(self.STAGES, ms.tolist()))
+
+    def debug_neighbors(self, which):
+        """(ptr, idx) neighbour CSR in original order with the FP64 support test."""
+        nrows = self.ns if which == 3 else self.nf
+        nnz = C.c_int64()
+        ptr = np.zeros(nrows + 1, np.int64)
+        _check(lib().sphfsi_debug_neighbors(self.h, which, _ptr(ptr), None, C.byref(nnz)),
+               "sphfsi_debug_neighbors")
+        idx = np.zeros(max(nnz.value, 1), np.int64)
+        _check(lib().sphfsi_debug_neighbors(self.h, which, _ptr(ptr), _ptr(idx), C.byref(nnz)),
+               "sphfsi_debug_neighbors")
+        return ptr, idx[:nnz.value]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sphfsi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,237 @@
+// Internal device data structures and helpers of the sphfsi library.
+// Method: Zhang, Rezavand & Hu, multi-resolution SPH for FSI (arXiv 1911.13255).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+// device status bits (Ctl::status)
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+constexpr int kBlock = 128;           // threads per block of the particle kernels
+constexpr int kSolidBlock = 256;      // threads per block of the solid sub-step kernel
+constexpr long long kSpinLimit = 1ll << 22;   // bounded spin of the grid barrier (~0.5-2 s)
+
+// Fixed uniform cell grid with cell edge >= 2 h_F (support radius).  Linear
+// cell index = x + nc[0] * (y + nc[1] * z).
+struct Grid {
+    double lo[3];
+    double cs[3];    // cell edges (FP64), cs[0] = Lx / nc[0] when periodic in x
+    float csf[3];    // the same edges rounded to FP32 (pair-loop offsets)
+    int nc[3];
+    int ncell;
+    int periodic_x;
+    double x_lo, Lx;
+};
+
+// Device-resident control block: one per context, read by every kernel of a
+// step, so a captured step graph needs no host-side values.
+struct Ctl {
+    double t;          // time at the start of the current step
+    double dt;         // dt_F of the current step
+    double dts;        // dt_S = dt_F / K
+    double dt_fixed;   // > 0: fixed dt_F
+    long long step;    // index of the current step
+    int K;             // solid sub-steps of the current step
+    int K_fixed;       // > 0: fixed K
+    int reinit;        // this step reinitialises density and normals
+    int n_reinit;
+    int status;        // ST_* bits, sticky until read by the host
+    int pad0;
+    unsigned vmaxF, vmaxS, amaxS, pad1;      // maxima of the current step (float bits)
+    float prev_vmaxF, prev_vmaxS, prev_amaxS, pad2;
+    double mom_fluid[3], mom_solid[3];       // FP64 fluid-solid momentum sums
+    unsigned long long n_ff, n_fw, n_fs, n_sf;
+    unsigned long long pairs_total;
+    double last_dt;
+    int last_K, pad3;
+};
+
+// Physical constants of the fluid, the walls and the solid (by value).
+struct Phys {
+    int dim;
+    float g[3];
+    // fluid
+    float rho0, c0, eta, hF, inv_hF, rc2F;   // rc2F = (2 h_F)^2 in FP32
+    float WcF;        // alpha_d(h_F): W = WcF (1 - q/2)^4 (1 + 2q)
+    float dWcF;       // -5 alpha_d(h_F) / h_F: dW/dr = dWcF q (1 - q/2)^3
+    float mF;         // rho0 dp_F^d
+    float p_coef;     // rho0 c0^2 / 7
+    float inv_p_coef;
+    float hreg;       // 0.01 h_F, viscous regularisation of the fluid-solid force
+    float sigma0;     // lattice number density at h_F / dp_F = 1.3
+    float VW, VS;     // wall and solid particle volumes
+    float VW_VF, VS_VF;   // volume ratios for the number density
+    int free_surface;
+    double rc2F_d;    // (2 h_F)^2 in FP64 (debug neighbour sets)
+    double hF_d, c0_d, eta_d, rho0_d;
+    double alphaF_d, sigma0_d, VW_VF_d, VS_VF_d;   // FP64 number density
+    // solid
+    float rhoS, mS, mu, lam, hS;
+    double hS_d, cS_d;
+    // inflow
+    int inflow_on, inflow_profile;
+    double in_w, in_y0, in_H, in_U, in_tramp;
+};
+
+// Fluid state, storage order = cell order of the last binning.
+struct FluidState {
+    double *x, *y, *z;
+    float *vx, *vy, *vz;
+    float *drho;      // rho - rho0
+    float *rhodot;    // density rate of the last step (reading R12)
+    int *id;          // original index
+};
+
+struct Fluid {
+    int n;
+    FluidState s[2];
+    int cur;
+    float4 *P4;       // (x - x_cell, y - y_cell, z - z_cell, p)   sorted records
+    float4 *V4;       // (v^n, rho - rho0)
+    float4 *W4;       // (v^{n+1}, rho - rho0)
+    float *dvdt;      // n * dim, sorted order (a4 accelerations)
+    int *key;         // cell of each particle (storage order)
+    int *perm;        // sorted slot -> storage index
+    int *cell_of;     // cell of each sorted slot
+    int *cstart;      // ncell + 1
+    int *ccount;      // ncell (histogram / scatter cursor)
+};
+
+// Static walls, binned once.
+struct Walls {
+    int n;
+    double *x, *y, *z;     // original order
+    float *nx, *ny, *nz;
+    float4 *A4;            // (rel position, 0) sorted
+    float4 *N4;            // (normal, 0) sorted
+    int *key, *perm, *cstart, *ccount, *cell_of;
+};
+
+// Elastic body (original order) + its records in the fluid grid.
+struct Solid {
+    int n;
+    int nnz;
+    double *x, *y, *z;        // current positions (FP64)
+    double *x0, *y0, *z0;     // reference positions
+    double *xs, *ys, *zs;     // positions at the start of the step
+    float4 *v4;               // velocity (vx, vy, vz, 0)
+    float *H;                 // n * 9 displacement gradient F - I (row-major, dim x dim used)
+    float *Hd;                // n * 9 dF/dt of the last evaluation
+    float *B0;                // n * 9
+    float4 *Q4;               // P B0 (2-D: one float4; 3-D: three float4 rows)
+    float *n0;                // n * 3 reference normals
+    float *nrm;               // n * 3 current normals
+    uint8_t *cons;
+    double *vbar, *abar;      // n * 3 time averages (FP64)
+    double *asum;             // n * 3 sum of dt_S a over the sub-steps (FP64)
+    float *fF;                // n * 3 fluid force of the step
+    int *nb_ptr;              // n + 1
+    float4 *nb;               // nnz: (V0 grad0_a W_ab, b as int bits in .w)
+    // records in the fluid grid (sorted by cell)
+    float4 *A4, *VB4, *AB4, *N4;
+    int *key, *perm, *cstart, *ccount, *cell_of;
+    unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned fbits(float f) { return __float_as_uint(f); }
+
+__device__ __forceinline__ void atomic_max_pos(unsigned *addr, float v)
+{
+    // non-negative floats order like their bit patterns; NaN (0x7fc...) wins
+    atomicMax(addr, __float_as_uint(fabsf(v)));
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ unsigned warp_sum_u(unsigned v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// cell coordinates of a position (FP64, clamped into the grid)
+__device__ __forceinline__ int cell_coord(double x, double lo, double cs, int n)
+{
+    int c = (int)floor((x - lo) / cs);
+    return c < 0 ? 0 : (c >= n ? n - 1 : c);
+}
+
+// Tait pressure from rho - rho0 (Eq. eqeos), cancellation-free in FP32:
+// p = rho0 c^2 / 7 * expm1(7 log1p(drho / rho0))
+__device__ __forceinline__ float eos_p(float drho, const Phys &P)
+{
+    return P.p_coef * expm1f(7.0f * log1pf(drho / P.rho0));
+}
+// inverse (ghost density), rho = rho0 (1 + p / p_coef)^(1/7)
+__device__ __forceinline__ float eos_rho(float p, const Phys &P)
+{
+    return P.rho0 * expf(log1pf(p * P.inv_p_coef) * (1.0f / 7.0f));
+}
+
+// Wendland C2 derivative dW/dr at h_F (Section 4); caller guarantees q < 2
+__device__ __forceinline__ float dW_F(float r, const Phys &P)
+{
+    float q = r * P.inv_hF;
+    float a = 1.0f - 0.5f * q;
+    return P.dWcF * q * a * a * a;
+}
+__device__ __forceinline__ float W_F(float r, const Phys &P)
+{
+    float q = r * P.inv_hF;
+    float a = 1.0f - 0.5f * q;
+    float a2 = a * a;
+    return P.WcF * a2 * a2 * (1.0f + 2.0f * q);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch wrappers (implemented in the .cu files)
+// ---------------------------------------------------------------------------
+int launch_control(Ctl *ctl, const Phys &P, int has_solid, cudaStream_t st);
+int launch_finish(Ctl *ctl, unsigned long long ss_pairs_per_step, cudaStream_t st);
+
+// binning / counting sort (sph_grid.cu)
+int launch_fluid_drift_bin(const Fluid &f, const Grid &g, const Phys &P, Ctl *ctl, int do_drift,
+                           cudaStream_t st);
+int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);
+int launch_scatter(const int *key, const int *cstart, int *ccount, int *perm, int n, cudaStream_t st);
+int launch_fluid_reorder(Fluid &f, const Grid &g, const Phys &P, cudaStream_t st);
+int launch_wall_bin(Walls &w, const Grid &g, cudaStream_t st);
+int launch_solid_bin(Solid &s, const Grid &g, const Phys &P, Ctl *ctl, cudaStream_t st);
+int launch_solid_normals(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st);
+
+// fluid pair loops (sph_fluid.cu)
+int launch_reinit(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
+                  cudaStream_t st);
+int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
+                    cudaStream_t st);
+int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
+                             cudaStream_t st);
+int launch_density(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
+                   cudaStream_t st);
+int launch_debug_pairs(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, int which,
+                       int *counts, int *offs, int *out, cudaStream_t st);
+
+// solid (sph_solid.cu)
+int launch_solid_setup_count(Solid &s, const Phys &P, int *counts, cudaStream_t st);
+int launch_solid_setup_fill(Solid &s, const Phys &P, cudaStream_t st);
+int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStream_t st);
+
+}  // namespace sph

@@ -1,0 +1,433 @@
+// Total-Lagrangian elastic solid at h_S (Sections 2.2, 3.1, 3.3).
+//
+// Set-up (once): the static reference neighbour list (the solid keeps its
+// reference configuration's neighbours), the corrected reference kernel
+// gradients V0 grad0_a W_ab and the correction matrices
+// B0_a = (sum_b V_b (r0_b - r0_a) (x) grad0_a W_ab)^-1 (Eq. correctmatrix with
+// the neighbour volume, reading R8), all in FP64 then rounded to FP32.
+//
+// Sub-steps (every coarse step, K of them, dt_S = dt_F / K): one persistent
+// kernel.  Per sub-step: (A) half drift of the displacement gradient and the
+// position, neo-Hookean PK1 stress Q = P B0; (B) force loop and kick;
+// (C) deformation rate dF/dt = [sum_b V_b (v_b - v_a) (x) grad0 W_ab] B0 and
+// the second half drift (Eqs. verlet-first-half-solid ..
+// verlet-first-final-solid, solid-model-mr).  Phases that read other
+// particles' data are separated by a grid-wide barrier whose spin is
+// bounded: on time-out the kernel records ST_TIMEOUT and returns.
+//
+// The deformation gradient is stored as H = F - I (FP32) so that small
+// strains keep their precision: E = (H + H^T + H^T H) / 2, ln J =
+// log1p(det(I + H) - 1), S = C^-1 (2 mu E + lambda ln J I).
+#include "sph_common.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ double dW_solid_d(double r, double h, int D)
+{
+    const double pi = 3.14159265358979323846;
+    double alpha = D == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
+    double q = r / h;
+    if (q >= 2.0) return 0.0;
+    double a = 1.0 - 0.5 * q;
+    return -5.0 * alpha / h * q * a * a * a;
+}
+
+__device__ __forceinline__ double r2_d(double dx, double dy, double dz, int D)
+{
+    double r2 = __dmul_rn(dx, dx);
+    r2 = __dadd_rn(r2, __dmul_rn(dy, dy));
+    if (D == 3) r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+    return r2;
+}
+
+template <int D>
+__global__ void k_solid_count(Solid s, Phys P, int *counts)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    double rc2 = 4.0 * P.hS_d * P.hS_d;
+    double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
+    int c = 0;
+    for (int b = 0; b < s.n; b++) {
+        if (b == a) continue;
+        double dz = D == 3 ? za - s.z0[b] : 0.0;
+        if (r2_d(xa - s.x0[b], ya - s.y0[b], dz, D) < rc2) c++;
+    }
+    counts[a] = c;
+}
+
+template <int D>
+__global__ void k_solid_fill(Solid s, Phys P)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const double h = P.hS_d;
+    const double rc2 = 4.0 * h * h;
+    const double V0 = D == 2 ? (P.VS) : (P.VS);
+    double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
+    double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int q = s.nb_ptr[a];
+    for (int b = 0; b < s.n; b++) {
+        if (b == a) continue;
+        double d[3] = {xa - s.x0[b], ya - s.y0[b], D == 3 ? za - s.z0[b] : 0.0};
+        double r2 = r2_d(d[0], d[1], d[2], D);
+        if (!(r2 < rc2)) continue;
+        double r = sqrt(r2);
+        double dW = dW_solid_d(r, h, D);
+        double g[3] = {dW * d[0] / r, dW * d[1] / r, D == 3 ? dW * d[2] / r : 0.0};   // grad0_a W_ab
+        for (int i = 0; i < D; i++)
+            for (int j = 0; j < D; j++) M[i * D + j] += V0 * (-d[i]) * g[j];          // (r0_b - r0_a) (x) grad
+        s.nb[q++] = make_float4((float)(V0 * g[0]), (float)(V0 * g[1]), (float)(V0 * g[2]), __int_as_float(b));
+    }
+    double Bi[9];
+    if (D == 2) {
+        double det = M[0] * M[3] - M[1] * M[2];
+        Bi[0] = M[3] / det;
+        Bi[1] = -M[1] / det;
+        Bi[2] = -M[2] / det;
+        Bi[3] = M[0] / det;
+    } else {
+        double det = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                     M[2] * (M[3] * M[7] - M[4] * M[6]);
+        Bi[0] = (M[4] * M[8] - M[5] * M[7]) / det;
+        Bi[1] = (M[2] * M[7] - M[1] * M[8]) / det;
+        Bi[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+        Bi[3] = (M[5] * M[6] - M[3] * M[8]) / det;
+        Bi[4] = (M[0] * M[8] - M[2] * M[6]) / det;
+        Bi[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+        Bi[6] = (M[3] * M[7] - M[4] * M[6]) / det;
+        Bi[7] = (M[1] * M[6] - M[0] * M[7]) / det;
+        Bi[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+    }
+    for (int i = 0; i < 9; i++) {
+        s.B0[9 * a + i] = i < D * D ? (float)Bi[i] : 0.0f;
+        s.H[9 * a + i] = 0.0f;
+        s.Hd[9 * a + i] = 0.0f;
+    }
+}
+
+int launch_solid_setup_count(Solid &s, const Phys &P, int *counts, cudaStream_t st)
+{
+    if (s.n == 0) return 0;
+    int nb = (s.n + kBlock - 1) / kBlock;
+    if (P.dim == 2) k_solid_count<2><<<nb, kBlock, 0, st>>>(s, P, counts);
+    else k_solid_count<3><<<nb, kBlock, 0, st>>>(s, P, counts);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_solid_setup_fill(Solid &s, const Phys &P, cudaStream_t st)
+{
+    if (s.n == 0) return 0;
+    int nb = (s.n + kBlock - 1) / kBlock;
+    if (P.dim == 2) k_solid_fill<2><<<nb, kBlock, 0, st>>>(s, P);
+    else k_solid_fill<3><<<nb, kBlock, 0, st>>>(s, P);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ---------------------------------------------------------------------------
+// grid-wide barrier with a bounded spin (cooperative launch guarantees that
+// all blocks are resident); returns false after a time-out
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned prev = atomicAdd(bar, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > kSpinLimit) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// neo-Hookean PK1 times B0 from H = F - I (Eqs. Neo-Hookean-energy, 2rd-PK)
+template <int D>
+__device__ __forceinline__ void stress_QB(const float *H, const float *B, float mu, float lam, float *Q)
+{
+    if (D == 2) {
+        float h00 = H[0], h01 = H[1], h10 = H[2], h11 = H[3];
+        float E00 = h00 + 0.5f * (h00 * h00 + h10 * h10);
+        float E11 = h11 + 0.5f * (h01 * h01 + h11 * h11);
+        float E01 = 0.5f * (h01 + h10 + h00 * h01 + h10 * h11);
+        float C00 = 1.0f + 2.0f * E00, C11 = 1.0f + 2.0f * E11, C01 = 2.0f * E01;
+        float idet = 1.0f / (C00 * C11 - C01 * C01);
+        float Ci00 = C11 * idet, Ci11 = C00 * idet, Ci01 = -C01 * idet;
+        float lnJ = log1pf(h00 + h11 + h00 * h11 - h01 * h10);
+        float T00 = 2.0f * mu * E00 + lam * lnJ, T11 = 2.0f * mu * E11 + lam * lnJ, T01 = 2.0f * mu * E01;
+        float S00 = Ci00 * T00 + Ci01 * T01, S01 = Ci00 * T01 + Ci01 * T11;
+        float S10 = Ci01 * T00 + Ci11 * T01, S11 = Ci01 * T01 + Ci11 * T11;
+        float P00 = S00 + h00 * S00 + h01 * S10, P01 = S01 + h00 * S01 + h01 * S11;
+        float P10 = S10 + h10 * S00 + h11 * S10, P11 = S11 + h10 * S01 + h11 * S11;
+        Q[0] = P00 * B[0] + P01 * B[2];
+        Q[1] = P00 * B[1] + P01 * B[3];
+        Q[2] = P10 * B[0] + P11 * B[2];
+        Q[3] = P10 * B[1] + P11 * B[3];
+    } else {
+        float E[9], C[9], Ci[9], T[9], S[9], Pm[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                float hh = 0.0f;
+                for (int k = 0; k < 3; k++) hh += H[k * 3 + i] * H[k * 3 + j];
+                E[i * 3 + j] = 0.5f * (H[i * 3 + j] + H[j * 3 + i] + hh);
+                C[i * 3 + j] = (i == j ? 1.0f : 0.0f) + 2.0f * E[i * 3 + j];
+            }
+        float c00 = C[4] * C[8] - C[5] * C[7], c01 = C[2] * C[7] - C[1] * C[8], c02 = C[1] * C[5] - C[2] * C[4];
+        float c10 = C[5] * C[6] - C[3] * C[8], c11 = C[0] * C[8] - C[2] * C[6], c12 = C[2] * C[3] - C[0] * C[5];
+        float c20 = C[3] * C[7] - C[4] * C[6], c21 = C[1] * C[6] - C[0] * C[7], c22 = C[0] * C[4] - C[1] * C[3];
+        float idet = 1.0f / (C[0] * c00 + C[1] * c10 + C[2] * c20);
+        Ci[0] = c00 * idet; Ci[1] = c01 * idet; Ci[2] = c02 * idet;
+        Ci[3] = c10 * idet; Ci[4] = c11 * idet; Ci[5] = c12 * idet;
+        Ci[6] = c20 * idet; Ci[7] = c21 * idet; Ci[8] = c22 * idet;
+        // det(I + H) - 1 = tr H + principal 2x2 minors + det H
+        float trH = H[0] + H[4] + H[8];
+        float m2 = H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7];
+        float dH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                   H[2] * (H[3] * H[7] - H[4] * H[6]);
+        float lnJ = log1pf(trH + m2 + dH);
+        for (int i = 0; i < 9; i++) T[i] = 2.0f * mu * E[i] + ((i % 4) == 0 ? lam * lnJ : 0.0f);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                float v = 0.0f;
+                for (int k = 0; k < 3; k++) v += Ci[i * 3 + k] * T[k * 3 + j];
+                S[i * 3 + j] = v;
+            }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                float v = S[i * 3 + j];
+                for (int k = 0; k < 3; k++) v += H[i * 3 + k] * S[k * 3 + j];
+                Pm[i * 3 + j] = v;
+            }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                float v = 0.0f;
+                for (int k = 0; k < 3; k++) v += Pm[i * 3 + k] * B[k * 3 + j];
+                Q[i * 3 + j] = v;
+            }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void store_Q(float4 *Q4, int a, const float *Q)
+{
+    if (D == 2) {
+        Q4[a] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+    } else {
+        Q4[3 * a + 0] = make_float4(Q[0], Q[1], Q[2], 0.0f);
+        Q4[3 * a + 1] = make_float4(Q[3], Q[4], Q[5], 0.0f);
+        Q4[3 * a + 2] = make_float4(Q[6], Q[7], Q[8], 0.0f);
+    }
+}
+
+// dH/dt = [sum_b (v_b - v_a) (x) (V0 grad0_a W_ab)] B0_a   (reading R9)
+template <int D>
+__device__ __forceinline__ void deformation_rate(const Solid &s, int a, const float4 va, float *Hd)
+{
+    float M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
+    for (int q = q0; q < q1; q++) {
+        float4 e = s.nb[q];
+        int b = __float_as_int(e.w);
+        float4 vb = __ldcg(&s.v4[b]);
+        float dv[3] = {vb.x - va.x, vb.y - va.y, vb.z - va.z};
+        float g[3] = {e.x, e.y, e.z};
+        for (int i = 0; i < D; i++)
+            for (int j = 0; j < D; j++) M[i * D + j] += dv[i] * g[j];
+    }
+    const float *B = s.B0 + 9 * a;
+    for (int i = 0; i < D; i++)
+        for (int j = 0; j < D; j++) {
+            float v = 0.0f;
+            for (int k = 0; k < D; k++) v += M[i * D + k] * B[k * D + j];
+            Hd[i * D + j] = v;
+        }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Solid s, Phys P, Ctl *ctl)
+{
+    const int K = ctl->K;
+    const double dt = ctl->dt, dtsd = ctl->dts;
+    const float dts = (float)dtsd, hdts = 0.5f * dts;
+    const double hdtsd = 0.5 * dtsd;
+    const int G = gridDim.x * blockDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const float inv_rhoS = 1.0f / P.rhoS, inv_mS = 1.0f / P.mS;
+    float vmax = 0.0f, amax = 0.0f;
+
+    // start of step: save r^n, clear the acceleration sum, dH/dt(v^0)
+    for (int a = tid; a < s.n; a += G) {
+        s.xs[a] = s.x[a];
+        s.ys[a] = s.y[a];
+        if (D == 3) s.zs[a] = s.z[a];
+        s.asum[3 * a] = s.asum[3 * a + 1] = s.asum[3 * a + 2] = 0.0;
+        float Hd[9];
+        deformation_rate<D>(s, a, __ldcg(&s.v4[a]), Hd);
+        float *H = s.H + 9 * a;
+        for (int i = 0; i < D * D; i++) {
+            s.Hd[9 * a + i] = Hd[i];
+            H[i] = H[i] + hdts * Hd[i];           // first half drift of sub-step 0
+        }
+        if (!s.cons[a]) {
+            float4 v = __ldcg(&s.v4[a]);
+            s.x[a] = s.x[a] + hdtsd * (double)v.x;
+            s.y[a] = s.y[a] + hdtsd * (double)v.y;
+            if (D == 3) s.z[a] = s.z[a] + hdtsd * (double)v.z;
+        }
+        float Q[9];
+        stress_QB<D>(H, s.B0 + 9 * a, P.mu, P.lam, Q);
+        store_Q<D>(s.Q4, a, Q);
+    }
+    for (int kk = 0; kk < K; kk++) {
+        if (!grid_barrier(s.bar, &ctl->status)) return;
+        // (B) force loop and kick (Eqs. solid-model-mr, verlet-first-mediate-solid)
+        for (int a = tid; a < s.n; a += G) {
+            float acc[3] = {0.f, 0.f, 0.f};
+            float Qa[9];
+            if (D == 2) {
+                float4 q = __ldcg(&s.Q4[a]);
+                Qa[0] = q.x; Qa[1] = q.y; Qa[2] = q.z; Qa[3] = q.w;
+            } else {
+                for (int r = 0; r < 3; r++) {
+                    float4 q = __ldcg(&s.Q4[3 * a + r]);
+                    Qa[3 * r] = q.x; Qa[3 * r + 1] = q.y; Qa[3 * r + 2] = q.z;
+                }
+            }
+            int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
+            for (int q = q0; q < q1; q++) {
+                float4 e = s.nb[q];
+                int b = __float_as_int(e.w);
+                if (D == 2) {
+                    float4 qb = __ldcg(&s.Q4[b]);
+                    acc[0] += (Qa[0] + qb.x) * e.x + (Qa[1] + qb.y) * e.y;
+                    acc[1] += (Qa[2] + qb.z) * e.x + (Qa[3] + qb.w) * e.y;
+                } else {
+                    for (int r = 0; r < 3; r++) {
+                        float4 qb = __ldcg(&s.Q4[3 * b + r]);
+                        acc[r] += (Qa[3 * r] + qb.x) * e.x + (Qa[3 * r + 1] + qb.y) * e.y + (Qa[3 * r + 2] + qb.z) * e.z;
+                    }
+                }
+            }
+            if (!s.cons[a]) {
+                float4 v = __ldcg(&s.v4[a]);
+                float av[3];
+                for (int k = 0; k < D; k++) av[k] = acc[k] * inv_rhoS + s.fF[3 * a + k] * inv_mS + P.g[k];
+                v.x += dts * av[0];
+                v.y += dts * av[1];
+                if (D == 3) v.z += dts * av[2];
+                s.v4[a] = v;
+                float a2 = 0.0f;
+                for (int k = 0; k < D; k++) {
+                    s.asum[3 * a + k] += dtsd * (double)av[k];
+                    a2 += av[k] * av[k];
+                }
+                amax = fmaxf(amax, a2);
+                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+        }
+        if (!grid_barrier(s.bar, &ctl->status)) return;
+        // (C) deformation rate at v^{k+1}, second half drift; then the first
+        // half drift of the next sub-step and its stress
+        const bool more = kk + 1 < K;
+        for (int a = tid; a < s.n; a += G) {
+            float4 v = __ldcg(&s.v4[a]);
+            float Hd[9];
+            deformation_rate<D>(s, a, v, Hd);
+            float *H = s.H + 9 * a;
+            float Hl[9];
+            for (int i = 0; i < D * D; i++) {
+                Hl[i] = H[i] + hdts * Hd[i];
+                if (more) Hl[i] = Hl[i] + hdts * Hd[i];
+                H[i] = Hl[i];
+                s.Hd[9 * a + i] = Hd[i];
+            }
+            if (!s.cons[a]) {
+                double x = s.x[a] + hdtsd * (double)v.x;
+                double y = s.y[a] + hdtsd * (double)v.y;
+                double z = D == 3 ? s.z[a] + hdtsd * (double)v.z : 0.0;
+                if (more) {
+                    x = x + hdtsd * (double)v.x;
+                    y = y + hdtsd * (double)v.y;
+                    if (D == 3) z = z + hdtsd * (double)v.z;
+                }
+                s.x[a] = x;
+                s.y[a] = y;
+                if (D == 3) s.z[a] = z;
+            }
+            if (more) {
+                float Q[9];
+                stress_QB<D>(Hl, s.B0 + 9 * a, P.mu, P.lam, Q);
+                store_Q<D>(s.Q4, a, Q);
+            }
+        }
+    }
+    // a8: time averages as exact means of the discrete trajectory (reading R14)
+    const double idt = 1.0 / dt;
+    for (int a = tid; a < s.n; a += G) {
+        s.vbar[3 * a] = (s.x[a] - s.xs[a]) * idt;
+        s.vbar[3 * a + 1] = (s.y[a] - s.ys[a]) * idt;
+        s.vbar[3 * a + 2] = D == 3 ? (s.z[a] - s.zs[a]) * idt : 0.0;
+        for (int k = 0; k < 3; k++) s.abar[3 * a + k] = s.asum[3 * a + k] * idt;
+    }
+    float vm = warp_max(vmax), am = warp_max(amax);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
+        atomic_max_pos(&ctl->amaxS, sqrtf(am));
+    }
+}
+
+int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStream_t st)
+{
+    if (s.n == 0) return 0;
+    static int max_blocks[2] = {0, 0};
+    int di = P.dim == 2 ? 0 : 1;
+    if (max_blocks[di] == 0) {
+        int dev, nsm, per;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (P.dim == 2)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solid_substeps<2>, kSolidBlock, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solid_substeps<3>, kSolidBlock, 0);
+        max_blocks[di] = per * nsm;
+    }
+    int nb = (s.n + kSolidBlock - 1) / kSolidBlock;
+    if (nb > max_blocks[di]) nb = max_blocks[di];
+    if (nb < 1) return -3;
+    cudaMemsetAsync(s.bar, 0, sizeof(unsigned), st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kSolidBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (P.dim == 2) e = cudaLaunchKernelEx(&cfg, k_solid_substeps<2>, s, P, ctl);
+    else e = cudaLaunchKernelEx(&cfg, k_solid_substeps<3>, s, P, ctl);
+    if (path) *path = 2;
+    return e == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace sph
