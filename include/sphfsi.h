@@ -197,6 +197,34 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
 int sphfsi_set_profiling(sphfsi_ctx *c, int on);
 int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n);
 
+/* Allocation-free neighbour counting.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (a framework's
+ * caching allocator owns the device memory, a latency-critical loop cannot
+ * take the implicit synchronisation of cudaMalloc/cudaFree, or plug-in code
+ * that is only handed input and output buffers).  It allocates nothing.
+ *
+ * For each of the n points r (device pointer, n x dim FP64, row-major) it
+ * writes to counts (device pointer, n int32) the number of other points j
+ * with |r_i - r_j|^2 < (2 h)^2, h = 1.3 dp, computed in FP64 as dx*dx + dy*dy
+ * (+ dz*dz) with the minimal image in x when p->periodic_x (the same test as
+ * sphfsi_debug_neighbors).  The cell grid follows p (dim, domain box,
+ * periodic x) exactly as a context built from p would.  Work is issued on
+ * cuda_stream and is asynchronous.
+ *
+ * Scratch (cell keys, the permutation, the cell histogram) is one
+ * file-scope device array sized for at most SPHFSI_NOALLOC_MAX_PARTICLES
+ * points and SPHFSI_NOALLOC_MAX_CELLS cells (about 4 MB per GPU, held by
+ * every GPU that loads the library until the process exits); larger inputs
+ * return SPHFSI_E_CAPACITY.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race:
+ * serialise them.  Returns SPHFSI_E_INVAL for bad arguments. */
+#define SPHFSI_NOALLOC_MAX_PARTICLES (1 << 18)
+#define SPHFSI_NOALLOC_MAX_CELLS (1 << 18)
+int sphfsi_neighbor_counts_noalloc(const sphfsi_params *p, int64_t n, const double *r, double dp, int32_t *counts,
+                                   void *cuda_stream);
+
 void sphfsi_destroy(sphfsi_ctx *c);
 const char *sphfsi_strerror(int code);
 

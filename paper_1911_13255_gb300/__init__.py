@@ -78,6 +78,7 @@ _SIGS = {
     "sphfsi_debug_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_int64)]),
     "sphfsi_set_profiling": (C.c_int, [_vp, C.c_int]),
     "sphfsi_stage_times": (C.c_int, [_vp, _vp, C.c_int]),
+    "sphfsi_neighbor_counts_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, _vp, C.c_double, _vp, _vp]),
     "sphfsi_destroy": (None, [_vp]),
     "sphfsi_strerror": (C.c_char_p, [C.c_int]),
 }
