@@ -77,7 +77,9 @@ _SIGS = {
     "sphfsi_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
     "sphfsi_debug_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_int64)]),
     "sphfsi_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "sphfsi_set_solid_path": (C.c_int, [_vp, C.c_int]),
     "sphfsi_stage_times": (C.c_int, [_vp, _vp, C.c_int]),
+    "sphfsi_step_time": (C.c_int, [_vp, _vp]),
     "sphfsi_neighbor_counts_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, _vp, C.c_double, _vp, _vp]),
     "sphfsi_destroy": (None, [_vp]),
     "sphfsi_strerror": (C.c_char_p, [C.c_int]),
@@ -262,6 +264,10 @@ class Simulation:
     STAGES = ("control+solid_bin", "fluid_bin_sort", "reinit", "momentum", "solid_fluid_force",
               "continuity", "solid_substeps", "finish")
 
+    def set_solid_path(self, path):
+        """0 automatic (cluster-resident when the body fits), 2 cooperative grid."""
+        _check(lib().sphfsi_set_solid_path(self.h, int(path)), "sphfsi_set_solid_path")
+
     def set_profiling(self, on=True):
         _check(lib().sphfsi_set_profiling(self.h, int(bool(on))), "sphfsi_set_profiling")
 
@@ -272,6 +278,12 @@ class Simulation:
         if rc < 0:
             _check(rc, "sphfsi_stage_times")
         return dict(zip(self.STAGES, ms.tolist()))
+
+    def step_time(self):
+        """Device ms of the whole last step (needs set_profiling(True))."""
+        ms = np.zeros(1, np.float32)
+        _check(lib().sphfsi_step_time(self.h, _ptr(ms)), "sphfsi_step_time")
+        return float(ms[0])
 
     def debug_neighbors(self, which):
         """(ptr, idx) neighbour CSR in original order with the FP64 support test."""

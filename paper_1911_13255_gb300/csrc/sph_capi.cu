@@ -44,12 +44,19 @@ struct sphfsi_ctx {
     int solid_path = 0;
     unsigned long long ss_pairs = 0;
     int last_status = 0;
-    // per-stage CUDA events (sphfsi_set_profiling)
+    // per-stage CUDA events (sphfsi_set_profiling): start, solid binned,
+    // fluid sorted, reinit, momentum, solid-side force, continuity (main
+    // stream), solid sub-steps begin/end (side stream), end of step
     static constexpr int kStages = 8;
+    static constexpr int kEvents = 10;
     bool profiling = false;
     int graph_prof = -1;
-    cudaEvent_t ev[kStages + 1] = {};
+    cudaEvent_t ev[kEvents] = {};
     int kernels_per_step = 0;
+    // side stream for the solid sub-steps, which run concurrently with the
+    // continuity kernel (both need only the coupling force and the records)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -148,11 +155,12 @@ __global__ void k_set_step(Ctl *ctl, double dt_fixed, int K_fixed)
 
 // stage boundary: an event record when profiling (captured as an event node
 // inside a graph thanks to cudaEventRecordExternal)
-int mark(sphfsi_ctx *c, int k)
+int mark(sphfsi_ctx *c, int k, cudaStream_t st)
 {
     if (!c->profiling) return SPHFSI_OK;
-    return cuda_rc(cudaEventRecordWithFlags(c->ev[k], c->st, cudaEventRecordExternal));
+    return cuda_rc(cudaEventRecordWithFlags(c->ev[k], st, cudaEventRecordExternal));
 }
+int mark(sphfsi_ctx *c, int k) { return mark(c, k, c->st); }
 
 int enqueue_step(sphfsi_ctx *c, double dt)
 {
@@ -177,13 +185,20 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(mark(c, 4));
     TRY(launch_solid_fluid_force(c->F, c->S, c->g, c->P, c->ctl, st));
     TRY(mark(c, 5));
+    // a7 + a8 on the side stream, a6 on the main stream, joined before finish
+    if (c->S.n) {
+        TRY(cuda_rc(cudaEventRecord(c->fork_ev, st)));
+        TRY(cuda_rc(cudaStreamWaitEvent(c->side, c->fork_ev, 0)));
+        TRY(mark(c, 7, c->side));
+        TRY(launch_solid_substeps(c->S, c->P, c->ctl, &c->solid_path, c->side));
+        TRY(mark(c, 8, c->side));
+        TRY(cuda_rc(cudaEventRecord(c->join_ev, c->side)));
+    }
     TRY(launch_density(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
     TRY(mark(c, 6));
-    // a7 + a8
-    TRY(launch_solid_substeps(c->S, c->P, c->ctl, &c->solid_path, st));
-    TRY(mark(c, 7));
+    if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
     TRY(launch_finish(c->ctl, c->ss_pairs, st));
-    TRY(mark(c, 8));
+    TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
     c->kernels_per_step = 11 + (c->S.n ? 8 : 0);
     return cuda_rc(cudaGetLastError());
@@ -589,7 +604,10 @@ int sphfsi_finalize(sphfsi_ctx *c)
         }
     }
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    for (int k = 0; k <= sphfsi_ctx::kStages; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
+    for (int k = 0; k < sphfsi_ctx::kEvents; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
+    TRY(cuda_rc(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)));
+    TRY(cuda_rc(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)));
+    TRY(cuda_rc(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming)));
     c->finalized = true;
     // release the host staging copies
     c->f_r.clear(); c->f_v.clear(); c->f_p.clear();
@@ -984,6 +1002,18 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
     return rc;
 }
 
+int sphfsi_set_solid_path(sphfsi_ctx *c, int path)
+{
+    TRY(check_ctx(c, true));
+    if (path < 0 || path > 2) return SPHFSI_E_INVAL;
+    c->S.force_grid_path = path == 2 ? 1 : 0;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SPHFSI_OK;
+}
+
 int sphfsi_set_profiling(sphfsi_ctx *c, int on)
 {
     TRY(check_ctx(c, true));
@@ -997,8 +1027,28 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     if (!ms || n < sphfsi_ctx::kStages) return SPHFSI_E_INVAL;
     if (!c->profiling) return SPHFSI_E_STATE;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    for (int k = 0; k < sphfsi_ctx::kStages; k++) TRY(cuda_rc(cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1])));
+    auto el = [&](int a, int b, float *out) { return cuda_rc(cudaEventElapsedTime(out, c->ev[a], c->ev[b])); };
+    for (int k = 0; k < 6; k++) TRY(el(k, k + 1, &ms[k]));   // main-stream stages up to continuity
+    if (c->S.n) {
+        float fin_a = 0.f, fin_b = 0.f;
+        TRY(el(7, 8, &ms[6]));                                 // solid sub-steps (side stream)
+        TRY(el(6, 9, &fin_a));
+        TRY(el(8, 9, &fin_b));
+        ms[7] = fin_a < fin_b ? fin_a : fin_b;                 // finish, after the join
+    } else {
+        ms[6] = 0.0f;
+        TRY(el(6, 9, &ms[7]));
+    }
     return sphfsi_ctx::kStages;
+}
+
+int sphfsi_step_time(sphfsi_ctx *c, float *ms)
+{
+    TRY(check_ctx(c, true));
+    if (!ms) return SPHFSI_E_INVAL;
+    if (!c->profiling) return SPHFSI_E_STATE;
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    return cuda_rc(cudaEventElapsedTime(ms, c->ev[0], c->ev[9]));
 }
 
 void sphfsi_destroy(sphfsi_ctx *c)
@@ -1007,8 +1057,12 @@ void sphfsi_destroy(sphfsi_ctx *c)
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    for (int k = 0; k <= sphfsi_ctx::kStages; k++)
+    if (c->side) cudaStreamSynchronize(c->side);
+    for (int k = 0; k < sphfsi_ctx::kEvents; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     for (void *p : c->allocs) cudaFree(p);
     delete c;
 }

@@ -133,6 +133,7 @@ struct Solid {
     float4 *A4, *VB4, *AB4, *N4;
     int *key, *perm, *cstart, *ccount, *cell_of;
     unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
+    int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
 };
 
 // ---------------------------------------------------------------------------

@@ -395,9 +395,283 @@ __global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Solid s, Phys P,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Cluster-resident variant for bodies of up to kClusterMax * kPPC particles:
+// one thread-block cluster holds the whole body.  Each CTA owns kPPC
+// consecutive particles; their stress Q = P B0 and velocity live in the
+// CTA's shared memory, and neighbours owned by other CTAs of the cluster are
+// read through distributed shared memory.  kLanes consecutive threads share
+// one particle's neighbour list and reduce with warp shuffles; the group's
+// first lane keeps the particle's state (H, B0, FP64 position and sums) in
+// registers for all K sub-steps.  Phases are separated by the hardware
+// cluster barrier (no spin loop in this kernel).
+// ---------------------------------------------------------------------------
+constexpr int kCThreads = 512;
+constexpr int kLanes = 4;
+constexpr int kPPC = kCThreads / kLanes;
+constexpr int kClusterMax = 16;
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// generic address of the same shared-memory variable in CTA `rank` of the cluster
+template <typename T>
+__device__ __forceinline__ const T *dsmem(const T *p, unsigned rank)
+{
+    uint64_t in = reinterpret_cast<uint64_t>(p), out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(in), "r"(rank));
+    return reinterpret_cast<const T *>(out);
+}
+
+__device__ __forceinline__ float group_sum(float v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ctl *ctl)
+{
+    constexpr int QR = D == 3 ? 3 : 1;   // float4 rows of Q per particle
+    __shared__ float4 sQ[kPPC * QR];
+    __shared__ float4 sV[kPPC];
+    const unsigned rank = cluster_rank();
+    const int g = threadIdx.x / kLanes, lane = threadIdx.x % kLanes;
+    const int a = (int)rank * kPPC + g;
+    const bool own = a < s.n;
+    const int K = ctl->K;
+    const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
+    const float dts = (float)dtsd, hdts = 0.5f * dts;
+    const float inv_rhoS = 1.0f / P.rhoS, inv_mS = 1.0f / P.mS;
+
+    float H[9], B[9], fF[3] = {0.f, 0.f, 0.f};
+    double x = 0, y = 0, z = 0, xs = 0, ys = 0, zs = 0, as[3] = {0, 0, 0};
+    bool cons = true;
+    float vmax = 0.0f, amax = 0.0f;
+    int q0 = 0, q1 = 0;
+    if (own) {
+        q0 = s.nb_ptr[a];
+        q1 = s.nb_ptr[a + 1];
+        if (lane == 0) {
+            for (int i = 0; i < D * D; i++) {
+                H[i] = s.H[9 * a + i];
+                B[i] = s.B0[9 * a + i];
+            }
+            for (int k = 0; k < D; k++) fF[k] = s.fF[3 * a + k];
+            x = xs = s.x[a];
+            y = ys = s.y[a];
+            if (D == 3) z = zs = s.z[a];
+            cons = s.cons[a] != 0;
+            sV[g] = s.v4[a];
+        }
+    }
+    cluster_sync();
+
+    // dH/dt over this particle's neighbours at the velocities in sV (DSMEM)
+    auto rate = [&](float4 va, float *Hd) {
+        float M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int q = q0 + lane; q < q1; q += kLanes) {
+            float4 e = __ldg(&s.nb[q]);
+            int b = __float_as_int(e.w);
+            float4 vb = *dsmem(&sV[b % kPPC], (unsigned)(b / kPPC));
+            float dv[3] = {vb.x - va.x, vb.y - va.y, vb.z - va.z};
+            float ge[3] = {e.x, e.y, e.z};
+            for (int i = 0; i < D; i++)
+                for (int j = 0; j < D; j++) M[i * D + j] += dv[i] * ge[j];
+        }
+        for (int i = 0; i < D * D; i++) M[i] = group_sum(M[i]);
+        for (int i = 0; i < D; i++)
+            for (int j = 0; j < D; j++) {
+                float v = 0.0f;
+                for (int k = 0; k < D; k++) v += M[i * D + k] * B[k * D + j];
+                Hd[i * D + j] = v;
+            }
+    };
+    auto put_Q = [&]() {
+        float Q[9];
+        stress_QB<D>(H, B, P.mu, P.lam, Q);
+        if (D == 2) {
+            sQ[g] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        } else {
+            for (int r = 0; r < 3; r++) sQ[3 * g + r] = make_float4(Q[3 * r], Q[3 * r + 1], Q[3 * r + 2], 0.0f);
+        }
+    };
+
+    // All threads run the neighbour loops (empty for groups past the end of
+    // the body) so that the full-warp shuffles of group_sum see every lane;
+    // only the owning lane of a group updates state and shared memory.
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // start of step: dH/dt(v^0), first half drift of sub-step 0, stress
+    {
+        float4 va = own ? sV[g] : zero4;
+        float Hd[9];
+        rate(va, Hd);
+        if (own && lane == 0) {
+            for (int i = 0; i < D * D; i++) H[i] = H[i] + hdts * Hd[i];
+            if (!cons) {
+                x = x + hdtsd * (double)va.x;
+                y = y + hdtsd * (double)va.y;
+                if (D == 3) z = z + hdtsd * (double)va.z;
+            }
+            put_Q();
+        }
+    }
+    for (int kk = 0; kk < K; kk++) {
+        cluster_sync();
+        // (B) force loop and kick
+        {
+            float Qa[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (own) {
+                if (D == 2) {
+                    float4 t = sQ[g];
+                    Qa[0] = t.x; Qa[1] = t.y; Qa[2] = t.z; Qa[3] = t.w;
+                } else {
+                    for (int r = 0; r < 3; r++) {
+                        float4 t = sQ[3 * g + r];
+                        Qa[3 * r] = t.x; Qa[3 * r + 1] = t.y; Qa[3 * r + 2] = t.z;
+                    }
+                }
+            }
+            float acc[3] = {0.f, 0.f, 0.f};
+            for (int q = q0 + lane; q < q1; q += kLanes) {
+                float4 e = __ldg(&s.nb[q]);
+                int b = __float_as_int(e.w);
+                unsigned rb = (unsigned)(b / kPPC);
+                int lb = b % kPPC;
+                if (D == 2) {
+                    float4 qb = *dsmem(&sQ[lb], rb);
+                    acc[0] += (Qa[0] + qb.x) * e.x + (Qa[1] + qb.y) * e.y;
+                    acc[1] += (Qa[2] + qb.z) * e.x + (Qa[3] + qb.w) * e.y;
+                } else {
+                    for (int r = 0; r < 3; r++) {
+                        float4 qb = *dsmem(&sQ[3 * lb + r], rb);
+                        acc[r] += (Qa[3 * r] + qb.x) * e.x + (Qa[3 * r + 1] + qb.y) * e.y + (Qa[3 * r + 2] + qb.z) * e.z;
+                    }
+                }
+            }
+            for (int k = 0; k < D; k++) acc[k] = group_sum(acc[k]);
+            if (own && lane == 0 && !cons) {
+                float4 v = sV[g];
+                float av[3];
+                for (int k = 0; k < D; k++) av[k] = acc[k] * inv_rhoS + fF[k] * inv_mS + P.g[k];
+                v.x += dts * av[0];
+                v.y += dts * av[1];
+                if (D == 3) v.z += dts * av[2];
+                sV[g] = v;
+                float a2 = 0.0f;
+                for (int k = 0; k < D; k++) {
+                    as[k] += dtsd * (double)av[k];
+                    a2 += av[k] * av[k];
+                }
+                amax = fmaxf(amax, a2);
+                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
+            }
+        }
+        cluster_sync();
+        // (C) deformation rate at v^{k+1}; second half drift; next first half + stress
+        {
+            const bool more = kk + 1 < K;
+            float4 va = own ? sV[g] : zero4;
+            float Hd[9];
+            rate(va, Hd);
+            if (own && lane == 0) {
+                for (int i = 0; i < D * D; i++) {
+                    H[i] = H[i] + hdts * Hd[i];
+                    if (more) H[i] = H[i] + hdts * Hd[i];
+                }
+                if (!cons) {
+                    x = x + hdtsd * (double)va.x;
+                    y = y + hdtsd * (double)va.y;
+                    if (D == 3) z = z + hdtsd * (double)va.z;
+                    if (more) {
+                        x = x + hdtsd * (double)va.x;
+                        y = y + hdtsd * (double)va.y;
+                        if (D == 3) z = z + hdtsd * (double)va.z;
+                    }
+                }
+                if (more) put_Q();
+            }
+        }
+    }
+    // write back; a8 time averages (reading R14)
+    if (own && lane == 0) {
+        for (int i = 0; i < D * D; i++) s.H[9 * a + i] = H[i];
+        s.v4[a] = sV[g];
+        s.x[a] = x;
+        s.y[a] = y;
+        if (D == 3) s.z[a] = z;
+        const double idt = 1.0 / dt;
+        s.vbar[3 * a] = (x - xs) * idt;
+        s.vbar[3 * a + 1] = (y - ys) * idt;
+        s.vbar[3 * a + 2] = D == 3 ? (z - zs) * idt : 0.0;
+        for (int k = 0; k < 3; k++) s.abar[3 * a + k] = as[k] * idt;
+    }
+    float vm = warp_max(vmax), am = warp_max(amax);
+    if ((threadIdx.x & 31) == 0 && own) {
+        atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
+        atomic_max_pos(&ctl->amaxS, sqrtf(am));
+    }
+    // no CTA may exit while others can still read its shared memory
+    cluster_sync();
+}
+
+static int launch_solid_cluster(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st)
+{
+    int nctas = (s.n + kPPC - 1) / kPPC;
+    if (nctas > kClusterMax) return 1;
+    static int feasible[2][kClusterMax + 1] = {};   // 0 unknown, 1 yes, -1 no
+    int di = P.dim == 2 ? 0 : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nctas);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (feasible[di][nctas] == 0) {
+        int nclu = 0;
+        cudaError_t e;
+        if (P.dim == 2) {
+            cudaFuncSetAttribute(k_solid_cluster<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster<2>, &cfg);
+        } else {
+            cudaFuncSetAttribute(k_solid_cluster<3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster<3>, &cfg);
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        feasible[di][nctas] = (e == cudaSuccess && nclu >= 1) ? 1 : -1;
+    }
+    if (feasible[di][nctas] < 0) return 1;
+    cudaError_t e;
+    if (P.dim == 2) e = cudaLaunchKernelEx(&cfg, k_solid_cluster<2>, s, P, ctl);
+    else e = cudaLaunchKernelEx(&cfg, k_solid_cluster<3>, s, P, ctl);
+    return e == cudaSuccess ? 0 : -3;
+}
+
 int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStream_t st)
 {
     if (s.n == 0) return 0;
+    if (!s.force_grid_path) {
+        int rc = launch_solid_cluster(s, P, ctl, st);
+        if (rc <= 0) {
+            if (path) *path = 1;
+            return rc;
+        }
+    }
     static int max_blocks[2] = {0, 0};
     int di = P.dim == 2 ? 0 : 1;
     if (max_blocks[di] == 0) {

@@ -77,10 +77,11 @@ def _dt_K(ref):
     return dt, ref.substeps(dt, dts)
 
 
-def _one_step(case):
+def _one_step(case, solid_path=0):
     ref = O.OracleSim(case)
     dt, K = _dt_K(ref)
     sim = Simulation.from_case(case)
+    sim.set_solid_path(solid_path)
     sim.set_substeps(K)
     sim.step(dt)
     sim.sync()
@@ -88,11 +89,14 @@ def _one_step(case):
     return sim, ref, dt
 
 
+@pytest.mark.parametrize("solid_path", [0, 2], ids=["cluster", "grid"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_one_step_parity(name):
+def test_one_step_parity(name, solid_path):
     case = CASES[name]()
     s_r_start = np.array(case.s_r0, dtype=np.float64)
-    sim, ref, dt = _one_step(case)
+    sim, ref, dt = _one_step(case, solid_path)
+    if case.ns:
+        assert sim.info()["solid_path"] == (1 if solid_path == 0 else 2)
     g, s = sim.get_fluid(), sim.get_solid()
     e = {
         "dvdt": rel(g["dvdt"], ref.f_dvdt),
