@@ -32,6 +32,12 @@
  *   R16 density reinitialisation from the number density
  *   R17 normals n = normalize(F^-T n0)
  *   R18 inflow buffer + periodic x
+ *
+ * Parity unpinned: the exact limiter of the Riemann solver (R4) beyond its
+ * tested properties (equal-state averages, exchange symmetry, compression
+ * dissipation), the inflow/outflow buffer mechanism (R18) and the normal
+ * update (R17) have no independent pin; everything else is pinned by the
+ * tests in tests/test_oracle_pins.py.
  */
 #include <math.h>
 #include <stdint.h>
