@@ -44,7 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 FLOP_PER_PAIR = {"momentum": 55.0, "continuity": 30.0, "solid_fluid_force": 60.0, "reinit": 12.0}
 FLOP_SOLID_PAIR = 22.0        # force (12) + deformation rate (10) per static solid pair per sub-step
 FLOP_SOLID_PARTICLE = 80.0    # neo-Hookean stress + Verlet updates per particle per sub-step
-BYTES_PER_FLUID_PARTICLE = {"fluid_bin_sort": 90.0, "momentum": 48.0, "continuity": 64.0}
+BYTES_PER_FLUID_PARTICLE = {"bin_sort": 90.0, "momentum": 48.0, "continuity": 64.0}
 
 
 def _peaks():
@@ -240,7 +240,7 @@ def run_gpu(args, rank, world, local_rank):
     peaks, src = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     per_launch = {k: v / args.steps for k, v in stage_ms.items()}
-    kernels = {k: v for k, v in per_launch.items() if k not in ("finish", "control+solid_bin")}
+    kernels = {k: v for k, v in per_launch.items() if k not in ("finish", "control")}
     dom = max(kernels, key=kernels.get)
     nsteps = args.steps
     K = info1["last_K"]
@@ -255,12 +255,14 @@ def run_gpu(args, rank, world, local_rank):
         bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
         achieved = work / (per_launch[dom] * 1e-3) / 1e12
     else:
-        work = case.nf * BYTES_PER_FLUID_PARTICLE["fluid_bin_sort"]
+        work = case.nf * BYTES_PER_FLUID_PARTICLE["bin_sort"]
         bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
         achieved = work / (per_launch[dom] * 1e-3) / 1e9
-    kernel_names = {"solid_substeps": "k_solid_substeps", "momentum": "k_momentum", "continuity": "k_density",
+    solid_kernel = {1: "k_solid_cluster2d" if case.dim == 2 else "k_solid_cluster", 2: "k_solid_substeps"}.get(
+        info1["solid_path"], "k_solid_substeps")
+    kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
-                    "fluid_bin_sort": "k_fluid_reorder"}
+                    "bin_sort": "k_bin_all+k_scan2+k_scatter2+k_cellsort2+k_records_all"}
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": _traffic(kernel_names.get(dom, dom)), "kernel": kernel_names.get(dom, dom),
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,

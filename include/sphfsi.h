@@ -185,18 +185,22 @@ int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out);
  * *nnz entries.  Rows in original order, columns sorted ascending. */
 int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx, int64_t *nnz);
 
-/* Solid sub-step kernel selection: 0 automatic (the cluster-resident kernel
+/* Solid sub-step kernel selection: 0 automatic (a cluster-resident kernel
  * when the body fits one thread-block cluster of at most 16 CTAs x 128
- * particles and the device can launch it, else the cooperative grid
- * kernel), 2 always the cooperative grid kernel.  Both compute the same
- * sub-steps (Section 3.3); this exists to test and compare them. */
+ * particles and the device can launch it -- in 2-D with at most 24 static
+ * neighbours per particle the one-thread-per-particle variant, otherwise the
+ * four-lanes-per-particle variant -- else the cooperative grid kernel);
+ * 1 the four-lane cluster variant where it fits; 2 always the cooperative
+ * grid kernel.  All compute the same sub-steps (Section 3.3); the choice
+ * exists to test and compare them. */
 int sphfsi_set_solid_path(sphfsi_ctx *c, int path);
 
 /* Per-stage device timing.  With on != 0 every later step records CUDA
  * events on the context stream at its stage boundaries (also inside the
  * captured graph of sphfsi_run).  sphfsi_stage_times waits for the stream
  * and writes the durations in ms of the last step's 8 stages into ms[0..7]:
- * 0 control + solid binning, 1 fluid drift + binning + sort, 2 density
+ * 0 control + normal update, 1 fluid drift + fluid and solid binning and
+ * sort, 2 density
  * reinitialisation, 3 momentum (a4), 4 solid-side coupling force (a5),
  * 5 continuity + drift (a6), 6 solid sub-steps (a7, a8; they run on a
  * side stream concurrently with stage 5), 7 finish (after both).

@@ -261,7 +261,7 @@ class Simulation:
         _check(lib().sphfsi_get_info(self.h, C.byref(i)), "sphfsi_get_info")
         return i.as_dict()
 
-    STAGES = ("control+solid_bin", "fluid_bin_sort", "reinit", "momentum", "solid_fluid_force",
+    STAGES = ("control", "bin_sort", "reinit", "momentum", "solid_fluid_force",
               "continuity", "solid_substeps", "finish")
 
     def set_solid_path(self, path):

@@ -1,6 +1,7 @@
 // C-ABI of the sphfsi library (include/sphfsi.h): context, set-up, the
 // per-step launch sequence a1..a8 and its CUDA-graph replay, state I/O.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,6 +29,7 @@ struct sphfsi_ctx {
     double w_dp = 0;
     std::vector<double> s_r0, s_v0, s_n0;
     std::vector<uint8_t> s_cons;
+    std::vector<int> s_order;   // device (locality) index -> original solid index
     double s_dp = 0, s_rho0 = 1, s_E = 1, s_nu = 0.3;
     // device
     Grid g{};
@@ -166,16 +168,12 @@ int enqueue_step(sphfsi_ctx *c, double dt)
 {
     cudaStream_t st = c->st;
     TRY(mark(c, 0));
-    k_set_step<<<1, 1, 0, st>>>(c->ctl, dt > 0.0 ? dt : 0.0, c->K_fixed);
-    TRY(launch_control(c->ctl, c->P, c->S.n > 0, st));
-    // a3 (normals part) before the solid records are built
-    TRY(launch_solid_normals(c->S, c->P, c->ctl, st));
-    // a2: solid particles into the fluid grid at r^n
-    TRY(launch_solid_bin(c->S, c->g, c->P, c->ctl, st));
+    // dt_F, K, reinit flag; a3 normal update before the solid records are built
+    TRY(launch_control_normals(c->ctl, c->P, c->S, dt > 0.0 ? dt : 0.0, c->K_fixed, st));
     TRY(mark(c, 1));
-    // a1 + a2: inflow, first half drift, fluid binning and reorder
-    TRY(launch_fluid_drift_bin(c->F, c->g, c->P, c->ctl, 1, st));
-    TRY(launch_fluid_reorder(c->F, c->g, c->P, st));
+    // a1 + a2: inflow, fluid first half drift; fluid (r^{n+1/2}) and solid
+    // (r^n) binning, counting sort and FP32 records
+    TRY(launch_bin_all(c->F, c->S, c->g, c->P, c->ctl, 1, st));
     TRY(mark(c, 2));
     // a3: density reinitialisation (no-op on other steps)
     TRY(launch_reinit(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
@@ -200,7 +198,7 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_finish(c->ctl, c->ss_pairs, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
-    c->kernels_per_step = 11 + (c->S.n ? 8 : 0);
+    c->kernels_per_step = 10 + (c->S.n ? 2 : 0);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -561,6 +559,39 @@ int sphfsi_finalize(sphfsi_ctx *c)
         TRY(dalloc(c, &S.ccount, g.ncell));
         TRY(dalloc(c, &S.bar, 2));
         if (n > 0) {
+            // Locality order of the body on the device: lexicographic on the
+            // lattice index along the axes sorted by decreasing extent, so
+            // that a particle's neighbours sit within a few rows of it and
+            // mostly in the same CTA of the cluster-resident sub-step kernel.
+            {
+                double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                for (int a = 0; a < n; a++)
+                    for (int k = 0; k < D; k++) {
+                        lo[k] = std::min(lo[k], c->s_r0[(size_t)a * D + k]);
+                        hi[k] = std::max(hi[k], c->s_r0[(size_t)a * D + k]);
+                    }
+                int ax[3] = {0, 1, 2};
+                std::sort(ax, ax + D, [&](int p, int q) { return hi[p] - lo[p] > hi[q] - lo[q]; });
+                std::vector<std::array<long long, 4>> key(n);
+                for (int a = 0; a < n; a++) {
+                    for (int k = 0; k < 3; k++)
+                        key[a][k] = k < D ? std::llround((c->s_r0[(size_t)a * D + ax[k]] - lo[ax[k]]) / c->s_dp) : 0;
+                    key[a][3] = a;
+                }
+                std::sort(key.begin(), key.end());
+                c->s_order.resize(n);
+                for (int a = 0; a < n; a++) c->s_order[a] = (int)key[a][3];
+                auto perm_rows = [&](auto &v, int w) {
+                    auto t = v;
+                    for (int a = 0; a < n; a++)
+                        for (int j = 0; j < w; j++) t[(size_t)a * w + j] = v[(size_t)c->s_order[a] * w + j];
+                    v.swap(t);
+                };
+                perm_rows(c->s_r0, D);
+                perm_rows(c->s_v0, D);
+                perm_rows(c->s_n0, D);
+                perm_rows(c->s_cons, 1);
+            }
             std::vector<double> xyz[3];
             deinterleave(c->s_r0, D, c->ns, xyz);
             std::vector<float4> v4(n);
@@ -595,7 +626,11 @@ int sphfsi_finalize(sphfsi_ctx *c)
             std::vector<int> hc;
             TRY(download(c, hc, counts, n));
             std::vector<int> ptr(n + 1, 0);
-            for (int a = 0; a < n; a++) ptr[a + 1] = ptr[a] + hc[a];
+            S.max_nb = 0;
+            for (int a = 0; a < n; a++) {
+                ptr[a + 1] = ptr[a] + hc[a];
+                S.max_nb = std::max(S.max_nb, hc[a]);
+            }
             S.nnz = ptr[n];
             TRY(upload(c, S.nb_ptr, ptr));
             TRY(dalloc(c, &S.nb, S.nnz));
@@ -739,15 +774,17 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
     const Solid &S = c->S;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     if (n == 0) return SPHFSI_OK;
+    const std::vector<int> &ord = c->s_order;   // device index -> original index
     if (r) {
         std::vector<double> x, y, z, out(n * D);
         TRY(download(c, x, S.x, n));
         TRY(download(c, y, S.y, n));
         if (D == 3) TRY(download(c, z, S.z, n));
         for (int64_t a = 0; a < n; a++) {
-            out[a * D] = x[a];
-            out[a * D + 1] = y[a];
-            if (D == 3) out[a * D + 2] = z[a];
+            size_t o = (size_t)ord[a] * D;
+            out[o] = x[a];
+            out[o + 1] = y[a];
+            if (D == 3) out[o + 2] = z[a];
         }
         TRY(deliver(r, out));
     }
@@ -756,9 +793,10 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
         TRY(download(c, h, S.v4, n));
         std::vector<float> out(n * D);
         for (int64_t a = 0; a < n; a++) {
-            out[a * D] = h[a].x;
-            out[a * D + 1] = h[a].y;
-            if (D == 3) out[a * D + 2] = h[a].z;
+            size_t o = (size_t)ord[a] * D;
+            out[o] = h[a].x;
+            out[o + 1] = h[a].y;
+            if (D == 3) out[o + 2] = h[a].z;
         }
         TRY(deliver(v, out));
     }
@@ -767,7 +805,8 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
         std::vector<double> out(n * D * D);
         TRY(download(c, h, S.H, (size_t)9 * n));
         for (int64_t a = 0; a < n; a++)
-            for (int i = 0; i < D * D; i++) out[a * D * D + i] = (double)h[9 * a + i] + ((i % (D + 1)) == 0 ? 1.0 : 0.0);
+            for (int i = 0; i < D * D; i++)
+                out[(size_t)ord[a] * D * D + i] = (double)h[9 * a + i] + ((i % (D + 1)) == 0 ? 1.0 : 0.0);
         TRY(deliver(F, out));
     }
     auto vec3 = [&](const auto *src, auto *dst, auto zero) -> int {
@@ -777,7 +816,7 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
         int rc = download(c, h, src, (size_t)3 * n);
         if (rc) return rc;
         for (int64_t a = 0; a < n; a++)
-            for (int k = 0; k < D; k++) out[a * D + k] = h[3 * a + k];
+            for (int k = 0; k < D; k++) out[(size_t)ord[a] * D + k] = h[3 * a + k];
         return deliver(dst, out);
     };
     TRY(vec3(S.vbar, vbar, 0.0));
@@ -874,8 +913,16 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     if (n == 0) return SPHFSI_OK;
     std::vector<double> in;
+    // rows arrive in original order; the device keeps its locality order
+    auto to_dev = [&](int w) {
+        std::vector<double> t(in.size());
+        for (int64_t a = 0; a < n; a++)
+            for (int j = 0; j < w; j++) t[(size_t)a * w + j] = in[(size_t)c->s_order[a] * w + j];
+        in.swap(t);
+    };
     if (r) {
         TRY(fetch(in, r, (size_t)n * D));
+        to_dev(D);
         std::vector<double> xyz[3];
         deinterleave(in, D, n, xyz);
         TRY(upload(c, S.x, xyz[0]));
@@ -884,6 +931,7 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     }
     if (v) {
         TRY(fetch(in, v, (size_t)n * D));
+        to_dev(D);
         std::vector<float4> h(n);
         for (int64_t a = 0; a < n; a++)
             h[a] = make_float4((float)in[a * D], (float)in[a * D + 1], D == 3 ? (float)in[a * D + 2] : 0.0f, 0.0f);
@@ -891,6 +939,7 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     }
     if (F) {
         TRY(fetch(in, F, (size_t)n * D * D));
+        to_dev(D * D);
         std::vector<float> h(9 * (size_t)n, 0.0f);
         for (int64_t a = 0; a < n; a++)
             for (int i = 0; i < D * D; i++) h[9 * a + i] = (float)(in[a * D * D + i] - ((i % (D + 1)) == 0 ? 1.0 : 0.0));
@@ -901,6 +950,7 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
         if (!src) return SPHFSI_OK;
         int rc = fetch(in, src, (size_t)n * D);
         if (rc) return rc;
+        to_dev(D);
         std::vector<T> h(3 * (size_t)n, (T)0);
         for (int64_t a = 0; a < n; a++)
             for (int k = 0; k < D; k++) h[3 * a + k] = (T)in[a * D + k];
@@ -968,21 +1018,22 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
     if (which < 0 || which > 3 || !nnz) return SPHFSI_E_INVAL;
     int64_t nrows = which == 3 ? c->ns : c->nf;
     // bin the current positions (no drift) and build the solid records
-    TRY(launch_fluid_drift_bin(c->F, c->g, c->P, c->ctl, 0, c->st));
-    TRY(launch_fluid_reorder(c->F, c->g, c->P, c->st));
-    TRY(launch_solid_bin(c->S, c->g, c->P, c->ctl, c->st));
+    TRY(launch_bin_all(c->F, c->S, c->g, c->P, c->ctl, 0, c->st));
     int *counts = nullptr, *offs = nullptr, *out = nullptr;
     if (cudaMalloc(&counts, sizeof(int) * (nrows + 1)) != cudaSuccess) return SPHFSI_E_NOMEM;
     int rc = launch_debug_pairs(c->F, c->W, c->S, c->g, c->P, which, counts, nullptr, nullptr, c->st);
-    std::vector<int> hc;
-    if (!rc) rc = download(c, hc, counts, nrows);
+    // solid rows (which 3) and solid columns (which 2) come in the device's
+    // locality order; rows and columns are reported in original order
+    std::vector<int> hc_dev, hc(nrows, 0);
+    if (!rc) rc = download(c, hc_dev, counts, nrows);
+    for (int64_t i = 0; i < nrows && !rc; i++) hc[which == 3 ? c->s_order[i] : i] = hc_dev[i];
     std::vector<int64_t> p(nrows + 1, 0);
     for (int64_t i = 0; i < nrows && !rc; i++) p[i + 1] = p[i] + hc[i];
     *nnz = p[nrows];
     if (!rc && ptr) std::memcpy(ptr, p.data(), sizeof(int64_t) * (nrows + 1));
     if (!rc && idx && p[nrows] > 0) {
         std::vector<int> po(nrows);
-        for (int64_t i = 0; i < nrows; i++) po[i] = (int)p[i];
+        for (int64_t i = 0; i < nrows; i++) po[i] = (int)p[which == 3 ? c->s_order[i] : i];
         if (cudaMalloc(&offs, sizeof(int) * nrows) != cudaSuccess || cudaMalloc(&out, sizeof(int) * p[nrows]) != cudaSuccess)
             rc = SPHFSI_E_NOMEM;
         if (!rc) rc = upload(c, offs, po);
@@ -990,6 +1041,8 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
         std::vector<int> h;
         if (!rc) rc = download(c, h, out, (size_t)p[nrows]);
         if (!rc) {
+            if (which == 2)
+                for (auto &col : h) col = c->s_order[col];
             for (int64_t i = 0; i < nrows; i++) {
                 std::sort(h.begin() + p[i], h.begin() + p[i + 1]);
                 for (int64_t q = p[i]; q < p[i + 1]; q++) idx[q] = h[q];
@@ -1007,6 +1060,7 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path)
     TRY(check_ctx(c, true));
     if (path < 0 || path > 2) return SPHFSI_E_INVAL;
     c->S.force_grid_path = path == 2 ? 1 : 0;
+    c->S.force_lane_path = path == 1 ? 1 : 0;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;

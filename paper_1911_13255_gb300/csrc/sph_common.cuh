@@ -134,6 +134,8 @@ struct Solid {
     int *key, *perm, *cstart, *ccount, *cell_of;
     unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
     int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
+    int force_lane_path;      // 1: in 2-D use the 4-lane cluster kernel, not the one-thread one
+    int max_nb;               // largest static neighbour count of a particle
 };
 
 // ---------------------------------------------------------------------------
@@ -206,6 +208,8 @@ __device__ __forceinline__ float W_F(float r, const Phys &P)
 // host-side launch wrappers (implemented in the .cu files)
 // ---------------------------------------------------------------------------
 int launch_control(Ctl *ctl, const Phys &P, int has_solid, cudaStream_t st);
+int launch_control_normals(Ctl *ctl, const Phys &P, const Solid &s, double dt_fixed, int K_fixed, cudaStream_t st);
+int launch_bin_all(Fluid &f, Solid &s, const Grid &g, const Phys &P, Ctl *ctl, int do_drift, cudaStream_t st);
 int launch_finish(Ctl *ctl, unsigned long long ss_pairs_per_step, cudaStream_t st);
 
 // binning / counting sort (sph_grid.cu)

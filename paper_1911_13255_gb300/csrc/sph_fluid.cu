@@ -5,14 +5,18 @@
 // counterparts (Eqs. F:p, F:v), continuity (Eq. fluid-model-mr-con) and the
 // density reinitialisation of Alg. 1.
 //
-// One thread per fluid particle in cell order.  A thread visits the 3^d
-// cells around its own; consecutive threads share those cells, so the
-// neighbour records (two float4 per particle) are served from L1/L2.
-// Pair geometry is FP32 on cell-relative coordinates: r_ij =
-// (x_i - x_cell_i) - (x_j - x_cell_j) - dcell * cell_edge.
+// L consecutive threads share one target particle (cell order): each visits
+// the 3^d cells around the target and takes every L-th candidate of each
+// cell; the partial sums are combined with warp shuffles.  Consecutive
+// targets share their neighbour cells, so the records (two float4 per
+// particle) are served from L1/L2.  Pair geometry is FP32 on cell-relative
+// coordinates: r_ij = (x_i - x_cell_i) - (x_j - x_cell_j) - dcell * edge.
 #include "sph_common.cuh"
 
 namespace sph {
+
+// lanes per target particle
+template <int D> struct Lanes { static constexpr int L = D == 2 ? 4 : 8; };
 
 // Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz)
 // receives the offset o = -(dcell) * edge to add to (rel_i - rel_j).
@@ -40,6 +44,21 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, int cx, int cy, int
             }
         }
     }
+}
+
+template <int L>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int L>
+__device__ __forceinline__ double group_sum_d(double v)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // p_i - p_j of Eq. eqeos without cancellation: with a = 1 + drho_i / rho0 and
@@ -125,33 +144,51 @@ __device__ __forceinline__ float fs_pair_drho(const float d[3], float r2, const 
     return Va * (-dW) * diff;   // times 2 rho_i by the caller
 }
 
+template <int D>
+__device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float ox, float oy, float oz, float d[3])
+{
+    d[0] = (Pi.x - Pj.x) + ox;
+    d[1] = (Pi.y - Pj.y) + oy;
+    d[2] = D == 3 ? (Pi.z - Pj.z) + oz : 0.0f;
+    return d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
+}
+
+template <int D>
+static inline int grid_blocks(int n)
+{
+    long long t = (long long)n * Lanes<D>::L;
+    return (int)((t + kBlock - 1) / kBlock);
+}
+
 // ---------------------------------------------------------------------------
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, Grid g, Phys P, Ctl *ctl)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool act = i < f.n;
+    constexpr int L = Lanes<D>::L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / L, lane = t % L;
+    const bool act = i < f.n;
     unsigned nff = 0, nfw = 0, nfs = 0;
-    float vmax2 = 0.0f;
-    double mfs[3] = {0.0, 0.0, 0.0};
+    float acc[3] = {0.f, 0.f, 0.f}, afs[3] = {0.f, 0.f, 0.f};
+    float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Vi = Pi;
     if (act) {
-        const float4 Pi = f.P4[i], Vi = f.V4[i];
+        Pi = f.P4[i];
+        Vi = f.V4[i];
         const float vi[3] = {Vi.x, Vi.y, Vi.z};
         const float rhoi = P.rho0 + Vi.w, pi = Pi.w;
-        float acc[3] = {0.f, 0.f, 0.f}, afs[3] = {0.f, 0.f, 0.f};
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], g, cx, cy, cz);
         const float c0 = P.c0, eta2 = 2.0f * P.eta;
         for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
             // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
-            int j0 = f.cstart[c], j1 = f.cstart[c + 1];
-            for (int j = j0; j < j1; j++) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 if (j == i) continue;
                 const float4 Pj = f.P4[j];
-                float d[3] = {(Pi.x - Pj.x) + ox, (Pi.y - Pj.y) + oy, D == 3 ? (Pi.z - Pj.z) + oz : 0.0f};
-                float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
+                float d[3];
+                float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
                 if (r2 >= P.rc2F) continue;
                 nff++;
                 const float4 Vj = f.V4[j];
@@ -170,11 +207,10 @@ __global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, 
                 if (D == 3) acc[2] += sc * (-2.0f * Ps * d[2] + eta2 * (vi[2] - Vj.z));
             }
             // walls: v~ = a~ = 0
-            int a0 = w.cstart[c], a1 = w.cstart[c + 1];
-            for (int a = a0; a < a1; a++) {
-                const float4 A = w.A4[a];
-                float d[3] = {(Pi.x - A.x) + ox, (Pi.y - A.y) + oy, D == 3 ? (Pi.z - A.z) + oz : 0.0f};
-                float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
+            const int a1 = w.cstart[c + 1];
+            for (int a = w.cstart[c] + lane; a < a1; a += L) {
+                float d[3];
+                float r2 = rel_d<D>(Pi, w.A4[a], ox, oy, oz, d);
                 if (r2 >= P.rc2F) continue;
                 nfw++;
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -185,29 +221,39 @@ __global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, 
                 acc[2] += o[2];
             }
             // solid particles at their start-of-step positions with v~, a~
-            int b0 = s.n ? s.cstart[c] : 0, b1 = s.n ? s.cstart[c + 1] : 0;
-            for (int b = b0; b < b1; b++) {
-                const float4 A = s.A4[b];
-                float d[3] = {(Pi.x - A.x) + ox, (Pi.y - A.y) + oy, D == 3 ? (Pi.z - A.z) + oz : 0.0f};
-                float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-                if (r2 >= P.rc2F) continue;
-                nfs++;
-                float o[3];
-                fs_pair_force<D>(d, r2, vi, rhoi, pi, s.VB4[b], s.AB4[b], s.N4[b], P.VS, P, o);
-                afs[0] += o[0];
-                afs[1] += o[1];
-                afs[2] += o[2];
+            if (s.n) {
+                const int b1 = s.cstart[c + 1];
+                for (int b = s.cstart[c] + lane; b < b1; b += L) {
+                    float d[3];
+                    float r2 = rel_d<D>(Pi, s.A4[b], ox, oy, oz, d);
+                    if (r2 >= P.rc2F) continue;
+                    nfs++;
+                    float o[3];
+                    fs_pair_force<D>(d, r2, vi, rhoi, pi, s.VB4[b], s.AB4[b], s.N4[b], P.VS, P, o);
+                    afs[0] += o[0];
+                    afs[1] += o[1];
+                    afs[2] += o[2];
+                }
             }
         });
+    }
+    for (int k = 0; k < D; k++) {
+        acc[k] = group_sum<L>(acc[k]);
+        afs[k] = group_sum<L>(afs[k]);
+    }
+    float vmax2 = 0.0f;
+    double mfs[3] = {0.0, 0.0, 0.0};
+    if (act && lane == 0) {
+        const float rhoi = P.rho0 + Vi.w;
+        const float vi[3] = {Vi.x, Vi.y, Vi.z};
         float inv_rho = 1.0f / rhoi;
-        float a[3], vn[3];
+        float a[3], vn[3] = {0.f, 0.f, 0.f};
         double dt = ctl->dt;
         for (int k = 0; k < D; k++) {
             a[k] = (acc[k] + afs[k]) * inv_rho + P.g[k];
             vn[k] = vi[k] + (float)dt * a[k];
             f.dvdt[(size_t)i * D + k] = a[k];
         }
-        if (D == 2) vn[2] = 0.0f;
         f.W4[i] = make_float4(vn[0], vn[1], vn[2], Vi.w);
         vmax2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
         float Vi_ = P.mF / rhoi;   // force = V_i * afs (same V_i as the solid side)
@@ -232,9 +278,8 @@ int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &
                     cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    int nb = (f.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_momentum<2><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_momentum<3><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (P.dim == 2) k_momentum<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    else k_momentum<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -245,19 +290,21 @@ int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Fluid f, Solid s, Grid g, Phys P, Ctl *ctl)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    bool act = k < s.n;
+    constexpr int L = Lanes<D>::L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = t / L, lane = t % L;
+    const bool act = k < s.n;
     unsigned nsf = 0;
-    double ms[3] = {0.0, 0.0, 0.0};
+    float fa[3] = {0.f, 0.f, 0.f};
+    int a = 0;
     if (act) {
         const float4 A = s.A4[k], VB = s.VB4[k], AB = s.AB4[k], N = s.N4[k];
-        int a = __float_as_int(N.w);
-        float fa[3] = {0.f, 0.f, 0.f};
+        a = __float_as_int(N.w);
         int cx, cy, cz;
         cell_xyz(s.cell_of[k], g, cx, cy, cz);
         for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
-            int j0 = f.cstart[c], j1 = f.cstart[c + 1];
-            for (int j = j0; j < j1; j++) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 const float4 Pj = f.P4[j];
                 // the fluid side sees this pair with the opposite cell offset
                 float d[3] = {(Pj.x - A.x) - ox, (Pj.y - A.y) - oy, D == 3 ? (Pj.z - A.z) - oz : 0.0f};
@@ -275,13 +322,17 @@ __global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Fluid f, Solid s, 
                 fa[2] -= Vf * o[2];
             }
         });
+    }
+    for (int q = 0; q < D; q++) fa[q] = group_sum<L>(fa[q]);
+    double ms[3] = {0.0, 0.0, 0.0};
+    if (act && lane == 0) {
         for (int q = 0; q < 3; q++) s.fF[3 * a + q] = q < D ? fa[q] : 0.0f;
         for (int q = 0; q < D; q++) ms[q] = (double)fa[q];
     }
-    unsigned t = warp_sum_u(nsf);
+    unsigned tt = warp_sum_u(nsf);
     for (int q = 0; q < D; q++) ms[q] = warp_sum_d(ms[q]);
-    if ((threadIdx.x & 31) == 0 && t) {
-        atomicAdd(&ctl->n_sf, (unsigned long long)t);
+    if ((threadIdx.x & 31) == 0 && tt) {
+        atomicAdd(&ctl->n_sf, (unsigned long long)tt);
         for (int q = 0; q < D; q++) atomicAdd(&ctl->mom_solid[q], ms[q]);
     }
 }
@@ -293,9 +344,8 @@ int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, cons
         if (s.n) cudaMemsetAsync(s.fF, 0, sizeof(float) * 3 * s.n, st);
         return cudaGetLastError() == cudaSuccess ? 0 : -3;
     }
-    int nb = (s.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_solid_fluid_force<2><<<nb, kBlock, 0, st>>>(f, s, g, P, ctl);
-    else k_solid_fluid_force<3><<<nb, kBlock, 0, st>>>(f, s, g, P, ctl);
+    if (P.dim == 2) k_solid_fluid_force<2><<<grid_blocks<2>(s.n), kBlock, 0, st>>>(f, s, g, P, ctl);
+    else k_solid_fluid_force<3><<<grid_blocks<3>(s.n), kBlock, 0, st>>>(f, s, g, P, ctl);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -306,52 +356,62 @@ int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, cons
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_density(Fluid f, Walls w, Solid s, Grid g, Phys P, Ctl *ctl)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.n) return;
-    const float4 Pi = f.P4[i], Wi = f.W4[i];
-    const float vi[3] = {Wi.x, Wi.y, Wi.z};
-    const float drhoi = Wi.w, rhoi = P.rho0 + Wi.w, pi = Pi.w;
+    constexpr int L = Lanes<D>::L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / L, lane = t % L;
+    const bool act = i < f.n;
     float rate = 0.0f;
-    int cx, cy, cz;
-    cell_xyz(f.cell_of[i], g, cx, cy, cz);
-    const float inv2c0 = 0.5f / P.c0;
-    for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
-        int j0 = f.cstart[c], j1 = f.cstart[c + 1];
-        for (int j = j0; j < j1; j++) {
-            if (j == i) continue;
-            const float4 Pj = f.P4[j];
-            float d[3] = {(Pi.x - Pj.x) + ox, (Pi.y - Pj.y) + oy, D == 3 ? (Pi.z - Pj.z) + oz : 0.0f};
-            float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-            if (r2 >= P.rc2F) continue;
-            const float4 Wj = f.W4[j];
-            const float rhoj = P.rho0 + Wj.w;
-            float r = sqrtf(r2), invr = 1.0f / r;
-            float dW = dW_F(r, P);
-            float UL = -(vi[0] * d[0] + vi[1] * d[1] + (D == 3 ? vi[2] * d[2] : 0.0f)) * invr;
-            float UR = -(Wj.x * d[0] + Wj.y * d[1] + (D == 3 ? Wj.z * d[2] : 0.0f)) * invr;
-            float rb = 0.5f * (rhoi + rhoj);
-            // (v_i - v~_ij).grad_i W = -dW (U_L - U*), U* = (U_L + U_R)/2 + (p_i - p_j) / (2 rho c0)
-            float diff = 0.5f * (UL - UR) - eos_dp(drhoi, Wj.w, P) * inv2c0 / rb;
-            rate += (P.mF / rhoj) * (-dW) * diff;
-        }
-        int a0 = w.cstart[c], a1 = w.cstart[c + 1];
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int a = a0; a < a1; a++) {
-            const float4 A = w.A4[a];
-            float d[3] = {(Pi.x - A.x) + ox, (Pi.y - A.y) + oy, D == 3 ? (Pi.z - A.z) + oz : 0.0f};
-            float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-            if (r2 >= P.rc2F) continue;
-            rate += fs_pair_drho<D>(d, r2, vi, rhoi, pi, z4, z4, w.N4[a], P.VW, P);
-        }
-        int b0 = s.n ? s.cstart[c] : 0, b1 = s.n ? s.cstart[c + 1] : 0;
-        for (int b = b0; b < b1; b++) {
-            const float4 A = s.A4[b];
-            float d[3] = {(Pi.x - A.x) + ox, (Pi.y - A.y) + oy, D == 3 ? (Pi.z - A.z) + oz : 0.0f};
-            float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-            if (r2 >= P.rc2F) continue;
-            rate += fs_pair_drho<D>(d, r2, vi, rhoi, pi, s.VB4[b], s.AB4[b], s.N4[b], P.VS, P);
-        }
-    });
+    float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Wi = Pi;
+    if (act) {
+        Pi = f.P4[i];
+        Wi = f.W4[i];
+        const float vi[3] = {Wi.x, Wi.y, Wi.z};
+        const float drhoi = Wi.w, rhoi = P.rho0 + Wi.w, pi = Pi.w;
+        int cx, cy, cz;
+        cell_xyz(f.cell_of[i], g, cx, cy, cz);
+        const float inv2c0 = 0.5f / P.c0;
+        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
+                if (j == i) continue;
+                const float4 Pj = f.P4[j];
+                float d[3];
+                float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+                if (r2 >= P.rc2F) continue;
+                const float4 Wj = f.W4[j];
+                const float rhoj = P.rho0 + Wj.w;
+                float r = sqrtf(r2), invr = 1.0f / r;
+                float dW = dW_F(r, P);
+                float UL = -(vi[0] * d[0] + vi[1] * d[1] + (D == 3 ? vi[2] * d[2] : 0.0f)) * invr;
+                float UR = -(Wj.x * d[0] + Wj.y * d[1] + (D == 3 ? Wj.z * d[2] : 0.0f)) * invr;
+                float rb = 0.5f * (rhoi + rhoj);
+                // (v_i - v~_ij).grad_i W = -dW (U_L - U*), U* = (U_L + U_R)/2 + (p_i - p_j) / (2 rho c0)
+                float diff = 0.5f * (UL - UR) - eos_dp(drhoi, Wj.w, P) * inv2c0 / rb;
+                rate += (P.mF / rhoj) * (-dW) * diff;
+            }
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int a1 = w.cstart[c + 1];
+            for (int a = w.cstart[c] + lane; a < a1; a += L) {
+                float d[3];
+                float r2 = rel_d<D>(Pi, w.A4[a], ox, oy, oz, d);
+                if (r2 >= P.rc2F) continue;
+                rate += fs_pair_drho<D>(d, r2, vi, rhoi, pi, z4, z4, w.N4[a], P.VW, P);
+            }
+            if (s.n) {
+                const int b1 = s.cstart[c + 1];
+                for (int b = s.cstart[c] + lane; b < b1; b += L) {
+                    float d[3];
+                    float r2 = rel_d<D>(Pi, s.A4[b], ox, oy, oz, d);
+                    if (r2 >= P.rc2F) continue;
+                    rate += fs_pair_drho<D>(d, r2, vi, rhoi, pi, s.VB4[b], s.AB4[b], s.N4[b], P.VS, P);
+                }
+            }
+        });
+    }
+    rate = group_sum<L>(rate);
+    if (!act || lane != 0) return;
+    const float vi[3] = {Wi.x, Wi.y, Wi.z};
+    const float rhoi = P.rho0 + Wi.w;
     float rhodot = 2.0f * rhoi * rate;
     // second half drift (Eq. verlet-first-final) and the new state
     const FluidState M = f.s[1], S = f.s[0];
@@ -379,54 +439,81 @@ int launch_density(const Fluid &f, const Walls &w, const Solid &s, const Grid &g
                    cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    int nb = (f.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_density<2><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_density<3><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (P.dim == 2) k_density<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    else k_density<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 // ---------------------------------------------------------------------------
-// a3: density reinitialisation rho = rho0 sigma / sigma0 (reading R16)
+// a3: density reinitialisation rho = rho0 sigma / sigma0 (reading R16).
+// rho0 (sigma - sigma0) / sigma0 cancels about three digits, so each kernel
+// value is evaluated in FP64 from the FP64 positions (the FP32 records only
+// screen out candidates well outside the support) and summed in FP64.
 // ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ double W_fp64_shape(double dx, double dy, double dz, const Grid &g, double rc2,
+                                               double inv_h)
+{
+    if (g.periodic_x) {
+        if (dx > 0.5 * g.Lx) dx -= g.Lx;
+        else if (dx < -0.5 * g.Lx) dx += g.Lx;
+    }
+    double r2 = dx * dx + dy * dy + (D == 3 ? dz * dz : 0.0);
+    if (!(r2 < rc2)) return 0.0;
+    // FP64 square root from the FP32 one and one Newton step (relative error ~1e-14)
+    float rf = sqrtf((float)r2);
+    double r = rf > 0.0f ? (double)rf + (r2 - (double)rf * (double)rf) * (double)(0.5f / rf) : 0.0;
+    double q = r * inv_h, a = 1.0 - 0.5 * q, a2 = a * a;
+    return a2 * a2 * (1.0 + 2.0 * q);   // times alpha_d by the caller
+}
+
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_reinit(Fluid f, Walls w, Solid s, Grid g, Phys P, const Ctl *ctl)
 {
     if (!ctl->reinit) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f.n) return;
-    // rho0 (sigma - sigma0) / sigma0 cancels about three digits, so the
-    // number density is summed in FP64 from the FP64 positions
+    constexpr int L = Lanes<D>::L;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / L, lane = t % L;
+    const bool act = i < f.n;
     const FluidState M = f.s[1];
-    const double xi = M.x[i], yi = M.y[i], zi = D == 3 ? M.z[i] : 0.0;
     const double inv_h = 1.0 / P.hF_d, rc2 = P.rc2F_d;
-    int cx, cy, cz;
-    cell_xyz(f.cell_of[i], g, cx, cy, cz);
-    auto Wd = [&](double dx, double dy, double dz) -> double {
-        if (g.periodic_x) {
-            if (dx > 0.5 * g.Lx) dx -= g.Lx;
-            else if (dx < -0.5 * g.Lx) dx += g.Lx;
-        }
-        double r2 = dx * dx + dy * dy + (D == 3 ? dz * dz : 0.0);
-        if (!(r2 < rc2)) return 0.0;
-        double q = sqrt(r2) * inv_h, a = 1.0 - 0.5 * q, a2 = a * a;
-        return a2 * a2 * (1.0 + 2.0 * q);   // times alpha_d below
-    };
+    const float screen = P.rc2F * 1.0001f;
     double sF = 0.0, sW = 0.0, sS = 0.0;
-    for_each_cell<D>(g, cx, cy, cz, [&](int c, float, float, float) {
-        for (int j = f.cstart[c]; j < f.cstart[c + 1]; j++) {
-            if (j == i) continue;
-            sF += Wd(xi - M.x[j], yi - M.y[j], D == 3 ? zi - M.z[j] : 0.0);
-        }
-        for (int q = w.cstart[c]; q < w.cstart[c + 1]; q++) {
-            int a = w.perm[q];
-            sW += Wd(xi - w.x[a], yi - w.y[a], D == 3 ? zi - w.z[a] : 0.0);
-        }
-        int b0 = s.n ? s.cstart[c] : 0, b1 = s.n ? s.cstart[c + 1] : 0;
-        for (int q = b0; q < b1; q++) {
-            int a = s.perm[q];
-            sS += Wd(xi - s.x[a], yi - s.y[a], D == 3 ? zi - s.z[a] : 0.0);
-        }
-    });
+    if (act) {
+        const float4 Pi = f.P4[i];
+        const double xi = M.x[i], yi = M.y[i], zi = D == 3 ? M.z[i] : 0.0;
+        int cx, cy, cz;
+        cell_xyz(f.cell_of[i], g, cx, cy, cz);
+        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
+                if (j == i) continue;
+                float d[3];
+                if (rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) >= screen) continue;
+                sF += W_fp64_shape<D>(xi - M.x[j], yi - M.y[j], D == 3 ? zi - M.z[j] : 0.0, g, rc2, inv_h);
+            }
+            const int a1 = w.cstart[c + 1];
+            for (int q = w.cstart[c] + lane; q < a1; q += L) {
+                float d[3];
+                if (rel_d<D>(Pi, w.A4[q], ox, oy, oz, d) >= screen) continue;
+                int a = w.perm[q];
+                sW += W_fp64_shape<D>(xi - w.x[a], yi - w.y[a], D == 3 ? zi - w.z[a] : 0.0, g, rc2, inv_h);
+            }
+            if (s.n) {
+                const int b1 = s.cstart[c + 1];
+                for (int q = s.cstart[c] + lane; q < b1; q += L) {
+                    float d[3];
+                    if (rel_d<D>(Pi, s.A4[q], ox, oy, oz, d) >= screen) continue;
+                    int a = s.perm[q];
+                    sS += W_fp64_shape<D>(xi - s.x[a], yi - s.y[a], D == 3 ? zi - s.z[a] : 0.0, g, rc2, inv_h);
+                }
+            }
+        });
+    }
+    sF = group_sum_d<L>(sF);
+    sW = group_sum_d<L>(sW);
+    sS = group_sum_d<L>(sS);
+    if (!act || lane != 0) return;
     double sigma = P.alphaF_d * (1.0 + sF + P.VW_VF_d * sW + P.VS_VF_d * sS);
     double dr = P.rho0_d * ((sigma - P.sigma0_d) / P.sigma0_d);
     if (P.free_surface && dr < 0.0) dr = 0.0;
@@ -440,9 +527,8 @@ int launch_reinit(const Fluid &f, const Walls &w, const Solid &s, const Grid &g,
                   cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    int nb = (f.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_reinit<2><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_reinit<3><<<nb, kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (P.dim == 2) k_reinit<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    else k_reinit<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -170,7 +170,7 @@ __device__ __forceinline__ void stress_QB(const float *H, const float *B, float 
         float E11 = h11 + 0.5f * (h01 * h01 + h11 * h11);
         float E01 = 0.5f * (h01 + h10 + h00 * h01 + h10 * h11);
         float C00 = 1.0f + 2.0f * E00, C11 = 1.0f + 2.0f * E11, C01 = 2.0f * E01;
-        float idet = 1.0f / (C00 * C11 - C01 * C01);
+        float idet = __frcp_rn(C00 * C11 - C01 * C01);
         float Ci00 = C11 * idet, Ci11 = C00 * idet, Ci01 = -C01 * idet;
         float lnJ = log1pf(h00 + h11 + h00 * h11 - h01 * h10);
         float T00 = 2.0f * mu * E00 + lam * lnJ, T11 = 2.0f * mu * E11 + lam * lnJ, T01 = 2.0f * mu * E01;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void stress_QB(const float *H, const float *B, float 
         float c00 = C[4] * C[8] - C[5] * C[7], c01 = C[2] * C[7] - C[1] * C[8], c02 = C[1] * C[5] - C[2] * C[4];
         float c10 = C[5] * C[6] - C[3] * C[8], c11 = C[0] * C[8] - C[2] * C[6], c12 = C[2] * C[3] - C[0] * C[5];
         float c20 = C[3] * C[7] - C[4] * C[6], c21 = C[1] * C[6] - C[0] * C[7], c22 = C[0] * C[4] - C[1] * C[3];
-        float idet = 1.0f / (C[0] * c00 + C[1] * c10 + C[2] * c20);
+        float idet = __frcp_rn(C[0] * c00 + C[1] * c10 + C[2] * c20);
         Ci[0] = c00 * idet; Ci[1] = c01 * idet; Ci[2] = c02 * idet;
         Ci[3] = c10 * idet; Ci[4] = c11 * idet; Ci[5] = c12 * idet;
         Ci[6] = c20 * idet; Ci[7] = c21 * idet; Ci[8] = c22 * idet;
@@ -477,17 +477,31 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
     }
     cluster_sync();
 
-    // dH/dt over this particle's neighbours at the velocities in sV (DSMEM)
+    // dH/dt over this particle's neighbours at the velocities in sV (DSMEM).
+    // Entries are taken kU at a time per lane so that their remote loads are
+    // in flight together.
+    constexpr int kU = 4;
     auto rate = [&](float4 va, float *Hd) {
         float M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = q0 + lane; q < q1; q += kLanes) {
-            float4 e = __ldg(&s.nb[q]);
-            int b = __float_as_int(e.w);
-            float4 vb = *dsmem(&sV[b % kPPC], (unsigned)(b / kPPC));
-            float dv[3] = {vb.x - va.x, vb.y - va.y, vb.z - va.z};
-            float ge[3] = {e.x, e.y, e.z};
-            for (int i = 0; i < D; i++)
-                for (int j = 0; j < D; j++) M[i * D + j] += dv[i] * ge[j];
+        for (int base = q0 + lane; base < q1; base += kLanes * kU) {
+            float4 e[kU], vb[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                int q = base + u * kLanes;
+                e[u] = q < q1 ? __ldg(&s.nb[q]) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                int b = __float_as_int(e[u].w);
+                vb[u] = b >= 0 ? *dsmem(&sV[b % kPPC], (unsigned)(b / kPPC)) : va;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                float dv[3] = {vb[u].x - va.x, vb[u].y - va.y, vb[u].z - va.z};
+                float ge[3] = {e[u].x, e[u].y, e[u].z};
+                for (int i = 0; i < D; i++)
+                    for (int j = 0; j < D; j++) M[i * D + j] += dv[i] * ge[j];
+            }
         }
         for (int i = 0; i < D * D; i++) M[i] = group_sum(M[i]);
         for (int i = 0; i < D; i++)
@@ -543,19 +557,37 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
                 }
             }
             float acc[3] = {0.f, 0.f, 0.f};
-            for (int q = q0 + lane; q < q1; q += kLanes) {
-                float4 e = __ldg(&s.nb[q]);
-                int b = __float_as_int(e.w);
-                unsigned rb = (unsigned)(b / kPPC);
-                int lb = b % kPPC;
+            for (int base = q0 + lane; base < q1; base += kLanes * kU) {
+                float4 e[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {
+                    int q = base + u * kLanes;
+                    e[u] = q < q1 ? __ldg(&s.nb[q]) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+                }
                 if (D == 2) {
-                    float4 qb = *dsmem(&sQ[lb], rb);
-                    acc[0] += (Qa[0] + qb.x) * e.x + (Qa[1] + qb.y) * e.y;
-                    acc[1] += (Qa[2] + qb.z) * e.x + (Qa[3] + qb.w) * e.y;
+                    float4 qb[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        int b = __float_as_int(e[u].w);
+                        qb[u] = b >= 0 ? *dsmem(&sQ[b % kPPC], (unsigned)(b / kPPC)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        acc[0] += (Qa[0] + qb[u].x) * e[u].x + (Qa[1] + qb[u].y) * e[u].y;
+                        acc[1] += (Qa[2] + qb[u].z) * e[u].x + (Qa[3] + qb[u].w) * e[u].y;
+                    }
                 } else {
-                    for (int r = 0; r < 3; r++) {
-                        float4 qb = *dsmem(&sQ[3 * lb + r], rb);
-                        acc[r] += (Qa[3 * r] + qb.x) * e.x + (Qa[3 * r + 1] + qb.y) * e.y + (Qa[3 * r + 2] + qb.z) * e.z;
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        int b = __float_as_int(e[u].w);
+                        if (b < 0) continue;
+                        unsigned rb = (unsigned)(b / kPPC);
+                        int lb = b % kPPC;
+                        for (int r = 0; r < 3; r++) {
+                            float4 qv = *dsmem(&sQ[3 * lb + r], rb);
+                            acc[r] += (Qa[3 * r] + qv.x) * e[u].x + (Qa[3 * r + 1] + qv.y) * e[u].y +
+                                      (Qa[3 * r + 2] + qv.z) * e[u].z;
+                        }
                     }
                 }
             }
@@ -625,8 +657,237 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
     cluster_sync();
 }
 
+// ---------------------------------------------------------------------------
+// 2-D cluster-resident variant with one thread per particle.  The static
+// neighbour entries (V0 grad0 W and the 32-bit shared::cluster addresses of
+// the neighbour's stress and velocity slots) are loaded once into registers;
+// every phase then issues all its neighbour loads back to back, so a phase
+// costs about one shared-memory (or DSMEM) latency instead of one per
+// neighbour.  Particles beyond kMaxNb2 neighbours use the 4-lane kernel.
+// ---------------------------------------------------------------------------
+constexpr int kC1Threads = 128;   // particles per CTA (128 measured faster than 256)
+constexpr int kMaxNb2 = 24;
+
+__device__ __forceinline__ uint32_t cl_addr(const void *p, uint32_t rank)
+{
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_cl(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ float2 ld_cl2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
+
+__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Solid s, Phys P, Ctl *ctl)
+{
+    __shared__ float4 sQ[kC1Threads];
+    __shared__ float4 sV[kC1Threads];
+    const unsigned rank = cluster_rank();
+    const int g = threadIdx.x;
+    const int a = (int)rank * kC1Threads + g;
+    const bool own = a < s.n;
+    const int K = ctl->K;
+    const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
+    const float dts = (float)dtsd, hdts = 0.5f * dts;
+    const float inv_rhoS = 1.0f / P.rhoS, inv_mS = 1.0f / P.mS;
+
+    float H[4] = {0, 0, 0, 0}, B[4] = {1, 0, 0, 1}, fF[2] = {0, 0};
+    double x = 0, y = 0, xs = 0, ys = 0, as0 = 0, as1 = 0;
+    bool cons = true;
+    float vmax = 0.0f, amax = 0.0f;
+    float gx[kMaxNb2], gy[kMaxNb2];
+    uint32_t aQ[kMaxNb2];   // neighbour's sQ slot; its sV slot is at aQ + dV (same layout in every CTA)
+    const uint32_t dV = (uint32_t)__cvta_generic_to_shared(&sV[0]) - (uint32_t)__cvta_generic_to_shared(&sQ[0]);
+    int nn = 0;
+    if (own) {
+        int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
+        nn = q1 - q0;   // the launcher guarantees nn <= kMaxNb2
+        for (int i = 0; i < 4; i++) {
+            H[i] = s.H[9 * a + i];
+            B[i] = s.B0[9 * a + i];
+        }
+        fF[0] = s.fF[3 * a];
+        fF[1] = s.fF[3 * a + 1];
+        x = xs = s.x[a];
+        y = ys = s.y[a];
+        cons = s.cons[a] != 0;
+        sV[g] = s.v4[a];
+    }
+#pragma unroll
+    for (int u = 0; u < kMaxNb2; u++) {
+        gx[u] = gy[u] = 0.0f;
+        aQ[u] = 0u;
+        if (u < nn) {
+            float4 e = s.nb[s.nb_ptr[a] + u];
+            int b = __float_as_int(e.w);
+            gx[u] = e.x;
+            gy[u] = e.y;
+            aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
+        }
+    }
+    cluster_sync();
+
+    auto rate = [&](float4 va, float *Hd) {
+        float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
+            float2 vb[kChunk2];
+#pragma unroll
+            for (int u = 0; u < kChunk2; u++)
+                if (c0 + u < nn) vb[u] = ld_cl2(aQ[c0 + u] + dV);
+#pragma unroll
+            for (int u = 0; u < kChunk2; u++)
+                if (c0 + u < nn) {
+                    float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
+                    M0 += dvx * gx[c0 + u];
+                    M1 += dvx * gy[c0 + u];
+                    M2 += dvy * gx[c0 + u];
+                    M3 += dvy * gy[c0 + u];
+                }
+        }
+        Hd[0] = M0 * B[0] + M1 * B[2];
+        Hd[1] = M0 * B[1] + M1 * B[3];
+        Hd[2] = M2 * B[0] + M3 * B[2];
+        Hd[3] = M2 * B[1] + M3 * B[3];
+    };
+    auto put_Q = [&]() {
+        float Q[4];
+        stress_QB<2>(H, B, P.mu, P.lam, Q);
+        sQ[g] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+    };
+
+    if (own) {
+        float4 va = sV[g];
+        float Hd[4];
+        rate(va, Hd);
+        for (int i = 0; i < 4; i++) H[i] = H[i] + hdts * Hd[i];
+        if (!cons) {
+            x = x + hdtsd * (double)va.x;
+            y = y + hdtsd * (double)va.y;
+        }
+        put_Q();
+    }
+    for (int kk = 0; kk < K; kk++) {
+        cluster_sync();
+        // (B) force loop and kick
+        if (own) {
+            const float4 Qa = sQ[g];
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
+                float4 qb[kChunk2];
+#pragma unroll
+                for (int u = 0; u < kChunk2; u++)
+                    if (c0 + u < nn) qb[u] = ld_cl(aQ[c0 + u]);
+#pragma unroll
+                for (int u = 0; u < kChunk2; u++)
+                    if (c0 + u < nn) {
+                        ax += (Qa.x + qb[u].x) * gx[c0 + u] + (Qa.y + qb[u].y) * gy[c0 + u];
+                        ay += (Qa.z + qb[u].z) * gx[c0 + u] + (Qa.w + qb[u].w) * gy[c0 + u];
+                    }
+            }
+            if (!cons) {
+                float4 v = sV[g];
+                float av0 = ax * inv_rhoS + fF[0] * inv_mS + P.g[0];
+                float av1 = ay * inv_rhoS + fF[1] * inv_mS + P.g[1];
+                v.x += dts * av0;
+                v.y += dts * av1;
+                sV[g] = v;
+                as0 += dtsd * (double)av0;
+                as1 += dtsd * (double)av1;
+                amax = fmaxf(amax, av0 * av0 + av1 * av1);
+                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y);
+            }
+        }
+        cluster_sync();
+        // (C) deformation rate at v^{k+1}; second half drift; next first half + stress
+        if (own) {
+            const bool more = kk + 1 < K;
+            float4 va = sV[g];
+            float Hd[4];
+            rate(va, Hd);
+            // second half drift of this sub-step and, unless it is the last,
+            // the first half drift of the next one with the same rate
+            const float hH = more ? dts : hdts;
+            const double hX = more ? dtsd : hdtsd;
+            for (int i = 0; i < 4; i++) H[i] = H[i] + hH * Hd[i];
+            if (!cons) {
+                x = x + hX * (double)va.x;
+                y = y + hX * (double)va.y;
+            }
+            if (more) put_Q();
+        }
+    }
+    if (own) {
+        for (int i = 0; i < 4; i++) s.H[9 * a + i] = H[i];
+        s.v4[a] = sV[g];
+        s.x[a] = x;
+        s.y[a] = y;
+        const double idt = 1.0 / dt;
+        s.vbar[3 * a] = (x - xs) * idt;
+        s.vbar[3 * a + 1] = (y - ys) * idt;
+        s.vbar[3 * a + 2] = 0.0;
+        s.abar[3 * a] = as0 * idt;
+        s.abar[3 * a + 1] = as1 * idt;
+        s.abar[3 * a + 2] = 0.0;
+    }
+    float vm = warp_max(vmax), am = warp_max(amax);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
+        atomic_max_pos(&ctl->amaxS, sqrtf(am));
+    }
+    cluster_sync();
+}
+
+static int launch_solid_cluster2d(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st)
+{
+    int nctas = (s.n + kC1Threads - 1) / kC1Threads;
+    if (P.dim != 2 || nctas > kClusterMax || s.max_nb > kMaxNb2) return 1;
+    static int feasible[kClusterMax + 1] = {};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nctas);
+    cfg.blockDim = dim3(kC1Threads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (feasible[nctas] == 0) {
+        int nclu = 0;
+        cudaFuncSetAttribute(k_solid_cluster2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster2d, &cfg);
+        if (e != cudaSuccess) cudaGetLastError();
+        feasible[nctas] = (e == cudaSuccess && nclu >= 1) ? 1 : -1;
+    }
+    if (feasible[nctas] < 0) return 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_solid_cluster2d, s, P, ctl);
+    return e == cudaSuccess ? 0 : -3;
+}
+
 static int launch_solid_cluster(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st)
 {
+    if (!s.force_lane_path) {
+        int rc = launch_solid_cluster2d(s, P, ctl, st);
+        if (rc <= 0) return rc;
+    }
     int nctas = (s.n + kPPC - 1) / kPPC;
     if (nctas > kClusterMax) return 1;
     static int feasible[2][kClusterMax + 1] = {};   // 0 unknown, 1 yes, -1 no

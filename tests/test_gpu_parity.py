@@ -89,14 +89,14 @@ def _one_step(case, solid_path=0):
     return sim, ref, dt
 
 
-@pytest.mark.parametrize("solid_path", [0, 2], ids=["cluster", "grid"])
+@pytest.mark.parametrize("solid_path", [0, 1, 2], ids=["auto", "cluster_lanes", "grid"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_one_step_parity(name, solid_path):
     case = CASES[name]()
     s_r_start = np.array(case.s_r0, dtype=np.float64)
     sim, ref, dt = _one_step(case, solid_path)
     if case.ns:
-        assert sim.info()["solid_path"] == (1 if solid_path == 0 else 2)
+        assert sim.info()["solid_path"] == (2 if solid_path == 2 else 1)
     g, s = sim.get_fluid(), sim.get_solid()
     e = {
         "dvdt": rel(g["dvdt"], ref.f_dvdt),
