@@ -202,8 +202,9 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path);
  * 0 control + normal update, 1 fluid drift + fluid and solid binning and
  * sort, 2 density
  * reinitialisation, 3 momentum (a4), 4 solid-side coupling force (a5),
- * 5 continuity + drift (a6), 6 solid sub-steps (a7, a8; they run on a
- * side stream concurrently with stage 5), 7 finish (after both).
+ * 5 continuity + drift (a6), 6 solid sub-steps (a7, a8), 7 finish.  Stages
+ * 4 and 6 run on a side stream concurrently with stages 3 and 5; finish
+ * follows the join of both streams.
  * Returns the number of stages, SPHFSI_E_INVAL if n < 8, SPHFSI_E_STATE if
  * profiling is off. */
 int sphfsi_set_profiling(sphfsi_ctx *c, int on);

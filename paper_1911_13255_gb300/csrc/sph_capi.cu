@@ -178,20 +178,21 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     // a3: density reinitialisation (no-op on other steps)
     TRY(launch_reinit(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
     TRY(mark(c, 3));
-    // a4, a5, a6
-    TRY(launch_momentum(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
-    TRY(mark(c, 4));
-    TRY(launch_solid_fluid_force(c->F, c->S, c->g, c->P, c->ctl, st));
-    TRY(mark(c, 5));
-    // a7 + a8 on the side stream, a6 on the main stream, joined before finish
+    // The solid branch (a5 then a7 + a8) reads only the records written so
+    // far, so it runs on the side stream while the main stream does a4 and
+    // a6; the two join before finish.
     if (c->S.n) {
         TRY(cuda_rc(cudaEventRecord(c->fork_ev, st)));
         TRY(cuda_rc(cudaStreamWaitEvent(c->side, c->fork_ev, 0)));
+        TRY(mark(c, 4, c->side));
+        TRY(launch_solid_fluid_force(c->F, c->S, c->g, c->P, c->ctl, c->side));
         TRY(mark(c, 7, c->side));
         TRY(launch_solid_substeps(c->S, c->P, c->ctl, &c->solid_path, c->side));
         TRY(mark(c, 8, c->side));
         TRY(cuda_rc(cudaEventRecord(c->join_ev, c->side)));
     }
+    TRY(launch_momentum(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
+    TRY(mark(c, 5));
     TRY(launch_density(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
     TRY(mark(c, 6));
     if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
@@ -1082,15 +1083,23 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     if (!c->profiling) return SPHFSI_E_STATE;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     auto el = [&](int a, int b, float *out) { return cuda_rc(cudaEventElapsedTime(out, c->ev[a], c->ev[b])); };
-    for (int k = 0; k < 6; k++) TRY(el(k, k + 1, &ms[k]));   // main-stream stages up to continuity
+    // events: 0 start, 1 control, 2 binning, 3 reinit, 5 momentum, 6 continuity
+    // (main stream); 4 branch start, 7 coupling force done, 8 sub-steps done
+    // (side stream); 9 end of step
+    TRY(el(0, 1, &ms[0]));
+    TRY(el(1, 2, &ms[1]));
+    TRY(el(2, 3, &ms[2]));
+    TRY(el(3, 5, &ms[3]));
+    TRY(el(5, 6, &ms[5]));
     if (c->S.n) {
         float fin_a = 0.f, fin_b = 0.f;
+        TRY(el(4, 7, &ms[4]));                                 // coupling force (side stream)
         TRY(el(7, 8, &ms[6]));                                 // solid sub-steps (side stream)
         TRY(el(6, 9, &fin_a));
         TRY(el(8, 9, &fin_b));
         ms[7] = fin_a < fin_b ? fin_a : fin_b;                 // finish, after the join
     } else {
-        ms[6] = 0.0f;
+        ms[4] = ms[6] = 0.0f;
         TRY(el(6, 9, &ms[7]));
     }
     return sphfsi_ctx::kStages;
