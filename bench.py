@@ -258,8 +258,8 @@ def run_gpu(args, rank, world, local_rank):
         work = case.nf * BYTES_PER_FLUID_PARTICLE["bin_sort"]
         bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
         achieved = work / (per_launch[dom] * 1e-3) / 1e9
-    solid_kernel = {1: "k_solid_cluster2d" if case.dim == 2 else "k_solid_cluster", 2: "k_solid_substeps"}.get(
-        info1["solid_path"], "k_solid_substeps")
+    solid_kernel = {1: "k_solid_cluster2d_one" if case.dim == 2 else "k_solid_cluster_one",
+                    2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
                     "bin_sort": "k_bin_all+k_scan2+k_scatter2+k_cellsort2+k_records_all"}

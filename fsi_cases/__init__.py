@@ -324,7 +324,8 @@ def cantilever(L=0.35, t=0.02, dpS=0.005, rho=10.0, E=1.4e3, nu=0.4, v_tip=0.05,
 # Paper benchmarks at the workload sizes
 # --------------------------------------------------------------------------
 
-def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0):
+def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0, L_D=25.0, H_D=4.1,
+                 flag_len=3.5, flag_thick=0.2, rho_S=10.0, E=1.4e3, nu=0.4, cy_D=2.0):
     """2-D channel flow past a rigid cylinder carrying an elastic flag (Section 4.1).
 
     Channel 25D x 4.1D, periodic in x with a velocity-imposing inflow buffer of
@@ -334,14 +335,18 @@ def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0):
     rho_S = 10, E = 1.4e3, Poisson 0.4; fluid spacing D/10, solid spacing D/20.
     Solid particles inside the cylinder are constrained (rigid).
     The initial fluid velocity is the inflow profile everywhere.
+
+    L_D x H_D (channel size in D), cy_D (cylinder centre height in D),
+    flag_len and flag_thick (in D), rho_S, E and nu override those values for
+    the batched variants (flag_batch).
     """
     rng = np.random.default_rng(seed)
     dpF = D / 10 if dpF is None else dpF
     dpS = dpF / ratio
-    Lx, H = 25 * D, 4.1 * D
-    cx, cy, R = 2 * D, 2 * D, D / 2
-    fx1 = cx + R + 3.5 * D
-    fy0, fy1 = cy - 0.1 * D, cy + 0.1 * D
+    Lx, H = L_D * D, H_D * D
+    cx, cy, R = 2 * D, cy_D * D, D / 2
+    fx1 = cx + R + flag_len * D
+    fy0, fy1 = cy - 0.5 * flag_thick * D, cy + 0.5 * flag_thick * D
 
     def in_body(p):
         inc = (p[:, 0] - cx) ** 2 + (p[:, 1] - cy) ** 2 < R * R
@@ -383,9 +388,44 @@ def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0):
         domain_lo=(0.0, -6 * dpF, 0.0), domain_hi=(Lx, H + 6 * dpF, 0.0),
         f_r=fr, f_v=fv, f_p=np.zeros(len(fr)), f_dp=dpF, f_rho0=1.0, f_c0=c0, f_eta=1e-3,
         w_r=wr, w_n=wn, w_dp=dpF,
-        s_r0=sr, s_v0=np.zeros_like(sr), s_n0=sn, s_cons=cons, s_dp=dpS, s_rho0=10.0,
-        s_E=1.4e3, s_nu=0.4, tip=tip, meta=dict(D=D),
+        s_r0=sr, s_v0=np.zeros_like(sr), s_n0=sn, s_cons=cons, s_dp=dpS, s_rho0=rho_S,
+        s_E=E, s_nu=nu, tip=tip, meta=dict(D=D),
     )
+
+
+def flag_batch(seed=0, n=256, nf_lo=2000, nf_hi=60000, D=0.1, jitter_amp=1e-3):
+    """Many independent cylinder-plus-flag channels of uneven size (batched workload).
+
+    Per instance b (own generator seeded from (seed, b)): a target fluid count
+    log-uniform in [nf_lo, nf_hi]; flag length uniform in [2D, 4D], thickness
+    uniform in [0.1D, 0.3D]; E log-uniform in [5e2, 5e4]; rho_S / rho_F
+    uniform in [1, 20]; the discretisation of channel_flag (dp_F = D/10,
+    dp_S = D/20).  The channel area is the target count times dp_F^2 plus the
+    body; the height is 4.1D scaled like the square root of that area (at
+    least 2.5D) and the length the rest (at least the flag's end + 2D).
+    Returns a list of Case.
+    """
+    dpF = D / 10
+    out = []
+    for b in range(n):
+        rng = np.random.default_rng([seed, b])
+        nf = math.exp(rng.uniform(math.log(nf_lo), math.log(nf_hi)))
+        fl = rng.uniform(2.0, 4.0)
+        ft = rng.uniform(0.1, 0.3)
+        E = math.exp(rng.uniform(math.log(5e2), math.log(5e4)))
+        rho_S = rng.uniform(1.0, 20.0)
+        area = nf * dpF * dpF / (D * D) + math.pi / 4 + fl * ft   # in D^2
+        H_D = max(2.5, 4.1 * math.sqrt(area / (25.0 * 4.1)))
+        L_D = max(area / H_D, 2.5 + fl + 2.0)
+        # whole numbers of fluid spacings in both directions
+        H_D = round(H_D * 10) / 10
+        L_D = round(L_D * 10) / 10
+        c = channel_flag(seed=int(rng.integers(1 << 30)), D=D, dpF=dpF, jitter_amp=jitter_amp, L_D=L_D,
+                         H_D=H_D, flag_len=fl, flag_thick=ft, rho_S=rho_S, E=E, cy_D=H_D / 2)
+        c.name = f"flag_batch[{b}]"
+        c.meta.update(L_D=L_D, H_D=H_D, flag_len=fl, flag_thick=ft)
+        out.append(c)
+    return out
 
 
 def dam_gate(seed=0, dpF=1e-3, ratio=2, jitter_amp=1e-3, E=12e6, tank_len=0.5):
@@ -488,4 +528,5 @@ def duct_plate_3d(seed=0, scale=1, jitter_amp=1e-3):
 
 BUILDERS = dict(tiny_box=tiny_box, tiny_box_3d=tiny_box_3d, floating_block=floating_block,
                 hydrostatic=hydrostatic_column, cantilever=cantilever,
-                channel_flag=channel_flag, dam_gate=dam_gate, duct_plate_3d=duct_plate_3d)
+                channel_flag=channel_flag, dam_gate=dam_gate, duct_plate_3d=duct_plate_3d,
+                flag_batch=flag_batch)

@@ -85,7 +85,7 @@ typedef struct {
     double width, y0, H, U, t_ramp;
 } sphfsi_inflow;
 
-/* Per-context counters and last-step diagnostics. */
+/* Counters and last-step diagnostics of the selected instance. */
 typedef struct {
     int64_t n_fluid, n_solid, n_wall, n_cells;
     int64_t step;            /* completed steps                                  */
@@ -107,6 +107,28 @@ typedef struct {
  * for the legacy default stream) on the current device.  *out receives the
  * context; the caller frees it with sphfsi_destroy. */
 int sphfsi_create(sphfsi_ctx **out, const sphfsi_params *p, void *cuda_stream);
+
+/* Batched context of n >= 1 independent instances (the paper has no
+ * counterpart: many small problems of the kind of Section 4 advanced by the
+ * same launches).  p points to n parameter blocks, all of the same dim.
+ * Every instance has its own particles, grid, constants, time, dt_F and K;
+ * one sphfsi_step / sphfsi_run advances all of them.  The set-up calls
+ * (add_fluid, set_walls, add_solid, set_inflow), the getters and setters,
+ * sphfsi_set_time, sphfsi_get_info and sphfsi_debug_neighbors act on the
+ * instance chosen by sphfsi_select (0 after creation).  Each instance's
+ * body must fit one thread-block cluster (sphfsi_set_solid_path); a batch
+ * whose body does not gets SPHFSI_E_CAPACITY from the first step.
+ * sphfsi_create(out, p, s) is sphfsi_create_batch(out, 1, p, s).  n outside
+ * [1, 2^20] or mixed dim: SPHFSI_E_INVAL. */
+int sphfsi_create_batch(sphfsi_ctx **out, int32_t n, const sphfsi_params *p, void *cuda_stream);
+
+/* Choose the instance that the per-instance calls address (0 <= inst < n,
+ * else SPHFSI_E_INVAL). */
+int sphfsi_select(sphfsi_ctx *c, int32_t inst);
+
+/* Pair interactions of all instances since creation (sum of
+ * sphfsi_info.pairs_total over the instances); waits for the stream. */
+int sphfsi_pairs_total(sphfsi_ctx *c, int64_t *total);
 
 /* Fluid particles (Section 2.1): positions r (n x dim, FP64), velocities v
  * (n x dim), initial pressure p_init (n; the density follows from the
@@ -152,7 +174,8 @@ int sphfsi_step(sphfsi_ctx *c, double dt_F);
 int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F);
 
 /* Wait for the stream; return SPHFSI_E_UNSTABLE / SPHFSI_E_TIMEOUT if the
- * device flagged a non-finite state or a bounded wait ran out. */
+ * device flagged a non-finite state or a bounded wait ran out in any
+ * instance. */
 int sphfsi_sync(sphfsi_ctx *c);
 
 /* Fluid state in original order: r (n x dim FP64), v (n x dim FP32),
@@ -191,8 +214,10 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
  * neighbours per particle the one-thread-per-particle variant, otherwise the
  * four-lanes-per-particle variant -- else the cooperative grid kernel);
  * 1 the four-lane cluster variant where it fits; 2 always the cooperative
- * grid kernel.  All compute the same sub-steps (Section 3.3); the choice
- * exists to test and compare them. */
+ * grid kernel (single-instance contexts only; SPHFSI_E_INVAL in a batch).
+ * All compute the same sub-steps (Section 3.3); the choice exists to test
+ * and compare them.  In a batch the cluster kernels are persistent: as many
+ * clusters as fit on the device take instances from a device queue. */
 int sphfsi_set_solid_path(sphfsi_ctx *c, int path);
 
 /* Per-stage device timing.  With on != 0 every later step records CUDA

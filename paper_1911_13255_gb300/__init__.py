@@ -59,6 +59,9 @@ _vp = C.c_void_p
 # name -> (restype, argtypes)
 _SIGS = {
     "sphfsi_create": (C.c_int, [C.POINTER(_vp), C.POINTER(Params), _vp]),
+    "sphfsi_create_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, C.POINTER(Params), _vp]),
+    "sphfsi_select": (C.c_int, [_vp, C.c_int32]),
+    "sphfsi_pairs_total": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     "sphfsi_add_fluid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double]),
     "sphfsi_set_walls": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_double]),
     "sphfsi_add_solid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double,
@@ -130,50 +133,86 @@ def _f64(a, shape=None):
     return a if shape is None else a.reshape(shape)
 
 
+def _params(dim, gravity=(0, 0, 0), periodic_x=0, x_lo=0.0, Lx=0.0, free_surface=0, n_reinit=0,
+            domain_lo=(0, 0, 0), domain_hi=(1, 1, 1)):
+    p = Params()
+    p.dim, p.periodic_x, p.x_lo, p.Lx = dim, int(periodic_x), float(x_lo), float(Lx)
+    p.free_surface, p.n_reinit = int(free_surface), int(n_reinit)
+    for k in range(3):
+        p.gravity[k] = float(gravity[k]) if k < len(gravity) else 0.0
+        p.domain_lo[k] = float(domain_lo[k]) if k < len(domain_lo) else 0.0
+        p.domain_hi[k] = float(domain_hi[k]) if k < len(domain_hi) else 1.0
+    return p
+
+
+def _case_params(case):
+    return _params(case.dim, case.gravity, case.periodic_x, case.x_lo, case.Lx, case.free_surface,
+                   case.n_reinit, case.domain_lo, case.domain_hi)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
 class Simulation:
-    """One FSI problem on the current CUDA device (see include/sphfsi.h)."""
+    """One FSI problem, or a batch of independent ones, on the current CUDA
+    device (see include/sphfsi.h).  Per-instance calls act on the instance
+    chosen by select()."""
 
     def __init__(self, dim, gravity=(0, 0, 0), periodic_x=0, x_lo=0.0, Lx=0.0, free_surface=0,
-                 n_reinit=0, domain_lo=(0, 0, 0), domain_hi=(1, 1, 1), stream=None):
+                 n_reinit=0, domain_lo=(0, 0, 0), domain_hi=(1, 1, 1), stream=None, params=None):
         L = lib()
-        p = Params()
-        p.dim, p.periodic_x, p.x_lo, p.Lx = dim, int(periodic_x), float(x_lo), float(Lx)
-        p.free_surface, p.n_reinit = int(free_surface), int(n_reinit)
-        for k in range(3):
-            p.gravity[k] = float(gravity[k]) if k < len(gravity) else 0.0
-            p.domain_lo[k] = float(domain_lo[k]) if k < len(domain_lo) else 0.0
-            p.domain_hi[k] = float(domain_hi[k]) if k < len(domain_hi) else 1.0
-        if stream is None:
-            st = 0
-        elif isinstance(stream, int):
-            st = stream
-        else:
-            st = stream.cuda_stream
+        if params is None:
+            params = [_params(dim, gravity, periodic_x, x_lo, Lx, free_surface, n_reinit, domain_lo, domain_hi)]
+        arr = (Params * len(params))(*params)
         self._stream = stream
         h = _vp()
-        _check(L.sphfsi_create(C.byref(h), C.byref(p), st), "sphfsi_create")
+        _check(L.sphfsi_create_batch(C.byref(h), len(params), arr, _stream_handle(stream)), "sphfsi_create_batch")
         self.h = h
         self.dim = dim
-        self.nf = self.ns = self.nw = 0
-        self._keep = []
+        self.n_instances = len(params)
+        self._sel = 0
+        self._counts = [[0, 0, 0] for _ in params]   # nf, ns, nw per instance
+
+    @property
+    def nf(self):
+        return self._counts[self._sel][0]
+
+    @property
+    def ns(self):
+        return self._counts[self._sel][1]
+
+    @property
+    def nw(self):
+        return self._counts[self._sel][2]
+
+    def select(self, b):
+        """Address instance b with the per-instance calls."""
+        _check(lib().sphfsi_select(self.h, int(b)), "sphfsi_select")
+        self._sel = int(b)
+        return self
 
     # --- set-up -----------------------------------------------------------
     def add_fluid(self, r, v, p_init, dp, rho0, c0, eta):
         r, v = _f64(r), _f64(v)
         p = None if p_init is None else _f64(p_init)
-        self.nf = len(r)
+        self._counts[self._sel][0] = len(r)
         _check(lib().sphfsi_add_fluid(self.h, self.nf, _ptr(r), _ptr(v), _ptr(p), dp, rho0, c0, eta),
                "sphfsi_add_fluid")
 
     def set_walls(self, r, nrm, dp):
         r, nrm = _f64(r), _f64(nrm)
-        self.nw = len(r)
+        self._counts[self._sel][2] = len(r)
         _check(lib().sphfsi_set_walls(self.h, self.nw, _ptr(r), _ptr(nrm), dp), "sphfsi_set_walls")
 
     def add_solid(self, r0, v0, n0, constrained, dp, rho0, E, nu):
         r0, v0, n0 = _f64(r0), _f64(v0), _f64(n0)
         cons = np.ascontiguousarray(np.asarray(constrained, np.uint8))
-        self.ns = len(r0)
+        self._counts[self._sel][1] = len(r0)
         _check(lib().sphfsi_add_solid(self.h, self.ns, _ptr(r0), _ptr(v0), _ptr(n0), _ptr(cons), dp, rho0, E,
                                       nu), "sphfsi_add_solid")
 
@@ -185,21 +224,40 @@ class Simulation:
         _check(lib().sphfsi_finalize(self.h), "sphfsi_finalize")
         return self
 
+    def _add_case(self, case):
+        self.add_fluid(case.f_r, case.f_v, case.f_p, case.f_dp, case.f_rho0, case.f_c0, case.f_eta)
+        if case.nw:
+            self.set_walls(case.w_r, case.w_n, case.w_dp)
+        if case.ns:
+            self.add_solid(case.s_r0, case.s_v0, case.s_n0, case.s_cons, case.s_dp, case.s_rho0, case.s_E,
+                           case.s_nu)
+        if case.inflow_on:
+            self.set_inflow(1, case.inflow_profile, case.inflow_width, case.inflow_y0, case.inflow_H,
+                            case.inflow_U, case.inflow_tramp)
+
     @classmethod
     def from_case(cls, case, stream=None):
         """Build from any object with the attributes of a test/bench case."""
-        s = cls(case.dim, case.gravity, case.periodic_x, case.x_lo, case.Lx, case.free_surface,
-                case.n_reinit, case.domain_lo, case.domain_hi, stream=stream)
-        s.add_fluid(case.f_r, case.f_v, case.f_p, case.f_dp, case.f_rho0, case.f_c0, case.f_eta)
-        if case.nw:
-            s.set_walls(case.w_r, case.w_n, case.w_dp)
-        if case.ns:
-            s.add_solid(case.s_r0, case.s_v0, case.s_n0, case.s_cons, case.s_dp, case.s_rho0, case.s_E,
-                        case.s_nu)
-        if case.inflow_on:
-            s.set_inflow(1, case.inflow_profile, case.inflow_width, case.inflow_y0, case.inflow_H,
-                         case.inflow_U, case.inflow_tramp)
+        s = cls(case.dim, stream=stream, params=[_case_params(case)])
+        s._add_case(case)
         return s.finalize()
+
+    @classmethod
+    def from_cases(cls, cases, stream=None):
+        """One batched context holding every case as an independent instance."""
+        cases = list(cases)
+        s = cls(cases[0].dim, stream=stream, params=[_case_params(c) for c in cases])
+        for b, case in enumerate(cases):
+            s.select(b)
+            s._add_case(case)
+        s.finalize()
+        return s.select(0)
+
+    def pairs_total(self):
+        """Pair interactions of all instances since creation."""
+        t = C.c_int64()
+        _check(lib().sphfsi_pairs_total(self.h, C.byref(t)), "sphfsi_pairs_total")
+        return t.value
 
     # --- stepping ---------------------------------------------------------
     def set_substeps(self, K):

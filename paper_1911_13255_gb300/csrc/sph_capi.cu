@@ -1,5 +1,6 @@
-// C-ABI of the sphfsi library (include/sphfsi.h): context, set-up, the
-// per-step launch sequence a1..a8 and its CUDA-graph replay, state I/O.
+// C-ABI of the sphfsi library (include/sphfsi.h): contexts of one or more
+// independent instances, set-up, the per-step launch sequence a1..a8 and its
+// CUDA-graph replay, state I/O.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -13,14 +14,12 @@
 
 using namespace sph;
 
-struct sphfsi_ctx {
-    sphfsi_params prm;
-    sphfsi_inflow inflow;
-    cudaStream_t st;
-    int dim;
-    bool finalized = false;
-    int K_fixed = 0;
-    // host staging until finalize
+namespace {
+
+// host staging and bookkeeping of one instance
+struct InstHost {
+    sphfsi_params prm{};
+    sphfsi_inflow inflow{};
     int64_t nf = 0, nw = 0, ns = 0;
     std::vector<double> f_r, f_v, f_p;
     bool f_has_p = false, f_added = false, w_added = false, s_added = false;
@@ -31,32 +30,43 @@ struct sphfsi_ctx {
     std::vector<uint8_t> s_cons;
     std::vector<int> s_order;   // device (locality) index -> original solid index
     double s_dp = 0, s_rho0 = 1, s_E = 1, s_nu = 0.3;
+    Inst d{};                   // descriptor as uploaded
+};
+
+}  // namespace
+
+struct sphfsi_ctx {
+    cudaStream_t st = nullptr;
+    int dim = 2;
+    int B = 1;
+    int sel = 0;
+    bool finalized = false;
+    int K_fixed = 0;
+    std::vector<InstHost> ih;
     // device
-    Grid g{};
-    Phys P{};
     Fluid F{};
     Walls W{};
     Solid S{};
+    Batch bt{};
+    Inst *d_inst = nullptr;
     Ctl *ctl = nullptr;
     std::vector<void *> allocs;
     // graph replay
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = 0.0;
     int graph_K = -1;
+    int graph_prof = -1;
     int solid_path = 0;
-    unsigned long long ss_pairs = 0;
     int last_status = 0;
-    // per-stage CUDA events (sphfsi_set_profiling): start, solid binned,
-    // fluid sorted, reinit, momentum, solid-side force, continuity (main
-    // stream), solid sub-steps begin/end (side stream), end of step
+    // per-stage CUDA events (sphfsi_set_profiling): start, control, binning,
+    // reinit, momentum, continuity (main stream); branch start, coupling
+    // force done, sub-steps done (side stream); end of step
     static constexpr int kStages = 8;
     static constexpr int kEvents = 10;
     bool profiling = false;
-    int graph_prof = -1;
     cudaEvent_t ev[kEvents] = {};
     int kernels_per_step = 0;
-    // side stream for the solid sub-steps, which run concurrently with the
-    // continuity kernel (both need only the coupling force and the records)
+    // side stream for the solid branch, which runs beside momentum and continuity
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
@@ -82,10 +92,10 @@ int dalloc(sphfsi_ctx *c, T **p, size_t count)
     return SPHFSI_OK;
 }
 
-#define TRY(x)                         \
-    do {                               \
-        int _rc = (x);                 \
-        if (_rc) return _rc < -7 ? SPHFSI_E_CUDA : _rc; \
+#define TRY(x)                                              \
+    do {                                                    \
+        int _rc = (x);                                      \
+        if (_rc) return _rc < -7 ? SPHFSI_E_CUDA : _rc;     \
     } while (0)
 
 // copy n elements from a user pointer (host or device) into a host vector
@@ -149,12 +159,6 @@ double lattice_sigma0(int dim, double dp, double h)
     return s;
 }
 
-__global__ void k_set_step(Ctl *ctl, double dt_fixed, int K_fixed)
-{
-    ctl->dt_fixed = dt_fixed;
-    ctl->K_fixed = K_fixed;
-}
-
 // stage boundary: an event record when profiling (captured as an event node
 // inside a graph thanks to cudaEventRecordExternal)
 int mark(sphfsi_ctx *c, int k, cudaStream_t st)
@@ -167,36 +171,37 @@ int mark(sphfsi_ctx *c, int k) { return mark(c, k, c->st); }
 int enqueue_step(sphfsi_ctx *c, double dt)
 {
     cudaStream_t st = c->st;
+    const int D = c->dim;
     TRY(mark(c, 0));
-    // dt_F, K, reinit flag; a3 normal update before the solid records are built
-    TRY(launch_control_normals(c->ctl, c->P, c->S, dt > 0.0 ? dt : 0.0, c->K_fixed, st));
+    // dt_F, K, reinit flag per instance; a3 normal update before the solid records
+    TRY(launch_control_normals(c->bt, c->S, dt > 0.0 ? dt : 0.0, c->K_fixed, D, st));
     TRY(mark(c, 1));
     // a1 + a2: inflow, fluid first half drift; fluid (r^{n+1/2}) and solid
     // (r^n) binning, counting sort and FP32 records
-    TRY(launch_bin_all(c->F, c->S, c->g, c->P, c->ctl, 1, st));
+    TRY(launch_bin_all(c->bt, c->F, c->S, D, 1, st));
     TRY(mark(c, 2));
     // a3: density reinitialisation (no-op on other steps)
-    TRY(launch_reinit(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
+    TRY(launch_reinit(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 3));
-    // The solid branch (a5 then a7 + a8) reads only the records written so
-    // far, so it runs on the side stream while the main stream does a4 and
-    // a6; the two join before finish.
+    // The solid branch (a5, then a7 + a8) depends only on the records written
+    // so far, so it runs on the side stream while the main stream does a4
+    // and a6; the two join before finish.
     if (c->S.n) {
         TRY(cuda_rc(cudaEventRecord(c->fork_ev, st)));
         TRY(cuda_rc(cudaStreamWaitEvent(c->side, c->fork_ev, 0)));
         TRY(mark(c, 4, c->side));
-        TRY(launch_solid_fluid_force(c->F, c->S, c->g, c->P, c->ctl, c->side));
+        TRY(launch_solid_fluid_force(c->bt, c->F, c->S, D, c->side));
         TRY(mark(c, 7, c->side));
-        TRY(launch_solid_substeps(c->S, c->P, c->ctl, &c->solid_path, c->side));
+        TRY(launch_solid_substeps(c->bt, c->S, c->ih[0].d.P, D, &c->solid_path, c->side));
         TRY(mark(c, 8, c->side));
         TRY(cuda_rc(cudaEventRecord(c->join_ev, c->side)));
     }
-    TRY(launch_momentum(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
+    TRY(launch_momentum(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 5));
-    TRY(launch_density(c->F, c->W, c->S, c->g, c->P, c->ctl, st));
+    TRY(launch_density(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 6));
     if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
-    TRY(launch_finish(c->ctl, c->ss_pairs, st));
+    TRY(launch_finish(c->bt, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
     c->kernels_per_step = 10 + (c->S.n ? 2 : 0);
@@ -216,6 +221,146 @@ void deinterleave(const std::vector<double> &src, int dim, int64_t n, std::vecto
     for (int k = 0; k < 3; k++) out[k].assign(n, 0.0);
     for (int64_t i = 0; i < n; i++)
         for (int k = 0; k < dim; k++) out[k][i] = src[i * dim + k];
+}
+
+int check_params(const sphfsi_params *p)
+{
+    if (!p || (p->dim != 2 && p->dim != 3)) return SPHFSI_E_INVAL;
+    if (p->periodic_x && !(p->Lx > 0.0)) return SPHFSI_E_INVAL;
+    for (int k = 0; k < p->dim; k++)
+        if (!(p->domain_hi[k] > p->domain_lo[k])) return SPHFSI_E_INVAL;
+    return SPHFSI_OK;
+}
+
+// grid and constants of one instance (cells of edge >= 2 h_F)
+int make_inst(const InstHost &h, int D, Inst &d)
+{
+    const double hF = 1.3 * h.f_dp;
+    Grid &g = d.g;
+    std::memset(&g, 0, sizeof(g));
+    int64_t ncell = 1;
+    for (int k = 0; k < 3; k++) {
+        if (k >= D) {
+            g.lo[k] = 0.0;
+            g.cs[k] = 1.0;
+            g.csf[k] = 1.0f;
+            g.cslo[k] = 0.0f;
+            g.nc[k] = 1;
+            continue;
+        }
+        double lo = h.prm.domain_lo[k], L = h.prm.domain_hi[k] - lo;
+        if (k == 0 && h.prm.periodic_x) {
+            lo = h.prm.x_lo;
+            L = h.prm.Lx;
+        }
+        int64_t n = (int64_t)std::floor(L / (2.0 * hF));
+        if (n < 1) n = 1;
+        if (k == 0 && h.prm.periodic_x && n < 3) return SPHFSI_E_INVAL;
+        g.lo[k] = lo;
+        g.nc[k] = (int)n;
+        g.cs[k] = L / (double)n;
+        g.csf[k] = (float)g.cs[k];
+        g.cslo[k] = (float)(g.cs[k] - (double)g.csf[k]);
+        ncell *= n;
+        if (ncell > ((int64_t)1 << 28)) return SPHFSI_E_CAPACITY;
+    }
+    g.ncell = (int)ncell;
+    g.periodic_x = h.prm.periodic_x;
+    g.x_lo = h.prm.x_lo;
+    g.Lx = h.prm.Lx;
+    Phys &P = d.P;
+    std::memset(&P, 0, sizeof(P));
+    const double pi = 3.14159265358979323846;
+    P.dim = D;
+    for (int k = 0; k < 3; k++) P.g[k] = (float)h.prm.gravity[k];
+    P.rho0 = (float)h.f_rho0;
+    P.c0 = (float)h.f_c0;
+    P.eta = (float)h.f_eta;
+    P.hF = (float)hF;
+    P.inv_hF = (float)(1.0 / hF);
+    P.rc2F = (float)(4.0 * hF * hF);
+    P.rc2F_d = 4.0 * hF * hF;
+    double alpha = D == 2 ? 7.0 / (4.0 * pi * hF * hF) : 21.0 / (16.0 * pi * hF * hF * hF);
+    P.WcF = (float)alpha;
+    P.dWcF = (float)(-5.0 * alpha / hF);
+    double VF = std::pow(h.f_dp, D);
+    P.mF = (float)(h.f_rho0 * VF);
+    P.p_coef = (float)(h.f_rho0 * h.f_c0 * h.f_c0 / 7.0);
+    P.inv_p_coef = (float)(7.0 / (h.f_rho0 * h.f_c0 * h.f_c0));
+    P.hreg = (float)(0.01 * hF);
+    P.sigma0 = (float)lattice_sigma0(D, h.f_dp, hF);
+    P.sigma0_d = lattice_sigma0(D, h.f_dp, hF);
+    P.alphaF_d = alpha;
+    P.ihF_hi = (float)(1.0 / hF);
+    P.ihF_lo = (float)(1.0 / hF - (double)P.ihF_hi);
+    double VW = h.w_dp > 0 ? std::pow(h.w_dp, D) : VF;
+    double VS = h.s_dp > 0 ? std::pow(h.s_dp, D) : VF;
+    P.VW = (float)VW;
+    P.VS = (float)VS;
+    P.VW_VF = (float)(VW / VF);
+    P.VS_VF = (float)(VS / VF);
+    P.VW_VF_d = VW / VF;
+    P.VS_VF_d = VS / VF;
+    P.free_surface = h.prm.free_surface;
+    P.hF_d = hF;
+    P.c0_d = h.f_c0;
+    P.eta_d = h.f_eta;
+    P.rho0_d = h.f_rho0;
+    if (h.ns > 0) {
+        double mu = h.s_E / (2.0 * (1.0 + h.s_nu));   // reading R10
+        double lam = 2.0 * mu * h.s_nu / (1.0 - 2.0 * h.s_nu);
+        P.rhoS = (float)h.s_rho0;
+        P.mS = (float)(h.s_rho0 * VS);
+        P.mu = (float)mu;
+        P.lam = (float)lam;
+        P.hS = (float)(1.3 * h.s_dp);
+        P.hS_d = 1.3 * h.s_dp;
+        P.cS_d = std::sqrt(h.s_E / (3.0 * (1.0 - 2.0 * h.s_nu)) / h.s_rho0);
+    }
+    P.inflow_on = h.inflow.on;
+    P.inflow_profile = h.inflow.profile;
+    P.in_w = h.inflow.width;
+    P.in_y0 = h.inflow.y0;
+    P.in_H = h.inflow.H;
+    P.in_U = h.inflow.U;
+    P.in_tramp = h.inflow.t_ramp;
+    return SPHFSI_OK;
+}
+
+// Locality order of a body on the device: lexicographic on the lattice index
+// along the axes sorted by decreasing extent, so that a particle's neighbours
+// sit within a few rows of it and mostly in the same CTA of the cluster
+// sub-step kernels.  Permutes the staged arrays in place.
+void locality_order(InstHost &h, int D)
+{
+    const int n = (int)h.ns;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int a = 0; a < n; a++)
+        for (int k = 0; k < D; k++) {
+            lo[k] = std::min(lo[k], h.s_r0[(size_t)a * D + k]);
+            hi[k] = std::max(hi[k], h.s_r0[(size_t)a * D + k]);
+        }
+    int ax[3] = {0, 1, 2};
+    std::sort(ax, ax + D, [&](int p, int q) { return hi[p] - lo[p] > hi[q] - lo[q]; });
+    std::vector<std::array<long long, 4>> key(n);
+    for (int a = 0; a < n; a++) {
+        for (int k = 0; k < 3; k++)
+            key[a][k] = k < D ? std::llround((h.s_r0[(size_t)a * D + ax[k]] - lo[ax[k]]) / h.s_dp) : 0;
+        key[a][3] = a;
+    }
+    std::sort(key.begin(), key.end());
+    h.s_order.resize(n);
+    for (int a = 0; a < n; a++) h.s_order[a] = (int)key[a][3];
+    auto perm_rows = [&](auto &v, int w) {
+        auto t = v;
+        for (int a = 0; a < n; a++)
+            for (int j = 0; j < w; j++) t[(size_t)a * w + j] = v[(size_t)h.s_order[a] * w + j];
+        v.swap(t);
+    };
+    perm_rows(h.s_r0, D);
+    perm_rows(h.s_v0, D);
+    perm_rows(h.s_n0, D);
+    perm_rows(h.s_cons, 1);
 }
 
 }  // namespace
@@ -238,21 +383,34 @@ const char *sphfsi_strerror(int code)
     }
 }
 
-int sphfsi_create(sphfsi_ctx **out, const sphfsi_params *p, void *cuda_stream)
+int sphfsi_create_batch(sphfsi_ctx **out, int32_t n, const sphfsi_params *p, void *cuda_stream)
 {
-    if (!out || !p) return SPHFSI_E_INVAL;
+    if (!out || !p || n < 1 || n > (1 << 20)) return SPHFSI_E_INVAL;
     *out = nullptr;
-    if (p->dim != 2 && p->dim != 3) return SPHFSI_E_INVAL;
-    if (p->periodic_x && !(p->Lx > 0.0)) return SPHFSI_E_INVAL;
-    for (int k = 0; k < p->dim; k++)
-        if (!(p->domain_hi[k] > p->domain_lo[k])) return SPHFSI_E_INVAL;
+    for (int b = 0; b < n; b++) {
+        TRY(check_params(p + b));
+        if (p[b].dim != p[0].dim) return SPHFSI_E_INVAL;
+    }
     sphfsi_ctx *c = new (std::nothrow) sphfsi_ctx();
     if (!c) return SPHFSI_E_NOMEM;
-    c->prm = *p;
-    c->dim = p->dim;
+    c->ih.resize(n);
+    for (int b = 0; b < n; b++) c->ih[b].prm = p[b];
+    c->B = n;
+    c->dim = p[0].dim;
     c->st = (cudaStream_t)cuda_stream;
-    std::memset(&c->inflow, 0, sizeof(c->inflow));
     *out = c;
+    return SPHFSI_OK;
+}
+
+int sphfsi_create(sphfsi_ctx **out, const sphfsi_params *p, void *cuda_stream)
+{
+    return sphfsi_create_batch(out, 1, p, cuda_stream);
+}
+
+int sphfsi_select(sphfsi_ctx *c, int32_t inst)
+{
+    if (!c || inst < 0 || inst >= c->B) return SPHFSI_E_INVAL;
+    c->sel = inst;
     return SPHFSI_OK;
 }
 
@@ -260,32 +418,34 @@ int sphfsi_add_fluid(sphfsi_ctx *c, int64_t n, const double *r, const double *v,
                      double rho0, double c0, double eta)
 {
     TRY(check_ctx(c, false));
-    if (c->f_added || n < 0 || n > (int64_t)1 << 30 || !(dp > 0) || !(rho0 > 0) || !(c0 > 0) || eta < 0)
+    InstHost &h = c->ih[c->sel];
+    if (h.f_added || n < 0 || n > (int64_t)1 << 30 || !(dp > 0) || !(rho0 > 0) || !(c0 > 0) || eta < 0)
         return SPHFSI_E_INVAL;
     if (n > 0 && (!r || !v)) return SPHFSI_E_INVAL;
-    TRY(fetch(c->f_r, r, (size_t)n * c->dim));
-    TRY(fetch(c->f_v, v, (size_t)n * c->dim));
-    c->f_has_p = p_init != nullptr;
-    if (p_init) TRY(fetch(c->f_p, p_init, (size_t)n));
-    c->nf = n;
-    c->f_dp = dp;
-    c->f_rho0 = rho0;
-    c->f_c0 = c0;
-    c->f_eta = eta;
-    c->f_added = true;
+    TRY(fetch(h.f_r, r, (size_t)n * c->dim));
+    TRY(fetch(h.f_v, v, (size_t)n * c->dim));
+    h.f_has_p = p_init != nullptr;
+    if (p_init) TRY(fetch(h.f_p, p_init, (size_t)n));
+    h.nf = n;
+    h.f_dp = dp;
+    h.f_rho0 = rho0;
+    h.f_c0 = c0;
+    h.f_eta = eta;
+    h.f_added = true;
     return SPHFSI_OK;
 }
 
 int sphfsi_set_walls(sphfsi_ctx *c, int64_t n, const double *r, const double *nrm, double dp)
 {
     TRY(check_ctx(c, false));
-    if (c->w_added || n < 0 || n > (int64_t)1 << 30 || !(dp > 0)) return SPHFSI_E_INVAL;
+    InstHost &h = c->ih[c->sel];
+    if (h.w_added || n < 0 || n > (int64_t)1 << 30 || !(dp > 0)) return SPHFSI_E_INVAL;
     if (n > 0 && (!r || !nrm)) return SPHFSI_E_INVAL;
-    TRY(fetch(c->w_r, r, (size_t)n * c->dim));
-    TRY(fetch(c->w_n, nrm, (size_t)n * c->dim));
-    c->nw = n;
-    c->w_dp = dp;
-    c->w_added = true;
+    TRY(fetch(h.w_r, r, (size_t)n * c->dim));
+    TRY(fetch(h.w_n, nrm, (size_t)n * c->dim));
+    h.nw = n;
+    h.w_dp = dp;
+    h.w_added = true;
     return SPHFSI_OK;
 }
 
@@ -293,20 +453,21 @@ int sphfsi_add_solid(sphfsi_ctx *c, int64_t n, const double *r0, const double *v
                      const uint8_t *constrained, double dp, double rho0, double E, double nu)
 {
     TRY(check_ctx(c, false));
-    if (c->s_added || n < 0 || n > (int64_t)1 << 26 || !(dp > 0) || !(rho0 > 0) || !(E > 0) || !(nu > -1.0) ||
+    InstHost &h = c->ih[c->sel];
+    if (h.s_added || n < 0 || n > (int64_t)1 << 26 || !(dp > 0) || !(rho0 > 0) || !(E > 0) || !(nu > -1.0) ||
         !(nu < 0.5))
         return SPHFSI_E_INVAL;
     if (n > 0 && (!r0 || !v0 || !n0 || !constrained)) return SPHFSI_E_INVAL;
-    TRY(fetch(c->s_r0, r0, (size_t)n * c->dim));
-    TRY(fetch(c->s_v0, v0, (size_t)n * c->dim));
-    TRY(fetch(c->s_n0, n0, (size_t)n * c->dim));
-    TRY(fetch(c->s_cons, constrained, (size_t)n));
-    c->ns = n;
-    c->s_dp = dp;
-    c->s_rho0 = rho0;
-    c->s_E = E;
-    c->s_nu = nu;
-    c->s_added = true;
+    TRY(fetch(h.s_r0, r0, (size_t)n * c->dim));
+    TRY(fetch(h.s_v0, v0, (size_t)n * c->dim));
+    TRY(fetch(h.s_n0, n0, (size_t)n * c->dim));
+    TRY(fetch(h.s_cons, constrained, (size_t)n));
+    h.ns = n;
+    h.s_dp = dp;
+    h.s_rho0 = rho0;
+    h.s_E = E;
+    h.s_nu = nu;
+    h.s_added = true;
     return SPHFSI_OK;
 }
 
@@ -314,330 +475,265 @@ int sphfsi_set_inflow(sphfsi_ctx *c, const sphfsi_inflow *f)
 {
     TRY(check_ctx(c, false));
     if (!f || (f->on && (!(f->width > 0) || (f->profile == 0 && !(f->H > 0))))) return SPHFSI_E_INVAL;
-    c->inflow = *f;
+    c->ih[c->sel].inflow = *f;
     return SPHFSI_OK;
 }
 
 int sphfsi_finalize(sphfsi_ctx *c)
 {
     TRY(check_ctx(c, false));
-    if (!c->f_added) return SPHFSI_E_STATE;
-    const int D = c->dim;
-    const double hF = 1.3 * c->f_dp;
-    // ---- grid: cells of edge >= 2 h_F
-    Grid &g = c->g;
-    std::memset(&g, 0, sizeof(g));
-    int64_t ncell = 1;
-    for (int k = 0; k < 3; k++) {
-        if (k >= D) {
-            g.lo[k] = 0.0;
-            g.cs[k] = 1.0;
-            g.csf[k] = 1.0f;
-            g.nc[k] = 1;
-            continue;
-        }
-        double lo = c->prm.domain_lo[k], L = c->prm.domain_hi[k] - lo;
-        if (k == 0 && c->prm.periodic_x) {
-            lo = c->prm.x_lo;
-            L = c->prm.Lx;
-        }
-        int64_t n = (int64_t)std::floor(L / (2.0 * hF));
-        if (n < 1) n = 1;
-        if (k == 0 && c->prm.periodic_x && n < 3) return SPHFSI_E_INVAL;
-        g.lo[k] = lo;
-        g.nc[k] = (int)n;
-        g.cs[k] = L / (double)n;
-        g.csf[k] = (float)g.cs[k];
-        ncell *= n;
-        if (ncell > ((int64_t)1 << 28)) return SPHFSI_E_CAPACITY;
+    const int D = c->dim, B = c->B;
+    // ---- per-instance descriptors and offsets
+    int64_t nf = 0, nw = 0, ns = 0, ncell = 0;
+    int max_ns = 0;
+    for (int b = 0; b < B; b++) {
+        InstHost &h = c->ih[b];
+        if (!h.f_added) return SPHFSI_E_STATE;
+        TRY(make_inst(h, D, h.d));
+        h.d.f0 = (int)nf;
+        h.d.nf = (int)h.nf;
+        h.d.w0 = (int)nw;
+        h.d.nw = (int)h.nw;
+        h.d.s0 = (int)ns;
+        h.d.ns = (int)h.ns;
+        h.d.c0 = (int)ncell;
+        nf += h.nf;
+        nw += h.nw;
+        ns += h.ns;
+        ncell += h.d.g.ncell;
+        max_ns = std::max(max_ns, (int)h.ns);
+        if (nf > ((int64_t)1 << 30) || nw > ((int64_t)1 << 30) || ns > ((int64_t)1 << 28) ||
+            ncell > ((int64_t)1 << 29))
+            return SPHFSI_E_CAPACITY;
+        if (h.ns > 0) locality_order(h, D);
     }
-    g.ncell = (int)ncell;
-    g.periodic_x = c->prm.periodic_x;
-    g.x_lo = c->prm.x_lo;
-    g.Lx = c->prm.Lx;
-    // ---- physical constants
-    Phys &P = c->P;
-    std::memset(&P, 0, sizeof(P));
-    const double pi = 3.14159265358979323846;
-    P.dim = D;
-    for (int k = 0; k < 3; k++) P.g[k] = (float)c->prm.gravity[k];
-    P.rho0 = (float)c->f_rho0;
-    P.c0 = (float)c->f_c0;
-    P.eta = (float)c->f_eta;
-    P.hF = (float)hF;
-    P.inv_hF = (float)(1.0 / hF);
-    P.rc2F = (float)(4.0 * hF * hF);
-    P.rc2F_d = 4.0 * hF * hF;
-    double alpha = D == 2 ? 7.0 / (4.0 * pi * hF * hF) : 21.0 / (16.0 * pi * hF * hF * hF);
-    P.WcF = (float)alpha;
-    P.dWcF = (float)(-5.0 * alpha / hF);
-    double VF = std::pow(c->f_dp, D);
-    P.mF = (float)(c->f_rho0 * VF);
-    P.p_coef = (float)(c->f_rho0 * c->f_c0 * c->f_c0 / 7.0);
-    P.inv_p_coef = (float)(7.0 / (c->f_rho0 * c->f_c0 * c->f_c0));
-    P.hreg = (float)(0.01 * hF);
-    P.sigma0 = (float)lattice_sigma0(D, c->f_dp, hF);
-    P.sigma0_d = lattice_sigma0(D, c->f_dp, hF);
-    P.alphaF_d = alpha;
-    double VW = c->w_dp > 0 ? std::pow(c->w_dp, D) : VF;
-    double VS = c->s_dp > 0 ? std::pow(c->s_dp, D) : VF;
-    P.VW = (float)VW;
-    P.VS = (float)VS;
-    P.VW_VF = (float)(VW / VF);
-    P.VS_VF = (float)(VS / VF);
-    P.VW_VF_d = VW / VF;
-    P.VS_VF_d = VS / VF;
-    P.free_surface = c->prm.free_surface;
-    P.hF_d = hF;
-    P.c0_d = c->f_c0;
-    P.eta_d = c->f_eta;
-    P.rho0_d = c->f_rho0;
-    if (c->ns > 0) {
-        double mu = c->s_E / (2.0 * (1.0 + c->s_nu));            // reading R10
-        double lam = 2.0 * mu * c->s_nu / (1.0 - 2.0 * c->s_nu);
-        P.rhoS = (float)c->s_rho0;
-        P.mS = (float)(c->s_rho0 * VS);
-        P.mu = (float)mu;
-        P.lam = (float)lam;
-        P.hS = (float)(1.3 * c->s_dp);
-        P.hS_d = 1.3 * c->s_dp;
-        P.cS_d = std::sqrt(c->s_E / (3.0 * (1.0 - 2.0 * c->s_nu)) / c->s_rho0);
-    }
-    P.inflow_on = c->inflow.on;
-    P.inflow_profile = c->inflow.profile;
-    P.in_w = c->inflow.width;
-    P.in_y0 = c->inflow.y0;
-    P.in_H = c->inflow.H;
-    P.in_U = c->inflow.U;
-    P.in_tramp = c->inflow.t_ramp;
-
-    // ---- control block
-    TRY(dalloc(c, &c->ctl, 1));
+    TRY(dalloc(c, &c->ctl, B));
+    TRY(dalloc(c, &c->d_inst, B));
     // ---- fluid
     Fluid &F = c->F;
-    F.n = (int)c->nf;
-    for (int b = 0; b < 2; b++) {
-        FluidState &S = F.s[b];
-        TRY(dalloc(c, &S.x, F.n));
-        TRY(dalloc(c, &S.y, F.n));
-        TRY(dalloc(c, &S.z, D == 3 ? F.n : 1));
-        TRY(dalloc(c, &S.vx, F.n));
-        TRY(dalloc(c, &S.vy, F.n));
-        TRY(dalloc(c, &S.vz, D == 3 ? F.n : 1));
-        TRY(dalloc(c, &S.drho, F.n));
-        TRY(dalloc(c, &S.rhodot, F.n));
-        TRY(dalloc(c, &S.id, F.n));
+    F.n = (int)nf;
+    for (int k = 0; k < 2; k++) {
+        FluidState &S = F.s[k];
+        TRY(dalloc(c, &S.x, nf));
+        TRY(dalloc(c, &S.y, nf));
+        TRY(dalloc(c, &S.z, D == 3 ? nf : 1));
+        TRY(dalloc(c, &S.vx, nf));
+        TRY(dalloc(c, &S.vy, nf));
+        TRY(dalloc(c, &S.vz, D == 3 ? nf : 1));
+        TRY(dalloc(c, &S.drho, nf));
+        TRY(dalloc(c, &S.rhodot, nf));
+        TRY(dalloc(c, &S.id, nf));
         if (D == 2) S.z = nullptr, S.vz = nullptr;
     }
-    TRY(dalloc(c, &F.P4, F.n));
-    TRY(dalloc(c, &F.V4, F.n));
-    TRY(dalloc(c, &F.W4, F.n));
-    TRY(dalloc(c, &F.dvdt, (size_t)F.n * D));
-    TRY(dalloc(c, &F.key, F.n));
-    TRY(dalloc(c, &F.perm, F.n));
-    TRY(dalloc(c, &F.cell_of, F.n));
-    TRY(dalloc(c, &F.cstart, (size_t)g.ncell + 1));
-    TRY(dalloc(c, &F.ccount, g.ncell));
-    {
-        std::vector<double> xyz[3];
-        deinterleave(c->f_r, D, c->nf, xyz);
-        std::vector<float> v[3];
-        for (int k = 0; k < 3; k++) v[k].assign(c->nf, 0.0f);
-        std::vector<float> drho(c->nf, 0.0f);
-        std::vector<int> id(c->nf);
-        double vmax = 0.0;
-        for (int64_t i = 0; i < c->nf; i++) {
-            double v2 = 0.0;
-            for (int k = 0; k < D; k++) {
-                v[k][i] = (float)c->f_v[i * D + k];
-                v2 += (double)v[k][i] * (double)v[k][i];
-            }
-            vmax = std::max(vmax, std::sqrt(v2));
-            if (c->f_has_p) {
-                // inverse of Eq. eqeos: rho - rho0 = rho0 expm1(log1p(7 p / (rho0 c0^2)) / 7)
-                double x = 7.0 * c->f_p[i] / (c->f_rho0 * c->f_c0 * c->f_c0);
-                if (!(x > -1.0)) return SPHFSI_E_INVAL;
-                drho[i] = (float)(c->f_rho0 * std::expm1(std::log1p(x) / 7.0));
-            }
-            id[i] = (int)i;
-        }
-        FluidState &S = F.s[0];
-        TRY(upload(c, S.x, xyz[0]));
-        TRY(upload(c, S.y, xyz[1]));
-        if (D == 3) TRY(upload(c, S.z, xyz[2]));
-        TRY(upload(c, S.vx, v[0]));
-        TRY(upload(c, S.vy, v[1]));
-        if (D == 3) TRY(upload(c, S.vz, v[2]));
-        TRY(upload(c, S.drho, drho));
-        TRY(upload(c, S.id, id));
-        Ctl h{};
-        h.vmaxF = 0;
-        float vmf = (float)vmax;
-        std::memcpy(&h.vmaxF, &vmf, 4);
-        h.n_reinit = c->prm.n_reinit;
-        // solid maxima at rest
-        if (c->ns > 0) {
-            double vs = 0.0;
-            for (int64_t a = 0; a < c->ns; a++) {
-                if (c->s_cons[a]) continue;
-                double v2 = 0.0;
-                for (int k = 0; k < D; k++) v2 += c->s_v0[a * D + k] * c->s_v0[a * D + k];
-                vs = std::max(vs, std::sqrt(v2));
-            }
-            float vsf = (float)vs;
-            std::memcpy(&h.vmaxS, &vsf, 4);
-        }
-        TRY(cuda_rc(cudaMemcpyAsync(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice, c->st)));
-        TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    }
+    TRY(dalloc(c, &F.inst, nf));
+    TRY(dalloc(c, &F.P4, nf));
+    TRY(dalloc(c, &F.V4, nf));
+    TRY(dalloc(c, &F.W4, nf));
+    TRY(dalloc(c, &F.L4, nf));
+    TRY(dalloc(c, &F.dvdt, (size_t)nf * D));
+    TRY(dalloc(c, &F.key, nf));
+    TRY(dalloc(c, &F.perm, nf));
+    TRY(dalloc(c, &F.cell_of, nf));
+    TRY(dalloc(c, &F.cstart, (size_t)ncell + 1));
+    TRY(dalloc(c, &F.ccount, ncell));
     // ---- walls
     Walls &W = c->W;
-    W.n = (int)c->nw;
-    {
-        TRY(dalloc(c, &W.x, W.n));
-        TRY(dalloc(c, &W.y, W.n));
-        TRY(dalloc(c, &W.z, D == 3 ? W.n : 1));
-        TRY(dalloc(c, &W.nx, W.n));
-        TRY(dalloc(c, &W.ny, W.n));
-        TRY(dalloc(c, &W.nz, D == 3 ? W.n : 1));
-        if (D == 2) W.z = nullptr, W.nz = nullptr;
-        TRY(dalloc(c, &W.A4, W.n));
-        TRY(dalloc(c, &W.N4, W.n));
-        TRY(dalloc(c, &W.key, W.n));
-        TRY(dalloc(c, &W.perm, W.n));
-        TRY(dalloc(c, &W.cell_of, W.n));
-        TRY(dalloc(c, &W.cstart, (size_t)g.ncell + 1));
-        TRY(dalloc(c, &W.ccount, g.ncell));
-        std::vector<double> xyz[3], nn[3];
-        deinterleave(c->w_r, D, c->nw, xyz);
-        deinterleave(c->w_n, D, c->nw, nn);
-        std::vector<float> nf[3];
-        for (int k = 0; k < 3; k++) nf[k].assign(nn[k].begin(), nn[k].end());
-        TRY(upload(c, W.x, xyz[0]));
-        TRY(upload(c, W.y, xyz[1]));
-        if (D == 3) TRY(upload(c, W.z, xyz[2]));
-        TRY(upload(c, W.nx, nf[0]));
-        TRY(upload(c, W.ny, nf[1]));
-        if (D == 3) TRY(upload(c, W.nz, nf[2]));
-        TRY(launch_wall_bin(W, g, c->st));
-    }
+    W.n = (int)nw;
+    TRY(dalloc(c, &W.inst, nw));
+    TRY(dalloc(c, &W.x, nw));
+    TRY(dalloc(c, &W.y, nw));
+    TRY(dalloc(c, &W.z, D == 3 ? nw : 1));
+    TRY(dalloc(c, &W.nx, nw));
+    TRY(dalloc(c, &W.ny, nw));
+    TRY(dalloc(c, &W.nz, D == 3 ? nw : 1));
+    if (D == 2) W.z = nullptr, W.nz = nullptr;
+    TRY(dalloc(c, &W.A4, nw));
+    TRY(dalloc(c, &W.N4, nw));
+    TRY(dalloc(c, &W.L4, nw));
+    TRY(dalloc(c, &W.key, nw));
+    TRY(dalloc(c, &W.perm, nw));
+    TRY(dalloc(c, &W.cell_of, nw));
+    TRY(dalloc(c, &W.cstart, (size_t)ncell + 1));
+    TRY(dalloc(c, &W.ccount, ncell));
     // ---- solid
     Solid &S = c->S;
-    S.n = (int)c->ns;
+    S.n = (int)ns;
+    S.max_ns = max_ns;
+    TRY(dalloc(c, &S.inst, ns));
+    TRY(dalloc(c, &S.x, ns));
+    TRY(dalloc(c, &S.y, ns));
+    TRY(dalloc(c, &S.z, D == 3 ? ns : 1));
+    TRY(dalloc(c, &S.x0, ns));
+    TRY(dalloc(c, &S.y0, ns));
+    TRY(dalloc(c, &S.z0, D == 3 ? ns : 1));
+    TRY(dalloc(c, &S.xs, ns));
+    TRY(dalloc(c, &S.ys, ns));
+    TRY(dalloc(c, &S.zs, D == 3 ? ns : 1));
+    if (D == 2) S.z = S.z0 = S.zs = nullptr;
+    TRY(dalloc(c, &S.v4, ns));
+    TRY(dalloc(c, &S.H, (size_t)9 * ns));
+    TRY(dalloc(c, &S.Hd, (size_t)9 * ns));
+    TRY(dalloc(c, &S.B0, (size_t)9 * ns));
+    TRY(dalloc(c, &S.Q4, (size_t)(D == 2 ? 1 : 3) * ns));
+    TRY(dalloc(c, &S.n0, (size_t)3 * ns));
+    TRY(dalloc(c, &S.nrm, (size_t)3 * ns));
+    TRY(dalloc(c, &S.cons, ns));
+    TRY(dalloc(c, &S.vbar, (size_t)3 * ns));
+    TRY(dalloc(c, &S.abar, (size_t)3 * ns));
+    TRY(dalloc(c, &S.asum, (size_t)3 * ns));
+    TRY(dalloc(c, &S.fF, (size_t)3 * ns));
+    TRY(dalloc(c, &S.nb_ptr, (size_t)ns + 1));
+    TRY(dalloc(c, &S.A4, ns));
+    TRY(dalloc(c, &S.VB4, ns));
+    TRY(dalloc(c, &S.AB4, ns));
+    TRY(dalloc(c, &S.N4, ns));
+    TRY(dalloc(c, &S.L4, ns));
+    TRY(dalloc(c, &S.key, ns));
+    TRY(dalloc(c, &S.perm, ns));
+    TRY(dalloc(c, &S.cell_of, ns));
+    TRY(dalloc(c, &S.cstart, (size_t)ncell + 1));
+    TRY(dalloc(c, &S.ccount, ncell));
+    TRY(dalloc(c, &S.bar, 2));
+    TRY(dalloc(c, &S.queue, 1));
+
+    // ---- concatenated host copies and upload
     {
-        int n = S.n;
-        TRY(dalloc(c, &S.x, n));
-        TRY(dalloc(c, &S.y, n));
-        TRY(dalloc(c, &S.z, D == 3 ? n : 1));
-        TRY(dalloc(c, &S.x0, n));
-        TRY(dalloc(c, &S.y0, n));
-        TRY(dalloc(c, &S.z0, D == 3 ? n : 1));
-        TRY(dalloc(c, &S.xs, n));
-        TRY(dalloc(c, &S.ys, n));
-        TRY(dalloc(c, &S.zs, D == 3 ? n : 1));
-        if (D == 2) S.z = S.z0 = S.zs = nullptr;
-        TRY(dalloc(c, &S.v4, n));
-        TRY(dalloc(c, &S.H, (size_t)9 * n));
-        TRY(dalloc(c, &S.Hd, (size_t)9 * n));
-        TRY(dalloc(c, &S.B0, (size_t)9 * n));
-        TRY(dalloc(c, &S.Q4, (size_t)(D == 2 ? 1 : 3) * n));
-        TRY(dalloc(c, &S.n0, (size_t)3 * n));
-        TRY(dalloc(c, &S.nrm, (size_t)3 * n));
-        TRY(dalloc(c, &S.cons, n));
-        TRY(dalloc(c, &S.vbar, (size_t)3 * n));
-        TRY(dalloc(c, &S.abar, (size_t)3 * n));
-        TRY(dalloc(c, &S.asum, (size_t)3 * n));
-        TRY(dalloc(c, &S.fF, (size_t)3 * n));
-        TRY(dalloc(c, &S.nb_ptr, (size_t)n + 1));
-        TRY(dalloc(c, &S.A4, n));
-        TRY(dalloc(c, &S.VB4, n));
-        TRY(dalloc(c, &S.AB4, n));
-        TRY(dalloc(c, &S.N4, n));
-        TRY(dalloc(c, &S.key, n));
-        TRY(dalloc(c, &S.perm, n));
-        TRY(dalloc(c, &S.cell_of, n));
-        TRY(dalloc(c, &S.cstart, (size_t)g.ncell + 1));
-        TRY(dalloc(c, &S.ccount, g.ncell));
-        TRY(dalloc(c, &S.bar, 2));
-        if (n > 0) {
-            // Locality order of the body on the device: lexicographic on the
-            // lattice index along the axes sorted by decreasing extent, so
-            // that a particle's neighbours sit within a few rows of it and
-            // mostly in the same CTA of the cluster-resident sub-step kernel.
-            {
-                double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-                for (int a = 0; a < n; a++)
-                    for (int k = 0; k < D; k++) {
-                        lo[k] = std::min(lo[k], c->s_r0[(size_t)a * D + k]);
-                        hi[k] = std::max(hi[k], c->s_r0[(size_t)a * D + k]);
-                    }
-                int ax[3] = {0, 1, 2};
-                std::sort(ax, ax + D, [&](int p, int q) { return hi[p] - lo[p] > hi[q] - lo[q]; });
-                std::vector<std::array<long long, 4>> key(n);
-                for (int a = 0; a < n; a++) {
-                    for (int k = 0; k < 3; k++)
-                        key[a][k] = k < D ? std::llround((c->s_r0[(size_t)a * D + ax[k]] - lo[ax[k]]) / c->s_dp) : 0;
-                    key[a][3] = a;
-                }
-                std::sort(key.begin(), key.end());
-                c->s_order.resize(n);
-                for (int a = 0; a < n; a++) c->s_order[a] = (int)key[a][3];
-                auto perm_rows = [&](auto &v, int w) {
-                    auto t = v;
-                    for (int a = 0; a < n; a++)
-                        for (int j = 0; j < w; j++) t[(size_t)a * w + j] = v[(size_t)c->s_order[a] * w + j];
-                    v.swap(t);
-                };
-                perm_rows(c->s_r0, D);
-                perm_rows(c->s_v0, D);
-                perm_rows(c->s_n0, D);
-                perm_rows(c->s_cons, 1);
-            }
-            std::vector<double> xyz[3];
-            deinterleave(c->s_r0, D, c->ns, xyz);
-            std::vector<float4> v4(n);
-            std::vector<float> n0(3 * (size_t)n, 0.0f);
-            std::vector<double> vbar(3 * (size_t)n, 0.0);
-            for (int a = 0; a < n; a++) {
-                double vv[3] = {0, 0, 0};
+        std::vector<double> fx(nf), fy(nf), fz(D == 3 ? nf : 0);
+        std::vector<float> fvx(nf), fvy(nf), fvz(D == 3 ? nf : 0), fdr(nf, 0.0f);
+        std::vector<int> fid(nf), finst(nf);
+        std::vector<double> wx(nw), wy(nw), wz(D == 3 ? nw : 0);
+        std::vector<float> wnx(nw), wny(nw), wnz(D == 3 ? nw : 0);
+        std::vector<int> winst(nw);
+        std::vector<double> sx(ns), sy(ns), sz(D == 3 ? ns : 0), svbar(3 * (size_t)ns, 0.0);
+        std::vector<float4> sv4(ns);
+        std::vector<float> sn0(3 * (size_t)ns, 0.0f);
+        std::vector<uint8_t> scons(ns);
+        std::vector<int> sinst(ns);
+        std::vector<Ctl> hctl(B);
+        std::vector<Inst> hinst(B);
+        for (int b = 0; b < B; b++) {
+            InstHost &h = c->ih[b];
+            const int f0 = h.d.f0, w0 = h.d.w0, s0 = h.d.s0;
+            double vmax = 0.0;
+            for (int64_t i = 0; i < h.nf; i++) {
+                fx[f0 + i] = h.f_r[i * D];
+                fy[f0 + i] = h.f_r[i * D + 1];
+                if (D == 3) fz[f0 + i] = h.f_r[i * D + 2];
+                fvx[f0 + i] = (float)h.f_v[i * D];
+                fvy[f0 + i] = (float)h.f_v[i * D + 1];
+                if (D == 3) fvz[f0 + i] = (float)h.f_v[i * D + 2];
+                double v2 = 0.0;
                 for (int k = 0; k < D; k++) {
-                    vv[k] = c->s_cons[a] ? 0.0 : c->s_v0[(size_t)a * D + k];
-                    n0[3 * a + k] = (float)c->s_n0[(size_t)a * D + k];
-                    vbar[3 * a + k] = vv[k];
+                    double vk = (double)(float)h.f_v[i * D + k];
+                    v2 += vk * vk;
                 }
-                v4[a] = make_float4((float)vv[0], (float)vv[1], (float)vv[2], 0.0f);
+                vmax = std::max(vmax, std::sqrt(v2));
+                if (h.f_has_p) {
+                    // inverse of Eq. eqeos: rho - rho0 = rho0 expm1(log1p(7 p / (rho0 c0^2)) / 7)
+                    double x = 7.0 * h.f_p[i] / (h.f_rho0 * h.f_c0 * h.f_c0);
+                    if (!(x > -1.0)) return SPHFSI_E_INVAL;
+                    fdr[f0 + i] = (float)(h.f_rho0 * std::expm1(std::log1p(x) / 7.0));
+                }
+                fid[f0 + i] = (int)i;
+                finst[f0 + i] = b;
             }
-            TRY(upload(c, S.x0, xyz[0]));
-            TRY(upload(c, S.y0, xyz[1]));
-            TRY(upload(c, S.x, xyz[0]));
-            TRY(upload(c, S.y, xyz[1]));
-            if (D == 3) {
-                TRY(upload(c, S.z0, xyz[2]));
-                TRY(upload(c, S.z, xyz[2]));
+            for (int64_t q = 0; q < h.nw; q++) {
+                wx[w0 + q] = h.w_r[q * D];
+                wy[w0 + q] = h.w_r[q * D + 1];
+                if (D == 3) wz[w0 + q] = h.w_r[q * D + 2];
+                wnx[w0 + q] = (float)h.w_n[q * D];
+                wny[w0 + q] = (float)h.w_n[q * D + 1];
+                if (D == 3) wnz[w0 + q] = (float)h.w_n[q * D + 2];
+                winst[w0 + q] = b;
             }
-            TRY(upload(c, S.v4, v4));
-            TRY(upload(c, S.n0, n0));
-            TRY(upload(c, S.nrm, n0));
-            TRY(upload(c, S.cons, c->s_cons));
-            TRY(upload(c, S.vbar, vbar));
-            // static reference neighbour list: counts, host scan, fill
-            int *counts = nullptr;
-            TRY(dalloc(c, &counts, n));
-            TRY(launch_solid_setup_count(S, P, counts, c->st));
-            std::vector<int> hc;
-            TRY(download(c, hc, counts, n));
-            std::vector<int> ptr(n + 1, 0);
-            S.max_nb = 0;
-            for (int a = 0; a < n; a++) {
-                ptr[a + 1] = ptr[a] + hc[a];
-                S.max_nb = std::max(S.max_nb, hc[a]);
+            double vs = 0.0;
+            for (int64_t a = 0; a < h.ns; a++) {
+                sx[s0 + a] = h.s_r0[a * D];
+                sy[s0 + a] = h.s_r0[a * D + 1];
+                if (D == 3) sz[s0 + a] = h.s_r0[a * D + 2];
+                double vv[3] = {0, 0, 0}, v2 = 0.0;
+                for (int k = 0; k < D; k++) {
+                    vv[k] = h.s_cons[a] ? 0.0 : h.s_v0[a * D + k];
+                    sn0[3 * (s0 + a) + k] = (float)h.s_n0[a * D + k];
+                    svbar[3 * (s0 + a) + k] = vv[k];
+                    v2 += vv[k] * vv[k];
+                }
+                vs = std::max(vs, std::sqrt(v2));
+                sv4[s0 + a] = make_float4((float)vv[0], (float)vv[1], (float)vv[2], 0.0f);
+                scons[s0 + a] = h.s_cons[a];
+                sinst[s0 + a] = b;
             }
-            S.nnz = ptr[n];
-            TRY(upload(c, S.nb_ptr, ptr));
-            TRY(dalloc(c, &S.nb, S.nnz));
-            TRY(launch_solid_setup_fill(S, P, c->st));
-            c->ss_pairs = (unsigned long long)S.nnz;
+            Ctl &ct = hctl[b];
+            std::memset(&ct, 0, sizeof(ct));
+            float vmf = (float)vmax, vsf = (float)vs;
+            std::memcpy(&ct.vmaxF, &vmf, 4);
+            std::memcpy(&ct.vmaxS, &vsf, 4);
+            ct.n_reinit = h.prm.n_reinit;
+            hinst[b] = h.d;
         }
+        FluidState &S0 = F.s[0];
+        TRY(upload(c, S0.x, fx));
+        TRY(upload(c, S0.y, fy));
+        if (D == 3) TRY(upload(c, S0.z, fz));
+        TRY(upload(c, S0.vx, fvx));
+        TRY(upload(c, S0.vy, fvy));
+        if (D == 3) TRY(upload(c, S0.vz, fvz));
+        TRY(upload(c, S0.drho, fdr));
+        TRY(upload(c, S0.id, fid));
+        TRY(upload(c, F.inst, finst));
+        TRY(upload(c, W.x, wx));
+        TRY(upload(c, W.y, wy));
+        if (D == 3) TRY(upload(c, W.z, wz));
+        TRY(upload(c, W.nx, wnx));
+        TRY(upload(c, W.ny, wny));
+        if (D == 3) TRY(upload(c, W.nz, wnz));
+        TRY(upload(c, W.inst, winst));
+        TRY(upload(c, S.x0, sx));
+        TRY(upload(c, S.y0, sy));
+        TRY(upload(c, S.x, sx));
+        TRY(upload(c, S.y, sy));
+        if (D == 3) {
+            TRY(upload(c, S.z0, sz));
+            TRY(upload(c, S.z, sz));
+        }
+        TRY(upload(c, S.v4, sv4));
+        TRY(upload(c, S.n0, sn0));
+        TRY(upload(c, S.nrm, sn0));
+        TRY(upload(c, S.cons, scons));
+        TRY(upload(c, S.vbar, svbar));
+        TRY(upload(c, S.inst, sinst));
+        TRY(upload(c, c->ctl, hctl));
+        TRY(upload(c, c->d_inst, hinst));
+    }
+    c->bt.I = c->d_inst;
+    c->bt.ctl = c->ctl;
+    c->bt.B = B;
+    c->bt.ncell = (int)ncell;
+    // ---- walls binned once; solid static neighbour list and B0
+    TRY(launch_wall_bin(c->bt, W, D, c->st));
+    if (ns > 0) {
+        int *counts = nullptr;
+        TRY(dalloc(c, &counts, ns));
+        TRY(launch_solid_setup_count(c->bt, S, D, counts, c->st));
+        std::vector<int> hc;
+        TRY(download(c, hc, counts, ns));
+        std::vector<int> ptr(ns + 1, 0);
+        S.max_nb = 0;
+        for (int64_t a = 0; a < ns; a++) {
+            ptr[a + 1] = ptr[a] + hc[a];
+            S.max_nb = std::max(S.max_nb, hc[a]);
+        }
+        S.nnz = ptr[ns];
+        std::vector<Inst> hinst(B);
+        for (int b = 0; b < B; b++) {
+            InstHost &h = c->ih[b];
+            h.d.nnz = ptr[h.d.s0 + h.d.ns] - ptr[h.d.s0];
+            hinst[b] = h.d;
+        }
+        TRY(upload(c, S.nb_ptr, ptr));
+        TRY(upload(c, c->d_inst, hinst));
+        TRY(dalloc(c, &S.nb, S.nnz));
+        TRY(launch_solid_setup_fill(c->bt, S, D, c->st));
     }
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     for (int k = 0; k < sphfsi_ctx::kEvents; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
@@ -645,9 +741,12 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(cuda_rc(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)));
     TRY(cuda_rc(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming)));
     c->finalized = true;
-    // release the host staging copies
-    c->f_r.clear(); c->f_v.clear(); c->f_p.clear();
-    c->w_r.clear(); c->w_n.clear();
+    // release the host staging copies that are not needed any more
+    for (auto &h : c->ih) {
+        h.f_r.clear(); h.f_v.clear(); h.f_p.clear();
+        h.w_r.clear(); h.w_n.clear();
+        h.s_r0.clear(); h.s_v0.clear(); h.s_n0.clear();
+    }
     return SPHFSI_OK;
 }
 
@@ -703,8 +802,10 @@ int sphfsi_sync(sphfsi_ctx *c)
     if (!c) return SPHFSI_E_INVAL;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     if (!c->finalized) return SPHFSI_OK;
+    std::vector<Ctl> h;
+    TRY(download(c, h, c->ctl, c->B));
     int status = 0;
-    TRY(cuda_rc(cudaMemcpy(&status, &c->ctl->status, sizeof(int), cudaMemcpyDeviceToHost)));
+    for (const Ctl &x : h) status |= x.status;
     c->last_status = status;
     if (status & ST_TIMEOUT) return SPHFSI_E_TIMEOUT;
     if (status & ST_NONFINITE) return SPHFSI_E_UNSTABLE;
@@ -715,16 +816,17 @@ int sphfsi_get_fluid(sphfsi_ctx *c, double *r, float *v, double *rho, float *drh
 {
     TRY(check_ctx(c, true));
     const int D = c->dim;
-    const int64_t n = c->nf;
+    const InstHost &h = c->ih[c->sel];
+    const int64_t n = h.nf, f0 = h.d.f0;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     const FluidState &S = c->F.s[0];
     std::vector<int> id;
-    TRY(download(c, id, S.id, n));
+    TRY(download(c, id, S.id + f0, n));
     if (r) {
         std::vector<double> x, y, z, out(n * D);
-        TRY(download(c, x, S.x, n));
-        TRY(download(c, y, S.y, n));
-        if (D == 3) TRY(download(c, z, S.z, n));
+        TRY(download(c, x, S.x + f0, n));
+        TRY(download(c, y, S.y + f0, n));
+        if (D == 3) TRY(download(c, z, S.z + f0, n));
         for (int64_t k = 0; k < n; k++) {
             out[(size_t)id[k] * D] = x[k];
             out[(size_t)id[k] * D + 1] = y[k];
@@ -734,9 +836,9 @@ int sphfsi_get_fluid(sphfsi_ctx *c, double *r, float *v, double *rho, float *drh
     }
     if (v) {
         std::vector<float> x, y, z, out(n * D);
-        TRY(download(c, x, S.vx, n));
-        TRY(download(c, y, S.vy, n));
-        if (D == 3) TRY(download(c, z, S.vz, n));
+        TRY(download(c, x, S.vx + f0, n));
+        TRY(download(c, y, S.vy + f0, n));
+        if (D == 3) TRY(download(c, z, S.vz + f0, n));
         for (int64_t k = 0; k < n; k++) {
             out[(size_t)id[k] * D] = x[k];
             out[(size_t)id[k] * D + 1] = y[k];
@@ -747,19 +849,19 @@ int sphfsi_get_fluid(sphfsi_ctx *c, double *r, float *v, double *rho, float *drh
     if (rho) {
         std::vector<float> d;
         std::vector<double> out(n);
-        TRY(download(c, d, S.drho, n));
-        for (int64_t k = 0; k < n; k++) out[id[k]] = c->f_rho0 + (double)d[k];
+        TRY(download(c, d, S.drho + f0, n));
+        for (int64_t k = 0; k < n; k++) out[id[k]] = h.f_rho0 + (double)d[k];
         TRY(deliver(rho, out));
     }
     if (drho_dt) {
         std::vector<float> d, out(n);
-        TRY(download(c, d, S.rhodot, n));
+        TRY(download(c, d, S.rhodot + f0, n));
         for (int64_t k = 0; k < n; k++) out[id[k]] = d[k];
         TRY(deliver(drho_dt, out));
     }
     if (dvdt) {
         std::vector<float> d, out(n * D);
-        TRY(download(c, d, c->F.dvdt, (size_t)n * D));
+        TRY(download(c, d, c->F.dvdt + (size_t)f0 * D, (size_t)n * D));
         for (int64_t k = 0; k < n; k++)
             for (int q = 0; q < D; q++) out[(size_t)id[k] * D + q] = d[(size_t)k * D + q];
         TRY(deliver(dvdt, out));
@@ -771,16 +873,17 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
 {
     TRY(check_ctx(c, true));
     const int D = c->dim;
-    const int64_t n = c->ns;
+    const InstHost &h = c->ih[c->sel];
+    const int64_t n = h.ns, s0 = h.d.s0;
     const Solid &S = c->S;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     if (n == 0) return SPHFSI_OK;
-    const std::vector<int> &ord = c->s_order;   // device index -> original index
+    const std::vector<int> &ord = h.s_order;   // device index -> original index
     if (r) {
         std::vector<double> x, y, z, out(n * D);
-        TRY(download(c, x, S.x, n));
-        TRY(download(c, y, S.y, n));
-        if (D == 3) TRY(download(c, z, S.z, n));
+        TRY(download(c, x, S.x + s0, n));
+        TRY(download(c, y, S.y + s0, n));
+        if (D == 3) TRY(download(c, z, S.z + s0, n));
         for (int64_t a = 0; a < n; a++) {
             size_t o = (size_t)ord[a] * D;
             out[o] = x[a];
@@ -790,34 +893,34 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
         TRY(deliver(r, out));
     }
     if (v) {
-        std::vector<float4> h;
-        TRY(download(c, h, S.v4, n));
+        std::vector<float4> hv;
+        TRY(download(c, hv, S.v4 + s0, n));
         std::vector<float> out(n * D);
         for (int64_t a = 0; a < n; a++) {
             size_t o = (size_t)ord[a] * D;
-            out[o] = h[a].x;
-            out[o + 1] = h[a].y;
-            if (D == 3) out[o + 2] = h[a].z;
+            out[o] = hv[a].x;
+            out[o + 1] = hv[a].y;
+            if (D == 3) out[o + 2] = hv[a].z;
         }
         TRY(deliver(v, out));
     }
     if (F) {
-        std::vector<float> h;
+        std::vector<float> hh;
         std::vector<double> out(n * D * D);
-        TRY(download(c, h, S.H, (size_t)9 * n));
+        TRY(download(c, hh, S.H + 9 * s0, (size_t)9 * n));
         for (int64_t a = 0; a < n; a++)
             for (int i = 0; i < D * D; i++)
-                out[(size_t)ord[a] * D * D + i] = (double)h[9 * a + i] + ((i % (D + 1)) == 0 ? 1.0 : 0.0);
+                out[(size_t)ord[a] * D * D + i] = (double)hh[9 * a + i] + ((i % (D + 1)) == 0 ? 1.0 : 0.0);
         TRY(deliver(F, out));
     }
     auto vec3 = [&](const auto *src, auto *dst, auto zero) -> int {
         using T = decltype(zero);
         if (!dst) return SPHFSI_OK;
-        std::vector<T> h, out(n * D);
-        int rc = download(c, h, src, (size_t)3 * n);
+        std::vector<T> hv, out(n * D);
+        int rc = download(c, hv, src + 3 * s0, (size_t)3 * n);
         if (rc) return rc;
         for (int64_t a = 0; a < n; a++)
-            for (int k = 0; k < D; k++) out[(size_t)ord[a] * D + k] = h[3 * a + k];
+            for (int k = 0; k < D; k++) out[(size_t)ord[a] * D + k] = hv[3 * a + k];
         return deliver(dst, out);
     };
     TRY(vec3(S.vbar, vbar, 0.0));
@@ -831,40 +934,34 @@ int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, cons
 {
     TRY(check_ctx(c, true));
     const int D = c->dim;
-    const int64_t n = c->nf;
+    const InstHost &h = c->ih[c->sel];
+    const int64_t n = h.nf, f0 = h.d.f0;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     FluidState &S = c->F.s[0];
-    // the state is written in original order (storage order = id = identity)
+    // the instance's slots are rewritten in original order (id = index)
     std::vector<int> cur_id;
-    TRY(download(c, cur_id, S.id, n));
+    TRY(download(c, cur_id, S.id + f0, n));
     std::vector<int> inv(n);
     for (int64_t k = 0; k < n; k++) inv[cur_id[k]] = (int)k;
-    auto reorder_f = [&](const float *dev, std::vector<float> &out) -> int {
-        std::vector<float> h;
-        int rc = download(c, h, dev, n);
+    auto reorder = [&](auto *dev, auto &out) -> int {
+        using V = typename std::remove_reference<decltype(out)>::type;
+        V hv;
+        int rc = download(c, hv, dev + f0, n);
         if (rc) return rc;
         out.resize(n);
-        for (int64_t i = 0; i < n; i++) out[i] = h[inv[i]];
-        return SPHFSI_OK;
-    };
-    auto reorder_d = [&](const double *dev, std::vector<double> &out) -> int {
-        std::vector<double> h;
-        int rc = download(c, h, dev, n);
-        if (rc) return rc;
-        out.resize(n);
-        for (int64_t i = 0; i < n; i++) out[i] = h[inv[i]];
+        for (int64_t i = 0; i < n; i++) out[i] = hv[inv[i]];
         return SPHFSI_OK;
     };
     std::vector<double> x, y, z;
     std::vector<float> vx, vy, vz, dr, rd;
-    TRY(reorder_d(S.x, x));
-    TRY(reorder_d(S.y, y));
-    if (D == 3) TRY(reorder_d(S.z, z));
-    TRY(reorder_f(S.vx, vx));
-    TRY(reorder_f(S.vy, vy));
-    if (D == 3) TRY(reorder_f(S.vz, vz));
-    TRY(reorder_f(S.drho, dr));
-    TRY(reorder_f(S.rhodot, rd));
+    TRY(reorder(S.x, x));
+    TRY(reorder(S.y, y));
+    if (D == 3) TRY(reorder(S.z, z));
+    TRY(reorder(S.vx, vx));
+    TRY(reorder(S.vy, vy));
+    if (D == 3) TRY(reorder(S.vz, vz));
+    TRY(reorder(S.drho, dr));
+    TRY(reorder(S.rhodot, rd));
     std::vector<double> in;
     if (r) {
         TRY(fetch(in, r, (size_t)n * D));
@@ -884,7 +981,7 @@ int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     }
     if (rho) {
         TRY(fetch(in, rho, (size_t)n));
-        for (int64_t i = 0; i < n; i++) dr[i] = (float)(in[i] - c->f_rho0);
+        for (int64_t i = 0; i < n; i++) dr[i] = (float)(in[i] - h.f_rho0);
     }
     if (drho_dt) {
         TRY(fetch(in, drho_dt, (size_t)n));
@@ -892,15 +989,19 @@ int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     }
     std::vector<int> id(n);
     for (int64_t i = 0; i < n; i++) id[i] = (int)i;
-    TRY(upload(c, S.x, x));
-    TRY(upload(c, S.y, y));
-    if (D == 3) TRY(upload(c, S.z, z));
-    TRY(upload(c, S.vx, vx));
-    TRY(upload(c, S.vy, vy));
-    if (D == 3) TRY(upload(c, S.vz, vz));
-    TRY(upload(c, S.drho, dr));
-    TRY(upload(c, S.rhodot, rd));
-    TRY(upload(c, S.id, id));
+    auto put = [&](auto *dev, const auto &hv) -> int {
+        if (hv.empty()) return SPHFSI_OK;
+        return cuda_rc(cudaMemcpyAsync(dev + f0, hv.data(), sizeof(hv[0]) * hv.size(), cudaMemcpyHostToDevice, c->st));
+    };
+    TRY(put(S.x, x));
+    TRY(put(S.y, y));
+    if (D == 3) TRY(put(S.z, z));
+    TRY(put(S.vx, vx));
+    TRY(put(S.vy, vy));
+    if (D == 3) TRY(put(S.vz, vz));
+    TRY(put(S.drho, dr));
+    TRY(put(S.rhodot, rd));
+    TRY(put(S.id, id));
     return cuda_rc(cudaStreamSynchronize(c->st));
 }
 
@@ -909,7 +1010,8 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
 {
     TRY(check_ctx(c, true));
     const int D = c->dim;
-    const int64_t n = c->ns;
+    const InstHost &h = c->ih[c->sel];
+    const int64_t n = h.ns, s0 = h.d.s0;
     Solid &S = c->S;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     if (n == 0) return SPHFSI_OK;
@@ -918,33 +1020,37 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
     auto to_dev = [&](int w) {
         std::vector<double> t(in.size());
         for (int64_t a = 0; a < n; a++)
-            for (int j = 0; j < w; j++) t[(size_t)a * w + j] = in[(size_t)c->s_order[a] * w + j];
+            for (int j = 0; j < w; j++) t[(size_t)a * w + j] = in[(size_t)h.s_order[a] * w + j];
         in.swap(t);
+    };
+    auto put = [&](auto *dev, const auto &hv) -> int {
+        if (hv.empty()) return SPHFSI_OK;
+        return cuda_rc(cudaMemcpyAsync(dev, hv.data(), sizeof(hv[0]) * hv.size(), cudaMemcpyHostToDevice, c->st));
     };
     if (r) {
         TRY(fetch(in, r, (size_t)n * D));
         to_dev(D);
         std::vector<double> xyz[3];
         deinterleave(in, D, n, xyz);
-        TRY(upload(c, S.x, xyz[0]));
-        TRY(upload(c, S.y, xyz[1]));
-        if (D == 3) TRY(upload(c, S.z, xyz[2]));
+        TRY(put(S.x + s0, xyz[0]));
+        TRY(put(S.y + s0, xyz[1]));
+        if (D == 3) TRY(put(S.z + s0, xyz[2]));
     }
     if (v) {
         TRY(fetch(in, v, (size_t)n * D));
         to_dev(D);
-        std::vector<float4> h(n);
+        std::vector<float4> hv(n);
         for (int64_t a = 0; a < n; a++)
-            h[a] = make_float4((float)in[a * D], (float)in[a * D + 1], D == 3 ? (float)in[a * D + 2] : 0.0f, 0.0f);
-        TRY(upload(c, S.v4, h));
+            hv[a] = make_float4((float)in[a * D], (float)in[a * D + 1], D == 3 ? (float)in[a * D + 2] : 0.0f, 0.0f);
+        TRY(put(S.v4 + s0, hv));
     }
     if (F) {
         TRY(fetch(in, F, (size_t)n * D * D));
         to_dev(D * D);
-        std::vector<float> h(9 * (size_t)n, 0.0f);
+        std::vector<float> hv(9 * (size_t)n, 0.0f);
         for (int64_t a = 0; a < n; a++)
-            for (int i = 0; i < D * D; i++) h[9 * a + i] = (float)(in[a * D * D + i] - ((i % (D + 1)) == 0 ? 1.0 : 0.0));
-        TRY(upload(c, S.H, h));
+            for (int i = 0; i < D * D; i++) hv[9 * a + i] = (float)(in[a * D * D + i] - ((i % (D + 1)) == 0 ? 1.0 : 0.0));
+        TRY(put(S.H + 9 * s0, hv));
     }
     auto put3 = [&](const double *src, auto *dev, auto zero) -> int {
         using T = decltype(zero);
@@ -952,10 +1058,10 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
         int rc = fetch(in, src, (size_t)n * D);
         if (rc) return rc;
         to_dev(D);
-        std::vector<T> h(3 * (size_t)n, (T)0);
+        std::vector<T> hv(3 * (size_t)n, (T)0);
         for (int64_t a = 0; a < n; a++)
-            for (int k = 0; k < D; k++) h[3 * a + k] = (T)in[a * D + k];
-        return upload(c, dev, h);
+            for (int k = 0; k < D; k++) hv[3 * a + k] = (T)in[a * D + k];
+        return put(dev + 3 * s0, hv);
     };
     TRY(put3(vbar, S.vbar, 0.0));
     TRY(put3(abar, S.abar, 0.0));
@@ -967,49 +1073,64 @@ int sphfsi_set_time(sphfsi_ctx *c, double t, int64_t step)
 {
     TRY(check_ctx(c, true));
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    Ctl h;
-    TRY(cuda_rc(cudaMemcpy(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost)));
-    h.t = t;
-    h.step = step;
-    return cuda_rc(cudaMemcpy(c->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+    Ctl hc;
+    Ctl *dc = c->ctl + c->sel;
+    TRY(cuda_rc(cudaMemcpy(&hc, dc, sizeof(Ctl), cudaMemcpyDeviceToHost)));
+    hc.t = t;
+    hc.step = step;
+    return cuda_rc(cudaMemcpy(dc, &hc, sizeof(Ctl), cudaMemcpyHostToDevice));
 }
 
 int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out)
 {
     if (!c || !out) return SPHFSI_E_INVAL;
     std::memset(out, 0, sizeof(*out));
-    out->n_fluid = c->nf;
-    out->n_solid = c->ns;
-    out->n_wall = c->nw;
+    const InstHost &h = c->ih[c->sel];
+    out->n_fluid = h.nf;
+    out->n_solid = h.ns;
+    out->n_wall = h.nw;
     if (!c->finalized) return SPHFSI_OK;
-    out->n_cells = c->g.ncell;
+    out->n_cells = h.d.g.ncell;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    Ctl h;
-    TRY(cuda_rc(cudaMemcpy(&h, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost)));
-    out->step = h.step;
-    out->t = h.t;
-    out->last_dt = h.last_dt;
-    out->last_K = h.last_K;
-    out->status = h.status;
-    out->pairs_ff = (int64_t)h.n_ff;
-    out->pairs_fw = (int64_t)h.n_fw;
-    out->pairs_fs = (int64_t)h.n_fs;
-    out->pairs_sf = (int64_t)h.n_sf;
-    out->pairs_ss = (int64_t)c->S.nnz;
-    out->pairs_total = (int64_t)h.pairs_total;
+    Ctl hc;
+    TRY(cuda_rc(cudaMemcpy(&hc, c->ctl + c->sel, sizeof(Ctl), cudaMemcpyDeviceToHost)));
+    out->step = hc.step;
+    out->t = hc.t;
+    out->last_dt = hc.last_dt;
+    out->last_K = hc.last_K;
+    out->status = hc.status;
+    out->pairs_ff = (int64_t)hc.n_ff;
+    out->pairs_fw = (int64_t)hc.n_fw;
+    out->pairs_fs = (int64_t)hc.n_fs;
+    out->pairs_sf = (int64_t)hc.n_sf;
+    out->pairs_ss = (int64_t)h.d.nnz;
+    out->pairs_total = (int64_t)hc.pairs_total;
     float f;
-    std::memcpy(&f, &h.vmaxF, 4);
+    std::memcpy(&f, &hc.vmaxF, 4);
     out->vmax_f = f;
-    std::memcpy(&f, &h.vmaxS, 4);
+    std::memcpy(&f, &hc.vmaxS, 4);
     out->vmax_s = f;
-    std::memcpy(&f, &h.amaxS, 4);
+    std::memcpy(&f, &hc.amaxS, 4);
     out->amax_s = f;
     for (int k = 0; k < 3; k++) {
-        out->mom_fs_fluid[k] = h.mom_fluid[k];
-        out->mom_fs_solid[k] = h.mom_solid[k];
+        out->mom_fs_fluid[k] = hc.mom_fluid[k];
+        out->mom_fs_solid[k] = hc.mom_solid[k];
     }
     out->solid_path = c->solid_path;
     out->kernels_per_step = c->kernels_per_step;
+    return SPHFSI_OK;
+}
+
+int sphfsi_pairs_total(sphfsi_ctx *c, int64_t *total)
+{
+    TRY(check_ctx(c, true));
+    if (!total) return SPHFSI_E_INVAL;
+    std::vector<Ctl> h;
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    TRY(download(c, h, c->ctl, c->B));
+    int64_t s = 0;
+    for (const Ctl &x : h) s += (int64_t)x.pairs_total;
+    *total = s;
     return SPHFSI_OK;
 }
 
@@ -1017,36 +1138,37 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
 {
     TRY(check_ctx(c, true));
     if (which < 0 || which > 3 || !nnz) return SPHFSI_E_INVAL;
-    int64_t nrows = which == 3 ? c->ns : c->nf;
+    const InstHost &h = c->ih[c->sel];
+    const int64_t nrows = which == 3 ? h.ns : h.nf;
     // bin the current positions (no drift) and build the solid records
-    TRY(launch_bin_all(c->F, c->S, c->g, c->P, c->ctl, 0, c->st));
+    TRY(launch_bin_all(c->bt, c->F, c->S, c->dim, 0, c->st));
     int *counts = nullptr, *offs = nullptr, *out = nullptr;
     if (cudaMalloc(&counts, sizeof(int) * (nrows + 1)) != cudaSuccess) return SPHFSI_E_NOMEM;
-    int rc = launch_debug_pairs(c->F, c->W, c->S, c->g, c->P, which, counts, nullptr, nullptr, c->st);
+    int rc = launch_debug_pairs(c->bt, c->F, c->W, c->S, c->dim, c->sel, which, counts, nullptr, nullptr, c->st);
     // solid rows (which 3) and solid columns (which 2) come in the device's
     // locality order; rows and columns are reported in original order
     std::vector<int> hc_dev, hc(nrows, 0);
     if (!rc) rc = download(c, hc_dev, counts, nrows);
-    for (int64_t i = 0; i < nrows && !rc; i++) hc[which == 3 ? c->s_order[i] : i] = hc_dev[i];
+    for (int64_t i = 0; i < nrows && !rc; i++) hc[which == 3 ? h.s_order[i] : i] = hc_dev[i];
     std::vector<int64_t> p(nrows + 1, 0);
     for (int64_t i = 0; i < nrows && !rc; i++) p[i + 1] = p[i] + hc[i];
     *nnz = p[nrows];
     if (!rc && ptr) std::memcpy(ptr, p.data(), sizeof(int64_t) * (nrows + 1));
     if (!rc && idx && p[nrows] > 0) {
         std::vector<int> po(nrows);
-        for (int64_t i = 0; i < nrows; i++) po[i] = (int)p[which == 3 ? c->s_order[i] : i];
+        for (int64_t i = 0; i < nrows; i++) po[i] = (int)p[which == 3 ? h.s_order[i] : i];
         if (cudaMalloc(&offs, sizeof(int) * nrows) != cudaSuccess || cudaMalloc(&out, sizeof(int) * p[nrows]) != cudaSuccess)
             rc = SPHFSI_E_NOMEM;
         if (!rc) rc = upload(c, offs, po);
-        if (!rc) rc = launch_debug_pairs(c->F, c->W, c->S, c->g, c->P, which, counts, offs, out, c->st);
-        std::vector<int> h;
-        if (!rc) rc = download(c, h, out, (size_t)p[nrows]);
+        if (!rc) rc = launch_debug_pairs(c->bt, c->F, c->W, c->S, c->dim, c->sel, which, counts, offs, out, c->st);
+        std::vector<int> hv;
+        if (!rc) rc = download(c, hv, out, (size_t)p[nrows]);
         if (!rc) {
             if (which == 2)
-                for (auto &col : h) col = c->s_order[col];
+                for (auto &col : hv) col = h.s_order[col];
             for (int64_t i = 0; i < nrows; i++) {
-                std::sort(h.begin() + p[i], h.begin() + p[i + 1]);
-                for (int64_t q = p[i]; q < p[i + 1]; q++) idx[q] = h[q];
+                std::sort(hv.begin() + p[i], hv.begin() + p[i + 1]);
+                for (int64_t q = p[i]; q < p[i + 1]; q++) idx[q] = hv[q];
             }
         }
     }
@@ -1060,6 +1182,7 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path)
 {
     TRY(check_ctx(c, true));
     if (path < 0 || path > 2) return SPHFSI_E_INVAL;
+    if (path == 2 && c->B != 1) return SPHFSI_E_INVAL;
     c->S.force_grid_path = path == 2 ? 1 : 0;
     c->S.force_lane_path = path == 1 ? 1 : 0;
     if (c->gexec) {
@@ -1082,7 +1205,7 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     if (!ms || n < sphfsi_ctx::kStages) return SPHFSI_E_INVAL;
     if (!c->profiling) return SPHFSI_E_STATE;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
-    auto el = [&](int a, int b, float *out) { return cuda_rc(cudaEventElapsedTime(out, c->ev[a], c->ev[b])); };
+    auto el = [&](int a, int b, float *o) { return cuda_rc(cudaEventElapsedTime(o, c->ev[a], c->ev[b])); };
     // events: 0 start, 1 control, 2 binning, 3 reinit, 5 momentum, 6 continuity
     // (main stream); 4 branch start, 7 coupling force done, 8 sub-steps done
     // (side stream); 9 end of step
@@ -1093,11 +1216,11 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     TRY(el(5, 6, &ms[5]));
     if (c->S.n) {
         float fin_a = 0.f, fin_b = 0.f;
-        TRY(el(4, 7, &ms[4]));                                 // coupling force (side stream)
-        TRY(el(7, 8, &ms[6]));                                 // solid sub-steps (side stream)
+        TRY(el(4, 7, &ms[4]));
+        TRY(el(7, 8, &ms[6]));
         TRY(el(6, 9, &fin_a));
         TRY(el(8, 9, &fin_b));
-        ms[7] = fin_a < fin_b ? fin_a : fin_b;                 // finish, after the join
+        ms[7] = fin_a < fin_b ? fin_a : fin_b;
     } else {
         ms[4] = ms[6] = 0.0f;
         TRY(el(6, 9, &ms[7]));
@@ -1119,8 +1242,8 @@ void sphfsi_destroy(sphfsi_ctx *c)
     if (!c) return;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (int k = 0; k < sphfsi_ctx::kEvents; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);

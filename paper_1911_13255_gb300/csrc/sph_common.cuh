@@ -1,5 +1,13 @@
 // Internal device data structures and helpers of the sphfsi library.
 // Method: Zhang, Rezavand & Hu, multi-resolution SPH for FSI (arXiv 1911.13255).
+//
+// A context holds B >= 1 independent problem instances.  Their particles are
+// concatenated (instance b owns fluid slots [f0, f0 + nf), wall slots
+// [w0, w0 + nw), solid slots [s0, s0 + ns)) and their cell grids are laid
+// end to end in one global cell index space (instance b owns cells
+// [c0, c0 + ncell)).  Every kernel looks up the instance of the slot it
+// works on and takes that instance's grid, constants and control block, so
+// one launch advances all instances; a single problem is a batch of one.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -10,22 +18,23 @@ namespace sph {
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
 constexpr int kBlock = 128;           // threads per block of the particle kernels
-constexpr int kSolidBlock = 256;      // threads per block of the solid sub-step kernel
+constexpr int kSolidBlock = 256;      // threads per block of the cooperative solid kernel
 constexpr long long kSpinLimit = 1ll << 22;   // bounded spin of the grid barrier (~0.5-2 s)
 
-// Fixed uniform cell grid with cell edge >= 2 h_F (support radius).  Linear
-// cell index = x + nc[0] * (y + nc[1] * z).
+// Fixed uniform cell grid with cell edge >= 2 h_F (support radius).  Local
+// cell index = x + nc[0] * (y + nc[1] * z); global index = c0 + local.
 struct Grid {
     double lo[3];
     double cs[3];    // cell edges (FP64), cs[0] = Lx / nc[0] when periodic in x
     float csf[3];    // the same edges rounded to FP32 (pair-loop offsets)
+    float cslo[3];   // cs - csf rounded to FP32 (double-float offsets of the reinitialisation)
     int nc[3];
     int ncell;
     int periodic_x;
     double x_lo, Lx;
 };
 
-// Device-resident control block: one per context, read by every kernel of a
+// Device-resident control block, one per instance, read by every kernel of a
 // step, so a captured step graph needs no host-side values.
 struct Ctl {
     double t;          // time at the start of the current step
@@ -48,7 +57,7 @@ struct Ctl {
     int last_K, pad3;
 };
 
-// Physical constants of the fluid, the walls and the solid (by value).
+// Physical constants of the fluid, the walls and the solid of one instance.
 struct Phys {
     int dim;
     float g[3];
@@ -67,6 +76,7 @@ struct Phys {
     double rc2F_d;    // (2 h_F)^2 in FP64 (debug neighbour sets)
     double hF_d, c0_d, eta_d, rho0_d;
     double alphaF_d, sigma0_d, VW_VF_d, VS_VF_d;   // FP64 number density
+    float ihF_hi, ihF_lo;   // 1 / h_F as a double-float pair
     // solid
     float rhoS, mS, mu, lam, hS;
     double hS_d, cS_d;
@@ -75,44 +85,59 @@ struct Phys {
     double in_w, in_y0, in_H, in_U, in_tramp;
 };
 
-// Fluid state, storage order = cell order of the last binning.
+// Per-instance descriptor (device table, one entry per instance).
+struct Inst {
+    Grid g;
+    Phys P;
+    int f0, nf, w0, nw, s0, ns;
+    int c0;          // global index of the instance's first cell
+    int nnz;         // static solid neighbour entries of the instance
+};
+
+// Fluid state, storage order = cell order of the last binning (the slots of
+// an instance stay inside its segment).
 struct FluidState {
     double *x, *y, *z;
     float *vx, *vy, *vz;
     float *drho;      // rho - rho0
     float *rhodot;    // density rate of the last step (reading R12)
-    int *id;          // original index
+    int *id;          // original index within the instance
 };
 
 struct Fluid {
-    int n;
+    int n;            // total over the instances
+    int *inst;        // instance of each slot
     FluidState s[2];
-    int cur;
     float4 *P4;       // (x - x_cell, y - y_cell, z - z_cell, p)   sorted records
     float4 *V4;       // (v^n, rho - rho0)
     float4 *W4;       // (v^{n+1}, rho - rho0)
+    float4 *L4;       // rel position - FP32(rel position), written on reinitialisation steps
     float *dvdt;      // n * dim, sorted order (a4 accelerations)
-    int *key;         // cell of each particle (storage order)
-    int *perm;        // sorted slot -> storage index
-    int *cell_of;     // cell of each sorted slot
-    int *cstart;      // ncell + 1
-    int *ccount;      // ncell (histogram / scatter cursor)
+    int *key;         // global cell of each particle (storage order)
+    int *perm;        // sorted slot -> storage slot
+    int *cell_of;     // global cell of each sorted slot
+    int *cstart;      // total cells + 1
+    int *ccount;      // total cells (histogram / scatter cursor)
 };
 
 // Static walls, binned once.
 struct Walls {
     int n;
+    int *inst;
     double *x, *y, *z;     // original order
     float *nx, *ny, *nz;
     float4 *A4;            // (rel position, 0) sorted
     float4 *N4;            // (normal, 0) sorted
+    float4 *L4;            // rel position - FP32(rel position), sorted
     int *key, *perm, *cstart, *ccount, *cell_of;
 };
 
-// Elastic body (original order) + its records in the fluid grid.
+// Elastic bodies (device locality order within each instance) + their
+// records in the fluid grid.
 struct Solid {
     int n;
     int nnz;
+    int *inst;
     double *x, *y, *z;        // current positions (FP64)
     double *x0, *y0, *z0;     // reference positions
     double *xs, *ys, *zs;     // positions at the start of the step
@@ -127,22 +152,31 @@ struct Solid {
     double *vbar, *abar;      // n * 3 time averages (FP64)
     double *asum;             // n * 3 sum of dt_S a over the sub-steps (FP64)
     float *fF;                // n * 3 fluid force of the step
-    int *nb_ptr;              // n + 1
-    float4 *nb;               // nnz: (V0 grad0_a W_ab, b as int bits in .w)
+    int *nb_ptr;              // n + 1 (global entry offsets)
+    float4 *nb;               // nnz: (V0 grad0_a W_ab, global b as int bits in .w)
     // records in the fluid grid (sorted by cell)
     float4 *A4, *VB4, *AB4, *N4;
+    float4 *L4;               // rel position - FP32(rel position), written on reinitialisation steps
     int *key, *perm, *cstart, *ccount, *cell_of;
     unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
+    unsigned *queue;          // persistent solid kernel: next instance to take
     int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
     int force_lane_path;      // 1: in 2-D use the 4-lane cluster kernel, not the one-thread one
     int max_nb;               // largest static neighbour count of a particle
+    int max_ns;               // largest body of an instance
+};
+
+// What every kernel needs to find an instance.
+struct Batch {
+    const Inst *__restrict__ I;   // device table [B]
+    Ctl *ctl;                     // device control blocks [B]
+    int B;
+    int ncell;                    // total cells
 };
 
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned fbits(float f) { return __float_as_uint(f); }
-
 __device__ __forceinline__ void atomic_max_pos(unsigned *addr, float v)
 {
     // non-negative floats order like their bit patterns; NaN (0x7fc...) wins
@@ -168,6 +202,14 @@ __device__ __forceinline__ unsigned warp_sum_u(unsigned v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Per-warp reduction into per-instance counters.  Lanes of a warp may belong
+// to different instances (at segment boundaries): lanes whose instance equals
+// the warp's first lane's are reduced with shuffles, the others add directly.
+__device__ __forceinline__ bool warp_uniform(int b)
+{
+    return __all_sync(0xffffffffu, b == __shfl_sync(0xffffffffu, b, 0));
 }
 
 // cell coordinates of a position (FP64, clamped into the grid)
@@ -196,47 +238,30 @@ __device__ __forceinline__ float dW_F(float r, const Phys &P)
     float a = 1.0f - 0.5f * q;
     return P.dWcF * q * a * a * a;
 }
-__device__ __forceinline__ float W_F(float r, const Phys &P)
-{
-    float q = r * P.inv_hF;
-    float a = 1.0f - 0.5f * q;
-    float a2 = a * a;
-    return P.WcF * a2 * a2 * (1.0f + 2.0f * q);
-}
 
 // ---------------------------------------------------------------------------
 // host-side launch wrappers (implemented in the .cu files)
 // ---------------------------------------------------------------------------
-int launch_control(Ctl *ctl, const Phys &P, int has_solid, cudaStream_t st);
-int launch_control_normals(Ctl *ctl, const Phys &P, const Solid &s, double dt_fixed, int K_fixed, cudaStream_t st);
-int launch_bin_all(Fluid &f, Solid &s, const Grid &g, const Phys &P, Ctl *ctl, int do_drift, cudaStream_t st);
-int launch_finish(Ctl *ctl, unsigned long long ss_pairs_per_step, cudaStream_t st);
-
-// binning / counting sort (sph_grid.cu)
-int launch_fluid_drift_bin(const Fluid &f, const Grid &g, const Phys &P, Ctl *ctl, int do_drift,
-                           cudaStream_t st);
+// control, binning / counting sort, finish (sph_grid.cu)
+int launch_control_normals(const Batch &bt, const Solid &s, double dt_fixed, int K_fixed, int dim, cudaStream_t st);
+int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int do_drift, cudaStream_t st);
+int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
+int launch_finish(const Batch &bt, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);
 int launch_scatter(const int *key, const int *cstart, int *ccount, int *perm, int n, cudaStream_t st);
-int launch_fluid_reorder(Fluid &f, const Grid &g, const Phys &P, cudaStream_t st);
-int launch_wall_bin(Walls &w, const Grid &g, cudaStream_t st);
-int launch_solid_bin(Solid &s, const Grid &g, const Phys &P, Ctl *ctl, cudaStream_t st);
-int launch_solid_normals(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st);
 
 // fluid pair loops (sph_fluid.cu)
-int launch_reinit(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                  cudaStream_t st);
-int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                    cudaStream_t st);
-int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                             cudaStream_t st);
-int launch_density(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                   cudaStream_t st);
-int launch_debug_pairs(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, int which,
-                       int *counts, int *offs, int *out, cudaStream_t st);
+int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
+int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
+int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, int dim, cudaStream_t st);
+int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
+int launch_debug_pairs(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, int inst,
+                       int which, int *counts, int *offs, int *out, cudaStream_t st);
 
 // solid (sph_solid.cu)
-int launch_solid_setup_count(Solid &s, const Phys &P, int *counts, cudaStream_t st);
-int launch_solid_setup_fill(Solid &s, const Phys &P, cudaStream_t st);
-int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStream_t st);
+int launch_solid_setup_count(const Batch &bt, Solid &s, int dim, int *counts, cudaStream_t st);
+int launch_solid_setup_fill(const Batch &bt, Solid &s, int dim, cudaStream_t st);
+// P0: host copy of instance 0's constants (used when the batch holds one instance)
+int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, int *path, cudaStream_t st);
 
 }  // namespace sph

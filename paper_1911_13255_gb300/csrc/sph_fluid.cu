@@ -21,7 +21,7 @@ template <int D> struct Lanes { static constexpr int L = D == 2 ? 4 : 8; };
 // Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz)
 // receives the offset o = -(dcell) * edge to add to (rel_i - rel_j).
 template <int D, typename Fn>
-__device__ __forceinline__ void for_each_cell(const Grid &g, int cx, int cy, int cz, Fn &&fn)
+__device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int cy, int cz, Fn &&fn)
 {
     const int z0 = D == 3 ? -1 : 0, z1 = D == 3 ? 1 : 0;
 #pragma unroll 1
@@ -39,7 +39,7 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, int cx, int cy, int
                     if (!g.periodic_x) continue;
                     x = x < 0 ? x + g.nc[0] : x - g.nc[0];
                 }
-                int c = x + g.nc[0] * (y + g.nc[1] * z);
+                int c = c0 + x + g.nc[0] * (y + g.nc[1] * z);
                 fn(c, -(float)dx * g.csf[0], -(float)dy * g.csf[1], -(float)dz * g.csf[2]);
             }
         }
@@ -78,8 +78,11 @@ __device__ __forceinline__ float eos_dp(float drho_i, float drho_j, const Phys &
     return P.p_coef * ((drho_i - drho_j) * inv) * s;
 }
 
-__device__ __forceinline__ void cell_xyz(int key, const Grid &g, int &cx, int &cy, int &cz)
+// local cell coordinates of a global cell index
+__device__ __forceinline__ void cell_xyz(int gkey, const Inst &In, int &cx, int &cy, int &cz)
 {
+    const Grid &g = In.g;
+    const int key = gkey - In.c0;
     cx = key % g.nc[0];
     cy = (key / g.nc[0]) % g.nc[1];
     cz = key / (g.nc[0] * g.nc[1]);
@@ -153,6 +156,53 @@ __device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float
     return d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
 }
 
+// Add per-thread counters to the thread's instance control block: one
+// atomic per warp when the warp's lanes share an instance, else per lane.
+struct Counts {
+    unsigned ff, fw, fs, sf;
+    float vmax;
+    double mom[3];
+};
+
+template <int D>
+__device__ __forceinline__ void flush_counts(Batch bt, int b, bool valid, Counts c, bool fluid_side)
+{
+    if (warp_uniform(valid ? b : -1)) {
+        unsigned ff = warp_sum_u(c.ff), fw = warp_sum_u(c.fw), fs = warp_sum_u(c.fs), sf = warp_sum_u(c.sf);
+        float vm = warp_max(c.vmax);
+        double m[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < D; k++) m[k] = warp_sum_d(c.mom[k]);
+        if ((threadIdx.x & 31) == 0 && valid) {
+            Ctl *ctl = bt.ctl + b;
+            if (ff) atomicAdd(&ctl->n_ff, (unsigned long long)ff);
+            if (fw) atomicAdd(&ctl->n_fw, (unsigned long long)fw);
+            if (fs) atomicAdd(&ctl->n_fs, (unsigned long long)fs);
+            if (sf) atomicAdd(&ctl->n_sf, (unsigned long long)sf);
+            if (fluid_side) {
+                if (fs)
+                    for (int k = 0; k < D; k++) atomicAdd(&ctl->mom_fluid[k], m[k]);
+                atomic_max_pos(&ctl->vmaxF, vm);
+            } else if (sf) {
+                for (int k = 0; k < D; k++) atomicAdd(&ctl->mom_solid[k], m[k]);
+            }
+        }
+    } else if (valid) {
+        Ctl *ctl = bt.ctl + b;
+        if (c.ff) atomicAdd(&ctl->n_ff, (unsigned long long)c.ff);
+        if (c.fw) atomicAdd(&ctl->n_fw, (unsigned long long)c.fw);
+        if (c.fs) atomicAdd(&ctl->n_fs, (unsigned long long)c.fs);
+        if (c.sf) atomicAdd(&ctl->n_sf, (unsigned long long)c.sf);
+        if (fluid_side) {
+            for (int k = 0; k < D; k++)
+                if (c.mom[k] != 0.0) atomicAdd(&ctl->mom_fluid[k], c.mom[k]);
+            atomic_max_pos(&ctl->vmaxF, c.vmax);
+        } else {
+            for (int k = 0; k < D; k++)
+                if (c.mom[k] != 0.0) atomicAdd(&ctl->mom_solid[k], c.mom[k]);
+        }
+    }
+}
+
 template <int D>
 static inline int grid_blocks(int n)
 {
@@ -164,12 +214,16 @@ static inline int grid_blocks(int n)
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, Grid g, Phys P, Ctl *ctl)
+__global__ void __launch_bounds__(kBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
 {
     constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
+    const int b = act ? f.inst[i] : 0;
+    const Inst &In = bt.I[b];
+    const Grid &g = In.g;
+    const Phys &P = In.P;
     unsigned nff = 0, nfw = 0, nfs = 0;
     float acc[3] = {0.f, 0.f, 0.f}, afs[3] = {0.f, 0.f, 0.f};
     float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Vi = Pi;
@@ -179,9 +233,9 @@ __global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, 
         const float vi[3] = {Vi.x, Vi.y, Vi.z};
         const float rhoi = P.rho0 + Vi.w, pi = Pi.w;
         int cx, cy, cz;
-        cell_xyz(f.cell_of[i], g, cx, cy, cz);
+        cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float c0 = P.c0, eta2 = 2.0f * P.eta;
-        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
             // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
@@ -241,45 +295,31 @@ __global__ void __launch_bounds__(kBlock) k_momentum(Fluid f, Walls w, Solid s, 
         acc[k] = group_sum<L>(acc[k]);
         afs[k] = group_sum<L>(afs[k]);
     }
-    float vmax2 = 0.0f;
-    double mfs[3] = {0.0, 0.0, 0.0};
+    Counts cnt = {nff, nfw, nfs, 0u, 0.0f, {0.0, 0.0, 0.0}};
     if (act && lane == 0) {
         const float rhoi = P.rho0 + Vi.w;
         const float vi[3] = {Vi.x, Vi.y, Vi.z};
         float inv_rho = 1.0f / rhoi;
         float a[3], vn[3] = {0.f, 0.f, 0.f};
-        double dt = ctl->dt;
+        double dt = bt.ctl[b].dt;
         for (int k = 0; k < D; k++) {
             a[k] = (acc[k] + afs[k]) * inv_rho + P.g[k];
             vn[k] = vi[k] + (float)dt * a[k];
             f.dvdt[(size_t)i * D + k] = a[k];
         }
         f.W4[i] = make_float4(vn[0], vn[1], vn[2], Vi.w);
-        vmax2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
+        cnt.vmax = sqrtf(vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2]);
         float Vi_ = P.mF / rhoi;   // force = V_i * afs (same V_i as the solid side)
-        for (int k = 0; k < D; k++) mfs[k] = (double)(Vi_ * afs[k]);
+        for (int k = 0; k < D; k++) cnt.mom[k] = (double)(Vi_ * afs[k]);
     }
-    // warp reductions, one atomic per warp
-    unsigned tff = warp_sum_u(nff), tfw = warp_sum_u(nfw), tfs = warp_sum_u(nfs);
-    float vm = warp_max(vmax2);
-    for (int k = 0; k < D; k++) mfs[k] = warp_sum_d(mfs[k]);
-    if ((threadIdx.x & 31) == 0) {
-        if (tff) atomicAdd(&ctl->n_ff, (unsigned long long)tff);
-        if (tfw) atomicAdd(&ctl->n_fw, (unsigned long long)tfw);
-        if (tfs) {
-            atomicAdd(&ctl->n_fs, (unsigned long long)tfs);
-            for (int k = 0; k < D; k++) atomicAdd(&ctl->mom_fluid[k], mfs[k]);
-        }
-        atomic_max_pos(&ctl->vmaxF, sqrtf(vm));
-    }
+    flush_counts<D>(bt, b, act, cnt, true);
 }
 
-int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                    cudaStream_t st)
+int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (P.dim == 2) k_momentum<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_momentum<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (dim == 2) k_momentum<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    else k_momentum<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -288,7 +328,7 @@ int launch_momentum(const Fluid &f, const Walls &w, const Solid &s, const Grid &
 // the same pair expression and inputs as a4 (fluid at r^{n+1/2}, v^n)
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Fluid f, Solid s, Grid g, Phys P, Ctl *ctl)
+__global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
 {
     constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,13 +336,16 @@ __global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Fluid f, Solid s, 
     const bool act = k < s.n;
     unsigned nsf = 0;
     float fa[3] = {0.f, 0.f, 0.f};
-    int a = 0;
+    const int a = act ? __float_as_int(s.N4[k].w) : 0;
+    const int b = act ? s.inst[a] : 0;
+    const Inst &In = bt.I[b];
+    const Grid &g = In.g;
+    const Phys &P = In.P;
     if (act) {
         const float4 A = s.A4[k], VB = s.VB4[k], AB = s.AB4[k], N = s.N4[k];
-        a = __float_as_int(N.w);
         int cx, cy, cz;
-        cell_xyz(s.cell_of[k], g, cx, cy, cz);
-        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+        cell_xyz(s.cell_of[k], In, cx, cy, cz);
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 const float4 Pj = f.P4[j];
@@ -324,28 +367,22 @@ __global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Fluid f, Solid s, 
         });
     }
     for (int q = 0; q < D; q++) fa[q] = group_sum<L>(fa[q]);
-    double ms[3] = {0.0, 0.0, 0.0};
+    Counts cnt = {0u, 0u, 0u, nsf, 0.0f, {0.0, 0.0, 0.0}};
     if (act && lane == 0) {
         for (int q = 0; q < 3; q++) s.fF[3 * a + q] = q < D ? fa[q] : 0.0f;
-        for (int q = 0; q < D; q++) ms[q] = (double)fa[q];
+        for (int q = 0; q < D; q++) cnt.mom[q] = (double)fa[q];
     }
-    unsigned tt = warp_sum_u(nsf);
-    for (int q = 0; q < D; q++) ms[q] = warp_sum_d(ms[q]);
-    if ((threadIdx.x & 31) == 0 && tt) {
-        atomicAdd(&ctl->n_sf, (unsigned long long)tt);
-        for (int q = 0; q < D; q++) atomicAdd(&ctl->mom_solid[q], ms[q]);
-    }
+    flush_counts<D>(bt, b, act, cnt, false);
 }
 
-int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                             cudaStream_t st)
+int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, int dim, cudaStream_t st)
 {
     if (s.n == 0 || f.n == 0) {
         if (s.n) cudaMemsetAsync(s.fF, 0, sizeof(float) * 3 * s.n, st);
         return cudaGetLastError() == cudaSuccess ? 0 : -3;
     }
-    if (P.dim == 2) k_solid_fluid_force<2><<<grid_blocks<2>(s.n), kBlock, 0, st>>>(f, s, g, P, ctl);
-    else k_solid_fluid_force<3><<<grid_blocks<3>(s.n), kBlock, 0, st>>>(f, s, g, P, ctl);
+    if (dim == 2) k_solid_fluid_force<2><<<grid_blocks<2>(s.n), kBlock, 0, st>>>(bt, f, s);
+    else k_solid_fluid_force<3><<<grid_blocks<3>(s.n), kBlock, 0, st>>>(bt, f, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -354,12 +391,16 @@ int launch_solid_fluid_force(const Fluid &f, const Solid &s, const Grid &g, cons
 // writes the end-of-step state to s[0] in cell order
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_density(Fluid f, Walls w, Solid s, Grid g, Phys P, Ctl *ctl)
+__global__ void __launch_bounds__(kBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
 {
     constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
+    const int b = act ? f.inst[i] : 0;
+    const Inst &In = bt.I[b];
+    const Grid &g = In.g;
+    const Phys &P = In.P;
     float rate = 0.0f;
     float4 Pi = make_float4(0.f, 0.f, 0.f, 0.f), Wi = Pi;
     if (act) {
@@ -368,9 +409,9 @@ __global__ void __launch_bounds__(kBlock) k_density(Fluid f, Walls w, Solid s, G
         const float vi[3] = {Wi.x, Wi.y, Wi.z};
         const float drhoi = Wi.w, rhoi = P.rho0 + Wi.w, pi = Pi.w;
         int cx, cy, cz;
-        cell_xyz(f.cell_of[i], g, cx, cy, cz);
+        cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float inv2c0 = 0.5f / P.c0;
-        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 if (j == i) continue;
@@ -415,7 +456,7 @@ __global__ void __launch_bounds__(kBlock) k_density(Fluid f, Walls w, Solid s, G
     float rhodot = 2.0f * rhoi * rate;
     // second half drift (Eq. verlet-first-final) and the new state
     const FluidState M = f.s[1], S = f.s[0];
-    double h = 0.5 * ctl->dt;
+    double h = 0.5 * bt.ctl[b].dt;
     double x = M.x[i] + h * (double)vi[0];
     double y = M.y[i] + h * (double)vi[1];
     if (g.periodic_x) {
@@ -435,12 +476,11 @@ __global__ void __launch_bounds__(kBlock) k_density(Fluid f, Walls w, Solid s, G
     S.id[i] = M.id[i];
 }
 
-int launch_density(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                   cudaStream_t st)
+int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (P.dim == 2) k_density<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_density<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (dim == 2) k_density<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    else k_density<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -450,85 +490,155 @@ int launch_density(const Fluid &f, const Walls &w, const Solid &s, const Grid &g
 // value is evaluated in FP64 from the FP64 positions (the FP32 records only
 // screen out candidates well outside the support) and summed in FP64.
 // ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ double W_fp64_shape(double dx, double dy, double dz, const Grid &g, double rc2,
-                                               double inv_h)
+// ---------------------------------------------------------------------------
+// Density reinitialisation (Alg. 1, every n_reinit steps): rho = rho0 sigma /
+// sigma0 with the number density sigma = sum_j W_ij V_j / V_i, self term
+// included (reading R16).  rho - rho0 = rho0 (sigma - sigma0) / sigma0 loses
+// three to four digits to cancellation, so each W_ij must be good to far
+// better than FP32.  FP64 arithmetic is a small fraction of the FP32 rate on
+// this GPU; the pair terms are therefore evaluated in double-float
+// arithmetic (an unevaluated sum hi + lo of two FP32 numbers, about 44
+// significant bits, built from the error-free transformations TwoSum
+// (Knuth), FastTwoSum (Dekker) and TwoProduct with one FMA), starting from
+// cell-relative positions carried as hi + lo pairs.  Per-particle sums are
+// finished in FP64.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
 {
-    if (g.periodic_x) {
-        if (dx > 0.5 * g.Lx) dx -= g.Lx;
-        else if (dx < -0.5 * g.Lx) dx += g.Lx;
-    }
-    double r2 = dx * dx + dy * dy + (D == 3 ? dz * dz : 0.0);
-    if (!(r2 < rc2)) return 0.0;
-    // FP64 square root from the FP32 one and one Newton step (relative error ~1e-14)
-    float rf = sqrtf((float)r2);
-    double r = rf > 0.0f ? (double)rf + (r2 - (double)rf * (double)rf) * (double)(0.5f / rf) : 0.0;
-    double q = r * inv_h, a = 1.0 - 0.5 * q, a2 = a * a;
-    return a2 * a2 * (1.0 + 2.0 * q);   // times alpha_d by the caller
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqr(ff a)
+{
+    const float p = __fmul_rn(a.hi, a.hi);
+    const float e = fmaf(2.0f * a.hi, a.lo, fmaf(a.hi, a.hi, -p));
+    return ff_fast_two_sum(p, e);
+}
+// (xi + li) - (xj + lj) + (o + ol)
+__device__ __forceinline__ ff ff_delta(float xi, float li, float xj, float lj, float o, float ol)
+{
+    const ff t = ff_two_sum(xi, -xj);
+    const ff u = ff_two_sum(t.hi, o);
+    return ff_fast_two_sum(u.hi, __fadd_rn(__fadd_rn(t.lo, u.lo), __fadd_rn(__fsub_rn(li, lj), ol)));
+}
+// cell offset o = -dcell * edge as hi + lo (o is 0 or +-csf)
+__device__ __forceinline__ float off_lo(float o, float cslo)
+{
+    return o == 0.0f ? 0.0f : (o > 0.0f ? cslo : -cslo);
+}
+
+// Wendland C2 shape (1 - q/2)^4 (1 + 2q) of the pair, q = |r_ij| / h_F, in
+// double-float; 0 outside the support.
+template <int D>
+__device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, const float4 &Pj, const float4 &Lj,
+                                         float ox, float oy, float oz, const Grid &g, const Phys &P)
+{
+    const ff dx = ff_delta(Pi.x, Li.x, Pj.x, Lj.x, ox, off_lo(ox, g.cslo[0]));
+    const ff dy = ff_delta(Pi.y, Li.y, Pj.y, Lj.y, oy, off_lo(oy, g.cslo[1]));
+    ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
+    if (D == 3) r2 = ff_add(r2, ff_sqr(ff_delta(Pi.z, Li.z, Pj.z, Lj.z, oz, off_lo(oz, g.cslo[2]))));
+    if (!(r2.hi > 0.0f)) return {1.0f, 0.0f};
+    // r = sqrt(r2): FP32 root s plus one Newton correction (r2 - s^2) / (2 s)
+    const float s = sqrtf(r2.hi);
+    const float p = __fmul_rn(s, s);
+    const float res = __fadd_rn(__fsub_rn(__fsub_rn(r2.hi, p), fmaf(s, s, -p)), r2.lo);
+    const ff r = ff_fast_two_sum(s, __fmul_rn(res, __fmul_rn(0.5f, __frcp_rn(s))));
+    const ff q = ff_mul(r, ff{P.ihF_hi, P.ihF_lo});
+    if (q.hi >= 2.0f) return {0.0f, 0.0f};
+    const ff a = {1.0f, 0.0f};
+    const ff ha = ff_add(a, ff{-0.5f * q.hi, -0.5f * q.lo});       // 1 - q/2
+    const ff bq = ff_add(a, ff{2.0f * q.hi, 2.0f * q.lo});         // 1 + 2q
+    const ff a2 = ff_sqr(ha);
+    return ff_mul(ff_sqr(a2), bq);
 }
 
 template <int D>
-__global__ void __launch_bounds__(kBlock) k_reinit(Fluid f, Walls w, Solid s, Grid g, Phys P, const Ctl *ctl)
+__global__ void __launch_bounds__(kBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
 {
-    if (!ctl->reinit) return;
     constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
-    const bool act = i < f.n;
-    const FluidState M = f.s[1];
-    const double inv_h = 1.0 / P.hF_d, rc2 = P.rc2F_d;
+    const int b = i < f.n ? f.inst[i] : 0;
+    // the L lanes of a particle share its instance, so this is group-uniform
+    const bool act = i < f.n && bt.ctl[b].reinit;
+    const Inst &In = bt.I[b];
+    const Grid &g = In.g;
+    const Phys &P = In.P;
     const float screen = P.rc2F * 1.0001f;
-    double sF = 0.0, sW = 0.0, sS = 0.0;
+    ff sF = {0.0f, 0.0f}, sW = {0.0f, 0.0f}, sS = {0.0f, 0.0f};
     if (act) {
-        const float4 Pi = f.P4[i];
-        const double xi = M.x[i], yi = M.y[i], zi = D == 3 ? M.z[i] : 0.0;
+        const float4 Pi = f.P4[i], Li = f.L4[i];
         int cx, cy, cz;
-        cell_xyz(f.cell_of[i], g, cx, cy, cz);
-        for_each_cell<D>(g, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+        cell_xyz(f.cell_of[i], In, cx, cy, cz);
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 if (j == i) continue;
                 float d[3];
-                if (rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) >= screen) continue;
-                sF += W_fp64_shape<D>(xi - M.x[j], yi - M.y[j], D == 3 ? zi - M.z[j] : 0.0, g, rc2, inv_h);
+                const float4 Pj = f.P4[j];
+                if (rel_d<D>(Pi, Pj, ox, oy, oz, d) >= screen) continue;
+                sF = ff_add(sF, W_ff_shape<D>(Pi, Li, Pj, f.L4[j], ox, oy, oz, g, P));
             }
             const int a1 = w.cstart[c + 1];
             for (int q = w.cstart[c] + lane; q < a1; q += L) {
                 float d[3];
-                if (rel_d<D>(Pi, w.A4[q], ox, oy, oz, d) >= screen) continue;
-                int a = w.perm[q];
-                sW += W_fp64_shape<D>(xi - w.x[a], yi - w.y[a], D == 3 ? zi - w.z[a] : 0.0, g, rc2, inv_h);
+                const float4 Aq = w.A4[q];
+                if (rel_d<D>(Pi, Aq, ox, oy, oz, d) >= screen) continue;
+                sW = ff_add(sW, W_ff_shape<D>(Pi, Li, Aq, w.L4[q], ox, oy, oz, g, P));
             }
             if (s.n) {
                 const int b1 = s.cstart[c + 1];
                 for (int q = s.cstart[c] + lane; q < b1; q += L) {
                     float d[3];
-                    if (rel_d<D>(Pi, s.A4[q], ox, oy, oz, d) >= screen) continue;
-                    int a = s.perm[q];
-                    sS += W_fp64_shape<D>(xi - s.x[a], yi - s.y[a], D == 3 ? zi - s.z[a] : 0.0, g, rc2, inv_h);
+                    const float4 Aq = s.A4[q];
+                    if (rel_d<D>(Pi, Aq, ox, oy, oz, d) >= screen) continue;
+                    sS = ff_add(sS, W_ff_shape<D>(Pi, Li, Aq, s.L4[q], ox, oy, oz, g, P));
                 }
             }
         });
     }
-    sF = group_sum_d<L>(sF);
-    sW = group_sum_d<L>(sW);
-    sS = group_sum_d<L>(sS);
+    const double dF = group_sum_d<L>((double)sF.hi + (double)sF.lo);
+    const double dW = group_sum_d<L>((double)sW.hi + (double)sW.lo);
+    const double dS = group_sum_d<L>((double)sS.hi + (double)sS.lo);
     if (!act || lane != 0) return;
-    double sigma = P.alphaF_d * (1.0 + sF + P.VW_VF_d * sW + P.VS_VF_d * sS);
+    double sigma = P.alphaF_d * (1.0 + dF + P.VW_VF_d * dW + P.VS_VF_d * dS);
     double dr = P.rho0_d * ((sigma - P.sigma0_d) / P.sigma0_d);
     if (P.free_surface && dr < 0.0) dr = 0.0;
     float drho = (float)dr;
-    M.drho[i] = drho;
+    f.s[1].drho[i] = drho;
     f.P4[i].w = eos_p(drho, P);
     f.V4[i].w = drho;
 }
 
-int launch_reinit(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, Ctl *ctl,
-                  cudaStream_t st)
+int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (P.dim == 2) k_reinit<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
-    else k_reinit<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(f, w, s, g, P, ctl);
+    if (dim == 2) k_reinit<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    else k_reinit<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -546,21 +656,25 @@ __device__ __forceinline__ double r2_fp64(double dx, double dy, double dz, int D
 }
 
 template <int D>
-__global__ void k_debug_pairs(Fluid f, Walls w, Solid s, Grid g, Phys P, int which, int *counts,
+__global__ void k_debug_pairs(Batch bt, Fluid f, Walls w, Solid s, int inst, int which, int *counts,
                               const int *offs, int *out)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    int nrows = which == 3 ? s.n : f.n;
-    if (k >= nrows) return;
+    const Inst &In = bt.I[inst];
+    const Grid &g = In.g;
+    const Phys &P = In.P;
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int nrows = which == 3 ? In.ns : In.nf;
+    if (r >= nrows) return;
     double xi, yi, zi;
     int row, key;
     const FluidState M = f.s[1];
+    const int k = (which == 3 ? In.s0 : In.f0) + r;   // sorted slot
     if (which == 3) {
         int a = s.perm[k];
         xi = s.x[a];
         yi = s.y[a];
         zi = D == 3 ? s.z[a] : 0.0;
-        row = a;
+        row = a - In.s0;
         key = s.cell_of[k];
     } else {
         xi = M.x[k];
@@ -570,10 +684,10 @@ __global__ void k_debug_pairs(Fluid f, Walls w, Solid s, Grid g, Phys P, int whi
         key = f.cell_of[k];
     }
     int cx, cy, cz;
-    cell_xyz(key, g, cx, cy, cz);
+    cell_xyz(key, In, cx, cy, cz);
     int cnt = 0;
     int base = out ? offs[row] : 0;
-    for_each_cell<D>(g, cx, cy, cz, [&](int c, float, float, float) {
+    for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float, float, float) {
         int j0, j1;
         if (which == 0 || which == 3) {
             j0 = f.cstart[c];
@@ -599,13 +713,13 @@ __global__ void k_debug_pairs(Fluid f, Walls w, Solid s, Grid g, Phys P, int whi
                 xj = w.x[a];
                 yj = w.y[a];
                 zj = D == 3 ? w.z[a] : 0.0;
-                col = a;
+                col = a - In.w0;
             } else {
                 int a = s.perm[j];
                 xj = s.x[a];
                 yj = s.y[a];
                 zj = D == 3 ? s.z[a] : 0.0;
-                col = a;
+                col = a - In.s0;
             }
             double dx = xi - xj;
             if (g.periodic_x) {
@@ -621,14 +735,14 @@ __global__ void k_debug_pairs(Fluid f, Walls w, Solid s, Grid g, Phys P, int whi
     if (!out) counts[row] = cnt;
 }
 
-int launch_debug_pairs(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, const Phys &P, int which,
-                       int *counts, int *offs, int *out, cudaStream_t st)
+int launch_debug_pairs(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, int inst,
+                       int which, int *counts, int *offs, int *out, cudaStream_t st)
 {
-    int nrows = which == 3 ? s.n : f.n;
+    int nrows = which == 3 ? s.n : f.n;   // upper bound of the instance's rows
     if (nrows == 0) return 0;
     int nb = (nrows + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_debug_pairs<2><<<nb, kBlock, 0, st>>>(f, w, s, g, P, which, counts, offs, out);
-    else k_debug_pairs<3><<<nb, kBlock, 0, st>>>(f, w, s, g, P, which, counts, offs, out);
+    if (dim == 2) k_debug_pairs<2><<<nb, kBlock, 0, st>>>(bt, f, w, s, inst, which, counts, offs, out);
+    else k_debug_pairs<3><<<nb, kBlock, 0, st>>>(bt, f, w, s, inst, which, counts, offs, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

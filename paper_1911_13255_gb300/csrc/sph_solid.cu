@@ -41,14 +41,16 @@ __device__ __forceinline__ double r2_d(double dx, double dy, double dz, int D)
 }
 
 template <int D>
-__global__ void k_solid_count(Solid s, Phys P, int *counts)
+__global__ void k_solid_count(Batch bt, Solid s, int *counts)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= s.n) return;
+    const Inst &In = bt.I[s.inst[a]];
+    const Phys &P = In.P;
     double rc2 = 4.0 * P.hS_d * P.hS_d;
     double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
     int c = 0;
-    for (int b = 0; b < s.n; b++) {
+    for (int b = In.s0; b < In.s0 + In.ns; b++) {
         if (b == a) continue;
         double dz = D == 3 ? za - s.z0[b] : 0.0;
         if (r2_d(xa - s.x0[b], ya - s.y0[b], dz, D) < rc2) c++;
@@ -57,17 +59,19 @@ __global__ void k_solid_count(Solid s, Phys P, int *counts)
 }
 
 template <int D>
-__global__ void k_solid_fill(Solid s, Phys P)
+__global__ void k_solid_fill(Batch bt, Solid s)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= s.n) return;
+    const Inst &In = bt.I[s.inst[a]];
+    const Phys &P = In.P;
     const double h = P.hS_d;
     const double rc2 = 4.0 * h * h;
-    const double V0 = D == 2 ? (P.VS) : (P.VS);
+    const double V0 = P.VS;
     double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
     double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int q = s.nb_ptr[a];
-    for (int b = 0; b < s.n; b++) {
+    for (int b = In.s0; b < In.s0 + In.ns; b++) {
         if (b == a) continue;
         double d[3] = {xa - s.x0[b], ya - s.y0[b], D == 3 ? za - s.z0[b] : 0.0};
         double r2 = r2_d(d[0], d[1], d[2], D);
@@ -106,21 +110,21 @@ __global__ void k_solid_fill(Solid s, Phys P)
     }
 }
 
-int launch_solid_setup_count(Solid &s, const Phys &P, int *counts, cudaStream_t st)
+int launch_solid_setup_count(const Batch &bt, Solid &s, int dim, int *counts, cudaStream_t st)
 {
     if (s.n == 0) return 0;
     int nb = (s.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_solid_count<2><<<nb, kBlock, 0, st>>>(s, P, counts);
-    else k_solid_count<3><<<nb, kBlock, 0, st>>>(s, P, counts);
+    if (dim == 2) k_solid_count<2><<<nb, kBlock, 0, st>>>(bt, s, counts);
+    else k_solid_count<3><<<nb, kBlock, 0, st>>>(bt, s, counts);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-int launch_solid_setup_fill(Solid &s, const Phys &P, cudaStream_t st)
+int launch_solid_setup_fill(const Batch &bt, Solid &s, int dim, cudaStream_t st)
 {
     if (s.n == 0) return 0;
     int nb = (s.n + kBlock - 1) / kBlock;
-    if (P.dim == 2) k_solid_fill<2><<<nb, kBlock, 0, st>>>(s, P);
-    else k_solid_fill<3><<<nb, kBlock, 0, st>>>(s, P);
+    if (dim == 2) k_solid_fill<2><<<nb, kBlock, 0, st>>>(bt, s);
+    else k_solid_fill<3><<<nb, kBlock, 0, st>>>(bt, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -263,8 +267,11 @@ __device__ __forceinline__ void deformation_rate(const Solid &s, int a, const fl
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Solid s, Phys P, Ctl *ctl)
+__global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Batch bt, Solid s)
 {
+    // one instance only (the launcher checks): its whole body over the grid
+    const Phys &P = bt.I[0].P;
+    Ctl *ctl = bt.ctl;
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -439,16 +446,15 @@ __device__ __forceinline__ float group_sum(float v)
     return v;
 }
 
+// K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster
 template <int D>
-__global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ctl *ctl)
+__device__ __forceinline__ void solid_lanes_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
+                                                 float4 *sV, unsigned rank)
 {
-    constexpr int QR = D == 3 ? 3 : 1;   // float4 rows of Q per particle
-    __shared__ float4 sQ[kPPC * QR];
-    __shared__ float4 sV[kPPC];
-    const unsigned rank = cluster_rank();
     const int g = threadIdx.x / kLanes, lane = threadIdx.x % kLanes;
-    const int a = (int)rank * kPPC + g;
-    const bool own = a < s.n;
+    const int la = (int)rank * kPPC + g;
+    const int a = s0 + la;
+    const bool own = la < ns;
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -493,6 +499,7 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
 #pragma unroll
             for (int u = 0; u < kU; u++) {
                 int b = __float_as_int(e[u].w);
+                b = b >= 0 ? b - s0 : -1;   // local index in the body
                 vb[u] = b >= 0 ? *dsmem(&sV[b % kPPC], (unsigned)(b / kPPC)) : va;
             }
 #pragma unroll
@@ -569,6 +576,7 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
 #pragma unroll
                     for (int u = 0; u < kU; u++) {
                         int b = __float_as_int(e[u].w);
+                        b = b >= 0 ? b - s0 : -1;
                         qb[u] = b >= 0 ? *dsmem(&sQ[b % kPPC], (unsigned)(b / kPPC)) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
@@ -581,6 +589,7 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
                     for (int u = 0; u < kU; u++) {
                         int b = __float_as_int(e[u].w);
                         if (b < 0) continue;
+                        b -= s0;
                         unsigned rb = (unsigned)(b / kPPC);
                         int lb = b % kPPC;
                         for (int r = 0; r < 3; r++) {
@@ -653,8 +662,48 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Solid s, Phys P, Ct
         atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
         atomic_max_pos(&ctl->amaxS, sqrtf(am));
     }
-    // no CTA may exit while others can still read its shared memory
+    // no CTA may reuse or release its shared memory while others read it
     cluster_sync();
+}
+
+// Persistent cluster kernels: each cluster takes instance indices from an
+// atomic queue (reset before the launch) until all instances are done, so
+// bodies with different K per instance balance over the clusters.  The
+// index is read by every CTA of the cluster from its first CTA's shared
+// memory between two cluster barriers.
+__device__ __forceinline__ int next_instance(unsigned *queue, int *slot, unsigned rank)
+{
+    if (rank == 0 && threadIdx.x == 0) *slot = (int)atomicAdd(queue, 1u);
+    cluster_sync();
+    int b = *dsmem(slot, 0u);
+    cluster_sync();
+    return b;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kCThreads) k_solid_cluster(Batch bt, Solid s)
+{
+    constexpr int QR = D == 3 ? 3 : 1;   // float4 rows of Q per particle
+    __shared__ float4 sQ[kPPC * QR];
+    __shared__ float4 sV[kPPC];
+    __shared__ int s_inst;
+    const unsigned rank = cluster_rank();
+    for (;;) {
+        const int b = next_instance(s.queue, &s_inst, rank);
+        if (b >= bt.B) break;
+        const Inst &In = bt.I[b];
+        solid_lanes_body<D>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
+    }
+}
+
+// single instance: one cluster, constants in the parameter space
+template <int D>
+__global__ void __launch_bounds__(kCThreads) k_solid_cluster_one(Solid s, const __grid_constant__ Phys P, Ctl *ctl)
+{
+    constexpr int QR = D == 3 ? 3 : 1;
+    __shared__ float4 sQ[kPPC * QR];
+    __shared__ float4 sV[kPPC];
+    solid_lanes_body<D>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
 }
 
 // ---------------------------------------------------------------------------
@@ -693,14 +742,14 @@ __device__ __forceinline__ float2 ld_cl2(uint32_t addr)
 
 constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 
-__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Solid s, Phys P, Ctl *ctl)
+// K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster
+__device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
+                                             float4 *sV, unsigned rank)
 {
-    __shared__ float4 sQ[kC1Threads];
-    __shared__ float4 sV[kC1Threads];
-    const unsigned rank = cluster_rank();
     const int g = threadIdx.x;
-    const int a = (int)rank * kC1Threads + g;
-    const bool own = a < s.n;
+    const int la = (int)rank * kC1Threads + g;
+    const int a = s0 + la;
+    const bool own = la < ns;
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -734,7 +783,7 @@ __global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Solid s, Phys P,
         aQ[u] = 0u;
         if (u < nn) {
             float4 e = s.nb[s.nb_ptr[a] + u];
-            int b = __float_as_int(e.w);
+            int b = __float_as_int(e.w) - s0;   // local index in the body
             gx[u] = e.x;
             gy[u] = e.y;
             aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
@@ -854,92 +903,111 @@ __global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Solid s, Phys P,
     cluster_sync();
 }
 
-static int launch_solid_cluster2d(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st)
+__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Batch bt, Solid s)
 {
-    int nctas = (s.n + kC1Threads - 1) / kC1Threads;
-    if (P.dim != 2 || nctas > kClusterMax || s.max_nb > kMaxNb2) return 1;
-    static int feasible[kClusterMax + 1] = {};
+    __shared__ float4 sQ[kC1Threads];
+    __shared__ float4 sV[kC1Threads];
+    __shared__ int s_inst;
+    const unsigned rank = cluster_rank();
+    for (;;) {
+        const int b = next_instance(s.queue, &s_inst, rank);
+        if (b >= bt.B) break;
+        const Inst &In = bt.I[b];
+        solid2d_body(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
+    }
+}
+
+// single instance: one cluster, constants in the parameter space (the
+// persistent kernel's global-memory constants cost registers)
+__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P, Ctl *ctl)
+{
+    __shared__ float4 sQ[kC1Threads];
+    __shared__ float4 sV[kC1Threads];
+    solid2d_body(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
+}
+
+// Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
+// with kernel arguments args.  Returns 1 when the device cannot run such a
+// cluster (the caller falls back), else 0 or -3.
+template <typename Kern, typename... Args>
+static int launch_clusters(Kern kern, int threads, int ctas, int want, int *max_clusters, cudaStream_t st,
+                           Args... args)
+{
+    if (ctas < 1 || ctas > kClusterMax) return 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nctas);
-    cfg.blockDim = dim3(kC1Threads);
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(threads);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nctas;
+    attr[0].val.clusterDim.x = ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (feasible[nctas] == 0) {
+    if (max_clusters[ctas] == 0) {
         int nclu = 0;
-        cudaFuncSetAttribute(k_solid_cluster2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster2d, &cfg);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&nclu, kern, &cfg);
         if (e != cudaSuccess) cudaGetLastError();
-        feasible[nctas] = (e == cudaSuccess && nclu >= 1) ? 1 : -1;
+        max_clusters[ctas] = (e == cudaSuccess && nclu >= 1) ? nclu : -1;
     }
-    if (feasible[nctas] < 0) return 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_solid_cluster2d, s, P, ctl);
+    if (max_clusters[ctas] < 0) return 1;
+    int nclusters = want < max_clusters[ctas] ? want : max_clusters[ctas];
+    cfg.gridDim = dim3(nclusters * ctas);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
     return e == cudaSuccess ? 0 : -3;
 }
 
-static int launch_solid_cluster(Solid &s, const Phys &P, Ctl *ctl, cudaStream_t st)
+// Launch a persistent cluster kernel: as many clusters as can be resident,
+// at most one per instance, taking instances from the queue.
+template <typename Kern>
+static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, Solid &s, int *max_clusters,
+                             cudaStream_t st)
 {
-    if (!s.force_lane_path) {
-        int rc = launch_solid_cluster2d(s, P, ctl, st);
+    if (ctas < 1 || ctas > kClusterMax) return 1;
+    if (cudaMemsetAsync(s.queue, 0, sizeof(unsigned), st) != cudaSuccess) return -3;
+    return launch_clusters(kern, threads, ctas, bt.B, max_clusters, st, bt, s);
+}
+
+static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
+{
+    static int mc2d[2][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
+    const bool one = bt.B == 1;
+    if (dim == 2 && !s.force_lane_path && s.max_nb <= kMaxNb2) {
+        const int ctas = (s.max_ns + kC1Threads - 1) / kC1Threads;
+        int rc = one ? launch_clusters(k_solid_cluster2d_one, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
+                     : launch_persistent(k_solid_cluster2d, kC1Threads, ctas, bt, s, mc2d[1], st);
         if (rc <= 0) return rc;
     }
-    int nctas = (s.n + kPPC - 1) / kPPC;
-    if (nctas > kClusterMax) return 1;
-    static int feasible[2][kClusterMax + 1] = {};   // 0 unknown, 1 yes, -1 no
-    int di = P.dim == 2 ? 0 : 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nctas);
-    cfg.blockDim = dim3(kCThreads);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nctas;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (feasible[di][nctas] == 0) {
-        int nclu = 0;
-        cudaError_t e;
-        if (P.dim == 2) {
-            cudaFuncSetAttribute(k_solid_cluster<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster<2>, &cfg);
-        } else {
-            cudaFuncSetAttribute(k_solid_cluster<3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            e = cudaOccupancyMaxActiveClusters(&nclu, k_solid_cluster<3>, &cfg);
-        }
-        if (e != cudaSuccess) cudaGetLastError();
-        feasible[di][nctas] = (e == cudaSuccess && nclu >= 1) ? 1 : -1;
+    const int ctas = (s.max_ns + kPPC - 1) / kPPC;
+    if (one) {
+        if (dim == 2) return launch_clusters(k_solid_cluster_one<2>, kCThreads, ctas, 1, mcl[0], st, s, P0, bt.ctl);
+        return launch_clusters(k_solid_cluster_one<3>, kCThreads, ctas, 1, mcl[1], st, s, P0, bt.ctl);
     }
-    if (feasible[di][nctas] < 0) return 1;
-    cudaError_t e;
-    if (P.dim == 2) e = cudaLaunchKernelEx(&cfg, k_solid_cluster<2>, s, P, ctl);
-    else e = cudaLaunchKernelEx(&cfg, k_solid_cluster<3>, s, P, ctl);
-    return e == cudaSuccess ? 0 : -3;
+    if (dim == 2) return launch_persistent(k_solid_cluster<2>, kCThreads, ctas, bt, s, mcl[2], st);
+    return launch_persistent(k_solid_cluster<3>, kCThreads, ctas, bt, s, mcl[3], st);
 }
 
-int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStream_t st)
+int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, int *path, cudaStream_t st)
 {
     if (s.n == 0) return 0;
     if (!s.force_grid_path) {
-        int rc = launch_solid_cluster(s, P, ctl, st);
+        int rc = launch_solid_cluster(bt, s, P0, dim, st);
         if (rc <= 0) {
             if (path) *path = 1;
             return rc;
         }
     }
+    // cooperative grid kernel: one large body (a batch needs the cluster path)
+    if (bt.B != 1) return -7;
     static int max_blocks[2] = {0, 0};
-    int di = P.dim == 2 ? 0 : 1;
+    int di = dim == 2 ? 0 : 1;
     if (max_blocks[di] == 0) {
         int dev, nsm, per;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (P.dim == 2)
+        if (dim == 2)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solid_substeps<2>, kSolidBlock, 0);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solid_substeps<3>, kSolidBlock, 0);
@@ -959,8 +1027,8 @@ int launch_solid_substeps(Solid &s, const Phys &P, Ctl *ctl, int *path, cudaStre
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (P.dim == 2) e = cudaLaunchKernelEx(&cfg, k_solid_substeps<2>, s, P, ctl);
-    else e = cudaLaunchKernelEx(&cfg, k_solid_substeps<3>, s, P, ctl);
+    if (dim == 2) e = cudaLaunchKernelEx(&cfg, k_solid_substeps<2>, bt, s);
+    else e = cudaLaunchKernelEx(&cfg, k_solid_substeps<3>, bt, s);
     if (path) *path = 2;
     return e == cudaSuccess ? 0 : -3;
 }

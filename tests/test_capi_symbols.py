@@ -43,3 +43,29 @@ def test_strerror_and_argument_checks_without_gpu():
     assert L.sphfsi_create(ctypes.byref(h), ctypes.byref(p), None) == -1
     assert L.sphfsi_step(None, 1.0) == -1
     assert L.sphfsi_set_substeps(None, 2) == -1
+
+
+def test_batch_creation_checks_without_gpu():
+    """sphfsi_create_batch validates its arguments; sphfsi_select its index."""
+    import paper_1911_13255_gb300 as pkg
+    L = pkg.lib()
+    ps = (pkg.Params * 3)()
+    for k in range(3):
+        ps[k].dim = 2
+        for d in range(2):
+            ps[k].domain_lo[d], ps[k].domain_hi[d] = 0.0, 1.0
+    h = ctypes.c_void_p()
+    assert L.sphfsi_create_batch(ctypes.byref(h), 0, ps, None) == -1
+    ps[2].dim = 3
+    assert L.sphfsi_create_batch(ctypes.byref(h), 3, ps, None) == -1
+    ps[2].dim = 2
+    ps[1].domain_hi[0] = -1.0
+    assert L.sphfsi_create_batch(ctypes.byref(h), 3, ps, None) == -1
+    ps[1].domain_hi[0] = 1.0
+    assert L.sphfsi_create_batch(ctypes.byref(h), 3, ps, None) == 0
+    assert L.sphfsi_select(h, 2) == 0
+    assert L.sphfsi_select(h, 3) == -1
+    assert L.sphfsi_select(h, -1) == -1
+    assert L.sphfsi_select(None, 0) == -1
+    assert L.sphfsi_step(h, 1.0) == -4      # not finalized
+    L.sphfsi_destroy(h)

@@ -1,0 +1,141 @@
+"""Batched contexts: independent instances of uneven size, advanced by the same
+launches, give instance by instance the same bits as one context per
+instance, and a batch member matches the FP64 oracle like a single problem.
+
+The batch mixes what the per-instance look-ups must keep apart: channels with
+flags of different sizes and materials (uneven K), a tank without a solid, a
+periodic blob without walls, and a walled box with a free block.
+"""
+import numpy as np
+import pytest
+
+import fsi_cases as fc
+import oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1911_13255_gb300 import Simulation, SphError  # noqa: E402
+
+ACC_TOL = 1e-5
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _mixed_cases():
+    cases = fc.flag_batch(seed=7, n=4, nf_lo=2000, nf_hi=9000)
+    cases.insert(1, fc.hydrostatic_column(seed=2))
+    cases.append(fc.floating_block(seed=4))
+    cases.append(fc.tiny_box(seed=6))
+    return cases
+
+
+def _state(sim):
+    g = sim.get_fluid()
+    out = {f"f_{k}": v for k, v in g.items()}
+    if sim.ns:
+        out.update({f"s_{k}": v for k, v in sim.get_solid().items()})
+    info = sim.info()
+    for k in ("t", "step", "last_dt", "last_K", "pairs_ff", "pairs_fw", "pairs_fs", "pairs_sf", "pairs_ss",
+              "pairs_total", "vmax_f", "vmax_s"):
+        out[k] = np.asarray(info[k])
+    return out
+
+
+@pytest.mark.parametrize("mode", ["step", "graph"])
+def test_batch_equals_single_instances_bitwise(mode):
+    cases = _mixed_cases()
+    nsteps = 12
+    stream = torch.cuda.Stream()
+    batch = Simulation.from_cases(cases, stream=stream)
+    assert batch.n_instances == len(cases)
+    if mode == "graph":
+        batch.run(nsteps, 0.0)
+    else:
+        for _ in range(nsteps):
+            batch.step(0.0)
+    batch.sync()
+    Ks = []
+    total = 0
+    for b, case in enumerate(cases):
+        single = Simulation.from_case(case, stream=stream)
+        for _ in range(nsteps):
+            single.step(0.0)
+        single.sync()
+        want = _state(single)
+        got = _state(batch.select(b))
+        assert set(want) == set(got)
+        for k in want:
+            assert np.array_equal(got[k], want[k]), (b, case.name, k)
+        Ks.append(int(want["last_K"]))
+        total += int(want["pairs_total"])
+        single.close()
+    assert batch.pairs_total() == total
+    # the flags' materials differ, so do their sub-step counts
+    flag_K = [K for K, c in zip(Ks, cases) if c.name.startswith("flag_batch")]
+    assert len(set(flag_K)) > 1, flag_K
+    batch.close()
+
+
+def test_batch_member_parity_with_oracle():
+    cases = _mixed_cases()
+    batch = Simulation.from_cases(cases)
+    batch.step(0.0)
+    batch.sync()
+    for b in (0, 1, len(cases) - 2):
+        case = cases[b]
+        info = batch.select(b).info()
+        ref = O.OracleSim(case)
+        dt_ref, _, dts = ref.suggest_dt()
+        assert abs(info["last_dt"] - dt_ref) <= 1e-6 * dt_ref
+        if case.ns:
+            assert info["last_K"] == ref.substeps(info["last_dt"], dts)
+        ref.step(info["last_dt"], max(info["last_K"], 1))
+        g = batch.get_fluid()
+        e = dict(dvdt=rel(g["dvdt"], ref.f_dvdt), drho=rel(g["drho"], ref.f_drho), v=rel(g["v"], ref.f_v))
+        if case.ns:
+            s = batch.get_solid()
+            e["fF"] = rel(s["fF"], ref.s_fF)
+            e["F-I"] = rel(s["F"] - np.eye(2), ref.s_F - np.eye(2))
+            e["abar"] = rel(s["abar"], ref.s_abar)
+        print(case.name, {k: f"{v:.2e}" for k, v in e.items()})
+        assert max(e.values()) < ACC_TOL, (case.name, e)
+    batch.close()
+
+
+def test_batch_neighbor_sets_bit_exact_per_instance():
+    cases = _mixed_cases()[:3]
+    batch = Simulation.from_cases(cases)
+    for b, case in enumerate(cases):
+        batch.select(b)
+        P = O.make_params(case)
+        rc = 2 * 1.3 * case.f_dp
+        f_r = batch.get_fluid()["r"]
+        want = {0: O.pairs(P, f_r, f_r, rc, 1)}
+        if case.nw:
+            want[1] = O.pairs(P, f_r, case.w_r, rc, 0)
+        if case.ns:
+            s_r = batch.get_solid()["r"]
+            want[2] = O.pairs(P, f_r, s_r, rc, 0)
+            want[3] = O.pairs(P, s_r, f_r, rc, 0)
+        for which, (p, i) in want.items():
+            gp, gi = batch.debug_neighbors(which)
+            assert np.array_equal(gp, p) and np.array_equal(gi, i), (b, which)
+    batch.close()
+
+
+def test_batch_rejects_bad_selection_and_grid_path():
+    cases = _mixed_cases()[:2]
+    batch = Simulation.from_cases(cases)
+    with pytest.raises(SphError):
+        batch.select(len(cases))
+    with pytest.raises(SphError):
+        batch.set_solid_path(2)
+    batch.close()
