@@ -1,10 +1,16 @@
 """Benchmark: one coarse FSI step of the multi-resolution SPH method on GB300.
 
-Workload: 2-D dam break through an elastic rubber gate (water column
-0.1 m x 0.14 m, dp_F = 1 mm, ~14k fluid particles; gate 0.079 m x 0.005 m at
-dp_S = 0.5 mm, ~1.6k solid particles; rho_S = 1100, E = 12 MPa, Poisson
-0.47; c0 = 20 m/s), FP32 pair loops with FP64 positions, the paper's
-automatic dt_F (acoustic criterion) and K = [dt_F / dt_S] + 1 sub-steps.
+Default workload (--workload dam_gate): 2-D dam break through an elastic
+rubber gate (water column 0.1 m x 0.14 m, dp_F = 1 mm, ~14k fluid particles;
+gate 0.079 m x 0.005 m at dp_S = 0.5 mm, ~1.6k solid particles; rho_S = 1100,
+E = 12 MPa, Poisson 0.47; c0 = 20 m/s), FP32 pair loops with FP64 positions,
+the paper's automatic dt_F (acoustic criterion) and K = [dt_F / dt_S] + 1
+sub-steps.
+
+--workload flag_batch: 256 independent 2-D cylinder-plus-flag channels of
+uneven size (fluid counts 2k-60k log-uniform, flag 2D-4D x 0.1D-0.3D, E
+5e2-5e4, rho_S/rho_F 1-20, each with its own dt_F and K) advanced by the same
+launches of one batched context, launch shape picked by the autotuner.
 
 A "step" is one coarse fluid step: neighbour build, density reinit (every
 4th step), fluid momentum, solid-side coupling, continuity, K solid
@@ -34,7 +40,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = "dam_break_elastic_gate_2d"
+WORKLOADS = {"dam_gate": "dam_break_elastic_gate_2d",
+             "flag_batch": "flag_channel_batch_256_2d"}
 METRIC = "pair_interactions_per_s"
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -135,14 +142,24 @@ def _traffic(kernel):
     return None
 
 
-def make_case(seed=0):
+def make_cases(workload, seed=0):
     import fsi_cases
-    return fsi_cases.dam_gate(seed=seed)
+    if workload == "flag_batch":
+        return fsi_cases.flag_batch(seed=seed, n=256)
+    return [fsi_cases.dam_gate(seed=seed)]
 
 
-def cpu_baseline(case, budget_s=15.0, max_steps=400):
+def sample_case(cases):
+    """The instance the CPU baseline steps: the median-size one."""
+    order = sorted(range(len(cases)), key=lambda b: cases[b].nf)
+    return order[len(order) // 2]
+
+
+def cpu_baseline(cases, label, budget_s=15.0, max_steps=400):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
+    b = sample_case(cases)
+    case = cases[b]
     ref = oracle.OracleSim(case)
     dt, _, dts = ref.suggest_dt(vmax_f=0.0)
     K = ref.substeps(dt, dts)
@@ -155,23 +172,26 @@ def cpu_baseline(case, budget_s=15.0, max_steps=400):
         pairs += 2 * fl + d["n_sf"] + (fl if reinit else 0) + (2 * K + 1) * d["n_ss"]
         steps += 1
     el = time.perf_counter() - t0
+    which = f"instance {b} (n_fluid {case.nf}, the median) of " if len(cases) > 1 else ""
     return dict(value=pairs / el, unit=UNIT, cores=1, kind="oracle",
-                sample=f"first {steps} coarse steps of the {WORKLOAD} workload (seed 0, dt={dt:.3e} s, K={K}), "
-                       f"FP64 C oracle, single thread, {el:.1f} s",
+                sample=f"first {steps} coarse steps of {which}the {label} workload (seed 0, dt={dt:.3e} s, "
+                       f"K={K}), FP64 C oracle, single thread, {el:.1f} s",
                 steps=steps, seconds=el, sim_s_per_wall_s=steps * dt / el)
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    case = make_case(0)
+    label = WORKLOADS[args.workload]
+    cases = make_cases(args.workload, 0)
+    case = cases[sample_case(cases)]
     budget = min(240.0, 0.06 * (args.steps + args.warmup) + 10.0)
-    cb = cpu_baseline(case, budget_s=budget, max_steps=max(1, args.steps))
+    cb = cpu_baseline(cases, label, budget_s=budget, max_steps=max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": cb["steps"], "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / max(cb["steps"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_fluid": case.nf, "n_solid": case.ns,
-                                            "n_wall": case.nw},
+            "data": "synthetic", "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns,
+                                            "n_wall": case.nw, "instances_sampled": 1},
             "sim_s_per_wall_s": cb["sim_s_per_wall_s"],
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -187,15 +207,19 @@ def run_gpu(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    case = make_case(seed=rank)
+    label = WORKLOADS[args.workload]
+    cases = make_cases(args.workload, seed=rank)
+    case = cases[0]
     st = torch.cuda.Stream(device=dev)
-    sim = Simulation.from_case(case, stream=st)
+    sim = Simulation.from_cases(cases, stream=st)
+    tuning = sim.autotune(0.0, steps=10) if len(cases) > 1 else sim.tuning()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sim.set_profiling(True)
     for _ in range(args.warmup):
         sim.run(1, 0.0)
     sim.sync()
-    info0 = sim.info()
+    pairs0 = sim.pairs_total()
+    t0s = [sim.select(b).info()["t"] for b in range(len(cases))]
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     stage_ms = {}
@@ -217,10 +241,11 @@ def run_gpu(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     sim.sync()
-    info1 = sim.info()
+    infos = [sim.select(b).info() for b in range(len(cases))]
+    info1 = infos[0]
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
-    pairs = info1["pairs_total"] - info0["pairs_total"]
-    simt = info1["t"] - info0["t"]
+    pairs = sim.pairs_total() - pairs0
+    simt = sum(i["t"] for i in infos) - sum(t0s)     # simulated seconds summed over the instances
     if dist:
         t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -233,7 +258,7 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
 
     # ---- e2e through the public API with pinned host buffers
-    e2e = e2e_run(case, dev, steps=min(args.steps, 400))
+    e2e = e2e_run(cases, dev, steps=min(args.steps, 400), tuning=tuning)
     if rank != 0:
         return
     # ---- roofline of the dominant stage (device-timed live above)
@@ -244,22 +269,27 @@ def run_gpu(args, rank, world, local_rank):
     dom = max(kernels, key=kernels.get)
     nsteps = args.steps
     K = info1["last_K"]
-    fl = info1["pairs_ff"] + info1["pairs_fw"] + info1["pairs_fs"]
+    fl = sum(i["pairs_ff"] + i["pairs_fw"] + i["pairs_fs"] for i in infos)
+    n_fluid = sum(c.nf for c in cases)
     if dom == "solid_substeps":
-        work = K * (info1["pairs_ss"] * FLOP_SOLID_PAIR + case.ns * FLOP_SOLID_PARTICLE)
+        work = sum(i["last_K"] * (i["pairs_ss"] * FLOP_SOLID_PAIR + c.ns * FLOP_SOLID_PARTICLE)
+                   for i, c in zip(infos, cases))
         bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
         achieved = work / (per_launch[dom] * 1e-3) / 1e12
     elif dom in ("momentum", "continuity", "solid_fluid_force", "reinit"):
-        npairs = info1["pairs_sf"] if dom == "solid_fluid_force" else fl
+        npairs = sum(i["pairs_sf"] for i in infos) if dom == "solid_fluid_force" else fl
         work = npairs * FLOP_PER_PAIR[dom]
         bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
         achieved = work / (per_launch[dom] * 1e-3) / 1e12
     else:
-        work = case.nf * BYTES_PER_FLUID_PARTICLE["bin_sort"]
+        work = n_fluid * BYTES_PER_FLUID_PARTICLE["bin_sort"]
         bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
         achieved = work / (per_launch[dom] * 1e-3) / 1e9
-    solid_kernel = {1: "k_solid_cluster2d_one" if case.dim == 2 else "k_solid_cluster_one",
-                    2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
+    if len(cases) > 1:
+        solid_kernel = "k_solid_cluster" if (case.dim == 3 or tuning["solid_variant"]) else "k_solid_cluster2d"
+    else:
+        solid_kernel = {1: "k_solid_cluster2d_one" if case.dim == 2 else "k_solid_cluster_one",
+                        2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
                     "bin_sort": "k_bin_all+k_scan2+k_scatter2+k_cellsort2+k_records_all"}
@@ -268,15 +298,20 @@ def run_gpu(args, rank, world, local_rank):
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,
             "peak_source": ("FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz) if bound == "alu"
             else f"{src} hbm_gbs"}
-    cb = cpu_baseline(case) if world == 1 else None
+    cb = cpu_baseline(cases, label) if world == 1 else None
     line = {
         "metric": METRIC, "value": pairs_all / (dev_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": nsteps, "warmup": args.warmup, "ms_per_step": dev_ms_max / nsteps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": "FP32 pair loops; FP64 positions, solid displacement, time averages, momentum sums",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_fluid": case.nf, "n_solid": case.ns, "n_wall": case.nw,
-                   "dp_F": case.f_dp, "dp_S": case.s_dp, "K_last": K, "dt_last": info1["last_dt"],
+        "config": {"workload": label, "instances": len(cases), "n_fluid": n_fluid,
+                   "n_solid": sum(c.ns for c in cases), "n_wall": sum(c.nw for c in cases),
+                   "dp_F": case.f_dp, "dp_S": case.s_dp,
+                   "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
+                   "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
+                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant")},
+                   "autotuned": len(cases) > 1,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
         "sim_s_per_wall_s": simt_all / world / (dev_ms_max * 1e-3),
@@ -291,43 +326,59 @@ def run_gpu(args, rank, world, local_rank):
     print(json.dumps(line))
 
 
-def e2e_run(case, dev, steps):
-    """The same metric through the public API: the initial state goes up from
-    pinned host memory, every step reads the solid positions (the gate-tip
-    observer) back into pinned host memory; host-timed, copies included."""
+def e2e_run(cases, dev, steps, tuning):
+    """The same metric through the public API: the initial state of every
+    instance goes up from pinned host memory, every step reads all solid
+    positions (the flag / gate observers) back into pinned host memory;
+    host-timed, copies included."""
     import torch
-    from paper_1911_13255_gb300 import Simulation
+    from paper_1911_13255_gb300 import Simulation, _case_params
 
-    def pin(a, dtype=torch.float64):
-        t = torch.from_numpy(np.ascontiguousarray(a)).to(dtype).pin_memory()
-        return t
+    def pin(arrs, dtype=torch.float64):
+        """One pinned buffer per field; per-instance views into it."""
+        rows = [np.asarray(a, np.float64) for a in arrs]
+        width = max((r.shape[1] if r.ndim > 1 else 1) for r in rows)
+        flat = np.concatenate([r.reshape(len(r), width) for r in rows])
+        t = torch.from_numpy(np.ascontiguousarray(flat)).to(dtype).pin_memory()
+        views, o = [], 0
+        for a in arrs:
+            views.append(t[o:o + len(a)].reshape(np.asarray(a).shape))
+            o += len(a)
+        return t, views
 
-    fr, fv, fp = pin(case.f_r), pin(case.f_v), pin(case.f_p)
-    wr, wn = pin(case.w_r), pin(case.w_n)
-    sr, sv, sn = pin(case.s_r0), pin(case.s_v0), pin(case.s_n0)
-    out = torch.empty((case.ns, case.dim), dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in (fr, fv, fp, wr, wn, sr, sv, sn)) + case.ns
+    fields = {k: pin([getattr(c, k) for c in cases]) for k in ("f_r", "f_v", "f_p", "w_r", "w_n", "s_r0", "s_v0",
+                                                                  "s_n0")}
+    n_s = sum(c.ns for c in cases)
+    out = torch.empty((n_s, cases[0].dim), dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t, _ in fields.values()) + n_s
     st = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = Simulation(case.dim, case.gravity, case.periodic_x, case.x_lo, case.Lx, case.free_surface,
-                     case.n_reinit, case.domain_lo, case.domain_hi, stream=st)
-    sim.add_fluid(fr, fv, fp, case.f_dp, case.f_rho0, case.f_c0, case.f_eta)
-    sim.set_walls(wr, wn, case.w_dp)
-    sim.add_solid(sr, sv, sn, case.s_cons, case.s_dp, case.s_rho0, case.s_E, case.s_nu)
+    sim = Simulation(cases[0].dim, stream=st, params=[_case_params(c) for c in cases])
+    for b, c in enumerate(cases):
+        v = {k: fields[k][1][b] for k in fields}
+        sim.select(b)
+        sim.add_fluid(v["f_r"], v["f_v"], v["f_p"], c.f_dp, c.f_rho0, c.f_c0, c.f_eta)
+        if c.nw:
+            sim.set_walls(v["w_r"], v["w_n"], c.w_dp)
+        if c.ns:
+            sim.add_solid(v["s_r0"], v["s_v0"], v["s_n0"], c.s_cons, c.s_dp, c.s_rho0, c.s_E, c.s_nu)
+        if c.inflow_on:
+            sim.set_inflow(1, c.inflow_profile, c.inflow_width, c.inflow_y0, c.inflow_H, c.inflow_U, c.inflow_tramp)
     sim.finalize()
-    info0 = sim.info()
+    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"])
+    p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)
-        sim.get_solid_positions(out)
+        sim.get_solid_positions_all(out)
     sim.sync()
     t1 = time.perf_counter()
-    info1 = sim.info()
+    pairs = sim.pairs_total() - p0
     sim.close()
-    pairs = info1["pairs_total"] - info0["pairs_total"]
     return {"value": pairs / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": out.numel() * 8, "steps": steps,
-            "note": "context creation + set-up upload amortised over the steps; per-step solid-position readback"}
+            "note": "context creation + set-up upload amortised over the steps; per-step readback of all "
+                    "solid positions"}
 
 
 def main():
@@ -336,6 +387,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dam_gate", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

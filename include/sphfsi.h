@@ -190,6 +190,10 @@ int sphfsi_get_fluid(sphfsi_ctx *c, double *r, float *v, double *rho, float *drh
 int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar, double *abar, float *fF,
                      float *nrm);
 
+/* Solid positions of every instance (original order within each instance,
+ * instances in order, n_total x dim FP64); one device read for the batch. */
+int sphfsi_get_solid_positions_all(sphfsi_ctx *c, double *r);
+
 /* Overwrite the dynamic state (original order, FP64 inputs; NULL keeps a
  * field).  Used for checkpoint/resume and for parity at a given state. */
 int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, const double *rho,
@@ -236,6 +240,35 @@ int sphfsi_set_profiling(sphfsi_ctx *c, int on);
 int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n);
 /* Device ms of the whole last step (first to last event of the step). */
 int sphfsi_step_time(sphfsi_ctx *c, float *ms);
+
+/* Launch shape of the pair loops and the solid kernel variant.  None of
+ * these changes what is computed; the summation order of a particle's pair
+ * terms follows the lane count, so results agree to rounding across
+ * settings and bit for bit at equal settings. */
+typedef struct {
+    int32_t lanes;         /* threads per target particle in the fluid pair loops:
+                              2, 4 or 8 in 2-D (default 4); 4, 8 or 16 in 3-D (default 8) */
+    int32_t block;         /* threads per block of those loops: 64, 128 (default) or 256 */
+    int32_t solid_variant; /* 0: automatic cluster kernel choice; 1: the four-lane
+                              cluster kernel (sphfsi_set_solid_path 1) */
+    float step_ms;         /* sphfsi_autotune: device ms per step measured for this setting */
+} sphfsi_tuning;
+
+/* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */
+int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t);
+int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t);
+
+/* Autotuner (no counterpart in the paper).  Times the context's own
+ * workload: for each candidate setting, `steps` graph-replayed steps of size
+ * dt_F (as sphfsi_run) to warm up, then `steps` timed with CUDA events.  The
+ * search goes over the lane count (block 128), then the block size, then
+ * (2-D with a solid) the solid kernel variant, keeping the fastest of each.
+ * Every device allocation of the context is saved before and restored after
+ * each trial and at the end, so the simulation state, time and counters are
+ * exactly as before the call; the best setting stays selected and is
+ * written to *best.  Needs a non-default stream, and free device memory for
+ * one copy of the context's state (else SPHFSI_E_NOMEM). */
+int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *best);
 
 /* Allocation-free neighbour counting.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc (a framework's

@@ -54,6 +54,13 @@ class Info(C.Structure):
         return d
 
 
+class Tuning(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("block", C.c_int32), ("solid_variant", C.c_int32), ("step_ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = C.c_void_p
 
 # name -> (restype, argtypes)
@@ -62,6 +69,10 @@ _SIGS = {
     "sphfsi_create_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, C.POINTER(Params), _vp]),
     "sphfsi_select": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_pairs_total": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "sphfsi_get_solid_positions_all": (C.c_int, [_vp, _vp]),
+    "sphfsi_set_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
+    "sphfsi_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
+    "sphfsi_autotune": (C.c_int, [_vp, C.c_double, C.c_int32, C.POINTER(Tuning)]),
     "sphfsi_add_fluid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double]),
     "sphfsi_set_walls": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_double]),
     "sphfsi_add_solid": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_double,
@@ -253,6 +264,21 @@ class Simulation:
         s.finalize()
         return s.select(0)
 
+    def autotune(self, dt=0.0, steps=10):
+        """Pick the fastest launch shape on this workload (state left unchanged)."""
+        t = Tuning()
+        _check(lib().sphfsi_autotune(self.h, float(dt), int(steps), C.byref(t)), "sphfsi_autotune")
+        return t.as_dict()
+
+    def set_tuning(self, lanes, block=128, solid_variant=0):
+        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0)
+        _check(lib().sphfsi_set_tuning(self.h, C.byref(t)), "sphfsi_set_tuning")
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().sphfsi_get_tuning(self.h, C.byref(t)), "sphfsi_get_tuning")
+        return t.as_dict()
+
     def pairs_total(self):
         """Pair interactions of all instances since creation."""
         t = C.c_int64()
@@ -301,6 +327,11 @@ class Simulation:
         """Solid positions into a caller buffer (numpy host array or CUDA tensor), n x dim FP64."""
         _check(lib().sphfsi_get_solid(self.h, _ptr(out), None, None, None, None, None, None),
                "sphfsi_get_solid")
+        return out
+
+    def get_solid_positions_all(self, out):
+        """Solid positions of all instances (concatenated, original order) into a caller buffer."""
+        _check(lib().sphfsi_get_solid_positions_all(self.h, _ptr(out)), "sphfsi_get_solid_positions_all")
         return out
 
     def set_fluid_state(self, r=None, v=None, rho=None, drho=None):

@@ -50,7 +50,7 @@ struct sphfsi_ctx {
     Batch bt{};
     Inst *d_inst = nullptr;
     Ctl *ctl = nullptr;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // every device allocation (pointer, bytes)
     // graph replay
     cudaGraphExec_t gexec = nullptr;
     double graph_dt = 0.0;
@@ -87,7 +87,7 @@ int dalloc(sphfsi_ctx *c, T **p, size_t count)
         return SPHFSI_E_NOMEM;
     }
     cudaMemsetAsync(q, 0, sizeof(T) * count, c->st);
-    c->allocs.push_back(q);
+    c->allocs.push_back({q, sizeof(T) * count});
     *p = (T *)q;
     return SPHFSI_OK;
 }
@@ -512,6 +512,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // ---- fluid
     Fluid &F = c->F;
     F.n = (int)nf;
+    F.lanes = D == 2 ? 4 : 8;
+    F.block = 128;
     for (int k = 0; k < 2; k++) {
         FluidState &S = F.s[k];
         TRY(dalloc(c, &S.x, nf));
@@ -930,6 +932,29 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
     return SPHFSI_OK;
 }
 
+int sphfsi_get_solid_positions_all(sphfsi_ctx *c, double *r)
+{
+    TRY(check_ctx(c, true));
+    if (!r) return SPHFSI_E_INVAL;
+    const int D = c->dim;
+    const Solid &S = c->S;
+    const int64_t n = S.n;
+    if (n == 0) return SPHFSI_OK;
+    std::vector<double> xyz[3];
+    TRY(download(c, xyz[0], S.x, n));
+    TRY(download(c, xyz[1], S.y, n));
+    if (D == 3) TRY(download(c, xyz[2], S.z, n));
+    std::vector<double> out((size_t)n * D);
+    for (const InstHost &h : c->ih) {
+        const int64_t s0 = h.d.s0;
+        for (int64_t a = 0; a < h.ns; a++) {
+            const size_t o = (size_t)(s0 + h.s_order[a]) * D;
+            for (int k = 0; k < D; k++) out[o + k] = xyz[k][s0 + a];
+        }
+    }
+    return deliver(r, out);
+}
+
 int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, const double *rho, const double *drho_dt)
 {
     TRY(check_ctx(c, true));
@@ -1192,6 +1217,126 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path)
     return SPHFSI_OK;
 }
 
+static bool valid_lanes(int dim, int L)
+{
+    return dim == 2 ? (L == 2 || L == 4 || L == 8) : (L == 4 || L == 8 || L == 16);
+}
+
+int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
+{
+    TRY(check_ctx(c, true));
+    if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
+        t->solid_variant < 0 || t->solid_variant > 1)
+        return SPHFSI_E_INVAL;
+    c->F.lanes = t->lanes;
+    c->F.block = t->block;
+    c->S.force_lane_path = t->solid_variant;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SPHFSI_OK;
+}
+
+int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
+{
+    TRY(check_ctx(c, true));
+    if (!t) return SPHFSI_E_INVAL;
+    t->lanes = c->F.lanes;
+    t->block = c->F.block;
+    t->solid_variant = c->S.force_lane_path;
+    t->step_ms = 0.0f;
+    return SPHFSI_OK;
+}
+
+int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *best)
+{
+    TRY(check_ctx(c, true));
+    if (!best || steps < 1 || steps > 10000 || std::isnan(dt_F) || c->st == nullptr) return SPHFSI_E_INVAL;
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    // snapshot of every device allocation, restored before each trial and at the end
+    size_t total = 0;
+    for (auto &a : c->allocs) total += (a.second + 255) & ~(size_t)255;
+    char *snap = nullptr;
+    if (cudaMalloc(&snap, total) != cudaSuccess) {
+        cudaGetLastError();
+        return SPHFSI_E_NOMEM;
+    }
+    auto copy_all = [&](bool save) -> int {
+        size_t off = 0;
+        for (auto &a : c->allocs) {
+            void *dst = save ? (void *)(snap + off) : a.first;
+            const void *src = save ? a.first : (const void *)(snap + off);
+            if (cudaMemcpyAsync(dst, src, a.second, cudaMemcpyDeviceToDevice, c->st) != cudaSuccess) return SPHFSI_E_CUDA;
+            off += (a.second + 255) & ~(size_t)255;
+        }
+        return cuda_rc(cudaStreamSynchronize(c->st));
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sphfsi_tuning cur{}, keep{};
+    sphfsi_get_tuning(c, &keep);
+    int rc = copy_all(true);
+    if (!rc) rc = cuda_rc(cudaEventCreate(&e0));
+    if (!rc) rc = cuda_rc(cudaEventCreate(&e1));
+    auto trial = [&](const sphfsi_tuning &t, float *ms) -> int {
+        int r = copy_all(false);
+        if (!r) r = sphfsi_set_tuning(c, &t);
+        if (!r) r = sphfsi_run(c, steps, dt_F);   // capture + warm-up
+        if (!r) r = cuda_rc(cudaEventRecord(e0, c->st));
+        if (!r) r = sphfsi_run(c, steps, dt_F);
+        if (!r) r = cuda_rc(cudaEventRecord(e1, c->st));
+        if (!r) r = sphfsi_sync(c);
+        if (!r) r = cuda_rc(cudaEventElapsedTime(ms, e0, e1));
+        if (!r) *ms /= (float)steps;
+        return r;
+    };
+    best->step_ms = 0.0f;
+    if (!rc) {
+        // coordinate search: lanes, then block size, then the 2-D solid kernel variant
+        cur = keep;
+        cur.solid_variant = 0;
+        const int lanes2[3] = {2, 4, 8}, lanes3[3] = {4, 8, 16}, blocks[3] = {64, 128, 256};
+        float tbest = 0.0f;
+        bool have = false;
+        auto consider = [&](const sphfsi_tuning &t) -> int {
+            float ms = 0.0f;
+            int r = trial(t, &ms);
+            if (r) return r;
+            if (!have || ms < tbest) {
+                have = true;
+                tbest = ms;
+                *best = t;
+                best->step_ms = ms;
+            }
+            return SPHFSI_OK;
+        };
+        for (int k = 0; k < 3 && !rc; k++) {
+            cur.lanes = c->dim == 2 ? lanes2[k] : lanes3[k];
+            cur.block = 128;
+            rc = consider(cur);
+        }
+        cur = *best;
+        for (int k = 0; k < 3 && !rc; k++) {
+            if (blocks[k] == 128) continue;
+            cur.block = blocks[k];
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc && c->dim == 2 && c->S.n && !c->S.force_grid_path) {
+            cur.solid_variant = 1;
+            rc = consider(cur);
+        }
+    }
+    int rc2 = copy_all(false);
+    if (!rc) rc = rc2;
+    if (!rc) rc = sphfsi_set_tuning(c, best);
+    else sphfsi_set_tuning(c, &keep);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(snap);
+    return rc;
+}
+
 int sphfsi_set_profiling(sphfsi_ctx *c, int on)
 {
     TRY(check_ctx(c, true));
@@ -1249,7 +1394,7 @@ void sphfsi_destroy(sphfsi_ctx *c)
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     if (c->join_ev) cudaEventDestroy(c->join_ev);
     if (c->side) cudaStreamDestroy(c->side);
-    for (void *p : c->allocs) cudaFree(p);
+    for (auto &a : c->allocs) cudaFree(a.first);
     delete c;
 }
 

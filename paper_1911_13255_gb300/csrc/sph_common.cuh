@@ -18,6 +18,7 @@ namespace sph {
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
 constexpr int kBlock = 128;           // threads per block of the particle kernels
+constexpr int kMaxBlock = 256;        // largest block of the tunable pair-loop kernels
 constexpr int kSolidBlock = 256;      // threads per block of the cooperative solid kernel
 constexpr long long kSpinLimit = 1ll << 22;   // bounded spin of the grid barrier (~0.5-2 s)
 
@@ -106,6 +107,8 @@ struct FluidState {
 
 struct Fluid {
     int n;            // total over the instances
+    int lanes;        // threads per target particle of the pair loops (tuned)
+    int block;        // threads per block of the pair loops (tuned)
     int *inst;        // instance of each slot
     FluidState s[2];
     float4 *P4;       // (x - x_cell, y - y_cell, z - z_cell, p)   sorted records

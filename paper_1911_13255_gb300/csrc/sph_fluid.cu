@@ -11,12 +11,30 @@
 // targets share their neighbour cells, so the records (two float4 per
 // particle) are served from L1/L2.  Pair geometry is FP32 on cell-relative
 // coordinates: r_ij = (x_i - x_cell_i) - (x_j - x_cell_j) - dcell * edge.
+#include <type_traits>
+
 #include "sph_common.cuh"
 
 namespace sph {
 
-// lanes per target particle
-template <int D> struct Lanes { static constexpr int L = D == 2 ? 4 : 8; };
+// Lanes per target particle: a runtime choice (Fluid::lanes, set by the
+// autotuner) among compiled instances, 2/4/8 in 2-D and 4/8/16 in 3-D.
+template <int D, typename Fn>
+static bool with_lanes(int L, Fn &&fn)
+{
+    if constexpr (D == 2) {
+        if (L == 2) fn(std::integral_constant<int, 2>{});
+        else if (L == 4) fn(std::integral_constant<int, 4>{});
+        else if (L == 8) fn(std::integral_constant<int, 8>{});
+        else return false;
+    } else {
+        if (L == 4) fn(std::integral_constant<int, 4>{});
+        else if (L == 8) fn(std::integral_constant<int, 8>{});
+        else if (L == 16) fn(std::integral_constant<int, 16>{});
+        else return false;
+    }
+    return true;
+}
 
 // Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz)
 // receives the offset o = -(dcell) * edge to add to (rel_i - rel_j).
@@ -203,20 +221,32 @@ __device__ __forceinline__ void flush_counts(Batch bt, int b, bool valid, Counts
     }
 }
 
-template <int D>
-static inline int grid_blocks(int n)
+static inline int grid_blocks(int n, int L, int block)
 {
-    long long t = (long long)n * Lanes<D>::L;
-    return (int)((t + kBlock - 1) / kBlock);
+    long long t = (long long)n * L;
+    return (int)((t + block - 1) / block);
 }
+
+// launch KERN<dim, L> over n targets with the lane count and block size of f
+#define SPH_LAUNCH_LANES(KERN, n, ...)                                                        \
+    do {                                                                                      \
+        const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
+            constexpr int L_ = decltype(Lc)::value;                                           \
+            KERN<2, L_><<<grid_blocks(n, L_, f.block), f.block, 0, st>>>(__VA_ARGS__);        \
+        })                                                                                    \
+                                  : with_lanes<3>(f.lanes, [&](auto Lc) {                     \
+            constexpr int L_ = decltype(Lc)::value;                                           \
+            KERN<3, L_><<<grid_blocks(n, L_, f.block), f.block, 0, st>>>(__VA_ARGS__);        \
+        });                                                                                   \
+        if (!ok_ || f.block < 32 || f.block > kMaxBlock || f.block % 32) return -1;           \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
+template <int D, int L>
+__global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
 {
-    constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
@@ -318,8 +348,7 @@ __global__ void __launch_bounds__(kBlock) k_momentum(Batch bt, Fluid f, Walls w,
 int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (dim == 2) k_momentum<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
-    else k_momentum<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    SPH_LAUNCH_LANES(k_momentum, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -327,10 +356,9 @@ int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid
 // a5: fluid force on each solid particle, f_a^F = -sum_i V_i (pair term),
 // the same pair expression and inputs as a4 (fluid at r^{n+1/2}, v^n)
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
+template <int D, int L>
+__global__ void __launch_bounds__(kMaxBlock) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
 {
-    constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t / L, lane = t % L;
     const bool act = k < s.n;
@@ -381,8 +409,7 @@ int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, in
         if (s.n) cudaMemsetAsync(s.fF, 0, sizeof(float) * 3 * s.n, st);
         return cudaGetLastError() == cudaSuccess ? 0 : -3;
     }
-    if (dim == 2) k_solid_fluid_force<2><<<grid_blocks<2>(s.n), kBlock, 0, st>>>(bt, f, s);
-    else k_solid_fluid_force<3><<<grid_blocks<3>(s.n), kBlock, 0, st>>>(bt, f, s);
+    SPH_LAUNCH_LANES(k_solid_fluid_force, s.n, bt, f, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -390,10 +417,9 @@ int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, in
 // a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}) + second half drift;
 // writes the end-of-step state to s[0] in cell order
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
+template <int D, int L>
+__global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
 {
-    constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
@@ -479,8 +505,7 @@ __global__ void __launch_bounds__(kBlock) k_density(Batch bt, Fluid f, Walls w, 
 int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (dim == 2) k_density<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
-    else k_density<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    SPH_LAUNCH_LANES(k_density, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -576,10 +601,9 @@ __device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, con
     return ff_mul(ff_sqr(a2), bq);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
+template <int D, int L>
+__global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
 {
-    constexpr int L = Lanes<D>::L;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const int b = i < f.n ? f.inst[i] : 0;
@@ -637,8 +661,7 @@ __global__ void __launch_bounds__(kBlock) k_reinit(Batch bt, Fluid f, Walls w, S
 int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (dim == 2) k_reinit<2><<<grid_blocks<2>(f.n), kBlock, 0, st>>>(bt, f, w, s);
-    else k_reinit<3><<<grid_blocks<3>(f.n), kBlock, 0, st>>>(bt, f, w, s);
+    SPH_LAUNCH_LANES(k_reinit, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -139,3 +139,55 @@ def test_batch_rejects_bad_selection_and_grid_path():
     with pytest.raises(SphError):
         batch.set_solid_path(2)
     batch.close()
+
+
+@pytest.mark.parametrize("lanes,block", [(2, 64), (4, 128), (8, 256)])
+def test_every_launch_shape_matches_the_oracle(lanes, block):
+    """Each compiled lane count / block size computes the same step."""
+    case = fc.channel_flag(seed=0)
+    ref = O.OracleSim(case)
+    dt, _, dts = ref.suggest_dt()
+    K = ref.substeps(dt, dts)
+    sim = Simulation.from_case(case)
+    sim.set_tuning(lanes, block)
+    assert sim.tuning()["lanes"] == lanes and sim.tuning()["block"] == block
+    sim.set_substeps(K)
+    sim.step(dt)
+    sim.sync()
+    ref.step(dt, K)
+    g, s = sim.get_fluid(), sim.get_solid()
+    e = dict(dvdt=rel(g["dvdt"], ref.f_dvdt), drho=rel(g["drho"], ref.f_drho), fF=rel(s["fF"], ref.s_fF))
+    assert max(e.values()) < ACC_TOL, e
+    with pytest.raises(SphError):
+        sim.set_tuning(3, 128)
+    with pytest.raises(SphError):
+        sim.set_tuning(4, 96)
+
+
+def test_autotune_leaves_the_state_unchanged_and_keeps_parity():
+    cases = _mixed_cases()
+    stream = torch.cuda.Stream()
+    batch = Simulation.from_cases(cases, stream=stream)
+    for _ in range(3):
+        batch.step(0.0)
+    batch.sync()
+    before = [_state(batch.select(b)) for b in range(len(cases))]
+    best = batch.autotune(0.0, steps=3)
+    assert best["step_ms"] > 0 and best["lanes"] in (2, 4, 8) and best["block"] in (64, 128, 256)
+    assert batch.tuning()["lanes"] == best["lanes"]
+    after = [_state(batch.select(b)) for b in range(len(cases))]
+    for b in range(len(cases)):
+        for k in before[b]:
+            assert np.array_equal(before[b][k], after[b][k]), (b, k)
+    # the tuned batch keeps stepping like the default one, to rounding
+    ref = Simulation.from_cases(cases, stream=stream)
+    for _ in range(3):
+        ref.step(0.0)
+    for sim in (batch, ref):
+        sim.run(5, 0.0)
+        sim.sync()
+    for b in range(len(cases)):
+        g, h = batch.select(b).get_fluid(), ref.select(b).get_fluid()
+        assert rel(g["r"], h["r"]) < 1e-9 and rel(g["v"], h["v"]) < 1e-4
+    batch.close()
+    ref.close()
