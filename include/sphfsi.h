@@ -298,6 +298,64 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
 int sphfsi_neighbor_counts_noalloc(const sphfsi_params *p, int64_t n, const double *r, double dp, int32_t *counts,
                                    void *cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Learned sub-stepper building blocks (the paper has no learned form; the
+ * network is the message-passing model described with sphfsi_mpnn_*).
+ * ------------------------------------------------------------------- */
+
+/* Tensor-core GEMM: C[M x N] = A[M x K] . B[N x K]^T (+ bias[N] if not
+ * NULL), A and B bfloat16 (raw 16-bit patterns) row-major with K contiguous,
+ * C FP32 row-major, all device pointers, 16-byte aligned.  M % 128 == 0,
+ * N % 16 == 0, K % 64 == 0 (callers pad with zeros), else SPHFSI_E_INVAL.
+ * Asynchronous on cuda_stream; the FP32 accumulation order over K is fixed
+ * (ascending chunks of 16). */
+int sphfsi_gemm_bf16(const void *A, const void *B, const float *bias, float *C, int64_t M, int64_t N, int64_t K,
+                     void *cuda_stream);
+
+/* Status of the bounded tensor-core waits since the last reset: *status
+ * bit 0 set if one ran out (the affected outputs were not written). */
+int sphfsi_tc_status(int32_t *status, int32_t reset);
+
+/* Message-passing network over one body's static neighbour graph (the
+ * learned solid sub-stepper).  With x the N x 64 feature matrix (FP32):
+ *   h = silu(x W_enc^T + b_enc)                                 (N x 128)
+ *   3 times: z = [h, sum_b w_ab (h_b - h_a), sum_b g_ab,k (h_b - h_a)]_{k<dim}
+ *            h = h + silu(z W_l^T + b_l)                (W_l: 128 x 128 (2+dim))
+ *   out = h W_dec^T + b_dec                                      (N x 16)
+ * Parameters are one FP32 vector [W_enc (128x64), b_enc, (W_l, b_l) x 3,
+ * W_dec (16x128), b_dec], weights row-major [out][in]; its length is
+ * sphfsi_mpnn_n_params(dim).  GEMMs run on the tensor cores with bfloat16
+ * operands and FP32 accumulation; everything else in FP32.
+ *
+ * The graph (ptr n+1, idx nnz, w nnz, g nnz x dim; host or device) must be a
+ * symmetric relation without self entries, with w_ab = w_ba and
+ * g_ab = -g_ba (one body at one spacing), else SPHFSI_E_INVAL.  The context
+ * holds `replicas` copies of the graph side by side, so a batch of replicas
+ * samples is one network evaluation over replicas x n nodes (node r n + a is
+ * node a of sample r).  All work is issued on cuda_stream. */
+typedef struct sphfsi_mpnn sphfsi_mpnn;
+int64_t sphfsi_mpnn_n_params(int32_t dim);
+int sphfsi_mpnn_create(sphfsi_mpnn **out, int32_t dim, int64_t n, int64_t nnz, const int64_t *ptr,
+                       const int64_t *idx, const double *w, const double *g, int32_t replicas, void *cuda_stream);
+/* Load parameters (resets the Adam moments and step count) / read them. */
+int sphfsi_mpnn_set_params(sphfsi_mpnn *m, const float *theta);
+int sphfsi_mpnn_get_params(sphfsi_mpnn *m, float *theta);
+/* out (replicas n x 16, may be NULL) = network(x (replicas n x 64)). */
+int sphfsi_mpnn_forward(sphfsi_mpnn *m, const float *x, float *out);
+/* After sphfsi_mpnn_forward: grad (n_params) = gradient of
+ * sum(dout * out) with respect to the parameters. */
+int sphfsi_mpnn_backward(sphfsi_mpnn *m, const float *dout, float *grad);
+/* One training step: forward on x, loss = mean over the masked nodes (mask
+ * NULL = all) of the squared error of the first 2 dim outputs against
+ * target (replicas n x 16), backward, one Adam step (b1 0.9, b2 0.999,
+ * eps 1e-8, learning rate lr).  *loss (may be NULL) receives the loss. */
+int sphfsi_mpnn_train_step(sphfsi_mpnn *m, const float *x, const float *target, const uint8_t *mask, float lr,
+                           float *loss);
+/* Wait for the context's stream; SPHFSI_E_TIMEOUT if a bounded tensor-core
+ * wait ran out. */
+int sphfsi_mpnn_sync(sphfsi_mpnn *m);
+void sphfsi_mpnn_destroy(sphfsi_mpnn *m);
+
 void sphfsi_destroy(sphfsi_ctx *c);
 const char *sphfsi_strerror(int code);
 

@@ -95,6 +95,18 @@ _SIGS = {
     "sphfsi_stage_times": (C.c_int, [_vp, _vp, C.c_int]),
     "sphfsi_step_time": (C.c_int, [_vp, _vp]),
     "sphfsi_neighbor_counts_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, _vp, C.c_double, _vp, _vp]),
+    "sphfsi_gemm_bf16": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int64, _vp]),
+    "sphfsi_tc_status": (C.c_int, [C.POINTER(C.c_int32), C.c_int32]),
+    "sphfsi_mpnn_n_params": (C.c_int64, [C.c_int32]),
+    "sphfsi_mpnn_create": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32,
+                                     _vp]),
+    "sphfsi_mpnn_set_params": (C.c_int, [_vp, _vp]),
+    "sphfsi_mpnn_get_params": (C.c_int, [_vp, _vp]),
+    "sphfsi_mpnn_forward": (C.c_int, [_vp, _vp, _vp]),
+    "sphfsi_mpnn_backward": (C.c_int, [_vp, _vp, _vp]),
+    "sphfsi_mpnn_train_step": (C.c_int, [_vp, _vp, _vp, _vp, C.c_float, _vp]),
+    "sphfsi_mpnn_sync": (C.c_int, [_vp]),
+    "sphfsi_mpnn_destroy": (None, [_vp]),
     "sphfsi_destroy": (None, [_vp]),
     "sphfsi_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -389,6 +401,92 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None):
             lib().sphfsi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gemm_bf16(A, B, bias=None, out=None, stream=None):
+    """C = A . B^T (+ bias) on the tensor cores: A (M x K), B (N x K) bfloat16
+    CUDA tensors, C FP32 (M x N); M % 128 == 0, N % 16 == 0, K % 64 == 0."""
+    import torch
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().sphfsi_gemm_bf16(_ptr(A.contiguous()), _ptr(B.contiguous()), _ptr(bias), _ptr(out), M, N, K,
+                                  _stream_handle(stream)), "sphfsi_gemm_bf16")
+    return out
+
+
+def tc_status(reset=False):
+    s = C.c_int32()
+    _check(lib().sphfsi_tc_status(C.byref(s), int(bool(reset))), "sphfsi_tc_status")
+    return s.value
+
+
+class Mpnn:
+    """The learned sub-stepper's network over one body's graph, replicated
+    `replicas` times (see include/sphfsi.h).  Arrays may be numpy (host) or
+    CUDA tensors; FP32 for x, out, targets, parameters."""
+
+    FIN, NOUT, C = 64, 16, 128
+
+    def __init__(self, dim, graph, replicas=1, stream=None):
+        ptr, idx, w, g = graph
+        self.dim, self.n, self.replicas = dim, len(ptr) - 1, int(replicas)
+        self._g = [np.ascontiguousarray(ptr, np.int64), np.ascontiguousarray(idx, np.int64),
+                   np.ascontiguousarray(w, np.float64), np.ascontiguousarray(g, np.float64)]
+        self._stream = stream
+        h = _vp()
+        _check(lib().sphfsi_mpnn_create(C.byref(h), dim, self.n, len(self._g[1]), *[_ptr(a) for a in self._g],
+                                        self.replicas, _stream_handle(stream)), "sphfsi_mpnn_create")
+        self.h = h
+        self.n_params = int(lib().sphfsi_mpnn_n_params(dim))
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, np.float32) if not hasattr(theta, "data_ptr") else theta
+        _check(lib().sphfsi_mpnn_set_params(self.h, _ptr(t)), "sphfsi_mpnn_set_params")
+
+    def get_params(self):
+        t = np.zeros(self.n_params, np.float32)
+        _check(lib().sphfsi_mpnn_get_params(self.h, _ptr(t)), "sphfsi_mpnn_get_params")
+        return t
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, np.float32) if not hasattr(x, "data_ptr") else x
+        out = np.zeros((self.n * self.replicas, self.NOUT), np.float32)
+        _check(lib().sphfsi_mpnn_forward(self.h, _ptr(x), _ptr(out)), "sphfsi_mpnn_forward")
+        self.sync()
+        return out
+
+    def backward(self, dout):
+        d = np.ascontiguousarray(dout, np.float32)
+        grad = np.zeros(self.n_params, np.float32)
+        _check(lib().sphfsi_mpnn_backward(self.h, _ptr(d), _ptr(grad)), "sphfsi_mpnn_backward")
+        self.sync()
+        return grad
+
+    def train_step(self, x, target, mask=None, lr=1e-3):
+        conv = lambda a, dt: a if (a is None or hasattr(a, "data_ptr")) else np.ascontiguousarray(a, dt)
+        x, target, mask = conv(x, np.float32), conv(target, np.float32), conv(mask, np.uint8)
+        loss = np.zeros(1, np.float32)
+        _check(lib().sphfsi_mpnn_train_step(self.h, _ptr(x), _ptr(target), _ptr(mask), float(lr), _ptr(loss)),
+               "sphfsi_mpnn_train_step")
+        self.sync()
+        return float(loss[0])
+
+    def sync(self):
+        _check(lib().sphfsi_mpnn_sync(self.h), "sphfsi_mpnn_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sphfsi_mpnn_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,16 @@
+// Internal interface of the learned sub-stepper kernels (tensor-core GEMM,
+// graph aggregation, element-wise and optimiser kernels).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+// C[M x N] = A[M x K] . B[N x K]^T (+ bias), bfloat16 operands, FP32 result.
+// Returns 0, -1 (bad sizes or alignment), -7 (too large) or -3 (launch).
+int launch_gemm_bf16(const uint16_t *A, const uint16_t *B, const float *bias, float *C, long long M, long long N,
+                     long long K, cudaStream_t st);
+// status bits of the bounded tensor-core waits (bit 0: a wait ran out)
+int read_tc_status(unsigned *out, bool reset);
+
+}  // namespace sph
