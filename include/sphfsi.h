@@ -101,6 +101,9 @@ typedef struct {
     double mom_fs_solid[3];  /* sum of solid-side fluid forces, last step        */
     int32_t solid_path;      /* 1 = cluster-resident sub-steps, 2 = cooperative grid */
     int32_t kernels_per_step; /* this library's kernel launches per step        */
+    int64_t learned_accepted; /* steps whose learned solid step was accepted    */
+    int64_t learned_rejected; /* steps that fell back to the plain sub-steps    */
+    double learned_residual;  /* residual R of the last learned step            */
 } sphfsi_info;
 
 /* Create an empty context bound to a CUDA stream (cudaStream_t, may be 0
@@ -315,6 +318,30 @@ int sphfsi_gemm_bf16(const void *A, const void *B, const float *bias, float *C, 
 /* Status of the bounded tensor-core waits since the last reset: *status
  * bit 0 set if one ran out (the affected outputs were not written). */
 int sphfsi_tc_status(int32_t *status, int32_t reset);
+
+/* The graph the learned sub-stepper works on, for the selected instance in
+ * original order: ptr (n_solid + 1), idx, w (pairs_ss entries each, see
+ * sphfsi_info) and g (pairs_ss x dim): the static reference neighbour list of
+ * the solid with w_ab = V0 W(|r0_a - r0_b|, h_S) and g_ab = h_S V0 grad0_a W_ab.
+ * Host pointers; any may be NULL. */
+int sphfsi_solid_graph(sphfsi_ctx *c, int64_t *ptr, int64_t *idx, double *w, double *g);
+
+/* Learned sub-stepper (no counterpart in the paper): every later step runs,
+ * after the coupling force, the network of sphfsi_mpnn_* (parameters theta)
+ * on each body's graph with the features
+ *   [u / s_u, v / s_v, F - I (row-major), f^F / s_f, constrained, dt_F / s_t]
+ * (u = r - r0; scales = {s_u, s_v, s_f, s_t, s_du, s_dv}) and proposes
+ *   du = dt_F v + s_du out[0:dim],  dv = dt_F (f^F / m + g) + s_dv out[dim:2 dim]
+ * (0 for constrained particles).  The proposal of an instance is accepted
+ * when its residual
+ *   R = |m (v' - v) - dt_F (f_int(r + du/2) + f^F + m g)| / |m v'|
+ * (norms over the free particles; f_int one plain force evaluation with F
+ * from the positions, Eq. correctmatrix) is at most tol: positions,
+ * velocities, F (from the new positions) and the time averages
+ * (du / dt_F, dv / dt_F) are then committed and the K sub-steps skipped;
+ * otherwise the plain sub-steps run from the unchanged state.  tol < 0
+ * switches the learned path off. */
+int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, double tol);
 
 /* Message-passing network over one body's static neighbour graph (the
  * learned solid sub-stepper).  With x the N x 64 feature matrix (FP32):

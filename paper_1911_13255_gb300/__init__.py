@@ -45,7 +45,8 @@ class Info(C.Structure):
                 ("pairs_fs", C.c_int64), ("pairs_sf", C.c_int64), ("pairs_ss", C.c_int64),
                 ("pairs_total", C.c_int64), ("vmax_f", C.c_double), ("vmax_s", C.c_double),
                 ("amax_s", C.c_double), ("mom_fs_fluid", C.c_double * 3), ("mom_fs_solid", C.c_double * 3),
-                ("solid_path", C.c_int32), ("kernels_per_step", C.c_int32)]
+                ("solid_path", C.c_int32), ("kernels_per_step", C.c_int32),
+                ("learned_accepted", C.c_int64), ("learned_rejected", C.c_int64), ("learned_residual", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +98,8 @@ _SIGS = {
     "sphfsi_neighbor_counts_noalloc": (C.c_int, [C.POINTER(Params), C.c_int64, _vp, C.c_double, _vp, _vp]),
     "sphfsi_gemm_bf16": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int64, C.c_int64, _vp]),
     "sphfsi_tc_status": (C.c_int, [C.POINTER(C.c_int32), C.c_int32]),
+    "sphfsi_solid_graph": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "sphfsi_set_learned": (C.c_int, [_vp, _vp, _vp, C.c_double]),
     "sphfsi_mpnn_n_params": (C.c_int64, [C.c_int32]),
     "sphfsi_mpnn_create": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32,
                                      _vp]),
@@ -290,6 +293,24 @@ class Simulation:
         t = Tuning()
         _check(lib().sphfsi_get_tuning(self.h, C.byref(t)), "sphfsi_get_tuning")
         return t.as_dict()
+
+    def solid_graph(self):
+        """(ptr, idx, w, g) of the selected instance's body, original order."""
+        n = self.ns
+        nnz = self.info()["pairs_ss"]
+        ptr = np.zeros(n + 1, np.int64)
+        idx = np.zeros(max(nnz, 1), np.int64)
+        w = np.zeros(max(nnz, 1))
+        g = np.zeros((max(nnz, 1), self.dim))
+        _check(lib().sphfsi_solid_graph(self.h, _ptr(ptr), _ptr(idx), _ptr(w), _ptr(g)), "sphfsi_solid_graph")
+        return ptr, idx[:nnz], w[:nnz], g[:nnz]
+
+    def set_learned(self, theta, scales, tol):
+        """Learned sub-stepper with parameters theta and scales
+        (s_u, s_v, s_f, s_t, s_du, s_dv); tol < 0 switches it off."""
+        th = np.ascontiguousarray(theta, np.float32)
+        sc = np.ascontiguousarray(scales, np.float64)
+        _check(lib().sphfsi_set_learned(self.h, _ptr(th), _ptr(sc), float(tol)), "sphfsi_set_learned")
 
     def pairs_total(self):
         """Pair interactions of all instances since creation."""

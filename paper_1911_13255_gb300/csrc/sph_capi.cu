@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "sph_common.cuh"
+#include "sph_learn.cuh"
 #include "sphfsi.h"
 
 using namespace sph;
@@ -69,6 +70,8 @@ struct sphfsi_ctx {
     // side stream for the solid branch, which runs beside momentum and continuity
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // learned sub-stepper (sphfsi_set_learned)
+    sphfsi_mpnn *mpnn = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -191,6 +194,11 @@ int enqueue_step(sphfsi_ctx *c, double dt)
         TRY(cuda_rc(cudaStreamWaitEvent(c->side, c->fork_ev, 0)));
         TRY(mark(c, 4, c->side));
         TRY(launch_solid_fluid_force(c->bt, c->F, c->S, D, c->side));
+        if (c->S.learned) {
+            TRY(launch_learn_features(c->bt, c->S, mpnn_input(c->mpnn), D, c->side));
+            TRY(mpnn_forward_async(c->mpnn));
+            TRY(launch_learn_candidate(c->bt, c->S, mpnn_output(c->mpnn), D, c->side));
+        }
         TRY(mark(c, 7, c->side));
         TRY(launch_solid_substeps(c->bt, c->S, c->ih[0].d.P, D, &c->solid_path, c->side));
         TRY(mark(c, 8, c->side));
@@ -201,10 +209,10 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_density(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 6));
     if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
-    TRY(launch_finish(c->bt, st));
+    TRY(launch_finish(c->bt, c->S.learned, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
-    c->kernels_per_step = 10 + (c->S.n ? 2 : 0);
+    c->kernels_per_step = 10 + (c->S.n ? 2 : 0) + (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -1143,6 +1151,9 @@ int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out)
     }
     out->solid_path = c->solid_path;
     out->kernels_per_step = c->kernels_per_step;
+    out->learned_accepted = hc.l_acc;
+    out->learned_rejected = hc.l_rej;
+    out->learned_residual = hc.l_res;
     return SPHFSI_OK;
 }
 
@@ -1337,6 +1348,133 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
     return rc;
 }
 
+// Graph of the bodies for the network: the static reference neighbour
+// list, w_ab = V0 W(|r0_a - r0_b|, h_S) in FP64 and g_ab = h_S V0 grad0_a W_ab
+// (the list's FP32 entries).  inst < 0: every instance, device order, global
+// slots; else that instance in its original order with local indices.
+static int body_graph(sphfsi_ctx *c, int inst, std::vector<int64_t> &ptr, std::vector<int64_t> &idx,
+                      std::vector<double> &w, std::vector<double> &g)
+{
+    const int D = c->dim;
+    const Solid &S = c->S;
+    std::vector<int> hp;
+    std::vector<float4> hnb;
+    std::vector<double> X[3];
+    TRY(download(c, hp, S.nb_ptr, (size_t)S.n + 1));
+    TRY(download(c, hnb, S.nb, (size_t)S.nnz));
+    TRY(download(c, X[0], S.x0, S.n));
+    TRY(download(c, X[1], S.y0, S.n));
+    if (D == 3) TRY(download(c, X[2], S.z0, S.n));
+    const double pi = 3.14159265358979323846;
+    ptr.assign(1, 0);
+    idx.clear();
+    w.clear();
+    g.clear();
+    for (int b = 0; b < c->B; b++) {
+        if (inst >= 0 && b != inst) continue;
+        const InstHost &h = c->ih[b];
+        const int s0 = h.d.s0;
+        const double hS = h.d.P.hS_d, V0 = std::pow(h.s_dp, D);
+        const double alpha = D == 2 ? 7.0 / (4.0 * pi * hS * hS) : 21.0 / (16.0 * pi * hS * hS * hS);
+        std::vector<int> inv(h.ns);
+        for (int64_t a = 0; a < h.ns; a++) inv[h.s_order[a]] = (int)a;
+        for (int64_t r = 0; r < h.ns; r++) {
+            // row r: device slot (device order) or the slot of original particle r
+            const int a = s0 + (inst >= 0 ? inv[r] : (int)r);
+            for (int q = hp[a]; q < hp[a + 1]; q++) {
+                int bb;
+                std::memcpy(&bb, &hnb[q].w, sizeof(int));
+                double d2 = 0.0;
+                for (int k = 0; k < D; k++) d2 += (X[k][a] - X[k][bb]) * (X[k][a] - X[k][bb]);
+                const double qq = std::sqrt(d2) / hS, t = 1.0 - 0.5 * qq;
+                idx.push_back(inst >= 0 ? h.s_order[bb - s0] : bb);
+                w.push_back(V0 * alpha * t * t * t * t * (1.0 + 2.0 * qq));
+                const float e[3] = {hnb[q].x, hnb[q].y, hnb[q].z};
+                for (int k = 0; k < D; k++) g.push_back(hS * (double)e[k]);
+            }
+            ptr.push_back((int64_t)idx.size());
+        }
+    }
+    // rows in original order: sort each row's columns ascending
+    if (inst >= 0) {
+        const size_t n = ptr.size() - 1;
+        for (size_t r = 0; r < n; r++) {
+            std::vector<size_t> o(ptr[r + 1] - ptr[r]);
+            for (size_t k = 0; k < o.size(); k++) o[k] = ptr[r] + k;
+            std::sort(o.begin(), o.end(), [&](size_t p, size_t q) { return idx[p] < idx[q]; });
+            std::vector<int64_t> i2;
+            std::vector<double> w2, g2;
+            for (size_t p : o) {
+                i2.push_back(idx[p]);
+                w2.push_back(w[p]);
+                for (int k = 0; k < D; k++) g2.push_back(g[p * D + k]);
+            }
+            std::copy(i2.begin(), i2.end(), idx.begin() + ptr[r]);
+            std::copy(w2.begin(), w2.end(), w.begin() + ptr[r]);
+            std::copy(g2.begin(), g2.end(), g.begin() + ptr[r] * D);
+        }
+    }
+    return SPHFSI_OK;
+}
+
+int sphfsi_solid_graph(sphfsi_ctx *c, int64_t *ptr, int64_t *idx, double *w, double *g)
+{
+    TRY(check_ctx(c, true));
+    std::vector<int64_t> p, i;
+    std::vector<double> wv, gv;
+    TRY(body_graph(c, c->sel, p, i, wv, gv));
+    if (ptr) std::memcpy(ptr, p.data(), sizeof(int64_t) * p.size());
+    if (idx && !i.empty()) std::memcpy(idx, i.data(), sizeof(int64_t) * i.size());
+    if (w && !wv.empty()) std::memcpy(w, wv.data(), sizeof(double) * wv.size());
+    if (g && !gv.empty()) std::memcpy(g, gv.data(), sizeof(double) * gv.size());
+    return SPHFSI_OK;
+}
+
+int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, double tol)
+{
+    TRY(check_ctx(c, true));
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    if (tol < 0.0) {
+        c->S.learned = 0;
+        return SPHFSI_OK;
+    }
+    if (!theta || !scales || c->S.n == 0 || std::isnan(tol)) return SPHFSI_E_INVAL;
+    for (int k = 0; k < 6; k++)
+        if (!(scales[k] > 0.0)) return SPHFSI_E_INVAL;
+    Solid &S = c->S;
+    if (!c->mpnn) {
+        std::vector<int64_t> p, i;
+        std::vector<double> wv, gv;
+        TRY(body_graph(c, -1, p, i, wv, gv));
+        TRY(sphfsi_mpnn_create(&c->mpnn, c->dim, S.n, (int64_t)i.size(), p.data(), i.data(), wv.data(), gv.data(), 1,
+                               c->side));
+        const int n = S.n, D = c->dim;
+        TRY(dalloc(c, &S.lx, n));
+        TRY(dalloc(c, &S.ly, n));
+        TRY(dalloc(c, &S.lz, D == 3 ? n : 1));
+        TRY(dalloc(c, &S.mx, n));
+        TRY(dalloc(c, &S.my, n));
+        TRY(dalloc(c, &S.mz, D == 3 ? n : 1));
+        TRY(dalloc(c, &S.lv4, n));
+        TRY(dalloc(c, &S.lH, (size_t)9 * n));
+        TRY(dalloc(c, &S.lQ, (size_t)(D == 2 ? 1 : 3) * n));
+        TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    }
+    TRY(sphfsi_mpnn_set_params(c->mpnn, theta));
+    S.l_su = (float)scales[0];
+    S.l_sv = (float)scales[1];
+    S.l_sf = (float)scales[2];
+    S.l_st = (float)scales[3];
+    S.l_sdu = (float)scales[4];
+    S.l_sdv = (float)scales[5];
+    S.l_tol = tol > 3.0e38 ? 3.0e38f : (float)tol;
+    S.learned = 1;
+    return SPHFSI_OK;
+}
+
 int sphfsi_set_profiling(sphfsi_ctx *c, int on)
 {
     TRY(check_ctx(c, true));
@@ -1388,6 +1526,7 @@ void sphfsi_destroy(sphfsi_ctx *c)
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     if (c->side) cudaStreamSynchronize(c->side);
+    if (c->mpnn) sphfsi_mpnn_destroy(c->mpnn);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     for (int k = 0; k < sphfsi_ctx::kEvents; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -56,6 +56,12 @@ struct Ctl {
     unsigned long long pairs_total;
     double last_dt;
     int last_K, pad3;
+    // learned sub-stepper of this step
+    int learned_ok;              // 1: the network's step was accepted, the sub-steps are skipped
+    int pad4;
+    double lnum, lden;           // residual sums |m (v' - v) - dt f(x_mid)|^2, |m v'|^2 (FP64)
+    double l_res;                // residual of the last step
+    long long l_acc, l_rej;      // accepted / rejected steps
 };
 
 // Physical constants of the fluid, the walls and the solid of one instance.
@@ -167,6 +173,15 @@ struct Solid {
     int force_lane_path;      // 1: in 2-D use the 4-lane cluster kernel, not the one-thread one
     int max_nb;               // largest static neighbour count of a particle
     int max_ns;               // largest body of an instance
+    // learned sub-stepper (when learned != 0)
+    int learned;
+    float l_tol;              // residual threshold
+    float l_su, l_sv, l_sf, l_st, l_sdu, l_sdv;   // feature / output scales
+    double *lx, *ly, *lz;     // candidate end positions
+    double *mx, *my, *mz;     // mid positions
+    float4 *lv4;              // candidate end velocities
+    float *lH;                // n * 9 displacement gradient at the candidate end positions
+    float4 *lQ;               // P B0 at the mid positions (2-D one, 3-D three float4)
 };
 
 // What every kernel needs to find an instance.
@@ -249,7 +264,7 @@ __device__ __forceinline__ float dW_F(float r, const Phys &P)
 int launch_control_normals(const Batch &bt, const Solid &s, double dt_fixed, int K_fixed, int dim, cudaStream_t st);
 int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int do_drift, cudaStream_t st);
 int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
-int launch_finish(const Batch &bt, cudaStream_t st);
+int launch_finish(const Batch &bt, int learned, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);
 int launch_scatter(const int *key, const int *cstart, int *ccount, int *perm, int n, cudaStream_t st);
 
@@ -266,5 +281,9 @@ int launch_solid_setup_count(const Batch &bt, Solid &s, int dim, int *counts, cu
 int launch_solid_setup_fill(const Batch &bt, Solid &s, int dim, cudaStream_t st);
 // P0: host copy of instance 0's constants (used when the batch holds one instance)
 int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, int *path, cudaStream_t st);
+// learned sub-stepper: features into x (n x 64), then, from the network's
+// outputs (n x 16), candidate, residual and accept / reject (sph_solid.cu)
+int launch_learn_features(const Batch &bt, const Solid &s, float *x, int dim, cudaStream_t st);
+int launch_learn_candidate(const Batch &bt, const Solid &s, const float *out, int dim, cudaStream_t st);
 
 }  // namespace sph

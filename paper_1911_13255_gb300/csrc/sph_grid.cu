@@ -48,6 +48,8 @@ __global__ void k_control_normals(Batch bt, Solid s, double dt_fixed, int K_fixe
         ctl->reinit = (ctl->n_reinit > 0 && (ctl->step % ctl->n_reinit) == 0) ? 1 : 0;
         ctl->n_ff = ctl->n_fw = ctl->n_fs = ctl->n_sf = 0ull;
         for (int k = 0; k < 3; k++) ctl->mom_fluid[k] = ctl->mom_solid[k] = 0.0;
+        ctl->learned_ok = 0;
+        ctl->lnum = ctl->lden = 0.0;
     }
     if (t >= s.n) return;
     const int a = t;
@@ -94,7 +96,7 @@ int launch_control_normals(const Batch &bt, const Solid &s, double dt_fixed, int
 }
 
 // finish: time, step, pair counters, non-finite check (one thread per instance)
-__global__ void k_finish(Batch bt)
+__global__ void k_finish(Batch bt, int learned)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= bt.B) return;
@@ -102,8 +104,16 @@ __global__ void k_finish(Batch bt)
     float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
     if (!(vF <= 3.0e38f) || !(vS <= 3.0e38f) || !(aS <= 3.0e38f)) ctl->status |= ST_NONFINITE;
     unsigned long long fl = ctl->n_ff + ctl->n_fw + ctl->n_fs;
-    unsigned long long p = 2ull * fl + ctl->n_sf + (ctl->reinit ? fl : 0ull) +
-                           (unsigned long long)(2 * ctl->K + 1) * (unsigned long long)bt.I[b].nnz;
+    const unsigned long long nnz = (unsigned long long)bt.I[b].nnz;
+    unsigned long long p = 2ull * fl + ctl->n_sf + (ctl->reinit ? fl : 0ull);
+    // learned step: F at the mid and end positions and one force loop (3
+    // solid pair loops); the sub-steps (2 K + 1) only when it was rejected
+    if (learned && bt.I[b].ns > 0) {
+        p += 3ull * nnz;
+        if (ctl->learned_ok) ctl->l_acc += 1;
+        else ctl->l_rej += 1;
+    }
+    if (!ctl->learned_ok) p += (unsigned long long)(2 * ctl->K + 1) * nnz;
     ctl->pairs_total += p;
     ctl->last_dt = ctl->dt;
     ctl->last_K = ctl->K;
@@ -111,9 +121,9 @@ __global__ void k_finish(Batch bt)
     ctl->step += 1;
 }
 
-int launch_finish(const Batch &bt, cudaStream_t st)
+int launch_finish(const Batch &bt, int learned, cudaStream_t st)
 {
-    k_finish<<<(bt.B + kBlock - 1) / kBlock, kBlock, 0, st>>>(bt);
+    k_finish<<<(bt.B + kBlock - 1) / kBlock, kBlock, 0, st>>>(bt, learned);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

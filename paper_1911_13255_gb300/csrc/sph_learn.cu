@@ -376,6 +376,13 @@ int stage_in(sphfsi_mpnn *m, void *dst, const void *src, size_t bytes)
 
 }  // namespace
 
+namespace sph {
+float *mpnn_input(sphfsi_mpnn *m) { return m->xin; }
+const float *mpnn_output(sphfsi_mpnn *m) { return m->out; }
+int mpnn_forward_async(sphfsi_mpnn *m) { return forward(m); }
+int mpnn_kernels_per_forward() { return 3 + 3 * kLayers + 2; }   // encoder, layers, decoder
+}  // namespace sph
+
 // ---------------------------------------------------------------------------
 // C-ABI
 // ---------------------------------------------------------------------------

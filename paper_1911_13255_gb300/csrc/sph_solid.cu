@@ -242,6 +242,20 @@ __device__ __forceinline__ void store_Q(float4 *Q4, int a, const float *Q)
     }
 }
 
+template <int D>
+__device__ __forceinline__ void load_Q(const float4 *Q4, int a, float *Q)
+{
+    if (D == 2) {
+        const float4 q = Q4[a];
+        Q[0] = q.x, Q[1] = q.y, Q[2] = q.z, Q[3] = q.w;
+    } else {
+        for (int r = 0; r < 3; r++) {
+            const float4 q = Q4[3 * a + r];
+            Q[3 * r] = q.x, Q[3 * r + 1] = q.y, Q[3 * r + 2] = q.z;
+        }
+    }
+}
+
 // dH/dt = [sum_b (v_b - v_a) (x) (V0 grad0_a W_ab)] B0_a   (reading R9)
 template <int D>
 __device__ __forceinline__ void deformation_rate(const Solid &s, int a, const float4 va, float *Hd)
@@ -272,6 +286,7 @@ __global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Batch bt, Solid 
     // one instance only (the launcher checks): its whole body over the grid
     const Phys &P = bt.I[0].P;
     Ctl *ctl = bt.ctl;
+    if (ctl->learned_ok) return;   // the learned step was accepted: no sub-steps
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -455,6 +470,7 @@ __device__ __forceinline__ void solid_lanes_body(const Solid &s, const Phys &P, 
     const int la = (int)rank * kPPC + g;
     const int a = s0 + la;
     const bool own = la < ns;
+    if (ctl->learned_ok) return;   // the learned step was accepted: no sub-steps
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -750,6 +766,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     const int la = (int)rank * kC1Threads + g;
     const int a = s0 + la;
     const bool own = la < ns;
+    if (ctl->learned_ok) return;   // the learned step was accepted: no sub-steps
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
     const float dts = (float)dtsd, hdts = 0.5f * dts;
@@ -1031,6 +1048,211 @@ int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, in
     else e = cudaLaunchKernelEx(&cfg, k_solid_substeps<3>, bt, s);
     if (path) *path = 2;
     return e == cudaSuccess ? 0 : -3;
+}
+
+// ---------------------------------------------------------------------------
+// Learned sub-stepper (the paper has none): the network proposes the step's
+// displacement and velocity change of every particle; the proposal is kept
+// only if its momentum-balance residual over the body,
+//   R = |m (v' - v) - dt (f_int(x_mid) + f^F + m g)| / |m v'|
+// with x_mid = r + du / 2 and f_int one plain force evaluation (F from the
+// positions, Eq. correctmatrix; neo-Hookean P B0; force loop), is at most the
+// threshold; else the plain sub-steps run (they test ctl->learned_ok).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_learn_features(Batch bt, Solid s, float *x)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const Ctl &ctl = bt.ctl[s.inst[a]];
+    float *row = x + (size_t)a * 64;
+    const double u[3] = {s.x[a] - s.x0[a], s.y[a] - s.y0[a], D == 3 ? s.z[a] - s.z0[a] : 0.0};
+    const float4 v = s.v4[a];
+    const float vv[3] = {v.x, v.y, v.z};
+    int o = 0;
+    for (int k = 0; k < D; k++) row[o++] = (float)(u[k] / (double)s.l_su);
+    for (int k = 0; k < D; k++) row[o++] = vv[k] / s.l_sv;
+    for (int k = 0; k < D * D; k++) row[o++] = s.H[9 * a + k];
+    for (int k = 0; k < D; k++) row[o++] = s.fF[3 * a + k] / s.l_sf;
+    row[o++] = s.cons[a] ? 1.0f : 0.0f;
+    row[o++] = (float)(ctl.dt / (double)s.l_st);
+}
+
+// candidate end and mid states from the outputs
+template <int D>
+__global__ void k_learn_apply(Batch bt, Solid s, const float *__restrict__ out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const int b = s.inst[a];
+    const Phys &P = bt.I[b].P;
+    const double dt = bt.ctl[b].dt;
+    const float4 v = s.v4[a];
+    const float vv[3] = {v.x, v.y, v.z};
+    const float *y = out + (size_t)a * 16;
+    double du[3] = {0.0, 0.0, 0.0};
+    float vn[3] = {0.f, 0.f, 0.f};
+    if (!s.cons[a]) {
+        for (int k = 0; k < D; k++) {
+            du[k] = dt * (double)vv[k] + (double)s.l_sdu * (double)y[k];
+            const float dv = (float)dt * (s.fF[3 * a + k] / P.mS + P.g[k]) + s.l_sdv * y[D + k];
+            vn[k] = vv[k] + dv;
+        }
+    }
+    s.lx[a] = s.x[a] + du[0];
+    s.ly[a] = s.y[a] + du[1];
+    s.mx[a] = s.x[a] + 0.5 * du[0];
+    s.my[a] = s.y[a] + 0.5 * du[1];
+    if (D == 3) {
+        s.lz[a] = s.z[a] + du[2];
+        s.mz[a] = s.z[a] + 0.5 * du[2];
+    }
+    s.lv4[a] = make_float4(vn[0], vn[1], vn[2], 0.0f);
+}
+
+// H = [sum_b ((p_b - p_a) - (X_b - X_a)) (x) V0 grad0_a W_ab] B0 at the mid
+// positions (-> P B0) and at the end positions (-> lH)
+template <int D>
+__global__ void k_learn_stress(Batch bt, Solid s)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const Phys &P = bt.I[s.inst[a]].P;
+    float Gm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Ge[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const double Xa[3] = {s.x0[a], s.y0[a], D == 3 ? s.z0[a] : 0.0};
+    const double Ma[3] = {s.mx[a], s.my[a], D == 3 ? s.mz[a] : 0.0};
+    const double Ea[3] = {s.lx[a], s.ly[a], D == 3 ? s.lz[a] : 0.0};
+    for (int q = s.nb_ptr[a]; q < s.nb_ptr[a + 1]; q++) {
+        const float4 e = s.nb[q];
+        const int b = __float_as_int(e.w);
+        const float g[3] = {e.x, e.y, e.z};
+        const double Xb[3] = {s.x0[b], s.y0[b], D == 3 ? s.z0[b] : 0.0};
+        const double Mb[3] = {s.mx[b], s.my[b], D == 3 ? s.mz[b] : 0.0};
+        const double Eb[3] = {s.lx[b], s.ly[b], D == 3 ? s.lz[b] : 0.0};
+        for (int i = 0; i < D; i++) {
+            const float dm = (float)((Mb[i] - Ma[i]) - (Xb[i] - Xa[i]));
+            const float de = (float)((Eb[i] - Ea[i]) - (Xb[i] - Xa[i]));
+            for (int j = 0; j < D; j++) {
+                Gm[i * D + j] += dm * g[j];
+                Ge[i * D + j] += de * g[j];
+            }
+        }
+    }
+    const float *B = s.B0 + 9 * a;
+    float Hm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < D; i++)
+        for (int j = 0; j < D; j++) {
+            float hm = 0.f, he = 0.f;
+            for (int k = 0; k < D; k++) {
+                hm += Gm[i * D + k] * B[k * D + j];
+                he += Ge[i * D + k] * B[k * D + j];
+            }
+            Hm[i * D + j] = hm;
+            s.lH[9 * a + i * D + j] = he;
+        }
+    float Q[9];
+    stress_QB<D>(Hm, B, P.mu, P.lam, Q);
+    store_Q<D>(s.lQ, a, Q);
+}
+
+// residual sums of the instance (free particles)
+template <int D>
+__global__ void k_learn_residual(Batch bt, Solid s)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n || s.cons[a]) return;
+    const int b = s.inst[a];
+    const Phys &P = bt.I[b].P;
+    Ctl *ctl = bt.ctl + b;
+    float Qa[9];
+    load_Q<D>(s.lQ, a, Qa);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int q = s.nb_ptr[a]; q < s.nb_ptr[a + 1]; q++) {
+        const float4 e = s.nb[q];
+        const int c = __float_as_int(e.w);
+        const float g[3] = {e.x, e.y, e.z};
+        float Qb[9];
+        load_Q<D>(s.lQ, c, Qb);
+        for (int i = 0; i < D; i++)
+            for (int j = 0; j < D; j++) acc[i] += (Qa[i * D + j] + Qb[i * D + j]) * g[j];
+    }
+    const float4 v = s.v4[a], vn = s.lv4[a];
+    const float vv[3] = {v.x, v.y, v.z}, vnn[3] = {vn.x, vn.y, vn.z};
+    const float dt = (float)ctl->dt;
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < D; k++) {
+        const float f = acc[k] / P.rhoS + s.fF[3 * a + k] / P.mS + P.g[k];
+        const double e = (double)(vnn[k] - vv[k]) - (double)dt * (double)f;
+        num += e * e;
+        den += (double)vnn[k] * (double)vnn[k];
+    }
+    atomicAdd(&ctl->lnum, num);
+    atomicAdd(&ctl->lden, den);
+}
+
+// accept (commit the candidate, time averages, maxima) or reject
+template <int D>
+__global__ void k_learn_commit(Batch bt, Solid s)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const int b = s.inst[a];
+    Ctl *ctl = bt.ctl + b;
+    const double R = sqrt(ctl->lnum) / (sqrt(ctl->lden) + 1e-30);
+    const bool ok = R <= (double)s.l_tol;
+    if (a == bt.I[b].s0) {
+        ctl->learned_ok = ok ? 1 : 0;
+        ctl->l_res = R;
+    }
+    if (!ok) return;
+    const double dt = ctl->dt, idt = 1.0 / dt;
+    const float4 v = s.v4[a], vn = s.lv4[a];
+    const double xe[3] = {s.lx[a], s.ly[a], D == 3 ? s.lz[a] : 0.0};
+    const double xs[3] = {s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0};
+    const float vv[3] = {v.x, v.y, v.z}, vnn[3] = {vn.x, vn.y, vn.z};
+    float vm = 0.f, am = 0.f;
+    for (int k = 0; k < 3; k++) {
+        const double vb = k < D ? (xe[k] - xs[k]) * idt : 0.0;
+        const double ab = k < D ? ((double)vnn[k] - (double)vv[k]) * idt : 0.0;
+        s.vbar[3 * a + k] = vb;
+        s.abar[3 * a + k] = ab;
+        vm += vnn[k] * vnn[k];
+        am += (float)(ab * ab);
+    }
+    s.x[a] = xe[0];
+    s.y[a] = xe[1];
+    if (D == 3) s.z[a] = xe[2];
+    s.v4[a] = vn;
+    for (int k = 0; k < D * D; k++) s.H[9 * a + k] = s.lH[9 * a + k];
+    atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
+    atomic_max_pos(&ctl->amaxS, sqrtf(am));
+}
+
+int launch_learn_features(const Batch &bt, const Solid &s, float *x, int dim, cudaStream_t st)
+{
+    if (s.n == 0) return 0;
+    const int nb = (s.n + kBlock - 1) / kBlock;
+    if (dim == 2) k_learn_features<2><<<nb, kBlock, 0, st>>>(bt, s, x);
+    else k_learn_features<3><<<nb, kBlock, 0, st>>>(bt, s, x);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int launch_learn_candidate(const Batch &bt, const Solid &s, const float *out, int dim, cudaStream_t st)
+{
+    if (s.n == 0) return 0;
+    const int nb = (s.n + kBlock - 1) / kBlock;
+    if (dim == 2) {
+        k_learn_apply<2><<<nb, kBlock, 0, st>>>(bt, s, out);
+        k_learn_stress<2><<<nb, kBlock, 0, st>>>(bt, s);
+        k_learn_residual<2><<<nb, kBlock, 0, st>>>(bt, s);
+        k_learn_commit<2><<<nb, kBlock, 0, st>>>(bt, s);
+    } else {
+        k_learn_apply<3><<<nb, kBlock, 0, st>>>(bt, s, out);
+        k_learn_stress<3><<<nb, kBlock, 0, st>>>(bt, s);
+        k_learn_residual<3><<<nb, kBlock, 0, st>>>(bt, s);
+        k_learn_commit<3><<<nb, kBlock, 0, st>>>(bt, s);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 }  // namespace sph
