@@ -41,7 +41,9 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {"dam_gate": "dam_break_elastic_gate_2d",
-             "flag_batch": "flag_channel_batch_256_2d"}
+             "flag_batch": "flag_channel_batch_256_2d",
+             "duct_3d": "duct_flexible_plate_3d",
+             "flag_learned": "flag_channel_learned_substepper_2d"}
 METRIC = "pair_interactions_per_s"
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -52,6 +54,19 @@ FLOP_PER_PAIR = {"momentum": 55.0, "continuity": 30.0, "solid_fluid_force": 60.0
 FLOP_SOLID_PAIR = 22.0        # force (12) + deformation rate (10) per static solid pair per sub-step
 FLOP_SOLID_PARTICLE = 80.0    # neo-Hookean stress + Verlet updates per particle per sub-step
 BYTES_PER_FLUID_PARTICLE = {"bin_sort": 90.0, "momentum": 48.0, "continuity": 64.0}
+
+
+def _clean(x):
+    """JSON-safe copy: non-finite floats become null."""
+    if isinstance(x, dict):
+        return {k: _clean(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_clean(v) for v in x]
+    if isinstance(x, (float, np.floating)):
+        return float(x) if np.isfinite(x) else None
+    if isinstance(x, np.integer):
+        return int(x)
+    return x
 
 
 def _peaks():
@@ -146,6 +161,10 @@ def make_cases(workload, seed=0):
     import fsi_cases
     if workload == "flag_batch":
         return fsi_cases.flag_batch(seed=seed, n=256)
+    if workload == "duct_3d":
+        return [fsi_cases.duct_plate_3d(seed=seed, scale=1)]
+    if workload == "flag_learned":
+        return [fsi_cases.channel_flag(seed=seed)]
     return [fsi_cases.dam_gate(seed=seed)]
 
 
@@ -155,11 +174,25 @@ def sample_case(cases):
     return order[len(order) // 2]
 
 
+def cpu_case(cases, label):
+    """(case, words) the oracle steps for the CPU baseline: the workload
+    itself, the median instance of a batch, or for the 3 M-particle duct its
+    copy at four times the spacings (1/64 of the particles)."""
+    if label == WORKLOADS["duct_3d"]:
+        import fsi_cases
+        return fsi_cases.duct_plate_3d(seed=0, scale=2), "the copy at twice the spacings (1/8 of the particles) of "
+    b = sample_case(cases)
+    if len(cases) > 1:
+        return cases[b], f"instance {b} (n_fluid {cases[b].nf}, the median) of "
+    return cases[b], ""
+
+
 def cpu_baseline(cases, label, budget_s=15.0, max_steps=400):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
-    b = sample_case(cases)
-    case = cases[b]
+    case, which = cpu_case(cases, label)
+    if label == WORKLOADS["duct_3d"]:
+        max_steps = min(max_steps, 2)   # ~375k fluid particles in 3-D: each oracle step takes tens of seconds
     ref = oracle.OracleSim(case)
     dt, _, dts = ref.suggest_dt(vmax_f=0.0)
     K = ref.substeps(dt, dts)
@@ -172,7 +205,6 @@ def cpu_baseline(cases, label, budget_s=15.0, max_steps=400):
         pairs += 2 * fl + d["n_sf"] + (fl if reinit else 0) + (2 * K + 1) * d["n_ss"]
         steps += 1
     el = time.perf_counter() - t0
-    which = f"instance {b} (n_fluid {case.nf}, the median) of " if len(cases) > 1 else ""
     return dict(value=pairs / el, unit=UNIT, cores=1, kind="oracle",
                 sample=f"first {steps} coarse steps of {which}the {label} workload (seed 0, dt={dt:.3e} s, "
                        f"K={K}), FP64 C oracle, single thread, {el:.1f} s",
@@ -184,7 +216,7 @@ def run_reference(args, rank):
         return
     label = WORKLOADS[args.workload]
     cases = make_cases(args.workload, 0)
-    case = cases[sample_case(cases)]
+    case, _ = cpu_case(cases, label)
     budget = min(240.0, 0.06 * (args.steps + args.warmup) + 10.0)
     cb = cpu_baseline(cases, label, budget_s=budget, max_steps=max(1, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
@@ -195,7 +227,7 @@ def run_reference(args, rank):
             "sim_s_per_wall_s": cb["sim_s_per_wall_s"],
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    print(json.dumps(_clean(line)))
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -212,7 +244,7 @@ def run_gpu(args, rank, world, local_rank):
     case = cases[0]
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
-    tuning = sim.autotune(0.0, steps=10) if len(cases) > 1 else sim.tuning()
+    tuning = sim.autotune(0.0, steps=10) if args.workload != "dam_gate" else sim.tuning()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sim.set_profiling(True)
     for _ in range(args.warmup):
@@ -311,7 +343,7 @@ def run_gpu(args, rank, world, local_rank):
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
                    "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant")},
-                   "autotuned": len(cases) > 1,
+                   "autotuned": args.workload != "dam_gate",
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
         "sim_s_per_wall_s": simt_all / world / (dev_ms_max * 1e-3),
@@ -323,7 +355,160 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "wall_s_timed_loop": wall1 - wall0,
     }
-    print(json.dumps(line))
+    print(json.dumps(_clean(line)))
+
+
+def run_learned(args, rank, world, local_rank):
+    """Learned sub-stepper on the flag channel: train on plain steps, then
+    time the same window of steps with the plain sub-steps, with the network
+    always accepted, and with the network behind the residual check (plain
+    fallback above tol = 1e-3); report speed, tip error and acceptance."""
+    import torch
+    import paper_1911_13255_gb300 as pkg
+    from paper_1911_13255_gb300 import Simulation, learn
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    label = WORKLOADS["flag_learned"]
+    case = make_cases("flag_learned", seed=rank)[0]
+    d = case.dim
+    cons = np.asarray(case.s_cons)
+    m = case.s_rho0 * case.s_dp ** d
+    st = torch.cuda.Stream(device=dev)
+    n_collect, iters, R = 600, 3000, 32
+    t0 = time.perf_counter()
+    gen = Simulation.from_case(case, stream=st)
+    data = learn.collect(gen, n_collect, case.s_r0)
+    graph = gen.solid_graph()
+    gen.close()
+    t_collect = time.perf_counter() - t0
+    scales = learn.scales_from(data, m, case.gravity, cons)
+    theta, losses = learn.train(graph, d, data, cons, m, case.gravity, scales, iters=iters, replicas=R, lr=1e-3,
+                                stream=st, noise=0.02)
+    t_train = time.perf_counter() - t0 - t_collect
+
+    def start():
+        s = Simulation.from_case(case, stream=st)
+        s.run(n_collect, 0.0)
+        s.sync()
+        return s
+
+    def timed(sim, chunk=10):
+        """Device time of args.steps steps in chunks of `chunk` (graph replay);
+        stops at the first chunk after which the tip is not finite."""
+        sim.run(args.warmup, 0.0)
+        sim.sync()
+        i0 = sim.info()
+        ms, done, diverged = 0.0, 0, None
+        while done < args.steps:
+            n = min(chunk, args.steps - done)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sim.run(n, 0.0)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tip = sim.get_solid()["r"][case.tip]
+            if not np.all(np.isfinite(tip)) or not np.all(np.abs(tip) < 1e3):
+                diverged = done + n
+                break
+            ms += e0.elapsed_time(e1)
+            done += n
+        i1 = sim.info()
+        dt = i1["last_dt"]
+        return dict(ms_per_step=ms / max(done, 1), sim_s_per_wall_s=dt / max(ms / max(done, 1) * 1e-3, 1e-30),
+                    tip=sim.get_solid()["r"][case.tip].copy(), steps_ok=done, diverged_after=diverged,
+                    accepted=i1["learned_accepted"] - i0["learned_accepted"],
+                    rejected=i1["learned_rejected"] - i0["learned_rejected"],
+                    kernels_per_step=i1["kernels_per_step"], last_residual=i1["learned_residual"])
+
+    with ClockSampler(local_rank) as clk:
+        plain = timed(start())
+        pure_sim = start()
+        pure_sim.set_learned(theta, scales, 1e30)
+        pure = timed(pure_sim)
+        fb_sim = start()
+        fb_sim.set_learned(theta, scales, 1e-3)
+        fb = timed(fb_sim)
+    clocks = clk.summary()
+    disp = np.linalg.norm(plain["tip"] - case.s_r0[case.tip])
+
+    def tip_err(x):
+        """Tip distance from the plain run after the full window, relative to
+        the plain tip's displacement (None if the run diverged)."""
+        if x["diverged_after"] is not None:
+            return None
+        return float(np.linalg.norm(x["tip"] - plain["tip"]) / max(disp, 1e-300))
+
+    # tensor-core GEMM at the training batch's layer shape (R bodies x 512 -> 128)
+    peaks, src = _peaks()
+    M_ = ((R * case.ns + 127) // 128) * 128
+    A = torch.randn(M_, 128 * (2 + d), device=dev).to(torch.bfloat16)
+    B = torch.randn(128, 128 * (2 + d), device=dev).to(torch.bfloat16)
+    C = torch.empty(M_, 128, device=dev)
+    for _ in range(3):
+        pkg.gemm_bf16(A, B, out=C, stream=st)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(st)
+    for _ in range(50):
+        pkg.gemm_bf16(A, B, out=C, stream=st)
+    g1.record(st)
+    torch.cuda.synchronize()
+    gemm_ms = g0.elapsed_time(g1) / 50
+    flops = 2.0 * M_ * 128 * 128 * (2 + d)
+    ach = flops / (gemm_ms * 1e-3) / 1e12
+    # e2e: the fallback configuration through the public API, per-step tip readback
+    e2e_sim = start()
+    out = torch.empty((case.ns, d), dtype=torch.float64).pin_memory()
+    th = torch.from_numpy(np.ascontiguousarray(theta)).pin_memory()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e2e_sim.set_learned(th.numpy(), scales, 1e-3)
+    i0 = e2e_sim.info()
+    for _ in range(args.steps):
+        e2e_sim.run(1, 0.0)
+        e2e_sim.get_solid_positions(out)
+    e2e_sim.sync()
+    w1 = time.perf_counter()
+    simt = e2e_sim.info()["t"] - i0["t"]
+    cb = cpu_baseline([case], label) if world == 1 else None
+    if rank != 0:
+        return
+    line = {
+        "metric": "simulated_s_per_wall_s", "value": fb["sim_s_per_wall_s"], "unit": "simulated-s/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": fb["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+        "precision": "network GEMMs bf16 operands / FP32 accumulation; residual, state and plain path as the "
+                     "plain method (FP32 pair loops, FP64 positions and sums)",
+        "data": "synthetic",
+        "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns, "train_steps_collected": n_collect,
+                   "train_iters": iters, "train_batch_bodies": R, "tol": 1e-3,
+                   "window": f"steps {n_collect + args.warmup}..{n_collect + args.warmup + args.steps} after the "
+                             f"training data", "l2": "not flushed (whole working set ~2 MB)"},
+        "plain": {k: plain[k] for k in ("ms_per_step", "sim_s_per_wall_s", "kernels_per_step")},
+        "learned_always_accepted": {"ms_per_step": pure["ms_per_step"], "sim_s_per_wall_s": pure["sim_s_per_wall_s"],
+                                    "speedup_vs_plain": plain["ms_per_step"] / pure["ms_per_step"],
+                                    "tip_displacement_error_rel": tip_err(pure),
+                                    "steps_timed": pure["steps_ok"], "diverged_after_steps": pure["diverged_after"],
+                                    "kernels_per_step": pure["kernels_per_step"]},
+        "learned_with_fallback": {"ms_per_step": fb["ms_per_step"],
+                                  "speedup_vs_plain": plain["ms_per_step"] / fb["ms_per_step"],
+                                  "accepted": fb["accepted"], "rejected": fb["rejected"],
+                                  "last_residual": fb["last_residual"], "tip_displacement_error_rel": tip_err(fb)},
+        "training": {"loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean()),
+                     "collect_s": t_collect, "train_s": t_train},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "k_gemm_bf16",
+                     "shape": [M_, 128, 128 * (2 + d)], "ms_per_launch": gemm_ms,
+                     "peak_source": f"{src} bf16_tflops (burst)"},
+        "cpu_baseline": None if cb is None else {"value": cb["sim_s_per_wall_s"], "unit": "simulated-s/s",
+                                                 "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]},
+        "e2e": {"value": simt / (w1 - w0), "unit": "simulated-s/s", "h2d_bytes_per_step": th.numel() * 4 / args.steps,
+                "d2h_bytes_per_step": out.numel() * 8, "steps": args.steps,
+                "note": "learned with fallback; parameter upload amortised; per-step solid-position readback"},
+        "gpu_launches": int(fb["kernels_per_step"]) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(_clean(line)))
 
 
 def e2e_run(cases, dev, steps, tuning):
@@ -401,7 +586,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_gpu(args, rank, world, local_rank)
+    if args.workload == "flag_learned":
+        run_learned(args, rank, world, local_rank)
+    else:
+        run_gpu(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

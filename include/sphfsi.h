@@ -329,8 +329,8 @@ int sphfsi_solid_graph(sphfsi_ctx *c, int64_t *ptr, int64_t *idx, double *w, dou
 /* Learned sub-stepper (no counterpart in the paper): every later step runs,
  * after the coupling force, the network of sphfsi_mpnn_* (parameters theta)
  * on each body's graph with the features
- *   [u / s_u, v / s_v, F - I (row-major), f^F / s_f, constrained, dt_F / s_t]
- * (u = r - r0; scales = {s_u, s_v, s_f, s_t, s_du, s_dv}) and proposes
+ *   [u / s_u, v / s_v, (F - I) / s_H (row-major), f^F / s_f, constrained, dt_F / s_t]
+ * (u = r - r0; scales = {s_u, s_v, s_f, s_t, s_du, s_dv, s_H}) and proposes
  *   du = dt_F v + s_du out[0:dim],  dv = dt_F (f^F / m + g) + s_dv out[dim:2 dim]
  * (0 for constrained particles).  The proposal of an instance is accepted
  * when its residual

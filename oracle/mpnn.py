@@ -10,7 +10,7 @@ reference-configuration neighbour list the sub-steps use, support 2 h_S),
 and keeps the plain sub-stepping as fallback and judge.  This module states
 that network in plain numpy, FP64, node by node and layer by layer:
 
-  features   x_a = [u_a / s_u, v_a / s_v, H_a, f_a / s_f, c_a, dt / s_t, 0...]
+  features   x_a = [u_a / s_u, v_a / s_v, H_a / s_H, f_a / s_f, c_a, dt / s_t, 0...]
              u = r - r0, H = F - I (row-major), f the fluid force of the step,
              c = 1 for a constrained particle; padded to FIN columns
   encoder    h = silu(x W_enc^T + b_enc)                        (N x 128)
@@ -188,13 +188,13 @@ def aggregate_adjoint(dms, graph):
 # features and outputs
 # ---------------------------------------------------------------------------
 def features(u, v, H, f, cons, dt, scales, dim):
-    """Input matrix (N x FIN); scales = dict(s_u, s_v, s_f, s_t)."""
+    """Input matrix (N x FIN); scales = dict(s_u, s_v, s_H, s_f, s_t)."""
     n = len(u)
     x = np.zeros((n, FIN))
     o = 0
     x[:, o:o + dim] = np.asarray(u) / scales["s_u"]; o += dim
     x[:, o:o + dim] = np.asarray(v) / scales["s_v"]; o += dim
-    x[:, o:o + dim * dim] = np.asarray(H).reshape(n, dim * dim); o += dim * dim
+    x[:, o:o + dim * dim] = np.asarray(H).reshape(n, dim * dim) / scales["s_H"]; o += dim * dim
     x[:, o:o + dim] = np.asarray(f) / scales["s_f"]; o += dim
     x[:, o] = np.asarray(cons, np.float64); o += 1
     x[:, o] = dt / scales["s_t"]

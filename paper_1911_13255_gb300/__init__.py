@@ -307,7 +307,7 @@ class Simulation:
 
     def set_learned(self, theta, scales, tol):
         """Learned sub-stepper with parameters theta and scales
-        (s_u, s_v, s_f, s_t, s_du, s_dv); tol < 0 switches it off."""
+        (s_u, s_v, s_f, s_t, s_du, s_dv, s_H); tol < 0 switches it off."""
         th = np.ascontiguousarray(theta, np.float32)
         sc = np.ascontiguousarray(scales, np.float64)
         _check(lib().sphfsi_set_learned(self.h, _ptr(th), _ptr(sc), float(tol)), "sphfsi_set_learned")

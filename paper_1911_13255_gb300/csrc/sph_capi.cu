@@ -1442,7 +1442,7 @@ int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, 
         return SPHFSI_OK;
     }
     if (!theta || !scales || c->S.n == 0 || std::isnan(tol)) return SPHFSI_E_INVAL;
-    for (int k = 0; k < 6; k++)
+    for (int k = 0; k < 7; k++)
         if (!(scales[k] > 0.0)) return SPHFSI_E_INVAL;
     Solid &S = c->S;
     if (!c->mpnn) {
@@ -1470,6 +1470,7 @@ int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, 
     S.l_st = (float)scales[3];
     S.l_sdu = (float)scales[4];
     S.l_sdv = (float)scales[5];
+    S.l_sH = (float)scales[6];
     S.l_tol = tol > 3.0e38 ? 3.0e38f : (float)tol;
     S.learned = 1;
     return SPHFSI_OK;

@@ -176,7 +176,7 @@ struct Solid {
     // learned sub-stepper (when learned != 0)
     int learned;
     float l_tol;              // residual threshold
-    float l_su, l_sv, l_sf, l_st, l_sdu, l_sdv;   // feature / output scales
+    float l_su, l_sv, l_sf, l_st, l_sdu, l_sdv, l_sH;   // feature / output scales
     double *lx, *ly, *lz;     // candidate end positions
     double *mx, *my, *mz;     // mid positions
     float4 *lv4;              // candidate end velocities

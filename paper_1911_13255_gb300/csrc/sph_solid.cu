@@ -1072,7 +1072,7 @@ __global__ void k_learn_features(Batch bt, Solid s, float *x)
     int o = 0;
     for (int k = 0; k < D; k++) row[o++] = (float)(u[k] / (double)s.l_su);
     for (int k = 0; k < D; k++) row[o++] = vv[k] / s.l_sv;
-    for (int k = 0; k < D * D; k++) row[o++] = s.H[9 * a + k];
+    for (int k = 0; k < D * D; k++) row[o++] = s.H[9 * a + k] / s.l_sH;
     for (int k = 0; k < D; k++) row[o++] = s.fF[3 * a + k] / s.l_sf;
     row[o++] = s.cons[a] ? 1.0f : 0.0f;
     row[o++] = (float)(ctl.dt / (double)s.l_st);

@@ -64,8 +64,8 @@ def collect(sim, steps, r0, dt=0.0):
 
 
 def scales_from(data, m, g, cons):
-    """(s_u, s_v, s_f, s_t, s_du, s_dv): RMS sizes of the free particles'
-    inputs and of the corrections the network has to produce."""
+    """(s_u, s_v, s_f, s_t, s_du, s_dv, s_H): RMS sizes of the free
+    particles' inputs and of the corrections the network has to produce."""
     free = np.asarray(cons) == 0
     dim = data["u"].shape[-1]
     gv = np.asarray(g, np.float64)[:dim]
@@ -76,7 +76,8 @@ def scales_from(data, m, g, cons):
     def rms(a):
         return float(np.sqrt(np.mean(a[:, free] ** 2))) or 1.0
 
-    return np.array([rms(data["u"]), rms(data["v"]), rms(data["f"]), float(np.mean(data["dt"])), rms(ru), rms(rv)])
+    return np.array([rms(data["u"]), rms(data["v"]), rms(data["f"]), float(np.mean(data["dt"])), rms(ru), rms(rv),
+                     rms(data["H"])])
 
 
 def features(data, k, cons, scales):
@@ -87,7 +88,7 @@ def features(data, k, cons, scales):
     o = 0
     x[:, o:o + d] = data["u"][k] / scales[0]; o += d
     x[:, o:o + d] = data["v"][k] / scales[1]; o += d
-    x[:, o:o + d * d] = data["H"][k]; o += d * d
+    x[:, o:o + d * d] = data["H"][k] / scales[6]; o += d * d
     x[:, o:o + d] = data["f"][k] / scales[2]; o += d
     x[:, o] = np.asarray(cons, np.float32); o += 1
     x[:, o] = data["dt"][k] / scales[3]
@@ -106,8 +107,11 @@ def targets(data, k, m, g, scales):
 
 
 def train(graph, dim, data, cons, m, g, scales, iters=2000, replicas=32, lr=1e-3, seed=0, theta=None,
-          stream=None, log_every=0):
-    """Fit the network to the recorded steps; returns (theta, losses)."""
+          stream=None, log_every=0, noise=0.0):
+    """Fit the network to the recorded steps; returns (theta, losses).
+    noise > 0 adds Gaussian noise of that standard deviation to the
+    normalised state inputs (u, v, F - I) of every batch, so that the network
+    also sees states slightly off the recorded trajectories."""
     rng = np.random.default_rng(seed)
     nsteps = data["u"].shape[0]
     R = min(replicas, nsteps)
@@ -119,8 +123,13 @@ def train(graph, dim, data, cons, m, g, scales, iters=2000, replicas=32, lr=1e-3
     losses = []
     for it in range(iters):
         ks = rng.choice(nsteps, size=R, replace=False)
+        xb = X[ks].reshape(-1, FIN)
+        if noise > 0.0:
+            xb = xb.copy()
+            ns = 2 * dim + dim * dim
+            xb[:, :ns] += rng.normal(scale=noise, size=(xb.shape[0], ns)).astype(np.float32)
         lr_it = lr * 0.5 * (1.0 + math.cos(math.pi * it / iters))   # cosine decay
-        L = net.train_step(X[ks].reshape(-1, FIN), T[ks].reshape(-1, NOUT), mask, lr=max(lr_it, 1e-6))
+        L = net.train_step(xb, T[ks].reshape(-1, NOUT), mask, lr=max(lr_it, 1e-6))
         losses.append(L)
         if log_every and it % log_every == 0:
             print(f"iter {it} loss {L:.3e}", flush=True)

@@ -18,11 +18,12 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_1911_13255_gb300 import Simulation, learn  # noqa: E402
 
-SCALES = np.array([1e-4, 1e-2, 1e-5, 5e-4, 1e-6, 1e-4])
+SCALES = np.array([1e-4, 1e-2, 1e-5, 5e-4, 1e-6, 1e-4, 1e-3])
 
 
 def _sc():
-    return dict(s_u=SCALES[0], s_v=SCALES[1], s_f=SCALES[2], s_t=SCALES[3], s_du=SCALES[4], s_dv=SCALES[5])
+    return dict(s_u=SCALES[0], s_v=SCALES[1], s_f=SCALES[2], s_t=SCALES[3], s_du=SCALES[4], s_dv=SCALES[5],
+                s_H=SCALES[6])
 
 
 def rel(a, b):

@@ -125,7 +125,7 @@ def test_adam_first_step_closed_form():
 def test_outputs_and_targets_are_inverse():
     rng = np.random.default_rng(8)
     dim, n = 2, 30
-    sc = dict(s_u=1e-3, s_v=1e-2, s_f=1e-4, s_t=1e-3, s_du=1e-6, s_dv=1e-4)
+    sc = dict(s_u=1e-3, s_v=1e-2, s_f=1e-4, s_t=1e-3, s_du=1e-6, s_dv=1e-4, s_H=1e-3)
     v, f = rng.normal(size=(n, dim)), rng.normal(size=(n, dim))
     cons = (rng.uniform(size=n) < 0.3).astype(np.uint8)
     du, dv = rng.normal(size=(n, dim)), rng.normal(size=(n, dim))
