@@ -244,7 +244,12 @@ def run_gpu(args, rank, world, local_rank):
     case = cases[0]
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
-    tuning = sim.autotune(0.0, steps=10) if args.workload != "dam_gate" else sim.tuning()
+    if args.tuning:
+        vals = [int(x) for x in args.tuning.split(",")]
+        sim.set_tuning(*vals)
+        tuning = sim.tuning()
+    else:
+        tuning = sim.autotune(0.0, steps=10) if args.workload != "dam_gate" else sim.tuning()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sim.set_profiling(True)
     for _ in range(args.warmup):
@@ -342,8 +347,8 @@ def run_gpu(args, rank, world, local_rank):
                    "dp_F": case.f_dp, "dp_S": case.s_dp,
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
-                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant")},
-                   "autotuned": args.workload != "dam_gate",
+                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact")},
+                   "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
         "sim_s_per_wall_s": simt_all / world / (dev_ms_max * 1e-3),
@@ -551,7 +556,7 @@ def e2e_run(cases, dev, steps, tuning):
         if c.inflow_on:
             sim.set_inflow(1, c.inflow_profile, c.inflow_width, c.inflow_y0, c.inflow_H, c.inflow_U, c.inflow_tramp)
     sim.finalize()
-    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"])
+    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"])
     p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)
@@ -573,6 +578,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_gate", choices=sorted(WORKLOADS))
+    ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact]: fixed launch shape instead "
+                                                 "of the autotuner (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -255,6 +255,10 @@ typedef struct {
     int32_t solid_variant; /* 0: automatic cluster kernel choice; 1: the four-lane
                               cluster kernel (sphfsi_set_solid_path 1) */
     float step_ms;         /* sphfsi_autotune: device ms per step measured for this setting */
+    int32_t compact;       /* fluid-fluid pair loops: 0 evaluate each pair inside the
+                              candidate loop; 1 first collect each thread's in-support
+                              neighbours in shared memory, then evaluate them densely
+                              (default 1 in 2-D, 0 in 3-D) */
 } sphfsi_tuning;
 
 /* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */
@@ -264,8 +268,9 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t);
 /* Autotuner (no counterpart in the paper).  Times the context's own
  * workload: for each candidate setting, `steps` graph-replayed steps of size
  * dt_F (as sphfsi_run) to warm up, then `steps` timed with CUDA events.  The
- * search goes over the lane count (block 128), then the block size, then
- * (2-D with a solid) the solid kernel variant, keeping the fastest of each.
+ * search goes over the lane count (block 128), then the pair-loop form,
+ * then the block size, then (2-D with a solid) the solid kernel variant,
+ * keeping the fastest of each.
  * Every device allocation of the context is saved before and restored after
  * each trial and at the end, so the simulation state, time and counters are
  * exactly as before the call; the best setting stays selected and is

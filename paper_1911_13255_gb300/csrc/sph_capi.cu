@@ -212,7 +212,7 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_finish(c->bt, c->S.learned, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
-    c->kernels_per_step = 10 + (c->S.n ? 2 : 0) + (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
+    c->kernels_per_step = 11 + (c->S.n ? 2 : 0) + (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -333,6 +333,71 @@ int make_inst(const InstHost &h, int D, Inst &d)
     P.in_U = h.inflow.U;
     P.in_tramp = h.inflow.t_ramp;
     return SPHFSI_OK;
+}
+
+// Static reference neighbour list of every body (slots in device order,
+// global): pairs a != b of one instance with |r0_a - r0_b|^2 < (2 h_S)^2 in
+// FP64, computed as dx dx + dy dy (+ dz dz) without contraction, found
+// through a cell grid of edge 2 h_S over the body; each row ascending.
+void body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx)
+{
+    const int D = c->dim;
+    ptr.assign(1, 0);
+    idx.clear();
+    for (const InstHost &h : c->ih) {
+        const int n = (int)h.ns, s0 = h.d.s0;
+        if (n == 0) continue;
+        const double hS = 1.3 * h.s_dp, rc2 = 4.0 * hS * hS, edge = 2.0 * hS;
+        double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int k = 0; k < D; k++) {
+            lo[k] = hi[k] = h.s_r0[k];
+            for (int a = 0; a < n; a++) {
+                lo[k] = std::min(lo[k], h.s_r0[(size_t)a * D + k]);
+                hi[k] = std::max(hi[k], h.s_r0[(size_t)a * D + k]);
+            }
+        }
+        int nc[3] = {1, 1, 1};
+        for (int k = 0; k < D; k++) nc[k] = (int)std::floor((hi[k] - lo[k]) / edge) + 1;
+        auto cell = [&](int a, int k) {
+            int q = (int)std::floor((h.s_r0[(size_t)a * D + k] - lo[k]) / edge);
+            return q < 0 ? 0 : (q >= nc[k] ? nc[k] - 1 : q);
+        };
+        const size_t ncl = (size_t)nc[0] * nc[1] * nc[2];
+        std::vector<int> start(ncl + 1, 0), items(n), cid(n);
+        for (int a = 0; a < n; a++) {
+            cid[a] = cell(a, 0) + nc[0] * (cell(a, 1) + nc[1] * (D == 3 ? cell(a, 2) : 0));
+            start[cid[a] + 1]++;
+        }
+        for (size_t q = 0; q < ncl; q++) start[q + 1] += start[q];
+        {
+            std::vector<int> cur(start.begin(), start.end() - 1);
+            for (int a = 0; a < n; a++) items[cur[cid[a]]++] = a;
+        }
+        std::vector<int> row;
+        for (int a = 0; a < n; a++) {
+            row.clear();
+            const int cx = cell(a, 0), cy = cell(a, 1), cz = D == 3 ? cell(a, 2) : 0;
+            for (int z = std::max(cz - 1, 0); z <= std::min(cz + 1, nc[2] - 1); z++)
+                for (int y = std::max(cy - 1, 0); y <= std::min(cy + 1, nc[1] - 1); y++)
+                    for (int x = std::max(cx - 1, 0); x <= std::min(cx + 1, nc[0] - 1); x++) {
+                        const int q = x + nc[0] * (y + nc[1] * z);
+                        for (int t = start[q]; t < start[q + 1]; t++) {
+                            const int b = items[t];
+                            if (b == a) continue;
+                            double r2 = 0.0;
+                            for (int k = 0; k < D; k++) {
+                                const double d = h.s_r0[(size_t)a * D + k] - h.s_r0[(size_t)b * D + k];
+                                const double dd = d * d;
+                                r2 = r2 + dd;
+                            }
+                            if (r2 < rc2) row.push_back(s0 + b);
+                        }
+                    }
+            std::sort(row.begin(), row.end());
+            idx.insert(idx.end(), row.begin(), row.end());
+            ptr.push_back((int)idx.size());
+        }
+    }
 }
 
 // Locality order of a body on the device: lexicographic on the lattice index
@@ -522,6 +587,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
     F.n = (int)nf;
     F.lanes = D == 2 ? 4 : 8;
     F.block = 128;
+    F.compact = D == 2 ? 1 : 0;
     for (int k = 0; k < 2; k++) {
         FluidState &S = F.s[k];
         TRY(dalloc(c, &S.x, nf));
@@ -546,6 +612,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &F.cell_of, nf));
     TRY(dalloc(c, &F.cstart, (size_t)ncell + 1));
     TRY(dalloc(c, &F.ccount, ncell));
+    TRY(dalloc(c, &F.big, 2 * (size_t)ncell));
+    TRY(dalloc(c, &F.nbig, 1));
     // ---- walls
     Walls &W = c->W;
     W.n = (int)nw;
@@ -722,18 +790,14 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // ---- walls binned once; solid static neighbour list and B0
     TRY(launch_wall_bin(c->bt, W, D, c->st));
     if (ns > 0) {
-        int *counts = nullptr;
-        TRY(dalloc(c, &counts, ns));
-        TRY(launch_solid_setup_count(c->bt, S, D, counts, c->st));
-        std::vector<int> hc;
-        TRY(download(c, hc, counts, ns));
-        std::vector<int> ptr(ns + 1, 0);
+        std::vector<int> ptr, nbi;
+        body_neighbours(c, ptr, nbi);
         S.max_nb = 0;
-        for (int64_t a = 0; a < ns; a++) {
-            ptr[a + 1] = ptr[a] + hc[a];
-            S.max_nb = std::max(S.max_nb, hc[a]);
-        }
+        for (int64_t a = 0; a < ns; a++) S.max_nb = std::max(S.max_nb, ptr[a + 1] - ptr[a]);
         S.nnz = ptr[ns];
+        int *d_nbi = nullptr;
+        TRY(dalloc(c, &d_nbi, nbi.size()));
+        TRY(upload(c, d_nbi, nbi));
         std::vector<Inst> hinst(B);
         for (int b = 0; b < B; b++) {
             InstHost &h = c->ih[b];
@@ -743,7 +807,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
         TRY(upload(c, S.nb_ptr, ptr));
         TRY(upload(c, c->d_inst, hinst));
         TRY(dalloc(c, &S.nb, S.nnz));
-        TRY(launch_solid_setup_fill(c->bt, S, D, c->st));
+        TRY(launch_solid_setup_fill(c->bt, S, d_nbi, D, c->st));
     }
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     for (int k = 0; k < sphfsi_ctx::kEvents; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
@@ -1237,10 +1301,11 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 1)
+        t->solid_variant < 0 || t->solid_variant > 1 || t->compact < 0 || t->compact > 1)
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
+    c->F.compact = t->compact;
     c->S.force_lane_path = t->solid_variant;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -1256,6 +1321,7 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
     t->lanes = c->F.lanes;
     t->block = c->F.block;
     t->solid_variant = c->S.force_lane_path;
+    t->compact = c->F.compact;
     t->step_ms = 0.0f;
     return SPHFSI_OK;
 }
@@ -1324,6 +1390,11 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         for (int k = 0; k < 3 && !rc; k++) {
             cur.lanes = c->dim == 2 ? lanes2[k] : lanes3[k];
             cur.block = 128;
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc) {
+            cur.compact = 1 - cur.compact;
             rc = consider(cur);
         }
         cur = *best;

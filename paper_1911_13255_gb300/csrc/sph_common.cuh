@@ -115,6 +115,7 @@ struct Fluid {
     int n;            // total over the instances
     int lanes;        // threads per target particle of the pair loops (tuned)
     int block;        // threads per block of the pair loops (tuned)
+    int compact;      // 1: fluid-fluid pairs through per-thread in-support lists (tuned)
     int *inst;        // instance of each slot
     FluidState s[2];
     float4 *P4;       // (x - x_cell, y - y_cell, z - z_cell, p)   sorted records
@@ -127,6 +128,7 @@ struct Fluid {
     int *cell_of;     // global cell of each sorted slot
     int *cstart;      // total cells + 1
     int *ccount;      // total cells (histogram / scatter cursor)
+    int *big, *nbig;  // cells (fluid, then solid) with more than 32 entries, for the block sort
 };
 
 // Static walls, binned once.
@@ -277,8 +279,8 @@ int launch_debug_pairs(const Batch &bt, const Fluid &f, const Walls &w, const So
                        int which, int *counts, int *offs, int *out, cudaStream_t st);
 
 // solid (sph_solid.cu)
-int launch_solid_setup_count(const Batch &bt, Solid &s, int dim, int *counts, cudaStream_t st);
-int launch_solid_setup_fill(const Batch &bt, Solid &s, int dim, cudaStream_t st);
+// nbi: the static neighbour list's global slots (host-built, rows ascending)
+int launch_solid_setup_fill(const Batch &bt, Solid &s, const int *nbi, int dim, cudaStream_t st);
 // P0: host copy of instance 0's constants (used when the batch holds one instance)
 int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, int *path, cudaStream_t st);
 // learned sub-stepper: features into x (n x 64), then, from the network's

@@ -36,8 +36,9 @@ static bool with_lanes(int L, Fn &&fn)
     return true;
 }
 
-// Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz)
-// receives the offset o = -(dcell) * edge to add to (rel_i - rel_j).
+// Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz, code)
+// receives the offset o = -(dcell) * edge to add to (rel_i - rel_j) and
+// code = (dx + 1) + 3 (dy + 1) + 9 (dz + 1) (cell_offset recovers o from it).
 template <int D, typename Fn>
 __device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int cy, int cz, Fn &&fn)
 {
@@ -58,9 +59,98 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int
                     x = x < 0 ? x + g.nc[0] : x - g.nc[0];
                 }
                 int c = c0 + x + g.nc[0] * (y + g.nc[1] * z);
-                fn(c, -(float)dx * g.csf[0], -(float)dy * g.csf[1], -(float)dz * g.csf[2]);
+                fn(c, -(float)dx * g.csf[0], -(float)dy * g.csf[1], -(float)dz * g.csf[2],
+                   (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
             }
         }
+    }
+}
+
+__device__ __forceinline__ void cell_offset(int code, const Grid &g, float &ox, float &oy, float &oz)
+{
+    const int dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
+    ox = -(float)dx * g.csf[0];
+    oy = -(float)dy * g.csf[1];
+    oz = -(float)dz * g.csf[2];
+}
+
+template <int D>
+__device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float ox, float oy, float oz, float d[3])
+{
+    d[0] = (Pi.x - Pj.x) + ox;
+    d[1] = (Pi.y - Pj.y) + oy;
+    d[2] = D == 3 ? (Pi.z - Pj.z) + oz : 0.0f;
+    return d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
+}
+
+// Fluid-fluid pairs of target i (this lane's share of the candidates), in
+// one of two forms chosen by the launch shape (Fluid::compact):
+//
+// direct (CP = false): pair(j, Pj, Xj, d, r2, ox, oy, oz) is evaluated inside
+// the candidate loop, Xj = fetch(j) being the neighbour's second record.
+//
+// compacted (CP = true): the candidate test passes only 1/3 (2-D) to 1/6
+// (3-D) of the candidates, so evaluating inside the loop runs the pair
+// arithmetic in almost every warp iteration with few lanes active.  Each
+// thread first writes its in-support neighbours (j << 5 | cell-offset code)
+// into its own list in shared memory (slot k at list[k * stride]), then
+// evaluates the list with all lanes busy; a full list is drained early.
+// Requires j < 2^27.
+//
+// Both return the number of in-support pairs and visit the pairs of a
+// target in the same order.
+constexpr int kPairCap = 32;
+
+template <int D, int L, bool CP, typename Fetch, typename Pair>
+__device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz, int i,
+                                                int lane, const float4 &Pi, float rc2, uint32_t *list, int stride,
+                                                Fetch &&fetch, Pair &&pair)
+{
+    unsigned cnt_total = 0;
+    if constexpr (!CP) {
+        for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
+                if (j == i) continue;
+                const float4 Pj = f.P4[j];
+                float d[3];
+                const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+                if (r2 >= rc2) continue;
+                cnt_total++;
+                pair(j, Pj, fetch(j), d, r2, ox, oy, oz);
+            }
+        });
+        return cnt_total;
+    } else {
+        int cnt = 0;
+        auto drain = [&]() {
+#pragma unroll 1
+            for (int k = 0; k < cnt; k++) {
+                const uint32_t e = list[k * stride];
+                const int j = (int)(e >> 5);
+                float ox, oy, oz;
+                cell_offset((int)(e & 31u), g, ox, oy, oz);
+                const float4 Pj = f.P4[j];
+                float d[3];
+                const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+                pair(j, Pj, fetch(j), d, r2, ox, oy, oz);
+            }
+            cnt = 0;
+        };
+        for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+            const int j1 = f.cstart[c + 1];
+            for (int j = f.cstart[c] + lane; j < j1; j += L) {
+                if (j == i) continue;
+                float d[3];
+                if (rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) >= rc2) continue;
+                list[cnt * stride] = ((uint32_t)j << 5) | (uint32_t)code;
+                cnt++;
+                cnt_total++;
+                if (cnt == kPairCap) drain();
+            }
+        });
+        drain();
+        return cnt_total;
     }
 }
 
@@ -165,14 +255,6 @@ __device__ __forceinline__ float fs_pair_drho(const float d[3], float r2, const 
     return Va * (-dW) * diff;   // times 2 rho_i by the caller
 }
 
-template <int D>
-__device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float ox, float oy, float oz, float d[3])
-{
-    d[0] = (Pi.x - Pj.x) + ox;
-    d[1] = (Pi.y - Pj.y) + oy;
-    d[2] = D == 3 ? (Pi.z - Pj.z) + oz : 0.0f;
-    return d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-}
 
 // Add per-thread counters to the thread's instance control block: one
 // atomic per warp when the warp's lanes share an instance, else per lane.
@@ -228,15 +310,38 @@ static inline int grid_blocks(int n, int L, int block)
 }
 
 // launch KERN<dim, L> over n targets with the lane count and block size of f
-#define SPH_LAUNCH_LANES(KERN, n, ...)                                                        \
+// and SMEM bytes of dynamic shared memory per thread
+#define SPH_LAUNCH_LANES(KERN, n, SMEM, ...)                                                  \
     do {                                                                                      \
+        const size_t sm_ = (size_t)(SMEM) * f.block;                                         \
         const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
             constexpr int L_ = decltype(Lc)::value;                                           \
-            KERN<2, L_><<<grid_blocks(n, L_, f.block), f.block, 0, st>>>(__VA_ARGS__);        \
+            KERN<2, L_><<<grid_blocks(n, L_, f.block), f.block, sm_, st>>>(__VA_ARGS__);      \
         })                                                                                    \
                                   : with_lanes<3>(f.lanes, [&](auto Lc) {                     \
             constexpr int L_ = decltype(Lc)::value;                                           \
-            KERN<3, L_><<<grid_blocks(n, L_, f.block), f.block, 0, st>>>(__VA_ARGS__);        \
+            KERN<3, L_><<<grid_blocks(n, L_, f.block), f.block, sm_, st>>>(__VA_ARGS__);      \
+        });                                                                                   \
+        if (!ok_ || f.block < 32 || f.block > kMaxBlock || f.block % 32) return -1;           \
+    } while (0)
+
+constexpr int kListBytes = kPairCap * 4;   // per-thread in-support list (fluid_pairs)
+
+// the same for the pair-loop kernels templated on the form (f.compact)
+#define SPH_LAUNCH_PAIRS(KERN, n, ...)                                                        \
+    do {                                                                                      \
+        const size_t sm_ = f.compact ? (size_t)kListBytes * f.block : 0;                      \
+        auto go_ = [&](auto Dc, auto Lc) {                                                    \
+            constexpr int D_ = decltype(Dc)::value, L_ = decltype(Lc)::value;                \
+            const int nb_ = grid_blocks(n, L_, f.block);                                      \
+            if (f.compact) KERN<D_, L_, true><<<nb_, f.block, sm_, st>>>(__VA_ARGS__);        \
+            else KERN<D_, L_, false><<<nb_, f.block, 0, st>>>(__VA_ARGS__);                   \
+        };                                                                                    \
+        const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
+            go_(std::integral_constant<int, 2>{}, Lc);                                        \
+        })                                                                                    \
+                                  : with_lanes<3>(f.lanes, [&](auto Lc) {                     \
+            go_(std::integral_constant<int, 3>{}, Lc);                                        \
         });                                                                                   \
         if (!ok_ || f.block < 32 || f.block > kMaxBlock || f.block % 32) return -1;           \
     } while (0)
@@ -244,9 +349,12 @@ static inline int grid_blocks(int n, int L, int block)
 // ---------------------------------------------------------------------------
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
-template <int D, int L>
+template <int D, int L, bool CP>
 __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
 {
+    extern __shared__ uint32_t s_pair_list[];
+    uint32_t *const list = s_pair_list + threadIdx.x;
+    const int stride = blockDim.x;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
@@ -265,17 +373,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float c0 = P.c0, eta2 = 2.0f * P.eta;
-        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
-            // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
-            const int j1 = f.cstart[c + 1];
-            for (int j = f.cstart[c] + lane; j < j1; j += L) {
-                if (j == i) continue;
-                const float4 Pj = f.P4[j];
-                float d[3];
-                float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
-                if (r2 >= P.rc2F) continue;
-                nff++;
-                const float4 Vj = f.V4[j];
+        // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
+        nff = fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride,
+                                [&](int j) { return f.V4[j]; },
+                                [&](int, const float4 &Pj, const float4 &Vj, const float *d, float r2, float, float,
+                                    float) {
                 const float rhoj = P.rho0 + Vj.w;
                 float r = sqrtf(r2), invr = 1.0f / r;
                 float dW = dW_F(r, P);
@@ -289,7 +391,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
                 acc[0] += sc * (-2.0f * Ps * d[0] + eta2 * (vi[0] - Vj.x));
                 acc[1] += sc * (-2.0f * Ps * d[1] + eta2 * (vi[1] - Vj.y));
                 if (D == 3) acc[2] += sc * (-2.0f * Ps * d[2] + eta2 * (vi[2] - Vj.z));
-            }
+            });
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             // walls: v~ = a~ = 0
             const int a1 = w.cstart[c + 1];
             for (int a = w.cstart[c] + lane; a < a1; a += L) {
@@ -348,7 +451,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
 int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    SPH_LAUNCH_LANES(k_momentum, f.n, bt, f, w, s);
+    if (f.n >= (1 << 27)) return -7;
+    SPH_LAUNCH_PAIRS(k_momentum, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -357,7 +461,7 @@ int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid
 // the same pair expression and inputs as a4 (fluid at r^{n+1/2}, v^n)
 // ---------------------------------------------------------------------------
 template <int D, int L>
-__global__ void __launch_bounds__(kMaxBlock) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
+__global__ void __launch_bounds__(kMaxBlock, 2) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t / L, lane = t % L;
@@ -373,7 +477,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_solid_fluid_force(Batch bt, Fluid
         const float4 A = s.A4[k], VB = s.VB4[k], AB = s.AB4[k], N = s.N4[k];
         int cx, cy, cz;
         cell_xyz(s.cell_of[k], In, cx, cy, cz);
-        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 const float4 Pj = f.P4[j];
@@ -409,7 +513,7 @@ int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, in
         if (s.n) cudaMemsetAsync(s.fF, 0, sizeof(float) * 3 * s.n, st);
         return cudaGetLastError() == cudaSuccess ? 0 : -3;
     }
-    SPH_LAUNCH_LANES(k_solid_fluid_force, s.n, bt, f, s);
+    SPH_LAUNCH_LANES(k_solid_fluid_force, s.n, 0, bt, f, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -417,9 +521,12 @@ int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, in
 // a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}) + second half drift;
 // writes the end-of-step state to s[0] in cell order
 // ---------------------------------------------------------------------------
-template <int D, int L>
+template <int D, int L, bool CP>
 __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
 {
+    extern __shared__ uint32_t s_pair_list[];
+    uint32_t *const list = s_pair_list + threadIdx.x;
+    const int stride = blockDim.x;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const bool act = i < f.n;
@@ -437,15 +544,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float inv2c0 = 0.5f / P.c0;
-        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
-            const int j1 = f.cstart[c + 1];
-            for (int j = f.cstart[c] + lane; j < j1; j += L) {
-                if (j == i) continue;
-                const float4 Pj = f.P4[j];
-                float d[3];
-                float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
-                if (r2 >= P.rc2F) continue;
-                const float4 Wj = f.W4[j];
+        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride,
+                          [&](int j) { return f.W4[j]; },
+                          [&](int, const float4 &, const float4 &Wj, const float *d, float r2, float, float, float) {
                 const float rhoj = P.rho0 + Wj.w;
                 float r = sqrtf(r2), invr = 1.0f / r;
                 float dW = dW_F(r, P);
@@ -455,7 +556,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
                 // (v_i - v~_ij).grad_i W = -dW (U_L - U*), U* = (U_L + U_R)/2 + (p_i - p_j) / (2 rho c0)
                 float diff = 0.5f * (UL - UR) - eos_dp(drhoi, Wj.w, P) * inv2c0 / rb;
                 rate += (P.mF / rhoj) * (-dW) * diff;
-            }
+            });
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             const int a1 = w.cstart[c + 1];
             for (int a = w.cstart[c] + lane; a < a1; a += L) {
@@ -505,7 +607,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
 int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    SPH_LAUNCH_LANES(k_density, f.n, bt, f, w, s);
+    if (f.n >= (1 << 27)) return -7;
+    SPH_LAUNCH_PAIRS(k_density, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -601,9 +704,12 @@ __device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, con
     return ff_mul(ff_sqr(a2), bq);
 }
 
-template <int D, int L>
+template <int D, int L, bool CP>
 __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
 {
+    extern __shared__ uint32_t s_pair_list[];
+    uint32_t *const list = s_pair_list + threadIdx.x;
+    const int stride = blockDim.x;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / L, lane = t % L;
     const int b = i < f.n ? f.inst[i] : 0;
@@ -618,15 +724,14 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
         const float4 Pi = f.P4[i], Li = f.L4[i];
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
-        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz) {
-            const int j1 = f.cstart[c + 1];
-            for (int j = f.cstart[c] + lane; j < j1; j += L) {
-                if (j == i) continue;
-                float d[3];
-                const float4 Pj = f.P4[j];
-                if (rel_d<D>(Pi, Pj, ox, oy, oz, d) >= screen) continue;
-                sF = ff_add(sF, W_ff_shape<D>(Pi, Li, Pj, f.L4[j], ox, oy, oz, g, P));
-            }
+        // the screen passes pairs up to 1.0001 (2 h)^2; W_ff_shape returns 0 beyond the support
+        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, screen, list, stride,
+                          [&](int j) { return f.L4[j]; },
+                          [&](int, const float4 &Pj, const float4 &Lj, const float *, float, float ox, float oy,
+                              float oz) {
+                sF = ff_add(sF, W_ff_shape<D>(Pi, Li, Pj, Lj, ox, oy, oz, g, P));
+            });
+        for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             const int a1 = w.cstart[c + 1];
             for (int q = w.cstart[c] + lane; q < a1; q += L) {
                 float d[3];
@@ -661,7 +766,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
 int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    SPH_LAUNCH_LANES(k_reinit, f.n, bt, f, w, s);
+    if (f.n >= (1 << 27)) return -7;
+    SPH_LAUNCH_PAIRS(k_reinit, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -710,7 +816,7 @@ __global__ void k_debug_pairs(Batch bt, Fluid f, Walls w, Solid s, int inst, int
     cell_xyz(key, In, cx, cy, cz);
     int cnt = 0;
     int base = out ? offs[row] : 0;
-    for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float, float, float) {
+    for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float, float, float, int) {
         int j0, j1;
         if (which == 0 || which == 3) {
             j0 = f.cstart[c];

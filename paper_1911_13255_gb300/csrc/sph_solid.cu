@@ -1,8 +1,9 @@
 // Total-Lagrangian elastic solid at h_S (Sections 2.2, 3.1, 3.3).
 //
-// Set-up (once): the static reference neighbour list (the solid keeps its
-// reference configuration's neighbours), the corrected reference kernel
-// gradients V0 grad0_a W_ab and the correction matrices
+// Set-up (once): from the static reference neighbour list (the solid keeps
+// its reference configuration's neighbours; built on the host through a cell
+// grid), the reference kernel gradients V0 grad0_a W_ab and the correction
+// matrices
 // B0_a = (sum_b V_b (r0_b - r0_a) (x) grad0_a W_ab)^-1 (Eq. correctmatrix with
 // the neighbour volume, reading R8), all in FP64 then rounded to FP32.
 //
@@ -41,25 +42,7 @@ __device__ __forceinline__ double r2_d(double dx, double dy, double dz, int D)
 }
 
 template <int D>
-__global__ void k_solid_count(Batch bt, Solid s, int *counts)
-{
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= s.n) return;
-    const Inst &In = bt.I[s.inst[a]];
-    const Phys &P = In.P;
-    double rc2 = 4.0 * P.hS_d * P.hS_d;
-    double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
-    int c = 0;
-    for (int b = In.s0; b < In.s0 + In.ns; b++) {
-        if (b == a) continue;
-        double dz = D == 3 ? za - s.z0[b] : 0.0;
-        if (r2_d(xa - s.x0[b], ya - s.y0[b], dz, D) < rc2) c++;
-    }
-    counts[a] = c;
-}
-
-template <int D>
-__global__ void k_solid_fill(Batch bt, Solid s)
+__global__ void k_solid_fill(Batch bt, Solid s, const int *__restrict__ nbi)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= s.n) return;
@@ -70,18 +53,17 @@ __global__ void k_solid_fill(Batch bt, Solid s)
     const double V0 = P.VS;
     double xa = s.x0[a], ya = s.y0[a], za = D == 3 ? s.z0[a] : 0.0;
     double M[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    int q = s.nb_ptr[a];
-    for (int b = In.s0; b < In.s0 + In.ns; b++) {
-        if (b == a) continue;
+    (void)rc2;
+    for (int q = s.nb_ptr[a]; q < s.nb_ptr[a + 1]; q++) {
+        const int b = nbi[q];
         double d[3] = {xa - s.x0[b], ya - s.y0[b], D == 3 ? za - s.z0[b] : 0.0};
         double r2 = r2_d(d[0], d[1], d[2], D);
-        if (!(r2 < rc2)) continue;
         double r = sqrt(r2);
         double dW = dW_solid_d(r, h, D);
         double g[3] = {dW * d[0] / r, dW * d[1] / r, D == 3 ? dW * d[2] / r : 0.0};   // grad0_a W_ab
         for (int i = 0; i < D; i++)
             for (int j = 0; j < D; j++) M[i * D + j] += V0 * (-d[i]) * g[j];          // (r0_b - r0_a) (x) grad
-        s.nb[q++] = make_float4((float)(V0 * g[0]), (float)(V0 * g[1]), (float)(V0 * g[2]), __int_as_float(b));
+        s.nb[q] = make_float4((float)(V0 * g[0]), (float)(V0 * g[1]), (float)(V0 * g[2]), __int_as_float(b));
     }
     double Bi[9];
     if (D == 2) {
@@ -110,21 +92,12 @@ __global__ void k_solid_fill(Batch bt, Solid s)
     }
 }
 
-int launch_solid_setup_count(const Batch &bt, Solid &s, int dim, int *counts, cudaStream_t st)
+int launch_solid_setup_fill(const Batch &bt, Solid &s, const int *nbi, int dim, cudaStream_t st)
 {
     if (s.n == 0) return 0;
     int nb = (s.n + kBlock - 1) / kBlock;
-    if (dim == 2) k_solid_count<2><<<nb, kBlock, 0, st>>>(bt, s, counts);
-    else k_solid_count<3><<<nb, kBlock, 0, st>>>(bt, s, counts);
-    return cudaGetLastError() == cudaSuccess ? 0 : -3;
-}
-
-int launch_solid_setup_fill(const Batch &bt, Solid &s, int dim, cudaStream_t st)
-{
-    if (s.n == 0) return 0;
-    int nb = (s.n + kBlock - 1) / kBlock;
-    if (dim == 2) k_solid_fill<2><<<nb, kBlock, 0, st>>>(bt, s);
-    else k_solid_fill<3><<<nb, kBlock, 0, st>>>(bt, s);
+    if (dim == 2) k_solid_fill<2><<<nb, kBlock, 0, st>>>(bt, s, nbi);
+    else k_solid_fill<3><<<nb, kBlock, 0, st>>>(bt, s, nbi);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

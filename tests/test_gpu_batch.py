@@ -141,16 +141,20 @@ def test_batch_rejects_bad_selection_and_grid_path():
     batch.close()
 
 
-@pytest.mark.parametrize("lanes,block", [(2, 64), (4, 128), (8, 256)])
-def test_every_launch_shape_matches_the_oracle(lanes, block):
-    """Each compiled lane count / block size computes the same step."""
-    case = fc.channel_flag(seed=0)
+@pytest.mark.parametrize("name,lanes,block,compact", [("channel_flag", 2, 64, 1), ("channel_flag", 4, 128, 0),
+                                                     ("channel_flag", 8, 256, 1), ("channel_flag", 8, 128, 0),
+                                                     ("tiny_box_3d", 4, 128, 0), ("tiny_box_3d", 16, 256, 1),
+                                                     ("tiny_box_3d", 8, 64, 1)])
+def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact):
+    """Each compiled lane count, block size and pair-loop form computes the same step."""
+    case = fc.channel_flag(seed=0) if name == "channel_flag" else fc.tiny_box_3d(seed=1)
     ref = O.OracleSim(case)
     dt, _, dts = ref.suggest_dt()
     K = ref.substeps(dt, dts)
     sim = Simulation.from_case(case)
-    sim.set_tuning(lanes, block)
-    assert sim.tuning()["lanes"] == lanes and sim.tuning()["block"] == block
+    sim.set_tuning(lanes, block, 0, compact)
+    t = sim.tuning()
+    assert (t["lanes"], t["block"], t["compact"]) == (lanes, block, compact)
     sim.set_substeps(K)
     sim.step(dt)
     sim.sync()
@@ -161,7 +165,7 @@ def test_every_launch_shape_matches_the_oracle(lanes, block):
     with pytest.raises(SphError):
         sim.set_tuning(3, 128)
     with pytest.raises(SphError):
-        sim.set_tuning(4, 96)
+        sim.set_tuning(4 if case.dim == 2 else 8, 96)
 
 
 def test_autotune_leaves_the_state_unchanged_and_keeps_parity():
