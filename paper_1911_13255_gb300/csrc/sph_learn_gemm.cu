@@ -3,18 +3,24 @@
 // both row-major with K contiguous ("K-major").  M % 128 == 0, N % 16 == 0,
 // K % 64 == 0 (callers pad).
 //
-// One CTA of 128 threads computes a 128 x NT tile with a single-thread-issued
-// tcgen05.mma (kind::f16, M = 128, N = NT, K = 16 per instruction) into an
-// FP32 accumulator in tensor memory.  K advances in chunks of 64 through two
-// shared-memory stages: all threads copy a chunk of A (128 x 64) and B
-// (NT x 64) into the canonical no-swizzle K-major layout (core matrices of
-// 8 rows x 16 bytes; LBO = 128 B between core matrices along K, SBO = 1 KB
-// between 8-row groups), the issuing thread launches 4 MMAs and commits them
-// to the stage's mbarrier, and the stage is refilled only after that
-// mbarrier fires.  The epilogue reads the accumulator with tcgen05.ld
-// (warp w owns TMEM lanes 32w..32w+31 = tile rows), adds the bias and stores
-// FP32.  Every wait is bounded; a timeout sets a status bit, skips the
-// epilogue and still frees the tensor memory.
+// One CTA of 128 threads computes a 128 x NT tile into an FP32 accumulator in
+// tensor memory.  K advances in chunks of 64 through a ring of four
+// shared-memory stages:
+//   - warp 0 (one thread) is the producer: it waits until a stage is empty,
+//     arms the stage's "full" mbarrier with the byte count and issues two TMA
+//     tile loads (cp.async.bulk.tensor.2d, 128-byte swizzle) of A (128 x 64)
+//     and B (NT x 64);
+//   - warp 1 (one thread) issues the MMAs: it waits until a stage is full,
+//     launches 4 tcgen05.mma (kind::f16, M = 128, N = NT, K = 16; shared-memory
+//     descriptors in the 128-byte-swizzle K-major layout, 1 KB between 8-row
+//     groups, +32 B per K step inside the swizzle atom) and commits them to the
+//     stage's "empty" mbarrier; after the last chunk it commits to "done";
+//   - all four warps wait for "done", read the accumulator with tcgen05.ld
+//     (warp w owns TMEM lanes 32w..32w+31 = tile rows), add the bias and store.
+// Every wait is bounded; a timeout sets a status bit, skips the epilogue and
+// still frees the tensor memory.
+#include <cuda.h>   // CUtensorMap and its enums; the encoder is taken from the driver at run time
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -35,17 +41,6 @@ constexpr long long kMbarSpin = 1ll << 26;
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor: start address, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
 }
 
 // instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major
@@ -70,33 +65,54 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
     return false;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(kTcThreads) k_gemm_bf16(const uint4 *__restrict__ A, const uint4 *__restrict__ B,
-                                                          const float *__restrict__ bias, float *__restrict__ C,
-                                                          int M, int N, int K)
+// shared-memory matrix descriptor, 128-byte swizzle, K-major: start address,
+// leading byte offset 16 (not used by this layout), stride 1 KB between
+// 8-row groups, descriptor version 1, layout type 2 (128-byte swizzle)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr)
 {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+constexpr int kStages = 4;
+
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads) k_gemm_bf16(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB,
+                                                          const float *__restrict__ bias, float *__restrict__ C,
+                                                          int M, int N, int K, int kper)
+{
+    // split K: slice blockIdx.z covers chunks [z kper, (z + 1) kper) and
+    // writes its partial tile to C + z M N (the caller reduces the slices)
+    C += (size_t)blockIdx.z * M * N;
     constexpr int kBStage = NT * kKChunk * 2;
-    constexpr int kStage = kAStage + kBStage;
+    constexpr int kStage = kAStage + kBStage;        // a multiple of 1 KB
     constexpr uint32_t kCols = NT < 32 ? 32 : NT;   // tensor-memory columns (power of 2 >= 32)
     extern __shared__ uint8_t dsm[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t s_tmem;
-    // 1 KB aligned stage buffers
     const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
-    uint8_t *const gbase = dsm + (base - smem_u32(dsm));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
-    const int kq = K >> 3;   // 16-byte pieces per row
+    const int kc0 = blockIdx.z * kper;
+    const int nk = min(K / kKChunk - kc0, kper);
 
-    if (warp == 0) {
+    if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        for (int s = 0; s < kStages; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -104,41 +120,48 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_bf16(const uint4 *__restric
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    const int nk = K / kKChunk;
-    uint32_t phase[2] = {0u, 0u};
     bool ok = true;
-    for (int kc = 0; kc < nk && ok; kc++) {
-        const int s = kc & 1;
-        if (kc >= 2) {
-            ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[s]), phase[s]));   // CTA-uniform
-            phase[s] ^= 1u;
-            if (!ok) break;
+    if (warp == 0 && lane == 0) {
+        // producer
+        uint32_t ph[kStages] = {0u, 0u, 0u, 0u};
+        for (int kc = 0; kc < nk; kc++) {
+            const int s = kc % kStages;
+            if (kc >= kStages) {
+                if (!mbar_wait(smem_u32(&empty[s]), ph[s])) {
+                    ok = false;
+                    break;
+                }
+                ph[s] ^= 1u;
+            }
+            const uint32_t a_s = base + s * kStage, b_s = a_s + kAStage, fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(a_s),
+                "l"(reinterpret_cast<uint64_t>(&tmA)), "r"((kc0 + kc) * kKChunk), "r"(m0), "r"(fb)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(b_s),
+                "l"(reinterpret_cast<uint64_t>(&tmB)), "r"((kc0 + kc) * kKChunk), "r"(n0), "r"(fb)
+                : "memory");
         }
-        uint8_t *As = gbase + s * kStage;
-        uint8_t *Bs = As + kAStage;
-        // piece p: row p / 8, 16-byte column group p % 8 of the chunk
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int p = tid + kTcThreads * i;
-            const int r = p >> 3, kg = p & 7;
-            const uint4 v = A[(size_t)(m0 + r) * kq + kc * 8 + kg];
-            *(uint4 *)(As + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) = v;
-        }
-        for (int p = tid; p < NT * 8; p += kTcThreads) {
-            const int r = p >> 3, kg = p & 7;
-            const uint4 v = B[(size_t)(n0 + r) * kq + kc * 8 + kg];
-            *(uint4 *)(Bs + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) = v;
-        }
-        // generic-proxy writes -> visible to the tensor core (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        uint32_t ph[kStages] = {0u, 0u, 0u, 0u};
+        for (int kc = 0; kc < nk; kc++) {
+            const int s = kc % kStages;
+            if (!mbar_wait(smem_u32(&full[s]), ph[s])) {
+                ok = false;
+                break;
+            }
+            ph[s] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = base + s * kStage, b0 = a0 + kAStage;
 #pragma unroll
             for (int kk = 0; kk < kKChunk / 16; kk++) {
-                const uint64_t ad = sdesc(a0 + kk * 256, 128, 1024);
-                const uint64_t bd = sdesc(b0 + kk * 256, 128, 1024);
+                const uint64_t ad = sdesc_sw128(a0 + kk * 32);
+                const uint64_t bd = sdesc_sw128(b0 + kk * 32);
                 const uint32_t acc = (kc | kk) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
@@ -148,23 +171,17 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_bf16(const uint4 *__restric
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar[s]))
+                             smem_u32(&empty[s]))
                          : "memory");
         }
+        // covers every MMA issued before it (arrives at once if there is none)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
     }
-    // the last commit covers every MMA issued before it
-    if (ok && nk > 0) {
-        const int s = (nk - 1) & 1;
-        ok = mbar_wait(smem_u32(&mbar[s]), phase[s]);
-    }
+    if (!mbar_wait(smem_u32(&done), 0u)) ok = false;
     ok = __syncthreads_and(ok);
-    // a CTA whose wait ran out must not free tensor memory under MMAs in
-    // flight: wait (bounded) once more for both stages before leaving
-    if (!ok) {
-        mbar_wait(smem_u32(&mbar[0]), phase[0]);
-        mbar_wait(smem_u32(&mbar[1]), phase[1]);
-        if (lane == 0) atomicOr(&g_tc_status, 1u);
-    }
+    if (!ok && tid == 0) atomicOr(&g_tc_status, 1u);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         const int row = m0 + warp * 32 + lane;
@@ -197,29 +214,105 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_bf16(const uint4 *__restric
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 2) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
     }
 }
+
+typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiled)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D tensor map of a row-major bfloat16 matrix (rows x cols), box 64 x box_rows
+int make_map(CUtensorMap *m, const void *ptr, long long rows, long long cols, int box_rows)
+{
+    EncodeTiled enc = encoder();
+    if (!enc) return -3;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKChunk, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+// C = bias + sum of the S partial tiles, in slice order (deterministic)
+__global__ void k_splitk_sum(const float *__restrict__ ws, int S, long long MN, int N, const float *__restrict__ bias,
+                             float *__restrict__ C)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MN) return;
+    float v = bias ? bias[i % N] : 0.0f;
+    for (int z = 0; z < S; z++) v += ws[(size_t)z * MN + i];
+    C[i] = v;
+}
+
+// split-K workspace, grown on demand outside stream capture
+float *g_ws = nullptr;
+size_t g_ws_floats = 0;
 
 template <int NT>
 int launch_tile(const uint16_t *A, const uint16_t *B, const float *bias, float *C, int M, int N, int K,
                 cudaStream_t st)
 {
     constexpr int kStage = kAStage + NT * kKChunk * 2;
-    // two stages + alignment slack; at least 64 KB so that at most three
-    // CTAs share an SM (3 x 128 tensor-memory columns <= 512)
-    int smem = 2 * kStage + 1024;
-    if (smem < 64 * 1024) smem = 64 * 1024;
+    const int smem = kStages * kStage + 1024;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(k_gemm_bf16<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return -3;
         attr_set = true;
     }
-    dim3 grid(M / 128, N / NT);
-    k_gemm_bf16<NT><<<grid, kTcThreads, smem, st>>>((const uint4 *)A, (const uint4 *)B, bias, C, M, N, K);
+    alignas(64) CUtensorMap ta, tb;
+    int rc = make_map(&ta, A, M, K, 128);
+    if (!rc) rc = make_map(&tb, B, N, K, NT);
+    if (rc) return rc;
+    // few output tiles and a long K loop: split K over up to 152 CTAs
+    const int tiles = (M / 128) * (N / NT), nk = K / kKChunk;
+    int S = 1;
+    if (tiles < 76 && nk >= 16) {
+        S = std::min(152 / tiles, nk / 8);
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cap);
+        const size_t need = (size_t)S * M * N;
+        if (S > 1 && cap == cudaStreamCaptureStatusNone && need > g_ws_floats) {
+            if (g_ws) cudaFree(g_ws);
+            g_ws = nullptr;
+            g_ws_floats = 0;
+            if (cudaMalloc(&g_ws, need * sizeof(float)) == cudaSuccess) g_ws_floats = need;
+            else cudaGetLastError();
+        }
+        if (S < 2 || need > g_ws_floats) S = 1;
+    }
+    const int kper = (nk + S - 1) / S;
+    S = (nk + kper - 1) / kper;
+    dim3 grid(M / 128, N / NT, S);
+    if (S == 1) {
+        k_gemm_bf16<NT><<<grid, kTcThreads, smem, st>>>(ta, tb, bias, C, M, N, K, kper);
+    } else {
+        k_gemm_bf16<NT><<<grid, kTcThreads, smem, st>>>(ta, tb, nullptr, g_ws, M, N, K, kper);
+        const long long MN = (long long)M * N;
+        k_splitk_sum<<<(unsigned)((MN + 255) / 256), 256, 0, st>>>(g_ws, S, MN, N, bias, C);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -232,6 +325,7 @@ int launch_gemm_bf16(const uint16_t *A, const uint16_t *B, const float *bias, fl
     if (M / 128 > 65535 * 1024LL || K > (1LL << 30) || N > (1LL << 30)) return -7;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15) return -1;
     const int m = (int)M, n = (int)N, k = (int)K;
+    if (n % 256 == 0) return launch_tile<256>(A, B, bias, C, m, n, k, st);
     if (n % 128 == 0) return launch_tile<128>(A, B, bias, C, m, n, k, st);
     if (n % 64 == 0) return launch_tile<64>(A, B, bias, C, m, n, k, st);
     if (n % 32 == 0) return launch_tile<32>(A, B, bias, C, m, n, k, st);

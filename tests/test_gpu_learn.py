@@ -13,7 +13,8 @@ import paper_1911_13255_gb300 as pkg  # noqa: E402
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (128, 128, 64), (256, 128, 128), (384, 512, 512),
-                                   (128, 64, 192), (256, 32, 1024), (1280, 48, 64), (512, 640, 256)])
+                                   (128, 64, 192), (256, 32, 1024), (1280, 48, 64), (512, 640, 256),
+                                   (256, 256, 320), (128, 512, 8192), (128, 16, 4160)])
 def test_gemm_matches_fp64_products_of_the_bf16_operands(M, N, K):
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16)
