@@ -250,7 +250,8 @@ int sphfsi_step_time(sphfsi_ctx *c, float *ms);
  * settings and bit for bit at equal settings. */
 typedef struct {
     int32_t lanes;         /* threads per target particle in the fluid pair loops:
-                              2, 4 or 8 in 2-D (default 4); 4, 8 or 16 in 3-D (default 8) */
+                              2, 4 or 8 in 2-D (default 4); 4, 8 or 16 in 3-D (default 8
+                              below 200 000 fluid particles in the context, else 4) */
     int32_t block;         /* threads per block of those loops: 64, 128 (default) or 256 */
     int32_t solid_variant; /* 0: automatic cluster kernel choice; 1: the four-lane
                               cluster kernel (sphfsi_set_solid_path 1) */

@@ -585,7 +585,10 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // ---- fluid
     Fluid &F = c->F;
     F.n = (int)nf;
-    F.lanes = D == 2 ? 4 : 8;
+    // 2-D: 4 lanes per target (more make the fluid loops faster but crowd the
+    // SMs that the solid branch, usually the longer one, runs on); 3-D: 8 for
+    // small problems, 4 for large ones
+    F.lanes = D == 2 ? 4 : (nf < 200000 ? 8 : 4);
     F.block = 128;
     F.compact = D == 2 ? 1 : 0;
     for (int k = 0; k < 2; k++) {
@@ -811,7 +814,14 @@ int sphfsi_finalize(sphfsi_ctx *c)
     }
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     for (int k = 0; k < sphfsi_ctx::kEvents; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
-    TRY(cuda_rc(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)));
+    // the solid branch (coupling force, sub-steps) is the longer branch of a
+    // step for small and medium problems: its stream gets the highest priority
+    // so that its blocks are scheduled ahead of queued fluid blocks
+    {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        TRY(cuda_rc(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi)));
+    }
     TRY(cuda_rc(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming)));
     TRY(cuda_rc(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming)));
     c->finalized = true;

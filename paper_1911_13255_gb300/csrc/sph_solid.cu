@@ -779,10 +779,20 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
         }
     }
+    // sum of the static gradients: (Q_a + Q_b) . g summed over b is
+    // Q_a . sum(g) + sum(Q_b . g)
+    float sgx = 0.f, sgy = 0.f;
+#pragma unroll
+    for (int u = 0; u < kMaxNb2; u++) {
+        sgx += gx[u];
+        sgy += gy[u];
+    }
     cluster_sync();
 
+    // Two accumulator sets (even / odd neighbour slots) in both loops, so that
+    // a thread has twice as many independent add chains in flight.
     auto rate = [&](float4 va, float *Hd) {
-        float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f;
+        float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, N3 = 0.f;
 #pragma unroll
         for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
             float2 vb[kChunk2];
@@ -790,15 +800,27 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             for (int u = 0; u < kChunk2; u++)
                 if (c0 + u < nn) vb[u] = ld_cl2(aQ[c0 + u] + dV);
 #pragma unroll
-            for (int u = 0; u < kChunk2; u++)
+            for (int u = 0; u < kChunk2; u += 2) {
                 if (c0 + u < nn) {
-                    float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
+                    const float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
                     M0 += dvx * gx[c0 + u];
                     M1 += dvx * gy[c0 + u];
                     M2 += dvy * gx[c0 + u];
                     M3 += dvy * gy[c0 + u];
                 }
+                if (c0 + u + 1 < nn) {
+                    const float dvx = vb[u + 1].x - va.x, dvy = vb[u + 1].y - va.y;
+                    N0 += dvx * gx[c0 + u + 1];
+                    N1 += dvx * gy[c0 + u + 1];
+                    N2 += dvy * gx[c0 + u + 1];
+                    N3 += dvy * gy[c0 + u + 1];
+                }
+            }
         }
+        M0 += N0;
+        M1 += N1;
+        M2 += N2;
+        M3 += N3;
         Hd[0] = M0 * B[0] + M1 * B[2];
         Hd[1] = M0 * B[1] + M1 * B[3];
         Hd[2] = M2 * B[0] + M3 * B[2];
@@ -826,7 +848,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         // (B) force loop and kick
         if (own) {
             const float4 Qa = sQ[g];
-            float ax = 0.f, ay = 0.f;
+            float ax = Qa.x * sgx + Qa.y * sgy, ay = Qa.z * sgx + Qa.w * sgy, bx = 0.f, by = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
                 float4 qb[kChunk2];
@@ -834,12 +856,19 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 for (int u = 0; u < kChunk2; u++)
                     if (c0 + u < nn) qb[u] = ld_cl(aQ[c0 + u]);
 #pragma unroll
-                for (int u = 0; u < kChunk2; u++)
+                for (int u = 0; u < kChunk2; u += 2) {
                     if (c0 + u < nn) {
-                        ax += (Qa.x + qb[u].x) * gx[c0 + u] + (Qa.y + qb[u].y) * gy[c0 + u];
-                        ay += (Qa.z + qb[u].z) * gx[c0 + u] + (Qa.w + qb[u].w) * gy[c0 + u];
+                        ax += qb[u].x * gx[c0 + u] + qb[u].y * gy[c0 + u];
+                        ay += qb[u].z * gx[c0 + u] + qb[u].w * gy[c0 + u];
                     }
+                    if (c0 + u + 1 < nn) {
+                        bx += qb[u + 1].x * gx[c0 + u + 1] + qb[u + 1].y * gy[c0 + u + 1];
+                        by += qb[u + 1].z * gx[c0 + u + 1] + qb[u + 1].w * gy[c0 + u + 1];
+                    }
+                }
             }
+            ax += bx;
+            ay += by;
             if (!cons) {
                 float4 v = sV[g];
                 float av0 = ax * inv_rhoS + fF[0] * inv_mS + P.g[0];
