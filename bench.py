@@ -358,7 +358,7 @@ def run_gpu(args, rank, world, local_rank):
                    "dp_F": case.f_dp, "dp_S": case.s_dp,
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
-                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact")},
+                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile")},
                    "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -569,7 +569,7 @@ def e2e_run(cases, dev, steps, tuning):
         if c.inflow_on:
             sim.set_inflow(1, c.inflow_profile, c.inflow_width, c.inflow_y0, c.inflow_H, c.inflow_U, c.inflow_tramp)
     sim.finalize()
-    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"])
+    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"])
     p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)

@@ -260,6 +260,10 @@ typedef struct {
                               candidate loop; 1 first collect each thread's in-support
                               neighbours in shared memory, then evaluate them densely
                               (default 1 in 2-D, 0 in 3-D) */
+    int32_t tile;          /* fluid pair loops: 0 one group of lanes per target particle
+                              over the whole grid; 1 one block per tile of grid cells (16 of a
+                              row in 2-D, 4 in 3-D) whose neighbour records are first staged in
+                              shared memory by bulk copies (default 0) */
 } sphfsi_tuning;
 
 /* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */
@@ -270,8 +274,8 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t);
  * workload: for each candidate setting, `steps` graph-replayed steps of size
  * dt_F (as sphfsi_run) to warm up, then `steps` timed with CUDA events.  The
  * search goes over the lane count (block 128), then the pair-loop form,
- * then the block size, then (2-D with a solid) the solid kernel variant,
- * keeping the fastest of each.
+ * then tiles on or off, then the block size, then (2-D with a solid) the
+ * solid kernel variant, keeping the fastest of each.
  * Every device allocation of the context is saved before and restored after
  * each trial and at the end, so the simulation state, time and counters are
  * exactly as before the call; the best setting stays selected and is

@@ -57,7 +57,7 @@ class Info(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("block", C.c_int32), ("solid_variant", C.c_int32), ("step_ms", C.c_float),
-                ("compact", C.c_int32)]
+                ("compact", C.c_int32), ("tile", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -286,10 +286,10 @@ class Simulation:
         _check(lib().sphfsi_autotune(self.h, float(dt), int(steps), C.byref(t)), "sphfsi_autotune")
         return t.as_dict()
 
-    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None):
+    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0):
         if compact is None:
             compact = 1 if self.dim == 2 else 0
-        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact))
+        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact), int(tile))
         _check(lib().sphfsi_set_tuning(self.h, C.byref(t)), "sphfsi_set_tuning")
 
     def tuning(self):

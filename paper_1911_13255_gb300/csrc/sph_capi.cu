@@ -591,6 +591,25 @@ int sphfsi_finalize(sphfsi_ctx *c)
     F.lanes = D == 2 ? 4 : (nf < 200000 ? 8 : 4);
     F.block = 128;
     F.compact = D == 2 ? 1 : 0;
+    F.tile = 0;
+    // tiles: T cells of a grid row per block (16 in 2-D, 4 in 3-D); the
+    // staging area holds about three times the mean neighbourhood
+    {
+        const int T = D == 2 ? 16 : 4;
+        std::vector<int4> tiles;
+        for (int b = 0; b < B; b++) {
+            const Grid &g = c->ih[b].d.g;
+            for (int z = 0; z < g.nc[2]; z++)
+                for (int y = 0; y < g.nc[1]; y++)
+                    for (int x = 0; x < g.nc[0]; x += T)
+                        tiles.push_back(make_int4(b, c->ih[b].d.c0 + x + g.nc[0] * (y + g.nc[1] * z),
+                                                  std::min(T, g.nc[0] - x), 0));
+        }
+        F.ntiles = (int)tiles.size();
+        F.tile_cap = D == 2 ? 1024 : 2048;
+        TRY(dalloc(c, &F.tiles, tiles.size()));
+        TRY(upload(c, F.tiles, tiles));
+    }
     for (int k = 0; k < 2; k++) {
         FluidState &S = F.s[k];
         TRY(dalloc(c, &S.x, nf));
@@ -1311,11 +1330,13 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 1 || t->compact < 0 || t->compact > 1)
+        t->solid_variant < 0 || t->solid_variant > 1 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
+        t->tile > 1)
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
     c->F.compact = t->compact;
+    c->F.tile = t->tile;
     c->S.force_lane_path = t->solid_variant;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -1332,6 +1353,7 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
     t->block = c->F.block;
     t->solid_variant = c->S.force_lane_path;
     t->compact = c->F.compact;
+    t->tile = c->F.tile;
     t->step_ms = 0.0f;
     return SPHFSI_OK;
 }
@@ -1405,6 +1427,11 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         cur = *best;
         if (!rc) {
             cur.compact = 1 - cur.compact;
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc) {
+            cur.tile = 1 - cur.tile;
             rc = consider(cur);
         }
         cur = *best;

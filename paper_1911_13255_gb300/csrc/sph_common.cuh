@@ -116,6 +116,10 @@ struct Fluid {
     int lanes;        // threads per target particle of the pair loops (tuned)
     int block;        // threads per block of the pair loops (tuned)
     int compact;      // 1: fluid-fluid pairs through per-thread in-support lists (tuned)
+    int tile;         // 1: one block per tile of cells, neighbours staged in shared memory (tuned)
+    int4 *tiles;      // (instance, first global cell, cells, 0) per tile
+    int ntiles;
+    int tile_cap;     // records a block can stage (shared memory: 32 B each)
     int *inst;        // instance of each slot
     FluidState s[2];
     float4 *P4;       // (x - x_cell, y - y_cell, z - z_cell, p)   sorted records

@@ -83,6 +83,154 @@ __device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float
     return d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
 }
 
+// ---------------------------------------------------------------------------
+// Tiles: a block owns T consecutive cells of one grid row (an instance's
+// cells [c_first, c_first + ntc)).  Every fluid neighbour of its targets lies
+// in the 3^(d-1) rows around it, x from the first cell - 1 to the last + 1;
+// these row pieces are contiguous in the cell-sorted records, so the block
+// stages them into shared memory with bulk copies (cp.async.bulk, completion
+// on an mbarrier) and its targets read their fluid neighbours from there.  A
+// row that wraps in a periodic x splits into two pieces.
+// ---------------------------------------------------------------------------
+struct TilePiece {
+    int c_lo, c_hi;   // global cells [c_lo, c_hi]; empty when c_lo > c_hi
+    int base;         // shared-memory slot of record j of these cells = j + base
+};
+
+struct TileSrc {
+    const float4 *sP, *sX;      // staged P4 and second records
+    const TilePiece *pieces;    // 2 per row, rows (dy + 1) + 3 (dz + 1)
+};
+
+constexpr int kTileRows = 9;
+
+__device__ __forceinline__ bool bulk_wait(uint32_t mbar)
+{
+    for (long long k = 0; k < (1ll << 26); k++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Stage the tile's neighbourhood: P4 into sP, X4 into sX (at most cap
+// records each).  Returns the number staged, or -1 when they do not fit (the
+// block then reads its neighbours from global memory) or a wait ran out.
+template <int D>
+__device__ int tile_stage(const Batch &bt, const Fluid &f, const float4 *X4, int4 tile, TilePiece *pieces,
+                          float4 *sP, float4 *sX, int cap, uint64_t *mbar, int *s_total)
+{
+    const Inst &In = bt.I[tile.x];
+    const Grid &g = In.g;
+    const int c_first = tile.y, ntc = tile.z;
+    const int key = c_first - In.c0;
+    const int cx0 = key % g.nc[0], cy = (key / g.nc[0]) % g.nc[1], cz = D == 3 ? key / (g.nc[0] * g.nc[1]) : 0;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        int off = 0;
+        for (int r = 0; r < kTileRows; r++) {
+            const int dy = r % 3 - 1, dz = r / 3 - 1;
+            TilePiece *pp = pieces + 2 * r;
+            pp[0] = pp[1] = TilePiece{1, 0, 0};
+            const int y = cy + dy, z = cz + dz;
+            if ((D == 2 && dz != 0) || y < 0 || y >= g.nc[1] || z < 0 || z >= g.nc[2]) continue;
+            const int row0 = In.c0 + g.nc[0] * (y + g.nc[1] * z);
+            int lo = cx0 - 1, hi = cx0 + ntc;
+            int a0 = 0, a1 = -1, b0 = 0, b1 = -1;   // local x ranges of the two pieces
+            if (!g.periodic_x) {
+                a0 = lo < 0 ? 0 : lo;
+                a1 = hi >= g.nc[0] ? g.nc[0] - 1 : hi;
+            } else if (ntc + 2 >= g.nc[0]) {
+                a0 = 0;
+                a1 = g.nc[0] - 1;
+            } else if (lo < 0) {
+                a0 = a1 = g.nc[0] - 1;
+                b0 = 0;
+                b1 = hi;
+            } else if (hi >= g.nc[0]) {
+                a0 = lo;
+                a1 = g.nc[0] - 1;
+                b0 = 0;
+                b1 = hi - g.nc[0];
+            } else {
+                a0 = lo;
+                a1 = hi;
+            }
+            if (a1 >= a0) {
+                const int p0 = f.cstart[row0 + a0];
+                pp[0] = TilePiece{row0 + a0, row0 + a1, off - p0};
+                off += f.cstart[row0 + a1 + 1] - p0;
+            }
+            if (b1 >= b0) {
+                const int p0 = f.cstart[row0 + b0];
+                pp[1] = TilePiece{row0 + b0, row0 + b1, off - p0};
+                off += f.cstart[row0 + b1 + 1] - p0;
+            }
+        }
+        *s_total = off <= cap ? off : -1;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int total = *s_total;
+    if (total < 0) return -1;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(total * 32)
+                     : "memory");
+        for (int q = 0; q < 2 * kTileRows; q++) {
+            const TilePiece pc = pieces[q];
+            if (pc.c_lo > pc.c_hi) continue;
+            const int p0 = f.cstart[pc.c_lo], n = f.cstart[pc.c_hi + 1] - p0;
+            if (n == 0) continue;
+            const int o = p0 + pc.base;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(sP + o)),
+                         "l"(f.P4 + p0), "r"(n * 16), "r"(mb)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             (uint32_t)__cvta_generic_to_shared(sX + o)),
+                         "l"(X4 + p0), "r"(n * 16), "r"(mb)
+                         : "memory");
+        }
+    }
+    const bool ok = __syncthreads_and(bulk_wait(mb));
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(&bt.ctl[tile.x].status, ST_TIMEOUT);
+        return -1;
+    }
+    return total;
+}
+
+// Run body(i, act, ts) for every target of the block's tile, L lanes per
+// target, the same number of rounds in every thread (act = false past the
+// end); ts is null when the neighbourhood did not fit in shared memory.
+template <int D, int L, typename Body>
+__device__ __forceinline__ void tile_loop(const Batch &bt, const Fluid &f, const float4 *X4, uint8_t *stage, Body &&body)
+{
+    __shared__ TilePiece s_pieces[2 * kTileRows];
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ int s_total;
+    const int4 tile = f.tiles[blockIdx.x];
+    float4 *sP = (float4 *)stage, *sX = sP + f.tile_cap;
+    const int staged = tile_stage<D>(bt, f, X4, tile, s_pieces, sP, sX, f.tile_cap, &s_mbar, &s_total);
+    const TileSrc src{sP, sX, s_pieces};
+    const TileSrc *ts = staged >= 0 ? &src : nullptr;
+    const int tp0 = f.cstart[tile.y], tp1 = f.cstart[tile.y + tile.z];
+    const int per = blockDim.x / L;
+    const int rounds = (tp1 - tp0 + per - 1) / per;
+    for (int k = 0; k < rounds; k++) {
+        const int i = tp0 + k * per + (int)threadIdx.x / L;
+        body(i, i < tp1, ts);
+    }
+}
+
 // Fluid-fluid pairs of target i (this lane's share of the candidates), in
 // one of two forms chosen by the launch shape (Fluid::compact):
 //
@@ -102,9 +250,9 @@ __device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float
 constexpr int kPairCap = 32;
 
 template <int D, int L, bool CP, typename Fetch, typename Pair>
-__device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz, int i,
-                                                int lane, const float4 &Pi, float rc2, uint32_t *list, int stride,
-                                                Fetch &&fetch, Pair &&pair)
+__device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz,
+                                                       int i, int lane, const float4 &Pi, float rc2, uint32_t *list,
+                                                       int stride, Fetch &&fetch, Pair &&pair)
 {
     unsigned cnt_total = 0;
     if constexpr (!CP) {
@@ -152,6 +300,63 @@ __device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Grid &g, i
         drain();
         return cnt_total;
     }
+}
+
+// The same over staged records: record j of neighbour cell c sits at slot
+// j + base(c) of the staged arrays; list entries hold slots.
+template <int D, int L, bool CP, typename Pair>
+__device__ __forceinline__ unsigned fluid_pairs_tile(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz,
+                                                     int i, int lane, const float4 &Pi, float rc2, uint32_t *list,
+                                                     int stride, const TileSrc &ts, Pair &&pair)
+{
+    unsigned cnt_total = 0;
+    int cnt = 0;
+    auto drain = [&]() {
+#pragma unroll 1
+        for (int k = 0; k < cnt; k++) {
+            const uint32_t e = list[k * stride];
+            const int q = (int)(e >> 5);
+            float ox, oy, oz;
+            cell_offset((int)(e & 31u), g, ox, oy, oz);
+            const float4 Pj = ts.sP[q];
+            float d[3];
+            const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+            pair(q, Pj, ts.sX[q], d, r2, ox, oy, oz);
+        }
+        cnt = 0;
+    };
+    for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+        const TilePiece *pp = ts.pieces + 2 * ((code / 3) % 3 + 3 * (code / 9));
+        const int base = (c >= pp[0].c_lo && c <= pp[0].c_hi) ? pp[0].base : pp[1].base;
+        const int j1 = f.cstart[c + 1];
+        for (int j = f.cstart[c] + lane; j < j1; j += L) {
+            if (j == i) continue;
+            const int q = j + base;
+            const float4 Pj = ts.sP[q];
+            float d[3];
+            const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+            if (r2 >= rc2) continue;
+            cnt_total++;
+            if constexpr (CP) {
+                list[cnt * stride] = ((uint32_t)q << 5) | (uint32_t)code;
+                cnt++;
+                if (cnt == kPairCap) drain();
+            } else {
+                pair(q, Pj, ts.sX[q], d, r2, ox, oy, oz);
+            }
+        }
+    });
+    if constexpr (CP) drain();
+    return cnt_total;
+}
+
+template <int D, int L, bool CP, typename Fetch, typename Pair>
+__device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz, int i,
+                                                int lane, const float4 &Pi, float rc2, uint32_t *list, int stride,
+                                                const TileSrc *ts, Fetch &&fetch, Pair &&pair)
+{
+    if (ts) return fluid_pairs_tile<D, L, CP>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, *ts, pair);
+    return fluid_pairs_global<D, L, CP>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, fetch, pair);
 }
 
 template <int L>
@@ -327,15 +532,31 @@ static inline int grid_blocks(int n, int L, int block)
 
 constexpr int kListBytes = kPairCap * 4;   // per-thread in-support list (fluid_pairs)
 
-// the same for the pair-loop kernels templated on the form (f.compact)
+// the same for the pair-loop kernels templated on the pair form (f.compact)
+// and on tiles (f.tile: one block per tile, the staging area after the lists)
+template <typename K>
+static void allow_smem(K kern, size_t bytes)
+{
+    // dynamic plus static shared memory above the default 48 KB needs the opt-in
+    if (bytes > 32 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 #define SPH_LAUNCH_PAIRS(KERN, n, ...)                                                        \
     do {                                                                                      \
-        const size_t sm_ = f.compact ? (size_t)kListBytes * f.block : 0;                      \
+        const size_t sm_ = (f.compact ? (size_t)kListBytes * f.block : 0) +                  \
+                           (f.tile ? (size_t)f.tile_cap * 32 : 0);                            \
         auto go_ = [&](auto Dc, auto Lc) {                                                    \
             constexpr int D_ = decltype(Dc)::value, L_ = decltype(Lc)::value;                \
-            const int nb_ = grid_blocks(n, L_, f.block);                                      \
-            if (f.compact) KERN<D_, L_, true><<<nb_, f.block, sm_, st>>>(__VA_ARGS__);        \
-            else KERN<D_, L_, false><<<nb_, f.block, 0, st>>>(__VA_ARGS__);                   \
+            const int nb_ = f.tile ? f.ntiles : grid_blocks(n, L_, f.block);                  \
+            if (nb_ == 0) return;                                                             \
+            auto run_ = [&](auto kern) {                                                      \
+                allow_smem(kern, sm_);                                                        \
+                kern<<<nb_, f.block, sm_, st>>>(__VA_ARGS__);                                 \
+            };                                                                                \
+            if (f.compact && f.tile) run_(KERN<D_, L_, true, true>);                          \
+            else if (f.compact) run_(KERN<D_, L_, true, false>);                              \
+            else if (f.tile) run_(KERN<D_, L_, false, true>);                                 \
+            else run_(KERN<D_, L_, false, false>);                                            \
         };                                                                                    \
         const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
             go_(std::integral_constant<int, 2>{}, Lc);                                        \
@@ -350,14 +571,10 @@ constexpr int kListBytes = kPairCap * 4;   // per-thread in-support list (fluid_
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
 template <int D, int L, bool CP>
-__global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
+__device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
+                                                 bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
-    extern __shared__ uint32_t s_pair_list[];
-    uint32_t *const list = s_pair_list + threadIdx.x;
-    const int stride = blockDim.x;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / L, lane = t % L;
-    const bool act = i < f.n;
+    const bool act = act_;
     const int b = act ? f.inst[i] : 0;
     const Inst &In = bt.I[b];
     const Grid &g = In.g;
@@ -374,7 +591,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float c0 = P.c0, eta2 = 2.0f * P.eta;
         // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
-        nff = fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride,
+        nff = fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
                                 [&](int j) { return f.V4[j]; },
                                 [&](int, const float4 &Pj, const float4 &Vj, const float *d, float r2, float, float,
                                     float) {
@@ -446,6 +663,23 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
         for (int k = 0; k < D; k++) cnt.mom[k] = (double)(Vi_ * afs[k]);
     }
     flush_counts<D>(bt, b, act, cnt, true);
+}
+
+template <int D, int L, bool CP, bool TILE>
+__global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
+{
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
+    const int stride = blockDim.x;
+    if constexpr (!TILE) {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        momentum_one<D, L, CP>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+    } else {
+        tile_loop<D, L>(bt, f, f.V4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
+                        [&](int i, bool act, const TileSrc *ts) {
+                            momentum_one<D, L, CP>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                        });
+    }
 }
 
 int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
@@ -522,14 +756,10 @@ int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, in
 // writes the end-of-step state to s[0] in cell order
 // ---------------------------------------------------------------------------
 template <int D, int L, bool CP>
-__global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
+__device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
+                                                 bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
-    extern __shared__ uint32_t s_pair_list[];
-    uint32_t *const list = s_pair_list + threadIdx.x;
-    const int stride = blockDim.x;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / L, lane = t % L;
-    const bool act = i < f.n;
+    const bool act = act_;
     const int b = act ? f.inst[i] : 0;
     const Inst &In = bt.I[b];
     const Grid &g = In.g;
@@ -544,7 +774,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
         const float inv2c0 = 0.5f / P.c0;
-        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride,
+        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
                           [&](int j) { return f.W4[j]; },
                           [&](int, const float4 &, const float4 &Wj, const float *d, float r2, float, float, float) {
                 const float rhoj = P.rho0 + Wj.w;
@@ -602,6 +832,23 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
     S.drho[i] = M.drho[i] + (float)h * rhodot;
     S.rhodot[i] = rhodot;
     S.id[i] = M.id[i];
+}
+
+template <int D, int L, bool CP, bool TILE>
+__global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
+{
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
+    const int stride = blockDim.x;
+    if constexpr (!TILE) {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        density_one<D, L, CP>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+    } else {
+        tile_loop<D, L>(bt, f, f.W4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
+                        [&](int i, bool act, const TileSrc *ts) {
+                            density_one<D, L, CP>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                        });
+    }
 }
 
 int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
@@ -705,16 +952,12 @@ __device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, con
 }
 
 template <int D, int L, bool CP>
-__global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
+__device__ __forceinline__ void reinit_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
+                                                 bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
-    extern __shared__ uint32_t s_pair_list[];
-    uint32_t *const list = s_pair_list + threadIdx.x;
-    const int stride = blockDim.x;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / L, lane = t % L;
-    const int b = i < f.n ? f.inst[i] : 0;
+    const int b = act_ ? f.inst[i] : 0;
     // the L lanes of a particle share its instance, so this is group-uniform
-    const bool act = i < f.n && bt.ctl[b].reinit;
+    const bool act = act_ && bt.ctl[b].reinit;
     const Inst &In = bt.I[b];
     const Grid &g = In.g;
     const Phys &P = In.P;
@@ -725,7 +968,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
         int cx, cy, cz;
         cell_xyz(f.cell_of[i], In, cx, cy, cz);
         // the screen passes pairs up to 1.0001 (2 h)^2; W_ff_shape returns 0 beyond the support
-        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, screen, list, stride,
+        fluid_pairs<D, L, CP>(f, g, In.c0, cx, cy, cz, i, lane, Pi, screen, list, stride, ts,
                           [&](int j) { return f.L4[j]; },
                           [&](int, const float4 &Pj, const float4 &Lj, const float *, float, float ox, float oy,
                               float oz) {
@@ -761,6 +1004,24 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
     f.s[1].drho[i] = drho;
     f.P4[i].w = eos_p(drho, P);
     f.V4[i].w = drho;
+}
+
+template <int D, int L, bool CP, bool TILE>
+__global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
+{
+    extern __shared__ __align__(16) uint8_t s_dyn[];
+    uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
+    const int stride = blockDim.x;
+    if constexpr (!TILE) {
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        reinit_one<D, L, CP>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+    } else {
+        if (!bt.ctl[f.tiles[blockIdx.x].x].reinit) return;   // not a reinitialisation step of this instance
+        tile_loop<D, L>(bt, f, f.L4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
+                        [&](int i, bool act, const TileSrc *ts) {
+                            reinit_one<D, L, CP>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                        });
+    }
 }
 
 int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)

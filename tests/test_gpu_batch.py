@@ -141,20 +141,22 @@ def test_batch_rejects_bad_selection_and_grid_path():
     batch.close()
 
 
-@pytest.mark.parametrize("name,lanes,block,compact", [("channel_flag", 2, 64, 1), ("channel_flag", 4, 128, 0),
-                                                     ("channel_flag", 8, 256, 1), ("channel_flag", 8, 128, 0),
-                                                     ("tiny_box_3d", 4, 128, 0), ("tiny_box_3d", 16, 256, 1),
-                                                     ("tiny_box_3d", 8, 64, 1)])
-def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact):
-    """Each compiled lane count, block size and pair-loop form computes the same step."""
-    case = fc.channel_flag(seed=0) if name == "channel_flag" else fc.tiny_box_3d(seed=1)
+@pytest.mark.parametrize("name,lanes,block,compact,tile", [
+    ("channel_flag", 2, 64, 1, 0), ("channel_flag", 4, 128, 0, 0), ("channel_flag", 8, 256, 1, 0),
+    ("channel_flag", 8, 128, 0, 0), ("tiny_box_3d", 4, 128, 0, 0), ("tiny_box_3d", 16, 256, 1, 0),
+    ("tiny_box_3d", 8, 64, 1, 0), ("channel_flag", 4, 128, 1, 1), ("channel_flag", 2, 256, 0, 1),
+    ("tiny_box_3d", 4, 128, 0, 1), ("tiny_box_3d", 8, 64, 1, 1), ("dam_gate", 4, 128, 1, 1)])
+def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact, tile):
+    """Each compiled lane count, block size, pair-loop form and tile mode computes the same step."""
+    case = {"channel_flag": lambda: fc.channel_flag(seed=0), "tiny_box_3d": lambda: fc.tiny_box_3d(seed=1),
+            "dam_gate": lambda: fc.dam_gate(seed=0, dpF=0.002)}[name]()
     ref = O.OracleSim(case)
     dt, _, dts = ref.suggest_dt()
     K = ref.substeps(dt, dts)
     sim = Simulation.from_case(case)
-    sim.set_tuning(lanes, block, 0, compact)
+    sim.set_tuning(lanes, block, 0, compact, tile)
     t = sim.tuning()
-    assert (t["lanes"], t["block"], t["compact"]) == (lanes, block, compact)
+    assert (t["lanes"], t["block"], t["compact"], t["tile"]) == (lanes, block, compact, tile)
     sim.set_substeps(K)
     sim.step(dt)
     sim.sync()
