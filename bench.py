@@ -393,7 +393,11 @@ def run_learned(args, rank, world, local_rank):
     cons = np.asarray(case.s_cons)
     m = case.s_rho0 * case.s_dp ** d
     st = torch.cuda.Stream(device=dev)
-    n_collect, iters, R = 600, 3000, 32
+    n_collect, iters, R = 800, 6000, 32
+    # residual threshold calibrated to the plain method: one midpoint force
+    # evaluation leaves R = 0.05-0.10 on the plain K-sub-step result of this
+    # workload (oracle), so 0.15 admits network steps no less consistent
+    tol_cal = 0.15
     t0 = time.perf_counter()
     gen = Simulation.from_case(case, stream=st)
     data = learn.collect(gen, n_collect, case.s_r0)
@@ -447,6 +451,9 @@ def run_learned(args, rank, world, local_rank):
         fb_sim = start()
         fb_sim.set_learned(theta, scales, 1e-3)
         fb = timed(fb_sim)
+        cal_sim = start()
+        cal_sim.set_learned(theta, scales, tol_cal)
+        cal = timed(cal_sim)
     clocks = clk.summary()
     disp = np.linalg.norm(plain["tip"] - case.s_r0[case.tip])
 
@@ -508,6 +515,11 @@ def run_learned(args, rank, world, local_rank):
                                     "tip_displacement_error_rel": tip_err(pure),
                                     "steps_timed": pure["steps_ok"], "diverged_after_steps": pure["diverged_after"],
                                     "kernels_per_step": pure["kernels_per_step"]},
+        "learned_calibrated_tol": {"tol": tol_cal, "ms_per_step": cal["ms_per_step"],
+                                   "speedup_vs_plain": plain["ms_per_step"] / cal["ms_per_step"],
+                                   "accepted": cal["accepted"], "rejected": cal["rejected"],
+                                   "last_residual": cal["last_residual"], "tip_displacement_error_rel": tip_err(cal),
+                                   "diverged_after_steps": cal["diverged_after"]},
         "learned_with_fallback": {"ms_per_step": fb["ms_per_step"],
                                   "speedup_vs_plain": plain["ms_per_step"] / fb["ms_per_step"],
                                   "accepted": fb["accepted"], "rejected": fb["rejected"],
