@@ -230,6 +230,19 @@ def run_reference(args, rank):
     print(json.dumps(_clean(line)))
 
 
+def combine_ranks(dev_ms, pairs, simt, dist, device):
+    """Whole-job figures of the replicas: the slowest rank's device time and
+    the work (pairs, simulated seconds) summed over the ranks."""
+    if not dist:
+        return dev_ms, float(pairs), simt
+    import torch
+    t = torch.tensor([dev_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(pairs), simt], device=device, dtype=torch.float64)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p[0].item()), float(p[1].item())
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_1911_13255_gb300 import Simulation
@@ -294,15 +307,7 @@ def run_gpu(args, rank, world, local_rank):
     dev_ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
     pairs = pairs_timed
     simt = simt_timed
-    if dist:
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms_max = float(t.item())
-        p = torch.tensor([float(pairs), simt], device=dev, dtype=torch.float64)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        pairs_all, simt_all = float(p[0].item()), float(p[1].item())
-    else:
-        dev_ms_max, pairs_all, simt_all = dev_ms, float(pairs), simt
+    dev_ms_max, pairs_all, simt_all = combine_ranks(dev_ms, pairs, simt, dist, dev)
     clocks = clk.summary()
 
     # ---- e2e through the public API with pinned host buffers
@@ -341,7 +346,14 @@ def run_gpu(args, rank, world, local_rank):
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
                     "bin_sort": "k_bin_all+k_scan2+k_scatter2+k_cellsort2+k_records_all"}
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+    extra = {}
+    if dom == "solid_substeps" and info1["solid_path"] == 1 and case.dim == 2:
+        # one cluster per body, one CTA of 128 threads per 128 particles: the
+        # kernel can only ever use that many SMs
+        ctas = (max(c.ns for c in cases) + 127) // 128
+        sm_peak = fp32_peak_tflops(sm_mhz, n_sm=min(152, ctas * min(len(cases), 152 // max(ctas, 1))))
+        extra = {"ctas_per_body": ctas, "frac_of_the_sms_it_occupies": achieved / sm_peak}
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak, **extra,
             "traffic": _traffic(kernel_names.get(dom, dom)), "kernel": kernel_names.get(dom, dom),
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,
             "peak_source": ("FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz) if bound == "alu"
