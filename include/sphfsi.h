@@ -253,8 +253,9 @@ typedef struct {
                               2, 4 or 8 in 2-D (default 4); 4, 8 or 16 in 3-D (default 8
                               below 200 000 fluid particles in the context, else 4) */
     int32_t block;         /* threads per block of those loops: 64, 128 (default) or 256 */
-    int32_t solid_variant; /* 0: automatic cluster kernel choice; 1: the four-lane
-                              cluster kernel (sphfsi_set_solid_path 1) */
+    int32_t solid_variant; /* 2-D cluster sub-step kernel: 0 one thread per particle;
+                              1 four lanes per particle (sphfsi_set_solid_path 1);
+                              2 two threads per particle */
     float step_ms;         /* sphfsi_autotune: device ms per step measured for this setting */
     int32_t compact;       /* fluid-fluid pair loops: 0 evaluate each pair inside the
                               candidate loop; 1 first collect each thread's in-support

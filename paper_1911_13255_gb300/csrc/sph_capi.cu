@@ -1330,7 +1330,7 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 1 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
+        t->solid_variant < 0 || t->solid_variant > 2 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
         t->tile > 1)
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
@@ -1442,8 +1442,11 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         if (!rc && c->dim == 2 && c->S.n && !c->S.force_grid_path) {
-            cur.solid_variant = 1;
-            rc = consider(cur);
+            for (int v = 0; v < 3 && !rc; v++) {
+                if (v == best->solid_variant) continue;
+                cur.solid_variant = v;
+                rc = consider(cur);
+            }
         }
     }
     int rc2 = copy_all(false);

@@ -176,7 +176,7 @@ struct Solid {
     unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
     unsigned *queue;          // persistent solid kernel: next instance to take
     int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
-    int force_lane_path;      // 1: in 2-D use the 4-lane cluster kernel, not the one-thread one
+    int force_lane_path;      // 2-D cluster kernel: 0 one thread per particle, 1 four lanes, 2 two threads
     int max_nb;               // largest static neighbour count of a particle
     int max_ns;               // largest body of an instance
     // learned sub-stepper (when learned != 0)

@@ -731,11 +731,26 @@ __device__ __forceinline__ float2 ld_cl2(uint32_t addr)
 
 constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 
-// K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster
+// K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster,
+// LP threads per particle (128 particles per CTA).  With LP = 2 the two
+// threads of a particle (adjacent lanes) split its static neighbour entries
+// (entry u goes to thread u % 2), combine their partial sums with one
+// shuffle, and both carry the particle's own state identically; the first
+// writes it out.  Two threads per particle give each SM sub-partition two
+// warps to interleave in these latency-bound loops.
+template <int LP>
 __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
                                              float4 *sV, unsigned rank)
 {
-    const int g = threadIdx.x;
+    constexpr int NB = kMaxNb2 / LP;                   // entries per thread
+    constexpr int CH = NB < kChunk2 ? NB : kChunk2;    // loads in flight per round
+    const int g = threadIdx.x / LP, sub = threadIdx.x % LP;
+    const bool lead = sub == 0;
+    const unsigned pmask = LP == 1 ? 0xffffffffu : (3u << ((threadIdx.x & 31) & ~1));
+    auto pair_sum = [&](float v) {
+        if constexpr (LP == 2) v += __shfl_xor_sync(pmask, v, 1);
+        return v;
+    };
     const int la = (int)rank * kC1Threads + g;
     const int a = s0 + la;
     const bool own = la < ns;
@@ -749,13 +764,15 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     double x = 0, y = 0, xs = 0, ys = 0, as0 = 0, as1 = 0;
     bool cons = true;
     float vmax = 0.0f, amax = 0.0f;
-    float gx[kMaxNb2], gy[kMaxNb2];
-    uint32_t aQ[kMaxNb2];   // neighbour's sQ slot; its sV slot is at aQ + dV (same layout in every CTA)
+    float4 vown = make_float4(0.f, 0.f, 0.f, 0.f), Qown = vown;   // the particle's v and P B0
+    float gx[NB], gy[NB];
+    uint32_t aQ[NB];   // neighbour's sQ slot; its sV slot is at aQ + dV (same layout in every CTA)
     const uint32_t dV = (uint32_t)__cvta_generic_to_shared(&sV[0]) - (uint32_t)__cvta_generic_to_shared(&sQ[0]);
-    int nn = 0;
+    int nn = 0;   // this thread's entries
     if (own) {
         int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
-        nn = q1 - q0;   // the launcher guarantees nn <= kMaxNb2
+        const int ntot = q1 - q0;   // the launcher guarantees ntot <= kMaxNb2
+        nn = (ntot - sub + LP - 1) / LP;
         for (int i = 0; i < 4; i++) {
             H[i] = s.H[9 * a + i];
             B[i] = s.B0[9 * a + i];
@@ -765,14 +782,15 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         x = xs = s.x[a];
         y = ys = s.y[a];
         cons = s.cons[a] != 0;
-        sV[g] = s.v4[a];
+        vown = s.v4[a];
+        if (lead) sV[g] = vown;
     }
 #pragma unroll
-    for (int u = 0; u < kMaxNb2; u++) {
+    for (int u = 0; u < NB; u++) {
         gx[u] = gy[u] = 0.0f;
         aQ[u] = 0u;
         if (u < nn) {
-            float4 e = s.nb[s.nb_ptr[a] + u];
+            float4 e = s.nb[s.nb_ptr[a] + sub + LP * u];
             int b = __float_as_int(e.w) - s0;   // local index in the body
             gx[u] = e.x;
             gy[u] = e.y;
@@ -783,24 +801,28 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     // Q_a . sum(g) + sum(Q_b . g)
     float sgx = 0.f, sgy = 0.f;
 #pragma unroll
-    for (int u = 0; u < kMaxNb2; u++) {
+    for (int u = 0; u < NB; u++) {
         sgx += gx[u];
         sgy += gy[u];
     }
+    if (own) {
+        sgx = pair_sum(sgx);
+        sgy = pair_sum(sgy);
+    }
     cluster_sync();
 
-    // Two accumulator sets (even / odd neighbour slots) in both loops, so that
-    // a thread has twice as many independent add chains in flight.
+    // Two accumulator sets (even / odd slots) in both loops, so that a thread
+    // has twice as many independent add chains in flight.
     auto rate = [&](float4 va, float *Hd) {
         float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, N3 = 0.f;
 #pragma unroll
-        for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
-            float2 vb[kChunk2];
+        for (int c0 = 0; c0 < NB; c0 += CH) {
+            float2 vb[CH];
 #pragma unroll
-            for (int u = 0; u < kChunk2; u++)
+            for (int u = 0; u < CH; u++)
                 if (c0 + u < nn) vb[u] = ld_cl2(aQ[c0 + u] + dV);
 #pragma unroll
-            for (int u = 0; u < kChunk2; u += 2) {
+            for (int u = 0; u < CH; u += 2) {
                 if (c0 + u < nn) {
                     const float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
                     M0 += dvx * gx[c0 + u];
@@ -808,7 +830,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                     M2 += dvy * gx[c0 + u];
                     M3 += dvy * gy[c0 + u];
                 }
-                if (c0 + u + 1 < nn) {
+                if (u + 1 < CH && c0 + u + 1 < nn) {
                     const float dvx = vb[u + 1].x - va.x, dvy = vb[u + 1].y - va.y;
                     N0 += dvx * gx[c0 + u + 1];
                     N1 += dvx * gy[c0 + u + 1];
@@ -817,10 +839,10 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 }
             }
         }
-        M0 += N0;
-        M1 += N1;
-        M2 += N2;
-        M3 += N3;
+        M0 = pair_sum(M0 + N0);
+        M1 = pair_sum(M1 + N1);
+        M2 = pair_sum(M2 + N2);
+        M3 = pair_sum(M3 + N3);
         Hd[0] = M0 * B[0] + M1 * B[2];
         Hd[1] = M0 * B[1] + M1 * B[3];
         Hd[2] = M2 * B[0] + M3 * B[2];
@@ -829,11 +851,12 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     auto put_Q = [&]() {
         float Q[4];
         stress_QB<2>(H, B, P.mu, P.lam, Q);
-        sQ[g] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        Qown = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        if (lead) sQ[g] = Qown;
     };
 
     if (own) {
-        float4 va = sV[g];
+        const float4 va = vown;
         float Hd[4];
         rate(va, Hd);
         for (int i = 0; i < 4; i++) H[i] = H[i] + hdts * Hd[i];
@@ -847,35 +870,36 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         cluster_sync();
         // (B) force loop and kick
         if (own) {
-            const float4 Qa = sQ[g];
-            float ax = Qa.x * sgx + Qa.y * sgy, ay = Qa.z * sgx + Qa.w * sgy, bx = 0.f, by = 0.f;
+            const float4 Qa = Qown;
+            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
 #pragma unroll
-            for (int c0 = 0; c0 < kMaxNb2; c0 += kChunk2) {
-                float4 qb[kChunk2];
+            for (int c0 = 0; c0 < NB; c0 += CH) {
+                float4 qb[CH];
 #pragma unroll
-                for (int u = 0; u < kChunk2; u++)
+                for (int u = 0; u < CH; u++)
                     if (c0 + u < nn) qb[u] = ld_cl(aQ[c0 + u]);
 #pragma unroll
-                for (int u = 0; u < kChunk2; u += 2) {
+                for (int u = 0; u < CH; u += 2) {
                     if (c0 + u < nn) {
                         ax += qb[u].x * gx[c0 + u] + qb[u].y * gy[c0 + u];
                         ay += qb[u].z * gx[c0 + u] + qb[u].w * gy[c0 + u];
                     }
-                    if (c0 + u + 1 < nn) {
+                    if (u + 1 < CH && c0 + u + 1 < nn) {
                         bx += qb[u + 1].x * gx[c0 + u + 1] + qb[u + 1].y * gy[c0 + u + 1];
                         by += qb[u + 1].z * gx[c0 + u + 1] + qb[u + 1].w * gy[c0 + u + 1];
                     }
                 }
             }
-            ax += bx;
-            ay += by;
+            ax = Qa.x * sgx + Qa.y * sgy + pair_sum(ax + bx);
+            ay = Qa.z * sgx + Qa.w * sgy + pair_sum(ay + by);
             if (!cons) {
-                float4 v = sV[g];
+                float4 v = vown;
                 float av0 = ax * inv_rhoS + fF[0] * inv_mS + P.g[0];
                 float av1 = ay * inv_rhoS + fF[1] * inv_mS + P.g[1];
                 v.x += dts * av0;
                 v.y += dts * av1;
-                sV[g] = v;
+                vown = v;
+                if (lead) sV[g] = v;
                 as0 += dtsd * (double)av0;
                 as1 += dtsd * (double)av1;
                 amax = fmaxf(amax, av0 * av0 + av1 * av1);
@@ -886,7 +910,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         // (C) deformation rate at v^{k+1}; second half drift; next first half + stress
         if (own) {
             const bool more = kk + 1 < K;
-            float4 va = sV[g];
+            const float4 va = vown;
             float Hd[4];
             rate(va, Hd);
             // second half drift of this sub-step and, unless it is the last,
@@ -901,9 +925,9 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             if (more) put_Q();
         }
     }
-    if (own) {
+    if (own && lead) {
         for (int i = 0; i < 4; i++) s.H[9 * a + i] = H[i];
-        s.v4[a] = sV[g];
+        s.v4[a] = vown;
         s.x[a] = x;
         s.y[a] = y;
         const double idt = 1.0 / dt;
@@ -922,7 +946,8 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     cluster_sync();
 }
 
-__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Batch bt, Solid s)
+template <int LP>
+__global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, Solid s)
 {
     __shared__ float4 sQ[kC1Threads];
     __shared__ float4 sV[kC1Threads];
@@ -932,17 +957,19 @@ __global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d(Batch bt, Solid 
         const int b = next_instance(s.queue, &s_inst, rank);
         if (b >= bt.B) break;
         const Inst &In = bt.I[b];
-        solid2d_body(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
+        solid2d_body<LP>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
     }
 }
 
 // single instance: one cluster, constants in the parameter space (the
 // persistent kernel's global-memory constants cost registers)
-__global__ void __launch_bounds__(kC1Threads) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P, Ctl *ctl)
+template <int LP>
+__global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
+                                                                         Ctl *ctl)
 {
     __shared__ float4 sQ[kC1Threads];
     __shared__ float4 sV[kC1Threads];
-    solid2d_body(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
+    solid2d_body<LP>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
 }
 
 // Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
@@ -991,12 +1018,17 @@ static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, 
 
 static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
 {
-    static int mc2d[2][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
+    static int mc2d[4][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
     const bool one = bt.B == 1;
-    if (dim == 2 && !s.force_lane_path && s.max_nb <= kMaxNb2) {
+    if (dim == 2 && s.force_lane_path != 1 && s.max_nb <= kMaxNb2) {
         const int ctas = (s.max_ns + kC1Threads - 1) / kC1Threads;
-        int rc = one ? launch_clusters(k_solid_cluster2d_one, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
-                     : launch_persistent(k_solid_cluster2d, kC1Threads, ctas, bt, s, mc2d[1], st);
+        int rc;
+        if (s.force_lane_path == 2)   // two threads per particle
+            rc = one ? launch_clusters(k_solid_cluster2d_one<2>, 2 * kC1Threads, ctas, 1, mc2d[2], st, s, P0, bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<2>, 2 * kC1Threads, ctas, bt, s, mc2d[3], st);
+        else
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1>, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<1>, kC1Threads, ctas, bt, s, mc2d[1], st);
         if (rc <= 0) return rc;
     }
     const int ctas = (s.max_ns + kPPC - 1) / kPPC;

@@ -197,3 +197,46 @@ def test_autotune_leaves_the_state_unchanged_and_keeps_parity():
         assert rel(g["r"], h["r"]) < 1e-9 and rel(g["v"], h["v"]) < 1e-4
     batch.close()
     ref.close()
+
+
+@pytest.mark.parametrize("name", ["dam_gate", "channel_flag", "floating_block"])
+def test_two_thread_solid_kernel_matches_the_oracle(name):
+    """The 2-D cluster sub-step kernel with two threads per particle."""
+    case = {"dam_gate": lambda: fc.dam_gate(seed=0), "channel_flag": lambda: fc.channel_flag(seed=0),
+            "floating_block": lambda: fc.floating_block(seed=1)}[name]()
+    ref = O.OracleSim(case)
+    dt, _, dts = ref.suggest_dt()
+    K = ref.substeps(dt, dts)
+    sim = Simulation.from_case(case)
+    sim.set_tuning(4, 128, 2)
+    assert sim.tuning()["solid_variant"] == 2
+    sim.set_substeps(K)
+    s_r0 = np.array(case.s_r0)
+    sim.step(dt)
+    sim.sync()
+    ref.step(dt, K)
+    s = sim.get_solid()
+    e = dict(v=rel(s["v"], ref.s_v), F=rel(s["F"] - np.eye(2), ref.s_F - np.eye(2)), abar=rel(s["abar"], ref.s_abar),
+             dr=rel(s["r"] - s_r0, ref.s_r - s_r0))
+    assert max(e.values()) < ACC_TOL, e
+
+
+def test_two_thread_solid_kernel_batch_equals_single():
+    cases = _mixed_cases()
+    batch = Simulation.from_cases(cases)
+    batch.set_tuning(4, 128, 2)
+    for _ in range(6):
+        batch.step(0.0)
+    batch.sync()
+    for b, case in enumerate(cases):
+        single = Simulation.from_case(case)
+        single.set_tuning(4, 128, 2)
+        for _ in range(6):
+            single.step(0.0)
+        single.sync()
+        if case.ns:
+            want, got = single.get_solid(), batch.select(b).get_solid()
+            for k in want:
+                assert np.array_equal(got[k], want[k]), (b, k)
+        single.close()
+    batch.close()
