@@ -539,7 +539,7 @@ def run_learned(args, rank, world, local_rank):
         "training": {"loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean()),
                      "collect_s": t_collect, "train_s": t_train},
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16_tflops"], "traffic": None, "kernel": "k_gemm_bf16",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": _traffic("k_gemm_bf16"), "kernel": "k_gemm_bf16",
                      "shape": [M_, 128, 128 * (2 + d)], "ms_per_launch": gemm_ms,
                      "peak_source": f"{src} bf16_tflops (burst)"},
         "cpu_baseline": None if cb is None else {"value": cb["sim_s_per_wall_s"], "unit": "simulated-s/s",

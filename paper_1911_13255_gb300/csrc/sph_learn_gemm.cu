@@ -19,7 +19,7 @@
 //     (warp w owns TMEM lanes 32w..32w+31 = tile rows), add the bias and store.
 // Every wait is bounded; a timeout sets a status bit, skips the epilogue and
 // still frees the tensor memory.
-#include <cuda.h>   // CUtensorMap and its enums; the encoder is taken from the driver at run time
+#include <cuda.h>   // CUtensorMap and its enums; the encoder comes from the CUDA driver library at run time
 #include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
