@@ -345,7 +345,7 @@ def run_gpu(args, rank, world, local_rank):
                         2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
-                    "bin_sort": "k_bin_all+k_scan2+k_scatter2+k_cellsort2+k_records_all"}
+                    "bin_sort": "k_bin_all+k_scan_seg+k_scatter2+k_cell_records"}
     extra = {}
     if dom == "solid_substeps" and info1["solid_path"] == 1 and case.dim == 2:
         # one cluster per body, one CTA of 128 threads per 128 particles: the
@@ -370,7 +370,7 @@ def run_gpu(args, rank, world, local_rank):
                    "dp_F": case.f_dp, "dp_S": case.s_dp,
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
-                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile")},
+                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows")},
                    "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -593,7 +593,8 @@ def e2e_run(cases, dev, steps, tuning):
         if c.inflow_on:
             sim.set_inflow(1, c.inflow_profile, c.inflow_width, c.inflow_y0, c.inflow_H, c.inflow_U, c.inflow_tramp)
     sim.finalize()
-    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"])
+    sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"],
+                   tuning["records"], tuning["rows"])
     p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)
@@ -615,7 +616,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_gate", choices=sorted(WORKLOADS))
-    ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact]: fixed launch shape instead "
+    ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact[,tile[,records[,rows]]]]: fixed launch shape instead "
                                                  "of the autotuner (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -230,14 +230,13 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path);
 /* Per-stage device timing.  With on != 0 every later step records CUDA
  * events on the context stream at its stage boundaries (also inside the
  * captured graph of sphfsi_run).  sphfsi_stage_times waits for the stream
- * and writes the durations in ms of the last step's 8 stages into ms[0..7]:
- * 0 control + normal update, 1 fluid drift + fluid and solid binning and
- * sort, 2 density
- * reinitialisation, 3 momentum (a4), 4 solid-side coupling force (a5),
- * 5 continuity + drift (a6), 6 solid sub-steps (a7, a8), 7 finish.  Stages
- * 4 and 6 run on a side stream concurrently with stages 3 and 5; finish
- * follows the join of both streams.
- * Returns the number of stages, SPHFSI_E_INVAL if n < 8, SPHFSI_E_STATE if
+ * and writes the durations in ms of the last step's 7 stages into ms[0..6]:
+ * 0 step control, normal update, fluid drift, fluid and solid binning, sort
+ * and records, 1 density reinitialisation, 2 momentum (a4), 3 solid-side
+ * coupling force (a5), 4 continuity + drift (a6), 5 solid sub-steps (a7,
+ * a8), 6 finish.  Stages 3 and 5 run on a side stream concurrently with
+ * stages 2 and 4; finish follows the join of both streams.
+ * Returns the number of stages, SPHFSI_E_INVAL if n < 7, SPHFSI_E_STATE if
  * profiling is off. */
 int sphfsi_set_profiling(sphfsi_ctx *c, int on);
 int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n);
@@ -265,6 +264,15 @@ typedef struct {
                               over the whole grid; 1 one block per tile of grid cells (16 of a
                               row in 2-D, 4 in 3-D) whose neighbour records are first staged in
                               shared memory by bulk copies (default 0) */
+    int32_t records;       /* binning: 0 a group of lanes per non-empty cell ranks the cell's
+                              entries and writes their records; 1 the groups only rank, then
+                              one thread per slot writes the records (one more launch; default
+                              1 from 262 144 particles in the context, else 0) */
+    int32_t rows;          /* fluid pair loops without tiles: 0 visit the neighbour cells one at a
+                              time; 1 a row of three cells at a time, the cell starts of the row
+                              (fluid, walls, solid) loaded together: fewer dependent loads, a few
+                              more instructions per candidate (default 1 below 262 144 particles
+                              in the context, else 0) */
 } sphfsi_tuning;
 
 /* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */
@@ -275,8 +283,9 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t);
  * workload: for each candidate setting, `steps` graph-replayed steps of size
  * dt_F (as sphfsi_run) to warm up, then `steps` timed with CUDA events.  The
  * search goes over the lane count (block 128), then the pair-loop form,
- * then tiles on or off, then the block size, then (2-D with a solid) the
- * solid kernel variant, keeping the fastest of each.
+ * then tiles on or off, then the row form, then the block size, then the
+ * records form, then (2-D with a solid) the solid kernel variant, keeping the
+ * fastest of each.
  * Every device allocation of the context is saved before and restored after
  * each trial and at the end, so the simulation state, time and counters are
  * exactly as before the call; the best setting stays selected and is

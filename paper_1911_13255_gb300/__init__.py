@@ -57,7 +57,7 @@ class Info(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("block", C.c_int32), ("solid_variant", C.c_int32), ("step_ms", C.c_float),
-                ("compact", C.c_int32), ("tile", C.c_int32)]
+                ("compact", C.c_int32), ("tile", C.c_int32), ("records", C.c_int32), ("rows", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -286,10 +286,17 @@ class Simulation:
         _check(lib().sphfsi_autotune(self.h, float(dt), int(steps), C.byref(t)), "sphfsi_autotune")
         return t.as_dict()
 
-    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0):
+    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0, records=None, rows=None):
+        """Launch shape (include/sphfsi.h, sphfsi_tuning); records and rows
+        default to the current setting (rows is 0 with tiles)."""
         if compact is None:
             compact = 1 if self.dim == 2 else 0
-        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact), int(tile))
+        cur = self.tuning()
+        if records is None:
+            records = cur["records"]
+        if rows is None:
+            rows = 0 if tile else cur["rows"]
+        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact), int(tile), int(records), int(rows))
         _check(lib().sphfsi_set_tuning(self.h, C.byref(t)), "sphfsi_set_tuning")
 
     def tuning(self):
@@ -386,7 +393,7 @@ class Simulation:
         _check(lib().sphfsi_get_info(self.h, C.byref(i)), "sphfsi_get_info")
         return i.as_dict()
 
-    STAGES = ("control", "bin_sort", "reinit", "momentum", "solid_fluid_force",
+    STAGES = ("bin_sort", "reinit", "momentum", "solid_fluid_force",
               "continuity", "solid_substeps", "finish")
 
     def set_solid_path(self, path):
@@ -398,8 +405,8 @@ class Simulation:
 
     def stage_times(self):
         """Device ms of the last step's stages (needs set_profiling(True))."""
-        ms = np.zeros(8, np.float32)
-        rc = lib().sphfsi_stage_times(self.h, _ptr(ms), 8)
+        ms = np.zeros(len(self.STAGES), np.float32)
+        rc = lib().sphfsi_stage_times(self.h, _ptr(ms), len(self.STAGES))
         if rc < 0:
             _check(rc, "sphfsi_stage_times")
         return dict(zip(self.STAGES, ms.tolist()))

@@ -59,10 +59,11 @@ struct sphfsi_ctx {
     int graph_prof = -1;
     int solid_path = 0;
     int last_status = 0;
-    // per-stage CUDA events (sphfsi_set_profiling): start, control, binning,
-    // reinit, momentum, continuity (main stream); branch start, coupling
-    // force done, sub-steps done (side stream); end of step
-    static constexpr int kStages = 8;
+    // per-stage CUDA events (sphfsi_set_profiling), by index: 0 start, 2
+    // binning, 3 reinit, 5 momentum, 6 continuity (main stream); 4 branch
+    // start, 7 coupling force done, 8 sub-steps done (side stream); 9 end of
+    // step (1 is unused)
+    static constexpr int kStages = 7;
     static constexpr int kEvents = 10;
     bool profiling = false;
     cudaEvent_t ev[kEvents] = {};
@@ -176,12 +177,10 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     cudaStream_t st = c->st;
     const int D = c->dim;
     TRY(mark(c, 0));
-    // dt_F, K, reinit flag per instance; a3 normal update before the solid records
-    TRY(launch_control_normals(c->bt, c->S, dt > 0.0 ? dt : 0.0, c->K_fixed, D, st));
-    TRY(mark(c, 1));
+    // step control (dt_F, K, reinit flag per instance), a3 normal update,
     // a1 + a2: inflow, fluid first half drift; fluid (r^{n+1/2}) and solid
     // (r^n) binning, counting sort and FP32 records
-    TRY(launch_bin_all(c->bt, c->F, c->S, D, 1, st));
+    TRY(launch_bin_all(c->bt, c->F, c->S, D, 1, dt > 0.0 ? dt : 0.0, c->K_fixed, st));
     TRY(mark(c, 2));
     // a3: density reinitialisation (no-op on other steps)
     TRY(launch_reinit(c->bt, c->F, c->W, c->S, D, st));
@@ -212,7 +211,8 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_finish(c->bt, c->S.learned, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
-    c->kernels_per_step = 11 + (c->S.n ? 2 : 0) + (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
+    c->kernels_per_step = 4 + bin_kernels(c->F) + (c->S.n ? 2 : 0) +
+                          (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
     return cuda_rc(cudaGetLastError());
 }
 
@@ -592,6 +592,11 @@ int sphfsi_finalize(sphfsi_ctx *c)
     F.block = 128;
     F.compact = D == 2 ? 1 : 0;
     F.tile = 0;
+    // records from the cell groups for small problems (one launch fewer),
+    // one thread per slot for large ones (no idle lanes)
+    F.split_records = nf + ns >= 262144 ? 1 : 0;
+    // neighbour cells a row at a time where latency, not issue, bounds the loops
+    F.rows = nf + ns < 262144 ? 1 : 0;
     // tiles: T cells of a grid row per block (16 in 2-D, 4 in 3-D); the
     // staging area holds about three times the mean neighbourhood
     {
@@ -631,11 +636,12 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &F.dvdt, (size_t)nf * D));
     TRY(dalloc(c, &F.key, nf));
     TRY(dalloc(c, &F.perm, nf));
+    TRY(dalloc(c, &F.sperm, nf));
     TRY(dalloc(c, &F.cell_of, nf));
     TRY(dalloc(c, &F.cstart, (size_t)ncell + 1));
     TRY(dalloc(c, &F.ccount, ncell));
-    TRY(dalloc(c, &F.big, 2 * (size_t)ncell));
-    TRY(dalloc(c, &F.nbig, 1));
+    TRY(dalloc(c, &F.live, 2 * (size_t)ncell));
+    TRY(dalloc(c, &F.nlive, 1));
     // ---- walls
     Walls &W = c->W;
     W.n = (int)nw;
@@ -690,6 +696,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &S.L4, ns));
     TRY(dalloc(c, &S.key, ns));
     TRY(dalloc(c, &S.perm, ns));
+    TRY(dalloc(c, &S.sperm, ns));
     TRY(dalloc(c, &S.cell_of, ns));
     TRY(dalloc(c, &S.cstart, (size_t)ncell + 1));
     TRY(dalloc(c, &S.ccount, ncell));
@@ -765,9 +772,9 @@ int sphfsi_finalize(sphfsi_ctx *c)
             }
             Ctl &ct = hctl[b];
             std::memset(&ct, 0, sizeof(ct));
-            float vmf = (float)vmax, vsf = (float)vs;
-            std::memcpy(&ct.vmaxF, &vmf, 4);
-            std::memcpy(&ct.vmaxS, &vsf, 4);
+            // the first step's dt_F and K come from the initial velocities
+            ct.prev_vmaxF = (float)vmax;
+            ct.prev_vmaxS = (float)vs;
             ct.n_reinit = h.prm.n_reinit;
             hinst[b] = h.d;
         }
@@ -1231,13 +1238,10 @@ int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out)
     out->pairs_sf = (int64_t)hc.n_sf;
     out->pairs_ss = (int64_t)h.d.nnz;
     out->pairs_total = (int64_t)hc.pairs_total;
-    float f;
-    std::memcpy(&f, &hc.vmaxF, 4);
-    out->vmax_f = f;
-    std::memcpy(&f, &hc.vmaxS, 4);
-    out->vmax_s = f;
-    std::memcpy(&f, &hc.amaxS, 4);
-    out->amax_s = f;
+    // maxima of the last step (the finish kernel moves them to prev_*)
+    out->vmax_f = hc.prev_vmaxF;
+    out->vmax_s = hc.prev_vmaxS;
+    out->amax_s = hc.prev_amaxS;
     for (int k = 0; k < 3; k++) {
         out->mom_fs_fluid[k] = hc.mom_fluid[k];
         out->mom_fs_solid[k] = hc.mom_solid[k];
@@ -1270,7 +1274,7 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
     const InstHost &h = c->ih[c->sel];
     const int64_t nrows = which == 3 ? h.ns : h.nf;
     // bin the current positions (no drift) and build the solid records
-    TRY(launch_bin_all(c->bt, c->F, c->S, c->dim, 0, c->st));
+    TRY(launch_bin_all(c->bt, c->F, c->S, c->dim, 0, 0.0, 0, c->st));
     int *counts = nullptr, *offs = nullptr, *out = nullptr;
     if (cudaMalloc(&counts, sizeof(int) * (nrows + 1)) != cudaSuccess) return SPHFSI_E_NOMEM;
     int rc = launch_debug_pairs(c->bt, c->F, c->W, c->S, c->dim, c->sel, which, counts, nullptr, nullptr, c->st);
@@ -1331,12 +1335,14 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
         t->solid_variant < 0 || t->solid_variant > 2 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
-        t->tile > 1)
+        t->tile > 1 || t->records < 0 || t->records > 1 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
     c->F.compact = t->compact;
     c->F.tile = t->tile;
+    c->F.split_records = t->records;
+    c->F.rows = t->rows;
     c->S.force_lane_path = t->solid_variant;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -1354,6 +1360,8 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
     t->solid_variant = c->S.force_lane_path;
     t->compact = c->F.compact;
     t->tile = c->F.tile;
+    t->records = c->F.split_records;
+    t->rows = c->F.rows;
     t->step_ms = 0.0f;
     return SPHFSI_OK;
 }
@@ -1401,7 +1409,7 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
     };
     best->step_ms = 0.0f;
     if (!rc) {
-        // coordinate search: lanes, then block size, then the 2-D solid kernel variant
+        // coordinate search: lanes, pair form, tiles, rows, block size, records form, 2-D solid variant
         cur = keep;
         cur.solid_variant = 0;
         const int lanes2[3] = {2, 4, 8}, lanes3[3] = {4, 8, 16}, blocks[3] = {64, 128, 256};
@@ -1432,12 +1440,23 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         cur = *best;
         if (!rc) {
             cur.tile = 1 - cur.tile;
+            if (cur.tile) cur.rows = 0;
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc && !cur.tile) {
+            cur.rows = 1 - cur.rows;
             rc = consider(cur);
         }
         cur = *best;
         for (int k = 0; k < 3 && !rc; k++) {
             if (blocks[k] == 128) continue;
             cur.block = blocks[k];
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc) {
+            cur.records = 1 - cur.records;
             rc = consider(cur);
         }
         cur = *best;
@@ -1601,24 +1620,23 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     if (!c->profiling) return SPHFSI_E_STATE;
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     auto el = [&](int a, int b, float *o) { return cuda_rc(cudaEventElapsedTime(o, c->ev[a], c->ev[b])); };
-    // events: 0 start, 1 control, 2 binning, 3 reinit, 5 momentum, 6 continuity
-    // (main stream); 4 branch start, 7 coupling force done, 8 sub-steps done
-    // (side stream); 9 end of step
-    TRY(el(0, 1, &ms[0]));
-    TRY(el(1, 2, &ms[1]));
-    TRY(el(2, 3, &ms[2]));
-    TRY(el(3, 5, &ms[3]));
-    TRY(el(5, 6, &ms[5]));
+    // events: 0 start, 2 binning, 3 reinit, 5 momentum, 6 continuity (main
+    // stream); 4 branch start, 7 coupling force done, 8 sub-steps done (side
+    // stream); 9 end of step
+    TRY(el(0, 2, &ms[0]));
+    TRY(el(2, 3, &ms[1]));
+    TRY(el(3, 5, &ms[2]));
+    TRY(el(5, 6, &ms[4]));
     if (c->S.n) {
         float fin_a = 0.f, fin_b = 0.f;
-        TRY(el(4, 7, &ms[4]));
-        TRY(el(7, 8, &ms[6]));
+        TRY(el(4, 7, &ms[3]));
+        TRY(el(7, 8, &ms[5]));
         TRY(el(6, 9, &fin_a));
         TRY(el(8, 9, &fin_b));
-        ms[7] = fin_a < fin_b ? fin_a : fin_b;
+        ms[6] = fin_a < fin_b ? fin_a : fin_b;
     } else {
-        ms[4] = ms[6] = 0.0f;
-        TRY(el(6, 9, &ms[7]));
+        ms[3] = ms[5] = 0.0f;
+        TRY(el(6, 9, &ms[6]));
     }
     return sphfsi_ctx::kStages;
 }

@@ -18,6 +18,41 @@ namespace sph {
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
 constexpr int kBlock = 128;           // threads per block of the particle kernels
+
+// Programmatic dependent launch.  The per-step kernels are launched with the
+// programmatic stream serialisation attribute (launch_k), so that a kernel's
+// blocks can be made resident while its predecessor in the stream finishes.
+// Each of them begins with pdl_wait() (griddepcontrol.wait: returns once the
+// preceding grid has completed and its memory operations are visible; it
+// returns at once for a kernel launched without the attribute) and then
+// allows its own successor to launch (pdl_trigger).  Nothing of a kernel
+// precedes its pdl_wait().
+constexpr bool kPDL = true;
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter()
+{
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                                   cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = kPDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 constexpr int kMaxBlock = 256;        // largest block of the tunable pair-loop kernels
 constexpr int kSolidBlock = 256;      // threads per block of the cooperative solid kernel
 constexpr long long kSpinLimit = 1ll << 22;   // bounded spin of the grid barrier (~0.5-2 s)
@@ -50,7 +85,7 @@ struct Ctl {
     int status;        // ST_* bits, sticky until read by the host
     int pad0;
     unsigned vmaxF, vmaxS, amaxS, pad1;      // maxima of the current step (float bits)
-    float prev_vmaxF, prev_vmaxS, prev_amaxS, pad2;
+    float prev_vmaxF, prev_vmaxS, prev_amaxS, pad2;   // maxima of the last finished step
     double mom_fluid[3], mom_solid[3];       // FP64 fluid-solid momentum sums
     unsigned long long n_ff, n_fw, n_fs, n_sf;
     unsigned long long pairs_total;
@@ -117,6 +152,8 @@ struct Fluid {
     int block;        // threads per block of the pair loops (tuned)
     int compact;      // 1: fluid-fluid pairs through per-thread in-support lists (tuned)
     int tile;         // 1: one block per tile of cells, neighbours staged in shared memory (tuned)
+    int rows;         // 1: pair loops visit the neighbour cells a row at a time (tuned; not with tile)
+    int split_records;  // 1: binning ranks per cell, then writes records per slot (tuned)
     int4 *tiles;      // (instance, first global cell, cells, 0) per tile
     int ntiles;
     int tile_cap;     // records a block can stage (shared memory: 32 B each)
@@ -128,11 +165,12 @@ struct Fluid {
     float4 *L4;       // rel position - FP32(rel position), written on reinitialisation steps
     float *dvdt;      // n * dim, sorted order (a4 accelerations)
     int *key;         // global cell of each particle (storage order)
-    int *perm;        // sorted slot -> storage slot
+    int *perm;        // the scatter's slot -> storage slot (cell order, arbitrary inside a cell)
+    int *sperm;       // sorted slot -> storage slot (large batches: ranks, then records)
     int *cell_of;     // global cell of each sorted slot
     int *cstart;      // total cells + 1
     int *ccount;      // total cells (histogram / scatter cursor)
-    int *big, *nbig;  // cells (fluid, then solid) with more than 32 entries, for the block sort
+    int *live, *nlive;  // non-empty cells of the step (fluid c, solid ncell + c), listed by the scatter
 };
 
 // Static walls, binned once.
@@ -173,6 +211,7 @@ struct Solid {
     float4 *A4, *VB4, *AB4, *N4;
     float4 *L4;               // rel position - FP32(rel position), written on reinitialisation steps
     int *key, *perm, *cstart, *ccount, *cell_of;
+    int *sperm;                  // sorted slot -> particle (large batches: ranks, then records)
     unsigned *bar;            // grid barrier: [0] arrivals, [1] generation
     unsigned *queue;          // persistent solid kernel: next instance to take
     int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
@@ -267,8 +306,9 @@ __device__ __forceinline__ float dW_F(float r, const Phys &P)
 // host-side launch wrappers (implemented in the .cu files)
 // ---------------------------------------------------------------------------
 // control, binning / counting sort, finish (sph_grid.cu)
-int launch_control_normals(const Batch &bt, const Solid &s, double dt_fixed, int K_fixed, int dim, cudaStream_t st);
-int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int do_drift, cudaStream_t st);
+int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, double dt_fixed, int K_fixed,
+                   cudaStream_t st);
+int bin_kernels(const Fluid &f);
 int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
 int launch_finish(const Batch &bt, int learned, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);

@@ -12,50 +12,53 @@
 namespace sph {
 
 // ---------------------------------------------------------------------------
-// control (one thread per instance) + normal update on reinit steps (one
-// thread per solid particle); the reinit decision is recomputed from the
-// instance's step index, which no thread of this kernel modifies
+// Step control, done by the binning kernel of a step: dt_F, K and the
+// reinitialisation flag of the step from the instance's maxima of the
+// previous step (which the finish kernel moves to prev_*), so that every
+// thread can evaluate it and the leader thread of the instance stores it.
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void k_control_normals(Batch bt, Solid s, double dt_fixed, int K_fixed)
+__device__ __forceinline__ double step_dt(const Phys &P, const Ctl *ctl, double dt_fixed)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < bt.B) {
-        const Phys &P = bt.I[t].P;
-        Ctl *ctl = bt.ctl + t;
-        const int has_solid = bt.I[t].ns > 0;
-        ctl->dt_fixed = dt_fixed;
-        ctl->K_fixed = K_fixed;
-        float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
-        ctl->prev_vmaxF = vF;
-        ctl->prev_vmaxS = vS;
-        ctl->prev_amaxS = aS;
-        ctl->vmaxF = ctl->vmaxS = ctl->amaxS = 0u;
-        double dt = dt_fixed > 0.0 ? dt_fixed : 0.6 * P.hF_d / (P.c0_d + (double)vF);   // Eq. dt-relax
-        int K = 1;
-        if (K_fixed > 0) {
-            K = K_fixed;
-        } else if (has_solid) {
-            double b1 = P.hS_d / (P.cS_d + (double)vS);
-            double b2 = aS > 0.0f ? sqrt(P.hS_d / (double)aS) : 1e300;
-            double dts = 0.6 * (b1 < b2 ? b1 : b2);   // Eq. dts-advection
-            double k = floor(dt / dts) + 1.0;          // kappa = [dt_F / dt_S] + 1
-            K = k > 1e6 ? 1000000 : (int)k;
-        }
-        ctl->dt = dt;
-        ctl->K = K;
-        ctl->dts = dt / (double)K;
-        ctl->reinit = (ctl->n_reinit > 0 && (ctl->step % ctl->n_reinit) == 0) ? 1 : 0;
-        ctl->n_ff = ctl->n_fw = ctl->n_fs = ctl->n_sf = 0ull;
-        for (int k = 0; k < 3; k++) ctl->mom_fluid[k] = ctl->mom_solid[k] = 0.0;
-        ctl->learned_ok = 0;
-        ctl->lnum = ctl->lden = 0.0;
+    return dt_fixed > 0.0 ? dt_fixed : 0.6 * P.hF_d / (P.c0_d + (double)ctl->prev_vmaxF);   // Eq. dt-relax
+}
+
+__device__ __forceinline__ bool step_reinit(const Ctl *ctl)
+{
+    return ctl->n_reinit > 0 && (ctl->step % ctl->n_reinit) == 0;
+}
+
+__device__ void step_control(const Inst &In, Ctl *ctl, double dt_fixed, int K_fixed)
+{
+    const Phys &P = In.P;
+    const double dt = step_dt(P, ctl, dt_fixed);
+    int K = 1;
+    if (K_fixed > 0) {
+        K = K_fixed;
+    } else if (In.ns > 0) {
+        const float vS = ctl->prev_vmaxS, aS = ctl->prev_amaxS;
+        double b1 = P.hS_d / (P.cS_d + (double)vS);
+        double b2 = aS > 0.0f ? sqrt(P.hS_d / (double)aS) : 1e300;
+        double dts = 0.6 * (b1 < b2 ? b1 : b2);   // Eq. dts-advection
+        double k = floor(dt / dts) + 1.0;          // kappa = [dt_F / dt_S] + 1
+        K = k > 1e6 ? 1000000 : (int)k;
     }
-    if (t >= s.n) return;
-    const int a = t;
-    const Ctl *cb = bt.ctl + s.inst[a];
-    if (!(cb->n_reinit > 0 && (cb->step % cb->n_reinit) == 0)) return;
-    // n = normalize(F^-T n0), F^-T = cof(F) / det F   (Alg. 1, normal update)
+    ctl->dt_fixed = dt_fixed;
+    ctl->K_fixed = K_fixed;
+    ctl->dt = dt;
+    ctl->K = K;
+    ctl->dts = dt / (double)K;
+    ctl->reinit = step_reinit(ctl) ? 1 : 0;
+    ctl->n_ff = ctl->n_fw = ctl->n_fs = ctl->n_sf = 0ull;
+    for (int k = 0; k < 3; k++) ctl->mom_fluid[k] = ctl->mom_solid[k] = 0.0;
+    ctl->learned_ok = 0;
+    ctl->lnum = ctl->lden = 0.0;
+}
+
+// normal update n = normalize(F^-T n0), F^-T = cof(F) / det F (Alg. 1, on
+// reinitialisation steps)
+template <int D>
+__device__ void update_normal(const Solid &s, int a)
+{
     const float *Hm = s.H + 9 * a;
     float F[9];
     for (int i = 0; i < 9; i++) F[i] = Hm[i];
@@ -86,23 +89,21 @@ __global__ void k_control_normals(Batch bt, Solid s, double dt_fixed, int K_fixe
     s.nrm[3 * a + 2] = n[2] * inv;
 }
 
-int launch_control_normals(const Batch &bt, const Solid &s, double dt_fixed, int K_fixed, int dim, cudaStream_t st)
-{
-    int nt = s.n > bt.B ? s.n : bt.B;
-    int nb = (nt + kBlock - 1) / kBlock;
-    if (dim == 2) k_control_normals<2><<<nb, kBlock, 0, st>>>(bt, s, dt_fixed, K_fixed);
-    else k_control_normals<3><<<nb, kBlock, 0, st>>>(bt, s, dt_fixed, K_fixed);
-    return cudaGetLastError() == cudaSuccess ? 0 : -3;
-}
-
-// finish: time, step, pair counters, non-finite check (one thread per instance)
+// finish: time, step, pair counters, non-finite check, maxima for the next
+// step's control (one thread per instance)
 __global__ void k_finish(Batch bt, int learned)
 {
+    pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= bt.B) return;
     Ctl *ctl = bt.ctl + b;
     float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
     if (!(vF <= 3.0e38f) || !(vS <= 3.0e38f) || !(aS <= 3.0e38f)) ctl->status |= ST_NONFINITE;
+    // the maxima of this step set the next step's dt_F and K
+    ctl->prev_vmaxF = vF;
+    ctl->prev_vmaxS = vS;
+    ctl->prev_amaxS = aS;
+    ctl->vmaxF = ctl->vmaxS = ctl->amaxS = 0u;
     unsigned long long fl = ctl->n_ff + ctl->n_fw + ctl->n_fs;
     const unsigned long long nnz = (unsigned long long)bt.I[b].nnz;
     unsigned long long p = 2ull * fl + ctl->n_sf + (ctl->reinit ? fl : 0ull);
@@ -123,7 +124,7 @@ __global__ void k_finish(Batch bt, int learned)
 
 int launch_finish(const Batch &bt, int learned, cudaStream_t st)
 {
-    k_finish<<<(bt.B + kBlock - 1) / kBlock, kBlock, 0, st>>>(bt, learned);
+    launch_k(k_finish, (bt.B + kBlock - 1) / kBlock, kBlock, 0, st, bt, learned);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -151,21 +152,29 @@ __device__ __forceinline__ int global_key(const Inst &In, double x, double y, do
     return In.c0 + cx + g.nc[0] * (cy + g.nc[1] * cz);
 }
 
+// With step = 1 (a coarse step) the kernel also does the step control: one
+// leader thread per instance (after the particles' threads) stores dt_F, K
+// and the reinitialisation flag and clears the step's counters; the fluid
+// threads evaluate the same dt_F themselves, the solid threads update their
+// normals on reinitialisation steps.  Thread 0 clears the list of non-empty
+// cells that the scatter fills.
 template <int D>
-__global__ void k_bin_all(Batch bt, Fluid f, Solid s, int do_drift)
+__global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
 {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *f.nlive = 0;
     if (t < f.n) {
         const int i = t;
         const int b = f.inst[i];
         const Inst &In = bt.I[b];
         FluidState S = f.s[0];
         double x = S.x[i], y = S.y[i], z = D == 3 ? S.z[i] : 0.0;
-        if (do_drift) {
+        if (step) {
             const Phys &P = In.P;
             const Grid &g = In.g;
             const Ctl *ctl = bt.ctl + b;
-            double dt = ctl->dt, tm = ctl->t;
+            const double dt = step_dt(P, ctl, dt_fixed), tm = ctl->t;
             float vx = S.vx[i], vy = S.vy[i], vz = D == 3 ? S.vz[i] : 0.0f;
             if (P.inflow_on && x >= g.x_lo && x < g.x_lo + P.in_w) {   // inflow buffer (reading R18)
                 vx = (float)inflow_u(P, y, tm);
@@ -193,76 +202,87 @@ __global__ void k_bin_all(Batch bt, Fluid f, Solid s, int do_drift)
         atomicAdd(&f.ccount[key], 1);
     } else if (t < f.n + s.n) {
         const int a = t - f.n;
-        int key = global_key<D>(bt.I[s.inst[a]], s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0);
+        const int b = s.inst[a];
+        if (step && step_reinit(bt.ctl + b)) update_normal<D>(s, a);
+        int key = global_key<D>(bt.I[b], s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0);
         s.key[a] = key;
         atomicAdd(&s.ccount[key], 1);
+    } else if (step && t < f.n + s.n + bt.B) {
+        const int b = t - f.n - s.n;
+        step_control(bt.I[b], bt.ctl + b, dt_fixed, K_fixed);
     }
 }
 
 // ---------------------------------------------------------------------------
 // exclusive scan of the cell histograms, one block per (instance, set):
 // set 0 fluid, 1 solid, 2 walls; the cells of instance b are [c0, c0+ncell)
-// and its slots start at f0 / s0 / w0.  Tiles of 8192 cells are loaded and
-// stored coalesced through shared memory.
+// and its slots start at f0 / s0 / w0.  A tile is 24 rows of 32 cells per
+// warp (24 576 cells per block of 1024 threads): the rows are loaded
+// coalesced and all at once, scanned with warp shuffles, then offset by the
+// scanned warp totals.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
-constexpr int kTile = 8 * kScanThreads;
+constexpr int kScanRows = 24;
+constexpr int kTile = kScanRows * kScanThreads;
 
-// returns base + the sum of the counts (to every thread)
+// returns base + the sum of the counts (to every thread); count may alias
+// count_in: each thread writes only the cells it has read
 __device__ int scan_cells(const int *count_in, int *count, int *start, int n, int base)
 {
-    __shared__ int sm[kTile];
-    __shared__ int warp_tot[32];
-    __shared__ int carry;
+    __shared__ int warp_off[32];
+    __shared__ int tile_sum;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t == 0) carry = base;
-    __syncthreads();
+    int carry = base;
     for (int b0 = 0; b0 < n; b0 += kTile) {
+        const int w0 = b0 + w * 32 * kScanRows;
+        int ex[kScanRows];
+        int run = 0;
+        if (w0 < n) {   // warp-uniform: a warp past the end has nothing to scan
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int i = b0 + j * kScanThreads + t;
-            sm[j * kScanThreads + t] = i < n ? count_in[i] : 0;
-        }
-        __syncthreads();
-        int v[8], loc = 0;
+            for (int r = 0; r < kScanRows; r++) {
+                const int i = w0 + r * 32 + lane;
+                ex[r] = i < n ? count_in[i] : 0;
+            }
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            v[j] = sm[t * 8 + j];
-            loc += v[j];
+            for (int r = 0; r < kScanRows; r++) {
+                const int v = ex[r];
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += u;
+                }
+                ex[r] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
         }
-        int incl = loc;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        if (lane == 31) warp_tot[w] = incl;
+        if (lane == 0) warp_off[w] = run;
         __syncthreads();
         if (w == 0) {
-            int x = warp_tot[lane], xi = x;
+            const int x = warp_off[lane];
+            int xi = x;
+#pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, xi, o);
+                const int u = __shfl_up_sync(0xffffffffu, xi, o);
                 if (lane >= o) xi += u;
             }
-            warp_tot[lane] = xi - x;
+            warp_off[lane] = xi - x;
+            if (lane == 31) tile_sum = xi;
         }
         __syncthreads();
-        int run = carry + warp_tot[w] + incl - loc;
+        const int off = carry + warp_off[w];
+        if (w0 < n) {
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            sm[t * 8 + j] = run;
-            run += v[j];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int i = b0 + j * kScanThreads + t;
-            if (i < n) {
-                start[i] = sm[j * kScanThreads + t];
-                count[i] = 0;   // the histogram becomes the scatter cursor
+            for (int r = 0; r < kScanRows; r++) {
+                const int i = w0 + r * 32 + lane;
+                if (i < n) {
+                    start[i] = off + ex[r];
+                    count[i] = 0;   // the histogram becomes the scatter cursor
+                }
             }
         }
-        if (t == kScanThreads - 1) carry = run;
-        __syncthreads();
+        carry += tile_sum;
+        __syncthreads();   // warp_off and tile_sum are rewritten by the next tile
     }
     return carry;
 }
@@ -271,6 +291,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_seg(Batch bt, int *fcount
                                                            int *sstart, int ns, int *wcount, int *wstart, int nw,
                                                            int set0)
 {
+    pdl_enter();
     const int b = blockIdx.x % bt.B, set = set0 + blockIdx.x / bt.B;
     const Inst &In = bt.I[b];
     int *count = set == 0 ? fcount : (set == 1 ? scount : wcount);
@@ -280,21 +301,39 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_seg(Batch bt, int *fcount
     if (b == bt.B - 1 && threadIdx.x == 0) start[bt.ncell] = set == 0 ? nf : (set == 1 ? ns : nw);
 }
 
-__global__ void k_scatter2(Fluid f, Solid s)
+// Scatter into the cells' slot ranges (arbitrary order inside a cell); with
+// list_cells the particle that opens a cell appends it to the list of
+// non-empty cells (fluid cell c as c, solid cell c as ncell + c), one atomic
+// per warp (on one counter: for small problems only).
+__global__ void k_scatter2(Fluid f, Solid s, int ncell, int list_cells)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int opened = -1;
     if (t < f.n) {
-        int k = f.key[t];
-        f.perm[f.cstart[k] + atomicAdd(&f.ccount[k], 1)] = t;
+        const int k = f.key[t];
+        const int q = atomicAdd(&f.ccount[k], 1);
+        f.perm[f.cstart[k] + q] = t;
+        if (q == 0) opened = k;
     } else if (t < f.n + s.n) {
-        int a = t - f.n;
-        int k = s.key[a];
-        s.perm[s.cstart[k] + atomicAdd(&s.ccount[k], 1)] = a;
+        const int a = t - f.n;
+        const int k = s.key[a];
+        const int q = atomicAdd(&s.ccount[k], 1);
+        s.perm[s.cstart[k] + q] = a;
+        if (q == 0) opened = ncell + k;
     }
+    if (!list_cells) return;
+    const unsigned m = __ballot_sync(0xffffffffu, opened >= 0);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    int base = 0;
+    if (lane == lead) base = atomicAdd(f.nlive, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, lead);
+    if (opened >= 0) f.live[base + __popc(m & ((1u << lane) - 1u))] = opened;
 }
 
-// per-cell insertion sort by particle id (fluid) or slot (solid, walls), and
-// the cursor reset for the next binning
+// per-cell insertion sort by slot (walls, binned once), and the cursor reset
+// for the next binning
 __device__ __forceinline__ void sort_cell(int a, int b, int *perm, const int *id)
 {
     for (int i = a + 1; i < b; i++) {
@@ -309,85 +348,6 @@ __device__ __forceinline__ void sort_cell(int a, int b, int *perm, const int *id
             j--;
         }
         perm[j + 1] = v;
-    }
-}
-
-// Canonical order inside every cell (the scatter's atomics leave it
-// arbitrary): fluid entries by original id, solid entries by slot.  Keys are
-// unique in a cell, so an entry's place is the number of smaller keys.
-// Pass 1: a group of G lanes per cell (fluid cells, then solid cells); cells
-// of up to G entries are ranked in registers with shuffles, larger ones are
-// listed for pass 2, where blocks rank them in shared memory.  G = 16 in 2-D
-// (about 7 fluid particles per cell), 32 in 3-D (about 18).
-constexpr int kBigCellCap = 4096;
-
-template <int G>
-__global__ void k_cellsort_group(Fluid f, Solid s, int ncell, int *big, int *nbig)
-{
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = (int)(t / G), lane = threadIdx.x % G;
-    const int total = (s.n ? 2 : 1) * ncell;
-    const bool valid = w < total;
-    const bool fl = w < ncell;
-    const int c = fl ? w : w - ncell;
-    int *perm = fl ? f.perm : s.perm;
-    const int *id = fl ? f.s[0].id : nullptr;
-    int a = 0, n = 0;
-    if (valid) {
-        const int *cs = fl ? f.cstart : s.cstart;
-        if (lane == 0) (fl ? f.ccount : s.ccount)[c] = 0;
-        a = cs[c];
-        n = cs[c + 1] - a;
-        if (n > G) {
-            if (lane == 0) big[atomicAdd(nbig, 1)] = w;
-            n = 0;
-        }
-    }
-    // every lane of the warp runs the shuffle loop up to the warp's largest cell
-    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
-    if (nmax <= 1) return;
-    const bool mine = lane < n;
-    const int v = mine ? perm[a + lane] : 0;
-    const int kv = mine ? (id ? id[v] : v) : 0x7fffffff;
-    int rank = 0;
-    for (int k = 0; k < nmax; k++) {
-        const int kk = __shfl_sync(0xffffffffu, kv, k, G);
-        rank += (k < n && kk < kv) ? 1 : 0;
-    }
-    __syncwarp();
-    if (mine && n > 1) perm[a + rank] = v;
-}
-
-__global__ void __launch_bounds__(256) k_cellsort_big(Fluid f, Solid s, int ncell, const int *big, const int *nbig)
-{
-    __shared__ int keys[kBigCellCap], vals[kBigCellCap];
-    const int nb = *nbig;
-    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
-        const int w = big[t];
-        const bool fl = w < ncell;
-        const int c = fl ? w : w - ncell;
-        int *perm = fl ? f.perm : s.perm;
-        const int *id = fl ? f.s[0].id : nullptr;
-        const int *cs = fl ? f.cstart : s.cstart;
-        const int a = cs[c], n = cs[c + 1] - a;
-        if (n > kBigCellCap) {   // beyond the shared-memory stage: one thread, in place
-            if (threadIdx.x == 0) sort_cell(a, a + n, perm, id);
-            __syncthreads();
-            continue;
-        }
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int v = perm[a + k];
-            vals[k] = v;
-            keys[k] = id ? id[v] : v;
-        }
-        __syncthreads();
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int kv = keys[k];
-            int r = 0;
-            for (int m = 0; m < n; m++) r += keys[m] < kv;
-            perm[a + r] = vals[k];
-        }
-        __syncthreads();
     }
 }
 
@@ -409,75 +369,172 @@ __device__ __forceinline__ float4 rel_pos(const Inst &In, int gkey, double x, do
     return make_float4(xr, yr, zr, 0.0f);
 }
 
+// Record of fluid slot k (cell order) from storage slot src: the sorted
+// copy of the state in s[1] and the FP32 records the pair loops read.
 template <int D>
-__global__ void k_records_all(Batch bt, Fluid f, Solid s)
+__device__ __forceinline__ void fluid_record(const Batch &bt, const Fluid &f, int k, int src)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < f.n) {
-        const int k = t;
-        FluidState A = f.s[0], B = f.s[1];
-        int src = f.perm[k];
-        const Inst &In = bt.I[f.inst[k]];
-        double x = A.x[src], y = A.y[src], z = D == 3 ? A.z[src] : 0.0;
-        float vx = A.vx[src], vy = A.vy[src], vz = D == 3 ? A.vz[src] : 0.0f;
-        float dr = A.drho[src];
-        B.x[k] = x;
-        B.y[k] = y;
-        B.vx[k] = vx;
-        B.vy[k] = vy;
-        if (D == 3) {
-            B.z[k] = z;
-            B.vz[k] = vz;
+    FluidState A = f.s[0], B = f.s[1];
+    const int b = f.inst[k];
+    const Inst &In = bt.I[b];
+    double x = A.x[src], y = A.y[src], z = D == 3 ? A.z[src] : 0.0;
+    float vx = A.vx[src], vy = A.vy[src], vz = D == 3 ? A.vz[src] : 0.0f;
+    float dr = A.drho[src];
+    B.x[k] = x;
+    B.y[k] = y;
+    B.vx[k] = vx;
+    B.vy[k] = vy;
+    if (D == 3) {
+        B.z[k] = z;
+        B.vz[k] = vz;
+    }
+    B.drho[k] = dr;
+    B.rhodot[k] = A.rhodot[src];
+    B.id[k] = A.id[src];
+    int key = f.key[src];
+    f.cell_of[k] = key;
+    const bool reinit = bt.ctl[b].reinit;
+    float4 lo;
+    float4 r = rel_pos<D>(In, key, x, y, z, reinit ? &lo : nullptr);
+    if (reinit) f.L4[k] = lo;
+    r.w = eos_p(dr, In.P);
+    f.P4[k] = r;
+    f.V4[k] = make_float4(vx, vy, vz, dr);
+}
+
+// Record of solid slot k of the fluid grid from solid particle a (N4.w
+// carries a).
+template <int D>
+__device__ __forceinline__ void solid_record(const Batch &bt, const Solid &s, int k, int a)
+{
+    int key = s.key[a];
+    s.cell_of[k] = key;
+    const int b = s.inst[a];
+    const bool reinit = bt.ctl[b].reinit;
+    float4 lo;
+    s.A4[k] = rel_pos<D>(bt.I[b], key, s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0, reinit ? &lo : nullptr);
+    if (reinit) s.L4[k] = lo;
+    s.VB4[k] = make_float4((float)s.vbar[3 * a], (float)s.vbar[3 * a + 1], (float)s.vbar[3 * a + 2], 0.0f);
+    s.AB4[k] = make_float4((float)s.abar[3 * a], (float)s.abar[3 * a + 1], (float)s.abar[3 * a + 2], 0.0f);
+    s.N4[k] = make_float4(s.nrm[3 * a], s.nrm[3 * a + 1], s.nrm[3 * a + 2], __int_as_float(a));
+}
+
+// Canonical order inside every cell (the scatter's atomics leave it
+// arbitrary) and the records, in one pass over the non-empty cells (listed)
+// or over all cells (fluid, then solid): a group
+// of G lanes per cell ranks the cell's entries by key (fluid: original id,
+// solid: particle index; keys are unique in a cell, so an entry's place is
+// the number of smaller keys) and writes entry e's record to slot
+// start + rank(e).  Entries and keys are compared G at a time through
+// shuffles, so a cell of any size is ranked by the same group (quadratic in
+// its size; about 7 fluid entries per cell in 2-D, 18 in 3-D).  The perm
+// array is only read, so ranking and writing need no ordering.  Every loop
+// bound is uniform over the warp (the largest cell of its groups), as the
+// shuffles require.  G = 16 in 2-D, 32 in 3-D.  REC = false only ranks
+// (sperm[start + rank(e)] = e) and k_records_sorted writes the records with
+// one thread per slot (Fluid::split_records): one launch more, but no idle
+// lanes while writing, which pays for large batches.
+template <int D, int G, bool REC>
+__global__ void __launch_bounds__(256) k_cell_records(Batch bt, Fluid f, Solid s, int listed, int ncells)
+{
+    pdl_enter();
+    const int nlive = listed ? *f.nlive : ncells;
+    const int lane = threadIdx.x % G;
+    const int per_grid = gridDim.x * (blockDim.x / G);
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / G;; w += per_grid) {
+        const bool valid = w < nlive;
+        if (!__any_sync(0xffffffffu, valid)) break;
+        const int e = valid ? (listed ? f.live[w] : w) : 0;
+        const bool fl = e < bt.ncell;
+        const int c = fl ? e : e - bt.ncell;
+        const int *cs = fl ? f.cstart : s.cstart;
+        const int *perm = fl ? f.perm : s.perm;
+        const int *id = fl ? f.s[0].id : nullptr;
+        int a = 0, n = 0;
+        if (valid) {
+            a = cs[c];
+            n = cs[c + 1] - a;
+            if (lane == 0) (fl ? f.ccount : s.ccount)[c] = 0;   // cursor reset for the next binning
         }
-        B.drho[k] = dr;
-        B.rhodot[k] = A.rhodot[src];
-        B.id[k] = A.id[src];
-        int key = f.key[src];
-        f.cell_of[k] = key;
-        const bool reinit = bt.ctl[f.inst[k]].reinit;
-        float4 lo;
-        float4 r = rel_pos<D>(In, key, x, y, z, reinit ? &lo : nullptr);
-        if (reinit) f.L4[k] = lo;
-        r.w = eos_p(dr, In.P);
-        f.P4[k] = r;
-        f.V4[k] = make_float4(vx, vy, vz, dr);
-    } else if (t < f.n + s.n) {
-        const int k = t - f.n;
-        int a = s.perm[k];
-        int key = s.key[a];
-        s.cell_of[k] = key;
-        const int b = s.inst[a];
-        const bool reinit = bt.ctl[b].reinit;
-        float4 lo;
-        s.A4[k] = rel_pos<D>(bt.I[b], key, s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0, reinit ? &lo : nullptr);
-        if (reinit) s.L4[k] = lo;
-        s.VB4[k] = make_float4((float)s.vbar[3 * a], (float)s.vbar[3 * a + 1], (float)s.vbar[3 * a + 2], 0.0f);
-        s.AB4[k] = make_float4((float)s.abar[3 * a], (float)s.abar[3 * a + 1], (float)s.abar[3 * a + 2], 0.0f);
-        s.N4[k] = make_float4(s.nrm[3 * a], s.nrm[3 * a + 1], s.nrm[3 * a + 2], __int_as_float(a));
+        const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+        for (int m0 = 0; m0 < nmax; m0 += G) {
+            const bool mine = m0 + lane < n;
+            const int v = mine ? perm[a + m0 + lane] : 0;
+            const int kv = mine ? (id ? id[v] : v) : 0x7fffffff;
+            int rank = 0;
+            for (int c0 = 0; c0 < nmax; c0 += G) {
+                int ko = kv;
+                if (c0 != m0) {
+                    const bool has = c0 + lane < n;
+                    const int u = has ? perm[a + c0 + lane] : 0;
+                    ko = has ? (id ? id[u] : u) : 0x7fffffff;
+                }
+                const int lim = nmax - c0 < G ? nmax - c0 : G;
+                for (int q = 0; q < lim; q++) rank += __shfl_sync(0xffffffffu, ko, q, G) < kv ? 1 : 0;
+            }
+            if (mine) {
+                if (!REC) (fl ? f.sperm : s.sperm)[a + rank] = v;
+                else if (fl) fluid_record<D>(bt, f, a + rank, v);
+                else solid_record<D>(bt, s, a + rank, v);
+            }
+        }
     }
 }
 
-int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int do_drift, cudaStream_t st)
+template <int D>
+__global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
 {
-    const int nt = f.n + s.n;
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < f.n) fluid_record<D>(bt, f, t, f.sperm[t]);
+    else if (t < f.n + s.n) solid_record<D>(bt, s, t - f.n, s.sperm[t - f.n]);
+}
+
+constexpr int kRecordBlocksPerSM = 64;
+
+// kernels launch_bin_all launches in a step with particles
+int bin_kernels(const Fluid &f) { return f.split_records ? 5 : 4; }
+
+int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, double dt_fixed, int K_fixed,
+                   cudaStream_t st)
+{
+    const int np = f.n + s.n;
+    const int nt = np + (step ? bt.B : 0);
     if (nt == 0) return 0;
-    const int nb = (nt + kBlock - 1) / kBlock;
-    if (dim == 2) k_bin_all<2><<<nb, kBlock, 0, st>>>(bt, f, s, do_drift);
-    else k_bin_all<3><<<nb, kBlock, 0, st>>>(bt, f, s, do_drift);
-    k_scan_seg<<<bt.B * (s.n ? 2 : 1), kScanThreads, 0, st>>>(bt, f.ccount, f.cstart, f.n, s.ccount, s.cstart, s.n,
-                                                               nullptr, nullptr, 0, 0);
-    k_scatter2<<<nb, kBlock, 0, st>>>(f, s);
-    cudaMemsetAsync(f.nbig, 0, sizeof(int), st);
-    const long long groups = (long long)(s.n ? 2 : 1) * bt.ncell;
-    if (dim == 2)
-        k_cellsort_group<16><<<(unsigned)((groups * 16 + kBlock - 1) / kBlock), kBlock, 0, st>>>(f, s, bt.ncell, f.big,
-                                                                                                f.nbig);
-    else
-        k_cellsort_group<32><<<(unsigned)((groups * 32 + kBlock - 1) / kBlock), kBlock, 0, st>>>(f, s, bt.ncell, f.big,
-                                                                                                f.nbig);
-    k_cellsort_big<<<2 * 152, 256, 0, st>>>(f, s, bt.ncell, f.big, f.nbig);
-    if (dim == 2) k_records_all<2><<<nb, kBlock, 0, st>>>(bt, f, s);
-    else k_records_all<3><<<nb, kBlock, 0, st>>>(bt, f, s);
+    const unsigned nbt = (unsigned)((nt + kBlock - 1) / kBlock);
+    if (dim == 2) launch_k(k_bin_all<2>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);
+    else launch_k(k_bin_all<3>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);
+    if (np == 0) return cudaGetLastError() == cudaSuccess ? 0 : -3;
+    launch_k(k_scan_seg, bt.B * (s.n ? 2 : 1), kScanThreads, 0, st, bt, f.ccount, f.cstart, f.n, s.ccount, s.cstart,
+             s.n, (int *)nullptr, (int *)nullptr, 0, 0);
+    // records from the cell groups: over the listed non-empty cells; ranks
+    // only (large problems): over all cells, no list (its counter would
+    // serialise one atomic per warp)
+    const bool split = f.split_records != 0;
+    launch_k(k_scatter2, (np + kBlock - 1) / kBlock, kBlock, 0, st, f, s, bt.ncell, split ? 0 : 1);
+    const long long cells_all = (long long)(s.n ? 2 : 1) * bt.ncell;
+    const long long cells = split ? cells_all : (cells_all < np ? cells_all : np);
+    const long long cap = (long long)kRecordBlocksPerSM * 152;
+    const unsigned nbr = (unsigned)((np + kBlock - 1) / kBlock);
+    const int G = dim == 2 ? 16 : 32;
+    const long long nb = (cells * G + kBlock - 1) / kBlock;
+    const unsigned grid = (unsigned)(split || nb < cap ? nb : cap);   // all cells: one group each
+    const int listed = split ? 0 : 1, ncells = (int)cells_all;
+    if (dim == 2) {
+        if (split) {
+            launch_k(k_cell_records<2, 16, false>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
+            launch_k(k_records_sorted<2>, nbr, kBlock, 0, st, bt, f, s);
+        } else {
+            launch_k(k_cell_records<2, 16, true>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
+        }
+    } else {
+        if (split) {
+            launch_k(k_cell_records<3, 32, false>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
+            launch_k(k_records_sorted<3>, nbr, kBlock, 0, st, bt, f, s);
+        } else {
+            launch_k(k_cell_records<3, 32, true>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
+        }
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

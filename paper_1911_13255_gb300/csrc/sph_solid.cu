@@ -672,6 +672,7 @@ __device__ __forceinline__ int next_instance(unsigned *queue, int *slot, unsigne
 template <int D>
 __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Batch bt, Solid s)
 {
+    pdl_enter();
     constexpr int QR = D == 3 ? 3 : 1;   // float4 rows of Q per particle
     __shared__ float4 sQ[kPPC * QR];
     __shared__ float4 sV[kPPC];
@@ -689,6 +690,7 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster(Batch bt, Solid s)
 template <int D>
 __global__ void __launch_bounds__(kCThreads) k_solid_cluster_one(Solid s, const __grid_constant__ Phys P, Ctl *ctl)
 {
+    pdl_enter();
     constexpr int QR = D == 3 ? 3 : 1;
     __shared__ float4 sQ[kPPC * QR];
     __shared__ float4 sV[kPPC];
@@ -949,6 +951,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
 template <int LP>
 __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, Solid s)
 {
+    pdl_enter();
     __shared__ float4 sQ[kC1Threads];
     __shared__ float4 sV[kC1Threads];
     __shared__ int s_inst;
@@ -967,6 +970,7 @@ template <int LP>
 __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
                                                                          Ctl *ctl)
 {
+    pdl_enter();
     __shared__ float4 sQ[kC1Threads];
     __shared__ float4 sV[kC1Threads];
     solid2d_body<LP>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
@@ -984,13 +988,15 @@ static int launch_clusters(Kern kern, int threads, int ctas, int want, int *max_
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(threads);
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 1;   // the occupancy query below sees the cluster shape only
     if (max_clusters[ctas] == 0) {
         int nclu = 0;
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1001,6 +1007,7 @@ static int launch_clusters(Kern kern, int threads, int ctas, int want, int *max_
     if (max_clusters[ctas] < 0) return 1;
     int nclusters = want < max_clusters[ctas] ? want : max_clusters[ctas];
     cfg.gridDim = dim3(nclusters * ctas);
+    cfg.numAttrs = kPDL ? 2 : 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
     return e == cudaSuccess ? 0 : -3;
 }

@@ -141,22 +141,25 @@ def test_batch_rejects_bad_selection_and_grid_path():
     batch.close()
 
 
-@pytest.mark.parametrize("name,lanes,block,compact,tile", [
-    ("channel_flag", 2, 64, 1, 0), ("channel_flag", 4, 128, 0, 0), ("channel_flag", 8, 256, 1, 0),
-    ("channel_flag", 8, 128, 0, 0), ("tiny_box_3d", 4, 128, 0, 0), ("tiny_box_3d", 16, 256, 1, 0),
-    ("tiny_box_3d", 8, 64, 1, 0), ("channel_flag", 4, 128, 1, 1), ("channel_flag", 2, 256, 0, 1),
-    ("tiny_box_3d", 4, 128, 0, 1), ("tiny_box_3d", 8, 64, 1, 1), ("dam_gate", 4, 128, 1, 1)])
-def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact, tile):
-    """Each compiled lane count, block size, pair-loop form and tile mode computes the same step."""
+@pytest.mark.parametrize("name,lanes,block,compact,tile,records,rows", [
+    ("channel_flag", 2, 64, 1, 0, 0, 1), ("channel_flag", 4, 128, 0, 0, 1, 0), ("channel_flag", 8, 256, 1, 0, 1, 0),
+    ("channel_flag", 8, 128, 0, 0, 0, 1), ("tiny_box_3d", 4, 128, 0, 0, 1, 1), ("tiny_box_3d", 16, 256, 1, 0, 0, 0),
+    ("tiny_box_3d", 8, 64, 1, 0, 1, 1), ("channel_flag", 4, 128, 1, 1, 0, 0), ("channel_flag", 2, 256, 0, 1, 1, 0),
+    ("tiny_box_3d", 4, 128, 0, 1, 0, 0), ("tiny_box_3d", 8, 64, 1, 1, 1, 0), ("dam_gate", 4, 128, 1, 1, 1, 0),
+    ("dam_gate", 4, 128, 1, 0, 0, 1), ("dam_gate", 8, 128, 1, 0, 1, 0), ("tiny_box_3d", 16, 128, 0, 0, 0, 1)])
+def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact, tile, records, rows):
+    """Each compiled lane count, block size, pair-loop form, tile mode, records form and cell-visit form
+    computes the same step."""
     case = {"channel_flag": lambda: fc.channel_flag(seed=0), "tiny_box_3d": lambda: fc.tiny_box_3d(seed=1),
             "dam_gate": lambda: fc.dam_gate(seed=0, dpF=0.002)}[name]()
     ref = O.OracleSim(case)
     dt, _, dts = ref.suggest_dt()
     K = ref.substeps(dt, dts)
     sim = Simulation.from_case(case)
-    sim.set_tuning(lanes, block, 0, compact, tile)
+    sim.set_tuning(lanes, block, 0, compact, tile, records, rows)
     t = sim.tuning()
-    assert (t["lanes"], t["block"], t["compact"], t["tile"]) == (lanes, block, compact, tile)
+    assert (t["lanes"], t["block"], t["compact"], t["tile"], t["records"], t["rows"]) == \
+        (lanes, block, compact, tile, records, rows)
     sim.set_substeps(K)
     sim.step(dt)
     sim.sync()
@@ -164,6 +167,8 @@ def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact, tile
     g, s = sim.get_fluid(), sim.get_solid()
     e = dict(dvdt=rel(g["dvdt"], ref.f_dvdt), drho=rel(g["drho"], ref.f_drho), fF=rel(s["fF"], ref.s_fF))
     assert max(e.values()) < ACC_TOL, e
+    with pytest.raises(SphError):
+        sim.set_tuning(4 if case.dim == 2 else 8, 128, 0, 1, 1, 0, 1)   # rows with tiles
     with pytest.raises(SphError):
         sim.set_tuning(3, 128)
     with pytest.raises(SphError):
