@@ -700,22 +700,6 @@ static inline int grid_blocks(int n, int L, int block)
     return (int)((t + block - 1) / block);
 }
 
-// launch KERN<dim, L> over n targets with the lane count and block size of f
-// and SMEM bytes of dynamic shared memory per thread
-#define SPH_LAUNCH_LANES(KERN, n, SMEM, ...)                                                  \
-    do {                                                                                      \
-        const size_t sm_ = (size_t)(SMEM) * f.block;                                         \
-        const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
-            constexpr int L_ = decltype(Lc)::value;                                           \
-            launch_k(KERN<2, L_>, grid_blocks(n, L_, f.block), f.block, sm_, st, __VA_ARGS__); \
-        })                                                                                    \
-                                  : with_lanes<3>(f.lanes, [&](auto Lc) {                     \
-            constexpr int L_ = decltype(Lc)::value;                                           \
-            launch_k(KERN<3, L_>, grid_blocks(n, L_, f.block), f.block, sm_, st, __VA_ARGS__); \
-        });                                                                                   \
-        if (!ok_ || f.block < 32 || f.block > kMaxBlock || f.block % 32) return -1;           \
-    } while (0)
-
 constexpr int kListBytes = kPairCap * 4;   // per-thread in-support list (fluid_pairs)
 
 // the same for the pair-loop kernels templated on the pair form (f.compact),
