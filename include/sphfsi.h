@@ -254,7 +254,11 @@ typedef struct {
     int32_t block;         /* threads per block of those loops: 64, 128 (default) or 256 */
     int32_t solid_variant; /* 2-D cluster sub-step kernel: 0 one thread per particle;
                               1 four lanes per particle (sphfsi_set_solid_path 1);
-                              2 two threads per particle */
+                              2 two threads per particle; 3 one thread per particle reading
+                              the neighbours across the cluster in every phase.  0 and 2 keep
+                              copies of the neighbours from other CTAs in each CTA (refreshed
+                              by their owners' remote stores) where they fit, else they too
+                              read across the cluster.  All compute the same values. */
     float step_ms;         /* sphfsi_autotune: device ms per step measured for this setting */
     int32_t compact;       /* fluid-fluid pair loops: 0 evaluate each pair inside the
                               candidate loop; 1 first collect each thread's in-support

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "sph_common.cuh"
@@ -552,6 +553,67 @@ int sphfsi_set_inflow(sphfsi_ctx *c, const sphfsi_inflow *f)
     return SPHFSI_OK;
 }
 
+// Halo maps of the 2-D cluster kernel's push form.  A body's particles are
+// split into CTAs of kSolidCta in device (locality) order.  For every static
+// neighbour entry q of particle a: the slot in CTA(a) where the neighbour's
+// stress and velocity are found (its own slot when it lives in CTA(a), else a
+// halo slot kSolidCta + h, h in order of first use); for every particle:
+// the (CTA, halo slot) copies other CTAs hold of it, which it writes after
+// each update.  push_ok = 0 when a halo or a push list exceeds kHaloMax or
+// kPushMax (the kernel then reads neighbours across the cluster instead).
+int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int> &nbi)
+{
+    Solid &S = c->S;
+    const int64_t ns = S.n;
+    std::vector<int> slot(nbi.size(), 0);
+    std::vector<std::vector<int2>> pushes(ns);
+    bool ok = true;
+    for (auto &h : c->ih) {
+        const int s0 = h.d.s0, n = h.d.ns;
+        const int ctas = (n + kSolidCta - 1) / kSolidCta;
+        std::vector<std::vector<int>> halo_of(ctas);                    // local particle per halo slot
+        std::vector<std::unordered_map<int, int>> where(ctas);          // local particle -> halo slot
+        for (int la = 0; la < n; la++) {
+            const int r = la / kSolidCta;
+            for (int q = ptr[s0 + la]; q < ptr[s0 + la + 1]; q++) {
+                const int lb = nbi[q] - s0;
+                if (lb / kSolidCta == r) {
+                    slot[q] = lb % kSolidCta;
+                    continue;
+                }
+                auto it = where[r].find(lb);
+                if (it == where[r].end()) {
+                    const int hs = kSolidCta + (int)halo_of[r].size();
+                    it = where[r].emplace(lb, hs).first;
+                    halo_of[r].push_back(lb);
+                }
+                slot[q] = it->second;
+            }
+        }
+        for (int r = 0; r < ctas; r++) {
+            if ((int)halo_of[r].size() > kHaloMax) ok = false;
+            for (size_t k = 0; k < halo_of[r].size(); k++)
+                pushes[s0 + halo_of[r][k]].push_back(make_int2(r, kSolidCta + (int)k));
+        }
+    }
+    std::vector<int> pptr(ns + 1, 0);
+    std::vector<int2> pl;
+    for (int64_t a = 0; a < ns; a++) {
+        if ((int)pushes[a].size() > kPushMax) ok = false;
+        pptr[a + 1] = pptr[a] + (int)pushes[a].size();
+        pl.insert(pl.end(), pushes[a].begin(), pushes[a].end());
+    }
+    if (pl.empty()) pl.push_back(make_int2(0, 0));
+    TRY(dalloc(c, &S.nb_slot, slot.size()));
+    TRY(upload(c, S.nb_slot, slot));
+    TRY(dalloc(c, &S.push_ptr, pptr.size()));
+    TRY(upload(c, S.push_ptr, pptr));
+    TRY(dalloc(c, &S.push, pl.size()));
+    TRY(upload(c, S.push, pl));
+    S.push_ok = ok ? 1 : 0;
+    return SPHFSI_OK;
+}
+
 int sphfsi_finalize(sphfsi_ctx *c)
 {
     TRY(check_ctx(c, false));
@@ -837,6 +899,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
         TRY(upload(c, c->d_inst, hinst));
         TRY(dalloc(c, &S.nb, S.nnz));
         TRY(launch_solid_setup_fill(c->bt, S, d_nbi, D, c->st));
+        if (D == 2) TRY(halo_maps(c, ptr, nbi));
     }
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     for (int k = 0; k < sphfsi_ctx::kEvents; k++) TRY(cuda_rc(cudaEventCreate(&c->ev[k])));
@@ -1334,7 +1397,7 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 2 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
+        t->solid_variant < 0 || t->solid_variant > 3 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
         t->tile > 1 || t->records < 0 || t->records > 1 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
@@ -1461,7 +1524,7 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         if (!rc && c->dim == 2 && c->S.n && !c->S.force_grid_path) {
-            for (int v = 0; v < 3 && !rc; v++) {
+            for (int v = 0; v < 4 && !rc; v++) {
                 if (v == best->solid_variant) continue;
                 cur.solid_variant = v;
                 rc = consider(cur);

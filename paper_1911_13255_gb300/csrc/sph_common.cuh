@@ -18,6 +18,9 @@ namespace sph {
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 
 constexpr int kBlock = 128;           // threads per block of the particle kernels
+// 2-D cluster sub-step kernel: particles per CTA, halo slots per CTA and
+// halo copies per particle of the push form
+constexpr int kSolidCta = 128, kHaloMax = 384, kPushMax = 4;
 
 // Programmatic dependent launch.  The per-step kernels are launched with the
 // programmatic stream serialisation attribute (launch_k), so that a kernel's
@@ -216,6 +219,13 @@ struct Solid {
     unsigned *queue;          // persistent solid kernel: next instance to take
     int force_grid_path;      // 1: always use the cooperative-grid sub-step kernel
     int force_lane_path;      // 2-D cluster kernel: 0 one thread per particle, 1 four lanes, 2 two threads
+    // 2-D cluster kernel, push form: CTA r of a body holds particles
+    // [r kSolidCta, (r + 1) kSolidCta) of it in slots 0.. and copies of the
+    // other CTAs' particles its particles read (its halo) in slots kSolidCta..
+    int *nb_slot;             // nnz: slot of entry q's neighbour in the reading CTA
+    int *push_ptr;            // n + 1: a particle's halo copies in other CTAs
+    int2 *push;               // (CTA rank, slot) of each copy
+    int push_ok;              // 1: every halo and push list fits the kernel's limits
     int max_nb;               // largest static neighbour count of a particle
     int max_ns;               // largest body of an instance
     // learned sub-stepper (when learned != 0)

@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(kCThreads) k_solid_cluster_one(Solid s, const 
 // costs about one shared-memory (or DSMEM) latency instead of one per
 // neighbour.  Particles beyond kMaxNb2 neighbours use the 4-lane kernel.
 // ---------------------------------------------------------------------------
-constexpr int kC1Threads = 128;   // particles per CTA (128 measured faster than 256)
+constexpr int kC1Threads = kSolidCta;   // particles per CTA (128 measured faster than 256)
 constexpr int kMaxNb2 = 24;
 
 __device__ __forceinline__ uint32_t cl_addr(const void *p, uint32_t rank)
@@ -731,16 +731,32 @@ __device__ __forceinline__ float2 ld_cl2(uint32_t addr)
     return v;
 }
 
+__device__ __forceinline__ void st_cl(uint32_t addr, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
+}
+
 constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 
 // K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster,
-// LP threads per particle (128 particles per CTA).  With LP = 2 the two
+// LP threads per particle (128 particles per CTA).  Two forms of the
+// neighbour reads: pull (PUSH = false) loads each neighbour's stress and
+// velocity from its CTA's shared memory across the cluster (DSMEM) in every
+// phase; push (PUSH = true) keeps in every CTA a copy of the neighbours it
+// reads (its halo, Solid::nb_slot), which each particle's thread refreshes
+// with remote stores right after updating its own value, so that the loops
+// read only local shared memory.  The cluster barrier after each phase
+// (release / acquire) makes those stores visible, and no CTA overwrites a
+// copy while another reads it: stresses are written in one phase and read
+// in the next, velocities likewise, with a barrier in between.  With LP = 2 the two
 // threads of a particle (adjacent lanes) split its static neighbour entries
 // (entry u goes to thread u % 2), combine their partial sums with one
 // shuffle, and both carry the particle's own state identically; the first
 // writes it out.  Two threads per particle give each SM sub-partition two
 // warps to interleave in these latency-bound loops.
-template <int LP>
+template <int LP, bool PUSH>
 __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
                                              float4 *sV, unsigned rank)
 {
@@ -768,8 +784,12 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     float vmax = 0.0f, amax = 0.0f;
     float4 vown = make_float4(0.f, 0.f, 0.f, 0.f), Qown = vown;   // the particle's v and P B0
     float gx[NB], gy[NB];
-    uint32_t aQ[NB];   // neighbour's sQ slot; its sV slot is at aQ + dV (same layout in every CTA)
+    // pull: the neighbour's sQ slot (cluster address); its sV slot is at
+    // aQ + dV (same layout in every CTA).  push: the local slot.
+    uint32_t aQ[NB];
     const uint32_t dV = (uint32_t)__cvta_generic_to_shared(&sV[0]) - (uint32_t)__cvta_generic_to_shared(&sQ[0]);
+    uint32_t pq[kPushMax];   // push: cluster addresses of this particle's sQ copies
+    int npush = 0;
     int nn = 0;   // this thread's entries
     if (own) {
         int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
@@ -785,18 +805,45 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         y = ys = s.y[a];
         cons = s.cons[a] != 0;
         vown = s.v4[a];
-        if (lead) sV[g] = vown;
+        if (PUSH && lead) {
+            const int p0 = s.push_ptr[a];
+            npush = s.push_ptr[a + 1] - p0;   // <= kPushMax when the push form runs
+#pragma unroll
+            for (int t = 0; t < kPushMax; t++) {
+                pq[t] = 0u;
+                if (t < npush) {
+                    const int2 e = s.push[p0 + t];
+                    pq[t] = cl_addr(&sQ[e.y], (uint32_t)e.x);
+                }
+            }
+        }
     }
+    // own value into the local slot and, in the push form, into the copies
+    auto publish = [&](float4 *arr, uint32_t off, const float4 &val) {
+        if (!lead) return;
+        arr[g] = val;
+        if constexpr (PUSH) {
+#pragma unroll
+            for (int t = 0; t < kPushMax; t++)
+                if (t < npush) st_cl(pq[t] + off, val);
+        }
+    };
+    if (own) publish(sV, dV, vown);
 #pragma unroll
     for (int u = 0; u < NB; u++) {
         gx[u] = gy[u] = 0.0f;
         aQ[u] = 0u;
         if (u < nn) {
-            float4 e = s.nb[s.nb_ptr[a] + sub + LP * u];
-            int b = __float_as_int(e.w) - s0;   // local index in the body
+            const int q = s.nb_ptr[a] + sub + LP * u;
+            float4 e = s.nb[q];
             gx[u] = e.x;
             gy[u] = e.y;
-            aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
+            if constexpr (PUSH) {
+                aQ[u] = (uint32_t)s.nb_slot[q];
+            } else {
+                int b = __float_as_int(e.w) - s0;   // local index in the body
+                aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
+            }
         }
     }
     // sum of the static gradients: (Q_a + Q_b) . g summed over b is
@@ -821,8 +868,16 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         for (int c0 = 0; c0 < NB; c0 += CH) {
             float2 vb[CH];
 #pragma unroll
-            for (int u = 0; u < CH; u++)
-                if (c0 + u < nn) vb[u] = ld_cl2(aQ[c0 + u] + dV);
+            for (int u = 0; u < CH; u++) {
+                if (c0 + u < nn) {
+                    if constexpr (PUSH) {
+                        const float4 t = sV[aQ[c0 + u]];
+                        vb[u] = make_float2(t.x, t.y);
+                    } else {
+                        vb[u] = ld_cl2(aQ[c0 + u] + dV);
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < CH; u += 2) {
                 if (c0 + u < nn) {
@@ -854,7 +909,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         float Q[4];
         stress_QB<2>(H, B, P.mu, P.lam, Q);
         Qown = make_float4(Q[0], Q[1], Q[2], Q[3]);
-        if (lead) sQ[g] = Qown;
+        publish(sQ, 0u, Qown);
     };
 
     if (own) {
@@ -879,7 +934,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 float4 qb[CH];
 #pragma unroll
                 for (int u = 0; u < CH; u++)
-                    if (c0 + u < nn) qb[u] = ld_cl(aQ[c0 + u]);
+                    if (c0 + u < nn) qb[u] = PUSH ? sQ[aQ[c0 + u]] : ld_cl(aQ[c0 + u]);
 #pragma unroll
                 for (int u = 0; u < CH; u += 2) {
                     if (c0 + u < nn) {
@@ -901,7 +956,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 v.x += dts * av0;
                 v.y += dts * av1;
                 vown = v;
-                if (lead) sV[g] = v;
+                publish(sV, dV, v);
                 as0 += dtsd * (double)av0;
                 as1 += dtsd * (double)av1;
                 amax = fmaxf(amax, av0 * av0 + av1 * av1);
@@ -948,32 +1003,32 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     cluster_sync();
 }
 
-template <int LP>
+template <int LP, bool PUSH>
 __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, Solid s)
 {
     pdl_enter();
-    __shared__ float4 sQ[kC1Threads];
-    __shared__ float4 sV[kC1Threads];
+    __shared__ float4 sQ[kC1Threads + (PUSH ? kHaloMax : 0)];
+    __shared__ float4 sV[kC1Threads + (PUSH ? kHaloMax : 0)];
     __shared__ int s_inst;
     const unsigned rank = cluster_rank();
     for (;;) {
         const int b = next_instance(s.queue, &s_inst, rank);
         if (b >= bt.B) break;
         const Inst &In = bt.I[b];
-        solid2d_body<LP>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
+        solid2d_body<LP, PUSH>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
     }
 }
 
 // single instance: one cluster, constants in the parameter space (the
 // persistent kernel's global-memory constants cost registers)
-template <int LP>
+template <int LP, bool PUSH>
 __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
                                                                          Ctl *ctl)
 {
     pdl_enter();
-    __shared__ float4 sQ[kC1Threads];
-    __shared__ float4 sV[kC1Threads];
-    solid2d_body<LP>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
+    __shared__ float4 sQ[kC1Threads + (PUSH ? kHaloMax : 0)];
+    __shared__ float4 sV[kC1Threads + (PUSH ? kHaloMax : 0)];
+    solid2d_body<LP, PUSH>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
 }
 
 // Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
@@ -1025,17 +1080,27 @@ static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, 
 
 static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
 {
-    static int mc2d[4][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
+    static int mc2d[8][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
     const bool one = bt.B == 1;
     if (dim == 2 && s.force_lane_path != 1 && s.max_nb <= kMaxNb2) {
         const int ctas = (s.max_ns + kC1Threads - 1) / kC1Threads;
         int rc;
-        if (s.force_lane_path == 2)   // two threads per particle
-            rc = one ? launch_clusters(k_solid_cluster2d_one<2>, 2 * kC1Threads, ctas, 1, mc2d[2], st, s, P0, bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<2>, 2 * kC1Threads, ctas, bt, s, mc2d[3], st);
+        const bool push = s.push_ok != 0 && s.force_lane_path != 3;   // 3: one thread per particle, pull form
+        if (s.force_lane_path == 2 && push)   // two threads per particle
+            rc = one ? launch_clusters(k_solid_cluster2d_one<2, true>, 2 * kC1Threads, ctas, 1, mc2d[2], st, s, P0,
+                                       bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<2, true>, 2 * kC1Threads, ctas, bt, s, mc2d[3], st);
+        else if (s.force_lane_path == 2)
+            rc = one ? launch_clusters(k_solid_cluster2d_one<2, false>, 2 * kC1Threads, ctas, 1, mc2d[4], st, s, P0,
+                                       bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<2, false>, 2 * kC1Threads, ctas, bt, s, mc2d[5], st);
+        else if (push)
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, true>, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<1, true>, kC1Threads, ctas, bt, s, mc2d[1], st);
         else
-            rc = one ? launch_clusters(k_solid_cluster2d_one<1>, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<1>, kC1Threads, ctas, bt, s, mc2d[1], st);
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, false>, kC1Threads, ctas, 1, mc2d[6], st, s, P0,
+                                       bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<1, false>, kC1Threads, ctas, bt, s, mc2d[7], st);
         if (rc <= 0) return rc;
     }
     const int ctas = (s.max_ns + kPPC - 1) / kPPC;
