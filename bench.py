@@ -144,14 +144,15 @@ def _source_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch from a committed ncu summary, only if the
-    kernel sources have not changed since it was taken."""
+def _traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
+    summary, only if the kernel sources have not changed since it was taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        if t.get("source_hash") == _source_hash() and kernel in t.get("kernels", {}):
-            return t["kernels"][kernel]
+        key = f"{workload}/{kernel}"
+        if t.get("source_hash") == _source_hash() and key in t.get("kernels", {}):
+            return t["kernels"][key]
     except Exception:
         pass
     return None
@@ -338,10 +339,12 @@ def run_gpu(args, rank, world, local_rank):
         work = n_fluid * BYTES_PER_FLUID_PARTICLE["bin_sort"]
         bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
         achieved = work / (per_launch[dom] * 1e-3) / 1e9
+    # the 2-D cluster kernel runs every solid variant but 1 (four lanes per particle)
+    two_d = case.dim == 2 and tuning["solid_variant"] != 1
     if len(cases) > 1:
-        solid_kernel = "k_solid_cluster" if (case.dim == 3 or tuning["solid_variant"]) else "k_solid_cluster2d"
+        solid_kernel = "k_solid_cluster2d" if two_d else "k_solid_cluster"
     else:
-        solid_kernel = {1: "k_solid_cluster2d_one" if case.dim == 2 else "k_solid_cluster_one",
+        solid_kernel = {1: "k_solid_cluster2d_one" if two_d else "k_solid_cluster_one",
                         2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
@@ -354,7 +357,7 @@ def run_gpu(args, rank, world, local_rank):
         sm_peak = fp32_peak_tflops(sm_mhz, n_sm=min(152, ctas * min(len(cases), 152 // max(ctas, 1))))
         extra = {"ctas_per_body": ctas, "frac_of_the_sms_it_occupies": achieved / sm_peak}
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak, **extra,
-            "traffic": _traffic(kernel_names.get(dom, dom)), "kernel": kernel_names.get(dom, dom),
+            "traffic": _traffic(kernel_names.get(dom, dom), args.workload), "kernel": kernel_names.get(dom, dom),
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,
             "peak_source": ("FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz) if bound == "alu"
             else f"{src} hbm_gbs"}
@@ -539,7 +542,7 @@ def run_learned(args, rank, world, local_rank):
         "training": {"loss_first": float(losses[:20].mean()), "loss_last": float(losses[-20:].mean()),
                      "collect_s": t_collect, "train_s": t_train},
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16_tflops"], "traffic": _traffic("k_gemm_bf16"), "kernel": "k_gemm_bf16",
+                     "frac": ach / peaks["bf16_tflops"], "traffic": _traffic("k_gemm_bf16", args.workload), "kernel": "k_gemm_bf16",
                      "shape": [M_, 128, 128 * (2 + d)], "ms_per_launch": gemm_ms,
                      "peak_source": f"{src} bf16_tflops (burst)"},
         "cpu_baseline": None if cb is None else {"value": cb["sim_s_per_wall_s"], "unit": "simulated-s/s",

@@ -249,8 +249,9 @@ int sphfsi_step_time(sphfsi_ctx *c, float *ms);
  * settings and bit for bit at equal settings. */
 typedef struct {
     int32_t lanes;         /* threads per target particle in the fluid pair loops:
-                              2, 4 or 8 in 2-D (default 4); 4, 8 or 16 in 3-D (default 8
-                              below 200 000 fluid particles in the context, else 4) */
+                              2, 4 or 8 in 2-D (default 8 below 262 144 particles in the
+                              context, else 4); 4, 8 or 16 in 3-D (default 8 below 200 000
+                              fluid particles in the context, else 4) */
     int32_t block;         /* threads per block of those loops: 64, 128 (default) or 256 */
     int32_t solid_variant; /* 2-D cluster sub-step kernel: 0 one thread per particle;
                               1 four lanes per particle (sphfsi_set_solid_path 1);
@@ -263,15 +264,18 @@ typedef struct {
     int32_t compact;       /* fluid-fluid pair loops: 0 evaluate each pair inside the
                               candidate loop; 1 first collect each thread's in-support
                               neighbours in shared memory, then evaluate them densely
-                              (default 1 in 2-D, 0 in 3-D) */
+                              (default 1 in 2-D from 262 144 particles in the context, else 0) */
     int32_t tile;          /* fluid pair loops: 0 one group of lanes per target particle
                               over the whole grid; 1 one block per tile of grid cells (16 of a
                               row in 2-D, 4 in 3-D) whose neighbour records are first staged in
                               shared memory by bulk copies (default 0) */
-    int32_t records;       /* binning: 0 a group of lanes per non-empty cell ranks the cell's
-                              entries and writes their records; 1 the groups only rank, then
-                              one thread per slot writes the records (one more launch; default
-                              1 from 262 144 particles in the context, else 0) */
+    int32_t records;       /* binning: 0 four kernels (keys and histograms, scan, scatter, then a
+                              group of lanes per non-empty cell ranks the cell's entries and
+                              writes their records); 1 the same, but the groups only rank and
+                              one thread per slot writes the records (one more launch); 2 the
+                              four phases of 0 in one cooperative kernel with grid barriers
+                              (one launch; falls back to 0 where it cannot be co-resident).
+                              Default 1 from 262 144 particles in the context, else 0 */
     int32_t rows;          /* fluid pair loops without tiles: 0 visit the neighbour cells one at a
                               time; 1 a row of three cells at a time, the cell starts of the row
                               (fluid, walls, solid) loaded together: fewer dependent loads, a few

@@ -287,11 +287,11 @@ class Simulation:
         return t.as_dict()
 
     def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0, records=None, rows=None):
-        """Launch shape (include/sphfsi.h, sphfsi_tuning); records and rows
-        default to the current setting (rows is 0 with tiles)."""
-        if compact is None:
-            compact = 1 if self.dim == 2 else 0
+        """Launch shape (include/sphfsi.h, sphfsi_tuning); compact, records and
+        rows default to the current setting (rows is 0 with tiles)."""
         cur = self.tuning()
+        if compact is None:
+            compact = cur["compact"]
         if records is None:
             records = cur["records"]
         if rows is None:

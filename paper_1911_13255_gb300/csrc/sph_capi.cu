@@ -209,7 +209,7 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_density(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 6));
     if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
-    TRY(launch_finish(c->bt, c->S.learned, st));
+    TRY(launch_finish(c->bt, c->S.learned, c->F.gbar, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
     c->kernels_per_step = 4 + bin_kernels(c->F) + (c->S.n ? 2 : 0) +
@@ -647,18 +647,24 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // ---- fluid
     Fluid &F = c->F;
     F.n = (int)nf;
-    // 2-D: 4 lanes per target (more make the fluid loops faster but crowd the
-    // SMs that the solid branch, usually the longer one, runs on); 3-D: 8 for
-    // small problems, 4 for large ones
-    F.lanes = D == 2 ? 4 : (nf < 200000 ? 8 : 4);
+    // small problems are latency-bound: 8 lanes per target and direct pair
+    // evaluation (dam break: 0.105 -> 0.102 ms per step); large 2-D problems
+    // are issue-bound: 4 lanes and compacted pairs; 3-D: 8 lanes below 200 000
+    // fluid particles, else 4, direct pairs
+    const bool small = nf + ns < 262144;
+    F.lanes = D == 2 ? (small ? 8 : 4) : (nf < 200000 ? 8 : 4);
     F.block = 128;
-    F.compact = D == 2 ? 1 : 0;
+    F.compact = D == 2 && !small ? 1 : 0;
     F.tile = 0;
     // records from the cell groups for small problems (one launch fewer),
     // one thread per slot for large ones (no idle lanes)
-    F.split_records = nf + ns >= 262144 ? 1 : 0;
+    F.split_records = small ? 0 : 1;
+    // the cooperative single-kernel binning (records form 2) measured slower
+    // than the four kernels with programmatic launches (dam break: binning
+    // 35.4 vs 31.2 us): off by default
+    F.bin_fused = 0;
     // neighbour cells a row at a time where latency, not issue, bounds the loops
-    F.rows = nf + ns < 262144 ? 1 : 0;
+    F.rows = small ? 1 : 0;
     // tiles: T cells of a grid row per block (16 in 2-D, 4 in 3-D); the
     // staging area holds about three times the mean neighbourhood
     {
@@ -704,6 +710,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &F.ccount, ncell));
     TRY(dalloc(c, &F.live, 2 * (size_t)ncell));
     TRY(dalloc(c, &F.nlive, 1));
+    TRY(dalloc(c, &F.bsum, 4096));
+    TRY(dalloc(c, &F.gbar, 2));
     // ---- walls
     Walls &W = c->W;
     W.n = (int)nw;
@@ -1398,13 +1406,14 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
         t->solid_variant < 0 || t->solid_variant > 3 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
-        t->tile > 1 || t->records < 0 || t->records > 1 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
+        t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
     c->F.compact = t->compact;
     c->F.tile = t->tile;
-    c->F.split_records = t->records;
+    c->F.split_records = t->records == 1 ? 1 : 0;
+    c->F.bin_fused = t->records == 2 ? 1 : 0;
     c->F.rows = t->rows;
     c->S.force_lane_path = t->solid_variant;
     if (c->gexec) {
@@ -1423,7 +1432,7 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
     t->solid_variant = c->S.force_lane_path;
     t->compact = c->F.compact;
     t->tile = c->F.tile;
-    t->records = c->F.split_records;
+    t->records = c->F.bin_fused ? 2 : c->F.split_records;
     t->rows = c->F.rows;
     t->step_ms = 0.0f;
     return SPHFSI_OK;
@@ -1518,8 +1527,9 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
             rc = consider(cur);
         }
         cur = *best;
-        if (!rc) {
-            cur.records = 1 - cur.records;
+        for (int r = 0; r < 3 && !rc; r++) {
+            if (r == best->records) continue;
+            cur.records = r;
             rc = consider(cur);
         }
         cur = *best;

@@ -174,6 +174,9 @@ struct Fluid {
     int *cstart;      // total cells + 1
     int *ccount;      // total cells (histogram / scatter cursor)
     int *live, *nlive;  // non-empty cells of the step (fluid c, solid ncell + c), listed by the scatter
+    int bin_fused;      // 1: binning as one cooperative kernel with grid barriers (small problems)
+    int *bsum;          // its per-block partial sums (kBinFusedMaxBlocks)
+    unsigned *gbar;     // its grid barrier: [0] arrivals, [1] generation
 };
 
 // Static walls, binned once.
@@ -250,6 +253,42 @@ struct Batch {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// grid-wide barrier with a bounded spin (cooperative launch guarantees that
+// all blocks are resident); returns false after a time-out
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned prev = atomicAdd(bar, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > kSpinLimit) {
+                    ok = 0;
+                    atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned *addr, float v)
 {
     // non-negative floats order like their bit patterns; NaN (0x7fc...) wins
@@ -320,7 +359,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
                    cudaStream_t st);
 int bin_kernels(const Fluid &f);
 int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
-int launch_finish(const Batch &bt, int learned, cudaStream_t st);
+int launch_finish(const Batch &bt, int learned, unsigned *gbar, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);
 int launch_scatter(const int *key, const int *cstart, int *ccount, int *perm, int n, cudaStream_t st);
 

@@ -91,10 +91,11 @@ __device__ void update_normal(const Solid &s, int a)
 
 // finish: time, step, pair counters, non-finite check, maxima for the next
 // step's control (one thread per instance)
-__global__ void k_finish(Batch bt, int learned)
+__global__ void k_finish(Batch bt, int learned, unsigned *gbar)
 {
     pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0 && gbar) gbar[0] = 0u;   // the fused binning's barrier, even after a time-out
     if (b >= bt.B) return;
     Ctl *ctl = bt.ctl + b;
     float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
@@ -122,9 +123,9 @@ __global__ void k_finish(Batch bt, int learned)
     ctl->step += 1;
 }
 
-int launch_finish(const Batch &bt, int learned, cudaStream_t st)
+int launch_finish(const Batch &bt, int learned, unsigned *gbar, cudaStream_t st)
 {
-    launch_k(k_finish, (bt.B + kBlock - 1) / kBlock, kBlock, 0, st, bt, learned);
+    launch_k(k_finish, (bt.B + kBlock - 1) / kBlock, kBlock, 0, st, bt, learned, gbar);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -159,11 +160,9 @@ __device__ __forceinline__ int global_key(const Inst &In, double x, double y, do
 // normals on reinitialisation steps.  Thread 0 clears the list of non-empty
 // cells that the scatter fills.
 template <int D>
-__global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
+__device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const Solid &s, int t, int step,
+                                        double dt_fixed, int K_fixed)
 {
-    pdl_enter();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *f.nlive = 0;
     if (t < f.n) {
         const int i = t;
         const int b = f.inst[i];
@@ -211,6 +210,15 @@ __global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed,
         const int b = t - f.n - s.n;
         step_control(bt.I[b], bt.ctl + b, dt_fixed, K_fixed);
     }
+}
+
+template <int D>
+__global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
+{
+    pdl_enter();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *f.nlive = 0;
+    bin_one<D>(bt, f, s, t, step, dt_fixed, K_fixed);
 }
 
 // ---------------------------------------------------------------------------
@@ -305,10 +313,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_seg(Batch bt, int *fcount
 // list_cells the particle that opens a cell appends it to the list of
 // non-empty cells (fluid cell c as c, solid cell c as ncell + c), one atomic
 // per warp (on one counter: for small problems only).
-__global__ void k_scatter2(Fluid f, Solid s, int ncell, int list_cells)
+// (called by all 32 lanes of a warp together)
+__device__ __forceinline__ void scatter_one(const Fluid &f, const Solid &s, int t, int ncell, int list_cells)
 {
-    pdl_enter();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     int opened = -1;
     if (t < f.n) {
         const int k = f.key[t];
@@ -330,6 +337,12 @@ __global__ void k_scatter2(Fluid f, Solid s, int ncell, int list_cells)
     if (lane == lead) base = atomicAdd(f.nlive, __popc(m));
     base = __shfl_sync(0xffffffffu, base, lead);
     if (opened >= 0) f.live[base + __popc(m & ((1u << lane) - 1u))] = opened;
+}
+
+__global__ void k_scatter2(Fluid f, Solid s, int ncell, int list_cells)
+{
+    pdl_enter();
+    scatter_one(f, s, blockIdx.x * blockDim.x + threadIdx.x, ncell, list_cells);
 }
 
 // per-cell insertion sort by slot (walls, binned once), and the cursor reset
@@ -370,36 +383,65 @@ __device__ __forceinline__ float4 rel_pos(const Inst &In, int gkey, double x, do
 }
 
 // Record of fluid slot k (cell order) from storage slot src: the sorted
-// copy of the state in s[1] and the FP32 records the pair loops read.
+// copy of the state in s[1] and the FP32 records the pair loops read.  The
+// source is read first (fluid_src) and written later (fluid_put), so that the
+// ranking kernel can issue the reads before ranking.  An instance's slots
+// are the same range in storage and in cell order, so src's instance is k's.
+struct FluidSrc {
+    double x, y, z;
+    float vx, vy, vz, dr, rd;
+    int id, key, b;
+};
+
+template <int D>
+__device__ __forceinline__ FluidSrc fluid_src(const Fluid &f, int src)
+{
+    const FluidState A = f.s[0];
+    FluidSrc v;
+    v.x = A.x[src];
+    v.y = A.y[src];
+    v.z = D == 3 ? A.z[src] : 0.0;
+    v.vx = A.vx[src];
+    v.vy = A.vy[src];
+    v.vz = D == 3 ? A.vz[src] : 0.0f;
+    v.dr = A.drho[src];
+    v.rd = A.rhodot[src];
+    v.id = A.id[src];
+    v.key = f.key[src];
+    v.b = f.inst[src];
+    return v;
+}
+
+template <int D>
+__device__ __forceinline__ void fluid_put(const Batch &bt, const Fluid &f, int k, const FluidSrc &v)
+{
+    const FluidState B = f.s[1];
+    const Inst &In = bt.I[v.b];
+    B.x[k] = v.x;
+    B.y[k] = v.y;
+    B.vx[k] = v.vx;
+    B.vy[k] = v.vy;
+    if (D == 3) {
+        B.z[k] = v.z;
+        B.vz[k] = v.vz;
+    }
+    B.drho[k] = v.dr;
+    B.rhodot[k] = v.rd;
+    B.id[k] = v.id;
+    f.cell_of[k] = v.key;
+    const bool reinit = bt.ctl[v.b].reinit;
+    float4 lo;
+    float4 r = rel_pos<D>(In, v.key, v.x, v.y, v.z, reinit ? &lo : nullptr);
+    if (reinit) f.L4[k] = lo;
+    r.w = eos_p(v.dr, In.P);
+    f.P4[k] = r;
+    f.V4[k] = make_float4(v.vx, v.vy, v.vz, v.dr);
+}
+
 template <int D>
 __device__ __forceinline__ void fluid_record(const Batch &bt, const Fluid &f, int k, int src)
 {
-    FluidState A = f.s[0], B = f.s[1];
-    const int b = f.inst[k];
-    const Inst &In = bt.I[b];
-    double x = A.x[src], y = A.y[src], z = D == 3 ? A.z[src] : 0.0;
-    float vx = A.vx[src], vy = A.vy[src], vz = D == 3 ? A.vz[src] : 0.0f;
-    float dr = A.drho[src];
-    B.x[k] = x;
-    B.y[k] = y;
-    B.vx[k] = vx;
-    B.vy[k] = vy;
-    if (D == 3) {
-        B.z[k] = z;
-        B.vz[k] = vz;
-    }
-    B.drho[k] = dr;
-    B.rhodot[k] = A.rhodot[src];
-    B.id[k] = A.id[src];
-    int key = f.key[src];
-    f.cell_of[k] = key;
-    const bool reinit = bt.ctl[b].reinit;
-    float4 lo;
-    float4 r = rel_pos<D>(In, key, x, y, z, reinit ? &lo : nullptr);
-    if (reinit) f.L4[k] = lo;
-    r.w = eos_p(dr, In.P);
-    f.P4[k] = r;
-    f.V4[k] = make_float4(vx, vy, vz, dr);
+    fluid_put<D>(bt, f, k, fluid_src<D>(f, src));
 }
 
 // Record of solid slot k of the fluid grid from solid particle a (N4.w
@@ -434,6 +476,57 @@ __device__ __forceinline__ void solid_record(const Batch &bt, const Solid &s, in
 // (sperm[start + rank(e)] = e) and k_records_sorted writes the records with
 // one thread per slot (Fluid::split_records): one launch more, but no idle
 // lanes while writing, which pays for large batches.
+// One cell per group of G lanes (valid: this group has cell e); every lane
+// of the warp calls it together.  A fluid entry's source state is read
+// before the ranking, so those loads overlap the shuffles.
+template <int D, int G, bool REC>
+__device__ __forceinline__ void rank_cell(const Batch &bt, const Fluid &f, const Solid &s, bool valid, int e,
+                                          int lane)
+{
+    const bool fl = e < bt.ncell;
+    const int c = fl ? e : e - bt.ncell;
+    const int *cs = fl ? f.cstart : s.cstart;
+    const int *perm = fl ? f.perm : s.perm;
+    int a = 0, n = 0;
+    if (valid) {
+        a = cs[c];
+        n = cs[c + 1] - a;
+        if (lane == 0) (fl ? f.ccount : s.ccount)[c] = 0;   // cursor reset for the next binning
+    }
+    const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
+    for (int m0 = 0; m0 < nmax; m0 += G) {
+        const bool mine = m0 + lane < n;
+        const int v = mine ? perm[a + m0 + lane] : 0;
+        FluidSrc src{};
+        int kv = 0x7fffffff;
+        if (mine) {
+            if (fl) {
+                if (REC) src = fluid_src<D>(f, v);
+                else src.id = f.s[0].id[v];
+                kv = src.id;
+            } else {
+                kv = v;
+            }
+        }
+        int rank = 0;
+        for (int c0 = 0; c0 < nmax; c0 += G) {
+            int ko = kv;
+            if (c0 != m0) {
+                const bool has = c0 + lane < n;
+                const int u = has ? perm[a + c0 + lane] : 0;
+                ko = has ? (fl ? f.s[0].id[u] : u) : 0x7fffffff;
+            }
+            const int lim = nmax - c0 < G ? nmax - c0 : G;
+            for (int q = 0; q < lim; q++) rank += __shfl_sync(0xffffffffu, ko, q, G) < kv ? 1 : 0;
+        }
+        if (mine) {
+            if (!REC) (fl ? f.sperm : s.sperm)[a + rank] = v;
+            else if (fl) fluid_put<D>(bt, f, a + rank, src);
+            else solid_record<D>(bt, s, a + rank, v);
+        }
+    }
+}
+
 template <int D, int G, bool REC>
 __global__ void __launch_bounds__(256) k_cell_records(Batch bt, Fluid f, Solid s, int listed, int ncells)
 {
@@ -444,40 +537,7 @@ __global__ void __launch_bounds__(256) k_cell_records(Batch bt, Fluid f, Solid s
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) / G;; w += per_grid) {
         const bool valid = w < nlive;
         if (!__any_sync(0xffffffffu, valid)) break;
-        const int e = valid ? (listed ? f.live[w] : w) : 0;
-        const bool fl = e < bt.ncell;
-        const int c = fl ? e : e - bt.ncell;
-        const int *cs = fl ? f.cstart : s.cstart;
-        const int *perm = fl ? f.perm : s.perm;
-        const int *id = fl ? f.s[0].id : nullptr;
-        int a = 0, n = 0;
-        if (valid) {
-            a = cs[c];
-            n = cs[c + 1] - a;
-            if (lane == 0) (fl ? f.ccount : s.ccount)[c] = 0;   // cursor reset for the next binning
-        }
-        const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)n);
-        for (int m0 = 0; m0 < nmax; m0 += G) {
-            const bool mine = m0 + lane < n;
-            const int v = mine ? perm[a + m0 + lane] : 0;
-            const int kv = mine ? (id ? id[v] : v) : 0x7fffffff;
-            int rank = 0;
-            for (int c0 = 0; c0 < nmax; c0 += G) {
-                int ko = kv;
-                if (c0 != m0) {
-                    const bool has = c0 + lane < n;
-                    const int u = has ? perm[a + c0 + lane] : 0;
-                    ko = has ? (id ? id[u] : u) : 0x7fffffff;
-                }
-                const int lim = nmax - c0 < G ? nmax - c0 : G;
-                for (int q = 0; q < lim; q++) rank += __shfl_sync(0xffffffffu, ko, q, G) < kv ? 1 : 0;
-            }
-            if (mine) {
-                if (!REC) (fl ? f.sperm : s.sperm)[a + rank] = v;
-                else if (fl) fluid_record<D>(bt, f, a + rank, v);
-                else solid_record<D>(bt, s, a + rank, v);
-            }
-        }
+        rank_cell<D, G, REC>(bt, f, s, valid, valid ? (listed ? f.live[w] : w) : 0, lane);
     }
 }
 
@@ -492,8 +552,152 @@ __global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
 
 constexpr int kRecordBlocksPerSM = 64;
 
+// ---------------------------------------------------------------------------
+// Binning as one cooperative kernel (Fluid::bin_fused, small problems, where
+// the four kernels above cost more in launch gaps and tails than in work):
+// the same four phases, each a grid-stride loop, separated by grid barriers
+// (all blocks are resident: cooperative launch).  The scan is two-level:
+// every block sums its range of the concatenated histograms [fluid | solid],
+// then scans its range from the sum of the preceding blocks' totals.  One
+// exclusive scan over all instances' cells gives every instance's starts,
+// because instance b's cells and slots both follow those of instance b - 1
+// (the solid half is offset back by the fluid total).
+// ---------------------------------------------------------------------------
+constexpr int kBinFusedThreads = 512, kBinFusedMaxBlocks = 4096;
+
+// sum over the block (every thread calls it; every thread gets the sum)
+__device__ __forceinline__ int block_sum(int v, int *red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    int t = lane < nw ? red[lane] : 0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+// inclusive scan over the block in thread order; *total gets the block sum
+__device__ __forceinline__ int block_scan(int v, int *red, int *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    __syncthreads();
+    if (lane == 31) red[w] = x;
+    __syncthreads();
+    int y = lane < nw ? red[lane] : 0, yi = y;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, yi, o);
+        if (lane >= o) yi += u;
+    }
+    *total = __shfl_sync(0xffffffffu, yi, 31);
+    return x + (__shfl_sync(0xffffffffu, yi, w) - __shfl_sync(0xffffffffu, y, w));
+}
+
+template <int D, int G>
+__global__ void __launch_bounds__(kBinFusedThreads, 1)
+    k_bin_fused(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
+{
+    pdl_enter();
+    __shared__ int red[32];
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    int *status = &bt.ctl[0].status;
+    const int np = f.n + s.n;
+    // (1) step control, drift, cell keys, histograms
+    if (gt == 0) *f.nlive = 0;
+    for (int t = gt; t < np + (step ? bt.B : 0); t += gs) bin_one<D>(bt, f, s, t, step, dt_fixed, K_fixed);
+    if (!grid_barrier(f.gbar, status)) return;
+    // (2) exclusive scan of [fluid counts | solid counts]
+    const int ncell = bt.ncell, L = (s.n ? 2 : 1) * ncell;
+    const int chunk = (L + gridDim.x - 1) / gridDim.x;
+    const int i0 = min(L, (int)blockIdx.x * chunk), i1 = min(L, i0 + chunk);
+    auto count_at = [&](int i) { return i < ncell ? f.ccount[i] : s.ccount[i - ncell]; };
+    int part = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) part += count_at(i);
+    part = block_sum(part, red);
+    if (threadIdx.x == 0) f.bsum[blockIdx.x] = part;
+    if (!grid_barrier(f.gbar, status)) return;
+    int off = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += blockDim.x) off += f.bsum[j];
+    off = block_sum(off, red);
+    for (int b0 = i0; b0 < i1; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < i1 ? count_at(i) : 0;
+        int tot;
+        const int incl = block_scan(v, red, &tot);
+        if (i < i1) {
+            const int st = off + incl - v;
+            if (i < ncell) {
+                f.cstart[i] = st;
+                f.ccount[i] = 0;   // the histogram becomes the scatter cursor
+            } else {
+                s.cstart[i - ncell] = st - f.n;
+                s.ccount[i - ncell] = 0;
+            }
+        }
+        off += tot;
+    }
+    if (gt == 0) {
+        f.cstart[ncell] = f.n;
+        if (s.n) s.cstart[ncell] = s.n;
+    }
+    if (!grid_barrier(f.gbar, status)) return;
+    // (3) scatter and the list of non-empty cells (whole warps per call)
+    for (int t = gt; t < ((np + 31) & ~31); t += gs) scatter_one(f, s, t, ncell, 1);
+    if (!grid_barrier(f.gbar, status)) return;
+    // (4) canonical order and records of the non-empty cells
+    const int nlive = *f.nlive;
+    const int lane = threadIdx.x % G;
+    const int per_grid = gridDim.x * (blockDim.x / G);
+    for (int w = gt / G;; w += per_grid) {
+        const bool valid = w < nlive;
+        if (!__any_sync(0xffffffffu, valid)) break;
+        rank_cell<D, G, true>(bt, f, s, valid, valid ? f.live[w] : 0, lane);
+    }
+}
+
+// grid of the fused binning kernel: one block per SM (0: it cannot run)
+template <typename K>
+static int bin_fused_blocks(K kern, int dim)
+{
+    static int cached_d[2] = {-1, -1};
+    int &cached = cached_d[dim == 2 ? 0 : 1];
+    if (cached < 0) {
+        int dev = 0, nsm = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kBinFusedThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per = 0;
+        }
+        cached = per >= 1 ? (nsm < kBinFusedMaxBlocks ? nsm : kBinFusedMaxBlocks) : 0;
+    }
+    return cached;
+}
+
+template <typename K>
+static int launch_bin_fused(K kern, int nb, cudaStream_t st, const Batch &bt, const Fluid &f, const Solid &s, int step,
+                            double dt_fixed, int K_fixed)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kBinFusedThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, bt, f, s, step, dt_fixed, K_fixed) == cudaSuccess ? 0 : -3;
+}
+
 // kernels launch_bin_all launches in a step with particles
-int bin_kernels(const Fluid &f) { return f.split_records ? 5 : 4; }
+int bin_kernels(const Fluid &f) { return f.bin_fused ? 1 : (f.split_records ? 5 : 4); }
 
 int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, double dt_fixed, int K_fixed,
                    cudaStream_t st)
@@ -501,6 +705,11 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
     const int np = f.n + s.n;
     const int nt = np + (step ? bt.B : 0);
     if (nt == 0) return 0;
+    if (f.bin_fused && np > 0) {
+        auto kern = dim == 2 ? k_bin_fused<2, 16> : k_bin_fused<3, 32>;
+        const int nb = bin_fused_blocks(kern, dim);
+        if (nb > 0) return launch_bin_fused(kern, nb, st, bt, f, s, step, dt_fixed, K_fixed);
+    }
     const unsigned nbt = (unsigned)((nt + kBlock - 1) / kBlock);
     if (dim == 2) launch_k(k_bin_all<2>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);
     else launch_k(k_bin_all<3>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);

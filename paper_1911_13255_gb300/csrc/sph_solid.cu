@@ -101,42 +101,6 @@ int launch_solid_setup_fill(const Batch &bt, Solid &s, const int *nbi, int dim, 
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-// ---------------------------------------------------------------------------
-// grid-wide barrier with a bounded spin (cooperative launch guarantees that
-// all blocks are resident); returns false after a time-out
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status)
-{
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *vgen = bar + 1;
-        unsigned gen = *vgen;
-        __threadfence();
-        unsigned prev = atomicAdd(bar, 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == gen) {
-                if (++it > kSpinLimit) {
-                    ok = 0;
-                    atomicOr(status, ST_TIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
 // neo-Hookean PK1 times B0 from H = F - I (Eqs. Neo-Hookean-energy, 2rd-PK)
 template <int D>
 __device__ __forceinline__ void stress_QB(const float *H, const float *B, float mu, float lam, float *Q)

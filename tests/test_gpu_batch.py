@@ -146,7 +146,8 @@ def test_batch_rejects_bad_selection_and_grid_path():
     ("channel_flag", 8, 128, 0, 0, 0, 1), ("tiny_box_3d", 4, 128, 0, 0, 1, 1), ("tiny_box_3d", 16, 256, 1, 0, 0, 0),
     ("tiny_box_3d", 8, 64, 1, 0, 1, 1), ("channel_flag", 4, 128, 1, 1, 0, 0), ("channel_flag", 2, 256, 0, 1, 1, 0),
     ("tiny_box_3d", 4, 128, 0, 1, 0, 0), ("tiny_box_3d", 8, 64, 1, 1, 1, 0), ("dam_gate", 4, 128, 1, 1, 1, 0),
-    ("dam_gate", 4, 128, 1, 0, 0, 1), ("dam_gate", 8, 128, 1, 0, 1, 0), ("tiny_box_3d", 16, 128, 0, 0, 0, 1)])
+    ("dam_gate", 4, 128, 1, 0, 0, 1), ("dam_gate", 8, 128, 1, 0, 1, 0), ("tiny_box_3d", 16, 128, 0, 0, 0, 1),
+    ("dam_gate", 8, 128, 0, 0, 2, 1), ("tiny_box_3d", 8, 128, 1, 0, 2, 0), ("channel_flag", 4, 64, 1, 1, 2, 0)])
 def test_every_launch_shape_matches_the_oracle(name, lanes, block, compact, tile, records, rows):
     """Each compiled lane count, block size, pair-loop form, tile mode, records form and cell-visit form
     computes the same step."""
@@ -265,3 +266,47 @@ def test_solid_push_and_pull_forms_are_bitwise_equal(name):
     for k in a:
         assert np.array_equal(a[k], b[k]), k
     assert sims[0].info()["solid_path"] == 1
+
+
+@pytest.mark.parametrize("name", ["dam_gate", "tiny_box_3d"])
+def test_binning_forms_are_bitwise_equal(name):
+    """The three binning forms (four kernels with records from the cell groups, the same with
+    records per slot, one cooperative kernel) produce the same records, hence the same steps."""
+    case = {"dam_gate": lambda: fc.dam_gate(seed=0), "tiny_box_3d": lambda: fc.tiny_box_3d(seed=1)}[name]()
+    states = []
+    for records in (0, 1, 2):
+        sim = Simulation.from_case(case)
+        t = sim.tuning()
+        sim.set_tuning(t["lanes"], t["block"], t["solid_variant"], t["compact"], t["tile"], records, t["rows"])
+        assert sim.tuning()["records"] == records
+        for _ in range(5):
+            sim.step(0.0)
+        sim.sync()
+        states.append((sim.get_fluid(), sim.get_solid() if case.ns else {}))
+    for fl, so in states[1:]:
+        for k in states[0][0]:
+            assert np.array_equal(fl[k], states[0][0][k]), k
+        for k in states[0][1]:
+            assert np.array_equal(so[k], states[0][1][k]), k
+
+
+def test_fused_binning_batch_equals_single():
+    """A batch stepped with the cooperative binning kernel matches its instances stepped alone."""
+    cases = _mixed_cases()
+    batch = Simulation.from_cases(cases)
+    t = batch.tuning()
+    batch.set_tuning(t["lanes"], t["block"], 0, t["compact"], 0, 2, t["rows"])
+    for _ in range(4):
+        batch.step(0.0)
+    batch.sync()
+    for b, case in enumerate(cases):
+        single = Simulation.from_case(case)
+        single.set_tuning(t["lanes"], t["block"], 0, t["compact"], 0, 0, t["rows"])
+        for _ in range(4):
+            single.step(0.0)
+        single.sync()
+        want, got = single.get_fluid(), batch.select(b).get_fluid()
+        for k in want:
+            assert np.array_equal(got[k], want[k]), (b, k)
+        single.close()
+    batch.close()
