@@ -735,7 +735,8 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     };
     const int la = (int)rank * kC1Threads + g;
     const int a = s0 + la;
-    const bool own = la < ns;
+    // threads past kC1Threads * LP (a padded launch) only take part in the barriers
+    const bool own = threadIdx.x < kC1Threads * LP && la < ns;
     if (ctl->learned_ok) return;   // the learned step was accepted: no sub-steps
     const int K = ctl->K;
     const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
@@ -939,11 +940,11 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             const float hH = more ? dts : hdts;
             const double hX = more ? dtsd : hdtsd;
             for (int i = 0; i < 4; i++) H[i] = H[i] + hH * Hd[i];
+            if (more) put_Q();   // first, so that its stores are under way during the drift
             if (!cons) {
                 x = x + hX * (double)va.x;
                 y = y + hX * (double)va.y;
             }
-            if (more) put_Q();
         }
     }
     if (own && lead) {
@@ -985,9 +986,12 @@ __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, S
 
 // single instance: one cluster, constants in the parameter space (the
 // persistent kernel's global-memory constants cost registers)
+// With LP = 1 it may be launched with 2 kC1Threads threads, the second half
+// idle: the CTA then holds its SM's registers, so no fluid block of the
+// concurrent main-stream loops shares the SM with the sub-steps.
 template <int LP, bool PUSH>
-__global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
-                                                                         Ctl *ctl)
+__global__ void __launch_bounds__(kC1Threads * 2) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
+                                                                        Ctl *ctl)
 {
     pdl_enter();
     __shared__ float4 sQ[kC1Threads + (PUSH ? kHaloMax : 0)];
@@ -1042,6 +1046,10 @@ static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, 
     return launch_clusters(kern, threads, ctas, bt.B, max_clusters, st, bt, s);
 }
 
+// 1: the single-body push-form kernel runs with idle padding threads (see
+// k_solid_cluster2d_one)
+constexpr int kPadSolidOne = 1;
+
 static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
 {
     static int mc2d[8][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
@@ -1059,7 +1067,8 @@ static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int d
                                        bt.ctl)
                      : launch_persistent(k_solid_cluster2d<2, false>, 2 * kC1Threads, ctas, bt, s, mc2d[5], st);
         else if (push)
-            rc = one ? launch_clusters(k_solid_cluster2d_one<1, true>, kC1Threads, ctas, 1, mc2d[0], st, s, P0, bt.ctl)
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, true>, kC1Threads * (kPadSolidOne ? 2 : 1), ctas, 1,
+                                       mc2d[0], st, s, P0, bt.ctl)
                      : launch_persistent(k_solid_cluster2d<1, true>, kC1Threads, ctas, bt, s, mc2d[1], st);
         else
             rc = one ? launch_clusters(k_solid_cluster2d_one<1, false>, kC1Threads, ctas, 1, mc2d[6], st, s, P0,
