@@ -256,10 +256,14 @@ typedef struct {
     int32_t solid_variant; /* 2-D cluster sub-step kernel: 0 one thread per particle;
                               1 four lanes per particle (sphfsi_set_solid_path 1);
                               2 two threads per particle; 3 one thread per particle reading
-                              the neighbours across the cluster in every phase.  0 and 2 keep
-                              copies of the neighbours from other CTAs in each CTA (refreshed
-                              by their owners' remote stores) where they fit, else they too
-                              read across the cluster.  All compute the same values. */
+                              the neighbours across the cluster in every phase; 4 one thread
+                              per particle whose halo copies (below) are refreshed by
+                              asynchronous remote stores that each CTA awaits on its own
+                              mbarriers instead of cluster barriers (measured slower).  0 and
+                              2 keep copies of the neighbours from other CTAs in each CTA,
+                              refreshed by their owners' remote stores and ordered by the
+                              cluster barrier between phases, where they fit, else they read
+                              across the cluster.  All compute the same values. */
     float step_ms;         /* sphfsi_autotune: device ms per step measured for this setting */
     int32_t compact;       /* fluid-fluid pair loops: 0 evaluate each pair inside the
                               candidate loop; 1 first collect each thread's in-support

@@ -567,8 +567,10 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
     const int64_t ns = S.n;
     std::vector<int> slot(nbi.size(), 0);
     std::vector<std::vector<int2>> pushes(ns);
+    std::vector<int> halo_n(c->ih.size() * 16, 0);
     bool ok = true;
-    for (auto &h : c->ih) {
+    for (size_t bi = 0; bi < c->ih.size(); bi++) {
+        auto &h = c->ih[bi];
         const int s0 = h.d.s0, n = h.d.ns;
         const int ctas = (n + kSolidCta - 1) / kSolidCta;
         std::vector<std::vector<int>> halo_of(ctas);                    // local particle per halo slot
@@ -591,7 +593,8 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
             }
         }
         for (int r = 0; r < ctas; r++) {
-            if ((int)halo_of[r].size() > kHaloMax) ok = false;
+            if ((int)halo_of[r].size() > kHaloMax || r >= 16) ok = false;
+            else halo_n[bi * 16 + r] = (int)halo_of[r].size();
             for (size_t k = 0; k < halo_of[r].size(); k++)
                 pushes[s0 + halo_of[r][k]].push_back(make_int2(r, kSolidCta + (int)k));
         }
@@ -610,6 +613,8 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
     TRY(upload(c, S.push_ptr, pptr));
     TRY(dalloc(c, &S.push, pl.size()));
     TRY(upload(c, S.push, pl));
+    TRY(dalloc(c, &S.halo_n, halo_n.size()));
+    TRY(upload(c, S.halo_n, halo_n));
     S.push_ok = ok ? 1 : 0;
     return SPHFSI_OK;
 }
@@ -1405,7 +1410,7 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 3 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
+        t->solid_variant < 0 || t->solid_variant > 4 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
         t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
@@ -1534,7 +1539,7 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         if (!rc && c->dim == 2 && c->S.n && !c->S.force_grid_path) {
-            for (int v = 0; v < 4 && !rc; v++) {
+            for (int v = 0; v < 5 && !rc; v++) {
                 if (v == best->solid_variant) continue;
                 cur.solid_variant = v;
                 rc = consider(cur);

@@ -228,6 +228,7 @@ struct Solid {
     int *nb_slot;             // nnz: slot of entry q's neighbour in the reading CTA
     int *push_ptr;            // n + 1: a particle's halo copies in other CTAs
     int2 *push;               // (CTA rank, slot) of each copy
+    int *halo_n;              // [instance * 16 + CTA]: halo slots of each CTA of each body
     int push_ok;              // 1: every halo and push list fits the kernel's limits
     int max_nb;               // largest static neighbour count of a particle
     int max_ns;               // largest body of an instance

@@ -702,6 +702,47 @@ __device__ __forceinline__ void st_cl(uint32_t addr, float4 v)
                  : "memory");
 }
 
+// 16-byte store into another CTA's shared memory whose arrival completes 16
+// bytes of a transaction on that CTA's mbarrier (both cluster addresses)
+__device__ __forceinline__ void st_async(uint32_t addr, float4 v, uint32_t mbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     addr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mb, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(mb)), "r"(count)
+                 : "memory");
+}
+
+// one thread arms a use of the mbarrier with the bytes it will receive; every
+// thread then waits for that use (parity) to complete, boundedly: false
+// after a time-out (status bit set)
+__device__ __forceinline__ bool mbar_use(uint64_t *mb, unsigned bytes, unsigned parity, int *status)
+{
+    const uint32_t m = (uint32_t)__cvta_generic_to_shared(mb);
+    if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+    for (long long it = 0;; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(m), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > (1ll << 20)) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 
 // K sub-steps of one instance's body (slots [s0, s0 + ns)) by one cluster,
@@ -720,10 +761,12 @@ constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 // shuffle, and both carry the particle's own state identically; the first
 // writes it out.  Two threads per particle give each SM sub-partition two
 // warps to interleave in these latency-bound loops.
-template <int LP, bool PUSH>
+template <int LP, int MODE>
 __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
-                                             float4 *sV, unsigned rank)
+                                             float4 *sV, unsigned rank, uint64_t *mb, int halo_n, unsigned &phs)
 {
+    constexpr bool PUSH = MODE != 0, MB = MODE == 2;
+    constexpr int SLOTS = kC1Threads + kHaloMax;   // one buffer of the double-buffered (MB) arrays
     constexpr int NB = kMaxNb2 / LP;                   // entries per thread
     constexpr int CH = NB < kChunk2 ? NB : kChunk2;    // loads in flight per round
     const int g = threadIdx.x / LP, sub = threadIdx.x % LP;
@@ -754,6 +797,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     uint32_t aQ[NB];
     const uint32_t dV = (uint32_t)__cvta_generic_to_shared(&sV[0]) - (uint32_t)__cvta_generic_to_shared(&sQ[0]);
     uint32_t pq[kPushMax];   // push: cluster addresses of this particle's sQ copies
+    uint32_t prk[kPushMax];  // and the ranks of the CTAs holding them
     int npush = 0;
     int nn = 0;   // this thread's entries
     if (own) {
@@ -776,24 +820,44 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
 #pragma unroll
             for (int t = 0; t < kPushMax; t++) {
                 pq[t] = 0u;
+                prk[t] = 0u;
                 if (t < npush) {
                     const int2 e = s.push[p0 + t];
                     pq[t] = cl_addr(&sQ[e.y], (uint32_t)e.x);
+                    prk[t] = (uint32_t)e.x;
                 }
             }
         }
     }
-    // own value into the local slot and, in the push form, into the copies
-    auto publish = [&](float4 *arr, uint32_t off, const float4 &val) {
+    // own value into the local slot and, in the push forms, into the copies:
+    // buffer buf of arr (sQ: off 0, mbarriers 0, 1; sV: off dV, mbarriers 2, 3)
+    auto publish = [&](float4 *arr, uint32_t off, int buf, const float4 &val) {
         if (!lead) return;
-        arr[g] = val;
+        arr[(MB ? buf * SLOTS : 0) + g] = val;
         if constexpr (PUSH) {
 #pragma unroll
-            for (int t = 0; t < kPushMax; t++)
-                if (t < npush) st_cl(pq[t] + off, val);
+            for (int t = 0; t < kPushMax; t++) {
+                if (t < npush) {
+                    if constexpr (MB)
+                        st_async(pq[t] + off + (uint32_t)(buf * SLOTS * 16), val,
+                                 cl_addr(&mb[(off ? 2 : 0) + buf], prk[t]));
+                    else
+                        st_cl(pq[t] + off, val);
+                }
+            }
         }
     };
-    if (own) publish(sV, dV, vown);
+    // MB: every copy of the awaited buffer (mbarrier i: 0, 1 stresses, 2, 3
+    // velocities) has arrived; own slots written by this CTA's threads are
+    // visible after the block barrier
+    bool dead = false;   // a wait timed out: later waits are skipped (the step is flagged)
+    auto halo_wait = [&](int i) {
+        __syncthreads();
+        const unsigned par = (phs >> i) & 1u;
+        phs ^= 1u << i;
+        if (!dead) dead = !mbar_use(&mb[i], (unsigned)halo_n * 16u, par, &ctl->status);
+    };
+    if (own) publish(sV, dV, 0, vown);
 #pragma unroll
     for (int u = 0; u < NB; u++) {
         gx[u] = gy[u] = 0.0f;
@@ -827,7 +891,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
 
     // Two accumulator sets (even / odd slots) in both loops, so that a thread
     // has twice as many independent add chains in flight.
-    auto rate = [&](float4 va, float *Hd) {
+    auto rate = [&](float4 va, float *Hd, int vo) {   // vo: first slot of the velocity buffer
         float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, N3 = 0.f;
 #pragma unroll
         for (int c0 = 0; c0 < NB; c0 += CH) {
@@ -836,7 +900,7 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             for (int u = 0; u < CH; u++) {
                 if (c0 + u < nn) {
                     if constexpr (PUSH) {
-                        const float4 t = sV[aQ[c0 + u]];
+                        const float4 t = sV[vo + aQ[c0 + u]];
                         vb[u] = make_float2(t.x, t.y);
                     } else {
                         vb[u] = ld_cl2(aQ[c0 + u] + dV);
@@ -870,36 +934,40 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
         Hd[2] = M2 * B[0] + M3 * B[2];
         Hd[3] = M2 * B[1] + M3 * B[3];
     };
-    auto put_Q = [&]() {
+    auto put_Q = [&](int buf) {
         float Q[4];
         stress_QB<2>(H, B, P.mu, P.lam, Q);
         Qown = make_float4(Q[0], Q[1], Q[2], Q[3]);
-        publish(sQ, 0u, Qown);
+        publish(sQ, 0u, buf, Qown);
     };
 
+    if constexpr (MB) halo_wait(2);   // v^0
     if (own) {
         const float4 va = vown;
         float Hd[4];
-        rate(va, Hd);
+        rate(va, Hd, 0);
         for (int i = 0; i < 4; i++) H[i] = H[i] + hdts * Hd[i];
         if (!cons) {
             x = x + hdtsd * (double)va.x;
             y = y + hdtsd * (double)va.y;
         }
-        put_Q();
+        put_Q(0);
     }
     for (int kk = 0; kk < K; kk++) {
-        cluster_sync();
+        const int qb_ = kk & 1, vb_ = (kk + 1) & 1;   // buffers of Q^k and v^(k+1) (MB)
+        if constexpr (MB) halo_wait(qb_);
+        else cluster_sync();
         // (B) force loop and kick
         if (own) {
             const float4 Qa = Qown;
+            const int qo = MB ? qb_ * SLOTS : 0;
             float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < NB; c0 += CH) {
                 float4 qb[CH];
 #pragma unroll
                 for (int u = 0; u < CH; u++)
-                    if (c0 + u < nn) qb[u] = PUSH ? sQ[aQ[c0 + u]] : ld_cl(aQ[c0 + u]);
+                    if (c0 + u < nn) qb[u] = PUSH ? sQ[qo + aQ[c0 + u]] : ld_cl(aQ[c0 + u]);
 #pragma unroll
                 for (int u = 0; u < CH; u += 2) {
                     if (c0 + u < nn) {
@@ -921,26 +989,29 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 v.x += dts * av0;
                 v.y += dts * av1;
                 vown = v;
-                publish(sV, dV, v);
+                publish(sV, dV, vb_, v);
                 as0 += dtsd * (double)av0;
                 as1 += dtsd * (double)av1;
                 amax = fmaxf(amax, av0 * av0 + av1 * av1);
                 vmax = fmaxf(vmax, v.x * v.x + v.y * v.y);
+            } else if (MB) {
+                publish(sV, dV, vb_, vown);   // a held particle's copies count towards the transaction too
             }
         }
-        cluster_sync();
+        if constexpr (MB) halo_wait(2 + vb_);
+        else cluster_sync();
         // (C) deformation rate at v^{k+1}; second half drift; next first half + stress
         if (own) {
             const bool more = kk + 1 < K;
             const float4 va = vown;
             float Hd[4];
-            rate(va, Hd);
+            rate(va, Hd, MB ? vb_ * SLOTS : 0);
             // second half drift of this sub-step and, unless it is the last,
             // the first half drift of the next one with the same rate
             const float hH = more ? dts : hdts;
             const double hX = more ? dtsd : hdtsd;
             for (int i = 0; i < 4; i++) H[i] = H[i] + hH * Hd[i];
-            if (more) put_Q();   // first, so that its stores are under way during the drift
+            if (more) put_Q(vb_);   // first, so that its stores are under way during the drift
             if (!cons) {
                 x = x + hX * (double)va.x;
                 y = y + hX * (double)va.y;
@@ -968,19 +1039,45 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     cluster_sync();
 }
 
-template <int LP, bool PUSH>
+// shared arrays of the 2-D body: own slots, plus halo slots in the push
+// forms, twice over in the mbarrier form (double-buffered)
+template <int MODE>
+__host__ __device__ constexpr int solid2d_slots()
+{
+    return (kC1Threads + (MODE ? kHaloMax : 0)) * (MODE == 2 ? 2 : 1);
+}
+
+// mbarrier form: each CTA's four mbarriers (stress and velocity copies, two
+// buffers each), initialised once and visible cluster-wide before any copy
+template <int MODE>
+__device__ __forceinline__ void solid2d_mbar_setup(uint64_t *mb)
+{
+    if constexpr (MODE == 2) {
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < 4; i++) mbar_init(&mb[i], 1u);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        cluster_sync();
+    }
+}
+
+template <int LP, int MODE>
 __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, Solid s)
 {
     pdl_enter();
-    __shared__ float4 sQ[kC1Threads + (PUSH ? kHaloMax : 0)];
-    __shared__ float4 sV[kC1Threads + (PUSH ? kHaloMax : 0)];
+    __shared__ float4 sQ[solid2d_slots<MODE>()];
+    __shared__ float4 sV[solid2d_slots<MODE>()];
+    __shared__ __align__(8) uint64_t mb[4];
     __shared__ int s_inst;
     const unsigned rank = cluster_rank();
+    unsigned phs = 0u;
+    solid2d_mbar_setup<MODE>(mb);
     for (;;) {
         const int b = next_instance(s.queue, &s_inst, rank);
         if (b >= bt.B) break;
         const Inst &In = bt.I[b];
-        solid2d_body<LP, PUSH>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank);
+        solid2d_body<LP, MODE>(s, In.P, bt.ctl + b, In.s0, In.ns, sQ, sV, rank, mb,
+                               MODE ? s.halo_n[b * kClusterMax + rank] : 0, phs);
     }
 }
 
@@ -989,14 +1086,18 @@ __global__ void __launch_bounds__(kC1Threads * LP) k_solid_cluster2d(Batch bt, S
 // With LP = 1 it may be launched with 2 kC1Threads threads, the second half
 // idle: the CTA then holds its SM's registers, so no fluid block of the
 // concurrent main-stream loops shares the SM with the sub-steps.
-template <int LP, bool PUSH>
+template <int LP, int MODE>
 __global__ void __launch_bounds__(kC1Threads * 2) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
                                                                         Ctl *ctl)
 {
     pdl_enter();
-    __shared__ float4 sQ[kC1Threads + (PUSH ? kHaloMax : 0)];
-    __shared__ float4 sV[kC1Threads + (PUSH ? kHaloMax : 0)];
-    solid2d_body<LP, PUSH>(s, P, ctl, 0, s.n, sQ, sV, cluster_rank());
+    __shared__ float4 sQ[solid2d_slots<MODE>()];
+    __shared__ float4 sV[solid2d_slots<MODE>()];
+    __shared__ __align__(8) uint64_t mb[4];
+    const unsigned rank = cluster_rank();
+    unsigned phs = 0u;
+    solid2d_mbar_setup<MODE>(mb);
+    solid2d_body<LP, MODE>(s, P, ctl, 0, s.n, sQ, sV, rank, mb, MODE ? s.halo_n[rank] : 0, phs);
 }
 
 // Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
@@ -1046,34 +1147,44 @@ static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, 
     return launch_clusters(kern, threads, ctas, bt.B, max_clusters, st, bt, s);
 }
 
-// 1: the single-body push-form kernel runs with idle padding threads (see
+// 1: the single-body push-form kernels run with idle padding threads (see
 // k_solid_cluster2d_one)
 constexpr int kPadSolidOne = 1;
 
 static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
 {
-    static int mc2d[8][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
+    static int mc2d[10][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
     const bool one = bt.B == 1;
     if (dim == 2 && s.force_lane_path != 1 && s.max_nb <= kMaxNb2) {
         const int ctas = (s.max_ns + kC1Threads - 1) / kC1Threads;
         int rc;
-        const bool push = s.push_ok != 0 && s.force_lane_path != 3;   // 3: one thread per particle, pull form
-        if (s.force_lane_path == 2 && push)   // two threads per particle
-            rc = one ? launch_clusters(k_solid_cluster2d_one<2, true>, 2 * kC1Threads, ctas, 1, mc2d[2], st, s, P0,
+        // solid variants: 0 one thread per particle, 2 two threads, both with
+        // halo copies and cluster barriers where the halos fit; 3 pull form;
+        // 4 halo copies awaited on mbarriers (correct, measured slower)
+        const int v = s.force_lane_path;
+        const int mode = !s.push_ok || v == 3 ? 0 : (v == 4 ? 2 : 1);
+        const int pad = kPadSolidOne ? 2 : 1;
+        if (v == 2) {   // two threads per particle
+            if (mode == 1)
+                rc = one ? launch_clusters(k_solid_cluster2d_one<2, 1>, 2 * kC1Threads, ctas, 1, mc2d[0], st, s, P0,
+                                           bt.ctl)
+                         : launch_persistent(k_solid_cluster2d<2, 1>, 2 * kC1Threads, ctas, bt, s, mc2d[1], st);
+            else
+                rc = one ? launch_clusters(k_solid_cluster2d_one<2, 0>, 2 * kC1Threads, ctas, 1, mc2d[2], st, s, P0,
+                                           bt.ctl)
+                         : launch_persistent(k_solid_cluster2d<2, 0>, 2 * kC1Threads, ctas, bt, s, mc2d[3], st);
+        } else if (mode == 2) {
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, 2>, kC1Threads * pad, ctas, 1, mc2d[4], st, s, P0,
                                        bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<2, true>, 2 * kC1Threads, ctas, bt, s, mc2d[3], st);
-        else if (s.force_lane_path == 2)
-            rc = one ? launch_clusters(k_solid_cluster2d_one<2, false>, 2 * kC1Threads, ctas, 1, mc2d[4], st, s, P0,
+                     : launch_persistent(k_solid_cluster2d<1, 2>, kC1Threads, ctas, bt, s, mc2d[5], st);
+        } else if (mode == 1) {
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, 1>, kC1Threads * pad, ctas, 1, mc2d[6], st, s, P0,
                                        bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<2, false>, 2 * kC1Threads, ctas, bt, s, mc2d[5], st);
-        else if (push)
-            rc = one ? launch_clusters(k_solid_cluster2d_one<1, true>, kC1Threads * (kPadSolidOne ? 2 : 1), ctas, 1,
-                                       mc2d[0], st, s, P0, bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<1, true>, kC1Threads, ctas, bt, s, mc2d[1], st);
-        else
-            rc = one ? launch_clusters(k_solid_cluster2d_one<1, false>, kC1Threads, ctas, 1, mc2d[6], st, s, P0,
-                                       bt.ctl)
-                     : launch_persistent(k_solid_cluster2d<1, false>, kC1Threads, ctas, bt, s, mc2d[7], st);
+                     : launch_persistent(k_solid_cluster2d<1, 1>, kC1Threads, ctas, bt, s, mc2d[7], st);
+        } else {
+            rc = one ? launch_clusters(k_solid_cluster2d_one<1, 0>, kC1Threads, ctas, 1, mc2d[8], st, s, P0, bt.ctl)
+                     : launch_persistent(k_solid_cluster2d<1, 0>, kC1Threads, ctas, bt, s, mc2d[9], st);
+        }
         if (rc <= 0) return rc;
     }
     const int ctas = (s.max_ns + kPPC - 1) / kPPC;

@@ -250,22 +250,27 @@ def test_two_thread_solid_kernel_batch_equals_single():
 
 @pytest.mark.parametrize("name", ["dam_gate", "channel_flag", "floating_block"])
 def test_solid_push_and_pull_forms_are_bitwise_equal(name):
-    """Variant 0 reads neighbours from the CTA's own halo copies, variant 3 from the owning CTAs
-    across the cluster: the same values in the same order, so the same bits."""
+    """Variants 0 and 4 read neighbours from the CTA's own halo copies (refreshed with
+    stores ordered by cluster barriers, or with asynchronous stores counted on mbarriers),
+    variant 3 from the owning CTAs across the cluster: the same values in the same order,
+    so the same bits."""
     case = {"dam_gate": lambda: fc.dam_gate(seed=0), "channel_flag": lambda: fc.channel_flag(seed=0),
             "floating_block": lambda: fc.floating_block(seed=1)}[name]()
     sims = []
-    for variant in (0, 3):
+    for variant in (0, 3, 4):
         sim = Simulation.from_case(case)
         sim.set_tuning(4, 128, variant)
         for _ in range(4):
             sim.step(0.0)
         sim.sync()
         sims.append(sim)
-    a, b = sims[0].get_solid(), sims[1].get_solid()
-    for k in a:
-        assert np.array_equal(a[k], b[k]), k
+    a = sims[0].get_solid()
+    for other in sims[1:]:
+        b = other.get_solid()
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
     assert sims[0].info()["solid_path"] == 1
+    assert all(sim.info()["status"] == 0 for sim in sims)
 
 
 @pytest.mark.parametrize("name", ["dam_gate", "tiny_box_3d"])
