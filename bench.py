@@ -158,15 +158,24 @@ def _traffic(kernel, workload):
     return None
 
 
-def make_cases(workload, seed=0):
+# cell grid of the pair loops per workload (sphfsi_params::cell_reach):
+# 1 = cells of >= 2 h_F, 2 = cells of >= h_F
+CELL_REACH = {"dam_gate": 1, "flag_batch": 1, "duct_3d": 1, "flag_learned": 1}
+
+
+def make_cases(workload, seed=0, cell_reach=None):
     import fsi_cases
     if workload == "flag_batch":
-        return fsi_cases.flag_batch(seed=seed, n=256)
-    if workload == "duct_3d":
-        return [fsi_cases.duct_plate_3d(seed=seed, scale=1)]
-    if workload == "flag_learned":
-        return [fsi_cases.channel_flag(seed=seed)]
-    return [fsi_cases.dam_gate(seed=seed)]
+        cases = fsi_cases.flag_batch(seed=seed, n=256)
+    elif workload == "duct_3d":
+        cases = [fsi_cases.duct_plate_3d(seed=seed, scale=1)]
+    elif workload == "flag_learned":
+        cases = [fsi_cases.channel_flag(seed=seed)]
+    else:
+        cases = [fsi_cases.dam_gate(seed=seed)]
+    for c in cases:
+        c.cell_reach = CELL_REACH[workload] if cell_reach is None else cell_reach
+    return cases
 
 
 def sample_case(cases):
@@ -254,7 +263,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     label = WORKLOADS[args.workload]
-    cases = make_cases(args.workload, seed=rank)
+    cases = make_cases(args.workload, seed=rank, cell_reach=args.cell_reach)
     case = cases[0]
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
@@ -374,6 +383,7 @@ def run_gpu(args, rank, world, local_rank):
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
                    "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows")},
+                   "cell_reach": case.cell_reach,
                    "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -619,6 +629,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_gate", choices=sorted(WORKLOADS))
+    ap.add_argument("--cell-reach", type=int, default=None, choices=[1, 2],
+                    help="cell grid of the pair loops: 1 cells of >= 2 h_F, 2 cells of >= h_F (default per workload)")
     ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact[,tile[,records[,rows]]]]: fixed launch shape instead "
                                                  "of the autotuner (profiling runs)")
     args = ap.parse_args()

@@ -64,7 +64,13 @@ typedef struct sphfsi_ctx sphfsi_ctx;
  * periodic_x wraps fluid particles in x over [x_lo, x_lo + Lx); the grid's
  * x extent is then that period.  free_surface selects the density
  * reinitialisation rho = max(rho0 sigma / sigma0, rho0).  n_reinit is the
- * cadence of density reinitialisation and normal update in steps (0 = off). */
+ * cadence of density reinitialisation and normal update in steps (0 = off).
+ * cell_reach (no counterpart in the paper) sets the cell grid of the pair
+ * loops: 1 (or 0) cells of edge >= 2 h_F, the 3^d cells around a particle's
+ * cell hold its neighbours; 2 cells of edge >= h_F and the 5^d cells around
+ * it, which test fewer candidates per particle (a volume of (5 h_F)^d
+ * instead of (6 h_F)^d) in more, smaller cells.  With 2 the pair loops run
+ * in the cell form without tiles.  Results agree to rounding. */
 typedef struct {
     int32_t dim; /* 2 or 3 */
     int32_t periodic_x;
@@ -73,6 +79,7 @@ typedef struct {
     int32_t free_surface;
     int32_t n_reinit;
     double domain_lo[3], domain_hi[3];
+    int32_t cell_reach; /* 0 or 1: cells of >= 2 h_F; 2: cells of >= h_F */
 } sphfsi_params;
 
 /* Velocity-imposing inflow buffer (Section 4.1): fluid particles with
@@ -316,7 +323,8 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
  * with |r_i - r_j|^2 < (2 h)^2, h = 1.3 dp, computed in FP64 as dx*dx + dy*dy
  * (+ dz*dz) with the minimal image in x when p->periodic_x (the same test as
  * sphfsi_debug_neighbors).  The cell grid follows p (dim, domain box,
- * periodic x) exactly as a context built from p would.  Work is issued on
+ * periodic x) as a context built from p with cell_reach 1 would (the
+ * counts do not depend on the cell grid).  Work is issued on
  * cuda_stream and is asynchronous.
  *
  * Scratch (cell keys, the permutation, the cell histogram) is one

@@ -30,7 +30,8 @@ class SphError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("dim", C.c_int32), ("periodic_x", C.c_int32), ("gravity", C.c_double * 3),
                 ("x_lo", C.c_double), ("Lx", C.c_double), ("free_surface", C.c_int32),
-                ("n_reinit", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3)]
+                ("n_reinit", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
+                ("cell_reach", C.c_int32)]
 
 
 class Inflow(C.Structure):
@@ -161,10 +162,11 @@ def _f64(a, shape=None):
 
 
 def _params(dim, gravity=(0, 0, 0), periodic_x=0, x_lo=0.0, Lx=0.0, free_surface=0, n_reinit=0,
-            domain_lo=(0, 0, 0), domain_hi=(1, 1, 1)):
+            domain_lo=(0, 0, 0), domain_hi=(1, 1, 1), cell_reach=1):
     p = Params()
     p.dim, p.periodic_x, p.x_lo, p.Lx = dim, int(periodic_x), float(x_lo), float(Lx)
     p.free_surface, p.n_reinit = int(free_surface), int(n_reinit)
+    p.cell_reach = int(cell_reach)
     for k in range(3):
         p.gravity[k] = float(gravity[k]) if k < len(gravity) else 0.0
         p.domain_lo[k] = float(domain_lo[k]) if k < len(domain_lo) else 0.0
@@ -174,7 +176,7 @@ def _params(dim, gravity=(0, 0, 0), periodic_x=0, x_lo=0.0, Lx=0.0, free_surface
 
 def _case_params(case):
     return _params(case.dim, case.gravity, case.periodic_x, case.x_lo, case.Lx, case.free_surface,
-                   case.n_reinit, case.domain_lo, case.domain_hi)
+                   case.n_reinit, case.domain_lo, case.domain_hi, getattr(case, "cell_reach", 1))
 
 
 def _stream_handle(stream):

@@ -69,6 +69,7 @@ struct sphfsi_ctx {
     bool profiling = false;
     cudaEvent_t ev[kEvents] = {};
     int kernels_per_step = 0;
+    int max_reach = 1;   // largest cell reach of the instances (sphfsi_params::cell_reach)
     // side stream for the solid branch, which runs beside momentum and continuity
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -247,6 +248,9 @@ int make_inst(const InstHost &h, int D, Inst &d)
     const double hF = 1.3 * h.f_dp;
     Grid &g = d.g;
     std::memset(&g, 0, sizeof(g));
+    const int R = h.prm.cell_reach == 2 ? 2 : 1;   // cells of >= 2 h_F / R; neighbours within R cells
+    if (h.prm.cell_reach < 0 || h.prm.cell_reach > 2) return SPHFSI_E_INVAL;
+    g.reach = R;
     int64_t ncell = 1;
     for (int k = 0; k < 3; k++) {
         if (k >= D) {
@@ -262,9 +266,9 @@ int make_inst(const InstHost &h, int D, Inst &d)
             lo = h.prm.x_lo;
             L = h.prm.Lx;
         }
-        int64_t n = (int64_t)std::floor(L / (2.0 * hF));
+        int64_t n = (int64_t)std::floor(L / (2.0 * hF / R));
         if (n < 1) n = 1;
-        if (k == 0 && h.prm.periodic_x && n < 3) return SPHFSI_E_INVAL;
+        if (k == 0 && h.prm.periodic_x && n < 2 * R + 1) return SPHFSI_E_INVAL;
         g.lo[k] = lo;
         g.nc[k] = (int)n;
         g.cs[k] = L / (double)n;
@@ -630,6 +634,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
         InstHost &h = c->ih[b];
         if (!h.f_added) return SPHFSI_E_STATE;
         TRY(make_inst(h, D, h.d));
+        c->max_reach = std::max(c->max_reach, h.d.g.reach);
         h.d.f0 = (int)nf;
         h.d.nf = (int)h.nf;
         h.d.w0 = (int)nw;
@@ -669,7 +674,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // 35.4 vs 31.2 us): off by default
     F.bin_fused = 0;
     // neighbour cells a row at a time where latency, not issue, bounds the loops
-    F.rows = small ? 1 : 0;
+    // (rows and tiles are built for cells of >= 2 h_F)
+    F.rows = small && c->max_reach == 1 ? 1 : 0;
     // tiles: T cells of a grid row per block (16 in 2-D, 4 in 3-D); the
     // staging area holds about three times the mean neighbourhood
     {
@@ -1411,7 +1417,8 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
         t->solid_variant < 0 || t->solid_variant > 4 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
-        t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile))
+        t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile) ||
+        (c->max_reach > 1 && (t->rows || t->tile)))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
@@ -1515,13 +1522,13 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
             rc = consider(cur);
         }
         cur = *best;
-        if (!rc) {
+        if (!rc && c->max_reach == 1) {
             cur.tile = 1 - cur.tile;
             if (cur.tile) cur.rows = 0;
             rc = consider(cur);
         }
         cur = *best;
-        if (!rc && !cur.tile) {
+        if (!rc && !cur.tile && c->max_reach == 1) {
             cur.rows = 1 - cur.rows;
             rc = consider(cur);
         }

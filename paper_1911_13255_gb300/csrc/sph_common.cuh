@@ -71,6 +71,7 @@ struct Grid {
     int ncell;
     int periodic_x;
     double x_lo, Lx;
+    int reach;       // neighbour cells per direction: 1 (cells of >= 2 h_F) or 2 (>= h_F)
 };
 
 // Device-resident control block, one per instance, read by every kernel of a

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
 int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (f.n >= (1 << 27)) return -7;
+    if (f.n >= kMaxPairTargets) return -7;
     SPH_LAUNCH_PAIRS(k_density, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -167,10 +167,12 @@ __device__ __forceinline__ ff ff_delta(float xi, float li, float xj, float lj, f
     const ff u = ff_two_sum(t.hi, o);
     return ff_fast_two_sum(u.hi, __fadd_rn(__fadd_rn(t.lo, u.lo), __fadd_rn(__fsub_rn(li, lj), ol)));
 }
-// cell offset o = -dcell * edge as hi + lo (o is 0 or +-csf)
-__device__ __forceinline__ float off_lo(float o, float cslo)
+// cell offset o = -dcell * edge as hi + lo (o is 0, +-csf or +-2 csf)
+__device__ __forceinline__ float off_lo(float o, float csf, float cslo)
 {
-    return o == 0.0f ? 0.0f : (o > 0.0f ? cslo : -cslo);
+    // o = -dcell csf exactly, |dcell| <= 2; the remainder scales the same way
+    const float m = fabsf(o) > 1.5f * csf ? 2.0f : 1.0f;
+    return o == 0.0f ? 0.0f : (o > 0.0f ? m * cslo : -m * cslo);
 }
 
 // Wendland C2 shape (1 - q/2)^4 (1 + 2q) of the pair, q = |r_ij| / h_F, in
@@ -179,10 +181,10 @@ template <int D>
 __device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, const float4 &Pj, const float4 &Lj,
                                          float ox, float oy, float oz, const Grid &g, const Phys &P)
 {
-    const ff dx = ff_delta(Pi.x, Li.x, Pj.x, Lj.x, ox, off_lo(ox, g.cslo[0]));
-    const ff dy = ff_delta(Pi.y, Li.y, Pj.y, Lj.y, oy, off_lo(oy, g.cslo[1]));
+    const ff dx = ff_delta(Pi.x, Li.x, Pj.x, Lj.x, ox, off_lo(ox, g.csf[0], g.cslo[0]));
+    const ff dy = ff_delta(Pi.y, Li.y, Pj.y, Lj.y, oy, off_lo(oy, g.csf[1], g.cslo[1]));
     ff r2 = ff_add(ff_sqr(dx), ff_sqr(dy));
-    if (D == 3) r2 = ff_add(r2, ff_sqr(ff_delta(Pi.z, Li.z, Pj.z, Lj.z, oz, off_lo(oz, g.cslo[2]))));
+    if (D == 3) r2 = ff_add(r2, ff_sqr(ff_delta(Pi.z, Li.z, Pj.z, Lj.z, oz, off_lo(oz, g.csf[2], g.cslo[2]))));
     if (!(r2.hi > 0.0f)) return {1.0f, 0.0f};
     // r = sqrt(r2): FP32 root s plus one Newton correction (r2 - s^2) / (2 s)
     const float s = sqrtf(r2.hi);
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
 int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (f.n >= (1 << 27)) return -7;
+    if (f.n >= kMaxPairTargets) return -7;
     SPH_LAUNCH_PAIRS(k_reinit, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

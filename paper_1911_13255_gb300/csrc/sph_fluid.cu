@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
 int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0) return 0;
-    if (f.n >= (1 << 27)) return -7;
+    if (f.n >= kMaxPairTargets) return -7;
     SPH_LAUNCH_PAIRS(k_momentum, f.n, bt, f, w, s);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -151,30 +151,39 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_solid_fluid_force(Batch bt, Fl
         const float4 A = s.A4[k], VB = s.VB4[k], AB = s.AB4[k], N = s.N4[k];
         int cx, cy, cz;
         cell_xyz(s.cell_of[k], In, cx, cy, cz);
-        // a row of neighbour cells at a time (their starts loaded together)
-        for_each_row<D>(g, In.c0, cx, cy, cz, [&](const int c[3], float oy, float oz, int) {
-            const Row3 r = row_of(f.cstart, c);
-            for (int q = lane; q < r.n; q += L) {
-                int k;
-                const int j = row_slot(r, q, k);
-                const float ox = row_ox(k, g);
-                const float4 Pj = f.P4[j];
-                // the fluid side sees this pair with the opposite cell offset
-                float d[3] = {(Pj.x - A.x) - ox, (Pj.y - A.y) - oy, D == 3 ? (Pj.z - A.z) - oz : 0.0f};
-                float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
-                if (r2 >= P.rc2F) continue;
-                nsf++;
-                const float4 Vj = f.V4[j];
-                const float vj[3] = {Vj.x, Vj.y, Vj.z};
-                const float rhoj = P.rho0 + Vj.w;
-                float o[3];
-                fs_pair_force<D>(d, r2, vj, rhoj, Pj.w, VB, AB, N, P.VS, P, o);
-                float Vf = P.mF / rhoj;
-                fa[0] -= Vf * o[0];
-                fa[1] -= Vf * o[1];
-                fa[2] -= Vf * o[2];
-            }
-        });
+        auto pair = [&](int j, float ox, float oy, float oz) {
+            const float4 Pj = f.P4[j];
+            // the fluid side sees this pair with the opposite cell offset
+            float d[3] = {(Pj.x - A.x) - ox, (Pj.y - A.y) - oy, D == 3 ? (Pj.z - A.z) - oz : 0.0f};
+            float r2 = d[0] * d[0] + d[1] * d[1] + (D == 3 ? d[2] * d[2] : 0.0f);
+            if (r2 >= P.rc2F) return;
+            nsf++;
+            const float4 Vj = f.V4[j];
+            const float vj[3] = {Vj.x, Vj.y, Vj.z};
+            const float rhoj = P.rho0 + Vj.w;
+            float o[3];
+            fs_pair_force<D>(d, r2, vj, rhoj, Pj.w, VB, AB, N, P.VS, P, o);
+            float Vf = P.mF / rhoj;
+            fa[0] -= Vf * o[0];
+            fa[1] -= Vf * o[1];
+            fa[2] -= Vf * o[2];
+        };
+        if (g.reach == 1) {
+            // a row of neighbour cells at a time (their starts loaded together)
+            for_each_row<D>(g, In.c0, cx, cy, cz, [&](const int c[3], float oy, float oz, int) {
+                const Row3 r = row_of(f.cstart, c);
+                for (int q = lane; q < r.n; q += L) {
+                    int k;
+                    const int j = row_slot(r, q, k);
+                    pair(j, row_ox(k, g), oy, oz);
+                }
+            });
+        } else {
+            for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+                const int j1 = f.cstart[c + 1];
+                for (int j = f.cstart[c] + lane; j < j1; j += L) pair(j, ox, oy, oz);
+            });
+        }
     }
     for (int q = 0; q < D; q++) fa[q] = group_sum<L>(fa[q]);
     Counts cnt = {0u, 0u, 0u, nsf, 0.0f, {0.0, 0.0, 0.0}};

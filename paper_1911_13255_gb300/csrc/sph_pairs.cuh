@@ -36,23 +36,25 @@ static bool with_lanes(int L, Fn &&fn)
     return true;
 }
 
-// Visit the 3^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy, oz, code)
-// receives the offset o = -(dcell) * edge to add to (rel_i - rel_j) and
-// code = (dx + 1) + 3 (dy + 1) + 9 (dz + 1) (cell_offset recovers o from it).
+// Visit the (2R + 1)^d neighbour cells of (cx, cy, cz), R = g.reach.
+// fn(cell, ox, oy, oz, code) receives the offset o = -(dcell) * edge to add
+// to (rel_i - rel_j) and code = (dx + R) + W (dy + R) + W^2 (dz + R), W =
+// 2R + 1 (cell_offset recovers o from it; code < 125).
 template <int D, typename Fn>
 __device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int cy, int cz, Fn &&fn)
 {
-    const int z0 = D == 3 ? -1 : 0, z1 = D == 3 ? 1 : 0;
+    const int R = g.reach, W = 2 * R + 1;
+    const int z0 = D == 3 ? -R : 0, z1 = D == 3 ? R : 0;
 #pragma unroll 1
     for (int dz = z0; dz <= z1; dz++) {
         int z = cz + dz;
         if (z < 0 || z >= g.nc[2]) continue;
 #pragma unroll 1
-        for (int dy = -1; dy <= 1; dy++) {
+        for (int dy = -R; dy <= R; dy++) {
             int y = cy + dy;
             if (y < 0 || y >= g.nc[1]) continue;
 #pragma unroll 1
-            for (int dx = -1; dx <= 1; dx++) {
+            for (int dx = -R; dx <= R; dx++) {
                 int x = cx + dx;
                 if (x < 0 || x >= g.nc[0]) {
                     if (!g.periodic_x) continue;
@@ -60,7 +62,7 @@ __device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int
                 }
                 int c = c0 + x + g.nc[0] * (y + g.nc[1] * z);
                 fn(c, -(float)dx * g.csf[0], -(float)dy * g.csf[1], -(float)dz * g.csf[2],
-                   (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                   (dx + R) + W * (dy + R) + W * W * (dz + R));
             }
         }
     }
@@ -138,7 +140,8 @@ __device__ __forceinline__ float row_ox(int k, const Grid &g) { return (float)(1
 
 __device__ __forceinline__ void cell_offset(int code, const Grid &g, float &ox, float &oy, float &oz)
 {
-    const int dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
+    const int R = g.reach, W = 2 * R + 1;
+    const int dx = code % W - R, dy = (code / W) % W - R, dz = code / (W * W) - R;
     ox = -(float)dx * g.csf[0];
     oy = -(float)dy * g.csf[1];
     oz = -(float)dz * g.csf[2];
@@ -310,14 +313,18 @@ __device__ __forceinline__ void tile_loop(const Batch &bt, const Fluid &f, const
 // compacted (CP = true): the candidate test passes only 1/3 (2-D) to 1/6
 // (3-D) of the candidates, so evaluating inside the loop runs the pair
 // arithmetic in almost every warp iteration with few lanes active.  Each
-// thread first writes its in-support neighbours (j << 5 | cell-offset code)
+// thread first writes its in-support neighbours (j << 7 | cell-offset code)
 // into its own list in shared memory (slot k at list[k * stride]), then
 // evaluates the list with all lanes busy; a full list is drained early.
-// Requires j < 2^27.
+// Requires j < 2^25.
 //
 // Both return the number of in-support pairs and visit the pairs of a
 // target in the same order.
 constexpr int kPairCap = 32;
+// list entry j << kCodeBits | cell-offset code (code < 125): j < 2^25
+constexpr int kCodeBits = 7;
+constexpr uint32_t kCodeMask = (1u << kCodeBits) - 1u;
+constexpr int kMaxPairTargets = 1 << (32 - kCodeBits);
 
 template <int D, int L, bool CP, typename Fetch, typename Pair>
 __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz,
@@ -345,9 +352,9 @@ __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Gri
 #pragma unroll 1
             for (int k = 0; k < cnt; k++) {
                 const uint32_t e = list[k * stride];
-                const int j = (int)(e >> 5);
+                const int j = (int)(e >> kCodeBits);
                 float ox, oy, oz;
-                cell_offset((int)(e & 31u), g, ox, oy, oz);
+                cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
                 const float4 Pj = f.P4[j];
                 float d[3];
                 const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -361,7 +368,7 @@ __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Gri
                 if (j == i) continue;
                 float d[3];
                 if (rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) >= rc2) continue;
-                list[cnt * stride] = ((uint32_t)j << 5) | (uint32_t)code;
+                list[cnt * stride] = ((uint32_t)j << kCodeBits) | (uint32_t)code;
                 cnt++;
                 cnt_total++;
                 if (cnt == kPairCap) drain();
@@ -385,9 +392,9 @@ __device__ __forceinline__ unsigned fluid_pairs_tile(const Fluid &f, const Grid 
 #pragma unroll 1
         for (int k = 0; k < cnt; k++) {
             const uint32_t e = list[k * stride];
-            const int q = (int)(e >> 5);
+            const int q = (int)(e >> kCodeBits);
             float ox, oy, oz;
-            cell_offset((int)(e & 31u), g, ox, oy, oz);
+            cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
             const float4 Pj = ts.sP[q];
             float d[3];
             const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -408,7 +415,7 @@ __device__ __forceinline__ unsigned fluid_pairs_tile(const Fluid &f, const Grid 
             if (r2 >= rc2) continue;
             cnt_total++;
             if constexpr (CP) {
-                list[cnt * stride] = ((uint32_t)q << 5) | (uint32_t)code;
+                list[cnt * stride] = ((uint32_t)q << kCodeBits) | (uint32_t)code;
                 cnt++;
                 if (cnt == kPairCap) drain();
             } else {
@@ -468,9 +475,9 @@ __device__ __forceinline__ unsigned fluid_pairs_rows(const Fluid &f, const Walls
 #pragma unroll 1
         for (int k = 0; k < cnt; k++) {
             const uint32_t e = list[k * stride];
-            const int j = (int)(e >> 5);
+            const int j = (int)(e >> kCodeBits);
             float ox, oy, oz;
-            cell_offset((int)(e & 31u), g, ox, oy, oz);
+            cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
             const float4 Pj = f.P4[j];
             float d[3];
             const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -499,7 +506,7 @@ __device__ __forceinline__ unsigned fluid_pairs_rows(const Fluid &f, const Walls
                 if (j == i) return;
                 float d[3];
                 if (rel_d<D>(Pi, Pj, row_ox(k, g), oy, oz, d) >= rc2) return;
-                list[cnt * stride] = ((uint32_t)j << 5) | (uint32_t)(code0 + k);
+                list[cnt * stride] = ((uint32_t)j << kCodeBits) | (uint32_t)(code0 + k);
                 cnt++;
                 cnt_total++;
                 if (cnt == kPairCap) drain();
