@@ -214,6 +214,27 @@ int sphfsi_set_time(sphfsi_ctx *c, double t, int64_t step);
 
 int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out);
 
+/* Time-step criteria of the selected instance at its current state, from
+ * the maxima of the last finished step (the initial velocities before the
+ * first step): dt_ac = 0.6 h_F / (c0 + |v|max,F) (Eq. dt-relax, the step a
+ * call with dt_F <= 0 takes); dt_ad = 0.25 min(h_F / |v|max,F, h_F^2 / nu)
+ * (advection and viscous limit); dt_S = 0.6 min(h_S / (c_S + |v|max,S),
+ * sqrt(h_S / |a|max,S)) (Eq. dts-advection; 1e300 without a solid).  The
+ * automatic sub-step count is K = floor(dt_F / dt_S) + 1. */
+int sphfsi_suggest_dt(sphfsi_ctx *c, double *dt_ac, double *dt_ad, double *dt_S);
+
+/* Checkpoint (no counterpart in the paper): the whole device state of a
+ * finalised context (every instance: particles, records, static lists,
+ * control blocks with time, step and counters) as one host blob.
+ * sphfsi_state_size gives its size; sphfsi_get_state writes it into
+ * caller-owned host memory of at least that size; sphfsi_set_state restores
+ * it into a context built by the same creation calls (same sizes; else
+ * SPHFSI_E_INVAL and nothing changes).  Both wait for the context's work.
+ * The learned sub-stepper's network is not part of the state. */
+int sphfsi_state_size(sphfsi_ctx *c, int64_t *bytes);
+int sphfsi_get_state(sphfsi_ctx *c, void *blob, int64_t bytes);
+int sphfsi_set_state(sphfsi_ctx *c, const void *blob, int64_t bytes);
+
 /* Neighbour sets from the device cell list at the current positions with the
  * FP64 in-support test r^2 < (2 h_F)^2 (dx*dx + dy*dy (+ dz*dz), no FMA).
  * which: 0 fluid-fluid, 1 fluid-wall, 2 fluid-solid, 3 solid-fluid.

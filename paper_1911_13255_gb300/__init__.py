@@ -92,6 +92,10 @@ _SIGS = {
     "sphfsi_set_solid_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sphfsi_set_time": (C.c_int, [_vp, C.c_double, C.c_int64]),
     "sphfsi_get_info": (C.c_int, [_vp, C.POINTER(Info)]),
+    "sphfsi_suggest_dt": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "sphfsi_state_size": (C.c_int, [_vp, _vp]),
+    "sphfsi_get_state": (C.c_int, [_vp, _vp, C.c_int64]),
+    "sphfsi_set_state": (C.c_int, [_vp, _vp, C.c_int64]),
     "sphfsi_debug_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_int64)]),
     "sphfsi_set_profiling": (C.c_int, [_vp, C.c_int]),
     "sphfsi_set_solid_path": (C.c_int, [_vp, C.c_int]),
@@ -389,6 +393,25 @@ class Simulation:
 
     def set_time(self, t, step):
         _check(lib().sphfsi_set_time(self.h, float(t), int(step)), "sphfsi_set_time")
+
+    def suggest_dt(self):
+        """(dt_ac, dt_ad, dt_S) of the selected instance (include/sphfsi.h)."""
+        out = [C.c_double(), C.c_double(), C.c_double()]
+        _check(lib().sphfsi_suggest_dt(self.h, *[C.byref(o) for o in out]), "sphfsi_suggest_dt")
+        return tuple(o.value for o in out)
+
+    def get_state(self):
+        """The whole device state as bytes (a checkpoint)."""
+        n = C.c_int64()
+        _check(lib().sphfsi_state_size(self.h, C.byref(n)), "sphfsi_state_size")
+        buf = np.empty(n.value, np.uint8)
+        _check(lib().sphfsi_get_state(self.h, _ptr(buf), n.value), "sphfsi_get_state")
+        return buf.tobytes()
+
+    def set_state(self, blob):
+        """Restore a checkpoint taken from a context built the same way."""
+        buf = np.frombuffer(bytes(blob), np.uint8)
+        _check(lib().sphfsi_set_state(self.h, _ptr(buf), buf.size), "sphfsi_set_state")
 
     def info(self):
         i = Info()

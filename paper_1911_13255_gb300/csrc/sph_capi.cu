@@ -1296,6 +1296,98 @@ int sphfsi_set_time(sphfsi_ctx *c, double t, int64_t step)
     return cuda_rc(cudaMemcpy(dc, &hc, sizeof(Ctl), cudaMemcpyHostToDevice));
 }
 
+// Time-step criteria of the selected instance at its current state (the
+// maxima of the last finished step, or the initial velocities before the
+// first): Eqs. dt-relax (acoustic), the advection/viscous limit, and Eq.
+// dts-advection (solid).
+int sphfsi_suggest_dt(sphfsi_ctx *c, double *dt_ac, double *dt_ad, double *dt_S)
+{
+    TRY(check_ctx(c, true));
+    if (!dt_ac || !dt_ad || !dt_S) return SPHFSI_E_INVAL;
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    Ctl hc;
+    TRY(cuda_rc(cudaMemcpy(&hc, c->ctl + c->sel, sizeof(Ctl), cudaMemcpyDeviceToHost)));
+    const Phys &P = c->ih[c->sel].d.P;
+    const double vF = hc.prev_vmaxF, vS = hc.prev_vmaxS, aS = hc.prev_amaxS;
+    *dt_ac = 0.6 * P.hF_d / (P.c0_d + vF);
+    const double nu = P.eta_d / P.rho0_d;
+    const double a1 = vF > 0.0 ? P.hF_d / vF : 1e300, a2 = nu > 0.0 ? P.hF_d * P.hF_d / nu : 1e300;
+    *dt_ad = 0.25 * (a1 < a2 ? a1 : a2);
+    if (c->ih[c->sel].ns > 0) {
+        const double b1 = P.hS_d / (P.cS_d + vS), b2 = aS > 0.0 ? std::sqrt(P.hS_d / aS) : 1e300;
+        *dt_S = 0.6 * (b1 < b2 ? b1 : b2);
+    } else {
+        *dt_S = 1e300;
+    }
+    return SPHFSI_OK;
+}
+
+// Checkpoint blob: a header, then every device allocation of the context in
+// allocation order, each preceded by its size.
+namespace {
+constexpr uint64_t kStateMagic = 0x3130305354534853ull;   // "SHSTS001"
+}
+
+int sphfsi_state_size(sphfsi_ctx *c, int64_t *bytes)
+{
+    TRY(check_ctx(c, true));
+    if (!bytes) return SPHFSI_E_INVAL;
+    uint64_t n = 3 * sizeof(uint64_t);
+    for (auto &a : c->allocs) n += sizeof(uint64_t) + a.second;
+    *bytes = (int64_t)n;
+    return SPHFSI_OK;
+}
+
+int sphfsi_get_state(sphfsi_ctx *c, void *blob, int64_t bytes)
+{
+    int64_t need = 0;
+    TRY(sphfsi_state_size(c, &need));
+    if (!blob || bytes < need) return SPHFSI_E_INVAL;
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    if (c->side) TRY(cuda_rc(cudaStreamSynchronize(c->side)));
+    uint8_t *p = (uint8_t *)blob;
+    const uint64_t head[3] = {kStateMagic, (uint64_t)c->allocs.size(), (uint64_t)need};
+    std::memcpy(p, head, sizeof(head));
+    p += sizeof(head);
+    for (auto &a : c->allocs) {
+        const uint64_t sz = a.second;
+        std::memcpy(p, &sz, sizeof(sz));
+        p += sizeof(sz);
+        TRY(cuda_rc(cudaMemcpy(p, a.first, a.second, cudaMemcpyDeviceToHost)));
+        p += a.second;
+    }
+    return SPHFSI_OK;
+}
+
+int sphfsi_set_state(sphfsi_ctx *c, const void *blob, int64_t bytes)
+{
+    int64_t need = 0;
+    TRY(sphfsi_state_size(c, &need));
+    if (!blob || bytes != need) return SPHFSI_E_INVAL;
+    const uint8_t *p = (const uint8_t *)blob;
+    uint64_t head[3];
+    std::memcpy(head, p, sizeof(head));
+    if (head[0] != kStateMagic || head[1] != (uint64_t)c->allocs.size() || head[2] != (uint64_t)need)
+        return SPHFSI_E_INVAL;
+    p += sizeof(head);
+    // check every size first, so that a mismatched blob leaves the state untouched
+    const uint8_t *q = p;
+    for (auto &a : c->allocs) {
+        uint64_t sz;
+        std::memcpy(&sz, q, sizeof(sz));
+        if (sz != a.second) return SPHFSI_E_INVAL;
+        q += sizeof(sz) + sz;
+    }
+    TRY(cuda_rc(cudaStreamSynchronize(c->st)));
+    if (c->side) TRY(cuda_rc(cudaStreamSynchronize(c->side)));
+    for (auto &a : c->allocs) {
+        p += sizeof(uint64_t);
+        TRY(cuda_rc(cudaMemcpy(a.first, p, a.second, cudaMemcpyHostToDevice)));
+        p += a.second;
+    }
+    return SPHFSI_OK;
+}
+
 int sphfsi_get_info(sphfsi_ctx *c, sphfsi_info *out)
 {
     if (!c || !out) return SPHFSI_E_INVAL;
