@@ -1,12 +1,13 @@
 // Cell-linked-list neighbour build (Alg. 1, "particle-neighbour list"; the
 // paper rebuilds it per advection step, this library every coarse step):
 // a counting sort of particles by the linear index of their cell, cells of
-// edge >= 2 h_F.  The sort is a single-digit radix sort whose digit is the
-// global cell index: histogram (atomics), exclusive scan per instance,
-// scatter, then a per-cell insertion sort by particle id so the order is
-// deterministic and depends on the current state only.  The records kernel
-// gathers the fluid state into cell order and emits the FP32 records the
-// pair loops read.  Also: the per-step control kernel and the finish kernel.
+// edge >= 2 h_F (or >= h_F, Grid::reach = 2).  The sort is a single-digit
+// radix sort whose digit is the global cell index: histogram (atomics),
+// exclusive scan per instance, scatter, then a per-cell ranking by particle
+// id so the order is deterministic and depends on the current state only;
+// the ranking kernel gathers the fluid state into cell order and emits the
+// FP32 records the pair loops read.  The binning kernel also does the step
+// control; the finish kernel ends a step.
 #include "sph_common.cuh"
 
 namespace sph {
