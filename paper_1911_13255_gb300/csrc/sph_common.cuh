@@ -307,9 +307,16 @@ __device__ __forceinline__ double warp_sum_d(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// maximum that keeps a NaN visible (as +inf: fmaxf alone would drop it), so
+// that a non-finite state reaches the finish kernel's check
+__device__ __forceinline__ float max_keep_nan(float a, float b)
+{
+    return (a != a || b != b) ? __int_as_float(0x7f800000) : fmaxf(a, b);
+}
+
 __device__ __forceinline__ float warp_max(float v)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 __device__ __forceinline__ unsigned warp_sum_u(unsigned v)

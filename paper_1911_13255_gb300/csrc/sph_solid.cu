@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Batch bt, Solid 
                     s.asum[3 * a + k] += dtsd * (double)av[k];
                     a2 += av[k] * av[k];
                 }
-                amax = fmaxf(amax, a2);
-                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
+                amax = max_keep_nan(amax, a2);
+                vmax = max_keep_nan(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
             }
         }
         if (!grid_barrier(s.bar, &ctl->status)) return;
@@ -567,8 +567,8 @@ __device__ __forceinline__ void solid_lanes_body(const Solid &s, const Phys &P, 
                     as[k] += dtsd * (double)av[k];
                     a2 += av[k] * av[k];
                 }
-                amax = fmaxf(amax, a2);
-                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
+                amax = max_keep_nan(amax, a2);
+                vmax = max_keep_nan(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
             }
         }
         cluster_sync();
@@ -992,8 +992,8 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 publish(sV, dV, vb_, v);
                 as0 += dtsd * (double)av0;
                 as1 += dtsd * (double)av1;
-                amax = fmaxf(amax, av0 * av0 + av1 * av1);
-                vmax = fmaxf(vmax, v.x * v.x + v.y * v.y);
+                amax = max_keep_nan(amax, av0 * av0 + av1 * av1);
+                vmax = max_keep_nan(vmax, v.x * v.x + v.y * v.y);
             } else if (MB) {
                 publish(sV, dV, vb_, vown);   // a held particle's copies count towards the transaction too
             }
