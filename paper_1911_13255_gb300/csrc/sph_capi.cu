@@ -721,6 +721,22 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &F.ccount, ncell));
     TRY(dalloc(c, &F.live, 2 * (size_t)ncell));
     TRY(dalloc(c, &F.nlive, 1));
+    {
+        // tiles of the histogram scan, segment by segment (fluid of every
+        // instance, then solid)
+        std::vector<int2> tiles;
+        const int sets = ns > 0 ? 2 : 1, tc = scan_tile_cells();
+        for (int set = 0; set < sets; set++)
+            for (int b = 0; b < B; b++) {
+                const int nt = (c->ih[b].d.g.ncell + tc - 1) / tc;
+                for (int k = 0; k < nt; k++) tiles.push_back(make_int2(set * B + b, k));
+            }
+        F.nscan_tiles = (int)tiles.size();
+        TRY(dalloc(c, &F.scan_tiles, tiles.size()));
+        TRY(upload(c, F.scan_tiles, tiles));
+        TRY(dalloc(c, &F.scan_status, tiles.size()));
+        TRY(dalloc(c, &F.scan_ctl, 2));
+    }
     TRY(dalloc(c, &F.bsum, 4096));
     TRY(dalloc(c, &F.gbar, 2));
     // ---- walls

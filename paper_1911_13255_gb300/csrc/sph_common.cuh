@@ -175,6 +175,12 @@ struct Fluid {
     int *cstart;      // total cells + 1
     int *ccount;      // total cells (histogram / scatter cursor)
     int *live, *nlive;  // non-empty cells of the step (fluid c, solid ncell + c), listed by the scatter
+    // decoupled look-back scan of the histograms: tiles of kScanTile cells,
+    // (segment, tile) per ticket, segment = set * B + instance
+    int2 *scan_tiles;
+    int nscan_tiles;
+    unsigned long long *scan_status;   // per tile: epoch, flag, value
+    unsigned *scan_ctl;                // [0] ticket, [1] epoch
     int bin_fused;      // 1: binning as one cooperative kernel with grid barriers (small problems)
     int *bsum;          // its per-block partial sums (kBinFusedMaxBlocks)
     unsigned *gbar;     // its grid barrier: [0] arrivals, [1] generation
@@ -367,6 +373,7 @@ __device__ __forceinline__ float dW_F(float r, const Phys &P)
 int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, double dt_fixed, int K_fixed,
                    cudaStream_t st);
 int bin_kernels(const Fluid &f);
+int scan_tile_cells();
 int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
 int launch_finish(const Batch &bt, int learned, unsigned *gbar, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);

@@ -218,7 +218,11 @@ __global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed,
 {
     pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *f.nlive = 0;
+    if (t == 0) {
+        *f.nlive = 0;
+        f.scan_ctl[0] = 0u;    // the scan's tickets
+        f.scan_ctl[1] += 1u;   // and its epoch: this binning's tile states
+    }
     bin_one<D>(bt, f, s, t, step, dt_fixed, K_fixed);
 }
 
@@ -308,6 +312,110 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_seg(Batch bt, int *fcount
     const int base = set == 0 ? In.f0 : (set == 1 ? In.s0 : In.w0);
     scan_cells(count + In.c0, count + In.c0, start + In.c0, In.g.ncell, base);
     if (b == bt.B - 1 && threadIdx.x == 0) start[bt.ncell] = set == 0 ? nf : (set == 1 ? ns : nw);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of the cell histograms over many blocks: every (instance,
+// set) segment is cut into tiles of kScanTile cells, and tiles take tickets
+// in segment order, so a tile only waits for tiles that started before it.
+// Each block scans its tile (8 consecutive cells per thread), publishes the
+// tile's sum, then adds the sums published by the tiles before it in its
+// segment, back to the first that has published its inclusive prefix
+// (decoupled look-back), and publishes its own inclusive prefix.  A tile's
+// state word holds the binning's epoch (bits 34..63), a flag (1 sum, 2
+// inclusive prefix) and the value, so no reset is needed between steps.
+// Waits are bounded: on a time-out the status bit is set.
+// ---------------------------------------------------------------------------
+constexpr int kScanLbThreads = 256, kScanLbPer = 8, kScanTile = kScanLbThreads * kScanLbPer;
+
+__device__ __forceinline__ unsigned long long scan_word(unsigned epoch, unsigned flag, int value)
+{
+    return ((unsigned long long)(epoch & 0x3fffffffu) << 34) | ((unsigned long long)flag << 32) | (unsigned)value;
+}
+
+__global__ void __launch_bounds__(kScanLbThreads) k_scan_lb(Batch bt, Fluid f, Solid s)
+{
+    pdl_enter();
+    __shared__ int s_tile, s_pre, s_warp[kScanLbThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) s_tile = (int)atomicAdd(&f.scan_ctl[0], 1u);
+    __syncthreads();
+    const int T = s_tile;
+    if (T >= f.nscan_tiles) return;
+    const unsigned epoch = f.scan_ctl[1];
+    const int2 tk = f.scan_tiles[T];
+    const int set = tk.x / bt.B, b = tk.x % bt.B;
+    const Inst &In = bt.I[b];
+    int *count = (set == 0 ? f.ccount : s.ccount) + In.c0;
+    int *start = (set == 0 ? f.cstart : s.cstart) + In.c0;
+    const int base = set == 0 ? In.f0 : In.s0;
+    const int n = In.g.ncell;
+    // this thread's cells c0 .. c0 + 7 of the tile
+    const int c0 = tk.y * kScanTile + t * kScanLbPer;
+    int v[kScanLbPer], run = 0;
+#pragma unroll
+    for (int j = 0; j < kScanLbPer; j++) {
+        v[j] = c0 + j < n ? count[c0 + j] : 0;
+        run += v[j];
+    }
+    int x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    int woff = 0, tile_sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanLbThreads / 32; k++) {
+        woff += k < w ? s_warp[k] : 0;
+        tile_sum += s_warp[k];
+    }
+    if (t == 0) {
+        int pre = 0;
+        if (tk.y == 0) {
+            __threadfence();
+            atomicExch(&f.scan_status[T], scan_word(epoch, 2u, tile_sum));
+        } else {
+            __threadfence();
+            atomicExch(&f.scan_status[T], scan_word(epoch, 1u, tile_sum));
+            for (int j = T - 1;;) {
+                const unsigned long long wd = atomicAdd(&f.scan_status[j], 0ull);
+                const unsigned fl = (unsigned)(wd >> 32) & 3u;
+                if ((unsigned)(wd >> 34) != (epoch & 0x3fffffffu) || fl == 0u) {
+                    long long it = 0;
+                    unsigned long long w2 = wd;
+                    while (((unsigned)(w2 >> 34) != (epoch & 0x3fffffffu) || ((unsigned)(w2 >> 32) & 3u) == 0u) &&
+                           ++it < kSpinLimit)
+                        w2 = atomicAdd(&f.scan_status[j], 0ull);
+                    if (it >= kSpinLimit) {
+                        atomicOr(&bt.ctl[b].status, ST_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                pre += (int)(unsigned)wd;
+                if (fl == 2u) break;
+                --j;
+            }
+            __threadfence();
+            atomicExch(&f.scan_status[T], scan_word(epoch, 2u, pre + tile_sum));
+        }
+        s_pre = pre;
+    }
+    __syncthreads();
+    int st = base + s_pre + woff + x - run;
+#pragma unroll
+    for (int j = 0; j < kScanLbPer; j++) {
+        if (c0 + j < n) {
+            start[c0 + j] = st;
+            count[c0 + j] = 0;   // the histogram becomes the scatter cursor
+        }
+        st += v[j];
+    }
+    // the end of the last instance's slots
+    if (b == bt.B - 1 && t == 0 && c0 <= n && n <= tk.y * kScanTile + kScanTile)
+        (set == 0 ? f.cstart : s.cstart)[bt.ncell] = set == 0 ? f.n : s.n;
 }
 
 // Scatter into the cells' slot ranges (arbitrary order inside a cell); with
@@ -552,6 +660,7 @@ __global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
 }
 
 constexpr int kRecordBlocksPerSM = 64;
+constexpr bool kScanLookBack = true;   // the many-block scan; false: one block per segment
 
 // ---------------------------------------------------------------------------
 // Binning as one cooperative kernel (Fluid::bin_fused, small problems, where
@@ -700,6 +809,8 @@ static int launch_bin_fused(K kern, int nb, cudaStream_t st, const Batch &bt, co
 // kernels launch_bin_all launches in a step with particles
 int bin_kernels(const Fluid &f) { return f.bin_fused ? 1 : (f.split_records ? 5 : 4); }
 
+int scan_tile_cells() { return kScanTile; }
+
 int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, double dt_fixed, int K_fixed,
                    cudaStream_t st)
 {
@@ -715,8 +826,11 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
     if (dim == 2) launch_k(k_bin_all<2>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);
     else launch_k(k_bin_all<3>, nbt, kBlock, 0, st, bt, f, s, step, dt_fixed, K_fixed);
     if (np == 0) return cudaGetLastError() == cudaSuccess ? 0 : -3;
-    launch_k(k_scan_seg, bt.B * (s.n ? 2 : 1), kScanThreads, 0, st, bt, f.ccount, f.cstart, f.n, s.ccount, s.cstart,
-             s.n, (int *)nullptr, (int *)nullptr, 0, 0);
+    if (kScanLookBack)
+        launch_k(k_scan_lb, (unsigned)f.nscan_tiles, kScanLbThreads, 0, st, bt, f, s);
+    else
+        launch_k(k_scan_seg, bt.B * (s.n ? 2 : 1), kScanThreads, 0, st, bt, f.ccount, f.cstart, f.n, s.ccount,
+                 s.cstart, s.n, (int *)nullptr, (int *)nullptr, 0, 0);
     // records from the cell groups: over the listed non-empty cells; ranks
     // only (large problems): over all cells, no list (its counter would
     // serialise one atomic per warp)
