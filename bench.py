@@ -272,7 +272,7 @@ def run_gpu(args, rank, world, local_rank):
         sim.set_tuning(*vals)
         tuning = sim.tuning()
     else:
-        tuning = sim.autotune(0.0, steps=10) if args.workload != "dam_gate" else sim.tuning()
+        tuning = sim.autotune(0.0, steps=20) if args.workload != "dam_gate" else sim.tuning()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         sim.run(1, 0.0)

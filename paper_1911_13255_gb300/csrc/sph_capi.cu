@@ -676,6 +676,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
     // neighbour cells a row at a time where latency, not issue, bounds the loops
     // (rows and tiles are built for cells of >= 2 h_F)
     F.rows = small && c->max_reach == 1 ? 1 : 0;
+    F.reach = c->max_reach;
     // tiles: T cells of a grid row per block (16 in 2-D, 4 in 3-D); the
     // staging area holds about three times the mean neighbourhood
     {

@@ -157,6 +157,7 @@ struct Fluid {
     int compact;      // 1: fluid-fluid pairs through per-thread in-support lists (tuned)
     int tile;         // 1: one block per tile of cells, neighbours staged in shared memory (tuned)
     int rows;         // 1: pair loops visit the neighbour cells a row at a time (tuned; not with tile)
+    int reach;        // neighbour cells per direction the pair kernels visit: the largest Grid::reach
     int split_records;  // 1: binning ranks per cell, then writes records per slot (tuned)
     int4 *tiles;      // (instance, first global cell, cells, 0) per tile
     int ntiles;

@@ -12,7 +12,7 @@ namespace sph {
 // a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}) + second half drift;
 // writes the end-of-step state to s[0] in cell order
 // ---------------------------------------------------------------------------
-template <int D, int L, bool CP, bool ROWS>
+template <int D, int L, bool CP, int FORM>
 __device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
                                                  bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
@@ -44,7 +44,7 @@ __device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, con
             if (r2 >= P.rc2F) return;
             rate += fs_pair_drho<D>(d, r2, vi, rhoi, pi, s.VB4[b], s.AB4[b], s.N4[b], P.VS, P);
         };
-        fluid_pairs<D, L, CP, ROWS>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
+        fluid_pairs<D, L, CP, FORM>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
                                 [&](int j) { return f.W4[j]; },
                                 [&](int, const float4 &, const float4 &Wj, const float *d, float r2, float, float,
                                     float) {
@@ -86,7 +86,7 @@ __device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, con
     S.id[i] = M.id[i];
 }
 
-template <int D, int L, bool CP, bool TILE, bool ROWS>
+template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
@@ -95,11 +95,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls 
     const int stride = blockDim.x;
     if constexpr (!TILE) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        density_one<D, L, CP, ROWS>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+        density_one<D, L, CP, FORM>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
     } else {
         tile_loop<D, L>(bt, f, f.W4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
                         [&](int i, bool act, const TileSrc *ts) {
-                            density_one<D, L, CP, ROWS>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                            density_one<D, L, CP, FORM>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
                         });
     }
 }
@@ -200,7 +200,7 @@ __device__ __forceinline__ ff W_ff_shape(const float4 &Pi, const float4 &Li, con
     return ff_mul(ff_sqr(a2), bq);
 }
 
-template <int D, int L, bool CP, bool ROWS>
+template <int D, int L, bool CP, int FORM>
 __device__ __forceinline__ void reinit_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
                                                  bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
@@ -229,7 +229,7 @@ __device__ __forceinline__ void reinit_one(const Batch &bt, const Fluid &f, cons
             sS = ff_add(sS, W_ff_shape<D>(Pi, Li, Aq, s.L4[q], ox, oy, oz, g, P));
         };
         // the screen passes pairs up to 1.0001 (2 h)^2; W_ff_shape returns 0 beyond the support
-        fluid_pairs<D, L, CP, ROWS>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, screen, list, stride, ts,
+        fluid_pairs<D, L, CP, FORM>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, screen, list, stride, ts,
                                 [&](int j) { return f.L4[j]; },
                                 [&](int, const float4 &Pj, const float4 &Lj, const float *, float, float ox, float oy,
                                     float oz) {
@@ -249,7 +249,7 @@ __device__ __forceinline__ void reinit_one(const Batch &bt, const Fluid &f, cons
     f.V4[i].w = drho;
 }
 
-template <int D, int L, bool CP, bool TILE, bool ROWS>
+template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
@@ -258,12 +258,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w
     const int stride = blockDim.x;
     if constexpr (!TILE) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        reinit_one<D, L, CP, ROWS>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+        reinit_one<D, L, CP, FORM>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
     } else {
         if (!bt.ctl[f.tiles[blockIdx.x].x].reinit) return;   // not a reinitialisation step of this instance
         tile_loop<D, L>(bt, f, f.L4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
                         [&](int i, bool act, const TileSrc *ts) {
-                            reinit_one<D, L, CP, ROWS>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                            reinit_one<D, L, CP, FORM>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
                         });
     }
 }

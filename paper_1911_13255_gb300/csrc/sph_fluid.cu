@@ -14,7 +14,7 @@ namespace sph {
 // ---------------------------------------------------------------------------
 // a4: equation of state + momentum + kick
 // ---------------------------------------------------------------------------
-template <int D, int L, bool CP, bool ROWS>
+template <int D, int L, bool CP, int FORM>
 __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int i,
                                                  bool act_, int lane, uint32_t *list, int stride, const TileSrc *ts)
 {
@@ -60,7 +60,7 @@ __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, co
             afs[2] += o[2];
         };
         // fluid neighbours: Riemann pressure + viscous (Eq. fluid-model-mr-mom, reading R4)
-        nff = fluid_pairs<D, L, CP, ROWS>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
+        nff = fluid_pairs<D, L, CP, FORM>(f, w, s, g, In.c0, cx, cy, cz, i, lane, Pi, P.rc2F, list, stride, ts,
                                       [&](int j) { return f.V4[j]; },
                                       [&](int, const float4 &Pj, const float4 &Vj, const float *d, float r2, float,
                                           float, float) {
@@ -103,7 +103,7 @@ __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, co
     flush_counts<D>(bt, b, act, cnt, true);
 }
 
-template <int D, int L, bool CP, bool TILE, bool ROWS>
+template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
@@ -112,11 +112,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls
     const int stride = blockDim.x;
     if constexpr (!TILE) {
         const int t = blockIdx.x * blockDim.x + threadIdx.x;
-        momentum_one<D, L, CP, ROWS>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
+        momentum_one<D, L, CP, FORM>(bt, f, w, s, t / L, t / L < f.n, t % L, list, stride, nullptr);
     } else {
         tile_loop<D, L>(bt, f, f.V4, s_dyn + (CP ? (size_t)kListBytes * blockDim.x : 0),
                         [&](int i, bool act, const TileSrc *ts) {
-                            momentum_one<D, L, CP, ROWS>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
+                            momentum_one<D, L, CP, FORM>(bt, f, w, s, i, act, (int)threadIdx.x % L, list, stride, ts);
                         });
     }
 }
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_solid_fluid_force(Batch bt, Fl
             fa[1] -= Vf * o[1];
             fa[2] -= Vf * o[2];
         };
-        if (g.reach == 1) {
+        if (f.reach == 1) {
             // a row of neighbour cells at a time (their starts loaded together)
             for_each_row<D>(g, In.c0, cx, cy, cz, [&](const int c[3], float oy, float oz, int) {
                 const Row3 r = row_of(f.cstart, c);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kMaxBlock, 2) k_solid_fluid_force(Batch bt, Fl
                 }
             });
         } else {
-            for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+            for_each_cell<D, 2>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
                 const int j1 = f.cstart[c + 1];
                 for (int j = f.cstart[c] + lane; j < j1; j += L) pair(j, ox, oy, oz);
             });
@@ -262,7 +262,7 @@ __global__ void k_debug_pairs(Batch bt, Fluid f, Walls w, Solid s, int inst, int
     cell_xyz(key, In, cx, cy, cz);
     int cnt = 0;
     int base = out ? offs[row] : 0;
-    for_each_cell<D>(g, In.c0, cx, cy, cz, [&](int c, float, float, float, int) {
+    auto visit = [&](int c, float, float, float, int) {
         int j0, j1;
         if (which == 0 || which == 3) {
             j0 = f.cstart[c];
@@ -306,7 +306,9 @@ __global__ void k_debug_pairs(Batch bt, Fluid f, Walls w, Solid s, int inst, int
                 cnt++;
             }
         }
-    });
+    };
+    if (f.reach == 2) for_each_cell<D, 2>(g, In.c0, cx, cy, cz, visit);
+    else for_each_cell<D, 1>(g, In.c0, cx, cy, cz, visit);
     if (!out) counts[row] = cnt;
 }
 

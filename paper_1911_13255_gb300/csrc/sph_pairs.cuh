@@ -36,14 +36,17 @@ static bool with_lanes(int L, Fn &&fn)
     return true;
 }
 
-// Visit the (2R + 1)^d neighbour cells of (cx, cy, cz), R = g.reach.
-// fn(cell, ox, oy, oz, code) receives the offset o = -(dcell) * edge to add
-// to (rel_i - rel_j) and code = (dx + R) + W (dy + R) + W^2 (dz + R), W =
-// 2R + 1 (cell_offset recovers o from it; code < 125).
-template <int D, typename Fn>
+// Visit the (2R + 1)^d neighbour cells of (cx, cy, cz).  fn(cell, ox, oy,
+// oz, code) receives the offset o = -(dcell) * edge to add to (rel_i -
+// rel_j) and code = (dx + R) + W (dy + R) + W^2 (dz + R), W = 2R + 1
+// (cell_offset<R> recovers o from it; code < 125).  R is a compile-time
+// constant (the kernels are instantiated per reach): a runtime reach costs
+// registers, hence occupancy, in every pair loop.  Visiting R = 2 over
+// cells of edge >= 2 h_F is correct, only slower.
+template <int D, int R, typename Fn>
 __device__ __forceinline__ void for_each_cell(const Grid &g, int c0, int cx, int cy, int cz, Fn &&fn)
 {
-    const int R = g.reach, W = 2 * R + 1;
+    constexpr int W = 2 * R + 1;
     const int z0 = D == 3 ? -R : 0, z1 = D == 3 ? R : 0;
 #pragma unroll 1
     for (int dz = z0; dz <= z1; dz++) {
@@ -138,9 +141,10 @@ __device__ __forceinline__ int row_slot(const Row3 &r, int q, int &k)
 // x offset -dx * edge of cell k of a row (the same value as for_each_cell's)
 __device__ __forceinline__ float row_ox(int k, const Grid &g) { return (float)(1 - k) * g.csf[0]; }
 
+template <int R>
 __device__ __forceinline__ void cell_offset(int code, const Grid &g, float &ox, float &oy, float &oz)
 {
-    const int R = g.reach, W = 2 * R + 1;
+    constexpr int W = 2 * R + 1;
     const int dx = code % W - R, dy = (code / W) % W - R, dz = code / (W * W) - R;
     ox = -(float)dx * g.csf[0];
     oy = -(float)dy * g.csf[1];
@@ -326,14 +330,14 @@ constexpr int kCodeBits = 7;
 constexpr uint32_t kCodeMask = (1u << kCodeBits) - 1u;
 constexpr int kMaxPairTargets = 1 << (32 - kCodeBits);
 
-template <int D, int L, bool CP, typename Fetch, typename Pair>
+template <int D, int L, bool CP, int R, typename Fetch, typename Pair>
 __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Grid &g, int c0, int cx, int cy, int cz,
                                                        int i, int lane, const float4 &Pi, float rc2, uint32_t *list,
                                                        int stride, Fetch &&fetch, Pair &&pair)
 {
     unsigned cnt_total = 0;
     if constexpr (!CP) {
-        for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+        for_each_cell<D, R>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 if (j == i) continue;
@@ -354,7 +358,7 @@ __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Gri
                 const uint32_t e = list[k * stride];
                 const int j = (int)(e >> kCodeBits);
                 float ox, oy, oz;
-                cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
+                cell_offset<R>((int)(e & kCodeMask), g, ox, oy, oz);
                 const float4 Pj = f.P4[j];
                 float d[3];
                 const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -362,7 +366,7 @@ __device__ __forceinline__ unsigned fluid_pairs_global(const Fluid &f, const Gri
             }
             cnt = 0;
         };
-        for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+        for_each_cell<D, R>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
             const int j1 = f.cstart[c + 1];
             for (int j = f.cstart[c] + lane; j < j1; j += L) {
                 if (j == i) continue;
@@ -394,7 +398,7 @@ __device__ __forceinline__ unsigned fluid_pairs_tile(const Fluid &f, const Grid 
             const uint32_t e = list[k * stride];
             const int q = (int)(e >> kCodeBits);
             float ox, oy, oz;
-            cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
+            cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
             const float4 Pj = ts.sP[q];
             float d[3];
             const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -402,7 +406,7 @@ __device__ __forceinline__ unsigned fluid_pairs_tile(const Fluid &f, const Grid 
         }
         cnt = 0;
     };
-    for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+    for_each_cell<D, 1>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
         const TilePiece *pp = ts.pieces + 2 * ((code / 3) % 3 + 3 * (code / 9));
         const int base = (c >= pp[0].c_lo && c <= pp[0].c_hi) ? pp[0].base : pp[1].base;
         const int j1 = f.cstart[c + 1];
@@ -477,7 +481,7 @@ __device__ __forceinline__ unsigned fluid_pairs_rows(const Fluid &f, const Walls
             const uint32_t e = list[k * stride];
             const int j = (int)(e >> kCodeBits);
             float ox, oy, oz;
-            cell_offset((int)(e & kCodeMask), g, ox, oy, oz);
+            cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
             const float4 Pj = f.P4[j];
             float d[3];
             const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -528,24 +532,26 @@ __device__ __forceinline__ unsigned fluid_pairs_rows(const Fluid &f, const Walls
 }
 
 // All neighbours of target i: fluid-fluid pairs through pair (their number
-// is returned), wall and solid candidates through wp and sp.  ROWS selects
-// the row form (global records only); otherwise the cell form visits the
-// fluid cells (from the staged tile when ts is set), then the wall and solid
-// entries cell by cell.
-template <int D, int L, bool CP, bool ROWS, typename Fetch, typename Pair, typename WP, typename SP>
+// is returned), wall and solid candidates through wp and sp.  FORM 1 is the
+// row form (global records only); otherwise the cell form visits the fluid
+// cells (from the staged tile when ts is set), then the wall and solid
+// entries cell by cell, over the 3^d cells (FORM 0) or the 5^d cells of
+// edge >= h_F (FORM 2).
+template <int D, int L, bool CP, int FORM, typename Fetch, typename Pair, typename WP, typename SP>
 __device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, int c0,
                                                 int cx, int cy, int cz, int i, int lane, const float4 &Pi, float rc2,
                                                 uint32_t *list, int stride, const TileSrc *ts, Fetch &&fetch,
                                                 Pair &&pair, WP &&wp, SP &&sp)
 {
-    if constexpr (ROWS) {
+    if constexpr (FORM == 1) {
         return fluid_pairs_rows<D, L, CP>(f, w, s, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, fetch, pair, wp,
                                           sp);
     } else {
+        constexpr int R = FORM == 2 ? 2 : 1;
         const unsigned n =
             ts ? fluid_pairs_tile<D, L, CP>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, *ts, pair)
-               : fluid_pairs_global<D, L, CP>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, fetch, pair);
-        for_each_cell<D>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+               : fluid_pairs_global<D, L, CP, R>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, fetch, pair);
+        for_each_cell<D, R>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
             ws_cell<L>(w, s, c, ox, oy, oz, lane, wp, sp);
         });
         return n;
@@ -731,12 +737,14 @@ static void allow_smem(K kern, size_t bytes)
                 allow_smem(kern, sm_);                                                        \
                 launch_k(kern, nb_, f.block, sm_, st, __VA_ARGS__);                           \
             };                                                                                \
-            if (f.compact && f.tile) run_(KERN<D_, L_, true, true, false>);                   \
-            else if (f.compact && f.rows) run_(KERN<D_, L_, true, false, true>);              \
-            else if (f.compact) run_(KERN<D_, L_, true, false, false>);                       \
-            else if (f.tile) run_(KERN<D_, L_, false, true, false>);                          \
-            else if (f.rows) run_(KERN<D_, L_, false, false, true>);                          \
-            else run_(KERN<D_, L_, false, false, false>);                                     \
+            if (f.compact && f.tile) run_(KERN<D_, L_, true, true, 0>);                       \
+            else if (f.compact && f.rows) run_(KERN<D_, L_, true, false, 1>);                 \
+            else if (f.compact && f.reach == 2) run_(KERN<D_, L_, true, false, 2>);           \
+            else if (f.compact) run_(KERN<D_, L_, true, false, 0>);                           \
+            else if (f.tile) run_(KERN<D_, L_, false, true, 0>);                              \
+            else if (f.rows) run_(KERN<D_, L_, false, false, 1>);                             \
+            else if (f.reach == 2) run_(KERN<D_, L_, false, false, 2>);                       \
+            else run_(KERN<D_, L_, false, false, 0>);                                         \
         };                                                                                    \
         const bool ok_ = dim == 2 ? with_lanes<2>(f.lanes, [&](auto Lc) {                     \
             go_(std::integral_constant<int, 2>{}, Lc);                                        \
