@@ -126,6 +126,9 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
             L.or_substeps.restype = C.c_int
             L.or_substeps.argtypes = [C.c_double, C.c_double]
+            L.or_single_dt.restype = C.c_double
+            L.or_single_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid), C.c_int,
+                                       C.c_double, C.c_double, C.c_double]
             L.or_eos_rho_array.restype = None
             L.or_eos_rho_array.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_double]
             _lib = L
@@ -289,6 +292,18 @@ class OracleSim:
 
     def substeps(self, dt_f, dt_s):
         return lib().or_substeps(dt_f, dt_s)
+
+    def single_dt(self, mode=1, vmax_f=None, vmax_s=None, amax_s=None):
+        """Step of the single-time-step baselines (K = 1): mode 1 the
+        criterion of Section 2.2, mode 2 min(dt_ac^F, dt^S) (Section 3.2)."""
+        if vmax_f is None:
+            vmax_f = float(np.sqrt((self.f_v ** 2).sum(1)).max()) if self.case.nf else 0.0
+        if vmax_s is None:
+            vmax_s = float(np.sqrt((self.s_v ** 2).sum(1)).max()) if self.case.ns else 0.0
+        if amax_s is None:
+            amax_s = 0.0
+        return lib().or_single_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), int(mode), vmax_f, vmax_s,
+                                  amax_s)
 
     def step(self, dt, K):
         rc = lib().or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),

@@ -892,3 +892,34 @@ int or_substeps(double dt_f, double dt_s)
 {
     return (int)floor(dt_f / dt_s) + 1;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Single time step for fluid and solid together (the baseline the paper     */
+/* compares its multiple time steps with, Tables 1 and 2, K = 1).            */
+/* mode 1: the single-step criterion of Section 2.2,                         */
+/*   dt = min(0.25 min(h_F/(c_F + |v|max), h_F^2/nu),                        */
+/*            0.6 min(h_S/(c_S + |v|max), sqrt(h_S/|dv/dt|max)))             */
+/* with |v|max over fluid and solid particles, |dv/dt|max over the solid,    */
+/* each phase's own smoothing length and nu = eta/rho0 (the printed h^2/eta  */
+/* read as h^2/nu, as in Eq. dtf-advection).                                 */
+/* mode 2: the solid step as the step of both (Section 3.2, the alternative  */
+/* to kappa sub-steps): dt = min(dt_ac^F, dt^S).                             */
+/* ------------------------------------------------------------------------ */
+double or_single_dt(const or_params *P, const or_fluid *f, const or_solid *s, int mode, double vmax_f,
+                    double vmax_s, double amax_s)
+{
+    (void)P;
+    double hF = 1.3 * f->dp, hS = 1.3 * s->dp;
+    double cS = s->n > 0 ? or_solid_sound_speed(s->E, s->nu, s->rho0) : 0.0;
+    double solid_acc = amax_s > 0.0 ? sqrt(hS / amax_s) : 1e300;
+    if (mode == 2) {
+        double dt_ac = 0.6 * hF / (f->c0 + vmax_f);
+        double dt_s = s->n > 0 ? 0.6 * fmin(hS / (cS + vmax_s), solid_acc) : 1e300;
+        return fmin(dt_ac, dt_s);
+    }
+    double vmax = fmax(vmax_f, vmax_s);
+    double nu = f->eta / f->rho0;
+    double fluid = fmin(hF / (f->c0 + vmax), nu > 0.0 ? hF * hF / nu : 1e300);
+    double solid = s->n > 0 ? fmin(hS / (cS + vmax), solid_acc) : 1e300;
+    return fmin(0.25 * fluid, 0.6 * solid);
+}

@@ -70,5 +70,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
 void or_suggest_dt(const or_params *P, const or_fluid *f, const or_solid *s, double vmax_f, double vmax_s,
                    double amax_s, double *dt_ac, double *dt_ad, double *dt_s);
 int or_substeps(double dt_f, double dt_s);
+double or_single_dt(const or_params *P, const or_fluid *f, const or_solid *s, int mode, double vmax_f,
+                    double vmax_s, double amax_s);
 void or_eos_rho_array(int64_t n, const double *p, double *rho, double rho0, double c0);
 #endif

@@ -423,3 +423,69 @@ def test_inflow_profile_mean_and_ramp():
     P.inflow_tramp = 2.0
     assert abs(O.lib().or_inflow_u(P, H / 2, 1.0) - 0.75) < 1e-12   # half-way up the ramp
     assert O.lib().or_inflow_u(P, H / 2, 0.0) == 0.0
+
+
+# --------------------------------------------------------------------------
+# Single-time-step baselines (Section 2.2 criterion; Section 3.2 alternative)
+# --------------------------------------------------------------------------
+
+def _dt_case(dpF=0.01, c0=10.0, eta=0.0, rho0=1.0, E=1e-6, rhoS=10.0):
+    import dataclasses
+    c = fc.tiny_box(seed=0, nx=8, ny=6, dpF=dpF, ratio=2, c0=c0, eta=eta, rho0=rho0)
+    return O.OracleSim(dataclasses.replace(c, s_E=E, s_rho0=rhoS))
+
+
+def test_single_dt_regimes_scale_as_their_physics():
+    """Each term of the single-step criterion, isolated by the parameters,
+    scales as its physics: the acoustic terms linearly with the particle
+    spacing and inversely with the signal speed, the viscous term with the
+    spacing squared over the kinematic viscosity, the acceleration term with
+    the square root of spacing over acceleration."""
+    def dt(mode=1, vf=0.0, vs=0.0, a=0.0, **kw):
+        return _dt_case(**kw).single_dt(mode, vf, vs, a)
+
+    # fluid acoustic (soft solid, no viscosity): 0.25 h_F / c_F at rest
+    base = dt()
+    assert base == pytest.approx(0.25 * 1.3 * 0.01 / 10.0, rel=1e-14)
+    assert dt(dpF=0.02) == pytest.approx(2.0 * base, rel=1e-14)
+    assert dt(c0=20.0) == pytest.approx(0.5 * base, rel=1e-14)
+    # the largest speed of either phase adds to the sound speed
+    assert dt(vf=10.0) == pytest.approx(0.5 * base, rel=1e-14)
+    assert dt(vs=10.0) == pytest.approx(0.5 * base, rel=1e-14)
+    # viscous: h_F^2 / nu, nu = eta / rho0
+    v1 = dt(eta=1.0)
+    assert v1 < base
+    assert dt(eta=1.0, dpF=0.02) == pytest.approx(4.0 * v1, rel=1e-14)
+    assert dt(eta=2.0) == pytest.approx(0.5 * v1, rel=1e-14)
+    assert dt(eta=1.0, rho0=2.0) == pytest.approx(2.0 * v1, rel=1e-14)
+    # solid acoustic (slow fluid, stiff solid): 0.6 h_S / c_S, c_S ~ sqrt(E / rho_S)
+    s1 = dt(c0=1e-3, E=1e4)
+    assert dt(c0=1e-3, E=4e4) == pytest.approx(0.5 * s1, rel=1e-12)
+    assert dt(c0=1e-3, E=1e4, rhoS=40.0) == pytest.approx(2.0 * s1, rel=1e-12)
+    assert dt(c0=1e-3, E=1e4, dpF=0.02) == pytest.approx(2.0 * s1, rel=1e-12)
+    # solid acceleration: 0.6 sqrt(h_S / |dv/dt|)
+    a1 = dt(c0=1e-3, E=1e-6, a=1e6)
+    assert a1 == pytest.approx(0.6 * math.sqrt(1.3 * 0.005 / 1e6), rel=1e-14)
+    assert dt(c0=1e-3, E=1e-6, a=4e6) == pytest.approx(0.5 * a1, rel=1e-14)
+    assert dt(c0=1e-3, E=1e-6, a=1e6, dpF=0.04) == pytest.approx(2.0 * a1, rel=1e-14)
+
+
+def test_single_dt_modes_bound_and_reduce():
+    """The Section 2.2 step never exceeds the solid step used as a single
+    step (mode 2), which is the smaller of the acoustic fluid step and the
+    solid step; a fluid without a body has no solid terms."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        s = _dt_case(c0=float(rng.uniform(1, 50)), eta=float(rng.choice([0.0, 1e-3, 1.0])),
+                     E=float(10 ** rng.uniform(-2, 6)))
+        vf, vs, a = (float(rng.uniform(0, 5)), float(rng.uniform(0, 5)), float(10 ** rng.uniform(-3, 6)))
+        m1, m2 = s.single_dt(1, vf, vs, a), s.single_dt(2, vf, vs, a)
+        ac, _, dS = s.suggest_dt(vf, vs, a)
+        assert m2 == min(ac, dS)
+        assert m1 <= m2
+        # with K = 1 the sub-step rule gives one sub-step for this step
+        assert s.substeps(m2, dS) == (1 if m2 < dS else 2)
+    c = fc.tiny_box(seed=0, nx=8, ny=6, with_solid=False)
+    s = O.OracleSim(c)
+    assert s.single_dt(1, 0.0, 0.0, 0.0) == pytest.approx(0.25 * 1.3 * c.f_dp / c.f_c0, rel=1e-14)
+    assert s.single_dt(2, 0.0, 0.0, 0.0) == pytest.approx(0.6 * 1.3 * c.f_dp / c.f_c0, rel=1e-14)
