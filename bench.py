@@ -43,7 +43,8 @@ import numpy as np  # noqa: E402
 WORKLOADS = {"dam_gate": "dam_break_elastic_gate_2d",
              "flag_batch": "flag_channel_batch_256_2d",
              "duct_3d": "duct_flexible_plate_3d",
-             "flag_learned": "flag_channel_learned_substepper_2d"}
+             "flag_learned": "flag_channel_learned_substepper_2d",
+             "flag_channel": "flag_channel_2d"}
 METRIC = "pair_interactions_per_s"
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -160,12 +161,16 @@ def _traffic(kernel, workload):
 
 # cell grid of the pair loops per workload (sphfsi_params::cell_reach):
 # 1 = cells of >= 2 h_F, 2 = cells of >= h_F
-CELL_REACH = {"dam_gate": 1, "flag_batch": 1, "duct_3d": 1, "flag_learned": 1}
+CELL_REACH = {"dam_gate": 1, "flag_batch": 1, "duct_3d": 1, "flag_learned": 1, "flag_channel": 1}
 
 
-def make_cases(workload, seed=0, cell_reach=None):
+def make_cases(workload, seed=0, cell_reach=None, ratio=2):
+    """ratio: dp_F / dp_S of the flag channel (Table 1: dp_S = a quarter of
+    the flag's thickness, dp_F = ratio x dp_S; 1 is Case I, 2 Cases III, IV)."""
     import fsi_cases
-    if workload == "flag_batch":
+    if workload == "flag_channel":
+        cases = [fsi_cases.channel_flag(seed=seed, dpF=ratio * 0.1 * 0.2 / 4, ratio=ratio)]
+    elif workload == "flag_batch":
         cases = fsi_cases.flag_batch(seed=seed, n=256)
     elif workload == "duct_3d":
         cases = [fsi_cases.duct_plate_3d(seed=seed, scale=1)]
@@ -197,7 +202,7 @@ def cpu_case(cases, label):
     return cases[b], ""
 
 
-def cpu_baseline(cases, label, budget_s=15.0, max_steps=400):
+def cpu_baseline(cases, label, budget_s=15.0, max_steps=400, time_stepping="multiple"):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
     case, which = cpu_case(cases, label)
@@ -206,6 +211,8 @@ def cpu_baseline(cases, label, budget_s=15.0, max_steps=400):
     ref = oracle.OracleSim(case)
     dt, _, dts = ref.suggest_dt(vmax_f=0.0)
     K = ref.substeps(dt, dts)
+    if time_stepping != "multiple":
+        dt, K = ref.single_dt({"single": 1, "single_solid": 2}[time_stepping], vmax_f=0.0), 1
     pairs, steps = 0, 0
     t0 = time.perf_counter()
     while steps < max_steps and time.perf_counter() - t0 < budget_s:
@@ -225,15 +232,16 @@ def run_reference(args, rank):
     if rank != 0:
         return
     label = WORKLOADS[args.workload]
-    cases = make_cases(args.workload, 0)
+    cases = make_cases(args.workload, 0, ratio=args.resolution_ratio)
     case, _ = cpu_case(cases, label)
     budget = min(240.0, 0.06 * (args.steps + args.warmup) + 10.0)
-    cb = cpu_baseline(cases, label, budget_s=budget, max_steps=max(1, args.steps))
+    cb = cpu_baseline(cases, label, budget_s=budget, max_steps=max(1, args.steps), time_stepping=args.time_stepping)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": cb["steps"], "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / max(cb["steps"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns,
-                                            "n_wall": case.nw, "instances_sampled": 1},
+                                            "n_wall": case.nw, "instances_sampled": 1,
+                                            "time_stepping": args.time_stepping},
             "sim_s_per_wall_s": cb["sim_s_per_wall_s"],
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -263,10 +271,11 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     label = WORKLOADS[args.workload]
-    cases = make_cases(args.workload, seed=rank, cell_reach=args.cell_reach)
+    cases = make_cases(args.workload, seed=rank, cell_reach=args.cell_reach, ratio=args.resolution_ratio)
     case = cases[0]
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
+    sim.set_time_stepping(args.time_stepping)
     if args.tuning:
         vals = [int(x) for x in args.tuning.split(",")]
         sim.set_tuning(*vals)
@@ -321,7 +330,7 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
 
     # ---- e2e through the public API with pinned host buffers
-    e2e = e2e_run(cases, dev, steps=min(args.steps, 400), tuning=tuning)
+    e2e = e2e_run(cases, dev, steps=min(args.steps, 400), tuning=tuning, time_stepping=args.time_stepping)
     if rank != 0:
         return
     # ---- roofline of the dominant stage (device-timed live above)
@@ -370,7 +379,7 @@ def run_gpu(args, rank, world, local_rank):
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,
             "peak_source": ("FP32 FMA: 152 SMs x 128 lanes x 2 x %.0f MHz" % sm_mhz) if bound == "alu"
             else f"{src} hbm_gbs"}
-    cb = cpu_baseline(cases, label) if world == 1 else None
+    cb = cpu_baseline(cases, label, time_stepping=args.time_stepping) if world == 1 else None
     line = {
         "metric": METRIC, "value": pairs_all / (dev_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": nsteps, "warmup": args.warmup, "ms_per_step": dev_ms_max / nsteps,
@@ -383,7 +392,7 @@ def run_gpu(args, rank, world, local_rank):
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
                    "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows")},
-                   "cell_reach": case.cell_reach,
+                   "cell_reach": case.cell_reach, "time_stepping": args.time_stepping,
                    "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -566,7 +575,7 @@ def run_learned(args, rank, world, local_rank):
     print(json.dumps(_clean(line)))
 
 
-def e2e_run(cases, dev, steps, tuning):
+def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
     """The same metric through the public API: the initial state of every
     instance goes up from pinned host memory, every step reads all solid
     positions (the flag / gate observers) back into pinned host memory;
@@ -608,6 +617,7 @@ def e2e_run(cases, dev, steps, tuning):
     sim.finalize()
     sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"],
                    tuning["records"], tuning["rows"])
+    sim.set_time_stepping(time_stepping)
     p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)
@@ -631,6 +641,11 @@ def main():
     ap.add_argument("--workload", default="dam_gate", choices=sorted(WORKLOADS))
     ap.add_argument("--cell-reach", type=int, default=None, choices=[1, 2],
                     help="cell grid of the pair loops: 1 cells of >= 2 h_F, 2 cells of >= h_F (default per workload)")
+    ap.add_argument("--time-stepping", default="multiple", choices=["multiple", "single", "single_solid"],
+                    help="multiple: kappa solid sub-steps per fluid step; single: one step for both from the "
+                         "single-step criterion (K = 1); single_solid: min(dt_ac, dt_S) for both (K = 1)")
+    ap.add_argument("--resolution-ratio", type=int, default=2, choices=[1, 2],
+                    help="dp_F / dp_S of the flag_channel workload (1: Case I, 2: Cases III and IV of Table 1)")
     ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact[,tile[,records[,rows]]]]: fixed launch shape instead "
                                                  "of the autotuner (profiling runs)")
     args = ap.parse_args()

@@ -173,6 +173,20 @@ int sphfsi_finalize(sphfsi_ctx *c);
  * (Section 3.2).  SPHFSI_E_INVAL for K < 0. */
 int sphfsi_set_substeps(sphfsi_ctx *c, int32_t K);
 
+/* Time stepping of fluid and solid (the paper's comparison of multiple and
+ * single time steps, Tables 1 and 2).  mode 0: multiple time steps, the
+ * setting of sphfsi_set_substeps (the default, kappa sub-steps).  mode 1:
+ * one time step for both, K = 1, dt = min(0.25 min(h_F / (c_F + |v|max),
+ * h_F^2 / nu), 0.6 min(h_S / (c_S + |v|max), sqrt(h_S / |dv/dt|max))), the
+ * single-step criterion of Section 2.2 with |v|max over fluid and solid,
+ * |dv/dt|max over the solid, nu = eta / rho0 and each phase's own h, from the
+ * previous step's maxima.  mode 2: K = 1, dt = min(dt_ac^F, dt^S), the solid
+ * step taken as the step of both (Section 3.2).  In modes 1 and 2 a step
+ * called with dt_F <= 0 takes that dt; dt_F > 0 still fixes it.  The last
+ * call of sphfsi_set_substeps or this one decides.  SPHFSI_E_INVAL for any
+ * other mode.  Applies to every instance of a batch. */
+int sphfsi_set_time_stepping(sphfsi_ctx *c, int32_t mode);
+
 /* One coarse step a1..a8.  dt_F > 0 fixes the step; dt_F <= 0 uses the
  * acoustic criterion 0.6 h_F / (c0 + |v|max) (Eq. dt-relax) from the
  * previous step's maximum fluid speed.  Asynchronous on the context stream;

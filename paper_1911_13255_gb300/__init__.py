@@ -83,6 +83,7 @@ _SIGS = {
     "sphfsi_set_inflow": (C.c_int, [_vp, C.POINTER(Inflow)]),
     "sphfsi_finalize": (C.c_int, [_vp]),
     "sphfsi_set_substeps": (C.c_int, [_vp, C.c_int32]),
+    "sphfsi_set_time_stepping": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_step": (C.c_int, [_vp, C.c_double]),
     "sphfsi_run": (C.c_int, [_vp, C.c_int64, C.c_double]),
     "sphfsi_sync": (C.c_int, [_vp]),
@@ -337,6 +338,14 @@ class Simulation:
     # --- stepping ---------------------------------------------------------
     def set_substeps(self, K):
         _check(lib().sphfsi_set_substeps(self.h, int(K)), "sphfsi_set_substeps")
+
+    TIME_STEPPING = {"multiple": 0, "single": 1, "single_solid": 2}
+
+    def set_time_stepping(self, mode):
+        """"multiple" (kappa sub-steps), "single" (Section 2.2 criterion,
+        K = 1) or "single_solid" (min(dt_ac, dt_S), K = 1)."""
+        m = self.TIME_STEPPING[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().sphfsi_set_time_stepping(self.h, m), "sphfsi_set_time_stepping")
 
     def step(self, dt=0.0):
         _check(lib().sphfsi_step(self.h, float(dt)), "sphfsi_step")

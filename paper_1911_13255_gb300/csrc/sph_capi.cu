@@ -966,6 +966,13 @@ int sphfsi_set_substeps(sphfsi_ctx *c, int32_t K)
     return SPHFSI_OK;
 }
 
+int sphfsi_set_time_stepping(sphfsi_ctx *c, int32_t mode)
+{
+    if (!c || mode < 0 || mode > 2) return SPHFSI_E_INVAL;
+    c->K_fixed = -mode;   // 0 keeps the kappa sub-steps
+    return SPHFSI_OK;
+}
+
 int sphfsi_step(sphfsi_ctx *c, double dt_F)
 {
     TRY(check_ctx(c, true));

@@ -83,7 +83,7 @@ struct Ctl {
     double dt_fixed;   // > 0: fixed dt_F
     long long step;    // index of the current step
     int K;             // solid sub-steps of the current step
-    int K_fixed;       // > 0: fixed K
+    int K_fixed;       // > 0: fixed K; 0: kappa sub-steps; -1, -2: single time step (K = 1)
     int reinit;        // this step reinitialises density and normals
     int n_reinit;
     int status;        // ST_* bits, sticky until read by the host

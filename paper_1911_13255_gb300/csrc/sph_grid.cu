@@ -18,9 +18,37 @@ namespace sph {
 // previous step (which the finish kernel moves to prev_*), so that every
 // thread can evaluate it and the leader thread of the instance stores it.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double step_dt(const Phys &P, const Ctl *ctl, double dt_fixed)
+// Solid step (Eq. dts-advection) from the solid's maxima
+__device__ __forceinline__ double solid_dt(const Phys &P, double vS, double aS)
 {
-    return dt_fixed > 0.0 ? dt_fixed : 0.6 * P.hF_d / (P.c0_d + (double)ctl->prev_vmaxF);   // Eq. dt-relax
+    const double b1 = P.hS_d / (P.cS_d + vS);
+    const double b2 = aS > 0.0 ? sqrt(P.hS_d / aS) : 1e300;
+    return 0.6 * (b1 < b2 ? b1 : b2);
+}
+
+// dt_F of the step.  K_fixed < 0 selects a single time step for fluid and
+// solid (K = 1), the baselines the paper compares multiple time steps with:
+// -1 the single-step criterion of Section 2.2 (|v|max over both phases,
+// |dv/dt|max over the solid, h^2/nu with nu = eta/rho0, each phase's own h),
+// -2 the smaller of the acoustic fluid step and the solid step (Section 3.2).
+__device__ __forceinline__ double step_dt(const Inst &In, const Ctl *ctl, double dt_fixed, int K_fixed)
+{
+    const Phys &P = In.P;
+    if (dt_fixed > 0.0) return dt_fixed;
+    const double vF = ctl->prev_vmaxF;
+    const double ac = 0.6 * P.hF_d / (P.c0_d + vF);   // Eq. dt-relax
+    if (K_fixed >= 0) return ac;
+    const double vS = ctl->prev_vmaxS, aS = ctl->prev_amaxS;
+    if (K_fixed == -2) {
+        const double ds = In.ns > 0 ? solid_dt(P, vS, aS) : 1e300;
+        return ac < ds ? ac : ds;
+    }
+    const double v = vF > vS ? vF : vS;
+    const double nu = P.eta_d / P.rho0_d;
+    double fl = P.hF_d / (P.c0_d + v);
+    if (nu > 0.0 && P.hF_d * P.hF_d / nu < fl) fl = P.hF_d * P.hF_d / nu;
+    const double so = In.ns > 0 ? solid_dt(P, v, aS) : 1e300;
+    return 0.25 * fl < so ? 0.25 * fl : so;
 }
 
 __device__ __forceinline__ bool step_reinit(const Ctl *ctl)
@@ -31,15 +59,12 @@ __device__ __forceinline__ bool step_reinit(const Ctl *ctl)
 __device__ void step_control(const Inst &In, Ctl *ctl, double dt_fixed, int K_fixed)
 {
     const Phys &P = In.P;
-    const double dt = step_dt(P, ctl, dt_fixed);
+    const double dt = step_dt(In, ctl, dt_fixed, K_fixed);
     int K = 1;
     if (K_fixed > 0) {
         K = K_fixed;
-    } else if (In.ns > 0) {
-        const float vS = ctl->prev_vmaxS, aS = ctl->prev_amaxS;
-        double b1 = P.hS_d / (P.cS_d + (double)vS);
-        double b2 = aS > 0.0f ? sqrt(P.hS_d / (double)aS) : 1e300;
-        double dts = 0.6 * (b1 < b2 ? b1 : b2);   // Eq. dts-advection
+    } else if (K_fixed == 0 && In.ns > 0) {
+        const double dts = solid_dt(P, ctl->prev_vmaxS, ctl->prev_amaxS);
         double k = floor(dt / dts) + 1.0;          // kappa = [dt_F / dt_S] + 1
         K = k > 1e6 ? 1000000 : (int)k;
     }
@@ -174,7 +199,7 @@ __device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const S
             const Phys &P = In.P;
             const Grid &g = In.g;
             const Ctl *ctl = bt.ctl + b;
-            const double dt = step_dt(P, ctl, dt_fixed), tm = ctl->t;
+            const double dt = step_dt(In, ctl, dt_fixed, K_fixed), tm = ctl->t;
             float vx = S.vx[i], vy = S.vy[i], vz = D == 3 ? S.vz[i] : 0.0f;
             if (P.inflow_on && x >= g.x_lo && x < g.x_lo + P.in_w) {   // inflow buffer (reading R18)
                 vx = (float)inflow_u(P, y, tm);

@@ -761,7 +761,7 @@ constexpr int kChunk2 = 12;   // neighbour loads in flight per phase step
 // shuffle, and both carry the particle's own state identically; the first
 // writes it out.  Two threads per particle give each SM sub-partition two
 // warps to interleave in these latency-bound loops.
-template <int LP, int MODE>
+template <int LP, int MODE, bool EARLY = false>
 __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl *ctl, int s0, int ns, float4 *sQ,
                                              float4 *sV, unsigned rank, uint64_t *mb, int halo_n, unsigned &phs)
 {
@@ -808,8 +808,6 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             H[i] = s.H[9 * a + i];
             B[i] = s.B0[9 * a + i];
         }
-        fF[0] = s.fF[3 * a];
-        fF[1] = s.fF[3 * a + 1];
         x = xs = s.x[a];
         y = ys = s.y[a];
         cons = s.cons[a] != 0;
@@ -886,6 +884,15 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     if (own) {
         sgx = pair_sum(sgx);
         sgy = pair_sum(sgy);
+    }
+    // EARLY: everything above reads data of earlier steps or of the set-up
+    // (and this step's control block, written before the coupling force),
+    // so it may overlap the coupling-force kernel; its output, f^F, only
+    // after that kernel has completed
+    if constexpr (EARLY) pdl_wait();
+    if (own) {
+        fF[0] = s.fF[3 * a];
+        fF[1] = s.fF[3 * a + 1];
     }
     cluster_sync();
 
@@ -1090,14 +1097,16 @@ template <int LP, int MODE>
 __global__ void __launch_bounds__(kC1Threads * 2) k_solid_cluster2d_one(Solid s, const __grid_constant__ Phys P,
                                                                         Ctl *ctl)
 {
-    pdl_enter();
+    // the wait for the coupling-force kernel comes inside the body, after
+    // the prologue (EARLY)
+    pdl_trigger();
     __shared__ float4 sQ[solid2d_slots<MODE>()];
     __shared__ float4 sV[solid2d_slots<MODE>()];
     __shared__ __align__(8) uint64_t mb[4];
     const unsigned rank = cluster_rank();
     unsigned phs = 0u;
     solid2d_mbar_setup<MODE>(mb);
-    solid2d_body<LP, MODE>(s, P, ctl, 0, s.n, sQ, sV, rank, mb, MODE ? s.halo_n[rank] : 0, phs);
+    solid2d_body<LP, MODE, true>(s, P, ctl, 0, s.n, sQ, sV, rank, mb, MODE ? s.halo_n[rank] : 0, phs);
 }
 
 // Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
