@@ -44,7 +44,8 @@ WORKLOADS = {"dam_gate": "dam_break_elastic_gate_2d",
              "flag_batch": "flag_channel_batch_256_2d",
              "duct_3d": "duct_flexible_plate_3d",
              "flag_learned": "flag_channel_learned_substepper_2d",
-             "flag_channel": "flag_channel_2d"}
+             "flag_channel": "flag_channel_2d",
+             "fiv": "flow_induced_vibration_flag_to_t200_2d"}
 METRIC = "pair_interactions_per_s"
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -575,6 +576,128 @@ def run_learned(args, rank, world, local_rank):
     print(json.dumps(_clean(line)))
 
 
+def _tip_oscillation(t, y, t0):
+    """Amplitude (half the mean peak-to-peak height of the full cycles) and
+    frequency (mean period between upward crossings of the mean) of a
+    sampled tip coordinate after time t0."""
+    t, y = np.asarray(t), np.asarray(y)
+    keep = t >= t0
+    t, y = t[keep], y[keep]
+    ym = y.mean()
+    z = y - ym
+    up = np.where((z[:-1] < 0) & (z[1:] >= 0))[0]
+    tc = t[up] + (t[up + 1] - t[up]) * (-z[up]) / (z[up + 1] - z[up])
+    if len(tc) < 3:
+        return None, None, len(tc)
+    amp = [0.5 * (y[a:b + 1].max() - y[a:b + 1].min()) for a, b in zip(up[:-1], up[1:])]
+    return float(np.mean(amp)), float((len(tc) - 1) / (tc[-1] - tc[0])), len(tc) - 1
+
+
+def run_fiv(args, rank, world, local_rank):
+    """Flow-induced vibration of the flag behind the cylinder to t* = 200
+    (Section 4.1, Tables 1 and 2): started with the inflow profile everywhere
+    (a ramp from rest drives the whole periodic column through the inflow
+    buffer and breaks up behind the buffer, in the oracle as on the GPU),
+    the tip's transverse oscillation in the periodic regime (t* >= 100)
+    against the paper's amplitude and frequency, and the wall time to
+    t* = 200 beside the paper's CPU time of the same case."""
+    import torch
+    import fsi_cases
+    from paper_1911_13255_gb300 import Simulation
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    label = WORKLOADS[args.workload]
+    D, U = 0.1, 1.0
+    r = args.resolution_ratio
+    case = fsi_cases.channel_flag(seed=rank, dpF=r * D * 0.2 / 4, ratio=r)
+    case.cell_reach = 1
+    t_end = args.t_star * D / U
+    st = torch.cuda.Stream(device=dev)
+    out = torch.empty((case.ns, 2), dtype=torch.float64).pin_memory()
+    chunk = 20
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    sim = Simulation.from_case(case, stream=st)
+    sim.set_time_stepping(args.time_stepping)
+    ts, ys, xs, dev_ms, steps = [], [], [], 0.0, 0
+    y0, x0 = case.s_r0[case.tip, 1], case.s_r0[case.tip, 0]
+    with ClockSampler(local_rank) as clk:
+        t = 0.0
+        while t < t_end:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sim.run(chunk, 0.0)
+            e1.record(st)
+            sim.get_solid_positions_all(out)   # waits for the chunk
+            dev_ms += e0.elapsed_time(e1)
+            steps += chunk
+            info = sim.info()
+            t = info["t"]
+            tip = out[case.tip].numpy()
+            if not np.all(np.isfinite(tip)) or info["status"] != 0:
+                break
+            ts.append(t)
+            xs.append(tip[0] - x0)
+            ys.append(tip[1] - y0)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    clocks = clk.summary()
+    kps = info["kernels_per_step"]
+    sim.close()
+    # frequency over the second half; amplitude over the last fifth (the
+    # oscillation may still be growing) and per window of 20 D/U
+    _, freq, cycles = _tip_oscillation(ts, ys, 0.5 * t_end)
+    amp, _, _ = _tip_oscillation(ts, ys, 0.8 * t_end)
+    tsa, ysa = np.asarray(ts), np.asarray(ys)
+    windows = {}
+    for w0 in np.arange(0.0, args.t_star, 20.0):
+        m = (tsa >= w0 * D / U) & (tsa < (w0 + 20.0) * D / U)
+        if m.any():
+            windows[f"{w0:.0f}-{w0 + 20:.0f}"] = float((ysa[m].max() - ysa[m].min()) / 2 / D)
+    if rank != 0:
+        return
+    gold = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_numbers.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            gold[k] = float(v)
+    paper_cpu = {(1, "multiple"): 1297.7, (2, "multiple"): 249.5, (2, "single"): 451.4,
+                 (2, "single_solid"): 451.4}.get((r, args.time_stepping))
+    line = {
+        "metric": "simulated_s_per_wall_s", "value": t / max(dev_ms * 1e-3, 1e-30), "unit": "simulated-s/s",
+        "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": dev_ms / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns, "n_wall": case.nw,
+                   "resolution_ratio": r, "time_stepping": args.time_stepping, "t_star_end": args.t_star,
+                   "dp_F": case.f_dp, "dp_S": case.s_dp, "D": D, "U": U, "Re": 100, "E_star": 1.4e3,
+                   "l2": "not flushed (whole working set ~5 MB); every 20 steps the solid positions are read back"},
+        "t_reached": t, "t_star_reached": t * U / D, "finite": bool(t >= t_end),
+        "validation": {"amplitude_y_over_D": None if amp is None else amp / D,
+                       "frequency_fD_over_U": None if freq is None else freq * D / U,
+                       "cycles_used": cycles,
+                       "window": "frequency over t* >= t*_end / 2, amplitude over t* >= 0.8 t*_end",
+                       "half_range_by_window_over_D": windows,
+                       "paper_case3": {"amplitude": gold.get("fiv_case3_amplitude_y"),
+                                       "frequency": gold.get("fiv_case3_frequency")},
+                       "paper_converged": {"amplitude": gold.get("fiv_converged_amplitude_y"),
+                                           "frequency": gold.get("fiv_converged_frequency")}},
+        "wall_s_to_t_star": wall1 - wall0, "device_s_to_t_star": dev_ms * 1e-3,
+        "paper_cpu_s_to_t_star_200": paper_cpu,
+        "tip_mean_dx_over_D": float(np.mean(np.asarray(xs)[np.asarray(ts) >= 10 * D])) / D if ts else None,
+        "e2e": {"value": t / (wall1 - wall0), "unit": "simulated-s/s",
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": out.numel() * 8 / chunk,
+                "note": "context creation and set-up upload, the run and the tip readbacks, host-timed"},
+        "gpu_launches": int(kps) * steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(_clean(line)))
+    if args.trace:
+        np.savetxt(args.trace, np.column_stack([ts, xs, ys]), header="t tip_dx tip_dy")
+
+
 def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
     """The same metric through the public API: the initial state of every
     instance goes up from pinned host memory, every step reads all solid
@@ -646,6 +769,8 @@ def main():
                          "single-step criterion (K = 1); single_solid: min(dt_ac, dt_S) for both (K = 1)")
     ap.add_argument("--resolution-ratio", type=int, default=2, choices=[1, 2],
                     help="dp_F / dp_S of the flag_channel workload (1: Case I, 2: Cases III and IV of Table 1)")
+    ap.add_argument("--t-star", type=float, default=200.0, help="fiv workload: end time in D/U")
+    ap.add_argument("--trace", default="", help="fiv workload: write the tip trajectory to this text file")
     ap.add_argument("--tuning", default="", help="lanes,block,solid_variant[,compact[,tile[,records[,rows]]]]: fixed launch shape instead "
                                                  "of the autotuner (profiling runs)")
     args = ap.parse_args()
@@ -663,6 +788,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "flag_learned":
         run_learned(args, rank, world, local_rank)
+    elif args.workload == "fiv":
+        run_fiv(args, rank, world, local_rank)
     else:
         run_gpu(args, rank, world, local_rank)
     if world > 1:

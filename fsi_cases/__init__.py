@@ -334,7 +334,8 @@ def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0, 
     rho_F = 1, nu = 1e-3 (Re = 100), U_mean = 1, c0 = 10 U_max = 15;
     rho_S = 10, E = 1.4e3, Poisson 0.4; fluid spacing D/10, solid spacing D/20.
     Solid particles inside the cylinder are constrained (rigid).
-    The initial fluid velocity is the inflow profile everywhere.
+    The initial fluid velocity is the inflow profile everywhere; with an
+    inflow ramp (t_ramp > 0, Section 4.1: t_s = 2 D/U) the fluid starts at rest.
 
     L_D x H_D (channel size in D), cy_D (cylinder centre height in D),
     flag_len and flag_thick (in D), rho_S, E and nu override those values for
@@ -375,7 +376,8 @@ def channel_flag(seed=0, D=0.1, dpF=None, ratio=2, jitter_amp=1e-3, t_ramp=0.0, 
     U = 1.0
     fv = np.zeros_like(fr)
     yy = np.clip(fr[:, 1], 0.0, H)
-    fv[:, 0] = 6.0 * U * yy * (H - yy) / (H * H)   # parabolic inflow profile (mean U)
+    if t_ramp <= 0.0:
+        fv[:, 0] = 6.0 * U * yy * (H - yy) / (H * H)   # parabolic inflow profile (mean U)
     # observer: free-end particle on the flag centre line
     tip_c = np.where(cons == 0)[0]
     tip = int(tip_c[np.argmin((sr[tip_c, 0] - fx1) ** 2 + (sr[tip_c, 1] - cy) ** 2)])
