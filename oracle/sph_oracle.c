@@ -548,6 +548,14 @@ static void fs_pair(const or_params *P, int dim, const fluid_consts *fc, const d
 {
     double d[3], e[3], vd[3];
     double r = sqrt(delta(P, dim, ri, ra, d)); /* d = r_i - r_a */
+    if (r == 0.0) {
+        /* coincident pair (reading R23): no direction and grad W = 0, so the
+           pair adds nothing (the regularised viscous term vanishes too) */
+        if (fout)
+            for (int k = 0; k < dim; k++) fout[k] = 0.0;
+        if (drho_out) *drho_out = 0.0;
+        return;
+    }
     double dW = or_kernel_dW(dim, r, fc->hF);
     double gW[3];
     for (int k = 0; k < dim; k++) {
@@ -700,6 +708,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
             int64_t j = FF.idx[q];
             double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            if (r == 0.0) continue; /* coincident pair: no direction, grad W = 0 (reading R23) */
             double dW = or_kernel_dW(dim, r, hF);
             double Vj = mF / f->rho[j];
             for (int k = 0; k < dim; k++) e[k] = -d[k] / r;
@@ -768,6 +777,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
             int64_t j = FF.idx[q];
             double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            if (r == 0.0) continue; /* coincident pair (reading R23) */
             double dW = or_kernel_dW(dim, r, hF);
             double Vj = mF / f->rho[j];
             for (int k = 0; k < dim; k++) e[k] = -d[k] / r;

@@ -489,3 +489,31 @@ def test_single_dt_modes_bound_and_reduce():
     s = O.OracleSim(c)
     assert s.single_dt(1, 0.0, 0.0, 0.0) == pytest.approx(0.25 * 1.3 * c.f_dp / c.f_c0, rel=1e-14)
     assert s.single_dt(2, 0.0, 0.0, 0.0) == pytest.approx(0.6 * 1.3 * c.f_dp / c.f_c0, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Coincident particles (reading R23): the pair rule at r = 0 is the limit r -> 0+
+# --------------------------------------------------------------------------
+
+def _with_coincident(eps):
+    """tiny_box plus a copy of one fluid particle and a fluid particle on a
+    solid particle, each displaced by eps dp (eps = 0: on top)."""
+    c = fc.tiny_box(seed=11)
+    k, m = len(c.f_r) // 3, len(c.s_r0) // 2
+    off = eps * c.f_dp * np.array([0.6, 0.8])
+    c.f_r = np.concatenate([c.f_r, c.f_r[k:k + 1] + off, c.s_r0[m:m + 1] + off])
+    c.f_v = np.concatenate([c.f_v, c.f_v[k:k + 1], c.s_v0[m:m + 1]])
+    c.f_p = np.concatenate([c.f_p, c.f_p[k:k + 1], [0.0]])
+    return c
+
+
+def test_coincident_pairs_are_the_limit_of_close_pairs():
+    out = []
+    for eps in (0.0, 1e-9):
+        s = O.OracleSim(_with_coincident(eps))
+        dt, _, dts = s.suggest_dt()
+        s.step(dt, s.substeps(dt, dts))
+        assert np.all(np.isfinite(s.f_dvdt)) and np.all(np.isfinite(s.f_drho)) and np.all(np.isfinite(s.s_fF))
+        out.append((s.f_dvdt.copy(), s.f_drho.copy(), s.s_fF.copy()))
+    for a, b in zip(*out):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
