@@ -48,6 +48,7 @@ __device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, con
                                 [&](int j) { return f.W4[j]; },
                                 [&](int, const float4 &, const float4 &Wj, const float *d, float r2, float, float,
                                     float) {
+                if (r2 == 0.0f) return;   // a clumped pair: no direction, dW(0) = 0
                 const float rhoj = P.rho0 + Wj.w;
                 float r = sqrtf(r2), invr = 1.0f / r;
                 float dW = dW_F(r, P);

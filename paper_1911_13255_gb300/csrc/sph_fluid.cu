@@ -64,6 +64,9 @@ __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, co
                                       [&](int j) { return f.V4[j]; },
                                       [&](int, const float4 &Pj, const float4 &Vj, const float *d, float r2, float,
                                           float, float) {
+                // two particles at one FP32 position (a clumped pair): the
+                // direction is undefined and the pair's terms vanish with r
+                if (r2 == 0.0f) return;
                 const float rhoj = P.rho0 + Vj.w;
                 float r = sqrtf(r2), invr = 1.0f / r;
                 float dW = dW_F(r, P);

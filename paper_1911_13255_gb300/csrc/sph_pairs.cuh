@@ -611,8 +611,11 @@ __device__ __forceinline__ void fs_pair_force(const float d[3], float r2, const 
                                               const float4 &vb, const float4 &ab, const float4 &n, float Va,
                                               const Phys &P, float out[3])
 {
+    // a particle on top of a boundary particle at FP32 resolution: the
+    // direction is undefined and the pressure term vanishes with r; the
+    // viscous term's limit is dropped with it
     float r = sqrtf(r2);
-    float invr = 1.0f / r;
+    float invr = r2 > 0.0f ? 1.0f / r : 0.0f;
     float dW = dW_F(r, P);
     float gn = (P.g[0] - ab.x) * n.x + (P.g[1] - ab.y) * n.y;
     float dn = d[0] * n.x + d[1] * n.y;
@@ -639,7 +642,7 @@ __device__ __forceinline__ float fs_pair_drho(const float d[3], float r2, const 
                                               const Phys &P)
 {
     float r = sqrtf(r2);
-    float invr = 1.0f / r;
+    float invr = r2 > 0.0f ? 1.0f / r : 0.0f;   // r = 0: no direction, dW(0) = 0
     float dW = dW_F(r, P);
     float gn = (P.g[0] - ab.x) * n.x + (P.g[1] - ab.y) * n.y;
     float dn = d[0] * n.x + d[1] * n.y;

@@ -126,3 +126,20 @@ def test_a_non_finite_state_is_reported():
     with pytest.raises(SphError):
         sim.sync()
     assert sim.info()["status"] != 0
+
+
+def test_coincident_particles():
+    """A fluid particle on top of another and one on top of a solid particle:
+    the pair has no direction and adds nothing on either side (the oracle's
+    rule, the limit of close pairs); the step stays finite and equals the
+    oracle's."""
+    case = fc.tiny_box(seed=11)
+    k, m = len(case.f_r) // 3, len(case.s_r0) // 2
+    case.f_r = np.concatenate([case.f_r, case.f_r[k:k + 1], case.s_r0[m:m + 1]])
+    case.f_v = np.concatenate([case.f_v, case.f_v[k:k + 1], case.s_v0[m:m + 1]])
+    case.f_p = np.concatenate([case.f_p, case.f_p[k:k + 1], [0.0]])
+    sim = _step_parity(case)
+    g = sim.get_fluid()
+    assert np.all(np.isfinite(g["dvdt"])) and np.all(np.isfinite(g["drho"]))
+    assert np.array_equal(g["dvdt"][k], g["dvdt"][-2])   # the twins feel the same
+    sim.close()
