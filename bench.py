@@ -688,7 +688,9 @@ def run_fiv(args, rank, world, local_rank):
         "paper_cpu_s_to_t_star_200": paper_cpu,
         "tip_mean_dx_over_D": float(np.mean(np.asarray(xs)[np.asarray(ts) >= 10 * D])) / D if ts else None,
         "e2e": {"value": t / (wall1 - wall0), "unit": "simulated-s/s",
-                "h2d_bytes_per_step": None, "d2h_bytes_per_step": out.numel() * 8 / chunk,
+                "h2d_bytes_per_step": sum(np.asarray(getattr(case, k)).nbytes for k in
+                                          ("f_r", "f_v", "f_p", "w_r", "w_n", "s_r0", "s_v0", "s_n0", "s_cons")) / max(steps, 1),
+                "d2h_bytes_per_step": out.numel() * 8 / chunk,
                 "note": "context creation and set-up upload, the run and the tip readbacks, host-timed"},
         "gpu_launches": int(kps) * steps,
         "clocks": clocks,
