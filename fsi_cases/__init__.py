@@ -34,7 +34,7 @@ class Case:
     Lx: float = 0.0
     free_surface: int = 0
     n_reinit: int = 0
-    # inflow buffer (profile 0: parabolic in y over [y0, y0+H]; 1: uniform)
+    # inflow buffer (profile 0: parabolic in y over [y0, y0+H]; 1: uniform; 2: Womersley)
     inflow_on: int = 0
     inflow_profile: int = 0
     inflow_width: float = 0.0
@@ -42,6 +42,8 @@ class Case:
     inflow_H: float = 1.0
     inflow_U: float = 0.0
     inflow_tramp: float = 0.0
+    inflow_period: float = 0.0     # profile 2 (Womersley): period T
+    inflow_wo: float = 0.0         # profile 2: Womersley number (H/2) sqrt(omega / nu)
     # bounding box for a fixed cell grid (particles outside are clamped in)
     domain_lo: tuple = (0.0, 0.0, 0.0)
     domain_hi: tuple = (1.0, 1.0, 1.0)

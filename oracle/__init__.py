@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("x_lo", C.c_double), ("Lx", C.c_double), ("free_surface", C.c_int32),
                 ("n_reinit", C.c_int32), ("inflow_on", C.c_int32), ("inflow_profile", C.c_int32),
                 ("inflow_width", C.c_double), ("inflow_y0", C.c_double), ("inflow_H", C.c_double),
-                ("inflow_U", C.c_double), ("inflow_tramp", C.c_double)]
+                ("inflow_U", C.c_double), ("inflow_tramp", C.c_double), ("inflow_period", C.c_double),
+                ("inflow_wo", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -156,6 +157,7 @@ def make_params(case) -> Params:
     P.inflow_on, P.inflow_profile = case.inflow_on, case.inflow_profile
     P.inflow_width, P.inflow_y0, P.inflow_H = case.inflow_width, case.inflow_y0, case.inflow_H
     P.inflow_U, P.inflow_tramp = case.inflow_U, case.inflow_tramp
+    P.inflow_period, P.inflow_wo = getattr(case, "inflow_period", 0.0), getattr(case, "inflow_wo", 0.0)
     return P
 
 

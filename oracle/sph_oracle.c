@@ -598,6 +598,21 @@ double or_inflow_u(const or_params *P, double y, double t)
     double H = P->inflow_H, yy = y - P->inflow_y0;
     if (yy < 0.0) yy = 0.0;
     if (yy > H) yy = H;
+    if (P->inflow_profile == 2) {
+        /* Womersley channel flow under dp/dx = -A cos(omega t) (Appendix A),
+           U = A / rho_F, omega = 2 pi / T, Wo = (H/2) sqrt(omega / nu).  With
+           beta = Wo / sqrt(2), s = 2 (y - H/2) / H, Phi_1,2 = beta (1 +- s) and
+           gamma = cosh(2 beta) + cos(2 beta), reading R24 of the printed form:
+           u = U / (omega gamma) [(sinh Phi_1 sin Phi_2 + sinh Phi_2 sin Phi_1) cos(omega t)
+                                  + (gamma - cosh Phi_1 cos Phi_2 - cosh Phi_2 cos Phi_1) sin(omega t)] */
+        double w = 2.0 * PI / P->inflow_period, beta = P->inflow_wo / sqrt(2.0);
+        double sy = 2.0 * (yy - 0.5 * H) / H;
+        double p1 = beta * (1.0 + sy), p2 = beta * (1.0 - sy);
+        double g = cosh(2.0 * beta) + cos(2.0 * beta);
+        double c = sinh(p1) * sin(p2) + sinh(p2) * sin(p1);
+        double q = g - cosh(p1) * cos(p2) - cosh(p2) * cos(p1);
+        return U / (w * g) * (c * cos(w * t) + q * sin(w * t));
+    }
     return 6.0 * U * yy * (H - yy) / (H * H);
 }
 

@@ -19,6 +19,7 @@ typedef struct {
     int32_t inflow_on;
     int32_t inflow_profile;
     double inflow_width, inflow_y0, inflow_H, inflow_U, inflow_tramp;
+    double inflow_period, inflow_wo; /* profile 2: Womersley period T and number Wo */
 } or_params;
 
 typedef struct {

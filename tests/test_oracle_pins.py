@@ -517,3 +517,48 @@ def test_coincident_pairs_are_the_limit_of_close_pairs():
         out.append((s.f_dvdt.copy(), s.f_drho.copy(), s.s_fF.copy()))
     for a, b in zip(*out):
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------------
+# Womersley inflow (Appendix A, reading R24)
+# --------------------------------------------------------------------------
+
+def _womersley_params(wo, H=5e-3, T=0.6, A_rho=2.5):
+    c = fc.channel_flag()
+    P = O.make_params(c)
+    P.inflow_profile, P.inflow_y0, P.inflow_H, P.inflow_U = 2, 0.0, H, A_rho
+    P.inflow_period, P.inflow_wo, P.inflow_tramp = T, wo, 0.0
+    w = 2 * math.pi / T
+    nu = w * (H / 2) ** 2 / wo ** 2
+    return P, w, nu
+
+
+@pytest.mark.parametrize("wo", [1.0, 5.0, 10.0])
+def test_womersley_profile_solves_the_oscillating_channel_flow(wo):
+    """u(y, t) satisfies u_t = (A/rho) cos(omega t) + nu u_yy (central
+    differences), vanishes on both walls and is periodic in T."""
+    P, w, nu = _womersley_params(wo)
+    H, U, T = P.inflow_H, P.inflow_U, P.inflow_period
+    u = lambda y, t: O.lib().or_inflow_u(P, y, t)
+    scale = U / w
+    for t in (0.0, 0.07, 0.21, 0.44):
+        assert abs(u(0.0, t)) < 1e-12 * scale and abs(u(H, t)) < 1e-12 * scale
+        assert abs(u(0.3 * H, t + T) - u(0.3 * H, t)) < 1e-12 * scale
+        for y in np.linspace(0.1, 0.9, 7) * H:
+            et, ey = 1e-5 * T, 1e-3 * H
+            ut = (u(y, t + et) - u(y, t - et)) / (2 * et)
+            uyy = (u(y + ey, t) - 2 * u(y, t) + u(y - ey, t)) / ey ** 2
+            res = ut - U * math.cos(w * t) - nu * uyy
+            assert abs(res) < 2e-5 * U, (wo, t, y, res)
+
+
+def test_womersley_low_frequency_limit_is_poiseuille():
+    """Wo -> 0: the profile is the steady channel flow of the instantaneous
+    pressure gradient, (A / (2 rho nu)) (y)(H - y) cos(omega t)."""
+    P, w, nu = _womersley_params(0.02)
+    H, U = P.inflow_H, P.inflow_U
+    for t in (0.0, 0.1, 0.25):
+        for y in (0.2 * H, 0.5 * H, 0.7 * H):
+            want = U / (2 * nu) * y * (H - y) * math.cos(w * t)
+            got = O.lib().or_inflow_u(P, y, t)
+            assert abs(got - want) < 1e-3 * U / (2 * nu) * H * H / 4
