@@ -474,6 +474,87 @@ def dam_gate(seed=0, dpF=1e-3, ratio=2, jitter_amp=1e-3, E=12e6, tank_len=0.5):
     )
 
 
+def venous_valve(seed=0, wo=10.0, DH=4e-3, L_H=8.0, leaflet_H=0.4, angle_deg=60.0, b=0.2e-3, ratio=2,
+                 jitter_amp=1e-3, A=2500.0, T=0.6):
+    """2-D vein with two straight flexible leaflets under a pulsatile inflow
+    (Section 4.3, Appendix A).
+
+    Printed: leaflet thickness b = 0.2 mm, dp_S = b/4, dp_F = 2 dp_S; blood
+    rho_F = 1000, leaflets rho_S = 1060, E = 1.5 MPa, Poisson 0.49
+    (neo-Hookean); inflow driven by dp/dx = -A cos(2 pi t / T) with
+    A = 2500 N/m^3, T = 0.6 s; Wo = (H/2) sqrt(omega / nu) in {1, 5, 10}, the
+    viscosity following from Wo.  The geometry is in a figure that is not in
+    the text; read as: channel height DH = 4 mm and length L_H DH, periodic in
+    x with the Womersley profile imposed in a 4 dp_F inflow buffer; one
+    leaflet rooted on each wall at x = 0.3 L, length leaflet_H DH, inclined
+    downstream at angle_deg to its wall, its part inside the wall (4 dp_S)
+    clamped.  c0 = 30 (A / (rho omega)) min(1, Wo^2 / 2): ten times three
+    times the inflow's velocity scale (Poiseuille amplitude at small Wo, plug
+    amplitude at large Wo; three for the acceleration through the gap).  The
+    initial fluid velocity is zero; the observer is the top leaflet's tip.
+    """
+    rng = np.random.default_rng(seed)
+    dpS = b / 4.0
+    dpF = ratio * dpS
+    L, H = L_H * DH, DH
+    w = 2.0 * np.pi / T
+    rho_F = 1000.0
+    nu = w * (H / 2) ** 2 / wo ** 2
+    c0 = 30.0 * A / (rho_F * w) * min(1.0, wo * wo / 2.0)
+    th = np.radians(angle_deg)
+    ll = leaflet_H * DH
+    xr = 0.3 * L
+    c_in = 4 * dpS
+    nx_, ne_ = int(round((ll + c_in) / dpS)), int(round(b / dpS))
+    xi = -c_in + (np.arange(nx_) + 0.5) * dpS
+    eta = -b / 2 + (np.arange(ne_) + 0.5) * dpS
+    XI, ETA = [g.ravel() for g in np.meshgrid(xi, eta, indexing="ij")]
+    srs, sns, scs, stips = [], [], [], []
+    leaflets = []
+    for root_y, sgn in ((0.0, 1.0), (H, -1.0)):
+        a = np.array([np.cos(th), sgn * np.sin(th)])
+        n = np.array([-a[1], a[0]])
+        root = np.array([xr, root_y])
+        leaflets.append((root, a, n))
+        r = root + XI[:, None] * a + ETA[:, None] * n
+        # outward normal of the nearest face: the two long sides and the tip
+        d_side = b / 2 - np.abs(ETA)
+        d_tip = ll - XI
+        nrm = np.where((d_tip < d_side)[:, None], a, np.sign(ETA)[:, None] * n)
+        srs.append(r)
+        sns.append(nrm)
+        scs.append((XI < 0.0).astype(np.uint8))
+        stips.append(np.argmin((XI - XI.max()) ** 2 + ETA ** 2 * 1e-3))
+    sr = np.concatenate(srs)
+    sn = np.concatenate(sns)
+    cons = np.concatenate(scs)
+    tip = len(srs[0]) + int(stips[1])   # the top leaflet's free end
+    fr = lattice((0.0, 0.0), (L, H), dpF)
+    keep = np.ones(len(fr), bool)
+    for root, a, n in leaflets:
+        q = fr - root
+        xi_f, eta_f = q @ a, q @ n
+        keep &= ~((xi_f > -c_in) & (xi_f < ll + 0.25 * dpF) & (np.abs(eta_f) < b / 2 + 0.25 * dpF))
+    fr = fr[keep]
+    wr_b, wn_b = _wall_layers_y(0.0, L, 0.0, -1, dpF, 4, 2)
+    wr_t, wn_t = _wall_layers_y(0.0, L, H, +1, dpF, 4, 2)
+    wr, wn = np.concatenate([wr_b, wr_t]), np.concatenate([wn_b, wn_t])
+    fr = jitter(fr, dpF, jitter_amp, rng)
+    sr = jitter(sr, dpS, jitter_amp, rng)
+    fr[:, 0] = np.mod(fr[:, 0], L)
+    return Case(
+        name=f"venous_valve_wo{wo:g}", dim=2, gravity=(0.0, 0.0, 0.0),
+        periodic_x=1, x_lo=0.0, Lx=L, n_reinit=5,
+        inflow_on=1, inflow_profile=2, inflow_width=4 * dpF, inflow_y0=0.0, inflow_H=H,
+        inflow_U=A / rho_F, inflow_tramp=0.0, inflow_period=T, inflow_wo=wo,
+        domain_lo=(0.0, -6 * dpF, 0.0), domain_hi=(L, H + 6 * dpF, 0.0),
+        f_r=fr, f_v=np.zeros_like(fr), f_p=np.zeros(len(fr)), f_dp=dpF, f_rho0=rho_F, f_c0=c0,
+        f_eta=rho_F * nu, w_r=wr, w_n=wn, w_dp=dpF,
+        s_r0=sr, s_v0=np.zeros_like(sr), s_n0=sn, s_cons=cons, s_dp=dpS, s_rho0=1060.0,
+        s_E=1.5e6, s_nu=0.49, tip=tip, meta=dict(DH=DH, L=L, T=T, wo=wo),
+    )
+
+
 def duct_plate_3d(seed=0, scale=1, jitter_amp=1e-3):
     """3-D channel flow past a clamped flexible plate.
 

@@ -86,10 +86,20 @@ typedef struct {
  * x in [x_lo, x_lo + width) get v = (U(y, t), 0, 0) at the start of a step.
  * profile 0: U = 6 Ubar (y - y0)(H - (y - y0)) / H^2 (mean Ubar, clamped to
  * [y0, y0 + H]); profile 1: uniform Ubar.  Ubar(t) = U (1 - cos(pi t /
- * t_ramp)) / 2 for t < t_ramp, else U. */
+ * t_ramp)) / 2 for t < t_ramp, else U.  profile 2 (Section 4.3, Appendix
+ * A): the Womersley flow of a channel of height H under the pressure
+ * gradient dp/dx = -A cos(2 pi t / period), with U = A / rho_F (m/s^2, ramped
+ * like Ubar) and womersley = (H / 2) sqrt(2 pi / (period nu)); with
+ * b = womersley / sqrt(2), s = 2 (y - y0) / H - 1, f1,2 = b (1 +- s),
+ * g = cosh 2b + cos 2b, w = 2 pi / period:
+ * u = U / (w g) [(sinh f1 sin f2 + sinh f2 sin f1) cos wt
+ *                + (g - cosh f1 cos f2 - cosh f2 cos f1) sin wt].
+ * SPHFSI_E_INVAL (when on) for width <= 0, an unknown profile, H <= 0 with
+ * profile 0 or 2, or period or womersley <= 0 with profile 2. */
 typedef struct {
     int32_t on, profile;
     double width, y0, H, U, t_ramp;
+    double period, womersley;   /* profile 2 only */
 } sphfsi_inflow;
 
 /* Counters and last-step diagnostics of the selected instance. */

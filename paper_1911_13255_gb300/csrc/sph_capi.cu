@@ -337,6 +337,8 @@ int make_inst(const InstHost &h, int D, Inst &d)
     P.in_H = h.inflow.H;
     P.in_U = h.inflow.U;
     P.in_tramp = h.inflow.t_ramp;
+    P.in_T = h.inflow.period;
+    P.in_wo = h.inflow.womersley;
     return SPHFSI_OK;
 }
 
@@ -552,7 +554,10 @@ int sphfsi_add_solid(sphfsi_ctx *c, int64_t n, const double *r0, const double *v
 int sphfsi_set_inflow(sphfsi_ctx *c, const sphfsi_inflow *f)
 {
     TRY(check_ctx(c, false));
-    if (!f || (f->on && (!(f->width > 0) || (f->profile == 0 && !(f->H > 0))))) return SPHFSI_E_INVAL;
+    if (!f || (f->on && (!(f->width > 0) || f->profile < 0 || f->profile > 2 ||
+                         (f->profile != 1 && !(f->H > 0)) ||
+                         (f->profile == 2 && (!(f->period > 0) || !(f->womersley > 0))))))
+        return SPHFSI_E_INVAL;
     c->ih[c->sel].inflow = *f;
     return SPHFSI_OK;
 }

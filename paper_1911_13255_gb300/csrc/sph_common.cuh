@@ -129,6 +129,7 @@ struct Phys {
     // inflow
     int inflow_on, inflow_profile;
     double in_w, in_y0, in_H, in_U, in_tramp;
+    double in_T, in_wo;   // Womersley profile: period, Womersley number
 };
 
 // Per-instance descriptor (device table, one entry per instance).

@@ -166,6 +166,18 @@ __device__ __forceinline__ double inflow_u(const Phys &P, double y, double t)
     if (P.inflow_profile == 1) return U;
     double yy = y - P.in_y0, H = P.in_H;
     yy = yy < 0.0 ? 0.0 : (yy > H ? H : yy);
+    if (P.inflow_profile == 2) {
+        // Womersley channel flow under dp/dx = -A cos(w t) (Appendix A), U = A / rho:
+        // with b = Wo / sqrt(2), s = 2 y / H - 1, f1,2 = b (1 +- s), g = cosh 2b + cos 2b,
+        // u = U / (w g) [(sinh f1 sin f2 + sinh f2 sin f1) cos wt + (g - cosh f1 cos f2 - cosh f2 cos f1) sin wt]
+        const double w = 2.0 * 3.14159265358979323846 / P.in_T, b = P.in_wo * 0.70710678118654752440;
+        const double sy = 2.0 * (yy - 0.5 * H) / H;
+        const double f1 = b * (1.0 + sy), f2 = b * (1.0 - sy);
+        const double g = cosh(2.0 * b) + cos(2.0 * b);
+        const double c = sinh(f1) * sin(f2) + sinh(f2) * sin(f1);
+        const double q = g - cosh(f1) * cos(f2) - cosh(f2) * cos(f1);
+        return U / (w * g) * (c * cos(w * t) + q * sin(w * t));
+    }
     return 6.0 * U * yy * (H - yy) / (H * H);
 }
 
