@@ -138,23 +138,39 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _source_hash():
+# The source file that defines each kernel with a DRAM-traffic record; the
+# record stays valid while that file, the launcher (sph_capi.cu, which sets
+# launch shapes) and every header are unchanged.
+KERNEL_SOURCE = {"k_momentum": "sph_fluid.cu", "k_solid_fluid_force": "sph_fluid.cu",
+                 "k_density": "sph_density.cu", "k_reinit": "sph_density.cu",
+                 "k_solid_cluster2d_one": "sph_solid.cu", "k_solid_cluster2d": "sph_solid.cu",
+                 "k_solid_cluster_one": "sph_solid.cu", "k_solid_cluster": "sph_solid.cu",
+                 "k_solid_substeps": "sph_solid.cu", "k_gemm_bf16": "sph_learn_gemm.cu"}
+
+
+def _source_hash(kernel=None):
+    """Hash of the CUDA sources: all of them, or those `kernel` depends on."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1911_13255_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    files = sorted(f for f in os.listdir(d) if f.endswith((".cu", ".cuh")))
+    if kernel is not None:
+        if kernel not in KERNEL_SOURCE:
+            return None
+        files = [f for f in files if f.endswith(".cuh") or f in (KERNEL_SOURCE[kernel], "sph_capi.cu")]
+    for f in files:
+        h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "sphfsi.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
-    summary, only if the kernel sources have not changed since it was taken."""
+    summary, only if the kernel's sources have not changed since it was taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
         key = f"{workload}/{kernel}"
-        if t.get("source_hash") == _source_hash() and key in t.get("kernels", {}):
+        if key in t.get("kernels", {}) and t.get("hashes", {}).get(key) == _source_hash(kernel):
             return t["kernels"][key]
     except Exception:
         pass
