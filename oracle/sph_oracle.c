@@ -13,7 +13,7 @@
  * r^2 = dx*dx + dy*dy (+ dz*dz) < (2h)^2 is bit-reproducible.
  *
  * Where the paper is silent or garbled a written reading is used; each is
- * named R1..R20 in the comments and listed in the design notes:
+ * named R1..R24 in the comments and listed in the design notes:
  *   R1  support radius 2h; in-support <=> r^2 < 4h^2 in FP64
  *   R2  solid volumes in all sums are the reference volumes V0 = dp_S^d
  *   R4  low-dissipation Riemann solver (the paper defers to its ref. [zhang2017])
@@ -32,12 +32,18 @@
  *   R16 density reinitialisation from the number density
  *   R17 normals n = normalize(F^-T n0)
  *   R18 inflow buffer + periodic x
+ *   R22 single-time-step criteria (the paper's baselines, K = 1)
+ *   R23 a coincident pair (r = 0) adds nothing
+ *   R24 Womersley inflow: the time factors of the printed solution
+ * (R19-R21 and R25 are geometry and workload readings of the input generators.)
  *
  * Parity unpinned: the exact limiter of the Riemann solver (R4) beyond its
  * tested properties (equal-state averages, exchange symmetry, compression
- * dissipation), the inflow/outflow buffer mechanism (R18) and the normal
- * update (R17) have no independent pin; everything else is pinned by the
- * tests in tests/test_oracle_pins.py.
+ * dissipation), the inflow/outflow buffer mechanism (R18), the normal
+ * update (R17) and the long-run behaviour of the paper's examples (its
+ * flow-induced-vibration amplitude and frequency, the valve leaflets) have
+ * no independent pin; everything else is pinned by the tests in
+ * tests/test_oracle_pins.py.
  */
 #include <math.h>
 #include <stdint.h>
