@@ -122,6 +122,10 @@ def lib():
             L.or_step.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Wall),
                                   C.POINTER(Solid), C.c_double, C.c_int, C.c_double, C.c_int64,
                                   C.POINTER(Diag)]
+            L.or_step_ex.restype = C.c_int
+            L.or_step_ex.argtypes = L.or_step.argtypes + [C.POINTER(Cache)]
+            L.or_cache_free.restype = None
+            L.or_cache_free.argtypes = [C.POINTER(Cache)]
             L.or_suggest_dt.restype = None
             L.or_suggest_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid),
                                         C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
@@ -217,6 +221,12 @@ def pairs(case_or_params, A, B, rc, same, brute=False):
 # whole-simulation driver
 # ---------------------------------------------------------------------------
 
+class Cache(C.Structure):
+    """Pair configuration frozen over an advection step (reading F2)."""
+    _fields_ = [("valid", C.c_int32), ("nf", C.c_int64), ("ns", C.c_int64), ("lists", C.c_void_p),
+                ("fr", C.POINTER(C.c_double)), ("sr", C.POINTER(C.c_double))]
+
+
 class OracleSim:
     """The oracle's simulation state for one Case (all FP64, original order)."""
 
@@ -307,9 +317,30 @@ class OracleSim:
         return lib().or_single_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), int(mode), vmax_f, vmax_s,
                                   amax_s)
 
+    def set_advection_cadence(self, n):
+        """Reading F2 (Algorithm 1): neighbour lists and kernel values built
+        once every n steps (an advection step of n acoustic steps) and held
+        over them; n = 0 rebuilds them every step (R15)."""
+        if getattr(self, "cache", None) is not None:
+            lib().or_cache_free(C.byref(self.cache))
+        self.cadence = int(n)
+        self.cache = Cache() if n > 0 else None
+
+    def __del__(self):
+        if getattr(self, "cache", None) is not None and _lib is not None:
+            _lib.or_cache_free(C.byref(self.cache))
+            self.cache = None
+
     def step(self, dt, K):
-        rc = lib().or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
-                           self.t, self.step_index, C.byref(self.diag))
+        cache = getattr(self, "cache", None)
+        if cache is not None:
+            if self.step_index % self.cadence == 0:
+                cache.valid = 0
+            rc = lib().or_step_ex(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
+                                  self.t, self.step_index, C.byref(self.diag), C.byref(cache))
+        else:
+            rc = lib().or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
+                               self.t, self.step_index, C.byref(self.diag))
         if rc != 0:
             raise RuntimeError(f"oracle step failed ({rc})")
         self.t += dt

@@ -642,8 +642,40 @@ static void wrap_x(const or_params *P, double *x)
  *  a7 K solid sub-steps (Eqs. verlet-first-half-solid .. -final-solid)
  *  a8 time-averaged solid velocity and acceleration (Eq. fs-coupling-mr)
  * ------------------------------------------------------------------------ */
+typedef struct {
+    csr_t FF, FW, FS, SF;
+} cached_lists;
+
+void or_cache_free(or_cache *c)
+{
+    if (!c) return;
+    if (c->lists) {
+        cached_lists *L = (cached_lists *)c->lists;
+        csr_free(&L->FF);
+        csr_free(&L->FW);
+        csr_free(&L->FS);
+        csr_free(&L->SF);
+        free(L);
+    }
+    free(c->fr);
+    free(c->sr);
+    c->lists = NULL;
+    c->fr = c->sr = NULL;
+    c->valid = 0;
+}
+
 int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K,
             double t, int64_t step_index, or_diag *dg)
+{
+    return or_step_ex(P, f, w, s, dt, K, t, step_index, dg, NULL);
+}
+
+/* c == NULL: lists and kernel values from this step's mid state (R15).
+ * c != NULL: the configuration frozen in c (reading F2), built here first
+ * when c is not valid; the drift, the state and the solid sub-steps are the
+ * same in both forms. */
+int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K,
+               double t, int64_t step_index, or_diag *dg, or_cache *c)
 {
     int dim = P->dim, dd = dim * dim;
     if (dim != 2 && dim != 3) return -1;
@@ -673,12 +705,45 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         wrap_x(P, &f->r[i * dim]);
     }
 
-    /* a2: neighbour lists (R15: rebuilt every coarse step) */
+    /* a2: neighbour lists (R15: rebuilt every coarse step; F2: once per
+       advection step, with the positions their kernel values are taken at) */
     csr_t FF, FW, FS, SF;
-    if (pairs_cells(P, dim, f->r, f->n, f->r, f->n, rcF, 1, &FF)) return -2;
-    if (pairs_cells(P, dim, f->r, f->n, w->r, w->n, rcF, 0, &FW)) return -2;
-    if (pairs_cells(P, dim, f->r, f->n, s->r, s->n, rcF, 0, &FS)) return -2;
-    if (pairs_cells(P, dim, s->r, s->n, f->r, f->n, rcF, 0, &SF)) return -2;
+    const double *fg = f->r, *sg_ = s->r; /* positions of the pair geometry */
+    int own = 1;
+    if (c && c->valid && c->nf == f->n && c->ns == s->n) {
+        cached_lists *L = (cached_lists *)c->lists;
+        FF = L->FF;
+        FW = L->FW;
+        FS = L->FS;
+        SF = L->SF;
+        fg = c->fr;
+        sg_ = c->sr;
+        own = 0;
+    } else {
+        if (pairs_cells(P, dim, f->r, f->n, f->r, f->n, rcF, 1, &FF)) return -2;
+        if (pairs_cells(P, dim, f->r, f->n, w->r, w->n, rcF, 0, &FW)) return -2;
+        if (pairs_cells(P, dim, f->r, f->n, s->r, s->n, rcF, 0, &FS)) return -2;
+        if (pairs_cells(P, dim, s->r, s->n, f->r, f->n, rcF, 0, &SF)) return -2;
+        if (c) {
+            or_cache_free(c);
+            cached_lists *L = (cached_lists *)malloc(sizeof(cached_lists));
+            L->FF = FF;
+            L->FW = FW;
+            L->FS = FS;
+            L->SF = SF;
+            c->lists = L;
+            c->fr = (double *)malloc(sizeof(double) * (f->n > 0 ? f->n * dim : 1));
+            c->sr = (double *)malloc(sizeof(double) * (s->n > 0 ? s->n * dim : 1));
+            memcpy(c->fr, f->r, sizeof(double) * f->n * dim);
+            if (s->n > 0) memcpy(c->sr, s->r, sizeof(double) * s->n * dim);
+            c->nf = f->n;
+            c->ns = s->n;
+            c->valid = 1;
+            fg = c->fr;
+            sg_ = c->sr;
+            own = 0;
+        }
+    }
     dg->n_ff = FF.ptr[f->n];
     dg->n_fw = FW.ptr[f->n];
     dg->n_fs = FS.ptr[f->n];
@@ -693,11 +758,11 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         for (int64_t i = 0; i < f->n; i++) {
             double sg = or_kernel_W(dim, 0.0, hF);
             for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++)
-                sg += or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, f->r + FF.idx[q] * dim, d)), hF);
+                sg += or_kernel_W(dim, sqrt(delta(P, dim, fg + i * dim, fg + FF.idx[q] * dim, d)), hF);
             for (int64_t q = FW.ptr[i]; q < FW.ptr[i + 1]; q++)
-                sg += VW / VF * or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, w->r + FW.idx[q] * dim, d)), hF);
+                sg += VW / VF * or_kernel_W(dim, sqrt(delta(P, dim, fg + i * dim, w->r + FW.idx[q] * dim, d)), hF);
             for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++)
-                sg += VS / VF * or_kernel_W(dim, sqrt(delta(P, dim, f->r + i * dim, s->r + FS.idx[q] * dim, d)), hF);
+                sg += VS / VF * or_kernel_W(dim, sqrt(delta(P, dim, fg + i * dim, sg_ + FS.idx[q] * dim, d)), hF);
             double rr = f->rho0 * sg / sigma0;
             if (P->free_surface && rr < f->rho0) rr = f->rho0;
             f->rho[i] = rr;
@@ -723,12 +788,12 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
 
     /* a4: fluid momentum at (r^{n+1/2}, rho^{n+1/2}, v^n), Eq. fluid-model-mr-mom */
     for (int64_t i = 0; i < f->n; i++) {
-        const double *ri = f->r + i * dim, *vi = f->v + i * dim;
+        const double *ri = fg + i * dim, *vi = f->v + i * dim;
         double Vi = mF / f->rho[i];
         double force[3] = {0, 0, 0}, e[3];
         for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
             int64_t j = FF.idx[q];
-            double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            double r = sqrt(delta(P, dim, ri, fg + j * dim, d));
             if (r == 0.0) continue; /* coincident pair: no direction, grad W = 0 (reading R23) */
             double dW = or_kernel_dW(dim, r, hF);
             double Vj = mF / f->rho[j];
@@ -751,7 +816,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++) {
             int64_t a = FS.idx[q];
             double fo[3];
-            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], s->r + a * dim, s->vbar + a * dim,
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], sg_ + a * dim, s->vbar + a * dim,
                     s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
             for (int k = 0; k < dim; k++) {
                 force[k] += fo[k];
@@ -769,7 +834,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
             int64_t i = SF.idx[q];
             double fo[3];
             fc.Vi = mF / f->rho[i];
-            fs_pair(P, dim, &fc, f->r + i * dim, f->v + i * dim, f->rho[i], p[i], s->r + a * dim,
+            fs_pair(P, dim, &fc, fg + i * dim, f->v + i * dim, f->rho[i], p[i], sg_ + a * dim,
                     s->vbar + a * dim, s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
             for (int k = 0; k < dim; k++) fa[k] -= fo[k];
         }
@@ -793,11 +858,11 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
 
     /* a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}), Eq. fluid-model-mr-con + R7 */
     for (int64_t i = 0; i < f->n; i++) {
-        const double *ri = f->r + i * dim, *vi = f->v + i * dim;
+        const double *ri = fg + i * dim, *vi = f->v + i * dim;
         double rate = 0.0, e[3], vs[3];
         for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++) {
             int64_t j = FF.idx[q];
-            double r = sqrt(delta(P, dim, ri, f->r + j * dim, d));
+            double r = sqrt(delta(P, dim, ri, fg + j * dim, d));
             if (r == 0.0) continue; /* coincident pair (reading R23) */
             double dW = or_kernel_dW(dim, r, hF);
             double Vj = mF / f->rho[j];
@@ -818,7 +883,7 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         for (int64_t q = FS.ptr[i]; q < FS.ptr[i + 1]; q++) {
             int64_t a = FS.idx[q];
             double dr;
-            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], s->r + a * dim, s->vbar + a * dim,
+            fs_pair(P, dim, &fc, ri, vi, f->rho[i], p[i], sg_ + a * dim, s->vbar + a * dim,
                     s->abar + a * dim, s->nrm + a * dim, VS, NULL, vi, &dr);
             rate += dr;
         }
@@ -831,10 +896,12 @@ int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, doub
         wrap_x(P, &f->r[i * dim]);
     }
     free(p);
-    csr_free(&FF);
-    csr_free(&FW);
-    csr_free(&FS);
-    csr_free(&SF);
+    if (own) {
+        csr_free(&FF);
+        csr_free(&FW);
+        csr_free(&FS);
+        csr_free(&SF);
+    }
 
     /* a7: K solid sub-steps with dt_S = dt / K (R13), f^F held constant */
     if (s->n > 0) {

@@ -68,6 +68,19 @@ int or_solid_accel(const or_params *P, const or_solid *s, const double *F, doubl
 double or_inflow_u(const or_params *P, double y, double t);
 int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K, double t,
             int64_t step_index, or_diag *dg);
+/* Pair configuration frozen over the acoustic steps of one advection step
+ * (Algorithm 1, reading F2): the neighbour lists and the fluid and solid
+ * positions that every pair's kernel value and gradient are evaluated at.
+ * valid = 0 makes the next or_step_ex build it at its mid state. */
+typedef struct {
+    int32_t valid;
+    int64_t nf, ns;
+    void *lists;
+    double *fr, *sr;
+} or_cache;
+int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K, double t,
+               int64_t step_index, or_diag *dg, or_cache *c);
+void or_cache_free(or_cache *c);
 void or_suggest_dt(const or_params *P, const or_fluid *f, const or_solid *s, double vmax_f, double vmax_s,
                    double amax_s, double *dt_ac, double *dt_ad, double *dt_s);
 int or_substeps(double dt_f, double dt_s);

@@ -562,3 +562,47 @@ def test_womersley_low_frequency_limit_is_poiseuille():
             want = U / (2 * nu) * y * (H - y) * math.cos(w * t)
             got = O.lib().or_inflow_u(P, y, t)
             assert abs(got - want) < 1e-3 * U / (2 * nu) * H * H / 4
+
+
+# --------------------------------------------------------------------------
+# Neighbour lists and kernel values held over an advection step (reading F2)
+# --------------------------------------------------------------------------
+
+def test_advection_cadence_one_is_the_per_step_rebuild():
+    case = fc.tiny_box(seed=3)
+    a, b = O.OracleSim(case), O.OracleSim(case)
+    b.set_advection_cadence(1)
+    dt, _, dts = a.suggest_dt()
+    K = a.substeps(dt, dts)
+    for _ in range(6):
+        a.step(dt, K)
+        b.step(dt, K)
+    for x, y in ((a.f_r, b.f_r), (a.f_v, b.f_v), (a.f_rho, b.f_rho), (a.s_r, b.s_r), (a.s_F, b.s_F)):
+        assert np.array_equal(x, y)
+
+
+def test_frozen_configuration_conserves_momentum_and_its_pair_counts():
+    """With the configuration held for 4 steps the pair terms still act
+    through one geometry on both sides, so the free block in fluid conserves
+    the total momentum to round-off; the pair counts stay those of the step
+    that built the configuration."""
+    case = fc.floating_block(seed=1)
+    s = O.OracleSim(case)
+    s.set_advection_cadence(4)
+    mF, mS = case.f_rho0 * case.f_dp ** 2, case.s_rho0 * case.s_dp ** 2
+
+    def mom():
+        return mF * s.f_v.sum(0) + mS * s.s_v.sum(0)
+
+    scale = mF * np.abs(s.f_v).sum() + mS * np.abs(s.s_v).sum()
+    P0 = mom()
+    dt, _, _ = s.suggest_dt()
+    counts = []
+    for _ in range(40):
+        d = s.step(dt, 3)
+        counts.append((d["n_ff"], d["n_fs"], d["n_sf"]))
+    assert np.abs(mom() - P0).max() < 1e-13 * scale
+    assert np.abs(s.s_v).max() > 1e-3
+    for w0 in range(0, 40, 4):
+        assert len(set(counts[w0:w0 + 4])) == 1
+    assert len(set(counts)) > 1   # the lists were rebuilt as the flow moved
