@@ -35,6 +35,8 @@
  *   R22 single-time-step criteria (the paper's baselines, K = 1)
  *   R23 a coincident pair (r = 0) adds nothing
  *   R24 Womersley inflow: the time factors of the printed solution
+ *   F2  neighbour lists and kernel values held over an advection step
+ *       (Algorithm 1; opt-in through or_step_ex)
  * (R19-R21 and R25 are geometry and workload readings of the input generators.)
  *
  * Parity unpinned: the exact limiter of the Riemann solver (R4) beyond its
