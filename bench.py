@@ -745,6 +745,7 @@ def run_valve(args, rank, world, local_rank):
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     sim = Simulation.from_case(case, stream=st)
+    sim.set_time_stepping(args.time_stepping)
     ts, xs, ys, dev_ms, steps, Ks = [], [], [], 0.0, 0, []
     x0, y0 = case.s_r0[case.tip]
     t = 0.0
@@ -785,7 +786,8 @@ def run_valve(args, rank, world, local_rank):
         "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": dev_ms / max(steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": label, "womersley": args.womersley, "n_fluid": case.nf, "n_solid": case.ns,
+        "config": {"workload": label, "womersley": args.womersley, "time_stepping": args.time_stepping,
+                   "n_fluid": case.nf, "n_solid": case.ns,
                    "n_wall": case.nw, "dp_F": case.f_dp, "dp_S": case.s_dp, "DH": DH, "inflow_period_s": T,
                    "c0": case.f_c0, "eta": case.f_eta, "K_median": float(np.median(Ks)) if Ks else None,
                    "l2": "not flushed (whole working set ~3 MB); every 50 steps the solid positions are read back"},
