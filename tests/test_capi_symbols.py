@@ -69,3 +69,32 @@ def test_batch_creation_checks_without_gpu():
     assert L.sphfsi_select(None, 0) == -1
     assert L.sphfsi_step(h, 1.0) == -4      # not finalized
     L.sphfsi_destroy(h)
+
+
+def test_time_stepping_and_inflow_checks_without_gpu():
+    """The single-time-step modes and the inflow profiles (Womersley needs
+    its period and number) are validated on the host."""
+    import paper_1911_13255_gb300 as pkg
+    L = pkg.lib()
+    p = pkg.Params()
+    p.dim = 2
+    for d in range(2):
+        p.domain_lo[d], p.domain_hi[d] = 0.0, 1.0
+    h = ctypes.c_void_p()
+    assert L.sphfsi_create(ctypes.byref(h), ctypes.byref(p), None) == 0
+    assert L.sphfsi_set_time_stepping(None, 1) == -1
+    for mode, rc in ((0, 0), (1, 0), (2, 0), (3, -1), (-1, -1)):
+        assert L.sphfsi_set_time_stepping(h, mode) == rc, mode
+    assert L.sphfsi_set_substeps(h, 4) == 0
+    cases = [((1, 2, 0.1, 0.0, 1.0, 2.5, 0.0, 0.6, 5.0), 0),
+             ((1, 2, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 5.0), -1),    # no period
+             ((1, 2, 0.1, 0.0, 1.0, 2.5, 0.0, 0.6, 0.0), -1),    # no Womersley number
+             ((1, 2, 0.1, 0.0, 0.0, 2.5, 0.0, 0.6, 5.0), -1),    # no channel height
+             ((1, 3, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0), -1),    # unknown profile
+             ((1, 0, 0.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0.0), -1),    # no buffer
+             ((1, 1, 0.1, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0), 0),     # uniform: no height needed
+             ((0, 7, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0), 0)]     # off: not checked
+    for vals, rc in cases:
+        f = pkg.Inflow(*vals)
+        assert L.sphfsi_set_inflow(h, ctypes.byref(f)) == rc, vals
+    L.sphfsi_destroy(h)
