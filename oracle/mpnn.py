@@ -7,7 +7,7 @@ The paper integrates the solid with K sub-steps per fluid step (Section 3.3).
 The learned form replaces those K sub-steps of one fluid step by one
 evaluation of a network over the body's static neighbour graph (the same
 reference-configuration neighbour list the sub-steps use, support 2 h_S),
-and keeps the plain sub-stepping as fallback and judge.  This module states
+and keeps the plain sub-stepping as fallback and as the measure of its error.  This module states
 that network in plain numpy, FP64, node by node and layer by layer:
 
   features   x_a = [u_a / s_u, v_a / s_v, H_a / s_H, f_a / s_f, c_a, dt / s_t, 0...]
