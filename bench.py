@@ -601,9 +601,11 @@ def _tip_oscillation(t, y, t0):
     """Amplitude (half the mean peak-to-peak height of the full cycles) and
     frequency (mean period between upward crossings of the mean) of a
     sampled tip coordinate after time t0."""
-    t, y = np.asarray(t), np.asarray(y)
+    t, y = np.asarray(t, np.float64), np.asarray(y, np.float64)
     keep = t >= t0
     t, y = t[keep], y[keep]
+    if len(t) < 2:
+        return None, None, 0
     ym = y.mean()
     z = y - ym
     up = np.where((z[:-1] < 0) & (z[1:] >= 0))[0]

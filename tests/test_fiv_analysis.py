@@ -26,3 +26,8 @@ def test_growing_signal_and_short_records():
     assert a_mid < a_late < 0.1 + 0.04 * 20.0
     # fewer than three upward crossings: no estimate
     assert bench._tip_oscillation(t, y, 19.5)[:2] == (None, None)
+
+
+def test_empty_and_short_windows():
+    assert bench._tip_oscillation([], [], 0.0) == (None, None, 0)
+    assert bench._tip_oscillation([0.1, 0.2], [0.0, 1.0], 5.0) == (None, None, 0)
