@@ -396,6 +396,11 @@ def run_gpu(args, rank, world, local_rank):
         ctas = (max(c.ns for c in cases) + 127) // 128
         sm_peak = fp32_peak_tflops(sm_mhz, n_sm=min(152, ctas * min(len(cases), 152 // max(ctas, 1))))
         extra = {"ctas_per_body": ctas, "frac_of_the_sms_it_occupies": achieved / sm_peak}
+    if dom == "solid_substeps":
+        # a latency-bound kernel: its sub-step rate (all bodies advance together)
+        k_mean = sum(i["last_K"] for i in infos) / len(infos)
+        extra["us_per_sub_step"] = per_launch[dom] * 1e3 / max(k_mean, 1.0)
+        extra["sub_steps_per_s"] = k_mean / (per_launch[dom] * 1e-3)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak, **extra,
             "traffic": _traffic(kernel_names.get(dom, dom), args.workload), "kernel": kernel_names.get(dom, dom),
             "stage": dom, "ms_per_launch": per_launch[dom], "work_per_launch": work,
