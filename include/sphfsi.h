@@ -367,10 +367,13 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
  * writes to counts (device pointer, n int32) the number of other points j
  * with |r_i - r_j|^2 < (2 h)^2, h = 1.3 dp, computed in FP64 as dx*dx + dy*dy
  * (+ dz*dz) with the minimal image in x when p->periodic_x (the same test as
- * sphfsi_debug_neighbors).  The cell grid follows p (dim, domain box,
- * periodic x) as a context built from p with cell_reach 1 would (the
- * counts do not depend on the cell grid).  Work is issued on
- * cuda_stream and is asynchronous.
+ * sphfsi_debug_neighbors); with periodic_x, x is first brought into
+ * [x_lo, x_lo + Lx) (points already inside keep their value bit for bit),
+ * so points may be given outside the period.  The cell grid follows p (dim,
+ * domain box, periodic x) as a context built from p with cell_reach 1 would
+ * (the counts do not depend on the cell grid; points outside the box fall
+ * into its border cells).  Work is issued on cuda_stream and is
+ * asynchronous.
  *
  * Scratch (cell keys, the permutation, the cell histogram) is one
  * file-scope device array sized for at most SPHFSI_NOALLOC_MAX_PARTICLES
@@ -380,7 +383,10 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
  * array's device address with that device current; make that first call
  * before any stream capture.  Every call shares the one array, so calls
  * whose work overlaps on the GPU (other streams, other host threads) race:
- * serialise them.  Returns SPHFSI_E_INVAL for bad arguments. */
+ * serialise them.  Returns SPHFSI_E_INVAL for bad arguments (including a
+ * non-finite dp, box or period) and SPHFSI_E_CAPACITY when the box holds
+ * more cells of edge 2 h than the maximum; both checks run before any
+ * device work. */
 #define SPHFSI_NOALLOC_MAX_PARTICLES (1 << 18)
 #define SPHFSI_NOALLOC_MAX_CELLS (1 << 18)
 int sphfsi_neighbor_counts_noalloc(const sphfsi_params *p, int64_t n, const double *r, double dp, int32_t *counts,
@@ -427,6 +433,14 @@ int sphfsi_solid_graph(sphfsi_ctx *c, int64_t *ptr, int64_t *idx, double *w, dou
  * otherwise the plain sub-steps run from the unchanged state.  tol < 0
  * switches the learned path off. */
 int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, double tol);
+
+/* The network's input rows of the selected instance from the last step that
+ * ran the learned sub-stepper (the feature rows described with
+ * sphfsi_set_learned, 64 FP32 columns, zero-padded), in original particle
+ * order: x receives n_solid x 64 floats (host or device pointer).  For
+ * checking training features against the ones a step feeds the network.
+ * SPHFSI_E_STATE before sphfsi_set_learned. */
+int sphfsi_get_learned_features(sphfsi_ctx *c, float *x);
 
 /* Message-passing network over one body's static neighbour graph (the
  * learned solid sub-stepper).  With x the N x 64 feature matrix (FP32):

@@ -41,11 +41,12 @@
  *
  * Parity unpinned: the exact limiter of the Riemann solver (R4) beyond its
  * tested properties (equal-state averages, exchange symmetry, compression
- * dissipation), the inflow/outflow buffer mechanism (R18), the normal
- * update (R17) and the long-run behaviour of the paper's examples (its
+ * dissipation), the choice of a periodic channel with a velocity buffer as
+ * the unprinted inflow/outflow mechanism (R18; the buffer's assignment
+ * itself is pinned) and the long-run behaviour of the paper's examples (its
  * flow-induced-vibration amplitude and frequency, the valve leaflets) have
- * no independent pin; everything else is pinned by the tests in
- * tests/test_oracle_pins.py.
+ * no independent pin; everything else, the normal update (R17) included, is
+ * pinned by the tests in tests/test_oracle_pins.py.
  */
 #include <math.h>
 #include <stdint.h>

@@ -108,6 +108,7 @@ _SIGS = {
     "sphfsi_tc_status": (C.c_int, [C.POINTER(C.c_int32), C.c_int32]),
     "sphfsi_solid_graph": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "sphfsi_set_learned": (C.c_int, [_vp, _vp, _vp, C.c_double]),
+    "sphfsi_get_learned_features": (C.c_int, [_vp, _vp]),
     "sphfsi_mpnn_n_params": (C.c_int64, [C.c_int32]),
     "sphfsi_mpnn_create": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.c_int32,
                                      _vp]),
@@ -331,6 +332,12 @@ class Simulation:
         th = np.ascontiguousarray(theta, np.float32)
         sc = np.ascontiguousarray(scales, np.float64)
         _check(lib().sphfsi_set_learned(self.h, _ptr(th), _ptr(sc), float(tol)), "sphfsi_set_learned")
+
+    def learned_features(self):
+        """Input rows (n_solid x 64, original order) the last learned step fed the network."""
+        x = np.zeros((self.ns, 64), np.float32)
+        _check(lib().sphfsi_get_learned_features(self.h, _ptr(x)), "sphfsi_get_learned_features")
+        return x
 
     def pairs_total(self):
         """Pair interactions of all instances since creation."""

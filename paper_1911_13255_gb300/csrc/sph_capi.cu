@@ -1812,6 +1812,22 @@ int sphfsi_set_learned(sphfsi_ctx *c, const float *theta, const double *scales, 
     return SPHFSI_OK;
 }
 
+int sphfsi_get_learned_features(sphfsi_ctx *c, float *x)
+{
+    TRY(check_ctx(c, true));
+    if (!x) return SPHFSI_E_INVAL;
+    if (!c->mpnn) return SPHFSI_E_STATE;
+    constexpr int kFin = 64;
+    std::vector<float> all;
+    TRY(download(c, all, mpnn_input(c->mpnn), (size_t)c->S.n * kFin));
+    const InstHost &h = c->ih[c->sel];
+    std::vector<float> out((size_t)h.ns * kFin);
+    // device row s0 + k holds original particle s_order[k]
+    for (int64_t k = 0; k < h.ns; k++)
+        std::memcpy(&out[(size_t)h.s_order[k] * kFin], &all[(size_t)(h.d.s0 + k) * kFin], sizeof(float) * kFin);
+    return deliver(x, out);
+}
+
 int sphfsi_set_profiling(sphfsi_ctx *c, int on)
 {
     TRY(check_ctx(c, true));

@@ -13,6 +13,7 @@
 // a stand-in, not a device address); the device address is looked up once
 // per device with cudaGetSymbolAddress, with that device current, on the
 // first call made on that device.
+#include <cmath>
 #include <mutex>
 
 #include "sph_common.cuh"
@@ -57,6 +58,18 @@ struct NGrid {
     double Lx, rc2;
 };
 
+// x brought into the period [lo, lo + Lx) when periodic in x (identity for
+// points already inside it), so that points given outside the period are
+// keyed into the cell they wrap to and one minimal-image correction of a
+// difference suffices
+__device__ __forceinline__ double wrap_x(double x, const NGrid &g)
+{
+    if (!g.periodic_x) return x;
+    double w = x - g.Lx * floor((x - g.lo[0]) / g.Lx);
+    // rounding can leave w == lo + Lx for x just below a multiple of the period
+    return w >= g.lo[0] + g.Lx ? w - g.Lx : (w < g.lo[0] ? w + g.Lx : w);
+}
+
 __global__ void k_na_clear(int *ccount, int ncell)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -68,7 +81,11 @@ __global__ void k_na_key(const double *__restrict__ r, int n, NGrid g, int *key,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c[3] = {0, 0, 0};
-    for (int k = 0; k < g.dim; k++) c[k] = cell_coord(r[(size_t)i * g.dim + k], g.lo[k], g.cs[k], g.nc[k]);
+    for (int k = 0; k < g.dim; k++) {
+        double x = r[(size_t)i * g.dim + k];
+        if (k == 0) x = wrap_x(x, g);
+        c[k] = cell_coord(x, g.lo[k], g.cs[k], g.nc[k]);
+    }
     int kk = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
     key[i] = kk;
     atomicAdd(&ccount[kk], 1);
@@ -82,6 +99,7 @@ __global__ void k_na_count(const double *__restrict__ r, int n, NGrid g, const i
     const int D = g.dim;
     double ri[3] = {0, 0, 0};
     for (int k = 0; k < D; k++) ri[k] = r[(size_t)i * D + k];
+    ri[0] = wrap_x(ri[0], g);
     int kk = key[i];
     int cx = kk % g.nc[0], cy = (kk / g.nc[0]) % g.nc[1], cz = kk / (g.nc[0] * g.nc[1]);
     int cnt = 0;
@@ -102,7 +120,7 @@ __global__ void k_na_count(const double *__restrict__ r, int n, NGrid g, const i
                 for (int q = cstart[c]; q < cstart[c + 1]; q++) {
                     int j = perm[q];
                     if (j == i) continue;
-                    double d0 = ri[0] - r[(size_t)j * D];
+                    double d0 = ri[0] - wrap_x(r[(size_t)j * D], g);
                     if (g.periodic_x) {
                         if (d0 > 0.5 * g.Lx) d0 -= g.Lx;
                         else if (d0 < -0.5 * g.Lx) d0 += g.Lx;
@@ -128,10 +146,10 @@ extern "C" int sphfsi_neighbor_counts_noalloc(const sphfsi_params *p, int64_t n,
                                               int32_t *counts, void *cuda_stream)
 {
     using namespace sph;
-    if (!p || (p->dim != 2 && p->dim != 3) || n < 0 || !(dp > 0.0)) return SPHFSI_E_INVAL;
+    if (!p || (p->dim != 2 && p->dim != 3) || n < 0 || !(dp > 0.0) || !std::isfinite(dp)) return SPHFSI_E_INVAL;
     if (n == 0) return SPHFSI_OK;
     if (!r || !counts) return SPHFSI_E_INVAL;
-    if (p->periodic_x && !(p->Lx > 0.0)) return SPHFSI_E_INVAL;
+    if (p->periodic_x && !(p->Lx > 0.0 && std::isfinite(p->Lx) && std::isfinite(p->x_lo))) return SPHFSI_E_INVAL;
     if (n > kMaxN) return SPHFSI_E_CAPACITY;
     const double h = 1.3 * dp;
     NGrid g{};
@@ -152,8 +170,12 @@ extern "C" int sphfsi_neighbor_counts_noalloc(const sphfsi_params *p, int64_t n,
             lo = p->x_lo;
             L = p->Lx;
         }
-        if (!(L > 0.0)) return SPHFSI_E_INVAL;
-        long long m = (long long)floor(L / (2.0 * h));
+        if (!(L > 0.0) || !std::isfinite(L) || !std::isfinite(lo)) return SPHFSI_E_INVAL;
+        // cells along this axis, checked as a double before the conversion
+        const double q = floor(L / (2.0 * h));
+        if (!std::isfinite(q)) return SPHFSI_E_INVAL;
+        if (q > (double)kMaxCells) return SPHFSI_E_CAPACITY;
+        long long m = (long long)q;
         if (m < 1) m = 1;
         if (k == 0 && p->periodic_x && m < 3) return SPHFSI_E_INVAL;
         if (m > kMaxCells) return SPHFSI_E_CAPACITY;

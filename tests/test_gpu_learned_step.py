@@ -65,7 +65,7 @@ def test_accepted_step_applies_the_network_and_matches_the_oracle_residual():
     cons = np.asarray(case.s_cons)
     free = cons == 0
     m = case.s_rho0 * case.s_dp ** d
-    graph = sim.solid_graph()
+    graph = M.build_graph(case.s_r0, case.s_dp, d)   # the oracle's own graph, not the library's
     x = M.features(pre["r"] - case.s_r0, pre["v"], pre["F"] - np.eye(d), fF, cons, dt, _sc(), d)
     x = x.astype(np.float32).astype(np.float64)
     y, _ = M.forward(theta.astype(np.float64), x, graph, d, round_bf16=True)
@@ -90,6 +90,50 @@ def test_accepted_step_applies_the_network_and_matches_the_oracle_residual():
     ref.set_solid_positions(post["r"])
     assert rel(post["F"] - np.eye(d), ref.F_from_positions() - np.eye(d)) < 1e-4
     assert rel(post["vbar"][free], ((post["r"] - pre["r"]) / dt)[free]) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["channel_flag", "tiny_box_3d"])
+def test_library_graph_equals_the_oracle_graph(name):
+    """sphfsi_solid_graph (the device's static list and V0 grad0 W entries)
+    against the oracle's brute-force graph: same rows and columns, w and g
+    equal to FP32 rounding."""
+    case = getattr(fc, name)(seed=0)
+    sim = Simulation.from_case(case)
+    ptr, idx, w, g = sim.solid_graph()
+    optr, oidx, ow, og = M.build_graph(case.s_r0, case.s_dp, case.dim)
+    assert np.array_equal(ptr, optr) and np.array_equal(idx, oidx)
+    assert np.abs(w - ow).max() <= 1e-12 * np.abs(ow).max()
+    assert np.abs(g - og).max() <= 1e-6 * np.abs(og).max()
+    sim.close()
+
+
+def test_in_step_features_equal_the_training_features():
+    """The feature rows the step's kernel feeds the network equal the rows
+    learn.features builds on the host from the same state (the state before
+    the step, the step's coupling force and dt), to FP32 rounding, so that
+    the network is trained on inputs laid out and scaled as in a step."""
+    case = fc.channel_flag(seed=0)
+    d = case.dim
+    sim = Simulation.from_case(case)
+    for _ in range(5):
+        sim.step(0.0)
+    sim.sync()
+    pre = sim.get_solid()
+    sim.set_learned(learn.init_params(d, 1), SCALES, tol=0.0)   # proposals rejected: the plain step runs
+    sim.step(0.0)
+    sim.sync()
+    post, info = sim.get_solid(), sim.info()
+    x_gpu = sim.learned_features()
+    data = {"u": (pre["r"] - case.s_r0)[None], "v": pre["v"].astype(np.float64)[None],
+            "H": (pre["F"] - np.eye(d)).reshape(1, case.ns, d * d), "f": post["fF"].astype(np.float64)[None],
+            "dt": np.array([info["last_dt"]])}
+    x_host = learn.features(data, 0, case.s_cons, SCALES)
+    nf = 2 * d + d * d + d + 2
+    assert np.all(x_gpu[:, nf:] == 0.0) and np.all(x_host[:, nf:] == 0.0)
+    for lo, hi in ((0, d), (d, 2 * d), (2 * d, 2 * d + d * d), (2 * d + d * d, 3 * d + d * d), (nf - 2, nf)):
+        a, b = x_gpu[:, lo:hi].astype(np.float64), x_host[:, lo:hi].astype(np.float64)
+        assert np.abs(a - b).max() <= 1e-6 * max(np.abs(b).max(), 1e-30), (lo, hi)
+    sim.close()
 
 
 def test_a_network_trained_on_plain_steps_learns_them():

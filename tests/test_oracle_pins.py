@@ -519,6 +519,157 @@ def test_coincident_pairs_are_the_limit_of_close_pairs():
         assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
 
 
+def _dyadic(x, bits=20):
+    """Round to a multiple of 2^-bits, so that half drifts by dt = 2^-12 of
+    velocities that are multiples of 2^-7 are exact in FP64."""
+    return np.round(np.asarray(x, np.float64) * 2.0 ** bits) / 2.0 ** bits
+
+
+def _coincident_at_mid_state(eps, dt):
+    """tiny_box plus two fluid particles with velocities unlike their
+    partners', placed so that after the first half drift (r + dt v / 2) one
+    sits exactly on fluid particle k and the other exactly on solid particle
+    m (both displaced by eps dp)."""
+    c = fc.tiny_box(seed=11)
+    c.n_reinit = 0
+    k, m = len(c.f_r) // 3, len(c.s_r0) // 2
+    c.f_r, c.f_v = c.f_r.copy(), c.f_v.copy()
+    c.f_r[k] = _dyadic(c.f_r[k])
+    c.f_v[k] = [2.0 ** -6, -2.0 ** -7]
+    dv = np.array([2.0 ** -5, -3 * 2.0 ** -7])
+    s0 = c.s_r0.copy()
+    s0[m] = _dyadic(s0[m])
+    c.s_r0 = s0
+    vs = np.array([-2.0 ** -6, 2.0 ** -5])
+    off = eps * c.f_dp * np.array([0.6, 0.8])
+    c.f_r = np.concatenate([c.f_r, (c.f_r[k] - 0.5 * dt * dv + off)[None], (s0[m] - 0.5 * dt * vs + off)[None]])
+    c.f_v = np.concatenate([c.f_v, (c.f_v[k] + dv)[None], vs[None]])
+    c.f_p = np.concatenate([c.f_p, c.f_p[k:k + 1], [0.0]])
+    return c, k
+
+
+def test_coincident_pair_with_unequal_velocities_drops_only_the_viscous_limit():
+    """Reading R23 with v_i != v_j.  As r -> 0 the Wendland kernel gives
+    (1/r) dW/dr -> -5 alpha_2 / h^2 (a closed form of the kernel of Section
+    4), so the fluid-fluid viscous term 2 eta V_i V_j (v_i - v_j) (1/r) dW/dr
+    has a finite limit, which the coincident pair drops; the pressure terms
+    vanish with dW.  The step at r = 1e-9 dp must therefore exceed the step
+    at r = 0 by exactly that limit on the pair (opposite on the partner) and
+    by nothing elsewhere; the fluid-solid viscous term, regularised by
+    r + 0.01 h_F, has limit zero, so the particle on the solid and the solid's
+    coupling force do not change."""
+    dt = 2.0 ** -12
+    out = []
+    for eps in (0.0, 1e-9):
+        case, k = _coincident_at_mid_state(eps, dt)
+        s = O.OracleSim(case)
+        rho = s.f_rho.copy()
+        s.step(dt, 2)
+        assert np.all(np.isfinite(s.f_dvdt)) and np.all(np.isfinite(s.s_fF))
+        out.append((s.f_dvdt.copy(), s.s_fF.copy()))
+    d = out[1][0] - out[0][0]
+    i, j = k, case.nf - 2
+    hF = 1.3 * case.f_dp
+    alpha = 7.0 / (4.0 * math.pi * hF ** 2)
+    m = case.f_rho0 * case.f_dp ** 2
+    lim = 2 * case.f_eta * (m / rho[i]) * (m / rho[j]) * (case.f_v[i] - case.f_v[j]) * (-5 * alpha / hF ** 2) / m
+    assert np.abs(lim).max() > 0.3     # the limit is not small: ~6 % of g here
+    assert np.abs(d[i] - lim).max() <= 1e-6 * np.abs(lim).max()
+    assert np.abs(d[j] + lim).max() <= 1e-6 * np.abs(lim).max()
+    rest = np.ones(case.nf, bool)
+    rest[[i, j]] = False
+    assert np.abs(d[rest]).max() <= 1e-6 * np.abs(lim).max()
+    assert np.abs(out[1][1] - out[0][1]).max() <= 1e-6 * np.abs(out[0][1]).max()
+
+
+# --------------------------------------------------------------------------
+# Normal update (reading R17): n = normalize(F^-T n0) at the reinit cadence
+# --------------------------------------------------------------------------
+
+def _rotation(dim, seed):
+    rng = np.random.default_rng(seed)
+    if dim == 2:
+        th = rng.uniform(0.3, 2.5)
+        return np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    return spatial.transform.Rotation.from_rotvec(rng.uniform(-1.0, 1.0, 3)).as_matrix()
+
+
+def _normals_after_one_reinit_step(dim, F):
+    case = fc.tiny_box(seed=3) if dim == 2 else fc.tiny_box_3d(seed=3)
+    case.n_reinit = 1      # step 0 is a reinitialisation step
+    s = O.OracleSim(case)
+    s.s_F[:] = F
+    s.step(1e-9, 1)        # the normals are set before the sub-steps move F
+    return s.s_n0.copy(), s.s_nrm.copy()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_normals_turn_with_a_rigid_rotation(dim):
+    """F = R (finite rotation): the surface turns with the body, n = R n0."""
+    R = _rotation(dim, seed=dim)
+    n0, n = _normals_after_one_reinit_step(dim, np.broadcast_to(R, (1, dim, dim)))
+    assert np.abs(n - n0 @ R.T).max() < 1e-12
+
+
+def _tangents(n0):
+    """Unit vectors spanning the plane normal to each row of n0."""
+    if n0.shape[1] == 2:
+        return [np.stack([-n0[:, 1], n0[:, 0]], 1)]
+    a = np.where(np.abs(n0[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]])
+    t1 = np.cross(n0, a)
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    return [t1, np.cross(n0, t1)]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_normals_of_an_affinely_deformed_surface(dim):
+    """F = A (a general affine map, det A > 0, different per particle): a
+    material surface element with normal n0 and tangents t maps to the
+    element spanned by A t, so the new unit normal must be orthogonal to
+    every A t and point to the same side as A n0 (the map keeps the
+    orientation).  Checked by geometry, not by the F^-T formula."""
+    rng = np.random.default_rng(7 + dim)
+    case_ns = len(fc.tiny_box(seed=3).s_r0) if dim == 2 else len(fc.tiny_box_3d(seed=3).s_r0)
+    A = np.eye(dim)[None] + rng.uniform(-0.45, 0.45, size=(case_ns, dim, dim))
+    assert np.all(np.linalg.det(A) > 0.05)
+    n0, n = _normals_after_one_reinit_step(dim, A)
+    assert np.abs(np.linalg.norm(n, axis=1) - 1.0).max() < 1e-14
+    for t in _tangents(n0):
+        At = np.einsum("aij,aj->ai", A, t)
+        assert np.abs((n * At).sum(1)).max() < 1e-13 * np.abs(At).max()
+    assert np.all((n * np.einsum("aij,aj->ai", A, n0)).sum(1) > 0.0)
+
+
+# --------------------------------------------------------------------------
+# Inflow buffer assignment (reading R18)
+# --------------------------------------------------------------------------
+
+def test_inflow_buffer_sets_exactly_the_particles_inside_it():
+    """With dt = 0 a step leaves the velocities as the inflow buffer (a1)
+    set them: every fluid particle with x in [x_lo, x_lo + width) carries
+    (U(y, t), 0) -- U the profile pinned above, half-way up its ramp here --
+    and every other particle keeps its velocity bit for bit.  Two particles
+    sit exactly on the buffer's edges (x_lo inside, x_lo + width outside)."""
+    case = fc.channel_flag(t_ramp=0.5)
+    rng = np.random.default_rng(5)
+    case.f_v = rng.uniform(-0.3, 0.3, size=case.f_v.shape)
+    edge = np.argsort(np.abs(case.f_r[:, 0] - case.inflow_width))[:1]
+    lo = np.argsort(np.abs(case.f_r[:, 0] - case.x_lo))[:1]
+    case.f_r = case.f_r.copy()
+    case.f_r[edge, 0] = case.x_lo + case.inflow_width
+    case.f_r[lo, 0] = case.x_lo
+    s = O.OracleSim(case)
+    s.t = 0.25
+    r0, v0 = s.f_r.copy(), s.f_v.copy()
+    s.step(0.0, 1)
+    inb = (r0[:, 0] >= case.x_lo) & (r0[:, 0] < case.x_lo + case.inflow_width)
+    assert inb[lo].all() and not inb[edge].any() and 100 < inb.sum() < case.nf // 10
+    P = O.make_params(case)
+    u = np.array([O.lib().or_inflow_u(P, y, 0.25) for y in r0[inb, 1]])
+    assert np.array_equal(s.f_v[inb, 0], u) and np.all(s.f_v[inb, 1] == 0.0)
+    assert np.array_equal(s.f_v[~inb], v0[~inb])
+
+
 # --------------------------------------------------------------------------
 # Womersley inflow (Appendix A, reading R24)
 # --------------------------------------------------------------------------

@@ -1,7 +1,8 @@
 """The allocation-free entry point sphfsi_neighbor_counts_noalloc, called
 through the C-ABI, gives the same per-particle neighbour counts as the
-context-based sphfsi_debug_neighbors (integer counts: exact), on two calls in
-a row with different inputs.
+context-based sphfsi_debug_neighbors and as the oracle's neighbour lists
+(integer counts: exact), on two calls in a row with different inputs, and
+for points given outside a periodic x range.
 
 It serves callers that cannot call cudaMalloc (for example code that only
 receives input/output buffers from a framework whose caching allocator owns
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 
 import fsi_cases as fc
+import oracle as O
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,13 +56,33 @@ def _noalloc_counts(case, stream):
     return counts.cpu().numpy()
 
 
+def _oracle_counts(case):
+    ptr, _ = O.pairs(case, case.f_r, case.f_r, 2.0 * (1.3 * case.f_dp), same=True)
+    return np.diff(ptr).astype(np.int32)
+
+
 def test_noalloc_neighbor_counts_match_context_entry_point_twice():
     stream = torch.cuda.Stream()
     for case in (fc.channel_flag(seed=0), fc.tiny_box_3d(seed=2)):
         want = _reference_counts(case)
         got = _noalloc_counts(case, stream)
         assert np.array_equal(got, want)
+        assert np.array_equal(got, _oracle_counts(case))
         assert want.sum() > 0
+
+
+def test_noalloc_counts_points_given_outside_the_period():
+    """Periodic x: shifting points by whole periods does not change their
+    neighbours; the counts equal the oracle's on the points inside."""
+    stream = torch.cuda.Stream()
+    case = fc.channel_flag(seed=1)
+    assert case.periodic_x
+    want = _oracle_counts(case)
+    rng = np.random.default_rng(3)
+    shifted = case.f_r.copy()
+    shifted[:, 0] += case.Lx * rng.choice([-2.0, -1.0, 0.0, 1.0], size=case.nf)
+    moved = fc.Case(**{**case.__dict__, "f_r": shifted})
+    assert np.array_equal(_noalloc_counts(moved, stream), want)
 
 
 def test_noalloc_rejects_oversized_input():
@@ -69,3 +91,9 @@ def test_noalloc_rejects_oversized_input():
     n = (1 << 18) + 1
     rc = pkg.lib().sphfsi_neighbor_counts_noalloc(ctypes.byref(p), n, 1, case.f_dp, 1, None)
     assert rc == -7   # SPHFSI_E_CAPACITY, checked before any device access
+    # a box of more cells than the maximum (tiny dp), and non-finite sizes,
+    # are rejected before any device access too
+    assert pkg.lib().sphfsi_neighbor_counts_noalloc(ctypes.byref(p), 10, 1, 1e-9, 1, None) == -7
+    assert pkg.lib().sphfsi_neighbor_counts_noalloc(ctypes.byref(p), 10, 1, float("inf"), 1, None) == -1
+    p.domain_hi[0] = float("inf")
+    assert pkg.lib().sphfsi_neighbor_counts_noalloc(ctypes.byref(p), 10, 1, case.f_dp, 1, None) == -1
