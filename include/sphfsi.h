@@ -197,6 +197,21 @@ int sphfsi_set_substeps(sphfsi_ctx *c, int32_t K);
  * other mode.  Applies to every instance of a batch. */
 int sphfsi_set_time_stepping(sphfsi_ctx *c, int32_t mode);
 
+/* Advection cadence of the pair configuration (Algorithm 1: the neighbour
+ * lists and the kernel values W_ij and gradients grad W_ij are updated once
+ * per advection step and held over its acoustic steps).  n <= 1 (the
+ * default): rebuilt every coarse step from the step's mid positions.  n > 1:
+ * rebuilt at steps whose index (instance 0's) is a multiple of n, and at the
+ * next step after any of sphfsi_set_fluid_state, sphfsi_set_solid_state,
+ * sphfsi_set_time or this call; on the steps in between every pair term
+ * takes its W and grad W at the fluid and solid positions of the last
+ * rebuild (the same pairs, in the same order), with current densities,
+ * pressures, velocities, time-averaged solid velocities and accelerations
+ * and normals.  All instances of a batch rebuild together.  While n > 1,
+ * sphfsi_debug_neighbors returns SPHFSI_E_STATE (its binning would replace
+ * the held configuration).  SPHFSI_E_INVAL for n < 0. */
+int sphfsi_set_advection_cadence(sphfsi_ctx *c, int32_t n);
+
 /* One coarse step a1..a8.  dt_F > 0 fixes the step; dt_F <= 0 uses the
  * acoustic criterion 0.6 h_F / (c0 + |v|max) (Eq. dt-relax) from the
  * previous step's maximum fluid speed.  Asynchronous on the context stream;

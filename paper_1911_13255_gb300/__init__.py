@@ -85,6 +85,7 @@ _SIGS = {
     "sphfsi_finalize": (C.c_int, [_vp]),
     "sphfsi_set_substeps": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_set_time_stepping": (C.c_int, [_vp, C.c_int32]),
+    "sphfsi_set_advection_cadence": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_step": (C.c_int, [_vp, C.c_double]),
     "sphfsi_run": (C.c_int, [_vp, C.c_int64, C.c_double]),
     "sphfsi_sync": (C.c_int, [_vp]),
@@ -356,6 +357,10 @@ class Simulation:
         K = 1) or "single_solid" (min(dt_ac, dt_S), K = 1)."""
         m = self.TIME_STEPPING[mode] if isinstance(mode, str) else int(mode)
         _check(lib().sphfsi_set_time_stepping(self.h, m), "sphfsi_set_time_stepping")
+
+    def set_advection_cadence(self, n):
+        """Hold the pair configuration over n coarse steps (Algorithm 1); n <= 1 rebuilds it every step."""
+        _check(lib().sphfsi_set_advection_cadence(self.h, int(n)), "sphfsi_set_advection_cadence")
 
     def step(self, dt=0.0):
         _check(lib().sphfsi_step(self.h, float(dt)), "sphfsi_step")

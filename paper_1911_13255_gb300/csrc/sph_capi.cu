@@ -210,12 +210,18 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_density(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 6));
     if (c->S.n) TRY(cuda_rc(cudaStreamWaitEvent(st, c->join_ev, 0)));
-    TRY(launch_finish(c->bt, c->S.learned, c->F.gbar, st));
+    TRY(launch_finish(c->bt, c->S.learned, c->F.gbar, c->F, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
     c->kernels_per_step = 4 + bin_kernels(c->F) + (c->S.n ? 2 : 0) +
                           (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
     return cuda_rc(cudaGetLastError());
+}
+
+// the next step rebuilds the held pair configuration (after a state change)
+int request_rebuild(sphfsi_ctx *c)
+{
+    return cuda_rc(cudaMemsetAsync(c->F.held, 0xff, sizeof(int), c->st));
 }
 
 int check_ctx(sphfsi_ctx *c, bool need_final)
@@ -745,6 +751,10 @@ int sphfsi_finalize(sphfsi_ctx *c)
     }
     TRY(dalloc(c, &F.bsum, 4096));
     TRY(dalloc(c, &F.gbar, 2));
+    // held pair configuration: off (rebuilt every step); the first step builds it
+    F.held_n = 1;
+    TRY(dalloc(c, &F.held, 2));
+    TRY(upload(c, F.held, std::vector<int>{1, 0}));
     // ---- walls
     Walls &W = c->W;
     W.n = (int)nw;
@@ -978,6 +988,18 @@ int sphfsi_set_time_stepping(sphfsi_ctx *c, int32_t mode)
     return SPHFSI_OK;
 }
 
+int sphfsi_set_advection_cadence(sphfsi_ctx *c, int32_t n)
+{
+    TRY(check_ctx(c, true));
+    if (n < 0) return SPHFSI_E_INVAL;
+    c->F.held_n = n < 1 ? 1 : n;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return request_rebuild(c);
+}
+
 int sphfsi_step(sphfsi_ctx *c, double dt_F)
 {
     TRY(check_ctx(c, true));
@@ -1177,6 +1199,7 @@ int sphfsi_get_solid_positions_all(sphfsi_ctx *c, double *r)
 int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, const double *rho, const double *drho_dt)
 {
     TRY(check_ctx(c, true));
+    TRY(request_rebuild(c));
     const int D = c->dim;
     const InstHost &h = c->ih[c->sel];
     const int64_t n = h.nf, f0 = h.d.f0;
@@ -1253,6 +1276,7 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
                            const double *abar, const double *nrm)
 {
     TRY(check_ctx(c, true));
+    TRY(request_rebuild(c));
     const int D = c->dim;
     const InstHost &h = c->ih[c->sel];
     const int64_t n = h.ns, s0 = h.d.s0;
@@ -1316,6 +1340,7 @@ int sphfsi_set_solid_state(sphfsi_ctx *c, const double *r, const double *v, cons
 int sphfsi_set_time(sphfsi_ctx *c, double t, int64_t step)
 {
     TRY(check_ctx(c, true));
+    TRY(request_rebuild(c));
     TRY(cuda_rc(cudaStreamSynchronize(c->st)));
     Ctl hc;
     Ctl *dc = c->ctl + c->sel;
@@ -1474,6 +1499,7 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
 {
     TRY(check_ctx(c, true));
     if (which < 0 || which > 3 || !nnz) return SPHFSI_E_INVAL;
+    if (c->F.held_n > 1) return SPHFSI_E_STATE;   // binning here would replace the held configuration
     const InstHost &h = c->ih[c->sel];
     const int64_t nrows = which == 3 ? h.ns : h.nf;
     // bin the current positions (no drift) and build the solid records

@@ -186,6 +186,16 @@ struct Fluid {
     int bin_fused;      // 1: binning as one cooperative kernel with grid barriers (small problems)
     int *bsum;          // its per-block partial sums (kBinFusedMaxBlocks)
     unsigned *gbar;     // its grid barrier: [0] arrivals, [1] generation
+    // Held pair configuration (Algorithm 1: the neighbour lists and the kernel
+    // values and gradients are updated once per advection step).  With
+    // held_n > 1 the binning (sort, cell lists, record positions) runs only on
+    // rebuild steps; on the other steps the particles keep their slots and
+    // the records keep the positions of the last rebuild, so every pair term
+    // takes W and grad W at those positions, while pressures, densities and
+    // velocities are refreshed (k_held_records).
+    int held_n;         // coarse steps per advection step; <= 1: rebuilt every step
+    int *held;          // [0] != 0: rebuild at the next step (set by the host's state setters),
+                        // [1]: the last finished step rebuilt the configuration
 };
 
 // Static walls, binned once.
@@ -259,6 +269,15 @@ struct Batch {
     int B;
     int ncell;                    // total cells
 };
+
+// Does this step rebuild the pair configuration?  Every kernel of a step
+// evaluates the same inputs (instance 0's step index, which the finish kernel
+// advances, and the host's rebuild request, which it clears), so they agree.
+// All instances of a context rebuild together.
+__device__ __forceinline__ bool rebuild_step(const Batch &bt, const Fluid &f)
+{
+    return f.held_n <= 1 || f.held[0] != 0 || bt.ctl[0].step % f.held_n == 0;
+}
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -377,7 +396,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
 int bin_kernels(const Fluid &f);
 int scan_tile_cells();
 int launch_wall_bin(const Batch &bt, Walls &w, int dim, cudaStream_t st);
-int launch_finish(const Batch &bt, int learned, unsigned *gbar, cudaStream_t st);
+int launch_finish(const Batch &bt, int learned, unsigned *gbar, const Fluid &f, cudaStream_t st);
 int launch_scan(int *ccount, int *cstart, int ncell, cudaStream_t st);
 int launch_scatter(const int *key, const int *cstart, int *ccount, int *perm, int n, cudaStream_t st);
 

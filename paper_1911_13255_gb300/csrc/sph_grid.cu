@@ -117,11 +117,16 @@ __device__ void update_normal(const Solid &s, int a)
 
 // finish: time, step, pair counters, non-finite check, maxima for the next
 // step's control (one thread per instance)
-__global__ void k_finish(Batch bt, int learned, unsigned *gbar)
+__global__ void k_finish(Batch bt, int learned, unsigned *gbar, Fluid f)
 {
     pdl_enter();
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0 && gbar) gbar[0] = 0u;   // the fused binning's barrier, even after a time-out
+    if (b == 0 && f.held) {
+        // before instance 0's step index advances (below, same thread)
+        f.held[1] = rebuild_step(bt, f) ? 1 : 0;
+        f.held[0] = 0;
+    }
     if (b >= bt.B) return;
     Ctl *ctl = bt.ctl + b;
     float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
@@ -149,9 +154,9 @@ __global__ void k_finish(Batch bt, int learned, unsigned *gbar)
     ctl->step += 1;
 }
 
-int launch_finish(const Batch &bt, int learned, unsigned *gbar, cudaStream_t st)
+int launch_finish(const Batch &bt, int learned, unsigned *gbar, const Fluid &f, cudaStream_t st)
 {
-    launch_k(k_finish, (bt.B + kBlock - 1) / kBlock, kBlock, 0, st, bt, learned, gbar);
+    launch_k(k_finish, (bt.B + kBlock - 1) / kBlock, kBlock, 0, st, bt, learned, gbar, f);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -201,6 +206,9 @@ template <int D>
 __device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const Solid &s, int t, int step,
                                         double dt_fixed, int K_fixed)
 {
+    // held configuration: no keys or histograms between rebuilds (the slots,
+    // cell lists and record positions of the last rebuild stay)
+    const bool rebuild = rebuild_step(bt, f);
     if (t < f.n) {
         const int i = t;
         const int b = f.inst[i];
@@ -234,6 +242,7 @@ __device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const S
             S.y[i] = y;
             if (D == 3) S.z[i] = z;
         }
+        if (!rebuild) return;
         int key = global_key<D>(In, x, y, z);
         f.key[i] = key;
         atomicAdd(&f.ccount[key], 1);
@@ -241,6 +250,7 @@ __device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const S
         const int a = t - f.n;
         const int b = s.inst[a];
         if (step && step_reinit(bt.ctl + b)) update_normal<D>(s, a);
+        if (!rebuild) return;
         int key = global_key<D>(bt.I[b], s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0);
         s.key[a] = key;
         atomicAdd(&s.ccount[key], 1);
@@ -373,6 +383,7 @@ __device__ __forceinline__ unsigned long long scan_word(unsigned epoch, unsigned
 __global__ void __launch_bounds__(kScanLbThreads) k_scan_lb(Batch bt, Fluid f, Solid s)
 {
     pdl_enter();
+    if (!rebuild_step(bt, f)) return;   // held configuration: cell starts stay
     __shared__ int s_tile, s_pre, s_warp[kScanLbThreads / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t == 0) s_tile = (int)atomicAdd(&f.scan_ctl[0], 1u);
@@ -485,9 +496,10 @@ __device__ __forceinline__ void scatter_one(const Fluid &f, const Solid &s, int 
     if (opened >= 0) f.live[base + __popc(m & ((1u << lane) - 1u))] = opened;
 }
 
-__global__ void k_scatter2(Fluid f, Solid s, int ncell, int list_cells)
+__global__ void k_scatter2(Batch bt, Fluid f, Solid s, int ncell, int list_cells)
 {
     pdl_enter();
+    if (!rebuild_step(bt, f)) return;
     scatter_one(f, s, blockIdx.x * blockDim.x + threadIdx.x, ncell, list_cells);
 }
 
@@ -575,7 +587,9 @@ __device__ __forceinline__ void fluid_put(const Batch &bt, const Fluid &f, int k
     B.rhodot[k] = v.rd;
     B.id[k] = v.id;
     f.cell_of[k] = v.key;
-    const bool reinit = bt.ctl[v.b].reinit;
+    // the double-float remainders serve the reinitialisation; with a held
+    // configuration a later step of the advection step may reinitialise
+    const bool reinit = bt.ctl[v.b].reinit || f.held_n > 1;
     float4 lo;
     float4 r = rel_pos<D>(In, v.key, v.x, v.y, v.z, reinit ? &lo : nullptr);
     if (reinit) f.L4[k] = lo;
@@ -593,12 +607,12 @@ __device__ __forceinline__ void fluid_record(const Batch &bt, const Fluid &f, in
 // Record of solid slot k of the fluid grid from solid particle a (N4.w
 // carries a).
 template <int D>
-__device__ __forceinline__ void solid_record(const Batch &bt, const Solid &s, int k, int a)
+__device__ __forceinline__ void solid_record(const Batch &bt, const Solid &s, int k, int a, bool held)
 {
     int key = s.key[a];
     s.cell_of[k] = key;
     const int b = s.inst[a];
-    const bool reinit = bt.ctl[b].reinit;
+    const bool reinit = bt.ctl[b].reinit || held;
     float4 lo;
     s.A4[k] = rel_pos<D>(bt.I[b], key, s.x[a], s.y[a], D == 3 ? s.z[a] : 0.0, reinit ? &lo : nullptr);
     if (reinit) s.L4[k] = lo;
@@ -668,7 +682,7 @@ __device__ __forceinline__ void rank_cell(const Batch &bt, const Fluid &f, const
         if (mine) {
             if (!REC) (fl ? f.sperm : s.sperm)[a + rank] = v;
             else if (fl) fluid_put<D>(bt, f, a + rank, src);
-            else solid_record<D>(bt, s, a + rank, v);
+            else solid_record<D>(bt, s, a + rank, v, f.held_n > 1);
         }
     }
 }
@@ -677,6 +691,7 @@ template <int D, int G, bool REC>
 __global__ void __launch_bounds__(256) k_cell_records(Batch bt, Fluid f, Solid s, int listed, int ncells)
 {
     pdl_enter();
+    if (!rebuild_step(bt, f)) return;   // held configuration: k_held_records refreshes the records
     const int nlive = listed ? *f.nlive : ncells;
     const int lane = threadIdx.x % G;
     const int per_grid = gridDim.x * (blockDim.x / G);
@@ -691,9 +706,48 @@ template <int D>
 __global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
 {
     pdl_enter();
+    if (!rebuild_step(bt, f)) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < f.n) fluid_record<D>(bt, f, t, f.sperm[t]);
-    else if (t < f.n + s.n) solid_record<D>(bt, s, t - f.n, s.sperm[t - f.n]);
+    else if (t < f.n + s.n) solid_record<D>(bt, s, t - f.n, s.sperm[t - f.n], f.held_n > 1);
+}
+
+// Held configuration, steps between rebuilds: every slot keeps its particle
+// and its record keeps the position of the last rebuild (the pair geometry);
+// the mid-step copy of the state and the records' pressure, velocity and
+// density (fluid) and time-averaged velocity, acceleration and normal (solid
+// records) are refreshed in place.
+template <int D>
+__global__ void k_held_records(Batch bt, Fluid f, Solid s)
+{
+    pdl_enter();
+    if (rebuild_step(bt, f)) return;   // the binning wrote every record
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < f.n) {
+        const FluidState A = f.s[0], B = f.s[1];
+        const Phys &P = bt.I[f.inst[t]].P;
+        const float vx = A.vx[t], vy = A.vy[t], vz = D == 3 ? A.vz[t] : 0.0f, dr = A.drho[t];
+        B.x[t] = A.x[t];
+        B.y[t] = A.y[t];
+        B.vx[t] = vx;
+        B.vy[t] = vy;
+        if (D == 3) {
+            B.z[t] = A.z[t];
+            B.vz[t] = vz;
+        }
+        B.drho[t] = dr;
+        B.rhodot[t] = A.rhodot[t];
+        B.id[t] = A.id[t];
+        f.P4[t].w = eos_p(dr, P);
+        f.V4[t] = make_float4(vx, vy, vz, dr);
+    } else if (t < f.n + s.n) {
+        const int k = t - f.n;
+        const float4 n4 = s.N4[k];
+        const int a = __float_as_int(n4.w);
+        s.VB4[k] = make_float4((float)s.vbar[3 * a], (float)s.vbar[3 * a + 1], (float)s.vbar[3 * a + 2], 0.0f);
+        s.AB4[k] = make_float4((float)s.abar[3 * a], (float)s.abar[3 * a + 1], (float)s.abar[3 * a + 2], 0.0f);
+        s.N4[k] = make_float4(s.nrm[3 * a], s.nrm[3 * a + 1], s.nrm[3 * a + 2], n4.w);
+    }
 }
 
 constexpr int kRecordBlocksPerSM = 64;
@@ -844,7 +898,11 @@ static int launch_bin_fused(K kern, int nb, cudaStream_t st, const Batch &bt, co
 }
 
 // kernels launch_bin_all launches in a step with particles
-int bin_kernels(const Fluid &f) { return f.bin_fused ? 1 : (f.split_records ? 5 : 4); }
+int bin_kernels(const Fluid &f)
+{
+    if (f.held_n > 1) return (f.split_records ? 5 : 4) + 1;
+    return f.bin_fused ? 1 : (f.split_records ? 5 : 4);
+}
 
 int scan_tile_cells() { return kScanTile; }
 
@@ -854,7 +912,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
     const int np = f.n + s.n;
     const int nt = np + (step ? bt.B : 0);
     if (nt == 0) return 0;
-    if (f.bin_fused && np > 0) {
+    if (f.bin_fused && np > 0 && f.held_n <= 1) {
         auto kern = dim == 2 ? k_bin_fused<2, 16> : k_bin_fused<3, 32>;
         const int nb = bin_fused_blocks(kern, dim);
         if (nb > 0) return launch_bin_fused(kern, nb, st, bt, f, s, step, dt_fixed, K_fixed);
@@ -872,7 +930,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
     // only (large problems): over all cells, no list (its counter would
     // serialise one atomic per warp)
     const bool split = f.split_records != 0;
-    launch_k(k_scatter2, (np + kBlock - 1) / kBlock, kBlock, 0, st, f, s, bt.ncell, split ? 0 : 1);
+    launch_k(k_scatter2, (np + kBlock - 1) / kBlock, kBlock, 0, st, bt, f, s, bt.ncell, split ? 0 : 1);
     const long long cells_all = (long long)(s.n ? 2 : 1) * bt.ncell;
     const long long cells = split ? cells_all : (cells_all < np ? cells_all : np);
     const long long cap = (long long)kRecordBlocksPerSM * 152;
@@ -895,6 +953,10 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
         } else {
             launch_k(k_cell_records<3, 32, true>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
         }
+    }
+    if (f.held_n > 1) {
+        if (dim == 2) launch_k(k_held_records<2>, nbr, kBlock, 0, st, bt, f, s);
+        else launch_k(k_held_records<3>, nbr, kBlock, 0, st, bt, f, s);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
