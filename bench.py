@@ -225,12 +225,14 @@ def cpu_case(cases, label):
 
 
 def cpu_baseline(cases, label, budget_s=15.0, max_steps=400, time_stepping="multiple"):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample."""
+    """The FP64 oracle as it stands on a bounded sample, in its OpenMP build
+    on every host core (the same bits as the single-threaded build)."""
     import oracle
     case, which = cpu_case(cases, label)
     if label == WORKLOADS["duct_3d"]:
-        max_steps = min(max_steps, 2)   # ~375k fluid particles in 3-D: each oracle step takes tens of seconds
-    ref = oracle.OracleSim(case)
+        max_steps = min(max_steps, 3)   # ~375k fluid particles in 3-D: seconds per oracle step
+    cores = oracle.threads()
+    ref = oracle.OracleSim(case, threaded=True)
     dt, _, dts = ref.suggest_dt(vmax_f=0.0)
     K = ref.substeps(dt, dts)
     if time_stepping != "multiple":
@@ -244,9 +246,10 @@ def cpu_baseline(cases, label, budget_s=15.0, max_steps=400, time_stepping="mult
         pairs += 2 * fl + d["n_sf"] + (fl if reinit else 0) + (2 * K + 1) * d["n_ss"]
         steps += 1
     el = time.perf_counter() - t0
-    return dict(value=pairs / el, unit=UNIT, cores=1, kind="oracle",
+    return dict(value=pairs / el, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"first {steps} coarse steps of {which}the {label} workload (seed 0, dt={dt:.3e} s, "
-                       f"K={K}), FP64 C oracle, single thread, {el:.1f} s",
+                       f"K={K}), FP64 C oracle, OpenMP build on {cores} host threads (bit-identical to its "
+                       f"single-threaded build), {el:.1f} s",
                 steps=steps, seconds=el, sim_s_per_wall_s=steps * dt / el)
 
 
@@ -375,6 +378,11 @@ def run_gpu(args, rank, world, local_rank):
         work = npairs * FLOP_PER_PAIR[dom]
         bound, unit, peak = "alu", "TFLOP/s", fp32_peak_tflops(sm_mhz)
         achieved = work / (per_launch[dom] * 1e-3) / 1e12
+    elif dom == "neighbour_rows":
+        # the records read once, every row entry and count word written once
+        work = n_fluid * 16.0 + 4.0 * (sum(i["pairs_ff"] + i["pairs_fw"] for i in infos) + n_fluid)
+        bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
+        achieved = work / (per_launch[dom] * 1e-3) / 1e9
     else:
         work = n_fluid * BYTES_PER_FLUID_PARTICLE["bin_sort"]
         bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
@@ -387,6 +395,7 @@ def run_gpu(args, rank, world, local_rank):
         solid_kernel = {1: "k_solid_cluster2d_one" if two_d else "k_solid_cluster_one",
                         2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
+                    "neighbour_rows": "k_pairlist",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
                     "bin_sort": "k_bin_all+k_scan_seg+k_scatter2+k_cell_records"}
     extra = {}
@@ -418,7 +427,8 @@ def run_gpu(args, rank, world, local_rank):
                    "dp_F": case.f_dp, "dp_S": case.s_dp,
                    "K_last": [i["last_K"] for i in infos] if len(cases) > 1 else K,
                    "dt_last": info1["last_dt"] if len(cases) == 1 else "per instance",
-                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows")},
+                   "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows",
+                                                     "list", "list_lanes")},
                    "cell_reach": case.cell_reach, "time_stepping": args.time_stepping,
                    "autotuned": args.workload != "dam_gate" and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
@@ -858,7 +868,7 @@ def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
                            c.inflow_period, c.inflow_wo)
     sim.finalize()
     sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"],
-                   tuning["records"], tuning["rows"])
+                   tuning["records"], tuning["rows"], tuning["list"], tuning["list_lanes"])
     sim.set_time_stepping(time_stepping)
     p0 = sim.pairs_total()
     for _ in range(steps):

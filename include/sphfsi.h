@@ -224,8 +224,21 @@ int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F);
 
 /* Wait for the stream; return SPHFSI_E_UNSTABLE / SPHFSI_E_TIMEOUT if the
  * device flagged a non-finite state or a bounded wait ran out in any
- * instance. */
+ * instance.  After SPHFSI_E_TIMEOUT the state is not a valid step of the
+ * method (the step that gave up was not completed, and when the cell-list
+ * scan gave up, that step's and later steps' kernels returned without
+ * work): sphfsi_step and sphfsi_run return SPHFSI_E_TIMEOUT without doing
+ * anything until sphfsi_set_state restores a checkpoint taken before. */
 int sphfsi_sync(sphfsi_ctx *c);
+
+/* Bounded device waits (no counterpart in the paper): the grid barrier of the
+ * cooperative sub-step kernel and the decoupled look-back of the cell-list
+ * scan give up after this many polling iterations, set SPHFSI_E_TIMEOUT and
+ * return, so a stalled wait never hangs the device.  0 restores the default
+ * (2^22 iterations, about 0.5 to 2 s); a small value makes waits give up
+ * almost at once (for checking how a time-out is reported).  Applies to the
+ * steps issued after the call.  SPHFSI_E_INVAL for a negative value. */
+int sphfsi_set_wait_limit(sphfsi_ctx *c, int64_t iterations);
 
 /* Fluid state in original order: r (n x dim FP64), v (n x dim FP32),
  * rho (n FP64: rho0 plus the FP32 deviation the library stores), drho_dt
@@ -297,13 +310,14 @@ int sphfsi_set_solid_path(sphfsi_ctx *c, int path);
 /* Per-stage device timing.  With on != 0 every later step records CUDA
  * events on the context stream at its stage boundaries (also inside the
  * captured graph of sphfsi_run).  sphfsi_stage_times waits for the stream
- * and writes the durations in ms of the last step's 7 stages into ms[0..6]:
+ * and writes the durations in ms of the last step's 8 stages into ms[0..7]:
  * 0 step control, normal update, fluid drift, fluid and solid binning, sort
  * and records, 1 density reinitialisation, 2 momentum (a4), 3 solid-side
  * coupling force (a5), 4 continuity + drift (a6), 5 solid sub-steps (a7,
- * a8), 6 finish.  Stages 3 and 5 run on a side stream concurrently with
- * stages 2 and 4; finish follows the join of both streams.
- * Returns the number of stages, SPHFSI_E_INVAL if n < 7, SPHFSI_E_STATE if
+ * a8), 6 finish, 7 neighbour rows (sphfsi_tuning.list; 0 without).  Stages 3
+ * and 5 run on a side stream concurrently with stages 2 and 4; finish
+ * follows the join of both streams.
+ * Returns the number of stages, SPHFSI_E_INVAL if n < 8, SPHFSI_E_STATE if
  * profiling is off. */
 int sphfsi_set_profiling(sphfsi_ctx *c, int on);
 int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n);
@@ -352,6 +366,15 @@ typedef struct {
                               (fluid, walls, solid) loaded together: fewer dependent loads, a few
                               more instructions per candidate (default 1 below 262 144 particles
                               in the context, else 0) */
+    int32_t list;          /* fluid pair loops: 0 test the candidates of the neighbour cells in
+                              every loop; 1 test them once per rebuild of the pair configuration,
+                              keeping each fluid particle's in-support fluid and wall neighbours in
+                              a row (at most 64 in 2-D, 128 in 3-D; a fuller row falls back to the
+                              cell visit for that particle), and stream the rows in momentum,
+                              continuity and reinitialisation; not with tiles or cell_reach 2
+                              (default 0) */
+    int32_t list_lanes;    /* threads per fluid particle of the row build: 8, 16 or 32 (default 16
+                              in 2-D, 32 in 3-D; 0 keeps the current value) */
 } sphfsi_tuning;
 
 /* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */
@@ -362,7 +385,9 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t);
  * workload: for each candidate setting, `steps` graph-replayed steps of size
  * dt_F (as sphfsi_run) to warm up, then `steps` timed with CUDA events.  The
  * search goes over the lane count (block 128), then the pair-loop form,
- * then tiles on or off, then the row form, then the block size, then the
+ * then neighbour rows on or off (with rows: the row build's lane count),
+ * then (without rows) tiles on or off and the row form, then the block
+ * size, then the
  * records form, then (2-D with a solid) the solid kernel variant, keeping the
  * fastest of each.
  * Every device allocation of the context is saved before and restored after

@@ -21,20 +21,29 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sph_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libsph_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libsph_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
+
+
+def _build_one(path, extra, force):
+    if force or not os.path.exists(path) or os.path.getmtime(path) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sph_oracle.h"))):
+        tmp = path + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"] + extra +
+                              ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, FP64, -ffp-contract=off)."""
+    """Compile the oracle with gcc (-O2, FP64, -ffp-contract=off): the plain
+    single-threaded library and the OpenMP build of the same source that the
+    benchmark times on all host cores."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sph_oracle.h"))):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    _build_one(_LIB_OMP, ["-fopenmp"], force)
+    return _build_one(_LIB, [], force)
 
 
 class Params(C.Structure):
@@ -81,63 +90,80 @@ class Diag(C.Structure):
                     mom_fs_solid=np.array(self.mom_fs_solid[:]), abs_fs=self.abs_fs)
 
 
-def lib():
-    global _lib
+def lib(threaded=False):
+    """The oracle library; threaded=True: its OpenMP build (same bits)."""
+    global _lib, _lib_omp
     with _lock:
+        if threaded:
+            if _lib_omp is None:
+                build()
+                _lib_omp = _declare(C.CDLL(_LIB_OMP))
+            return _lib_omp
         if _lib is None:
-            L = C.CDLL(build())
-            L.or_kernel_W.restype = C.c_double
-            L.or_kernel_W.argtypes = [C.c_int, C.c_double, C.c_double]
-            L.or_kernel_dW.restype = C.c_double
-            L.or_kernel_dW.argtypes = [C.c_int, C.c_double, C.c_double]
-            L.or_lattice_sigma0.restype = C.c_double
-            L.or_lattice_sigma0.argtypes = [C.c_int, C.c_double, C.c_double]
-            L.or_eos_p.restype = C.c_double
-            L.or_eos_p.argtypes = [C.c_double] * 3
-            L.or_eos_rho.restype = C.c_double
-            L.or_eos_rho.argtypes = [C.c_double] * 3
-            L.or_riemann.restype = C.c_double
-            L.or_riemann.argtypes = [C.c_int, _dp, _dp, _dp] + [C.c_double] * 5 + [_dp]
-            L.or_neo_hookean_P.restype = None
-            L.or_neo_hookean_P.argtypes = [C.c_int, _dp, C.c_double, C.c_double, _dp]
-            L.or_solid_sound_speed.restype = C.c_double
-            L.or_solid_sound_speed.argtypes = [C.c_double] * 3
-            L.or_pairs_count.restype = C.c_int64
-            L.or_pairs_count.argtypes = [C.POINTER(Params), C.c_int, _dp, C.c_int64, _dp, C.c_int64,
-                                         C.c_double, C.c_int, C.c_int]
-            L.or_pairs_fill.restype = C.c_int
-            L.or_pairs_fill.argtypes = [C.POINTER(Params), C.c_int, _dp, C.c_int64, _dp, C.c_int64,
-                                        C.c_double, C.c_int, C.c_int, _i64p, _i64p]
-            L.or_solid_count.restype = C.c_int64
-            L.or_solid_count.argtypes = [C.POINTER(Params), C.POINTER(Solid)]
-            L.or_solid_setup.restype = C.c_int
-            L.or_solid_setup.argtypes = [C.POINTER(Params), C.POINTER(Solid)]
-            L.or_solid_F_from_positions.restype = C.c_int
-            L.or_solid_F_from_positions.argtypes = [C.POINTER(Params), C.POINTER(Solid), _dp]
-            L.or_solid_accel.restype = C.c_int
-            L.or_solid_accel.argtypes = [C.POINTER(Params), C.POINTER(Solid), _dp, _dp]
-            L.or_inflow_u.restype = C.c_double
-            L.or_inflow_u.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
-            L.or_step.restype = C.c_int
-            L.or_step.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Wall),
-                                  C.POINTER(Solid), C.c_double, C.c_int, C.c_double, C.c_int64,
-                                  C.POINTER(Diag)]
-            L.or_step_ex.restype = C.c_int
-            L.or_step_ex.argtypes = L.or_step.argtypes + [C.POINTER(Cache)]
-            L.or_cache_free.restype = None
-            L.or_cache_free.argtypes = [C.POINTER(Cache)]
-            L.or_suggest_dt.restype = None
-            L.or_suggest_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid),
-                                        C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
-            L.or_substeps.restype = C.c_int
-            L.or_substeps.argtypes = [C.c_double, C.c_double]
-            L.or_single_dt.restype = C.c_double
-            L.or_single_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid), C.c_int,
-                                       C.c_double, C.c_double, C.c_double]
-            L.or_eos_rho_array.restype = None
-            L.or_eos_rho_array.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_double]
-            _lib = L
+            _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def threads():
+    """Threads the OpenMP build of the oracle runs its loops on."""
+    return lib(threaded=True).or_threads()
+
+
+def _declare(L):
+    """Argument and result types of the oracle's entry points."""
+    L.or_kernel_W.restype = C.c_double
+    L.or_kernel_W.argtypes = [C.c_int, C.c_double, C.c_double]
+    L.or_kernel_dW.restype = C.c_double
+    L.or_kernel_dW.argtypes = [C.c_int, C.c_double, C.c_double]
+    L.or_lattice_sigma0.restype = C.c_double
+    L.or_lattice_sigma0.argtypes = [C.c_int, C.c_double, C.c_double]
+    L.or_eos_p.restype = C.c_double
+    L.or_eos_p.argtypes = [C.c_double] * 3
+    L.or_eos_rho.restype = C.c_double
+    L.or_eos_rho.argtypes = [C.c_double] * 3
+    L.or_riemann.restype = C.c_double
+    L.or_riemann.argtypes = [C.c_int, _dp, _dp, _dp] + [C.c_double] * 5 + [_dp]
+    L.or_neo_hookean_P.restype = None
+    L.or_neo_hookean_P.argtypes = [C.c_int, _dp, C.c_double, C.c_double, _dp]
+    L.or_solid_sound_speed.restype = C.c_double
+    L.or_solid_sound_speed.argtypes = [C.c_double] * 3
+    L.or_pairs_count.restype = C.c_int64
+    L.or_pairs_count.argtypes = [C.POINTER(Params), C.c_int, _dp, C.c_int64, _dp, C.c_int64,
+                                 C.c_double, C.c_int, C.c_int]
+    L.or_pairs_fill.restype = C.c_int
+    L.or_pairs_fill.argtypes = [C.POINTER(Params), C.c_int, _dp, C.c_int64, _dp, C.c_int64,
+                                C.c_double, C.c_int, C.c_int, _i64p, _i64p]
+    L.or_solid_count.restype = C.c_int64
+    L.or_solid_count.argtypes = [C.POINTER(Params), C.POINTER(Solid)]
+    L.or_solid_setup.restype = C.c_int
+    L.or_solid_setup.argtypes = [C.POINTER(Params), C.POINTER(Solid)]
+    L.or_solid_F_from_positions.restype = C.c_int
+    L.or_solid_F_from_positions.argtypes = [C.POINTER(Params), C.POINTER(Solid), _dp]
+    L.or_solid_accel.restype = C.c_int
+    L.or_solid_accel.argtypes = [C.POINTER(Params), C.POINTER(Solid), _dp, _dp]
+    L.or_inflow_u.restype = C.c_double
+    L.or_inflow_u.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
+    L.or_step.restype = C.c_int
+    L.or_step.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Wall),
+                          C.POINTER(Solid), C.c_double, C.c_int, C.c_double, C.c_int64,
+                          C.POINTER(Diag)]
+    L.or_step_ex.restype = C.c_int
+    L.or_step_ex.argtypes = L.or_step.argtypes + [C.POINTER(Cache)]
+    L.or_cache_free.restype = None
+    L.or_cache_free.argtypes = [C.POINTER(Cache)]
+    L.or_suggest_dt.restype = None
+    L.or_suggest_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid),
+                                C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
+    L.or_substeps.restype = C.c_int
+    L.or_substeps.argtypes = [C.c_double, C.c_double]
+    L.or_single_dt.restype = C.c_double
+    L.or_single_dt.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Solid), C.c_int,
+                               C.c_double, C.c_double, C.c_double]
+    L.or_eos_rho_array.restype = None
+    L.or_eos_rho_array.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_double]
+    L.or_threads.restype = C.c_int
+    L.or_threads.argtypes = []
+    return L
 
 
 def _p(a):
@@ -228,10 +254,11 @@ class Cache(C.Structure):
 
 
 class OracleSim:
-    """The oracle's simulation state for one Case (all FP64, original order)."""
+    """The oracle's simulation state for one Case (all FP64, original order).
+    threaded=True steps with the OpenMP build (the same bits, many cores)."""
 
-    def __init__(self, case):
-        L = lib()
+    def __init__(self, case, threaded=False):
+        L = self._L = lib(threaded)
         self.case = case
         d = case.dim
         self.dim = d
@@ -298,12 +325,12 @@ class OracleSim:
         if amax_s is None:
             amax_s = 0.0
         a, b, c = C.c_double(), C.c_double(), C.c_double()
-        lib().or_suggest_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), vmax_f, vmax_s, amax_s,
+        self._L.or_suggest_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), vmax_f, vmax_s, amax_s,
                             C.byref(a), C.byref(b), C.byref(c))
         return a.value, b.value, c.value
 
     def substeps(self, dt_f, dt_s):
-        return lib().or_substeps(dt_f, dt_s)
+        return self._L.or_substeps(dt_f, dt_s)
 
     def single_dt(self, mode=1, vmax_f=None, vmax_s=None, amax_s=None):
         """Step of the single-time-step baselines (K = 1): mode 1 the
@@ -314,7 +341,7 @@ class OracleSim:
             vmax_s = float(np.sqrt((self.s_v ** 2).sum(1)).max()) if self.case.ns else 0.0
         if amax_s is None:
             amax_s = 0.0
-        return lib().or_single_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), int(mode), vmax_f, vmax_s,
+        return self._L.or_single_dt(C.byref(self.P), C.byref(self.F), C.byref(self.S), int(mode), vmax_f, vmax_s,
                                   amax_s)
 
     def set_advection_cadence(self, n):
@@ -322,13 +349,13 @@ class OracleSim:
         once every n steps (an advection step of n acoustic steps) and held
         over them; n = 0 rebuilds them every step (R15)."""
         if getattr(self, "cache", None) is not None:
-            lib().or_cache_free(C.byref(self.cache))
+            self._L.or_cache_free(C.byref(self.cache))
         self.cadence = int(n)
         self.cache = Cache() if n > 0 else None
 
     def __del__(self):
-        if getattr(self, "cache", None) is not None and _lib is not None:
-            _lib.or_cache_free(C.byref(self.cache))
+        if getattr(self, "cache", None) is not None and getattr(self, "_L", None) is not None:
+            self._L.or_cache_free(C.byref(self.cache))
             self.cache = None
 
     def step(self, dt, K):
@@ -336,10 +363,10 @@ class OracleSim:
         if cache is not None:
             if self.step_index % self.cadence == 0:
                 cache.valid = 0
-            rc = lib().or_step_ex(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
+            rc = self._L.or_step_ex(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
                                   self.t, self.step_index, C.byref(self.diag), C.byref(cache))
         else:
-            rc = lib().or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
+            rc = self._L.or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
                                self.t, self.step_index, C.byref(self.diag))
         if rc != 0:
             raise RuntimeError(f"oracle step failed ({rc})")
@@ -351,13 +378,13 @@ class OracleSim:
     # --- pieces used by the pins
     def F_from_positions(self):
         out = np.zeros_like(self.s_F)
-        lib().or_solid_F_from_positions(C.byref(self.P), C.byref(self.S), _p(out))
+        self._L.or_solid_F_from_positions(C.byref(self.P), C.byref(self.S), _p(out))
         return out
 
     def solid_accel(self, F=None):
         F = self.s_F if F is None else _c(F).reshape(self.s_F.shape)
         out = np.zeros_like(self.s_r)
-        lib().or_solid_accel(C.byref(self.P), C.byref(self.S), _p(F), _p(out))
+        self._L.or_solid_accel(C.byref(self.P), C.byref(self.S), _p(F), _p(out))
         return out
 
     def set_solid_positions(self, r):

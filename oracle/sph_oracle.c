@@ -8,9 +8,12 @@
  * smoke check and the benchmark's CPU-baseline leg may load it; the product
  * path never does.  It shares no code with the CUDA library.
  *
- * Everything is double precision, single threaded, compiled without FMA
- * contraction (-ffp-contract=off) so that the in-support test
- * r^2 = dx*dx + dy*dy (+ dz*dz) < (2h)^2 is bit-reproducible.
+ * Everything is double precision, compiled without FMA contraction
+ * (-ffp-contract=off) so that the in-support test r^2 = dx*dx + dy*dy
+ * (+ dz*dz) < (2h)^2 is bit-reproducible.  The plain build is single
+ * threaded; an OpenMP build of the same source, used only to time the
+ * oracle on all host cores, splits the independent per-particle loops over
+ * threads and gives the same bits (or_threads).
  *
  * Where the paper is silent or garbled a written reading is used; each is
  * named R1..R24 in the comments and listed in the design notes:
@@ -54,6 +57,9 @@
 #include <string.h>
 
 #include "sph_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PI 3.14159265358979323846
 
@@ -106,6 +112,20 @@ double or_lattice_sigma0(int dim, double dp, double h)
 /* Tait equation of state (Eq. eqeos) and its inverse for the ghost density */
 /* (Section 2.2, below Eq. fs-coupling), gamma = 7.                          */
 /* ------------------------------------------------------------------------ */
+/* Threads the loops below may use: the OpenMP build (used only to time the
+ * oracle on many cores) runs its independent per-particle loops in
+ * parallel, each particle's arithmetic and every reduction's order
+ * unchanged, so both builds give the same bits; the plain build is single
+ * threaded. */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 double or_eos_p(double rho, double rho0, double c0)
 {
     return rho0 * c0 * c0 / 7.0 * (pow(rho / rho0, 7.0) - 1.0);
@@ -493,6 +513,7 @@ static void solid_Fdot(const or_params *Q, int dim, const or_solid *s, double hS
 {
     int dd = dim * dim;
     double g[3];
+#pragma omp parallel for schedule(static) private(g)
     for (int64_t a = 0; a < s->n; a++) {
         double M[9] = {0};
         for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
@@ -517,11 +538,13 @@ int or_solid_accel(const or_params *P, const or_solid *s, const double *F, doubl
     Q.periodic_x = 0;
     lame(s->E, s->nu, &mu, &lam);
     double *PB = (double *)malloc(sizeof(double) * dd * (s->n > 0 ? s->n : 1));
+#pragma omp parallel for schedule(static)
     for (int64_t a = 0; a < s->n; a++) {
         double Pk[9];
         or_neo_hookean_P(dim, F + a * dd, mu, lam, Pk);
         matmul_d(dim, Pk, s->B0 + a * dd, PB + a * dd);
     }
+#pragma omp parallel for schedule(static) private(g)
     for (int64_t a = 0; a < s->n; a++) {
         double f[3] = {0, 0, 0};
         for (int64_t q = s->nb_ptr[a]; q < s->nb_ptr[a + 1]; q++) {
@@ -758,6 +781,7 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
     if (P->n_reinit > 0 && step_index % P->n_reinit == 0) {
         double sigma0 = or_lattice_sigma0(dim, f->dp, hF); /* lattice number density */
         double VF = pow(f->dp, dim);
+#pragma omp parallel for schedule(dynamic, 256) private(d)
         for (int64_t i = 0; i < f->n; i++) {
             double sg = or_kernel_W(dim, 0.0, hF);
             for (int64_t q = FF.ptr[i]; q < FF.ptr[i + 1]; q++)
@@ -770,6 +794,7 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
             if (P->free_surface && rr < f->rho0) rr = f->rho0;
             f->rho[i] = rr;
         }
+#pragma omp parallel for schedule(static)
         for (int64_t a = 0; a < s->n; a++) {
             double Fi[9], n[3] = {0, 0, 0}, nn = 0.0;
             inv_d(dim, s->F + a * dd, Fi);
@@ -785,11 +810,17 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
 
     /* pressures at the mid state */
     double *p = (double *)malloc(sizeof(double) * (f->n > 0 ? f->n : 1));
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < f->n; i++) p[i] = or_eos_p(f->rho[i], f->rho0, f->c0);
 
     fluid_consts fc = {f->rho0, f->c0, f->eta, hF, 0.0};
 
-    /* a4: fluid momentum at (r^{n+1/2}, rho^{n+1/2}, v^n), Eq. fluid-model-mr-mom */
+    /* a4: fluid momentum at (r^{n+1/2}, rho^{n+1/2}, v^n), Eq. fluid-model-mr-mom.
+       Every particle's sums are its own; the momentum diagnostics of the
+       fluid-solid forces are summed per particle here and over the particles
+       in order below, so a threaded build gives the same bits. */
+    double *fs_sum = (double *)calloc((size_t)(f->n > 0 ? f->n : 1) * 4, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 256) private(d) firstprivate(fc)
     for (int64_t i = 0; i < f->n; i++) {
         const double *ri = fg + i * dim, *vi = f->v + i * dim;
         double Vi = mF / f->rho[i];
@@ -823,14 +854,20 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
                     s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
             for (int k = 0; k < dim; k++) {
                 force[k] += fo[k];
-                dg->mom_fs_fluid[k] += fo[k];
-                dg->abs_fs += fabs(fo[k]);
+                fs_sum[i * 4 + k] += fo[k];
+                fs_sum[i * 4 + 3] += fabs(fo[k]);
             }
         }
         for (int k = 0; k < dim; k++) f->dvdt[i * dim + k] = force[k] / mF + P->g[k];
     }
+    for (int64_t i = 0; i < f->n; i++) {
+        for (int k = 0; k < dim; k++) dg->mom_fs_fluid[k] += fs_sum[i * 4 + k];
+        dg->abs_fs += fs_sum[i * 4 + 3];
+    }
+    free(fs_sum);
 
     /* a5: fluid force on the solid from the same pair terms (Eqs. F:p, F:v) */
+#pragma omp parallel for schedule(dynamic, 64) firstprivate(fc)
     for (int64_t a = 0; a < s->n; a++) {
         double fa[3] = {0, 0, 0};
         for (int64_t q = SF.ptr[a]; q < SF.ptr[a + 1]; q++) {
@@ -841,11 +878,10 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
                     s->vbar + a * dim, s->abar + a * dim, s->nrm + a * dim, VS, fo, NULL, NULL);
             for (int k = 0; k < dim; k++) fa[k] -= fo[k];
         }
-        for (int k = 0; k < dim; k++) {
-            s->fF[a * dim + k] = fa[k];
-            dg->mom_fs_solid[k] += fa[k];
-        }
+        for (int k = 0; k < dim; k++) s->fF[a * dim + k] = fa[k];
     }
+    for (int64_t a = 0; a < s->n; a++)
+        for (int k = 0; k < dim; k++) dg->mom_fs_solid[k] += s->fF[a * dim + k];
 
     /* kick: v^{n+1} = v^n + dt dv/dt (Eq. verlet-first-mediate) */
     double vmaxF = 0.0;
@@ -860,6 +896,7 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
     dg->vmax_f = sqrt(vmaxF);
 
     /* a6: continuity at (r^{n+1/2}, rho^{n+1/2}, v^{n+1}), Eq. fluid-model-mr-con + R7 */
+#pragma omp parallel for schedule(dynamic, 256) private(d) firstprivate(fc)
     for (int64_t i = 0; i < f->n; i++) {
         const double *ri = fg + i * dim, *vi = f->v + i * dim;
         double rate = 0.0, e[3], vs[3];

@@ -48,6 +48,7 @@ typedef struct {
     double mom_fs_fluid[3], mom_fs_solid[3], abs_fs;
 } or_diag;
 
+int or_threads(void);
 double or_kernel_W(int dim, double r, double h);
 double or_kernel_dW(int dim, double r, double h);
 double or_lattice_sigma0(int dim, double dp, double h);

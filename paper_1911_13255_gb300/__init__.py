@@ -59,7 +59,8 @@ class Info(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("block", C.c_int32), ("solid_variant", C.c_int32), ("step_ms", C.c_float),
-                ("compact", C.c_int32), ("tile", C.c_int32), ("records", C.c_int32), ("rows", C.c_int32)]
+                ("compact", C.c_int32), ("tile", C.c_int32), ("records", C.c_int32), ("rows", C.c_int32),
+                ("list", C.c_int32), ("list_lanes", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +87,7 @@ _SIGS = {
     "sphfsi_set_substeps": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_set_time_stepping": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_set_advection_cadence": (C.c_int, [_vp, C.c_int32]),
+    "sphfsi_set_wait_limit": (C.c_int, [_vp, C.c_int64]),
     "sphfsi_step": (C.c_int, [_vp, C.c_double]),
     "sphfsi_run": (C.c_int, [_vp, C.c_int64, C.c_double]),
     "sphfsi_sync": (C.c_int, [_vp]),
@@ -298,9 +300,11 @@ class Simulation:
         _check(lib().sphfsi_autotune(self.h, float(dt), int(steps), C.byref(t)), "sphfsi_autotune")
         return t.as_dict()
 
-    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0, records=None, rows=None):
-        """Launch shape (include/sphfsi.h, sphfsi_tuning); compact, records and
-        rows default to the current setting (rows is 0 with tiles)."""
+    def set_tuning(self, lanes, block=128, solid_variant=0, compact=None, tile=0, records=None, rows=None,
+                   list=None, list_lanes=0):
+        """Launch shape (include/sphfsi.h, sphfsi_tuning); compact, records,
+        rows and list default to the current setting (rows and list are 0
+        with tiles)."""
         cur = self.tuning()
         if compact is None:
             compact = cur["compact"]
@@ -308,7 +312,10 @@ class Simulation:
             records = cur["records"]
         if rows is None:
             rows = 0 if tile else cur["rows"]
-        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact), int(tile), int(records), int(rows))
+        if list is None:
+            list = 0 if tile else cur["list"]
+        t = Tuning(int(lanes), int(block), int(solid_variant), 0.0, int(compact), int(tile), int(records), int(rows),
+                   int(list), int(list_lanes))
         _check(lib().sphfsi_set_tuning(self.h, C.byref(t)), "sphfsi_set_tuning")
 
     def tuning(self):
@@ -361,6 +368,10 @@ class Simulation:
     def set_advection_cadence(self, n):
         """Hold the pair configuration over n coarse steps (Algorithm 1); n <= 1 rebuilds it every step."""
         _check(lib().sphfsi_set_advection_cadence(self.h, int(n)), "sphfsi_set_advection_cadence")
+
+    def set_wait_limit(self, iterations):
+        """Polling iterations before a bounded device wait gives up (0: the default)."""
+        _check(lib().sphfsi_set_wait_limit(self.h, int(iterations)), "sphfsi_set_wait_limit")
 
     def step(self, dt=0.0):
         _check(lib().sphfsi_step(self.h, float(dt)), "sphfsi_step")
@@ -443,7 +454,7 @@ class Simulation:
         return i.as_dict()
 
     STAGES = ("bin_sort", "reinit", "momentum", "solid_fluid_force",
-              "continuity", "solid_substeps", "finish")
+              "continuity", "solid_substeps", "finish", "neighbour_rows")
 
     def set_solid_path(self, path):
         """0 automatic (cluster-resident when the body fits), 2 cooperative grid."""

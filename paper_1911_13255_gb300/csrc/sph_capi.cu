@@ -60,11 +60,12 @@ struct sphfsi_ctx {
     int graph_prof = -1;
     int solid_path = 0;
     int last_status = 0;
+    bool failed = false;   // a bounded wait gave up (seen at a sync): no steps until a checkpoint is restored
     // per-stage CUDA events (sphfsi_set_profiling), by index: 0 start, 2
-    // binning, 3 reinit, 5 momentum, 6 continuity (main stream); 4 branch
-    // start, 7 coupling force done, 8 sub-steps done (side stream); 9 end of
-    // step (1 is unused)
-    static constexpr int kStages = 7;
+    // binning, 1 neighbour rows, 3 reinit, 5 momentum, 6 continuity (main
+    // stream); 4 branch start, 7 coupling force done, 8 sub-steps done (side
+    // stream); 9 end of step
+    static constexpr int kStages = 8;
     static constexpr int kEvents = 10;
     bool profiling = false;
     cudaEvent_t ev[kEvents] = {};
@@ -184,6 +185,9 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     // (r^n) binning, counting sort and FP32 records
     TRY(launch_bin_all(c->bt, c->F, c->S, D, 1, dt > 0.0 ? dt : 0.0, c->K_fixed, st));
     TRY(mark(c, 2));
+    // neighbour rows of the pair loops (rebuild steps, when on)
+    TRY(launch_pairlist(c->bt, c->F, c->W, c->S, D, st));
+    TRY(mark(c, 1));
     // a3: density reinitialisation (no-op on other steps)
     TRY(launch_reinit(c->bt, c->F, c->W, c->S, D, st));
     TRY(mark(c, 3));
@@ -213,7 +217,7 @@ int enqueue_step(sphfsi_ctx *c, double dt)
     TRY(launch_finish(c->bt, c->S.learned, c->F.gbar, c->F, st));
     TRY(mark(c, 9));
     // kernels of this library per step (memsets excluded)
-    c->kernels_per_step = 4 + bin_kernels(c->F) + (c->S.n ? 2 : 0) +
+    c->kernels_per_step = 4 + bin_kernels(c->F) + (c->S.n ? 2 : 0) + (c->F.list && c->F.n ? 1 : 0) +
                           (c->S.learned ? 5 + mpnn_kernels_per_forward() : 0);
     return cuda_rc(cudaGetLastError());
 }
@@ -751,6 +755,13 @@ int sphfsi_finalize(sphfsi_ctx *c)
     }
     TRY(dalloc(c, &F.bsum, 4096));
     TRY(dalloc(c, &F.gbar, 2));
+    // neighbour rows (tuned; off by default): about 20 (2-D) or 80 (3-D)
+    // neighbours per fluid particle on a lattice, wall neighbours included
+    F.list = 0;
+    F.list_lanes = D == 2 ? 16 : 32;
+    F.list_cap = D == 2 ? 64 : 128;
+    TRY(dalloc(c, &F.nbl, (size_t)nf * F.list_cap));
+    TRY(dalloc(c, &F.nbc, nf));
     // held pair configuration: off (rebuilt every step); the first step builds it
     F.held_n = 1;
     TRY(dalloc(c, &F.held, 2));
@@ -929,6 +940,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     c->bt.ctl = c->ctl;
     c->bt.B = B;
     c->bt.ncell = (int)ncell;
+    c->bt.spin = kSpinLimit;
+    TRY(dalloc(c, &c->bt.fail, 1));
     // ---- walls binned once; solid static neighbour list and B0
     TRY(launch_wall_bin(c->bt, W, D, c->st));
     if (ns > 0) {
@@ -1004,13 +1017,27 @@ int sphfsi_step(sphfsi_ctx *c, double dt_F)
 {
     TRY(check_ctx(c, true));
     if (std::isnan(dt_F)) return SPHFSI_E_INVAL;
+    if (c->failed) return SPHFSI_E_TIMEOUT;
     return enqueue_step(c, dt_F);
+}
+
+int sphfsi_set_wait_limit(sphfsi_ctx *c, int64_t iterations)
+{
+    TRY(check_ctx(c, true));
+    if (iterations < 0) return SPHFSI_E_INVAL;
+    c->bt.spin = iterations == 0 ? kSpinLimit : (long long)iterations;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    return SPHFSI_OK;
 }
 
 int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F)
 {
     TRY(check_ctx(c, true));
     if (nsteps < 0 || std::isnan(dt_F)) return SPHFSI_E_INVAL;
+    if (c->failed) return SPHFSI_E_TIMEOUT;
     if (nsteps == 0) return SPHFSI_OK;
     if (c->st == nullptr) {
         // the legacy default stream cannot be captured: plain launches
@@ -1050,7 +1077,10 @@ int sphfsi_sync(sphfsi_ctx *c)
     int status = 0;
     for (const Ctl &x : h) status |= x.status;
     c->last_status = status;
-    if (status & ST_TIMEOUT) return SPHFSI_E_TIMEOUT;
+    if (status & ST_TIMEOUT) {
+        c->failed = true;
+        return SPHFSI_E_TIMEOUT;
+    }
     if (status & ST_NONFINITE) return SPHFSI_E_UNSTABLE;
     return SPHFSI_OK;
 }
@@ -1439,6 +1469,12 @@ int sphfsi_set_state(sphfsi_ctx *c, const void *blob, int64_t bytes)
         TRY(cuda_rc(cudaMemcpy(a.first, p, a.second, cudaMemcpyHostToDevice)));
         p += a.second;
     }
+    // steps are allowed again unless the checkpoint itself was taken after a
+    // scan that gave up
+    int fail = 0;
+    TRY(cuda_rc(cudaMemcpy(&fail, c->bt.fail, sizeof(int), cudaMemcpyDeviceToHost)));
+    c->failed = fail != 0;
+    c->last_status = 0;
     return SPHFSI_OK;
 }
 
@@ -1565,7 +1601,9 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
         t->solid_variant < 0 || t->solid_variant > 4 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
         t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile) ||
-        (c->max_reach > 1 && (t->rows || t->tile)))
+        (c->max_reach > 1 && (t->rows || t->tile)) || t->list < 0 || t->list > 1 ||
+        (t->list && (t->tile || c->max_reach > 1)) ||
+        (t->list_lanes != 0 && t->list_lanes != 8 && t->list_lanes != 16 && t->list_lanes != 32))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
@@ -1574,6 +1612,8 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
     c->F.split_records = t->records == 1 ? 1 : 0;
     c->F.bin_fused = t->records == 2 ? 1 : 0;
     c->F.rows = t->rows;
+    c->F.list = t->list;
+    if (t->list_lanes) c->F.list_lanes = t->list_lanes;
     c->S.force_lane_path = t->solid_variant;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
@@ -1593,6 +1633,8 @@ int sphfsi_get_tuning(sphfsi_ctx *c, sphfsi_tuning *t)
     t->tile = c->F.tile;
     t->records = c->F.bin_fused ? 2 : c->F.split_records;
     t->rows = c->F.rows;
+    t->list = c->F.list;
+    t->list_lanes = c->F.list_lanes;
     t->step_ms = 0.0f;
     return SPHFSI_OK;
 }
@@ -1670,12 +1712,25 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         if (!rc && c->max_reach == 1) {
+            cur.list = 1 - cur.list;
+            if (cur.list) cur.tile = 0;
+            rc = consider(cur);
+        }
+        cur = *best;
+        for (int k = 0; k < 3 && !rc && cur.list; k++) {
+            const int ll[3] = {8, 16, 32};
+            if (ll[k] == best->list_lanes) continue;
+            cur.list_lanes = ll[k];
+            rc = consider(cur);
+        }
+        cur = *best;
+        if (!rc && c->max_reach == 1 && !cur.list) {
             cur.tile = 1 - cur.tile;
             if (cur.tile) cur.rows = 0;
             rc = consider(cur);
         }
         cur = *best;
-        if (!rc && !cur.tile && c->max_reach == 1) {
+        if (!rc && !cur.tile && !cur.list && c->max_reach == 1) {
             cur.rows = 1 - cur.rows;
             rc = consider(cur);
         }
@@ -1872,7 +1927,8 @@ int sphfsi_stage_times(sphfsi_ctx *c, float *ms, int n)
     // stream); 4 branch start, 7 coupling force done, 8 sub-steps done (side
     // stream); 9 end of step
     TRY(el(0, 2, &ms[0]));
-    TRY(el(2, 3, &ms[1]));
+    TRY(el(2, 1, &ms[7]));
+    TRY(el(1, 3, &ms[1]));
     TRY(el(3, 5, &ms[2]));
     TRY(el(5, 6, &ms[4]));
     if (c->S.n) {

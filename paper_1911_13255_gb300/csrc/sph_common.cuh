@@ -58,7 +58,7 @@ static inline cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsign
 }
 constexpr int kMaxBlock = 256;        // largest block of the tunable pair-loop kernels
 constexpr int kSolidBlock = 256;      // threads per block of the cooperative solid kernel
-constexpr long long kSpinLimit = 1ll << 22;   // bounded spin of the grid barrier (~0.5-2 s)
+constexpr long long kSpinLimit = 1ll << 22;   // default bounded spin of the grid barrier and the scan (~0.5-2 s)
 
 // Fixed uniform cell grid with cell edge >= 2 h_F (support radius).  Local
 // cell index = x + nc[0] * (y + nc[1] * z); global index = c0 + local.
@@ -196,7 +196,23 @@ struct Fluid {
     int held_n;         // coarse steps per advection step; <= 1: rebuilt every step
     int *held;          // [0] != 0: rebuild at the next step (set by the host's state setters),
                         // [1]: the last finished step rebuilt the configuration
+    // Neighbour rows (Fluid::list = 1, tuned): the candidate tests of the cell
+    // visit run once per rebuild (k_pairlist) and each target's in-support
+    // fluid neighbours (from the front) and wall neighbours (from the back)
+    // are kept as entries idx << 7 | cell-offset code in row i of list_cap
+    // entries; the pair loops stream the rows.  nbc[i] = nF | nW << 11 | flags.
+    int list;
+    int list_lanes;     // threads per target of the row build (8, 16 or 32; tuned)
+    int list_cap;
+    uint32_t *nbl;
+    uint32_t *nbc;
 };
+
+// nbc flags: solid particles in one of the target's neighbour cells (the pair
+// loops visit those cells for the solid candidates); the row overflowed (the
+// target takes the cell visit for everything)
+constexpr uint32_t kListSolid = 1u << 22, kListOver = 1u << 23;
+constexpr uint32_t kListCountMask = 0x7ffu;
 
 // Static walls, binned once.
 struct Walls {
@@ -268,7 +284,17 @@ struct Batch {
     Ctl *ctl;                     // device control blocks [B]
     int B;
     int ncell;                    // total cells
+    long long spin;               // iterations of a bounded wait before it gives up (sphfsi_set_wait_limit)
+    // Set when the histogram scan gave up waiting: the cell starts of the step
+    // are then not valid, so every later kernel that reads cell ranges (and the
+    // binning and finish of later steps) returns at once; the host refuses to
+    // step until a checkpoint is restored.  Only the scan writes it, and the
+    // kernels that read it start after the scan has completed, so all their
+    // threads read the same value.
+    int *fail;
 };
+
+__device__ __forceinline__ bool step_failed(const Batch &bt) { return *bt.fail != 0; }
 
 // Does this step rebuild the pair configuration?  Every kernel of a step
 // evaluates the same inputs (instance 0's step index, which the finish kernel
@@ -286,7 +312,9 @@ __device__ __forceinline__ bool rebuild_step(const Batch &bt, const Fluid &f)
 // grid-wide barrier with a bounded spin (cooperative launch guarantees that
 // all blocks are resident); returns false after a time-out
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status)
+// (fail: the context's failed-step word, set on a time-out where the waiting
+// kernel's partial results would leave invalid cell ranges behind)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status, long long spin, int *fail = nullptr)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -303,9 +331,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status)
         } else {
             long long it = 0;
             while (*vgen == gen) {
-                if (++it > kSpinLimit) {
+                if (++it > spin) {
                     ok = 0;
                     atomicOr(status, ST_TIMEOUT);
+                    if (fail) atomicExch(fail, 1);
                     break;
                 }
                 __nanosleep(64);
@@ -405,6 +434,8 @@ int launch_reinit(const Batch &bt, const Fluid &f, const Walls &w, const Solid &
 int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
 int launch_solid_fluid_force(const Batch &bt, const Fluid &f, const Solid &s, int dim, cudaStream_t st);
 int launch_density(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
+// neighbour rows of the fluid targets (Fluid::list), on rebuild steps
+int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st);
 int launch_debug_pairs(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, int inst,
                        int which, int *counts, int *offs, int *out, cudaStream_t st);
 

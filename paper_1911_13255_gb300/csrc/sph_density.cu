@@ -91,6 +91,7 @@ template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_density(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
     const int stride = blockDim.x;
@@ -254,6 +255,7 @@ template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_reinit(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
     const int stride = blockDim.x;

@@ -110,6 +110,7 @@ template <int D, int L, bool CP, bool TILE, int FORM>
 __global__ void __launch_bounds__(kMaxBlock) k_momentum(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
     extern __shared__ __align__(16) uint8_t s_dyn[];
     uint32_t *const list = (uint32_t *)s_dyn + threadIdx.x;
     const int stride = blockDim.x;
@@ -133,6 +134,110 @@ int launch_momentum(const Batch &bt, const Fluid &f, const Walls &w, const Solid
 }
 
 // ---------------------------------------------------------------------------
+// a2 (neighbour rows): each fluid target's in-support fluid neighbours (from
+// the front of its row) and in-support wall neighbours (from the back),
+// over the 3^(d-1) rows of three cells around its cell (a row's cells are
+// consecutive in the cell-sorted records, so its candidates are one flat
+// range), with the pair loops' own FP32 test on the records, and whether a
+// neighbour cell holds solid particles.  L lanes per target test 2 L
+// candidates a round (both loads issued first); the in-support ones get their
+// places by ballots over the L lanes, so a row lists its entries in the
+// candidate order whatever L is.  Entries that do not fit are dropped and the
+// row is marked overflowed (its target then takes the cell form; every
+// write stays inside the row).  Runs on rebuild steps.
+// ---------------------------------------------------------------------------
+template <int D, int L>
+__global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls w, Solid s)
+{
+    pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
+    if (!rebuild_step(bt, f)) return;   // held configuration: the rows stay
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / L, lane = t % L;
+    if (i >= f.n) return;   // the L lanes of a target leave together
+    const int wl = threadIdx.x & 31;
+    const unsigned gmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u) << (wl & ~(L - 1));
+    const unsigned below = (1u << wl) - 1u;
+    const Inst &In = bt.I[f.inst[i]];
+    const Grid &g = In.g;
+    const float rc2 = In.P.rc2F;
+    const float4 Pi = f.P4[i];
+    int cx, cy, cz;
+    cell_xyz(f.cell_of[i], In, cx, cy, cz);
+    uint32_t *row = f.nbl + (size_t)i * f.list_cap;
+    const int cap = f.list_cap;
+    int nF = 0, nW = 0;
+    bool solid = false;
+    // every loop bound below is the same for the L lanes of the target
+    for_each_row<D>(g, In.c0, cx, cy, cz, [&](const int c[3], float oy, float oz, int code0) {
+        const Row3 rf = row_of(f.cstart, c);
+        const Row3 rw = row_of(w.cstart, c);
+        if (s.n) solid = solid || row_of(s.cstart, c).n > 0;
+        for (int qb = 0; qb < rf.n; qb += 2 * L) {
+            const int q0 = qb + lane, q1 = q0 + L;
+            int k0 = 0, k1 = 0;
+            const int j0 = q0 < rf.n ? row_slot(rf, q0, k0) : -1;
+            const int j1 = q1 < rf.n ? row_slot(rf, q1, k1) : -1;
+            const float4 P0 = j0 >= 0 ? f.P4[j0] : Pi;
+            const float4 P1 = j1 >= 0 ? f.P4[j1] : Pi;
+            float d[3];
+            const bool in0 = j0 >= 0 && j0 != i && rel_d<D>(Pi, P0, row_ox(k0, g), oy, oz, d) < rc2;
+            const bool in1 = j1 >= 0 && j1 != i && rel_d<D>(Pi, P1, row_ox(k1, g), oy, oz, d) < rc2;
+            const unsigned m0 = __ballot_sync(gmask, in0) & gmask;
+            const unsigned m1 = __ballot_sync(gmask, in1) & gmask;
+            const int n0 = __popc(m0);
+            if (in0) {
+                const int q = nF + __popc(m0 & below);
+                if (q < cap) row[q] = ((uint32_t)j0 << kCodeBits) | (uint32_t)(code0 + k0);
+            }
+            if (in1) {
+                const int q = nF + n0 + __popc(m1 & below);
+                if (q < cap) row[q] = ((uint32_t)j1 << kCodeBits) | (uint32_t)(code0 + k1);
+            }
+            nF += n0 + __popc(m1);
+        }
+        for (int qb = 0; qb < rw.n; qb += L) {
+            const int q0 = qb + lane;
+            int k0 = 0;
+            const int a = q0 < rw.n ? row_slot(rw, q0, k0) : -1;
+            float d[3];
+            const bool in = a >= 0 && rel_d<D>(Pi, w.A4[a], row_ox(k0, g), oy, oz, d) < rc2;
+            const unsigned m = __ballot_sync(gmask, in) & gmask;
+            if (in) {
+                const int q = cap - 1 - (nW + __popc(m & below));
+                if (q >= 0) row[q] = ((uint32_t)a << kCodeBits) | (uint32_t)(code0 + k0);
+            }
+            nW += __popc(m);
+        }
+    });
+    if (lane == 0)
+        f.nbc[i] = (nF + nW > cap || nF > (int)kListCountMask || nW > (int)kListCountMask)
+                       ? kListOver
+                       : ((uint32_t)nF | ((uint32_t)nW << 11) | (solid ? kListSolid : 0u));
+}
+
+int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
+{
+    if (f.n == 0 || !f.list) return 0;
+    if (f.n >= kMaxPairTargets || w.n >= kMaxPairTargets) return -7;
+    // its own lane count: wide groups load a row's consecutive candidates together
+    auto go = [&](auto Dc, auto Lc) {
+        constexpr int D_ = decltype(Dc)::value, L_ = decltype(Lc)::value;
+        launch_k(k_pairlist<D_, L_>, grid_blocks(f.n, L_, 128), 128, 0, st, bt, f, w, s);
+    };
+    auto by_lanes = [&](auto Dc) {
+        if (f.list_lanes == 8) go(Dc, std::integral_constant<int, 8>{});
+        else if (f.list_lanes == 16) go(Dc, std::integral_constant<int, 16>{});
+        else if (f.list_lanes == 32) go(Dc, std::integral_constant<int, 32>{});
+        else return false;
+        return true;
+    };
+    const bool ok = dim == 2 ? by_lanes(std::integral_constant<int, 2>{}) : by_lanes(std::integral_constant<int, 3>{});
+    if (!ok) return -1;
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// ---------------------------------------------------------------------------
 // a5: fluid force on each solid particle, f_a^F = -sum_i V_i (pair term),
 // the same pair expression and inputs as a4 (fluid at r^{n+1/2}, v^n)
 // ---------------------------------------------------------------------------
@@ -140,6 +245,7 @@ template <int D, int L>
 __global__ void __launch_bounds__(kMaxBlock, 2) k_solid_fluid_force(Batch bt, Fluid f, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = t / L, lane = t % L;
     const bool act = k < s.n;

@@ -120,6 +120,7 @@ __device__ void update_normal(const Solid &s, int a)
 __global__ void k_finish(Batch bt, int learned, unsigned *gbar, Fluid f)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0 && gbar) gbar[0] = 0u;   // the fused binning's barrier, even after a time-out
     if (b == 0 && f.held) {
@@ -264,6 +265,7 @@ template <int D>
 __global__ void k_bin_all(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         *f.nlive = 0;
@@ -434,10 +436,12 @@ __global__ void __launch_bounds__(kScanLbThreads) k_scan_lb(Batch bt, Fluid f, S
                     long long it = 0;
                     unsigned long long w2 = wd;
                     while (((unsigned)(w2 >> 34) != (epoch & 0x3fffffffu) || ((unsigned)(w2 >> 32) & 3u) == 0u) &&
-                           ++it < kSpinLimit)
+                           ++it < bt.spin)
                         w2 = atomicAdd(&f.scan_status[j], 0ull);
-                    if (it >= kSpinLimit) {
+                    if (it >= bt.spin) {
+                        // this tile's prefix is unknown: the step's cell starts are invalid
                         atomicOr(&bt.ctl[b].status, ST_TIMEOUT);
+                        atomicExch(bt.fail, 1);
                         break;
                     }
                     continue;
@@ -499,6 +503,7 @@ __device__ __forceinline__ void scatter_one(const Fluid &f, const Solid &s, int 
 __global__ void k_scatter2(Batch bt, Fluid f, Solid s, int ncell, int list_cells)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     if (!rebuild_step(bt, f)) return;
     scatter_one(f, s, blockIdx.x * blockDim.x + threadIdx.x, ncell, list_cells);
 }
@@ -691,6 +696,7 @@ template <int D, int G, bool REC>
 __global__ void __launch_bounds__(256) k_cell_records(Batch bt, Fluid f, Solid s, int listed, int ncells)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     if (!rebuild_step(bt, f)) return;   // held configuration: k_held_records refreshes the records
     const int nlive = listed ? *f.nlive : ncells;
     const int lane = threadIdx.x % G;
@@ -706,6 +712,7 @@ template <int D>
 __global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     if (!rebuild_step(bt, f)) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < f.n) fluid_record<D>(bt, f, t, f.sperm[t]);
@@ -721,6 +728,7 @@ template <int D>
 __global__ void k_held_records(Batch bt, Fluid f, Solid s)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     if (rebuild_step(bt, f)) return;   // the binning wrote every record
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < f.n) {
@@ -805,6 +813,7 @@ __global__ void __launch_bounds__(kBinFusedThreads, 1)
     k_bin_fused(Batch bt, Fluid f, Solid s, int step, double dt_fixed, int K_fixed)
 {
     pdl_enter();
+    if (step_failed(bt)) return;
     __shared__ int red[32];
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
     int *status = &bt.ctl[0].status;
@@ -812,7 +821,7 @@ __global__ void __launch_bounds__(kBinFusedThreads, 1)
     // (1) step control, drift, cell keys, histograms
     if (gt == 0) *f.nlive = 0;
     for (int t = gt; t < np + (step ? bt.B : 0); t += gs) bin_one<D>(bt, f, s, t, step, dt_fixed, K_fixed);
-    if (!grid_barrier(f.gbar, status)) return;
+    if (!grid_barrier(f.gbar, status, bt.spin, bt.fail)) return;
     // (2) exclusive scan of [fluid counts | solid counts]
     const int ncell = bt.ncell, L = (s.n ? 2 : 1) * ncell;
     const int chunk = (L + gridDim.x - 1) / gridDim.x;
@@ -822,7 +831,7 @@ __global__ void __launch_bounds__(kBinFusedThreads, 1)
     for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) part += count_at(i);
     part = block_sum(part, red);
     if (threadIdx.x == 0) f.bsum[blockIdx.x] = part;
-    if (!grid_barrier(f.gbar, status)) return;
+    if (!grid_barrier(f.gbar, status, bt.spin, bt.fail)) return;
     int off = 0;
     for (int j = threadIdx.x; j < (int)blockIdx.x; j += blockDim.x) off += f.bsum[j];
     off = block_sum(off, red);
@@ -847,10 +856,10 @@ __global__ void __launch_bounds__(kBinFusedThreads, 1)
         f.cstart[ncell] = f.n;
         if (s.n) s.cstart[ncell] = s.n;
     }
-    if (!grid_barrier(f.gbar, status)) return;
+    if (!grid_barrier(f.gbar, status, bt.spin, bt.fail)) return;
     // (3) scatter and the list of non-empty cells (whole warps per call)
     for (int t = gt; t < ((np + 31) & ~31); t += gs) scatter_one(f, s, t, ncell, 1);
-    if (!grid_barrier(f.gbar, status)) return;
+    if (!grid_barrier(f.gbar, status, bt.spin, bt.fail)) return;
     // (4) canonical order and records of the non-empty cells
     const int nlive = *f.nlive;
     const int lane = threadIdx.x % G;

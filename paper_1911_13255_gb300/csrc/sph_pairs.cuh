@@ -531,19 +531,73 @@ __device__ __forceinline__ unsigned fluid_pairs_rows(const Fluid &f, const Walls
     return cnt_total;
 }
 
+// Neighbour-row form (Fluid::list): target i's in-support fluid neighbours
+// (front of its row) and wall neighbours (back of its row, last entry first)
+// come from its row (built by k_pairlist at the same
+// record positions, with the same FP32 support test), L lanes striding over
+// it with every lane busy; the solid candidates of its neighbour cells are
+// visited only when the row says there are any; a row that overflowed takes
+// the cell form.  Pairs in a row are in support by construction: pair() gets
+// them without a test (the count of this lane's fluid pairs is returned).
+template <int D, int L, typename Fetch, typename Pair, typename WP, typename SP>
+__device__ __forceinline__ unsigned fluid_pairs_list(const Fluid &f, const Walls &w, const Solid &s, const Grid &g,
+                                                     int c0, int cx, int cy, int cz, int i, int lane,
+                                                     const float4 &Pi, float rc2, Fetch &fetch, Pair &pair, WP &wp,
+                                                     SP &sp)
+{
+    const uint32_t cw = f.nbc[i];
+    if (cw & kListOver) {
+        const unsigned n = fluid_pairs_global<D, L, false, 1>(f, g, c0, cx, cy, cz, i, lane, Pi, rc2, nullptr, 0,
+                                                              fetch, pair);
+        for_each_cell<D, 1>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+            ws_cell<L>(w, s, c, ox, oy, oz, lane, wp, sp);
+        });
+        return n;
+    }
+    const int nF = (int)(cw & kListCountMask), nW = (int)((cw >> 11) & kListCountMask);
+    const uint32_t *__restrict__ row = f.nbl + (size_t)i * f.list_cap;
+#pragma unroll 2
+    for (int q = lane; q < nF; q += L) {
+        const uint32_t e = row[q];
+        const int j = (int)(e >> kCodeBits);
+        float ox, oy, oz;
+        cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
+        const float4 Pj = f.P4[j];
+        float d[3];
+        const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
+        pair(j, Pj, fetch(j), d, r2, ox, oy, oz);
+    }
+    const uint32_t *__restrict__ wrow = row + f.list_cap - 1;   // wall entries run from the back
+    for (int q = lane; q < nW; q += L) {
+        const uint32_t e = wrow[-q];
+        float ox, oy, oz;
+        cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
+        wp((int)(e >> kCodeBits), ox, oy, oz);
+    }
+    if (cw & kListSolid) {
+        for_each_cell<D, 1>(g, c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int) {
+            const int b1 = s.cstart[c + 1];
+            for (int b = s.cstart[c] + lane; b < b1; b += L) sp(b, ox, oy, oz);
+        });
+    }
+    return lane < nF ? (unsigned)((nF - lane + L - 1) / L) : 0u;
+}
+
 // All neighbours of target i: fluid-fluid pairs through pair (their number
 // is returned), wall and solid candidates through wp and sp.  FORM 1 is the
-// row form (global records only); otherwise the cell form visits the fluid
-// cells (from the staged tile when ts is set), then the wall and solid
-// entries cell by cell, over the 3^d cells (FORM 0) or the 5^d cells of
-// edge >= h_F (FORM 2).
+// row form (global records only); FORM 3 the neighbour-row form; otherwise
+// the cell form visits the fluid cells (from the staged tile when ts is set),
+// then the wall and solid entries cell by cell, over the 3^d cells (FORM 0)
+// or the 5^d cells of edge >= h_F (FORM 2).
 template <int D, int L, bool CP, int FORM, typename Fetch, typename Pair, typename WP, typename SP>
 __device__ __forceinline__ unsigned fluid_pairs(const Fluid &f, const Walls &w, const Solid &s, const Grid &g, int c0,
                                                 int cx, int cy, int cz, int i, int lane, const float4 &Pi, float rc2,
                                                 uint32_t *list, int stride, const TileSrc *ts, Fetch &&fetch,
                                                 Pair &&pair, WP &&wp, SP &&sp)
 {
-    if constexpr (FORM == 1) {
+    if constexpr (FORM == 3) {
+        return fluid_pairs_list<D, L>(f, w, s, g, c0, cx, cy, cz, i, lane, Pi, rc2, fetch, pair, wp, sp);
+    } else if constexpr (FORM == 1) {
         return fluid_pairs_rows<D, L, CP>(f, w, s, g, c0, cx, cy, cz, i, lane, Pi, rc2, list, stride, fetch, pair, wp,
                                           sp);
     } else {
@@ -730,7 +784,7 @@ static void allow_smem(K kern, size_t bytes)
 
 #define SPH_LAUNCH_PAIRS(KERN, n, ...)                                                        \
     do {                                                                                      \
-        const size_t sm_ = (f.compact ? (size_t)kListBytes * f.block : 0) +                  \
+        const size_t sm_ = f.list ? 0 : (f.compact ? (size_t)kListBytes * f.block : 0) +     \
                            (f.tile ? (size_t)f.tile_cap * 32 : 0);                            \
         auto go_ = [&](auto Dc, auto Lc) {                                                    \
             constexpr int D_ = decltype(Dc)::value, L_ = decltype(Lc)::value;                \
@@ -740,7 +794,8 @@ static void allow_smem(K kern, size_t bytes)
                 allow_smem(kern, sm_);                                                        \
                 launch_k(kern, nb_, f.block, sm_, st, __VA_ARGS__);                           \
             };                                                                                \
-            if (f.compact && f.tile) run_(KERN<D_, L_, true, true, 0>);                       \
+            if (f.list) run_(KERN<D_, L_, false, false, 3>);                                  \
+            else if (f.compact && f.tile) run_(KERN<D_, L_, true, true, 0>);                  \
             else if (f.compact && f.rows) run_(KERN<D_, L_, true, false, 1>);                 \
             else if (f.compact && f.reach == 2) run_(KERN<D_, L_, true, false, 2>);           \
             else if (f.compact) run_(KERN<D_, L_, true, false, 0>);                           \

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Batch bt, Solid 
         store_Q<D>(s.Q4, a, Q);
     }
     for (int kk = 0; kk < K; kk++) {
-        if (!grid_barrier(s.bar, &ctl->status)) return;
+        if (!grid_barrier(s.bar, &ctl->status, bt.spin)) return;
         // (B) force loop and kick (Eqs. solid-model-mr, verlet-first-mediate-solid)
         for (int a = tid; a < s.n; a += G) {
             float acc[3] = {0.f, 0.f, 0.f};
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kSolidBlock) k_solid_substeps(Batch bt, Solid 
                 vmax = max_keep_nan(vmax, v.x * v.x + v.y * v.y + v.z * v.z);
             }
         }
-        if (!grid_barrier(s.bar, &ctl->status)) return;
+        if (!grid_barrier(s.bar, &ctl->status, bt.spin)) return;
         // (C) deformation rate at v^{k+1}, second half drift; then the first
         // half drift of the next sub-step and its stress
         const bool more = kk + 1 < K;

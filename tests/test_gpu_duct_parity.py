@@ -6,9 +6,9 @@ oracle through the C-ABI: neighbour sets bit for bit, then one coarse step
 grid barrier spans many CTAs) element by element.
 
 The launch shapes are those the library picks for large problems (4 lanes
-per target, compacted fluid pairs, records written per slot, the cell form)
-and, as a second case, the 3-D direct form, so that the code paths that only
-large problems take are checked against the oracle."""
+per target, compacted fluid pairs, records written per slot, the cell form),
+the 3-D direct form and the neighbour-row form, so that the code paths that
+only large problems take are checked against the oracle."""
 import numpy as np
 import pytest
 
@@ -63,8 +63,9 @@ def _sets_equal(case, sim):
 
 
 SHAPES = {
-    "large_defaults": dict(lanes=4, block=128, compact=1, records=1, rows=0),
-    "direct_8_lanes": dict(lanes=8, block=128, compact=0, records=1, rows=0),
+    "large_defaults": dict(lanes=4, block=128, compact=1, records=1, rows=0, list=0),
+    "direct_8_lanes": dict(lanes=8, block=128, compact=0, records=1, rows=0, list=0),
+    "neighbour_rows": dict(lanes=4, block=128, compact=0, records=1, rows=0, list=1),
 }
 
 

@@ -31,6 +31,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _unwrap(case, d):
+    """Displacements with periodic x brought to the minimal image."""
+    d = np.array(d)
+    if case.periodic_x:
+        d[:, 0] -= case.Lx * np.round(d[:, 0] / case.Lx)
+    return d
+
+
 def _dt_K(ref):
     dt, _, dts = ref.suggest_dt()
     return dt, ref.substeps(dt, dts)
@@ -46,6 +54,7 @@ def test_held_configuration_steps_match_the_oracle(name):
     sim.set_substeps(K)
     sim.set_advection_cadence(N_HELD)
     counts = []
+    r_start = np.array(ref.f_r)
     for k in range(2 * N_HELD + 1):
         sim.step(dt)
         sim.sync()
@@ -56,8 +65,10 @@ def test_held_configuration_steps_match_the_oracle(name):
             e["fF"] = rel(s["fF"], ref.s_fF)
             e["v_s"] = rel(s["v"], ref.s_v)
         print(name, k, {q: f"{v:.1e}" for q, v in e.items()})
+        # independent trajectories: positions drift apart by the FP32 velocity
+        # differences, so displacements are compared relatively
+        e["dr"] = rel(_unwrap(case, g["r"] - r_start), _unwrap(case, ref.f_r - r_start))
         assert max(e.values()) < ACC_TOL, (k, e)
-        assert np.abs(g["r"] - ref.f_r).max() < 1e-9
         c = tuple(info["pairs_" + q] for q in ("ff", "fw", "fs", "sf"))
         assert c == tuple(ref.last["n_" + q] for q in ("ff", "fw", "fs", "sf")), (k, c)
         counts.append(c)

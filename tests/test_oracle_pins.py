@@ -757,3 +757,22 @@ def test_frozen_configuration_conserves_momentum_and_its_pair_counts():
     for w0 in range(0, 40, 4):
         assert len(set(counts[w0:w0 + 4])) == 1
     assert len(set(counts)) > 1   # the lists were rebuilt as the flow moved
+
+
+# --------------------------------------------------------------------------
+# The OpenMP build that times the oracle on many cores gives the same bits
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny_box", "tiny_box_3d", "channel_flag"])
+def test_threaded_oracle_build_is_bit_identical(name):
+    case = getattr(fc, name)(seed=6)
+    a, b = O.OracleSim(case), O.OracleSim(case, threaded=True)
+    dt, _, dts = a.suggest_dt()
+    K = a.substeps(dt, dts)
+    for _ in range(4):
+        da, db = a.step(dt, K), b.step(dt, K)
+    for k in ("f_r", "f_v", "f_rho", "f_drho", "f_dvdt", "s_r", "s_v", "s_F", "s_fF", "s_vbar", "s_abar", "s_nrm"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    for k in ("mom_fs_fluid", "mom_fs_solid"):
+        assert np.array_equal(da[k], db[k]), k
+    assert da["abs_fs"] == db["abs_fs"]
