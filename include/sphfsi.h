@@ -372,9 +372,11 @@ typedef struct {
                               a row (at most 64 in 2-D, 128 in 3-D; a fuller row falls back to the
                               cell visit for that particle), and stream the rows in momentum,
                               continuity and reinitialisation; not with tiles or cell_reach 2
-                              (default 0) */
-    int32_t list_lanes;    /* threads per fluid particle of the row build: 8, 16 or 32 (default 16
-                              in 2-D, 32 in 3-D; 0 keeps the current value) */
+                              (default 1 in 3-D from 262 144 particles in the context, else 0) */
+    int32_t list_lanes;    /* threads per fluid particle of the row build: 1 (one warp per cell,
+                              each candidate loaded once for the cell's particles), 8, 16 or 32
+                              (default 8 in 2-D, 1 in 3-D; 0 keeps the current value); all build
+                              the same rows */
 } sphfsi_tuning;
 
 /* Set or read the launch shape (SPHFSI_E_INVAL for values outside the lists). */

@@ -755,10 +755,14 @@ int sphfsi_finalize(sphfsi_ctx *c)
     }
     TRY(dalloc(c, &F.bsum, 4096));
     TRY(dalloc(c, &F.gbar, 2));
-    // neighbour rows (tuned; off by default): about 20 (2-D) or 80 (3-D)
-    // neighbours per fluid particle on a lattice, wall neighbours included
-    F.list = 0;
-    F.list_lanes = D == 2 ? 16 : 32;
+    // neighbour rows (tuned): about 20 (2-D) or 80 (3-D) neighbours per fluid
+    // particle on a lattice, wall neighbours included.  On by default for
+    // large 3-D problems (3-D duct, 3M fluid: momentum 6.2 -> 2.4 ms,
+    // continuity 4.9 -> 1.65 ms for a 2.4 ms row build); off for 2-D, where
+    // the row build costs more than it saves (dam break 0.100 -> 0.107 ms)
+    F.list = D == 3 && !small ? 1 : 0;
+    if (F.list) F.compact = 0;
+    F.list_lanes = D == 2 ? 8 : 1;
     F.list_cap = D == 2 ? 64 : 128;
     TRY(dalloc(c, &F.nbl, (size_t)nf * F.list_cap));
     TRY(dalloc(c, &F.nbc, nf));
@@ -1603,7 +1607,8 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
         t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile) ||
         (c->max_reach > 1 && (t->rows || t->tile)) || t->list < 0 || t->list > 1 ||
         (t->list && (t->tile || c->max_reach > 1)) ||
-        (t->list_lanes != 0 && t->list_lanes != 8 && t->list_lanes != 16 && t->list_lanes != 32))
+        (t->list_lanes != 0 && t->list_lanes != 1 && t->list_lanes != 8 && t->list_lanes != 16 &&
+         t->list_lanes != 32))
         return SPHFSI_E_INVAL;
     c->F.lanes = t->lanes;
     c->F.block = t->block;
@@ -1718,7 +1723,7 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         for (int k = 0; k < 3 && !rc && cur.list; k++) {
-            const int ll[3] = {8, 16, 32};
+            const int ll[3] = {1, 8, 32};
             if (ll[k] == best->list_lanes) continue;
             cur.list_lanes = ll[k];
             rc = consider(cur);

@@ -50,14 +50,15 @@ __device__ __forceinline__ void density_one(const Batch &bt, const Fluid &f, con
                                     float) {
                 if (r2 == 0.0f) return;   // a clumped pair: no direction, dW(0) = 0
                 const float rhoj = P.rho0 + Wj.w;
-                float r = sqrtf(r2), invr = 1.0f / r;
+                // one reciprocal square root for 1/r and r (r2 > 0 here)
+                const float invr = rsqrtf(r2), r = r2 * invr;
                 float dW = dW_F(r, P);
                 float UL = -(vi[0] * d[0] + vi[1] * d[1] + (D == 3 ? vi[2] * d[2] : 0.0f)) * invr;
                 float UR = -(Wj.x * d[0] + Wj.y * d[1] + (D == 3 ? Wj.z * d[2] : 0.0f)) * invr;
                 float rb = 0.5f * (rhoi + rhoj);
                 // (v_i - v~_ij).grad_i W = -dW (U_L - U*), U* = (U_L + U_R)/2 + (p_i - p_j) / (2 rho c0)
                 float diff = 0.5f * (UL - UR) - eos_dp(drhoi, Wj.w, P) * inv2c0 / rb;
-                rate += (P.mF / rhoj) * (-dW) * diff;
+                rate += __fdividef(P.mF, rhoj) * (-dW) * diff;
             }, wall_pair, solid_pair);
     }
     rate = group_sum<L>(rate);

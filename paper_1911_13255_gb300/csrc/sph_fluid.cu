@@ -68,7 +68,8 @@ __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, co
                 // direction is undefined and the pair's terms vanish with r
                 if (r2 == 0.0f) return;
                 const float rhoj = P.rho0 + Vj.w;
-                float r = sqrtf(r2), invr = 1.0f / r;
+                // one reciprocal square root for 1/r and r (r2 > 0 here)
+                const float invr = rsqrtf(r2), r = r2 * invr;
                 float dW = dW_F(r, P);
                 // U = v.e with e = -d / r (from i to j)
                 float UL = -(vi[0] * d[0] + vi[1] * d[1] + (D == 3 ? vi[2] * d[2] : 0.0f)) * invr;
@@ -76,7 +77,7 @@ __device__ __forceinline__ void momentum_one(const Batch &bt, const Fluid &f, co
                 float rb = 0.5f * (rhoi + rhoj);
                 float beta = fminf(3.0f * fmaxf(UL - UR, 0.0f), c0);
                 float Ps = 0.5f * (pi + Pj.w) + 0.5f * rb * beta * (UL - UR);
-                float sc = (P.mF / rhoj) * dW * invr;
+                float sc = __fdividef(P.mF, rhoj) * dW * invr;   // V_j dW / r
                 acc[0] += sc * (-2.0f * Ps * d[0] + eta2 * (vi[0] - Vj.x));
                 acc[1] += sc * (-2.0f * Ps * d[1] + eta2 * (vi[1] - Vj.y));
                 if (D == 3) acc[2] += sc * (-2.0f * Ps * d[2] + eta2 * (vi[2] - Vj.z));
@@ -188,11 +189,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls
             const int n0 = __popc(m0);
             if (in0) {
                 const int q = nF + __popc(m0 & below);
-                if (q < cap) row[q] = ((uint32_t)j0 << kCodeBits) | (uint32_t)(code0 + k0);
+                if (q < cap) row[q] = ((uint32_t)j0 << kCodeBits) | row_code(code0 + k0);
             }
             if (in1) {
                 const int q = nF + n0 + __popc(m1 & below);
-                if (q < cap) row[q] = ((uint32_t)j1 << kCodeBits) | (uint32_t)(code0 + k1);
+                if (q < cap) row[q] = ((uint32_t)j1 << kCodeBits) | row_code(code0 + k1);
             }
             nF += n0 + __popc(m1);
         }
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls
             const unsigned m = __ballot_sync(gmask, in) & gmask;
             if (in) {
                 const int q = cap - 1 - (nW + __popc(m & below));
-                if (q >= 0) row[q] = ((uint32_t)a << kCodeBits) | (uint32_t)(code0 + k0);
+                if (q >= 0) row[q] = ((uint32_t)a << kCodeBits) | row_code(code0 + k0);
             }
             nW += __popc(m);
         }
@@ -214,6 +215,65 @@ __global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls
         f.nbc[i] = (nF + nW > cap || nF > (int)kListCountMask || nW > (int)kListCountMask)
                        ? kListOver
                        : ((uint32_t)nF | ((uint32_t)nW << 11) | (solid ? kListSolid : 0u));
+}
+
+// The same rows, one warp per cell and one lane per particle of the cell:
+// every candidate of the 3^d neighbour cells is loaded once for the whole
+// warp (one broadcast load) and each lane tests its own particle against it
+// and appends to its own row, so the entries come in the same order as
+// above (fluid by cell, then slot, from the front; walls likewise from the
+// back).  Cells of more than 32 particles take several rounds.
+template <int D>
+__global__ void __launch_bounds__(128) k_pairlist_cells(Batch bt, Fluid f, Walls w, Solid s)
+{
+    pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
+    if (!rebuild_step(bt, f)) return;
+    const int cell = blockIdx.x * 4 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (cell >= bt.ncell) return;
+    const int t0 = f.cstart[cell], t1 = f.cstart[cell + 1];
+    if (t0 >= t1) return;
+    const Inst &In = bt.I[f.inst[t0]];
+    const Grid &g = In.g;
+    const float rc2 = In.P.rc2F;
+    const int cap = f.list_cap;
+    int cx, cy, cz;
+    cell_xyz(cell, In, cx, cy, cz);
+    for (int tb = t0; tb < t1; tb += 32) {
+        const int i = tb + lane;
+        const bool act = i < t1;
+        const float4 Pi = f.P4[act ? i : t0];
+        uint32_t *row = f.nbl + (size_t)(act ? i : t0) * cap;
+        int nF = 0, nW = 0;
+        bool solid = false;
+        for_each_cell<D, 1>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+            const uint32_t rc = row_code(code);
+            const int j1 = f.cstart[c + 1];
+#pragma unroll 4
+            for (int j = f.cstart[c]; j < j1; j++) {
+                float d[3];
+                const bool in = rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) < rc2 && j != i && act;
+                if (in) {
+                    if (nF < cap) row[nF] = ((uint32_t)j << kCodeBits) | rc;
+                    nF++;
+                }
+            }
+            const int a1 = w.cstart[c + 1];
+            for (int a = w.cstart[c]; a < a1; a++) {
+                float d[3];
+                const bool in = rel_d<D>(Pi, w.A4[a], ox, oy, oz, d) < rc2 && act;
+                if (in) {
+                    if (nW < cap) row[cap - 1 - nW] = ((uint32_t)a << kCodeBits) | rc;
+                    nW++;
+                }
+            }
+            if (s.n && s.cstart[c + 1] > s.cstart[c]) solid = true;
+        });
+        if (act)
+            f.nbc[i] = (nF + nW > cap || nF > (int)kListCountMask || nW > (int)kListCountMask)
+                           ? kListOver
+                           : ((uint32_t)nF | ((uint32_t)nW << 11) | (solid ? kListSolid : 0u));
+    }
 }
 
 int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
@@ -226,7 +286,9 @@ int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid
         launch_k(k_pairlist<D_, L_>, grid_blocks(f.n, L_, 128), 128, 0, st, bt, f, w, s);
     };
     auto by_lanes = [&](auto Dc) {
-        if (f.list_lanes == 8) go(Dc, std::integral_constant<int, 8>{});
+        constexpr int D_ = decltype(Dc)::value;
+        if (f.list_lanes == 1) launch_k(k_pairlist_cells<D_>, (bt.ncell + 3) / 4, 128, 0, st, bt, f, w, s);
+        else if (f.list_lanes == 8) go(Dc, std::integral_constant<int, 8>{});
         else if (f.list_lanes == 16) go(Dc, std::integral_constant<int, 16>{});
         else if (f.list_lanes == 32) go(Dc, std::integral_constant<int, 32>{});
         else return false;

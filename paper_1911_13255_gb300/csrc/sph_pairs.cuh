@@ -151,6 +151,19 @@ __device__ __forceinline__ void cell_offset(int code, const Grid &g, float &ox, 
     oz = -(float)dz * g.csf[2];
 }
 
+// Cell offset of a neighbour-row entry: 2 bits per axis, (dx + 1) | (dy + 1)
+// << 2 | (dz + 1) << 4 (reach 1), decoded with shifts and masks.
+__device__ __forceinline__ uint32_t row_code(int code27)
+{
+    return (uint32_t)(code27 % 3) | (uint32_t)((code27 / 3) % 3) << 2 | (uint32_t)(code27 / 9) << 4;
+}
+__device__ __forceinline__ void row_offset(uint32_t e, const Grid &g, float &ox, float &oy, float &oz)
+{
+    ox = (float)(1 - (int)(e & 3u)) * g.csf[0];
+    oy = (float)(1 - (int)((e >> 2) & 3u)) * g.csf[1];
+    oz = (float)(1 - (int)((e >> 4) & 3u)) * g.csf[2];
+}
+
 template <int D>
 __device__ __forceinline__ float rel_d(const float4 &Pi, const float4 &Pj, float ox, float oy, float oz, float d[3])
 {
@@ -561,7 +574,7 @@ __device__ __forceinline__ unsigned fluid_pairs_list(const Fluid &f, const Walls
         const uint32_t e = row[q];
         const int j = (int)(e >> kCodeBits);
         float ox, oy, oz;
-        cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
+        row_offset(e, g, ox, oy, oz);
         const float4 Pj = f.P4[j];
         float d[3];
         const float r2 = rel_d<D>(Pi, Pj, ox, oy, oz, d);
@@ -571,7 +584,7 @@ __device__ __forceinline__ unsigned fluid_pairs_list(const Fluid &f, const Walls
     for (int q = lane; q < nW; q += L) {
         const uint32_t e = wrow[-q];
         float ox, oy, oz;
-        cell_offset<1>((int)(e & kCodeMask), g, ox, oy, oz);
+        row_offset(e, g, ox, oy, oz);
         wp((int)(e >> kCodeBits), ox, oy, oz);
     }
     if (cw & kListSolid) {
