@@ -153,7 +153,8 @@ KERNEL_SOURCE = {"k_momentum": "sph_fluid.cu", "k_solid_fluid_force": "sph_fluid
                  "k_density": "sph_density.cu", "k_reinit": "sph_density.cu",
                  "k_solid_cluster2d_one": "sph_solid.cu", "k_solid_cluster2d": "sph_solid.cu",
                  "k_solid_cluster_one": "sph_solid.cu", "k_solid_cluster": "sph_solid.cu",
-                 "k_solid_substeps": "sph_solid.cu", "k_gemm_bf16": "sph_learn_gemm.cu"}
+                 "k_solid_substeps": "sph_solid.cu", "k_gemm_bf16": "sph_learn_gemm.cu",
+                 "k_pairlist": "sph_fluid.cu"}
 
 
 def _source_hash(kernel=None):
@@ -191,7 +192,7 @@ CELL_REACH = {"dam_gate": 1, "flag_batch": 1, "duct_3d": 1, "flag_learned": 1, "
               "valve": 1}
 
 
-def make_cases(workload, seed=0, cell_reach=None, ratio=2, wo=10.0):
+def make_cases(workload, seed=0, cell_reach=None, ratio=2, wo=10.0, duct_scale=1):
     """ratio: dp_F / dp_S of the flag channel (Table 1: dp_S = a quarter of
     the flag's thickness, dp_F = ratio x dp_S; 1 is Case I, 2 Cases III, IV);
     wo: Womersley number of the venous valve."""
@@ -203,7 +204,7 @@ def make_cases(workload, seed=0, cell_reach=None, ratio=2, wo=10.0):
     elif workload == "flag_batch":
         cases = fsi_cases.flag_batch(seed=seed, n=256)
     elif workload == "duct_3d":
-        cases = [fsi_cases.duct_plate_3d(seed=seed, scale=1)]
+        cases = [fsi_cases.duct_plate_3d(seed=seed, scale=duct_scale)]
     elif workload == "flag_learned":
         cases = [fsi_cases.channel_flag(seed=seed)]
     else:
@@ -303,8 +304,9 @@ def run_gpu(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    label = WORKLOADS[args.workload]
-    cases = make_cases(args.workload, seed=rank, cell_reach=args.cell_reach, ratio=args.resolution_ratio)
+    label = WORKLOADS[args.workload] + ("_eighth_copy" if args.workload == "duct_3d" and args.duct_scale == 2 else "")
+    cases = make_cases(args.workload, seed=rank, cell_reach=args.cell_reach, ratio=args.resolution_ratio,
+                       duct_scale=args.duct_scale)
     case = cases[0]
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
@@ -899,6 +901,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--duct-scale", type=int, default=1, choices=[1, 2],
+                    help="duct_3d workload: 1 the full duct, 2 its copy at twice the spacings (1/8 of the particles)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="duct_3d", choices=sorted(WORKLOADS))

@@ -569,8 +569,25 @@ __device__ __forceinline__ unsigned fluid_pairs_list(const Fluid &f, const Walls
     }
     const int nF = (int)(cw & kListCountMask), nW = (int)((cw >> 11) & kListCountMask);
     const uint32_t *__restrict__ row = f.nbl + (size_t)i * f.list_cap;
-#pragma unroll 2
-    for (int q = lane; q < nF; q += L) {
+    // two entries per lane per round, both gathers issued before either pair
+    // is evaluated (the loop is bound by the latency of entry -> record
+    // chains); the pairs are summed in the same order as one at a time
+    int q = lane;
+    for (; q + L < nF; q += 2 * L) {
+        const uint32_t e0 = row[q], e1 = row[q + L];
+        const int j0 = (int)(e0 >> kCodeBits), j1 = (int)(e1 >> kCodeBits);
+        const float4 P0 = f.P4[j0], P1 = f.P4[j1];
+        const auto X0 = fetch(j0);
+        const auto X1 = fetch(j1);
+        float ox, oy, oz, d[3];
+        row_offset(e0, g, ox, oy, oz);
+        float r2 = rel_d<D>(Pi, P0, ox, oy, oz, d);
+        pair(j0, P0, X0, d, r2, ox, oy, oz);
+        row_offset(e1, g, ox, oy, oz);
+        r2 = rel_d<D>(Pi, P1, ox, oy, oz, d);
+        pair(j1, P1, X1, d, r2, ox, oy, oz);
+    }
+    if (q < nF) {
         const uint32_t e = row[q];
         const int j = (int)(e >> kCodeBits);
         float ox, oy, oz;
