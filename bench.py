@@ -54,7 +54,8 @@ WORKLOADS = {"dam_gate": "dam_break_elastic_gate_2d",
              "flag_learned": "flag_channel_learned_substepper_2d",
              "flag_channel": "flag_channel_2d",
              "fiv": "flow_induced_vibration_flag_to_t200_2d",
-             "valve": "pulsatile_flow_venous_valve_2d"}
+             "valve": "pulsatile_flow_venous_valve_2d",
+             "gemm_bf16": "tensor_core_gemm_bf16_shapes"}
 METRIC = "pair_interactions_per_s"
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -264,6 +265,9 @@ def cpu_baseline(cases, label, budget_s=15.0, max_steps=400, time_stepping="mult
 
 def run_reference(args, rank):
     if rank != 0:
+        return
+    if args.workload == "gemm_bf16":
+        print(json.dumps({"impl": "reference", "unavailable": "the GEMM timing workload has no oracle counterpart"}))
         return
     label = WORKLOADS[args.workload]
     cases = make_cases(args.workload, 0, ratio=args.resolution_ratio, wo=args.womersley)
@@ -839,6 +843,41 @@ def run_valve(args, rank, world, local_rank):
         np.savetxt(args.trace, np.column_stack([ts, xs, ys]), header="t tip_dx tip_dy")
 
 
+def run_gemm(args):
+    """The learned form's tensor-core GEMM (sphfsi_gemm_bf16) alone at given
+    shapes (--gemm-shapes "M,N,K;M,N,K"; default: the network layer at a
+    training batch of 32 flag bodies, its weight gradient, a large product):
+    device time per call over 20 calls after 3 warm-up calls, throughput, the
+    error against FP32 products of the same bfloat16 operands."""
+    import torch
+    from paper_1911_13255_gb300 import gemm_bf16, tc_status
+    shapes = [tuple(int(v) for v in t.split(",")) for t in args.gemm_shapes.split(";") if t] or \
+        [(19072, 128, 512), (128, 512, 19072), (16384, 256, 4096)]
+    st = torch.cuda.Stream()
+    out = []
+    for M, N, K in shapes:
+        g = torch.Generator(device="cuda").manual_seed(M + N + K)
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        for _ in range(3):
+            gemm_bf16(A, B, out=C, stream=st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(20):
+            gemm_bf16(A, B, out=C, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        ref = A.float() @ B.float().T
+        err = ((C - ref).norm() / ref.norm()).item()
+        out.append({"M": M, "N": N, "K": K, "us_per_call": ms * 1e3, "tflops": 2.0 * M * N * K / ms / 1e9,
+                    "rel_err": err})
+    if tc_status():
+        raise SystemExit("a bounded tensor-core wait ran out")
+    print(json.dumps({"workload": WORKLOADS["gemm_bf16"], "shapes": out}))
+
+
 def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
     """The same metric through the public API: the initial state of every
     instance goes up from pinned host memory, every step reads all solid
@@ -901,6 +940,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--gemm-shapes", default="", help="gemm_bf16 workload: M,N,K;M,N,K ...")
     ap.add_argument("--duct-scale", type=int, default=1, choices=[1, 2],
                     help="duct_3d workload: 1 the full duct, 2 its copy at twice the spacings (1/8 of the particles)")
     ap.add_argument("--warmup", type=int, default=5)
@@ -932,7 +972,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload == "flag_learned":
+    if args.workload == "gemm_bf16":
+        run_gemm(args)
+    elif args.workload == "flag_learned":
         run_learned(args, rank, world, local_rank)
     elif args.workload == "fiv":
         run_fiv(args, rank, world, local_rank)
