@@ -648,6 +648,17 @@ def _tip_oscillation(t, y, t0):
     return float(np.mean(amp)), float((len(tc) - 1) / (tc[-1] - tc[0])), len(tc) - 1
 
 
+def apply_readings(case, args):
+    """The unprinted details the flow-induced vibration depends on (readings
+    R16, R18, F2), when given: inflow buffer width in dp_F, density
+    reinitialisation cadence in steps."""
+    if args.inflow_buffer > 0:
+        case.inflow_width = args.inflow_buffer * case.f_dp
+    if args.n_reinit >= 0:
+        case.n_reinit = args.n_reinit
+    return case
+
+
 def run_fiv(args, rank, world, local_rank):
     """Flow-induced vibration of the flag behind the cylinder to t* = 200
     (Section 4.1, Tables 1 and 2): started with the inflow profile everywhere
@@ -665,8 +676,9 @@ def run_fiv(args, rank, world, local_rank):
     label = WORKLOADS[args.workload]
     D, U = 0.1, 1.0
     r = args.resolution_ratio
-    case = fsi_cases.channel_flag(seed=rank, dpF=r * D * 0.2 / 4, ratio=r)
+    case = fsi_cases.channel_flag(seed=args.seed + rank, dpF=r * D * 0.2 / 4, ratio=r)
     case.cell_reach = 1
+    apply_readings(case, args)
     t_end = args.t_star * D / U
     st = torch.cuda.Stream(device=dev)
     out = torch.empty((case.ns, 2), dtype=torch.float64).pin_memory()
@@ -675,6 +687,7 @@ def run_fiv(args, rank, world, local_rank):
     wall0 = time.perf_counter()
     sim = Simulation.from_case(case, stream=st)
     sim.set_time_stepping(args.time_stepping)
+    sim.set_advection_cadence(args.advection_cadence)
     ts, ys, xs, dev_ms, steps = [], [], [], 0.0, 0
     y0, x0 = case.s_r0[case.tip, 1], case.s_r0[case.tip, 0]
     with ClockSampler(local_rank) as clk:
@@ -728,6 +741,8 @@ def run_fiv(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns, "n_wall": case.nw,
                    "resolution_ratio": r, "time_stepping": args.time_stepping, "t_star_end": args.t_star,
+                   "seed": args.seed, "inflow_buffer_dp": case.inflow_width / case.f_dp, "n_reinit": case.n_reinit,
+                   "advection_cadence": args.advection_cadence,
                    "dp_F": case.f_dp, "dp_S": case.s_dp, "D": D, "U": U, "Re": 100, "E_star": 1.4e3,
                    "l2": "not flushed (whole working set ~5 MB); every 20 steps the solid positions are read back"},
         "t_reached": t, "t_star_reached": t * U / D, "finite": bool(t >= t_end),
@@ -941,6 +956,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--gemm-shapes", default="", help="gemm_bf16 workload: M,N,K;M,N,K ...")
+    ap.add_argument("--seed", type=int, default=0, help="fiv workload: seed of the jittered lattice")
+    ap.add_argument("--inflow-buffer", type=float, default=0.0, help="fiv workload: inflow buffer width in dp_F (0: the case's)")
+    ap.add_argument("--n-reinit", type=int, default=-1, help="fiv workload: density reinitialisation cadence (-1: the case's)")
+    ap.add_argument("--advection-cadence", type=int, default=1,
+                    help="steps the pair configuration is held (Algorithm 1, reading F2; 1: rebuilt every step)")
     ap.add_argument("--duct-scale", type=int, default=1, choices=[1, 2],
                     help="duct_3d workload: 1 the full duct, 2 its copy at twice the spacings (1/8 of the particles)")
     ap.add_argument("--warmup", type=int, default=5)
