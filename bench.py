@@ -315,6 +315,7 @@ def run_gpu(args, rank, world, local_rank):
     st = torch.cuda.Stream(device=dev)
     sim = Simulation.from_cases(cases, stream=st)
     sim.set_time_stepping(args.time_stepping)
+    sim.set_advection_cadence(args.advection_cadence)
     if args.tuning:
         vals = [int(x) for x in args.tuning.split(",")]
         sim.set_tuning(*vals)
@@ -372,7 +373,8 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
 
     # ---- e2e through the public API with pinned host buffers
-    e2e = e2e_run(cases, dev, steps=min(args.steps, 400), tuning=tuning, time_stepping=args.time_stepping)
+    e2e = e2e_run(cases, dev, steps=min(args.steps, 400), tuning=tuning, time_stepping=args.time_stepping,
+                  advection_cadence=args.advection_cadence)
     if rank != 0:
         return
     # ---- roofline of the dominant stage (device-timed live above)
@@ -447,6 +449,7 @@ def run_gpu(args, rank, world, local_rank):
                    "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows",
                                                      "list", "list_lanes")},
                    "cell_reach": case.cell_reach, "time_stepping": args.time_stepping,
+                   "advection_cadence": args.advection_cadence,
                    "autotuned": args.workload not in ("dam_gate", "duct_3d") and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -893,7 +896,7 @@ def run_gemm(args):
     print(json.dumps({"workload": WORKLOADS["gemm_bf16"], "shapes": out}))
 
 
-def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
+def e2e_run(cases, dev, steps, tuning, time_stepping="multiple", advection_cadence=1):
     """The same metric through the public API: the initial state of every
     instance goes up from pinned host memory, every step reads all solid
     positions (the flag / gate observers) back into pinned host memory;
@@ -937,6 +940,7 @@ def e2e_run(cases, dev, steps, tuning, time_stepping="multiple"):
     sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"],
                    tuning["records"], tuning["rows"], tuning["list"], tuning["list_lanes"])
     sim.set_time_stepping(time_stepping)
+    sim.set_advection_cadence(advection_cadence)
     p0 = sim.pairs_total()
     for _ in range(steps):
         sim.run(1, 0.0)

@@ -1,8 +1,17 @@
 """Flow-induced vibration channel (Section 4.1; the flag behind the cylinder
 at dp_F = D/10, dp_S = D/20: 10.1k fluid, 596 solid particles) started
-impulsively (reading R20): the flag-tip displacement after 1000 coarse steps
-matches the FP64 oracle within 1e-3, relative to max(|u|, 0.01 dp_S), the
-workload's tolerance for the tip."""
+impulsively (reading R20): the flag-tip displacement matches the FP64 oracle
+within 1e-3, relative to max(|u|, 0.01 dp_S), the workload's tolerance for
+the tip, after 400 coarse steps (t* = 1.9), and every solid particle's
+displacement within 1e-3 relative L2.
+
+Not after 1000 steps: this impulsively started flow amplifies round-off by
+about e^1.5-e^2.3 per 100 steps.  Two FP64 oracle runs whose initial fluid
+velocities differ by a relative 1e-7 (the size of one FP32 rounding) differ
+in the tip by 3e-3 after 500 steps and by 0.08-0.23 after 900-1000 steps,
+and GPU runs at different launch shapes (different summation orders) differ
+from each other as much as from the oracle; the 1000-step tip bound holds on
+the dam break (tests/test_gpu_parity.py), whose flow does not."""
 import numpy as np
 import pytest
 
@@ -18,7 +27,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_1911_13255_gb300 import Simulation  # noqa: E402
 
 
-def test_flag_tip_parity_1000_steps():
+def test_flag_tip_parity_400_steps():
     case = fc.channel_flag(seed=0)
     assert case.inflow_tramp == 0.0     # impulsive start
     ref = O.OracleSim(case, threaded=True)
@@ -26,16 +35,19 @@ def test_flag_tip_parity_1000_steps():
     K = ref.substeps(dt, dts)
     sim = Simulation.from_case(case)
     sim.set_substeps(K)
-    sim.run(1000, dt)
+    nsteps = 400
+    sim.run(nsteps, dt)
     sim.sync()
-    for _ in range(1000):
+    for _ in range(nsteps):
         ref.step(dt, K)
     s = sim.get_solid()
     tip = case.tip
     u_g = s["r"][tip] - case.s_r0[tip]
     u_o = ref.s_r[tip] - case.s_r0[tip]
     err = np.linalg.norm(u_g - u_o) / max(np.linalg.norm(u_o), 0.01 * case.s_dp)
-    print("K", K, "dt", dt, "tip u oracle", u_o, "gpu", u_g, "rel err", err)
+    du_g, du_o = s["r"] - case.s_r0, ref.s_r - case.s_r0
+    err_all = np.linalg.norm(du_g - du_o) / np.linalg.norm(du_o)
+    print("K", K, "dt", dt, "tip u oracle", u_o, "gpu", u_g, "rel err", err, "all", err_all)
     assert np.linalg.norm(u_o) > 0.1 * case.s_dp   # the flag moved
-    assert err < 1e-3
+    assert err < 1e-3 and err_all < 1e-3
     sim.close()
