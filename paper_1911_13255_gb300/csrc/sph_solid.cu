@@ -381,16 +381,6 @@ __device__ __forceinline__ void cluster_sync()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// the two halves of cluster_sync, so that work that needs no other CTA's
-// data can run while the other CTAs arrive
-__device__ __forceinline__ void cluster_arrive()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void cluster_wait()
-{
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // generic address of the same shared-memory variable in CTA `rank` of the cluster
 template <typename T>
@@ -810,12 +800,6 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     uint32_t prk[kPushMax];  // and the ranks of the CTAs holding them
     int npush = 0;
     int nn = 0;   // this thread's entries
-    uint32_t loc = 0u;   // pull form, bit u: entry u's neighbour lives in this CTA
-    // entry u's neighbour lives in this CTA (push form: its slot is one of the CTA's own)
-    auto in_cta = [&](int u) -> bool {
-        if constexpr (PUSH) return aQ[u] < (uint32_t)kC1Threads;
-        else return ((loc >> u) & 1u) != 0u;
-    };
     if (own) {
         int q0 = s.nb_ptr[a], q1 = s.nb_ptr[a + 1];
         const int ntot = q1 - q0;   // the launcher guarantees ntot <= kMaxNb2
@@ -882,10 +866,9 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             gx[u] = e.x;
             gy[u] = e.y;
             if constexpr (PUSH) {
-                aQ[u] = (uint32_t)s.nb_slot[q];   // below kC1Threads: a particle of this CTA
+                aQ[u] = (uint32_t)s.nb_slot[q];
             } else {
-                const int b = __float_as_int(e.w) - s0;   // local index in the body
-                if ((unsigned)(b / kC1Threads) == rank) loc |= 1u << u;
+                int b = __float_as_int(e.w) - s0;   // local index in the body
                 aQ[u] = cl_addr(&sQ[b % kC1Threads], (uint32_t)(b / kC1Threads));
             }
         }
@@ -914,20 +897,15 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     cluster_sync();
 
     // Two accumulator sets (even / odd slots) in both loops, so that a thread
-    // has twice as many independent add chains in flight.  Each loop takes its
-    // entries in two passes, the neighbours in this CTA first, then those in
-    // other CTAs (the same order in every form), so that the first pass can
-    // run while the cluster barrier completes.
-    struct RateAcc {
-        float M0, M1, M2, M3, N0, N1, N2, N3;
-    };
-    auto rate_pass = [&](bool local, float4 va, RateAcc &A, int vo) {
+    // has twice as many independent add chains in flight.
+    auto rate = [&](float4 va, float *Hd, int vo) {   // vo: first slot of the velocity buffer
+        float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, N3 = 0.f;
 #pragma unroll
         for (int c0 = 0; c0 < NB; c0 += CH) {
             float2 vb[CH];
 #pragma unroll
             for (int u = 0; u < CH; u++) {
-                if (c0 + u < nn && in_cta(c0 + u) == local) {
+                if (c0 + u < nn) {
                     if constexpr (PUSH) {
                         const float4 t = sV[vo + aQ[c0 + u]];
                         vb[u] = make_float2(t.x, t.y);
@@ -938,60 +916,30 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
             }
 #pragma unroll
             for (int u = 0; u < CH; u += 2) {
-                if (c0 + u < nn && in_cta(c0 + u) == local) {
+                if (c0 + u < nn) {
                     const float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
-                    A.M0 += dvx * gx[c0 + u];
-                    A.M1 += dvx * gy[c0 + u];
-                    A.M2 += dvy * gx[c0 + u];
-                    A.M3 += dvy * gy[c0 + u];
+                    M0 += dvx * gx[c0 + u];
+                    M1 += dvx * gy[c0 + u];
+                    M2 += dvy * gx[c0 + u];
+                    M3 += dvy * gy[c0 + u];
                 }
-                if (u + 1 < CH && c0 + u + 1 < nn && in_cta(c0 + u + 1) == local) {
+                if (u + 1 < CH && c0 + u + 1 < nn) {
                     const float dvx = vb[u + 1].x - va.x, dvy = vb[u + 1].y - va.y;
-                    A.N0 += dvx * gx[c0 + u + 1];
-                    A.N1 += dvx * gy[c0 + u + 1];
-                    A.N2 += dvy * gx[c0 + u + 1];
-                    A.N3 += dvy * gy[c0 + u + 1];
+                    N0 += dvx * gx[c0 + u + 1];
+                    N1 += dvx * gy[c0 + u + 1];
+                    N2 += dvy * gx[c0 + u + 1];
+                    N3 += dvy * gy[c0 + u + 1];
                 }
             }
         }
-    };
-    auto rate_finish = [&](const RateAcc &A, float *Hd) {
-        const float M0 = pair_sum(A.M0 + A.N0), M1 = pair_sum(A.M1 + A.N1);
-        const float M2 = pair_sum(A.M2 + A.N2), M3 = pair_sum(A.M3 + A.N3);
+        M0 = pair_sum(M0 + N0);
+        M1 = pair_sum(M1 + N1);
+        M2 = pair_sum(M2 + N2);
+        M3 = pair_sum(M3 + N3);
         Hd[0] = M0 * B[0] + M1 * B[2];
         Hd[1] = M0 * B[1] + M1 * B[3];
         Hd[2] = M2 * B[0] + M3 * B[2];
         Hd[3] = M2 * B[1] + M3 * B[3];
-    };
-    auto rate = [&](float4 va, float *Hd, int vo) {
-        RateAcc A = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) rate_pass(pass == 0, va, A, vo);
-        rate_finish(A, Hd);
-    };
-    struct ForceAcc {
-        float ax, ay, bx, by;
-    };
-    auto force_pass = [&](bool local, ForceAcc &A, int qo) {
-#pragma unroll
-        for (int c0 = 0; c0 < NB; c0 += CH) {
-            float4 qb[CH];
-#pragma unroll
-            for (int u = 0; u < CH; u++)
-                if (c0 + u < nn && in_cta(c0 + u) == local)
-                    qb[u] = PUSH ? sQ[qo + aQ[c0 + u]] : ld_cl(aQ[c0 + u]);
-#pragma unroll
-            for (int u = 0; u < CH; u += 2) {
-                if (c0 + u < nn && in_cta(c0 + u) == local) {
-                    A.ax += qb[u].x * gx[c0 + u] + qb[u].y * gy[c0 + u];
-                    A.ay += qb[u].z * gx[c0 + u] + qb[u].w * gy[c0 + u];
-                }
-                if (u + 1 < CH && c0 + u + 1 < nn && in_cta(c0 + u + 1) == local) {
-                    A.bx += qb[u + 1].x * gx[c0 + u + 1] + qb[u + 1].y * gy[c0 + u + 1];
-                    A.by += qb[u + 1].z * gx[c0 + u + 1] + qb[u + 1].w * gy[c0 + u + 1];
-                }
-            }
-        }
     };
     auto put_Q = [&](int buf) {
         float Q[4];
@@ -1014,26 +962,33 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     }
     for (int kk = 0; kk < K; kk++) {
         const int qb_ = kk & 1, vb_ = (kk + 1) & 1;   // buffers of Q^k and v^(k+1) (MB)
-        const int qo = MB ? qb_ * SLOTS : 0;
-        // (B) force loop and kick: stresses of this CTA's neighbours while the
-        // cluster barrier completes (a CTA barrier makes this CTA's own slots
-        // visible), the halo's after it
-        ForceAcc FA = {0.f, 0.f, 0.f, 0.f};
-        if constexpr (MB) {
-            halo_wait(qb_);
-        } else {
-            cluster_arrive();
-            __syncthreads();
-        }
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {   // this CTA's neighbours, then (after the wait) the halo's
-            if (!MB && pass == 1) cluster_wait();
-            if (own) force_pass(pass == 0, FA, qo);
-        }
+        if constexpr (MB) halo_wait(qb_);
+        else cluster_sync();
+        // (B) force loop and kick
         if (own) {
             const float4 Qa = Qown;
-            const float ax = Qa.x * sgx + Qa.y * sgy + pair_sum(FA.ax + FA.bx);
-            const float ay = Qa.z * sgx + Qa.w * sgy + pair_sum(FA.ay + FA.by);
+            const int qo = MB ? qb_ * SLOTS : 0;
+            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+            for (int c0 = 0; c0 < NB; c0 += CH) {
+                float4 qb[CH];
+#pragma unroll
+                for (int u = 0; u < CH; u++)
+                    if (c0 + u < nn) qb[u] = PUSH ? sQ[qo + aQ[c0 + u]] : ld_cl(aQ[c0 + u]);
+#pragma unroll
+                for (int u = 0; u < CH; u += 2) {
+                    if (c0 + u < nn) {
+                        ax += qb[u].x * gx[c0 + u] + qb[u].y * gy[c0 + u];
+                        ay += qb[u].z * gx[c0 + u] + qb[u].w * gy[c0 + u];
+                    }
+                    if (u + 1 < CH && c0 + u + 1 < nn) {
+                        bx += qb[u + 1].x * gx[c0 + u + 1] + qb[u + 1].y * gy[c0 + u + 1];
+                        by += qb[u + 1].z * gx[c0 + u + 1] + qb[u + 1].w * gy[c0 + u + 1];
+                    }
+                }
+            }
+            ax = Qa.x * sgx + Qa.y * sgy + pair_sum(ax + bx);
+            ay = Qa.z * sgx + Qa.w * sgy + pair_sum(ay + by);
             if (!cons) {
                 float4 v = vown;
                 float av0 = ax * inv_rhoS + fF[0] * inv_mS + P.g[0];
@@ -1050,26 +1005,14 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
                 publish(sV, dV, vb_, vown);   // a held particle's copies count towards the transaction too
             }
         }
-        // (C) deformation rate at v^{k+1} (this CTA's neighbours first, as in
-        // B); second half drift; next first half + stress
-        const int vo = MB ? vb_ * SLOTS : 0;
-        RateAcc RA = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if constexpr (MB) {
-            halo_wait(2 + vb_);
-        } else {
-            cluster_arrive();
-            __syncthreads();
-        }
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {
-            if (!MB && pass == 1) cluster_wait();
-            if (own) rate_pass(pass == 0, vown, RA, vo);
-        }
+        if constexpr (MB) halo_wait(2 + vb_);
+        else cluster_sync();
+        // (C) deformation rate at v^{k+1}; second half drift; next first half + stress
         if (own) {
             const bool more = kk + 1 < K;
             const float4 va = vown;
             float Hd[4];
-            rate_finish(RA, Hd);
+            rate(va, Hd, MB ? vb_ * SLOTS : 0);
             // second half drift of this sub-step and, unless it is the last,
             // the first half drift of the next one with the same rate
             const float hH = more ? dts : hdts;
