@@ -246,34 +246,28 @@ __global__ void __launch_bounds__(128) k_pairlist_cells(Batch bt, Fluid f, Walls
         uint32_t *row = f.nbl + (size_t)(act ? i : t0) * cap;
         int nF = 0, nW = 0;
         bool solid = false;
-        // the 3^(d-1) rows of three cells (consecutive in the sorted records,
-        // so a row's candidates are one flat range), cells dx = -1, 0, +1 in
-        // order: the entries come in the same order as cell by cell
-        for_each_row<D>(g, In.c0, cx, cy, cz, [&](const int c[3], float oy, float oz, int code0) {
-            const Row3 rf = row_of(f.cstart, c);
+        for_each_cell<D, 1>(g, In.c0, cx, cy, cz, [&](int c, float ox, float oy, float oz, int code) {
+            const uint32_t rc = row_code(code);
+            const int j1 = f.cstart[c + 1];
 #pragma unroll 4
-            for (int q = 0; q < rf.n; q++) {
-                int k;
-                const int j = row_slot(rf, q, k);
+            for (int j = f.cstart[c]; j < j1; j++) {
                 float d[3];
-                const bool in = rel_d<D>(Pi, f.P4[j], row_ox(k, g), oy, oz, d) < rc2 && j != i && act;
+                const bool in = rel_d<D>(Pi, f.P4[j], ox, oy, oz, d) < rc2 && j != i && act;
                 if (in) {
-                    if (nF < cap) row[nF] = ((uint32_t)j << kCodeBits) | row_code(code0 + k);
+                    if (nF < cap) row[nF] = ((uint32_t)j << kCodeBits) | rc;
                     nF++;
                 }
             }
-            const Row3 rw = row_of(w.cstart, c);
-            for (int q = 0; q < rw.n; q++) {
-                int k;
-                const int a = row_slot(rw, q, k);
+            const int a1 = w.cstart[c + 1];
+            for (int a = w.cstart[c]; a < a1; a++) {
                 float d[3];
-                const bool in = rel_d<D>(Pi, w.A4[a], row_ox(k, g), oy, oz, d) < rc2 && act;
+                const bool in = rel_d<D>(Pi, w.A4[a], ox, oy, oz, d) < rc2 && act;
                 if (in) {
-                    if (nW < cap) row[cap - 1 - nW] = ((uint32_t)a << kCodeBits) | row_code(code0 + k);
+                    if (nW < cap) row[cap - 1 - nW] = ((uint32_t)a << kCodeBits) | rc;
                     nW++;
                 }
             }
-            if (s.n && row_of(s.cstart, c).n > 0) solid = true;
+            if (s.n && s.cstart[c + 1] > s.cstart[c]) solid = true;
         });
         if (act)
             f.nbc[i] = (nF + nW > cap || nF > (int)kListCountMask || nW > (int)kListCountMask)
