@@ -139,3 +139,68 @@ def test_held_graph_replay_and_checkpoint_continue_bitwise():
         c.debug_neighbors(0)
     for s in (a, b, c, d):
         s.close()
+
+
+def test_held_batch_equals_single_instances_bitwise():
+    """A batch of uneven instances with a held configuration (all instances
+    rebuild together, at instance 0's step index) gives, instance by
+    instance, the bits of one context per instance with the same cadence."""
+    cases = [fc.tiny_box(seed=3), fc.floating_block(seed=4), fc.tiny_box(seed=5, nx=12, ny=10)]
+    n, nsteps = 3, 8
+    stream = torch.cuda.Stream()
+    batch = Simulation.from_cases(cases, stream=stream)
+    batch.set_advection_cadence(n)
+    for _ in range(nsteps):
+        batch.step(0.0)
+    batch.sync()
+    for b, case in enumerate(cases):
+        single = Simulation.from_case(case, stream=stream)
+        single.set_advection_cadence(n)
+        for _ in range(nsteps):
+            single.step(0.0)
+        single.sync()
+        got, want = batch.select(b), single
+        for x, y in ((got.get_fluid(), want.get_fluid()), (got.get_solid(), want.get_solid())):
+            for k in x:
+                assert np.array_equal(x[k], y[k]), (b, k)
+        single.close()
+    batch.close()
+
+
+def test_state_setters_rebuild_the_held_configuration():
+    """A state setter in the middle of an advection step makes the next step
+    rebuild the configuration: afterwards the context steps bit for bit like
+    a fresh context loaded with the same state (whose first step builds it);
+    without the rebuild it would keep the old positions' W and grad W."""
+    case = fc.tiny_box(seed=8)
+    ref = O.OracleSim(case)
+    dt, K = _dt_K(ref)
+    n = 4
+
+    def make():
+        sim = Simulation.from_case(case)
+        sim.set_substeps(K)
+        sim.set_advection_cadence(n)
+        return sim
+
+    a = make()
+    for _ in range(n + 2):          # inside the second advection step
+        a.step(dt)
+    a.sync()
+    g, s, t = a.get_fluid(), a.get_solid(), a.info()["t"]
+    g["r"][0] += 0.01 * case.f_dp   # a changed state
+    b = make()
+    for sim in (a, b):
+        sim.set_fluid_state(r=g["r"], v=g["v"], rho=g["rho"], drho=g["drho"])
+        sim.set_solid_state(r=s["r"], v=s["v"], F=s["F"], vbar=s["vbar"], abar=s["abar"], nrm=s["nrm"])
+        sim.set_time(t, 0)
+    for _ in range(2 * n):
+        a.step(dt)
+        b.step(dt)
+    a.sync()
+    b.sync()
+    for x, y in ((a.get_fluid(), b.get_fluid()), (a.get_solid(), b.get_solid())):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+    a.close()
+    b.close()

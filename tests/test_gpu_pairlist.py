@@ -129,3 +129,32 @@ def test_rows_with_the_held_configuration_match_the_oracle(name):
         print(name, k, {q: f"{v:.1e}" for q, v in e.items()})
         assert max(e.values()) < ACC_TOL, (k, e)
         assert info["pairs_ff"] == ref.last["n_ff"] and info["pairs_fw"] == ref.last["n_fw"]
+
+
+@pytest.mark.parametrize("list_lanes", [1, 8])
+def test_rows_in_a_batch_equal_single_instances_bitwise(list_lanes):
+    """Rows in a batch of uneven instances (a cell's instance is found from
+    its first particle; every row indexes its own instance's slots) give,
+    instance by instance, the bits of one context per instance with rows."""
+    cases = [fc.tiny_box(seed=2), fc.channel_flag(seed=1), fc.tiny_box(seed=3, nx=10, ny=14)]
+    stream = torch.cuda.Stream()
+
+    def shaped(sim):
+        sim.set_tuning(4, 128, compact=0, rows=0, list=1, list_lanes=list_lanes)
+        return sim
+
+    batch = shaped(Simulation.from_cases(cases, stream=stream))
+    for _ in range(6):
+        batch.step(0.0)
+    batch.sync()
+    for b, case in enumerate(cases):
+        single = shaped(Simulation.from_case(case, stream=stream))
+        for _ in range(6):
+            single.step(0.0)
+        single.sync()
+        got = batch.select(b)
+        for x, y in ((got.get_fluid(), single.get_fluid()), (got.get_solid(), single.get_solid())):
+            for k in x:
+                assert np.array_equal(x[k], y[k]), (b, k)
+        single.close()
+    batch.close()
