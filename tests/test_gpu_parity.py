@@ -209,12 +209,14 @@ def test_auto_dt_and_substeps_follow_the_criteria():
     assert vmax_prev >= 0
 
 
-def test_gate_tip_parity_1000_steps():
-    """Dam break through the elastic gate at half resolution: the gate-tip
+@pytest.mark.parametrize("dpF", [0.002, 0.001], ids=["half_resolution", "workload_resolution"])
+def test_gate_tip_parity_1000_steps(dpF):
+    """Dam break through the elastic gate (at half resolution, and at the
+    workload's 1 mm with 14k fluid and 1.6k solid particles): the gate-tip
     displacement after 1000 fluid steps matches the oracle within 1e-3
     (relative to max(|u|, 0.01 dp_S))."""
-    case = fc.dam_gate(seed=0, dpF=0.002)
-    ref = O.OracleSim(case)
+    case = fc.dam_gate(seed=0, dpF=dpF)
+    ref = O.OracleSim(case, threaded=True)
     dt, _, dts = ref.suggest_dt(vmax_f=0.0)
     K = ref.substeps(dt, dts)
     sim = Simulation.from_case(case)
