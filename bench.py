@@ -1,7 +1,8 @@
 """Benchmark: one coarse FSI step of the multi-resolution SPH method on GB300.
 
 Default workload (--workload duct_3d): the 3-D channel flow past a clamped
-flexible plate (6 x 2 x 2 duct, periodic in x with a uniform inflow buffer;
+flexible plate (6 x 2 x 2 duct, periodic in x with an inflow buffer of mean
+velocity 1 and the duct profile, zero on the walls;
 plate 1.0 x 0.4 x 0.02 clamped at the floor; dp_F = 0.02, about 3.0M fluid
 particles; dp_S = 0.005, about 65k solid particles, four layers through the
 thickness; 0.5M wall particles; rho_S / rho_F = 10, E = 1e4, Poisson 0.45,
@@ -350,6 +351,10 @@ def run_gpu(args, rank, world, local_rank):
         pairs_timed = sim.pairs_total() - pairs0
         infos = [sim.select(b).info() for b in range(len(cases))]
         info1 = infos[0]
+        if any(i["status"] != 0 for i in infos):
+            # the steps after a run-away state do no work: a rate over them means nothing
+            raise RuntimeError(f"the {label} state ran away during the timed steps (status "
+                               f"{[i['status'] for i in infos]}); no measurement")
         simt_timed = sum(i["t"] for i in infos) - sum(t0s)   # simulated seconds summed over the instances
         # Per-stage device times for the roofline: the same run continues with
         # CUDA events recorded at the stage boundaries inside the step graph
@@ -521,7 +526,8 @@ def run_learned(args, rank, world, local_rank):
             e1.record(st)
             torch.cuda.synchronize()
             tip = sim.get_solid()["r"][case.tip]
-            if not np.all(np.isfinite(tip)) or not np.all(np.abs(tip) < 1e3):
+            # a run-away state stops the context's steps: no timing past it
+            if not np.all(np.isfinite(tip)) or not np.all(np.abs(tip) < 1e3) or sim.info()["status"] != 0:
                 diverged = done + n
                 break
             ms += e0.elapsed_time(e1)
@@ -944,7 +950,7 @@ def e2e_run(cases, dev, steps, tuning, time_stepping="multiple", advection_caden
             sim.add_solid(v["s_r0"], v["s_v0"], v["s_n0"], c.s_cons, c.s_dp, c.s_rho0, c.s_E, c.s_nu)
         if c.inflow_on:
             sim.set_inflow(1, c.inflow_profile, c.inflow_width, c.inflow_y0, c.inflow_H, c.inflow_U, c.inflow_tramp,
-                           c.inflow_period, c.inflow_wo)
+                           c.inflow_period, c.inflow_wo, c.inflow_z0, c.inflow_Hz)
     sim.finalize()
     sim.set_tuning(tuning["lanes"], tuning["block"], tuning["solid_variant"], tuning["compact"], tuning["tile"],
                    tuning["records"], tuning["rows"], tuning["list"], tuning["list_lanes"])

@@ -34,7 +34,8 @@ class Case:
     Lx: float = 0.0
     free_surface: int = 0
     n_reinit: int = 0
-    # inflow buffer (profile 0: parabolic in y over [y0, y0+H]; 1: uniform; 2: Womersley)
+    # inflow buffer (profile 0: parabolic in y over [y0, y0+H]; 1: uniform; 2: Womersley;
+    # 3: parabolic in y and in z over the duct [y0, y0+H] x [z0, z0+Hz])
     inflow_on: int = 0
     inflow_profile: int = 0
     inflow_width: float = 0.0
@@ -44,6 +45,8 @@ class Case:
     inflow_tramp: float = 0.0
     inflow_period: float = 0.0     # profile 2 (Womersley): period T
     inflow_wo: float = 0.0         # profile 2: Womersley number (H/2) sqrt(omega / nu)
+    inflow_z0: float = 0.0         # profile 3: the duct's z range [z0, z0 + Hz]
+    inflow_Hz: float = 0.0
     # bounding box for a fixed cell grid (particles outside are clamped in)
     domain_lo: tuple = (0.0, 0.0, 0.0)
     domain_hi: tuple = (1.0, 1.0, 1.0)
@@ -558,12 +561,17 @@ def venous_valve(seed=0, wo=10.0, DH=4e-3, L_H=8.0, leaflet_H=0.4, angle_deg=60.
 def duct_plate_3d(seed=0, scale=1, jitter_amp=1e-3):
     """3-D channel flow past a clamped flexible plate.
 
-    Duct 6 x 2 x 2 (periodic in x, walls on y and z), uniform inflow of 1
-    through a 4 dp_F buffer, plate 1.0 high x 0.4 span x 0.02 thick normal to
-    the flow, centred 1.5 downstream of the inlet and clamped at the duct floor
-    by 2 rows of constrained particles; rho_S/rho_F = 10, E = 1e4, Poisson 0.45,
-    nu = 0.01 (Re = 100 on the plate height).  scale=1: dp_F = 0.02,
-    dp_S = 0.005; scale=2 doubles both spacings (the 1/8-size copy).
+    Duct 6 x 2 x 2 (periodic in x, walls on y and z), inflow of mean 1
+    through a 4 dp_F buffer with the duct profile (parabolic across y and
+    across z, zero on the four walls; a uniform plug against the no-slip
+    walls ran away at the buffer's corners within 0.2-0.9 s in every setting
+    tried), the fluid starting with that profile, density reinitialisation
+    every 3 steps; plate 1.0 high x 0.4 span x 0.02 thick normal to the
+    flow, centred 1.5 downstream of the inlet and clamped at the duct floor
+    by 2 rows of constrained particles; rho_S/rho_F = 10, E = 1e4, Poisson
+    0.45, nu = 0.01 (Re = 100 on the plate height and the mean velocity),
+    c0 = 15.  scale=1: dp_F = 0.02, dp_S = 0.005; scale=2 doubles both
+    spacings (the 1/8-size copy).
     """
     rng = np.random.default_rng(seed)
     dpF = 0.02 * scale
@@ -595,14 +603,17 @@ def duct_plate_3d(seed=0, scale=1, jitter_amp=1e-3):
     fr = jitter(fr, dpF, jitter_amp, rng)
     sr = jitter(sr, dpS, jitter_amp, rng)
     fr[:, 0] = np.mod(fr[:, 0], L[0])
+    # initial velocity: the inflow profile (mean 1) at every particle's y, z
     fv = np.zeros_like(fr)
-    fv[:, 0] = 1.0
+    fy = 6.0 * fr[:, 1] * (L[1] - fr[:, 1]) / L[1] ** 2
+    fz = 6.0 * fr[:, 2] * (L[2] - fr[:, 2]) / L[2] ** 2
+    fv[:, 0] = np.clip(fy, 0.0, None) * np.clip(fz, 0.0, None)
     free = np.where(cons == 0)[0]
     tip = int(free[np.argmax(sr[free, 1] - 1e-3 * np.abs(sr[free, 2] - 1.0))])
     return Case(
         name="duct_plate_3d", dim=3, gravity=(0.0, 0.0, 0.0), periodic_x=1, x_lo=0.0, Lx=L[0],
-        n_reinit=5, inflow_on=1, inflow_profile=1, inflow_width=4 * dpF, inflow_y0=0.0,
-        inflow_H=L[1], inflow_U=1.0, inflow_tramp=0.0,
+        n_reinit=3, inflow_on=1, inflow_profile=3, inflow_width=4 * dpF, inflow_y0=0.0,
+        inflow_H=L[1], inflow_z0=0.0, inflow_Hz=L[2], inflow_U=1.0, inflow_tramp=0.0,
         domain_lo=(0.0, -6 * dpF, -6 * dpF), domain_hi=(L[0], L[1] + 6 * dpF, L[2] + 6 * dpF),
         f_r=fr, f_v=fv, f_p=np.zeros(len(fr)), f_dp=dpF, f_rho0=1.0, f_c0=15.0, f_eta=0.01,
         w_r=wr, w_n=wn, w_dp=dpF,

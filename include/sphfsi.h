@@ -52,7 +52,7 @@ extern "C" {
 #define SPHFSI_E_NOMEM (-2)    /* device allocation failed                   */
 #define SPHFSI_E_CUDA (-3)     /* a CUDA runtime call failed                 */
 #define SPHFSI_E_STATE (-4)    /* call out of order (e.g. step before finalize) */
-#define SPHFSI_E_UNSTABLE (-5) /* non-finite state detected on the device    */
+#define SPHFSI_E_UNSTABLE (-5) /* run-away (non-finite) state on the device  */
 #define SPHFSI_E_TIMEOUT (-6)  /* a bounded device-side wait ran out         */
 #define SPHFSI_E_CAPACITY (-7) /* problem exceeds a documented device limit  */
 
@@ -94,12 +94,18 @@ typedef struct {
  * g = cosh 2b + cos 2b, w = 2 pi / period:
  * u = U / (w g) [(sinh f1 sin f2 + sinh f2 sin f1) cos wt
  *                + (g - cosh f1 cos f2 - cosh f2 cos f1) sin wt].
- * SPHFSI_E_INVAL (when on) for width <= 0, an unknown profile, H <= 0 with
- * profile 0 or 2, or period or womersley <= 0 with profile 2. */
+ * profile 3 (3-D ducts; the channel profile of Section 4.1 across both
+ * walls' directions, no counterpart in the paper): U = 36 Ubar (y - y0)
+ * (H - (y - y0)) (z - z0) (Hz - (z - z0)) / (H^2 Hz^2), y and z clamped to
+ * the cross-section [y0, y0 + H] x [z0, z0 + Hz]: zero on its four walls,
+ * mean Ubar.  SPHFSI_E_INVAL (when on) for width <= 0, an unknown profile,
+ * H <= 0 with profile 0, 2 or 3, period or womersley <= 0 with profile 2,
+ * or Hz <= 0 or a non-finite z0 with profile 3. */
 typedef struct {
     int32_t on, profile;
     double width, y0, H, U, t_ramp;
     double period, womersley;   /* profile 2 only */
+    double z0, Hz;              /* profile 3 only */
 } sphfsi_inflow;
 
 /* Counters and last-step diagnostics of the selected instance. */
@@ -223,12 +229,21 @@ int sphfsi_step(sphfsi_ctx *c, double dt_F);
 int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F);
 
 /* Wait for the stream; return SPHFSI_E_UNSTABLE / SPHFSI_E_TIMEOUT if the
- * device flagged a non-finite state or a bounded wait ran out in any
+ * device flagged a run-away state or a bounded wait ran out in any
  * instance.  After SPHFSI_E_TIMEOUT the state is not a valid step of the
  * method (the step that gave up was not completed, and when the cell-list
  * scan gave up, that step's and later steps' kernels returned without
  * work): sphfsi_step and sphfsi_run return SPHFSI_E_TIMEOUT without doing
- * anything until sphfsi_set_state restores a checkpoint taken before. */
+ * anything until sphfsi_set_state restores a checkpoint taken before.
+ * A run-away state (no counterpart in the paper) is a step that ended with
+ * a non-finite maximum fluid speed, solid speed or solid acceleration, a
+ * fluid particle faster than the artificial sound speed c0 (outside the
+ * weakly-compressible model), or a solid step more than 10^6 times shorter
+ * than the fluid step.  The steps enqueued after it (in the same graph
+ * replay, or before the sync that reports it) do no work, and from that
+ * sync on sphfsi_step and sphfsi_run return SPHFSI_E_UNSTABLE until
+ * sphfsi_set_state restores a checkpoint taken before; in a batch this
+ * stops every instance. */
 int sphfsi_sync(sphfsi_ctx *c);
 
 /* Bounded device waits (no counterpart in the paper): the grid barrier of the

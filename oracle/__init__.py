@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("n_reinit", C.c_int32), ("inflow_on", C.c_int32), ("inflow_profile", C.c_int32),
                 ("inflow_width", C.c_double), ("inflow_y0", C.c_double), ("inflow_H", C.c_double),
                 ("inflow_U", C.c_double), ("inflow_tramp", C.c_double), ("inflow_period", C.c_double),
-                ("inflow_wo", C.c_double)]
+                ("inflow_wo", C.c_double), ("inflow_z0", C.c_double), ("inflow_Hz", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -143,6 +143,8 @@ def _declare(L):
     L.or_solid_accel.argtypes = [C.POINTER(Params), C.POINTER(Solid), _dp, _dp]
     L.or_inflow_u.restype = C.c_double
     L.or_inflow_u.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
+    L.or_inflow_u3.restype = C.c_double
+    L.or_inflow_u3.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double]
     L.or_step.restype = C.c_int
     L.or_step.argtypes = [C.POINTER(Params), C.POINTER(Fluid), C.POINTER(Wall),
                           C.POINTER(Solid), C.c_double, C.c_int, C.c_double, C.c_int64,
@@ -188,6 +190,7 @@ def make_params(case) -> Params:
     P.inflow_width, P.inflow_y0, P.inflow_H = case.inflow_width, case.inflow_y0, case.inflow_H
     P.inflow_U, P.inflow_tramp = case.inflow_U, case.inflow_tramp
     P.inflow_period, P.inflow_wo = getattr(case, "inflow_period", 0.0), getattr(case, "inflow_wo", 0.0)
+    P.inflow_z0, P.inflow_Hz = getattr(case, "inflow_z0", 0.0), getattr(case, "inflow_Hz", 0.0)
     return P
 
 

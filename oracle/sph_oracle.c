@@ -38,6 +38,8 @@
  *   R22 single-time-step criteria (the paper's baselines, K = 1)
  *   R23 a coincident pair (r = 0) adds nothing
  *   R24 Womersley inflow: the time factors of the printed solution
+ *   R26 inflow of a 3-D duct: the product of the channel profile across y
+ *       and across z (zero on the four walls, mean Ubar)
  *   F2  neighbour lists and kernel values held over an advection step
  *       (Algorithm 1; opt-in through or_step_ex)
  * (R19-R21 and R25 are geometry and workload readings of the input generators.)
@@ -648,6 +650,27 @@ double or_inflow_u(const or_params *P, double y, double t)
     return 6.0 * U * yy * (H - yy) / (H * H);
 }
 
+/* Inflow profile of a 3-D duct, reading R26: the product of the channel
+ * profile across y and across z,
+ * U(y, z) = 36 Ubar (y - y0)(H - (y - y0))(z - z0)(Hz - (z - z0)) / (H^2 Hz^2),
+ * with y and z clamped to the duct's cross-section: mean Ubar over it, zero
+ * on its four walls.  Every other profile depends on y alone. */
+double or_inflow_u3(const or_params *P, double y, double z, double t)
+{
+    if (P->inflow_profile != 3) return or_inflow_u(P, y, t);
+    double U = P->inflow_U;
+    if (P->inflow_tramp > 0.0 && t < P->inflow_tramp) U = 0.5 * U * (1.0 - cos(PI * t / P->inflow_tramp));
+    double H = P->inflow_H, yy = y - P->inflow_y0;
+    double Hz = P->inflow_Hz, zz = z - P->inflow_z0;
+    if (yy < 0.0) yy = 0.0;
+    if (yy > H) yy = H;
+    if (zz < 0.0) zz = 0.0;
+    if (zz > Hz) zz = Hz;
+    double fy = 6.0 * yy * (H - yy) / (H * H);
+    double fz = 6.0 * zz * (Hz - zz) / (Hz * Hz);
+    return U * fy * fz;
+}
+
 static void wrap_x(const or_params *P, double *x)
 {
     if (!P->periodic_x) return;
@@ -720,7 +743,7 @@ int or_step_ex(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, d
         for (int64_t i = 0; i < f->n; i++) {
             double *ri = f->r + i * dim;
             if (ri[0] >= P->x_lo && ri[0] < P->x_lo + P->inflow_width) {
-                f->v[i * dim + 0] = or_inflow_u(P, ri[1], t);
+                f->v[i * dim + 0] = or_inflow_u3(P, ri[1], dim == 3 ? ri[2] : 0.0, t);
                 for (int k = 1; k < dim; k++) f->v[i * dim + k] = 0.0;
             }
         }

@@ -20,6 +20,7 @@ typedef struct {
     int32_t inflow_profile;
     double inflow_width, inflow_y0, inflow_H, inflow_U, inflow_tramp;
     double inflow_period, inflow_wo; /* profile 2: Womersley period T and number Wo */
+    double inflow_z0, inflow_Hz;     /* profile 3: the duct's z range [z0, z0 + Hz] */
 } or_params;
 
 typedef struct {
@@ -67,6 +68,7 @@ int or_solid_setup(const or_params *P, or_solid *s);
 int or_solid_F_from_positions(const or_params *P, const or_solid *s, double *Fout);
 int or_solid_accel(const or_params *P, const or_solid *s, const double *F, double *acc);
 double or_inflow_u(const or_params *P, double y, double t);
+double or_inflow_u3(const or_params *P, double y, double z, double t);
 int or_step(const or_params *P, or_fluid *f, const or_wall *w, or_solid *s, double dt, int K, double t,
             int64_t step_index, or_diag *dg);
 /* Pair configuration frozen over the acoustic steps of one advection step

@@ -37,7 +37,7 @@ class Params(C.Structure):
 class Inflow(C.Structure):
     _fields_ = [("on", C.c_int32), ("profile", C.c_int32), ("width", C.c_double), ("y0", C.c_double),
                 ("H", C.c_double), ("U", C.c_double), ("t_ramp", C.c_double), ("period", C.c_double),
-                ("womersley", C.c_double)]
+                ("womersley", C.c_double), ("z0", C.c_double), ("Hz", C.c_double)]
 
 
 class Info(C.Structure):
@@ -255,9 +255,9 @@ class Simulation:
         _check(lib().sphfsi_add_solid(self.h, self.ns, _ptr(r0), _ptr(v0), _ptr(n0), _ptr(cons), dp, rho0, E,
                                       nu), "sphfsi_add_solid")
 
-    def set_inflow(self, on, profile, width, y0, H, U, t_ramp, period=0.0, womersley=0.0):
+    def set_inflow(self, on, profile, width, y0, H, U, t_ramp, period=0.0, womersley=0.0, z0=0.0, Hz=0.0):
         f = Inflow(int(on), int(profile), float(width), float(y0), float(H), float(U), float(t_ramp),
-                   float(period), float(womersley))
+                   float(period), float(womersley), float(z0), float(Hz))
         _check(lib().sphfsi_set_inflow(self.h, C.byref(f)), "sphfsi_set_inflow")
 
     def finalize(self):
@@ -274,7 +274,8 @@ class Simulation:
         if case.inflow_on:
             self.set_inflow(1, case.inflow_profile, case.inflow_width, case.inflow_y0, case.inflow_H,
                             case.inflow_U, case.inflow_tramp, getattr(case, "inflow_period", 0.0),
-                            getattr(case, "inflow_wo", 0.0))
+                            getattr(case, "inflow_wo", 0.0), getattr(case, "inflow_z0", 0.0),
+                            getattr(case, "inflow_Hz", 0.0))
 
     @classmethod
     def from_case(cls, case, stream=None):

@@ -61,6 +61,7 @@ struct sphfsi_ctx {
     int solid_path = 0;
     int last_status = 0;
     bool failed = false;   // a bounded wait gave up (seen at a sync): no steps until a checkpoint is restored
+    bool runaway = false;  // a step ended non-finite or run away (seen at a sync): likewise
     // per-stage CUDA events (sphfsi_set_profiling), by index: 0 start, 2
     // binning, 1 neighbour rows, 3 reinit, 5 momentum, 6 continuity (main
     // stream); 4 branch start, 7 coupling force done, 8 sub-steps done (side
@@ -349,6 +350,8 @@ int make_inst(const InstHost &h, int D, Inst &d)
     P.in_tramp = h.inflow.t_ramp;
     P.in_T = h.inflow.period;
     P.in_wo = h.inflow.womersley;
+    P.in_z0 = h.inflow.z0;
+    P.in_Hz = h.inflow.Hz;
     return SPHFSI_OK;
 }
 
@@ -466,7 +469,7 @@ const char *sphfsi_strerror(int code)
     case SPHFSI_E_NOMEM: return "device allocation failed";
     case SPHFSI_E_CUDA: return "CUDA runtime error";
     case SPHFSI_E_STATE: return "call out of order";
-    case SPHFSI_E_UNSTABLE: return "non-finite state detected on the device";
+    case SPHFSI_E_UNSTABLE: return "run-away (non-finite) state detected on the device";
     case SPHFSI_E_TIMEOUT: return "bounded device wait timed out";
     case SPHFSI_E_CAPACITY: return "problem exceeds a device limit";
     default: return "unknown error";
@@ -564,9 +567,10 @@ int sphfsi_add_solid(sphfsi_ctx *c, int64_t n, const double *r0, const double *v
 int sphfsi_set_inflow(sphfsi_ctx *c, const sphfsi_inflow *f)
 {
     TRY(check_ctx(c, false));
-    if (!f || (f->on && (!(f->width > 0) || f->profile < 0 || f->profile > 2 ||
+    if (!f || (f->on && (!(f->width > 0) || f->profile < 0 || f->profile > 3 ||
                          (f->profile != 1 && !(f->H > 0)) ||
-                         (f->profile == 2 && (!(f->period > 0) || !(f->womersley > 0))))))
+                         (f->profile == 2 && (!(f->period > 0) || !(f->womersley > 0))) ||
+                         (f->profile == 3 && (!(f->Hz > 0) || !std::isfinite(f->z0))))))
         return SPHFSI_E_INVAL;
     c->ih[c->sel].inflow = *f;
     return SPHFSI_OK;
@@ -1022,6 +1026,7 @@ int sphfsi_step(sphfsi_ctx *c, double dt_F)
     TRY(check_ctx(c, true));
     if (std::isnan(dt_F)) return SPHFSI_E_INVAL;
     if (c->failed) return SPHFSI_E_TIMEOUT;
+    if (c->runaway) return SPHFSI_E_UNSTABLE;
     return enqueue_step(c, dt_F);
 }
 
@@ -1042,6 +1047,7 @@ int sphfsi_run(sphfsi_ctx *c, int64_t nsteps, double dt_F)
     TRY(check_ctx(c, true));
     if (nsteps < 0 || std::isnan(dt_F)) return SPHFSI_E_INVAL;
     if (c->failed) return SPHFSI_E_TIMEOUT;
+    if (c->runaway) return SPHFSI_E_UNSTABLE;
     if (nsteps == 0) return SPHFSI_OK;
     if (c->st == nullptr) {
         // the legacy default stream cannot be captured: plain launches
@@ -1085,7 +1091,10 @@ int sphfsi_sync(sphfsi_ctx *c)
         c->failed = true;
         return SPHFSI_E_TIMEOUT;
     }
-    if (status & ST_NONFINITE) return SPHFSI_E_UNSTABLE;
+    if (status & ST_NONFINITE) {
+        c->runaway = true;
+        return SPHFSI_E_UNSTABLE;
+    }
     return SPHFSI_OK;
 }
 
@@ -1474,10 +1483,11 @@ int sphfsi_set_state(sphfsi_ctx *c, const void *blob, int64_t bytes)
         p += a.second;
     }
     // steps are allowed again unless the checkpoint itself was taken after a
-    // scan that gave up
+    // scan that gave up or a step that ran away
     int fail = 0;
     TRY(cuda_rc(cudaMemcpy(&fail, c->bt.fail, sizeof(int), cudaMemcpyDeviceToHost)));
-    c->failed = fail != 0;
+    c->failed = fail == kFailWait;
+    c->runaway = fail == kFailRunaway;
     c->last_status = 0;
     return SPHFSI_OK;
 }

@@ -16,6 +16,8 @@ namespace sph {
 
 // device status bits (Ctl::status)
 enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+// values of the context's stop word (Batch::fail)
+enum : int { kFailWait = 1, kFailRunaway = 2 };
 
 constexpr int kBlock = 128;           // threads per block of the particle kernels
 // 2-D cluster sub-step kernel: particles per CTA, halo slots per CTA and
@@ -130,6 +132,7 @@ struct Phys {
     int inflow_on, inflow_profile;
     double in_w, in_y0, in_H, in_U, in_tramp;
     double in_T, in_wo;   // Womersley profile: period, Womersley number
+    double in_z0, in_Hz;  // duct profile: the z range [z0, z0 + Hz]
 };
 
 // Per-instance descriptor (device table, one entry per instance).
@@ -285,12 +288,15 @@ struct Batch {
     int B;
     int ncell;                    // total cells
     long long spin;               // iterations of a bounded wait before it gives up (sphfsi_set_wait_limit)
-    // Set when the histogram scan gave up waiting: the cell starts of the step
-    // are then not valid, so every later kernel that reads cell ranges (and the
-    // binning and finish of later steps) returns at once; the host refuses to
-    // step until a checkpoint is restored.  Only the scan writes it, and the
-    // kernels that read it start after the scan has completed, so all their
-    // threads read the same value.
+    // Stops the context's device work: kFailWait when the histogram scan gave
+    // up waiting (the cell starts of the step are then not valid, so every
+    // later kernel that reads cell ranges returns at once), kFailRunaway when
+    // a step ended with a non-finite or run-away state (the finish kernel sets
+    // it; the next step's kernels return at once, so a blown-up state never
+    // reaches the binning, where particles clamped into a few cells would
+    // make the in-cell ranking quadratic).  The host refuses to step until a
+    // checkpoint is restored.  Its writers complete before the kernels that
+    // read it start, so all their threads read the same value.
     int *fail;
 };
 
@@ -334,7 +340,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status, long lo
                 if (++it > spin) {
                     ok = 0;
                     atomicOr(status, ST_TIMEOUT);
-                    if (fail) atomicExch(fail, 1);
+                    if (fail) atomicExch(fail, kFailWait);
                     break;
                 }
                 __nanosleep(64);

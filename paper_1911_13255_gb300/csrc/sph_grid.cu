@@ -66,7 +66,14 @@ __device__ void step_control(const Inst &In, Ctl *ctl, double dt_fixed, int K_fi
     } else if (K_fixed == 0 && In.ns > 0) {
         const double dts = solid_dt(P, ctl->prev_vmaxS, ctl->prev_amaxS);
         double k = floor(dt / dts) + 1.0;          // kappa = [dt_F / dt_S] + 1
-        K = k > 1e6 ? 1000000 : (int)k;
+        // a solid step a million times shorter than the fluid step (or a
+        // non-finite one): the state has run away; one sub-step, and the
+        // finish kernel stops the context
+        if (!(k <= 1e6)) {
+            k = 1.0;
+            ctl->status |= ST_NONFINITE;
+        }
+        K = (int)k;
     }
     ctl->dt_fixed = dt_fixed;
     ctl->K_fixed = K_fixed;
@@ -131,7 +138,12 @@ __global__ void k_finish(Batch bt, int learned, unsigned *gbar, Fluid f)
     if (b >= bt.B) return;
     Ctl *ctl = bt.ctl + b;
     float vF = __uint_as_float(ctl->vmaxF), vS = __uint_as_float(ctl->vmaxS), aS = __uint_as_float(ctl->amaxS);
-    if (!(vF <= 3.0e38f) || !(vS <= 3.0e38f) || !(aS <= 3.0e38f)) ctl->status |= ST_NONFINITE;
+    // non-finite maxima, or a fluid particle faster than the artificial sound
+    // speed (the weakly-compressible model holds for |v| << c0): the state
+    // has run away, and the context's later steps do nothing
+    if (!(vF <= 3.0e38f) || !(vS <= 3.0e38f) || !(aS <= 3.0e38f) || vF > bt.I[b].P.c0)
+        ctl->status |= ST_NONFINITE;
+    if (ctl->status & ST_NONFINITE) atomicCAS(bt.fail, 0, kFailRunaway);
     // the maxima of this step set the next step's dt_F and K
     ctl->prev_vmaxF = vF;
     ctl->prev_vmaxS = vS;
@@ -165,7 +177,7 @@ int launch_finish(const Batch &bt, int learned, unsigned *gbar, const Fluid &f, 
 // fluid: inflow buffer, first half drift (Eq. verlet-first-half), cell key;
 // solid: cell key at the start-of-step position
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double inflow_u(const Phys &P, double y, double t)
+__device__ __forceinline__ double inflow_u(const Phys &P, double y, double z, double t)
 {
     double U = P.in_U;
     if (P.in_tramp > 0.0 && t < P.in_tramp) U = 0.5 * U * (1.0 - cos(3.14159265358979323846 * t / P.in_tramp));
@@ -183,6 +195,14 @@ __device__ __forceinline__ double inflow_u(const Phys &P, double y, double t)
         const double c = sinh(f1) * sin(f2) + sinh(f2) * sin(f1);
         const double q = g - cosh(f1) * cos(f2) - cosh(f2) * cos(f1);
         return U / (w * g) * (c * cos(w * t) + q * sin(w * t));
+    }
+    if (P.inflow_profile == 3) {
+        // a 3-D duct: the channel profile across y times the one across z
+        // (zero on the four walls, mean U over the cross-section)
+        double zz = z - P.in_z0;
+        const double Hz = P.in_Hz;
+        zz = zz < 0.0 ? 0.0 : (zz > Hz ? Hz : zz);
+        return U * (6.0 * yy * (H - yy) / (H * H)) * (6.0 * zz * (Hz - zz) / (Hz * Hz));
     }
     return 6.0 * U * yy * (H - yy) / (H * H);
 }
@@ -223,7 +243,7 @@ __device__ __forceinline__ void bin_one(const Batch &bt, const Fluid &f, const S
             const double dt = step_dt(In, ctl, dt_fixed, K_fixed), tm = ctl->t;
             float vx = S.vx[i], vy = S.vy[i], vz = D == 3 ? S.vz[i] : 0.0f;
             if (P.inflow_on && x >= g.x_lo && x < g.x_lo + P.in_w) {   // inflow buffer (reading R18)
-                vx = (float)inflow_u(P, y, tm);
+                vx = (float)inflow_u(P, y, z, tm);
                 vy = 0.0f;
                 vz = 0.0f;
                 S.vx[i] = vx;
@@ -441,7 +461,7 @@ __global__ void __launch_bounds__(kScanLbThreads) k_scan_lb(Batch bt, Fluid f, S
                     if (it >= bt.spin) {
                         // this tile's prefix is unknown: the step's cell starts are invalid
                         atomicOr(&bt.ctl[b].status, ST_TIMEOUT);
-                        atomicExch(bt.fail, 1);
+                        atomicExch(bt.fail, kFailWait);
                         break;
                     }
                     continue;

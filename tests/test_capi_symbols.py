@@ -90,7 +90,11 @@ def test_time_stepping_and_inflow_checks_without_gpu():
              ((1, 2, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 5.0), -1),    # no period
              ((1, 2, 0.1, 0.0, 1.0, 2.5, 0.0, 0.6, 0.0), -1),    # no Womersley number
              ((1, 2, 0.1, 0.0, 0.0, 2.5, 0.0, 0.6, 5.0), -1),    # no channel height
-             ((1, 3, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0), -1),    # unknown profile
+             ((1, 4, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0), -1),    # unknown profile
+             ((1, 3, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0, 0.0, 1.0), 0),         # duct
+             ((1, 3, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0, 0.0, 0.0), -1),        # duct without its z extent
+             ((1, 3, 0.1, 0.0, 1.0, 2.5, 0.0, 0.0, 0.0, float("nan"), 1.0), -1),  # non-finite z0
+             ((1, 3, 0.1, 0.0, 0.0, 2.5, 0.0, 0.0, 0.0, 0.0, 1.0), -1),        # duct without its height
              ((1, 0, 0.0, 0.0, 1.0, 1.0, 0.0, 0.0, 0.0), -1),    # no buffer
              ((1, 1, 0.1, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0), 0),     # uniform: no height needed
              ((0, 7, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0), 0)]     # off: not checked

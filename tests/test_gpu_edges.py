@@ -128,6 +128,45 @@ def test_a_non_finite_state_is_reported():
     assert sim.info()["status"] != 0
 
 
+@pytest.mark.parametrize("how", ["nan", "faster_than_c0"])
+def test_a_run_away_state_stops_the_context_until_a_checkpoint_is_restored(how):
+    """A step that ends non-finite, or with a fluid particle faster than c0,
+    stops the context: steps enqueued after it do no work (the step counter
+    stays), later steps are refused, and restoring a checkpoint taken before
+    lets the context step again to the same result as before."""
+    case = fc.tiny_box(seed=8)
+    sim = Simulation.from_case(case)
+    sim.step(0.0)
+    sim.sync()
+    blob = sim.get_state()
+    sim.step(0.0)
+    sim.sync()
+    ref = sim.get_fluid()
+    sim.set_state(blob)
+    v = sim.get_fluid()["v"].astype(np.float64)
+    v[len(v) // 2, 0] = np.nan if how == "nan" else 2.0 * case.f_c0
+    sim.set_fluid_state(v=v)
+    sim.step(0.0)
+    sim.run(3, 0.0)   # enqueued before the sync that reports the run-away
+    with pytest.raises(SphError) as e:
+        sim.sync()
+    assert e.value.code == -5
+    assert sim.info()["status"] != 0
+    assert sim.info()["step"] == 2   # the run-away step completed; the three after it did nothing
+    with pytest.raises(SphError) as e:
+        sim.step(0.0)
+    assert e.value.code == -5
+    with pytest.raises(SphError):
+        sim.run(1, 0.0)
+    sim.set_state(blob)
+    sim.step(0.0)
+    sim.sync()
+    g = sim.get_fluid()
+    assert sim.info()["step"] == 2 and sim.info()["status"] == 0
+    assert np.array_equal(g["v"], ref["v"]) and np.array_equal(g["r"], ref["r"])
+    sim.close()
+
+
 def test_coincident_particles():
     """A fluid particle on top of another and one on top of a solid particle:
     the pair has no direction and adds nothing on either side (the oracle's

@@ -61,6 +61,6 @@ def test_womersley_inflow_rejected_without_its_parameters():
     with pytest.raises(SphError):
         sim.set_inflow(1, 2, case.inflow_width, 0.0, case.inflow_H, case.inflow_U, 0.0, 0.0, 5.0)
     with pytest.raises(SphError):
-        sim.set_inflow(1, 3, case.inflow_width, 0.0, case.inflow_H, case.inflow_U, 0.0)
+        sim.set_inflow(1, 4, case.inflow_width, 0.0, case.inflow_H, case.inflow_U, 0.0)
     sim.set_inflow(1, 2, case.inflow_width, 0.0, case.inflow_H, case.inflow_U, 0.0, 0.6, 5.0)
     sim.close()

@@ -670,6 +670,68 @@ def test_inflow_buffer_sets_exactly_the_particles_inside_it():
     assert np.array_equal(s.f_v[~inb], v0[~inb])
 
 
+def _duct_params(H=2.0, Hz=1.5, y0=0.3, z0=-0.2, U=1.0):
+    c = fc.tiny_box_3d()
+    P = O.make_params(c)
+    P.inflow_on, P.inflow_profile, P.inflow_U, P.inflow_tramp = 1, 3, U, 0.0
+    P.inflow_y0, P.inflow_H, P.inflow_z0, P.inflow_Hz = y0, H, z0, Hz
+    return P
+
+
+def test_duct_inflow_profile_closed_forms():
+    """Reading R26 on a rectangular cross-section (H != Hz, both origins
+    off zero, so a swapped axis, extent or origin fails): the mean over the
+    cross-section is Ubar (2-D quadrature), the value is 0 on all four walls
+    and 36/16 Ubar at the centre, it is symmetric about both mid-planes,
+    separable (u(y, z) u(yc, zc) = u(y, zc) u(yc, z)), clamped outside the
+    section, and follows the ramp; profiles other than 3 ignore z."""
+    H, Hz, y0, z0 = 2.0, 1.5, 0.3, -0.2
+    P = _duct_params(H, Hz, y0, z0, U=1.3)
+    u = lambda y, z, t=10.0: O.lib().or_inflow_u3(P, y, z, t)
+    mean, _ = integrate.dblquad(lambda z, y: u(y, z), y0, y0 + H, z0, z0 + Hz, epsabs=1e-13, epsrel=1e-13)
+    assert abs(mean / (H * Hz) - 1.3) < 1e-12
+    yc, zc = y0 + H / 2, z0 + Hz / 2
+    assert abs(u(yc, zc) - 1.3 * 2.25) < 1e-12
+    for y in np.linspace(y0, y0 + H, 7):   # (y0 + H) - y0 rounds: zero to round-off
+        assert abs(u(y, z0)) < 1e-14 and abs(u(y, z0 + Hz)) < 1e-14
+    for z in np.linspace(z0, z0 + Hz, 7):
+        assert abs(u(y0, z)) < 1e-14 and abs(u(y0 + H, z)) < 1e-14
+    rng = np.random.default_rng(3)
+    for y, z in zip(rng.uniform(y0, y0 + H, 20), rng.uniform(z0, z0 + Hz, 20)):
+        assert abs(u(y, z) - u(2 * yc - y, z)) < 1e-12 and abs(u(y, z) - u(y, 2 * zc - z)) < 1e-12
+        assert abs(u(y, z) * u(yc, zc) - u(y, zc) * u(yc, z)) < 1e-12
+        # across y alone: the channel profile of reading R18 (6 y (H - y) / H^2), times 1.5 at mid-z
+        assert abs(u(y, zc) - 1.3 * 1.5 * 6.0 * (y - y0) * (H - (y - y0)) / H ** 2) < 1e-12
+    assert u(y0 - 0.5, zc) == 0.0 and u(yc, z0 + Hz + 0.5) == 0.0
+    P.inflow_tramp = 2.0
+    assert abs(u(yc, zc, 1.0) - 0.5 * 1.3 * 2.25) < 1e-12
+    P.inflow_profile = 0
+    assert O.lib().or_inflow_u3(P, yc, 123.0, 10.0) == O.lib().or_inflow_u(P, yc, 10.0)
+
+
+def test_duct_inflow_buffer_sets_exactly_the_particles_inside_it():
+    """The 3-D counterpart of the buffer test above: with dt = 0, fluid
+    particles with x in [x_lo, x_lo + width) carry (U(y, z, t), 0, 0) with
+    the duct profile evaluated at their own y and z, every other particle
+    keeps its velocity bit for bit."""
+    case = fc.tiny_box_3d(seed=2)
+    L = case.f_r.max(0) + 0.5 * case.f_dp
+    case.inflow_on, case.inflow_profile, case.inflow_U, case.inflow_tramp = 1, 3, 0.7, 0.5
+    case.inflow_width, case.x_lo = 3 * case.f_dp, 0.0
+    case.inflow_y0, case.inflow_H, case.inflow_z0, case.inflow_Hz = 0.0, float(L[1]), 0.0, float(L[2])
+    s = O.OracleSim(case)
+    s.t = 0.25
+    r0, v0 = s.f_r.copy(), s.f_v.copy()
+    s.step(0.0, 1)
+    inb = (r0[:, 0] >= case.x_lo) & (r0[:, 0] < case.x_lo + case.inflow_width)
+    assert 20 < inb.sum() < case.nf // 2
+    P = O.make_params(case)
+    u = np.array([O.lib().or_inflow_u3(P, y, z, 0.25) for y, z in r0[inb, 1:3]])
+    assert len(np.unique(np.round(u, 12))) > 5   # the profile varies across the buffer
+    assert np.array_equal(s.f_v[inb, 0], u) and np.all(s.f_v[inb, 1:] == 0.0)
+    assert np.array_equal(s.f_v[~inb], v0[~inb])
+
+
 # --------------------------------------------------------------------------
 # Womersley inflow (Appendix A, reading R24)
 # --------------------------------------------------------------------------
