@@ -222,9 +222,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls
 // warp (one broadcast load) and each lane tests its own particle against it
 // and appends to its own row, so the entries come in the same order as
 // above (fluid by cell, then slot, from the front; walls likewise from the
-// back).  Cells of more than 32 particles take several rounds.
+// back).  Cells of more than 32 particles take several rounds.  16 resident
+// blocks per SM (32 registers a thread): the build is issue- and
+// load-latency bound, and the extra warps outweigh a few spilled registers
+// (3-D duct: 2.37 -> 2.32 ms; 56-register pair loops, by contrast, ran
+// slower than at 64).
 template <int D>
-__global__ void __launch_bounds__(128) k_pairlist_cells(Batch bt, Fluid f, Walls w, Solid s)
+__global__ void __launch_bounds__(128, 16) k_pairlist_cells(Batch bt, Fluid f, Walls w, Solid s)
 {
     pdl_enter();
     if (step_failed(bt)) return;   // the step's cell starts are not valid
