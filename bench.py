@@ -154,6 +154,7 @@ class ClockSampler:
 KERNEL_SOURCE = {"k_momentum": "sph_fluid.cu", "k_solid_fluid_force": "sph_fluid.cu",
                  "k_density": "sph_density.cu", "k_reinit": "sph_density.cu",
                  "k_solid_cluster2d_one": "sph_solid.cu", "k_solid_cluster2d": "sph_solid.cu",
+                 "k_solid_cluster2d_1b": "sph_solid.cu",
                  "k_solid_cluster_one": "sph_solid.cu", "k_solid_cluster": "sph_solid.cu",
                  "k_solid_substeps": "sph_solid.cu", "k_gemm_bf16": "sph_learn_gemm.cu",
                  "k_pairlist": "sph_fluid.cu"}
@@ -417,13 +418,13 @@ def run_gpu(args, rank, world, local_rank):
         solid_kernel = "k_solid_cluster2d" if two_d else "k_solid_cluster"
     else:
         solid_kernel = {1: "k_solid_cluster2d_one" if two_d else "k_solid_cluster_one",
-                        2: "k_solid_substeps"}.get(info1["solid_path"], "k_solid_substeps")
+                        2: "k_solid_substeps", 3: "k_solid_cluster2d_1b"}.get(info1["solid_path"], "k_solid_substeps")
     kernel_names = {"solid_substeps": solid_kernel, "momentum": "k_momentum", "continuity": "k_density",
                     "neighbour_rows": "k_pairlist",
                     "solid_fluid_force": "k_solid_fluid_force", "reinit": "k_reinit",
                     "bin_sort": "k_bin_all+k_scan_seg+k_scatter2+k_cell_records"}
     extra = {}
-    if dom == "solid_substeps" and info1["solid_path"] == 1 and case.dim == 2:
+    if dom == "solid_substeps" and info1["solid_path"] in (1, 3) and case.dim == 2:
         # one cluster per body, one CTA of 128 threads per 128 particles: the
         # kernel can only ever use that many SMs
         ctas = (max(c.ns for c in cases) + 127) // 128

@@ -122,7 +122,8 @@ typedef struct {
     double vmax_f, vmax_s, amax_s;  /* reductions of the last step               */
     double mom_fs_fluid[3];  /* sum of fluid-side fluid-solid forces, last step  */
     double mom_fs_solid[3];  /* sum of solid-side fluid forces, last step        */
-    int32_t solid_path;      /* 1 = cluster-resident sub-steps, 2 = cooperative grid */
+    int32_t solid_path;      /* 1 = cluster-resident sub-steps, 2 = cooperative grid,
+                                3 = cluster-resident, one cluster barrier per sub-step */
     int32_t kernels_per_step; /* this library's kernel launches per step        */
     int64_t learned_accepted; /* steps whose learned solid step was accepted    */
     int64_t learned_rejected; /* steps that fell back to the plain sub-steps    */
@@ -355,7 +356,11 @@ typedef struct {
                               the neighbours across the cluster in every phase; 4 one thread
                               per particle whose halo copies (below) are refreshed by
                               asynchronous remote stores that each CTA awaits on its own
-                              mbarriers instead of cluster barriers (measured slower).  0 and
+                              mbarriers instead of cluster barriers (measured slower); 5 (a
+                              single body, else as 0) one cluster barrier per sub-step instead
+                              of two: each CTA also evolves copies of the particles its own
+                              particles read (one extra thread each) and computes their
+                              stresses itself, so only velocities cross the cluster.  0 and
                               2 keep copies of the neighbours from other CTAs in each CTA,
                               refreshed by their owners' remote stores and ordered by the
                               cluster barrier between phases, where they fit, else they read

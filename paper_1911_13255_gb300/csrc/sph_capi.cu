@@ -592,6 +592,11 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
     std::vector<std::vector<int2>> pushes(ns);
     std::vector<int> halo_n(c->ih.size() * 16, 0);
     bool ok = true;
+    // one-barrier form: per (instance, CTA) its halo particles with their
+    // entries' velocity slots, and every particle's velocity copies
+    std::vector<int> h1_ptr(c->ih.size() * 16 + 1, 0), h1_part, h1_eptr(1, 0), h1_vslot;
+    std::vector<std::vector<int2>> push2(ns);
+    bool one_ok = true;
     for (size_t bi = 0; bi < c->ih.size(); bi++) {
         auto &h = c->ih[bi];
         const int s0 = h.d.s0, n = h.d.ns;
@@ -621,6 +626,35 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
             for (size_t k = 0; k < halo_of[r].size(); k++)
                 pushes[s0 + halo_of[r][k]].push_back(make_int2(r, kSolidCta + (int)k));
         }
+        // the velocity copies of CTA r: its halo in the same slots, then the
+        // other CTAs' neighbours of its halo particles, in order of first use
+        for (int r = 0; r < ctas && r < 16; r++) {
+            std::vector<int> vh = halo_of[r];
+            std::unordered_map<int, int> at = where[r];
+            if ((int)halo_of[r].size() > kSolidCta) one_ok = false;
+            for (int lb : halo_of[r]) {
+                h1_part.push_back(s0 + lb);
+                for (int q = ptr[s0 + lb]; q < ptr[s0 + lb + 1]; q++) {
+                    const int lc = nbi[q] - s0;
+                    if (lc / kSolidCta == r) {
+                        h1_vslot.push_back(lc % kSolidCta);
+                        continue;
+                    }
+                    auto it = at.find(lc);
+                    if (it == at.end()) {
+                        it = at.emplace(lc, kSolidCta + (int)vh.size()).first;
+                        vh.push_back(lc);
+                    }
+                    h1_vslot.push_back(it->second);
+                }
+                h1_eptr.push_back((int)h1_vslot.size());
+            }
+            h1_ptr[bi * 16 + r + 1] = (int)h1_part.size();
+            if ((int)vh.size() > kHaloMax) one_ok = false;
+            for (size_t k = 0; k < vh.size(); k++) push2[s0 + vh[k]].push_back(make_int2(r, kSolidCta + (int)k));
+        }
+        for (int r = ctas; r < 16; r++) h1_ptr[bi * 16 + r + 1] = (int)h1_part.size();
+        if (ctas > 16) one_ok = false;
     }
     std::vector<int> pptr(ns + 1, 0);
     std::vector<int2> pl;
@@ -630,6 +664,29 @@ int halo_maps(sphfsi_ctx *c, const std::vector<int> &ptr, const std::vector<int>
         pl.insert(pl.end(), pushes[a].begin(), pushes[a].end());
     }
     if (pl.empty()) pl.push_back(make_int2(0, 0));
+    std::vector<int> p2ptr(ns + 1, 0);
+    std::vector<int2> p2;
+    for (int64_t a = 0; a < ns; a++) {
+        if ((int)push2[a].size() > kPushMax) one_ok = false;
+        p2ptr[a + 1] = p2ptr[a] + (int)push2[a].size();
+        p2.insert(p2.end(), push2[a].begin(), push2[a].end());
+    }
+    if (p2.empty()) p2.push_back(make_int2(0, 0));
+    if (h1_part.empty()) h1_part.push_back(0);
+    if (h1_vslot.empty()) h1_vslot.push_back(0);
+    TRY(dalloc(c, &S.h1_ptr, h1_ptr.size()));
+    TRY(upload(c, S.h1_ptr, h1_ptr));
+    TRY(dalloc(c, &S.h1_part, h1_part.size()));
+    TRY(upload(c, S.h1_part, h1_part));
+    TRY(dalloc(c, &S.h1_eptr, h1_eptr.size()));
+    TRY(upload(c, S.h1_eptr, h1_eptr));
+    TRY(dalloc(c, &S.h1_vslot, h1_vslot.size()));
+    TRY(upload(c, S.h1_vslot, h1_vslot));
+    TRY(dalloc(c, &S.push2_ptr, p2ptr.size()));
+    TRY(upload(c, S.push2_ptr, p2ptr));
+    TRY(dalloc(c, &S.push2, p2.size()));
+    TRY(upload(c, S.push2, p2));
+    S.one_ok = one_ok && ok ? 1 : 0;
     TRY(dalloc(c, &S.nb_slot, slot.size()));
     TRY(upload(c, S.nb_slot, slot));
     TRY(dalloc(c, &S.push_ptr, pptr.size()));
@@ -1613,7 +1670,7 @@ int sphfsi_set_tuning(sphfsi_ctx *c, const sphfsi_tuning *t)
 {
     TRY(check_ctx(c, true));
     if (!t || !valid_lanes(c->dim, t->lanes) || (t->block != 64 && t->block != 128 && t->block != 256) ||
-        t->solid_variant < 0 || t->solid_variant > 4 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
+        t->solid_variant < 0 || t->solid_variant > 5 || t->compact < 0 || t->compact > 1 || t->tile < 0 ||
         t->tile > 1 || t->records < 0 || t->records > 2 || t->rows < 0 || t->rows > 1 || (t->rows && t->tile) ||
         (c->max_reach > 1 && (t->rows || t->tile)) || t->list < 0 || t->list > 1 ||
         (t->list && (t->tile || c->max_reach > 1)) ||
@@ -1763,7 +1820,7 @@ int sphfsi_autotune(sphfsi_ctx *c, double dt_F, int32_t steps, sphfsi_tuning *be
         }
         cur = *best;
         if (!rc && c->dim == 2 && c->S.n && !c->S.force_grid_path) {
-            for (int v = 0; v < 5 && !rc; v++) {
+            for (int v = 0; v < 6 && !rc; v++) {
                 if (v == best->solid_variant) continue;
                 cur.solid_variant = v;
                 rc = consider(cur);

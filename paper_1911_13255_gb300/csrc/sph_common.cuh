@@ -268,6 +268,18 @@ struct Solid {
     int2 *push;               // (CTA rank, slot) of each copy
     int *halo_n;              // [instance * 16 + CTA]: halo slots of each CTA of each body
     int push_ok;              // 1: every halo and push list fits the kernel's limits
+    // one-barrier form (single body): CTA r also computes the stresses of its
+    // halo particles itself (one extra thread each), so only velocities cross
+    // the cluster; its velocity copies then cover the neighbours of its halo
+    // particles too (slots kSolidCta + the halo's own numbering, then the
+    // second ring)
+    int *h1_ptr;              // [instance * 16 + CTA] + 1: the CTA's halo particles in h1_part
+    int *h1_part;             // body-local index of each halo particle
+    int *h1_eptr;             // per halo particle: its entries' first index in h1_vslot
+    int *h1_vslot;            // velocity slot, in the computing CTA, of each entry's neighbour
+    int *push2_ptr;           // n + 1: a particle's velocity copies in other CTAs
+    int2 *push2;              // (CTA rank, slot) of each velocity copy
+    int one_ok;               // 1: halos of at most kSolidCta particles, copies and push lists fit
     int max_nb;               // largest static neighbour count of a particle
     int max_ns;               // largest body of an instance
     // learned sub-stepper (when learned != 0)

@@ -1046,6 +1046,255 @@ __device__ __forceinline__ void solid2d_body(const Solid &s, const Phys &P, Ctl 
     cluster_sync();
 }
 
+// One-barrier form of the single-body 2-D sub-steps (solid variant 5).  A
+// CTA runs 2 kC1Threads threads: thread t < kC1Threads owns particle t of
+// the CTA's part of the body, thread kC1Threads + h carries a copy of halo
+// particle h (a particle of another CTA that an own particle reads).  Every
+// copy evolves its particle's displacement gradient with the same code and
+// the same inputs as the owner, so its stress is the owner's bit for bit,
+// and the stresses never cross the cluster.  Only velocities do: after the
+// kick each own particle writes its velocity to the copies other CTAs hold
+// of it (their halos and the neighbours of their halo particles), into one
+// of two buffers by sub-step parity.  Per sub-step: force loop and kick
+// (own), cluster barrier (the new velocities visible), deformation rate and
+// stress (own and halo copies, local reads only), CTA barrier.  A buffer is
+// rewritten one sub-step after its last read, and every reader passed a
+// cluster barrier in between, so no copy is overwritten while read.
+template <bool EARLY>
+__device__ __forceinline__ void solid2d_body_1b(const Solid &s, const Phys &P, Ctl *ctl, int ns, float4 *sQ,
+                                                float4 *sV, unsigned rank)
+{
+    constexpr int NB = kMaxNb2, CH = kChunk2;
+    constexpr int VS = kC1Threads + kHaloMax;   // one velocity buffer
+    const int t = threadIdx.x;
+    const int la = (int)rank * kC1Threads + t;
+    const int h0 = s.h1_ptr[rank], hn = s.h1_ptr[rank + 1] - h0, hi = t - kC1Threads;
+    const bool mine = t < kC1Threads && la < ns;      // an own particle
+    const bool copy = t >= kC1Threads && hi < hn;     // a halo particle's copy
+    const bool live = mine || copy;
+    const int a = mine ? la : (copy ? s.h1_part[h0 + hi] : 0);
+    const int self = mine ? t : kC1Threads + hi;      // its slot in sQ and sV
+    if (ctl->learned_ok) return;   // the learned step was accepted: no sub-steps
+    const int K = ctl->K;
+    const double dt = ctl->dt, dtsd = ctl->dts, hdtsd = 0.5 * dtsd;
+    const float dts = (float)dtsd, hdts = 0.5f * dts;
+    const float inv_rhoS = 1.0f / P.rhoS, inv_mS = 1.0f / P.mS;
+
+    float H[4] = {0, 0, 0, 0}, B[4] = {1, 0, 0, 1}, fF[2] = {0, 0};
+    double x = 0, y = 0, xs = 0, ys = 0, as0 = 0, as1 = 0;
+    bool cons = true;
+    float vmax = 0.0f, amax = 0.0f;
+    float4 vown = make_float4(0.f, 0.f, 0.f, 0.f), Qown = vown;
+    float gx[NB], gy[NB];
+    int sl[NB];              // the neighbour's slot: own or halo (stress and velocity), or second ring (velocity)
+    uint32_t pq[kPushMax];   // cluster addresses of this particle's velocity copies (buffer 0)
+    int npush = 0, nn = 0;
+    if (live) {
+        const int q0 = s.nb_ptr[a];
+        nn = s.nb_ptr[a + 1] - q0;   // the launcher guarantees nn <= kMaxNb2
+        for (int i = 0; i < 4; i++) {
+            H[i] = s.H[9 * a + i];
+            B[i] = s.B0[9 * a + i];
+        }
+        const int e0 = mine ? q0 : s.h1_eptr[h0 + hi];
+#pragma unroll
+        for (int u = 0; u < NB; u++) {
+            gx[u] = gy[u] = 0.0f;
+            sl[u] = 0;
+            if (u < nn) {
+                const float4 e = s.nb[q0 + u];
+                gx[u] = e.x;
+                gy[u] = e.y;
+                sl[u] = mine ? s.nb_slot[q0 + u] : s.h1_vslot[e0 + u];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < NB; u++) {
+            gx[u] = gy[u] = 0.0f;
+            sl[u] = 0;
+        }
+    }
+    if (mine) {
+        x = xs = s.x[a];
+        y = ys = s.y[a];
+        cons = s.cons[a] != 0;
+        vown = s.v4[a];
+        const int p0 = s.push2_ptr[a];
+        npush = s.push2_ptr[a + 1] - p0;   // <= kPushMax when this form runs
+#pragma unroll
+        for (int k = 0; k < kPushMax; k++) {
+            pq[k] = 0u;
+            if (k < npush) {
+                const int2 e = s.push2[p0 + k];
+                pq[k] = cl_addr(&sV[e.y], (uint32_t)e.x);
+            }
+        }
+    }
+    auto publish_v = [&](int buf, const float4 &v) {
+        sV[buf * VS + t] = v;
+#pragma unroll
+        for (int k = 0; k < kPushMax; k++)
+            if (k < npush) st_cl(pq[k] + (uint32_t)(buf * VS * 16), v);
+    };
+    // v^0 into both buffers: a held particle never writes its copies again
+    if (mine) {
+        publish_v(0, vown);
+        publish_v(1, vown);
+    }
+    float sgx = 0.f, sgy = 0.f;
+#pragma unroll
+    for (int u = 0; u < NB; u++) {
+        sgx += gx[u];
+        sgy += gy[u];
+    }
+    if constexpr (EARLY) pdl_wait();
+    if (mine) {
+        fF[0] = s.fF[3 * a];
+        fF[1] = s.fF[3 * a + 1];
+    }
+    cluster_sync();
+
+    // the deformation rate and the stress: the push form's arithmetic in the
+    // same order (two accumulator sets, even / odd entries)
+    auto rate = [&](float4 va, float *Hd, int vo) {
+        float M0 = 0.f, M1 = 0.f, M2 = 0.f, M3 = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, N3 = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < NB; c0 += CH) {
+            float2 vb[CH];
+#pragma unroll
+            for (int u = 0; u < CH; u++) {
+                if (c0 + u < nn) {
+                    const float4 w = sV[vo + sl[c0 + u]];
+                    vb[u] = make_float2(w.x, w.y);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; u += 2) {
+                if (c0 + u < nn) {
+                    const float dvx = vb[u].x - va.x, dvy = vb[u].y - va.y;
+                    M0 += dvx * gx[c0 + u];
+                    M1 += dvx * gy[c0 + u];
+                    M2 += dvy * gx[c0 + u];
+                    M3 += dvy * gy[c0 + u];
+                }
+                if (u + 1 < CH && c0 + u + 1 < nn) {
+                    const float dvx = vb[u + 1].x - va.x, dvy = vb[u + 1].y - va.y;
+                    N0 += dvx * gx[c0 + u + 1];
+                    N1 += dvx * gy[c0 + u + 1];
+                    N2 += dvy * gx[c0 + u + 1];
+                    N3 += dvy * gy[c0 + u + 1];
+                }
+            }
+        }
+        M0 = M0 + N0;
+        M1 = M1 + N1;
+        M2 = M2 + N2;
+        M3 = M3 + N3;
+        Hd[0] = M0 * B[0] + M1 * B[2];
+        Hd[1] = M0 * B[1] + M1 * B[3];
+        Hd[2] = M2 * B[0] + M3 * B[2];
+        Hd[3] = M2 * B[1] + M3 * B[3];
+    };
+    auto put_Q = [&]() {
+        float Q[4];
+        stress_QB<2>(H, B, P.mu, P.lam, Q);
+        Qown = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        sQ[self] = Qown;
+    };
+
+    if (live) {
+        const float4 va = mine ? vown : sV[self];
+        float Hd[4];
+        rate(va, Hd, 0);
+        for (int i = 0; i < 4; i++) H[i] = H[i] + hdts * Hd[i];
+        if (mine && !cons) {
+            x = x + hdtsd * (double)va.x;
+            y = y + hdtsd * (double)va.y;
+        }
+        put_Q();
+    }
+    __syncthreads();
+    for (int kk = 0; kk < K; kk++) {
+        const int vb_ = (kk + 1) & 1;   // the buffer of v^(k+1)
+        // (B) force loop and kick: own particles, stresses from local slots
+        if (mine) {
+            const float4 Qa = Qown;
+            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+#pragma unroll
+            for (int c0 = 0; c0 < NB; c0 += CH) {
+                float4 qb[CH];
+#pragma unroll
+                for (int u = 0; u < CH; u++)
+                    if (c0 + u < nn) qb[u] = sQ[sl[c0 + u]];
+#pragma unroll
+                for (int u = 0; u < CH; u += 2) {
+                    if (c0 + u < nn) {
+                        ax += qb[u].x * gx[c0 + u] + qb[u].y * gy[c0 + u];
+                        ay += qb[u].z * gx[c0 + u] + qb[u].w * gy[c0 + u];
+                    }
+                    if (u + 1 < CH && c0 + u + 1 < nn) {
+                        bx += qb[u + 1].x * gx[c0 + u + 1] + qb[u + 1].y * gy[c0 + u + 1];
+                        by += qb[u + 1].z * gx[c0 + u + 1] + qb[u + 1].w * gy[c0 + u + 1];
+                    }
+                }
+            }
+            ax = Qa.x * sgx + Qa.y * sgy + (ax + bx);
+            ay = Qa.z * sgx + Qa.w * sgy + (ay + by);
+            if (!cons) {
+                float4 v = vown;
+                float av0 = ax * inv_rhoS + fF[0] * inv_mS + P.g[0];
+                float av1 = ay * inv_rhoS + fF[1] * inv_mS + P.g[1];
+                v.x += dts * av0;
+                v.y += dts * av1;
+                vown = v;
+                publish_v(vb_, v);
+                as0 += dtsd * (double)av0;
+                as1 += dtsd * (double)av1;
+                amax = max_keep_nan(amax, av0 * av0 + av1 * av1);
+                vmax = max_keep_nan(vmax, v.x * v.x + v.y * v.y);
+            }
+        }
+        cluster_sync();
+        // (C) deformation rate at v^{k+1} (own particles and halo copies);
+        // second half drift; next first half and stress
+        if (live) {
+            const bool more = kk + 1 < K;
+            const float4 va = mine ? vown : sV[vb_ * VS + self];
+            float Hd[4];
+            rate(va, Hd, vb_ * VS);
+            const float hH = more ? dts : hdts;
+            const double hX = more ? dtsd : hdtsd;
+            for (int i = 0; i < 4; i++) H[i] = H[i] + hH * Hd[i];
+            if (more) put_Q();
+            if (mine && !cons) {
+                x = x + hX * (double)va.x;
+                y = y + hX * (double)va.y;
+            }
+        }
+        __syncthreads();
+    }
+    if (mine) {
+        for (int i = 0; i < 4; i++) s.H[9 * a + i] = H[i];
+        s.v4[a] = vown;
+        s.x[a] = x;
+        s.y[a] = y;
+        const double idt = 1.0 / dt;
+        s.vbar[3 * a] = (x - xs) * idt;
+        s.vbar[3 * a + 1] = (y - ys) * idt;
+        s.vbar[3 * a + 2] = 0.0;
+        s.abar[3 * a] = as0 * idt;
+        s.abar[3 * a + 1] = as1 * idt;
+        s.abar[3 * a + 2] = 0.0;
+    }
+    float vm = warp_max(vmax), am = warp_max(amax);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(&ctl->vmaxS, sqrtf(vm));
+        atomic_max_pos(&ctl->amaxS, sqrtf(am));
+    }
+    cluster_sync();
+}
+
 // shared arrays of the 2-D body: own slots, plus halo slots in the push
 // forms, twice over in the mbarrier form (double-buffered)
 template <int MODE>
@@ -1109,6 +1358,17 @@ __global__ void __launch_bounds__(kC1Threads * 2) k_solid_cluster2d_one(Solid s,
     solid2d_body<LP, MODE, true>(s, P, ctl, 0, s.n, sQ, sV, rank, mb, MODE ? s.halo_n[rank] : 0, phs);
 }
 
+// one-barrier form (solid variant 5): one cluster, 2 kC1Threads threads per
+// CTA (own particles, then the halo copies)
+__global__ void __launch_bounds__(kC1Threads * 2) k_solid_cluster2d_1b(Solid s, const __grid_constant__ Phys P,
+                                                                       Ctl *ctl)
+{
+    pdl_trigger();   // the wait for the coupling-force kernel comes after the prologue
+    __shared__ float4 sQ[2 * kC1Threads];
+    __shared__ float4 sV[2 * (kC1Threads + kHaloMax)];
+    solid2d_body_1b<true>(s, P, ctl, s.n, sQ, sV, cluster_rank());
+}
+
 // Launch `want` clusters of `ctas` CTAs (at most as many as can be resident)
 // with kernel arguments args.  Returns 1 when the device cannot run such a
 // cluster (the caller falls back), else 0 or -3.
@@ -1160,17 +1420,30 @@ static int launch_persistent(Kern kern, int threads, int ctas, const Batch &bt, 
 // k_solid_cluster2d_one)
 constexpr int kPadSolidOne = 1;
 
-static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st)
+static int launch_solid_cluster(const Batch &bt, Solid &s, const Phys &P0, int dim, cudaStream_t st, int *path)
 {
-    static int mc2d[10][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
+    *path = 1;
+    static int mc2d[11][kClusterMax + 1] = {}, mcl[4][kClusterMax + 1] = {};
     const bool one = bt.B == 1;
     if (dim == 2 && s.force_lane_path != 1 && s.max_nb <= kMaxNb2) {
         const int ctas = (s.max_ns + kC1Threads - 1) / kC1Threads;
         int rc;
         // solid variants: 0 one thread per particle, 2 two threads, both with
         // halo copies and cluster barriers where the halos fit; 3 pull form;
-        // 4 halo copies awaited on mbarriers (correct, measured slower)
-        const int v = s.force_lane_path;
+        // 4 halo copies awaited on mbarriers (correct, measured slower); 5 the
+        // one-barrier form (a single body whose halos fit; else as 0)
+        int v = s.force_lane_path;
+        if (v == 5) {
+            if (one && s.push_ok && s.one_ok) {
+                const int r1 =
+                    launch_clusters(k_solid_cluster2d_1b, 2 * kC1Threads, ctas, 1, mc2d[10], st, s, P0, bt.ctl);
+                if (r1 <= 0) {
+                    *path = 3;
+                    return r1;
+                }
+            }
+            v = 0;
+        }
         const int mode = !s.push_ok || v == 3 ? 0 : (v == 4 ? 2 : 1);
         const int pad = kPadSolidOne ? 2 : 1;
         if (v == 2) {   // two threads per particle
@@ -1209,9 +1482,10 @@ int launch_solid_substeps(const Batch &bt, Solid &s, const Phys &P0, int dim, in
 {
     if (s.n == 0) return 0;
     if (!s.force_grid_path) {
-        int rc = launch_solid_cluster(bt, s, P0, dim, st);
+        int cp = 1;
+        int rc = launch_solid_cluster(bt, s, P0, dim, st, &cp);
         if (rc <= 0) {
-            if (path) *path = 1;
+            if (path) *path = cp;
             return rc;
         }
     }

@@ -252,18 +252,20 @@ def test_two_thread_solid_kernel_batch_equals_single():
 def test_solid_push_and_pull_forms_are_bitwise_equal(name):
     """Variants 0 and 4 read neighbours from the CTA's own halo copies (refreshed with
     stores ordered by cluster barriers, or with asynchronous stores counted on mbarriers),
-    variant 3 from the owning CTAs across the cluster: the same values in the same order,
-    so the same bits."""
+    variant 3 from the owning CTAs across the cluster, variant 5 evolves the halo
+    particles' stresses in every CTA that reads them (one cluster barrier per sub-step):
+    the same values in the same order, so the same bits."""
     case = {"dam_gate": lambda: fc.dam_gate(seed=0), "channel_flag": lambda: fc.channel_flag(seed=0),
             "floating_block": lambda: fc.floating_block(seed=1)}[name]()
     sims = []
-    for variant in (0, 3, 4):
+    for variant in (0, 3, 4, 5):
         sim = Simulation.from_case(case)
         sim.set_tuning(4, 128, variant)
         for _ in range(4):
             sim.step(0.0)
         sim.sync()
         sims.append(sim)
+    assert sims[3].info()["solid_path"] == 3   # the one-barrier form ran
     a = sims[0].get_solid()
     for other in sims[1:]:
         b = other.get_solid()
