@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
+#include <utility>
 #include <unordered_map>
 #include <vector>
 
@@ -19,14 +21,73 @@ using namespace sph;
 namespace {
 
 // host staging and bookkeeping of one instance
+// Allocator of the large host staging arrays: resize leaves the elements
+// uninitialised (every element is written before it is read), so that no
+// single-threaded zero fill precedes the parallel loops that write them.
+template <typename T>
+struct DefaultInit : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = DefaultInit<U>;
+    };
+    DefaultInit() = default;
+    template <typename U>
+    DefaultInit(const DefaultInit<U> &) noexcept {}
+    template <typename U, typename... Args>
+    void construct(U *p, Args &&...args)
+    {
+        if constexpr (sizeof...(Args) == 0) ::new ((void *)p) U;
+        else ::new ((void *)p) U(std::forward<Args>(args)...);
+    }
+};
+template <typename T>
+using hvec = std::vector<T, DefaultInit<T>>;
+
+// Contiguous chunks of a set-up loop over n items for the host threads: at
+// most 16, and at least min_per items each.
+int host_chunks(int64_t n, int64_t min_per)
+{
+    unsigned nt = std::thread::hardware_concurrency();
+    if (nt == 0) nt = 1;
+    if (nt > 16) nt = 16;
+    const int64_t by_size = min_per > 0 ? (n + min_per - 1) / min_per : n;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)nt, by_size));
+}
+
+// body(k, lo, hi) for chunk k of `chunks` contiguous chunks [lo, hi) of
+// [0, n), each on its own host thread (chunk 0 on the calling thread; a
+// thread that cannot be started runs its chunk here).  The set-up loops
+// write disjoint outputs per item, so the result does not depend on the
+// split.
+template <typename F>
+void host_parallel(int64_t n, int chunks, F &&body)
+{
+    if (chunks <= 1) {
+        body(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(chunks - 1);
+    for (int k = 1; k < chunks; k++) {
+        const int64_t lo = n * k / chunks, hi = n * (k + 1) / chunks;
+        try {
+            th.emplace_back([&body, k, lo, hi] { body(k, lo, hi); });
+        } catch (...) {
+            body(k, lo, hi);
+        }
+    }
+    body(0, (int64_t)0, n / chunks);
+    for (auto &t : th) t.join();
+}
+
 struct InstHost {
     sphfsi_params prm{};
     sphfsi_inflow inflow{};
     int64_t nf = 0, nw = 0, ns = 0;
-    std::vector<double> f_r, f_v, f_p;
+    hvec<double> f_r, f_v, f_p;
     bool f_has_p = false, f_added = false, w_added = false, s_added = false;
     double f_dp = 0, f_rho0 = 1, f_c0 = 1, f_eta = 0;
-    std::vector<double> w_r, w_n;
+    hvec<double> w_r, w_n;
     double w_dp = 0;
     std::vector<double> s_r0, s_v0, s_n0;
     std::vector<uint8_t> s_cons;
@@ -106,13 +167,24 @@ int dalloc(sphfsi_ctx *c, T **p, size_t count)
         if (_rc) return _rc < -7 ? SPHFSI_E_CUDA : _rc;     \
     } while (0)
 
-// copy n elements from a user pointer (host or device) into a host vector
-template <typename T>
-int fetch(std::vector<T> &dst, const T *src, size_t n)
+// copy n elements from a user pointer (host or device) into a host vector;
+// host memory (pinned or not) is copied by the host threads
+template <typename T, typename A>
+int fetch(std::vector<T, A> &dst, const T *src, size_t n)
 {
     dst.resize(n);
     if (n == 0) return SPHFSI_OK;
     if (!src) return SPHFSI_E_INVAL;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+        (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered)) {
+        T *d = dst.data();
+        host_parallel((int64_t)n, host_chunks((int64_t)n, (int64_t)1 << 18), [&](int, int64_t lo, int64_t hi) {
+            std::memcpy(d + lo, src + lo, sizeof(T) * (size_t)(hi - lo));
+        });
+        return SPHFSI_OK;
+    }
+    cudaGetLastError();   // a pointer the runtime does not know is not an error here
     return cuda_rc(cudaMemcpy(dst.data(), src, sizeof(T) * n, cudaMemcpyDefault));
 }
 
@@ -124,8 +196,8 @@ int deliver(T *dst, const std::vector<T> &src)
     return cuda_rc(cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyDefault));
 }
 
-template <typename T>
-int upload(sphfsi_ctx *c, T *dst, const std::vector<T> &src)
+template <typename T, typename A>
+int upload(sphfsi_ctx *c, T *dst, const std::vector<T, A> &src)
 {
     if (src.empty()) return SPHFSI_OK;
     return cuda_rc(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, c->st));
@@ -393,29 +465,39 @@ void body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx
             std::vector<int> cur(start.begin(), start.end() - 1);
             for (int a = 0; a < n; a++) items[cur[cid[a]]++] = a;
         }
-        std::vector<int> row;
-        for (int a = 0; a < n; a++) {
-            row.clear();
-            const int cx = cell(a, 0), cy = cell(a, 1), cz = D == 3 ? cell(a, 2) : 0;
-            for (int z = std::max(cz - 1, 0); z <= std::min(cz + 1, nc[2] - 1); z++)
-                for (int y = std::max(cy - 1, 0); y <= std::min(cy + 1, nc[1] - 1); y++)
-                    for (int x = std::max(cx - 1, 0); x <= std::min(cx + 1, nc[0] - 1); x++) {
-                        const int q = x + nc[0] * (y + nc[1] * z);
-                        for (int t = start[q]; t < start[q + 1]; t++) {
-                            const int b = items[t];
-                            if (b == a) continue;
-                            double r2 = 0.0;
-                            for (int k = 0; k < D; k++) {
-                                const double d = h.s_r0[(size_t)a * D + k] - h.s_r0[(size_t)b * D + k];
-                                const double dd = d * d;
-                                r2 = r2 + dd;
+        // rows over the host threads, each chunk into its own lists, then
+        // concatenated in particle order
+        const int nch = host_chunks(n, 1024);
+        std::vector<std::vector<int>> cidx(nch), clen(nch);
+        host_parallel(n, nch, [&](int ch, int64_t lo_a, int64_t hi_a) {
+            std::vector<int> row;
+            for (int a = (int)lo_a; a < (int)hi_a; a++) {
+                row.clear();
+                const int cx = cell(a, 0), cy = cell(a, 1), cz = D == 3 ? cell(a, 2) : 0;
+                for (int z = std::max(cz - 1, 0); z <= std::min(cz + 1, nc[2] - 1); z++)
+                    for (int y = std::max(cy - 1, 0); y <= std::min(cy + 1, nc[1] - 1); y++)
+                        for (int x = std::max(cx - 1, 0); x <= std::min(cx + 1, nc[0] - 1); x++) {
+                            const int q = x + nc[0] * (y + nc[1] * z);
+                            for (int t = start[q]; t < start[q + 1]; t++) {
+                                const int b = items[t];
+                                if (b == a) continue;
+                                double r2 = 0.0;
+                                for (int k = 0; k < D; k++) {
+                                    const double d = h.s_r0[(size_t)a * D + k] - h.s_r0[(size_t)b * D + k];
+                                    const double dd = d * d;
+                                    r2 = r2 + dd;
+                                }
+                                if (r2 < rc2) row.push_back(s0 + b);
                             }
-                            if (r2 < rc2) row.push_back(s0 + b);
                         }
-                    }
-            std::sort(row.begin(), row.end());
-            idx.insert(idx.end(), row.begin(), row.end());
-            ptr.push_back((int)idx.size());
+                std::sort(row.begin(), row.end());
+                cidx[ch].insert(cidx[ch].end(), row.begin(), row.end());
+                clen[ch].push_back((int)row.size());
+            }
+        });
+        for (int ch = 0; ch < nch; ch++) {
+            idx.insert(idx.end(), cidx[ch].begin(), cidx[ch].end());
+            for (int len : clen[ch]) ptr.push_back(ptr.back() + len);
         }
     }
 }
@@ -894,12 +976,14 @@ int sphfsi_finalize(sphfsi_ctx *c)
 
     // ---- concatenated host copies and upload
     {
-        std::vector<double> fx(nf), fy(nf), fz(D == 3 ? nf : 0);
-        std::vector<float> fvx(nf), fvy(nf), fvz(D == 3 ? nf : 0), fdr(nf, 0.0f);
-        std::vector<int> fid(nf), finst(nf);
-        std::vector<double> wx(nw), wy(nw), wz(D == 3 ? nw : 0);
-        std::vector<float> wnx(nw), wny(nw), wnz(D == 3 ? nw : 0);
-        std::vector<int> winst(nw);
+        // fluid and walls: per-item loops over the host threads (every
+        // element written once)
+        hvec<double> fx(nf), fy(nf), fz(D == 3 ? nf : 0);
+        hvec<float> fvx(nf), fvy(nf), fvz(D == 3 ? nf : 0), fdr(nf);
+        hvec<int> fid(nf), finst(nf);
+        hvec<double> wx(nw), wy(nw), wz(D == 3 ? nw : 0);
+        hvec<float> wnx(nw), wny(nw), wnz(D == 3 ? nw : 0);
+        hvec<int> winst(nw);
         std::vector<double> sx(ns), sy(ns), sz(D == 3 ? ns : 0), svbar(3 * (size_t)ns, 0.0);
         std::vector<float4> sv4(ns);
         std::vector<float> sn0(3 * (size_t)ns, 0.0f);
@@ -911,37 +995,51 @@ int sphfsi_finalize(sphfsi_ctx *c)
             InstHost &h = c->ih[b];
             const int f0 = h.d.f0, w0 = h.d.w0, s0 = h.d.s0;
             double vmax = 0.0;
-            for (int64_t i = 0; i < h.nf; i++) {
-                fx[f0 + i] = h.f_r[i * D];
-                fy[f0 + i] = h.f_r[i * D + 1];
-                if (D == 3) fz[f0 + i] = h.f_r[i * D + 2];
-                fvx[f0 + i] = (float)h.f_v[i * D];
-                fvy[f0 + i] = (float)h.f_v[i * D + 1];
-                if (D == 3) fvz[f0 + i] = (float)h.f_v[i * D + 2];
-                double v2 = 0.0;
-                for (int k = 0; k < D; k++) {
-                    double vk = (double)(float)h.f_v[i * D + k];
-                    v2 += vk * vk;
+            const int fch = host_chunks(h.nf, (int64_t)1 << 15);
+            std::vector<double> cmax(fch, 0.0);
+            std::vector<char> cbad(fch, 0);
+            host_parallel(h.nf, fch, [&](int k, int64_t lo, int64_t hi) {
+                double m = 0.0;
+                for (int64_t i = lo; i < hi; i++) {
+                    fx[f0 + i] = h.f_r[i * D];
+                    fy[f0 + i] = h.f_r[i * D + 1];
+                    if (D == 3) fz[f0 + i] = h.f_r[i * D + 2];
+                    fvx[f0 + i] = (float)h.f_v[i * D];
+                    fvy[f0 + i] = (float)h.f_v[i * D + 1];
+                    if (D == 3) fvz[f0 + i] = (float)h.f_v[i * D + 2];
+                    double v2 = 0.0;
+                    for (int d = 0; d < D; d++) {
+                        double vk = (double)(float)h.f_v[i * D + d];
+                        v2 += vk * vk;
+                    }
+                    m = std::max(m, std::sqrt(v2));
+                    fdr[f0 + i] = 0.0f;
+                    if (h.f_has_p) {
+                        // inverse of Eq. eqeos: rho - rho0 = rho0 expm1(log1p(7 p / (rho0 c0^2)) / 7)
+                        double x = 7.0 * h.f_p[i] / (h.f_rho0 * h.f_c0 * h.f_c0);
+                        if (!(x > -1.0)) cbad[k] = 1;
+                        else fdr[f0 + i] = (float)(h.f_rho0 * std::expm1(std::log1p(x) / 7.0));
+                    }
+                    fid[f0 + i] = (int)i;
+                    finst[f0 + i] = b;
                 }
-                vmax = std::max(vmax, std::sqrt(v2));
-                if (h.f_has_p) {
-                    // inverse of Eq. eqeos: rho - rho0 = rho0 expm1(log1p(7 p / (rho0 c0^2)) / 7)
-                    double x = 7.0 * h.f_p[i] / (h.f_rho0 * h.f_c0 * h.f_c0);
-                    if (!(x > -1.0)) return SPHFSI_E_INVAL;
-                    fdr[f0 + i] = (float)(h.f_rho0 * std::expm1(std::log1p(x) / 7.0));
+                cmax[k] = m;
+            });
+            for (int k = 0; k < fch; k++) {
+                if (cbad[k]) return SPHFSI_E_INVAL;
+                vmax = std::max(vmax, cmax[k]);
+            }
+            host_parallel(h.nw, host_chunks(h.nw, (int64_t)1 << 15), [&](int, int64_t lo, int64_t hi) {
+                for (int64_t q = lo; q < hi; q++) {
+                    wx[w0 + q] = h.w_r[q * D];
+                    wy[w0 + q] = h.w_r[q * D + 1];
+                    if (D == 3) wz[w0 + q] = h.w_r[q * D + 2];
+                    wnx[w0 + q] = (float)h.w_n[q * D];
+                    wny[w0 + q] = (float)h.w_n[q * D + 1];
+                    if (D == 3) wnz[w0 + q] = (float)h.w_n[q * D + 2];
+                    winst[w0 + q] = b;
                 }
-                fid[f0 + i] = (int)i;
-                finst[f0 + i] = b;
-            }
-            for (int64_t q = 0; q < h.nw; q++) {
-                wx[w0 + q] = h.w_r[q * D];
-                wy[w0 + q] = h.w_r[q * D + 1];
-                if (D == 3) wz[w0 + q] = h.w_r[q * D + 2];
-                wnx[w0 + q] = (float)h.w_n[q * D];
-                wny[w0 + q] = (float)h.w_n[q * D + 1];
-                if (D == 3) wnz[w0 + q] = (float)h.w_n[q * D + 2];
-                winst[w0 + q] = b;
-            }
+            });
             double vs = 0.0;
             for (int64_t a = 0; a < h.ns; a++) {
                 sx[s0 + a] = h.s_r0[a * D];
@@ -1045,8 +1143,11 @@ int sphfsi_finalize(sphfsi_ctx *c)
     c->finalized = true;
     // release the host staging copies that are not needed any more
     for (auto &h : c->ih) {
-        h.f_r.clear(); h.f_v.clear(); h.f_p.clear();
-        h.w_r.clear(); h.w_n.clear();
+        hvec<double>().swap(h.f_r);
+        hvec<double>().swap(h.f_v);
+        hvec<double>().swap(h.f_p);
+        hvec<double>().swap(h.w_r);
+        hvec<double>().swap(h.w_n);
         h.s_r0.clear(); h.s_v0.clear(); h.s_n0.clear();
     }
     return SPHFSI_OK;
