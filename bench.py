@@ -935,7 +935,10 @@ def e2e_run(cases, dev, steps, tuning, time_stepping="multiple", advection_caden
     fields = {k: pin([getattr(c, k) for c in cases]) for k in ("f_r", "f_v", "f_p", "w_r", "w_n", "s_r0", "s_v0",
                                                                   "s_n0")}
     n_s = sum(c.ns for c in cases)
-    out = torch.empty((n_s, cases[0].dim), dtype=torch.float64).pin_memory()
+    # two pinned result buffers: step k's solid positions are read into one
+    # while the host consumes step k - 1's from the other
+    outs = [torch.empty((n_s, cases[0].dim), dtype=torch.float64).pin_memory() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
     h2d = sum(t.numel() * t.element_size() for t, _ in fields.values()) + n_s
     st = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
@@ -958,17 +961,25 @@ def e2e_run(cases, dev, steps, tuning, time_stepping="multiple", advection_caden
     sim.set_time_stepping(time_stepping)
     sim.set_advection_cadence(advection_cadence)
     p0 = sim.pairs_total()
-    for _ in range(steps):
+    seen = 0.0
+    for k in range(steps):
         sim.run(1, 0.0)
-        sim.get_solid_positions_all(out)
+        sim.get_solid_positions_async(outs[k % 2])
+        evs[k % 2].record(st)
+        if k > 0:   # the previous step's rows: wait for their copy, then use them on the host
+            evs[(k - 1) % 2].synchronize()
+            seen += float(outs[(k - 1) % 2].numpy()[:, 0].max())
     sim.sync()
+    seen += float(outs[(steps - 1) % 2].numpy()[:, 0].max())
     t1 = time.perf_counter()
     pairs = sim.pairs_total() - p0
     sim.close()
+    assert np.isfinite(seen)
     return {"value": pairs / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
-            "d2h_bytes_per_step": out.numel() * 8, "steps": steps,
-            "note": "context creation + set-up upload amortised over the steps; per-step readback of all "
-                    "solid positions"}
+            "d2h_bytes_per_step": outs[0].numel() * 8, "steps": steps,
+            "note": "context creation + set-up upload amortised over the steps; every step's solid "
+                    "positions read into pinned memory without waiting, each used on the host one step "
+                    "later, after its copy completed"}
 
 
 def main():

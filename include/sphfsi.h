@@ -272,6 +272,15 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
  * instances in order, n_total x dim FP64); one device read for the batch. */
 int sphfsi_get_solid_positions_all(sphfsi_ctx *c, double *r);
 
+/* The same rows, read without waiting: a gather kernel and a copy into r are
+ * enqueued on the context's stream after the steps enqueued so far, and the
+ * call returns at once.  r (n_total x dim FP64, host or device; pinned host
+ * memory for a copy that overlaps later steps) must stay valid, and is
+ * complete only once the stream has reached the copy (sphfsi_sync, or an
+ * event recorded on the stream after this call).  Returns SPHFSI_E_INVAL for
+ * a NULL r, SPHFSI_E_STATE before sphfsi_finalize. */
+int sphfsi_get_solid_positions_async(sphfsi_ctx *c, double *r);
+
 /* Overwrite the dynamic state (original order, FP64 inputs; NULL keeps a
  * field).  Used for checkpoint/resume and for parity at a given state. */
 int sphfsi_set_fluid_state(sphfsi_ctx *c, const double *r, const double *v, const double *rho,

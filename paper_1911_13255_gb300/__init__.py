@@ -75,6 +75,7 @@ _SIGS = {
     "sphfsi_select": (C.c_int, [_vp, C.c_int32]),
     "sphfsi_pairs_total": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
     "sphfsi_get_solid_positions_all": (C.c_int, [_vp, _vp]),
+    "sphfsi_get_solid_positions_async": (C.c_int, [_vp, _vp]),
     "sphfsi_set_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
     "sphfsi_get_tuning": (C.c_int, [_vp, C.POINTER(Tuning)]),
     "sphfsi_autotune": (C.c_int, [_vp, C.c_double, C.c_int32, C.POINTER(Tuning)]),
@@ -417,6 +418,13 @@ class Simulation:
     def get_solid_positions_all(self, out):
         """Solid positions of all instances (concatenated, original order) into a caller buffer."""
         _check(lib().sphfsi_get_solid_positions_all(self.h, _ptr(out)), "sphfsi_get_solid_positions_all")
+        return out
+
+    def get_solid_positions_async(self, out):
+        """The same rows enqueued on the context's stream without waiting; `out`
+        (a pinned host tensor for a copy that overlaps later steps) is complete
+        once the stream has reached the copy (sync, or an event recorded after)."""
+        _check(lib().sphfsi_get_solid_positions_async(self.h, _ptr(out)), "sphfsi_get_solid_positions_async")
         return out
 
     def set_fluid_state(self, r=None, v=None, rho=None, drho=None):

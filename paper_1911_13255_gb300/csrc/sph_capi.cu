@@ -136,6 +136,10 @@ struct sphfsi_ctx {
     // side stream for the solid branch, which runs beside momentum and continuity
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // asynchronous read of the solid positions: each device slot's output
+    // row (original order), and the gathered rows
+    int *d_orow = nullptr;
+    double *d_spos = nullptr;
     // learned sub-stepper (sphfsi_set_learned)
     sphfsi_mpnn *mpnn = nullptr;
 };
@@ -1096,6 +1100,12 @@ int sphfsi_finalize(sphfsi_ctx *c)
         TRY(upload(c, S.cons, scons));
         TRY(upload(c, S.vbar, svbar));
         TRY(upload(c, S.inst, sinst));
+        std::vector<int> orow(ns);
+        for (const InstHost &h : c->ih)
+            for (int64_t a = 0; a < h.ns; a++) orow[h.d.s0 + a] = (int)(h.d.s0 + h.s_order[a]);
+        TRY(dalloc(c, &c->d_orow, ns));
+        TRY(upload(c, c->d_orow, orow));
+        TRY(dalloc(c, &c->d_spos, (size_t)ns * D));
         TRY(upload(c, c->ctl, hctl));
         TRY(upload(c, c->d_inst, hinst));
     }
@@ -1372,6 +1382,31 @@ int sphfsi_get_solid(sphfsi_ctx *c, double *r, float *v, double *F, double *vbar
     TRY(vec3(S.fF, fF, 0.0f));
     TRY(vec3(S.nrm, nrm, 0.0f));
     return SPHFSI_OK;
+}
+
+// solid positions in original order (row orow[a] of out) for the
+// asynchronous read
+__global__ void k_gather_solid_positions(const double *x, const double *y, const double *z, const int *orow,
+                                         int n, int D, double *out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const size_t o = (size_t)orow[a] * D;
+    out[o] = x[a];
+    out[o + 1] = y[a];
+    if (D == 3) out[o + 2] = z[a];
+}
+
+int sphfsi_get_solid_positions_async(sphfsi_ctx *c, double *r)
+{
+    TRY(check_ctx(c, true));
+    if (!r) return SPHFSI_E_INVAL;
+    const int64_t n = c->S.n;
+    if (n == 0) return SPHFSI_OK;
+    k_gather_solid_positions<<<(unsigned)((n + 255) / 256), 256, 0, c->st>>>(c->S.x, c->S.y, c->S.z, c->d_orow,
+                                                                          (int)n, c->dim, c->d_spos);
+    TRY(cuda_rc(cudaGetLastError()));
+    return cuda_rc(cudaMemcpyAsync(r, c->d_spos, sizeof(double) * (size_t)n * c->dim, cudaMemcpyDefault, c->st));
 }
 
 int sphfsi_get_solid_positions_all(sphfsi_ctx *c, double *r)

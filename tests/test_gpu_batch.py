@@ -317,3 +317,36 @@ def test_fused_binning_batch_equals_single():
             assert np.array_equal(got[k], want[k]), (b, k)
         single.close()
     batch.close()
+
+
+def test_solid_position_reads_all_and_async_agree_per_step():
+    """The solid positions of a batch read after each graph-replayed step:
+    without waiting (enqueued on the stream into pinned buffers, read back
+    one step later, after an event) they are, bit for bit, the rows the
+    waiting read gives and each instance's own positions, step by step."""
+    cases = _mixed_cases()
+    stream = torch.cuda.Stream()
+    a = Simulation.from_cases(cases, stream=stream)
+    b = Simulation.from_cases(cases, stream=stream)
+    dim = cases[0].dim
+    n = sum(c.ns for c in cases)
+    bufs = [torch.empty((n, dim), dtype=torch.float64).pin_memory() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    want = np.zeros((n, dim))
+    prev = None
+    for k in range(6):
+        a.run(1, 0.0)
+        a.get_solid_positions_async(bufs[k % 2])
+        evs[k % 2].record(stream)
+        b.run(1, 0.0)
+        b.get_solid_positions_all(want)
+        rows = np.concatenate([b.select(i).get_solid()["r"] for i in range(len(cases))])
+        assert np.array_equal(want, rows), k
+        if prev is not None:
+            evs[(k - 1) % 2].synchronize()
+            assert np.array_equal(bufs[(k - 1) % 2].numpy(), prev), k - 1
+        prev = want.copy()
+    a.sync()
+    assert np.array_equal(bufs[5 % 2].numpy(), prev)
+    a.close()
+    b.close()
