@@ -455,7 +455,7 @@ def run_gpu(args, rank, world, local_rank):
                    "tuning": {k: tuning[k] for k in ("lanes", "block", "solid_variant", "compact", "tile", "records", "rows",
                                                      "list", "list_lanes")},
                    "cell_reach": case.cell_reach, "time_stepping": args.time_stepping,
-                   "advection_cadence": args.advection_cadence,
+                   "advection_cadence": args.advection_cadence or "auto",
                    "autotuned": args.workload not in ("dam_gate", "duct_3d") and not args.tuning,
                    "l2": "flushed between timed steps (256 MB write outside the timed window)",
                    "replicas": world},
@@ -761,7 +761,7 @@ def run_fiv(args, rank, world, local_rank):
         "config": {"workload": label, "n_fluid": case.nf, "n_solid": case.ns, "n_wall": case.nw,
                    "resolution_ratio": r, "time_stepping": args.time_stepping, "t_star_end": args.t_star,
                    "seed": args.seed, "inflow_buffer_dp": case.inflow_width / case.f_dp, "n_reinit": case.n_reinit,
-                   "advection_cadence": args.advection_cadence,
+                   "advection_cadence": args.advection_cadence or "auto",
                    "dp_F": case.f_dp, "dp_S": case.s_dp, "D": D, "U": U, "Re": 100, "E_star": 1.4e3,
                    "l2": "not flushed (whole working set ~5 MB); every 20 steps the solid positions are read back"},
         "t_reached": t, "t_star_reached": t * U / D, "finite": bool(t >= t_end),
@@ -993,7 +993,8 @@ def main():
     ap.add_argument("--n-reinit", type=int, default=-1,
                     help="fiv workload: density reinitialisation cadence, 0 off (-1: the workload's reading, 3)")
     ap.add_argument("--advection-cadence", type=int, default=1,
-                    help="steps the pair configuration is held (Algorithm 1, reading F2; 1: rebuilt every step)")
+                    help="steps the pair configuration is held (Algorithm 1, reading F2; 1: rebuilt every step; "
+                         "0: Algorithm 1's advection steps from the advection criterion, reading F3)")
     ap.add_argument("--duct-scale", type=int, default=1, choices=[1, 2],
                     help="duct_3d workload: 1 the full duct, 2 its copy at twice the spacings (1/8 of the particles)")
     ap.add_argument("--warmup", type=int, default=5)

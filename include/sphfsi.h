@@ -206,15 +206,21 @@ int sphfsi_set_time_stepping(sphfsi_ctx *c, int32_t mode);
 
 /* Advection cadence of the pair configuration (Algorithm 1: the neighbour
  * lists and the kernel values W_ij and gradients grad W_ij are updated once
- * per advection step and held over its acoustic steps).  n <= 1 (the
+ * per advection step and held over its acoustic steps).  n = 1 (the
  * default): rebuilt every coarse step from the step's mid positions.  n > 1:
- * rebuilt at steps whose index (instance 0's) is a multiple of n, and at the
- * next step after any of sphfsi_set_fluid_state, sphfsi_set_solid_state,
- * sphfsi_set_time or this call; on the steps in between every pair term
- * takes its W and grad W at the fluid and solid positions of the last
- * rebuild (the same pairs, in the same order), with current densities,
- * pressures, velocities, time-averaged solid velocities and accelerations
- * and normals.  All instances of a batch rebuild together.  While n > 1,
+ * rebuilt at steps whose index (instance 0's) is a multiple of n.  n = 0:
+ * the advection steps of Algorithm 1 (reading F3): an advection step starts
+ * with a rebuild and lasts while the coarse steps taken in it sum to at most
+ * dt_ad = 0.25 min(h_F / |v|max, h_F^2 / nu) (Eq. dtf-advection, nu =
+ * eta / rho0), evaluated at the fluid speed maximum each of its steps starts
+ * from, the smallest of those values counting (instance 0's values decide
+ * for a batch).  Every cadence also rebuilds at the next step after any of
+ * sphfsi_set_fluid_state, sphfsi_set_solid_state, sphfsi_set_time or this
+ * call.  On the steps between rebuilds every pair term takes its W and
+ * grad W at the fluid and solid positions of the last rebuild (the same
+ * pairs, in the same order), with current densities, pressures, velocities,
+ * time-averaged solid velocities and accelerations and normals.  All
+ * instances of a batch rebuild together.  While n != 1,
  * sphfsi_debug_neighbors returns SPHFSI_E_STATE (its binning would replace
  * the held configuration).  SPHFSI_E_INVAL for n < 0. */
 int sphfsi_set_advection_cadence(sphfsi_ctx *c, int32_t n);

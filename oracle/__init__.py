@@ -350,11 +350,21 @@ class OracleSim:
     def set_advection_cadence(self, n):
         """Reading F2 (Algorithm 1): neighbour lists and kernel values built
         once every n steps (an advection step of n acoustic steps) and held
-        over them; n = 0 rebuilds them every step (R15)."""
+        over them; n = 1 rebuilds them every step (R15).  n = 0 or "auto"
+        (reading F3): an advection step lasts while the acoustic steps taken
+        in it sum to at most dt_ad, the advection criterion (Eq.
+        dtf-advection) at the fluid speed maximum each step starts from, the
+        smallest value over the advection step counting."""
+        n = 0 if n == "auto" else int(n)
+        if n < 0:
+            raise ValueError("cadence must be >= 0")
         if getattr(self, "cache", None) is not None:
             self._L.or_cache_free(C.byref(self.cache))
-        self.cadence = int(n)
-        self.cache = Cache() if n > 0 else None
+        self.cadence = n
+        self.cache = Cache()
+        self.rebuilds = []          # step indices that built the configuration
+        self._rebuild_next = True   # Algorithm 1 starts an advection step
+        self._t_ad = self._t_acc = 0.0
 
     def __del__(self):
         if getattr(self, "cache", None) is not None and getattr(self, "_L", None) is not None:
@@ -364,10 +374,24 @@ class OracleSim:
     def step(self, dt, K):
         cache = getattr(self, "cache", None)
         if cache is not None:
-            if self.step_index % self.cadence == 0:
+            if self.cadence == 0:
+                # reading F3: dt_ad at the maximum this step starts from (the
+                # last step's post-kick maximum, else the initial speeds)
+                v0 = self.last["vmax_f"] if getattr(self, "last", None) else (
+                    float(np.sqrt((self.f_v ** 2).sum(1)).max()) if self.case.nf else 0.0)
+                _, ad, _ = self.suggest_dt(vmax_f=v0)
+                rebuild = self._rebuild_next
+                self._t_ad = ad if rebuild else min(self._t_ad, ad)
+            else:
+                rebuild = self.step_index % self.cadence == 0
+            if rebuild:
                 cache.valid = 0
+                self.rebuilds.append(self.step_index)
             rc = self._L.or_step_ex(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
                                   self.t, self.step_index, C.byref(self.diag), C.byref(cache))
+            if self.cadence == 0:
+                self._t_acc = (0.0 if rebuild else self._t_acc) + dt
+                self._rebuild_next = self._t_acc > self._t_ad
         else:
             rc = self._L.or_step(C.byref(self.P), C.byref(self.F), C.byref(self.W), C.byref(self.S), dt, int(K),
                                self.t, self.step_index, C.byref(self.diag))

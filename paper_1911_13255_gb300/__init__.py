@@ -368,8 +368,10 @@ class Simulation:
         _check(lib().sphfsi_set_time_stepping(self.h, m), "sphfsi_set_time_stepping")
 
     def set_advection_cadence(self, n):
-        """Hold the pair configuration over n coarse steps (Algorithm 1); n <= 1 rebuilds it every step."""
-        _check(lib().sphfsi_set_advection_cadence(self.h, int(n)), "sphfsi_set_advection_cadence")
+        """Hold the pair configuration over n coarse steps (Algorithm 1); 1 rebuilds it every step;
+        0 or "auto": over the advection steps of the advection criterion (Eq. dtf-advection)."""
+        n = 0 if n == "auto" else int(n)
+        _check(lib().sphfsi_set_advection_cadence(self.h, n), "sphfsi_set_advection_cadence")
 
     def set_wait_limit(self, iterations):
         """Polling iterations before a bounded device wait gives up (0: the default)."""

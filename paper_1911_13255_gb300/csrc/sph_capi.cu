@@ -915,8 +915,8 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(dalloc(c, &F.nbc, nf));
     // held pair configuration: off (rebuilt every step); the first step builds it
     F.held_n = 1;
-    TRY(dalloc(c, &F.held, 2));
-    TRY(upload(c, F.held, std::vector<int>{1, 0}));
+    TRY(dalloc(c, &F.held, 3));
+    TRY(upload(c, F.held, std::vector<int>{1, 0, 0}));
     // ---- walls
     Walls &W = c->W;
     W.n = (int)nw;
@@ -1181,7 +1181,7 @@ int sphfsi_set_advection_cadence(sphfsi_ctx *c, int32_t n)
 {
     TRY(check_ctx(c, true));
     if (n < 0) return SPHFSI_E_INVAL;
-    c->F.held_n = n < 1 ? 1 : n;
+    c->F.held_n = n;   // 0: automatic (the advection criterion)
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
@@ -1742,7 +1742,7 @@ int sphfsi_debug_neighbors(sphfsi_ctx *c, int which, int64_t *ptr, int64_t *idx,
 {
     TRY(check_ctx(c, true));
     if (which < 0 || which > 3 || !nnz) return SPHFSI_E_INVAL;
-    if (c->F.held_n > 1) return SPHFSI_E_STATE;   // binning here would replace the held configuration
+    if (c->F.held_n != 1) return SPHFSI_E_STATE;   // binning here would replace the held configuration
     const InstHost &h = c->ih[c->sel];
     const int64_t nrows = which == 3 ? h.ns : h.nf;
     // bin the current positions (no drift) and build the solid records

@@ -103,6 +103,9 @@ struct Ctl {
     double lnum, lden;           // residual sums |m (v' - v) - dt f(x_mid)|^2, |m v'|^2 (FP64)
     double l_res;                // residual of the last step
     long long l_acc, l_rej;      // accepted / rejected steps
+    // automatic advection step (Fluid::held_n == 0, instance 0's values
+    // decide): its advection time step dt_ad and the acoustic time so far
+    double t_ad, t_acc;
 };
 
 // Physical constants of the fluid, the walls and the solid of one instance.
@@ -191,14 +194,16 @@ struct Fluid {
     unsigned *gbar;     // its grid barrier: [0] arrivals, [1] generation
     // Held pair configuration (Algorithm 1: the neighbour lists and the kernel
     // values and gradients are updated once per advection step).  With
-    // held_n > 1 the binning (sort, cell lists, record positions) runs only on
+    // held_n != 1 the binning (sort, cell lists, record positions) runs only on
     // rebuild steps; on the other steps the particles keep their slots and
     // the records keep the positions of the last rebuild, so every pair term
     // takes W and grad W at those positions, while pressures, densities and
     // velocities are refreshed (k_held_records).
-    int held_n;         // coarse steps per advection step; <= 1: rebuilt every step
+    int held_n;         // coarse steps per advection step; 1: rebuilt every step; 0: as many
+                        // as fit the advection criterion (Algorithm 1, decided by the finish kernel)
     int *held;          // [0] != 0: rebuild at the next step (set by the host's state setters),
-                        // [1]: the last finished step rebuilt the configuration
+                        // [1]: the last finished step rebuilt the configuration,
+                        // [2] (held_n == 0): the next step rebuilds
     // Neighbour rows (Fluid::list = 1, tuned): the candidate tests of the cell
     // visit run once per rebuild (k_pairlist) and each target's in-support
     // fluid neighbours (from the front) and wall neighbours (from the back)
@@ -320,8 +325,13 @@ __device__ __forceinline__ bool step_failed(const Batch &bt) { return *bt.fail !
 // All instances of a context rebuild together.
 __device__ __forceinline__ bool rebuild_step(const Batch &bt, const Fluid &f)
 {
-    return f.held_n <= 1 || f.held[0] != 0 || bt.ctl[0].step % f.held_n == 0;
+    if (f.held_n == 1 || f.held[0] != 0) return true;
+    if (f.held_n == 0) return f.held[2] != 0;   // automatic: the last step's finish kernel decided
+    return bt.ctl[0].step % f.held_n == 0;
 }
+
+// the pair configuration is held over several steps (fixed or automatic cadence)
+__device__ __host__ __forceinline__ bool held_on(const Fluid &f) { return f.held_n != 1; }
 
 // ---------------------------------------------------------------------------
 // helpers

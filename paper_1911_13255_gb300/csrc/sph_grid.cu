@@ -122,6 +122,18 @@ __device__ void update_normal(const Solid &s, int a)
     s.nrm[3 * a + 2] = n[2] * inv;
 }
 
+// The advection criterion of Eq. dtf-advection, 0.25 min(h_F / |v|max,
+// h_F^2 / nu), nu = eta / rho0 (the printed eta read as the kinematic
+// viscosity, as in the single-step criterion); a zero speed or viscosity
+// drops its term.
+__device__ __forceinline__ double advection_dt(const Phys &P, double vmax)
+{
+    const double nu = P.eta_d / P.rho0_d;
+    const double a1 = vmax > 0.0 ? P.hF_d / vmax : 1e300;
+    const double a2 = nu > 0.0 ? P.hF_d * P.hF_d / nu : 1e300;
+    return 0.25 * (a1 < a2 ? a1 : a2);
+}
+
 // finish: time, step, pair counters, non-finite check, maxima for the next
 // step's control (one thread per instance)
 __global__ void k_finish(Batch bt, int learned, unsigned *gbar, Fluid f)
@@ -132,8 +144,23 @@ __global__ void k_finish(Batch bt, int learned, unsigned *gbar, Fluid f)
     if (b == 0 && gbar) gbar[0] = 0u;   // the fused binning's barrier, even after a time-out
     if (b == 0 && f.held) {
         // before instance 0's step index advances (below, same thread)
-        f.held[1] = rebuild_step(bt, f) ? 1 : 0;
+        const bool rb = rebuild_step(bt, f);
+        f.held[1] = rb ? 1 : 0;
         f.held[0] = 0;
+        if (f.held_n == 0) {
+            // Algorithm 1 (reading F3): an advection step lasts while the
+            // acoustic steps taken in it sum to at most dt_ad, the advection
+            // criterion (Eq. dtf-advection) at the maxima each step started
+            // from (its minimum over the advection step, so that one that
+            // starts at rest still ends); instance 0 decides for the context.
+            // This thread is instance 0's own, and prev_vmaxF is still the
+            // maximum this step's control used.
+            Ctl *c0 = bt.ctl;
+            const double ad = advection_dt(bt.I[0].P, c0->prev_vmaxF);
+            c0->t_ad = rb ? ad : fmin(c0->t_ad, ad);
+            c0->t_acc = (rb ? 0.0 : c0->t_acc) + c0->dt;
+            f.held[2] = c0->t_acc > c0->t_ad ? 1 : 0;
+        }
     }
     if (b >= bt.B) return;
     Ctl *ctl = bt.ctl + b;
@@ -614,7 +641,7 @@ __device__ __forceinline__ void fluid_put(const Batch &bt, const Fluid &f, int k
     f.cell_of[k] = v.key;
     // the double-float remainders serve the reinitialisation; with a held
     // configuration a later step of the advection step may reinitialise
-    const bool reinit = bt.ctl[v.b].reinit || f.held_n > 1;
+    const bool reinit = bt.ctl[v.b].reinit || held_on(f);
     float4 lo;
     float4 r = rel_pos<D>(In, v.key, v.x, v.y, v.z, reinit ? &lo : nullptr);
     if (reinit) f.L4[k] = lo;
@@ -707,7 +734,7 @@ __device__ __forceinline__ void rank_cell(const Batch &bt, const Fluid &f, const
         if (mine) {
             if (!REC) (fl ? f.sperm : s.sperm)[a + rank] = v;
             else if (fl) fluid_put<D>(bt, f, a + rank, src);
-            else solid_record<D>(bt, s, a + rank, v, f.held_n > 1);
+            else solid_record<D>(bt, s, a + rank, v, held_on(f));
         }
     }
 }
@@ -736,7 +763,7 @@ __global__ void k_records_sorted(Batch bt, Fluid f, Solid s)
     if (!rebuild_step(bt, f)) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < f.n) fluid_record<D>(bt, f, t, f.sperm[t]);
-    else if (t < f.n + s.n) solid_record<D>(bt, s, t - f.n, s.sperm[t - f.n], f.held_n > 1);
+    else if (t < f.n + s.n) solid_record<D>(bt, s, t - f.n, s.sperm[t - f.n], held_on(f));
 }
 
 // Held configuration, steps between rebuilds: every slot keeps its particle
@@ -929,7 +956,7 @@ static int launch_bin_fused(K kern, int nb, cudaStream_t st, const Batch &bt, co
 // kernels launch_bin_all launches in a step with particles
 int bin_kernels(const Fluid &f)
 {
-    if (f.held_n > 1) return (f.split_records ? 5 : 4) + 1;
+    if (held_on(f)) return (f.split_records ? 5 : 4) + 1;
     return f.bin_fused ? 1 : (f.split_records ? 5 : 4);
 }
 
@@ -941,7 +968,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
     const int np = f.n + s.n;
     const int nt = np + (step ? bt.B : 0);
     if (nt == 0) return 0;
-    if (f.bin_fused && np > 0 && f.held_n <= 1) {
+    if (f.bin_fused && np > 0 && !held_on(f)) {
         auto kern = dim == 2 ? k_bin_fused<2, 16> : k_bin_fused<3, 32>;
         const int nb = bin_fused_blocks(kern, dim);
         if (nb > 0) return launch_bin_fused(kern, nb, st, bt, f, s, step, dt_fixed, K_fixed);
@@ -983,7 +1010,7 @@ int launch_bin_all(const Batch &bt, Fluid &f, Solid &s, int dim, int step, doubl
             launch_k(k_cell_records<3, 32, true>, grid, kBlock, 0, st, bt, f, s, listed, ncells);
         }
     }
-    if (f.held_n > 1) {
+    if (held_on(f)) {
         if (dim == 2) launch_k(k_held_records<2>, nbr, kBlock, 0, st, bt, f, s);
         else launch_k(k_held_records<3>, nbr, kBlock, 0, st, bt, f, s);
     }

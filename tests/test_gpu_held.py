@@ -78,6 +78,52 @@ def test_held_configuration_steps_match_the_oracle(name):
     sim.close()
 
 
+def _fast_box_3d():
+    """tiny_box_3d with its velocities scaled to about c0 / 5: advection
+    steps of two to three acoustic steps."""
+    case = fc.tiny_box_3d(seed=1)
+    case.f_v = case.f_v * 40.0
+    return case
+
+
+@pytest.mark.parametrize("name", ["channel_flag", "fast_box_3d"])
+def test_automatic_advection_steps_match_the_oracle(name):
+    """Reading F3 (Algorithm 1's advection steps) on the GPU against the
+    oracle's: every step's accelerations and density rates within the
+    tolerance, the same pair counts (equal counts within each advection step
+    and new ones at each rebuild), and several rebuilds over the run."""
+    case = fc.channel_flag(seed=0) if name == "channel_flag" else _fast_box_3d()
+    ref = O.OracleSim(case)
+    ref.set_advection_cadence("auto")
+    dt, K = _dt_K(ref)
+    sim = Simulation.from_case(case)
+    sim.set_substeps(K)
+    sim.set_advection_cadence("auto")
+    r_start = np.array(ref.f_r)
+    counts = []
+    for k in range(12):
+        sim.step(dt)
+        sim.sync()
+        ref.step(dt, K)
+        g, s, info = sim.get_fluid(), sim.get_solid(), sim.info()
+        e = {"dvdt": rel(g["dvdt"], ref.f_dvdt), "drho": rel(g["drho"], ref.f_drho)}
+        if case.ns:
+            e["fF"] = rel(s["fF"], ref.s_fF)
+            e["v_s"] = rel(s["v"], ref.s_v)
+        e["dr"] = rel(_unwrap(case, g["r"] - r_start), _unwrap(case, ref.f_r - r_start))
+        print(name, k, {q: f"{v:.1e}" for q, v in e.items()})
+        assert max(e.values()) < ACC_TOL, (k, e)
+        c = tuple(info["pairs_" + q] for q in ("ff", "fw", "fs", "sf"))
+        assert c == tuple(ref.last["n_" + q] for q in ("ff", "fw", "fs", "sf")), (k, c)
+        counts.append(c)
+    print(name, "rebuilds", ref.rebuilds)
+    assert len(ref.rebuilds) >= 3 and ref.rebuilds[0] == 0
+    bounds = ref.rebuilds + [len(counts)]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        assert len(set(counts[a:b])) == 1, (a, b, counts[a:b])
+    sim.close()
+
+
 def test_held_configuration_differs_from_the_per_step_rebuild():
     """The held geometry is not a no-op: after a few steps it changes the
     accelerations by far more than the parity tolerance (on the oracle the

@@ -821,6 +821,62 @@ def test_frozen_configuration_conserves_momentum_and_its_pair_counts():
     assert len(set(counts)) > 1   # the lists were rebuilt as the flow moved
 
 
+def _translating_block(U=(0.7, 0.4), eta=0.0, dp=0.01, n=10):
+    """A free fluid block (no walls, body, gravity, initial pressure or
+    reinitialisation) moving rigidly: no pair term acts, its speed stays |U|."""
+    r = fc.lattice((0.0, 0.0), (n * dp, n * dp), dp)
+    return fc.Case(name="translating_block", dim=2, gravity=(0.0, 0.0, 0.0),
+                   domain_lo=(-1.0, -1.0, 0.0), domain_hi=(2.0, 2.0, 1.0),
+                   f_r=r, f_v=np.tile(np.asarray(U, float), (len(r), 1)), f_p=np.zeros(len(r)), f_dp=dp,
+                   f_rho0=1.0, f_c0=10.0, f_eta=eta, w_r=np.zeros((0, 2)), w_n=np.zeros((0, 2)), w_dp=dp,
+                   s_r0=np.zeros((0, 2)), s_v0=np.zeros((0, 2)), s_n0=np.zeros((0, 2)),
+                   s_cons=np.zeros(0, np.uint8), s_dp=dp / 2)
+
+
+@pytest.mark.parametrize("eta, ratio", [(0.0, 2.5), (0.0, 3.2), (0.05, 1.7)])
+def test_automatic_advection_steps_follow_the_criterion(eta, ratio):
+    """Reading F3 on a block whose speed stays |U| (checked): with a fixed dt
+    an advection step lasts while the steps taken in it sum to at most
+    dt_ad = 0.25 min(h / |U|, h^2 / nu), i.e. floor(dt_ad / dt) + 1 steps, so
+    the configuration is rebuilt every that many steps; the viscous limit
+    takes over when h^2 / nu is the smaller term."""
+    U = (0.7, 0.4)
+    case = _translating_block(U, eta)
+    s = O.OracleSim(case)
+    s.set_advection_cadence("auto")
+    h = 1.3 * case.f_dp
+    speed = float(np.hypot(*U))
+    nu = eta / case.f_rho0
+    dt_ad = 0.25 * min(h / speed, h * h / nu if nu > 0 else np.inf)
+    if eta > 0:
+        assert h * h / nu < h / speed   # the viscous term decides here
+    dt = dt_ad / ratio
+    m = int(np.floor(ratio)) + 1
+    for _ in range(4 * m):
+        s.step(dt, 1)
+    assert np.allclose(s.f_v, np.asarray(U), rtol=0, atol=1e-13)
+    assert s.rebuilds == list(range(0, 4 * m, m))
+
+
+def test_automatic_advection_step_takes_the_smallest_criterion_over_it():
+    """An advection step that starts at rest has dt_ad = infinity (no
+    viscosity); it ends once the criterion at a later step's maximum is
+    exceeded by the time taken since the rebuild."""
+    case = _translating_block((0.0, 0.0), 0.0)
+    s = O.OracleSim(case)
+    s.set_advection_cadence(0)
+    dt = 1e-3
+    for _ in range(3):
+        s.step(dt, 1)
+    assert s.rebuilds == [0]        # at rest: held
+    s.f_v[:] = (5.0, 0.0)           # now moving: dt_ad = 0.25 h / 5 = 1.625e-3
+    for _ in range(3):
+        s.step(dt, 1)
+    # step 3 starts from the last step's maximum (0: still held, 4 ms taken);
+    # step 4 starts from 5: dt_ad drops to 1.625 ms < 5 ms taken, so step 5 rebuilds
+    assert s.rebuilds == [0, 5]
+
+
 # --------------------------------------------------------------------------
 # The OpenMP build that times the oracle on many cores gives the same bits
 # --------------------------------------------------------------------------
