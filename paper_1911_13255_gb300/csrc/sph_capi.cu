@@ -58,26 +58,41 @@ int host_chunks(int64_t n, int64_t min_per)
 // [0, n), each on its own host thread (chunk 0 on the calling thread; a
 // thread that cannot be started runs its chunk here).  The set-up loops
 // write disjoint outputs per item, so the result does not depend on the
-// split.
+// split.  Returns false when a chunk threw (out of host memory): no
+// exception leaves a worker thread.
 template <typename F>
-void host_parallel(int64_t n, int chunks, F &&body)
+bool host_parallel(int64_t n, int chunks, F &&body)
 {
+    std::vector<char> bad(chunks > 1 ? chunks : 1, 0);
+    auto run = [&](int k, int64_t lo, int64_t hi) {
+        try {
+            body(k, lo, hi);
+        } catch (...) {
+            bad[k] = 1;
+        }
+    };
     if (chunks <= 1) {
-        body(0, (int64_t)0, n);
-        return;
+        run(0, (int64_t)0, n);
+        return !bad[0];
     }
     std::vector<std::thread> th;
-    th.reserve(chunks - 1);
+    try {
+        th.reserve(chunks - 1);
+    } catch (...) {
+    }
     for (int k = 1; k < chunks; k++) {
         const int64_t lo = n * k / chunks, hi = n * (k + 1) / chunks;
         try {
-            th.emplace_back([&body, k, lo, hi] { body(k, lo, hi); });
+            th.emplace_back([&run, k, lo, hi] { run(k, lo, hi); });
         } catch (...) {
-            body(k, lo, hi);
+            run(k, lo, hi);
         }
     }
-    body(0, (int64_t)0, n / chunks);
+    run(0, (int64_t)0, n / chunks);
     for (auto &t : th) t.join();
+    for (char b : bad)
+        if (b) return false;
+    return true;
 }
 
 struct InstHost {
@@ -185,7 +200,7 @@ int fetch(std::vector<T, A> &dst, const T *src, size_t n)
         T *d = dst.data();
         host_parallel((int64_t)n, host_chunks((int64_t)n, (int64_t)1 << 18), [&](int, int64_t lo, int64_t hi) {
             std::memcpy(d + lo, src + lo, sizeof(T) * (size_t)(hi - lo));
-        });
+        });   // memcpy does not throw
         return SPHFSI_OK;
     }
     cudaGetLastError();   // a pointer the runtime does not know is not an error here
@@ -435,7 +450,7 @@ int make_inst(const InstHost &h, int D, Inst &d)
 // global): pairs a != b of one instance with |r0_a - r0_b|^2 < (2 h_S)^2 in
 // FP64, computed as dx dx + dy dy (+ dz dz) without contraction, found
 // through a cell grid of edge 2 h_S over the body; each row ascending.
-void body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx)
+int body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx)
 {
     const int D = c->dim;
     ptr.assign(1, 0);
@@ -473,7 +488,7 @@ void body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx
         // concatenated in particle order
         const int nch = host_chunks(n, 1024);
         std::vector<std::vector<int>> cidx(nch), clen(nch);
-        host_parallel(n, nch, [&](int ch, int64_t lo_a, int64_t hi_a) {
+        const bool ok = host_parallel(n, nch, [&](int ch, int64_t lo_a, int64_t hi_a) {
             std::vector<int> row;
             for (int a = (int)lo_a; a < (int)hi_a; a++) {
                 row.clear();
@@ -499,11 +514,13 @@ void body_neighbours(sphfsi_ctx *c, std::vector<int> &ptr, std::vector<int> &idx
                 clen[ch].push_back((int)row.size());
             }
         });
+        if (!ok) return SPHFSI_E_NOMEM;
         for (int ch = 0; ch < nch; ch++) {
             idx.insert(idx.end(), cidx[ch].begin(), cidx[ch].end());
             for (int len : clen[ch]) ptr.push_back(ptr.back() + len);
         }
     }
+    return SPHFSI_OK;
 }
 
 // Locality order of a body on the device: lexicographic on the lattice index
@@ -1002,7 +1019,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
             const int fch = host_chunks(h.nf, (int64_t)1 << 15);
             std::vector<double> cmax(fch, 0.0);
             std::vector<char> cbad(fch, 0);
-            host_parallel(h.nf, fch, [&](int k, int64_t lo, int64_t hi) {
+            const bool fok = host_parallel(h.nf, fch, [&](int k, int64_t lo, int64_t hi) {
                 double m = 0.0;
                 for (int64_t i = lo; i < hi; i++) {
                     fx[f0 + i] = h.f_r[i * D];
@@ -1029,6 +1046,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
                 }
                 cmax[k] = m;
             });
+            if (!fok) return SPHFSI_E_NOMEM;
             for (int k = 0; k < fch; k++) {
                 if (cbad[k]) return SPHFSI_E_INVAL;
                 vmax = std::max(vmax, cmax[k]);
@@ -1119,7 +1137,7 @@ int sphfsi_finalize(sphfsi_ctx *c)
     TRY(launch_wall_bin(c->bt, W, D, c->st));
     if (ns > 0) {
         std::vector<int> ptr, nbi;
-        body_neighbours(c, ptr, nbi);
+        TRY(body_neighbours(c, ptr, nbi));
         S.max_nb = 0;
         for (int64_t a = 0; a < ns; a++) S.max_nb = std::max(S.max_nb, ptr[a + 1] - ptr[a]);
         S.nnz = ptr[ns];
