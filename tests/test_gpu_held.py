@@ -213,6 +213,46 @@ def test_held_batch_equals_single_instances_bitwise():
     batch.close()
 
 
+def test_automatic_advection_steps_in_a_batch_follow_instance_0():
+    """Reading F3 in a batch: instance 0's advection steps decide for all.
+    Instance 0 steps bit for bit like its own context with the automatic
+    cadence, and every instance keeps its pair counts over the advection
+    steps that the oracle's instance 0 takes (its rebuilds, at least three)."""
+    cases = [fc.channel_flag(seed=0), fc.tiny_box(seed=3), fc.floating_block(seed=4)]
+    refs = [O.OracleSim(c) for c in cases]
+    dt = min(r.suggest_dt()[0] for r in refs)
+    K = max(r.substeps(dt, r.suggest_dt()[2]) for r in refs)
+    ref0 = refs[0]
+    ref0.set_advection_cadence("auto")
+    stream = torch.cuda.Stream()
+    batch = Simulation.from_cases(cases, stream=stream)
+    single = Simulation.from_case(cases[0], stream=stream)
+    for sim in (batch, single):
+        sim.set_substeps(K)
+        sim.set_advection_cadence("auto")
+    nsteps = 12
+    counts = [[] for _ in cases]
+    for _ in range(nsteps):
+        batch.step(dt)
+        single.step(dt)
+        ref0.step(dt, K)
+        batch.sync()
+        for b in range(len(cases)):
+            i = batch.select(b).info()
+            counts[b].append(tuple(i["pairs_" + q] for q in ("ff", "fw", "fs", "sf")))
+    single.sync()
+    for x, y in ((batch.select(0).get_fluid(), single.get_fluid()), (batch.select(0).get_solid(), single.get_solid())):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+    assert len(ref0.rebuilds) >= 3, ref0.rebuilds
+    bounds = ref0.rebuilds + [nsteps]
+    for b in range(len(cases)):
+        for a, e in zip(bounds[:-1], bounds[1:]):
+            assert len(set(counts[b][a:e])) == 1, (b, a, e, counts[b][a:e])
+    single.close()
+    batch.close()
+
+
 def test_state_setters_rebuild_the_held_configuration():
     """A state setter in the middle of an advection step makes the next step
     rebuild the configuration: afterwards the context steps bit for bit like
