@@ -102,3 +102,29 @@ def test_time_stepping_and_inflow_checks_without_gpu():
         f = pkg.Inflow(*vals)
         assert L.sphfsi_set_inflow(h, ctypes.byref(f)) == rc, vals
     L.sphfsi_destroy(h)
+
+
+def test_new_entry_points_check_their_state_without_gpu():
+    """The asynchronous position read, the advection cadence (0 = automatic)
+    and the wait limit refuse a NULL context, and a context that is not
+    finalized yet (SPHFSI_E_STATE), before touching any device; the strings
+    of the two stop conditions name them."""
+    import paper_1911_13255_gb300 as pkg
+    L = pkg.lib()
+    buf = (ctypes.c_double * 4)()
+    assert L.sphfsi_get_solid_positions_async(None, buf) == -1
+    assert L.sphfsi_set_advection_cadence(None, 0) == -1
+    assert L.sphfsi_set_wait_limit(None, 0) == -1
+    p = pkg.Params()
+    p.dim = 2
+    for d in range(2):
+        p.domain_lo[d], p.domain_hi[d] = 0.0, 1.0
+    h = ctypes.c_void_p()
+    assert L.sphfsi_create(ctypes.byref(h), ctypes.byref(p), None) == 0
+    assert L.sphfsi_get_solid_positions_async(h, buf) == -4
+    assert L.sphfsi_set_advection_cadence(h, 0) == -4
+    assert L.sphfsi_set_advection_cadence(h, 3) == -4
+    assert L.sphfsi_step(h, 1.0) == -4
+    L.sphfsi_destroy(h)
+    assert b"run-away" in L.sphfsi_strerror(-5)
+    assert L.sphfsi_strerror(-6).startswith(b"bounded")
