@@ -217,33 +217,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_pairlist(Batch bt, Fluid f, Walls
                        : ((uint32_t)nF | ((uint32_t)nW << 11) | (solid ? kListSolid : 0u));
 }
 
-// The same rows, one warp per cell and one lane per particle of the cell:
-// every candidate of the 3^d neighbour cells is loaded once for the whole
-// warp (one broadcast load) and each lane tests its own particle against it
-// and appends to its own row, so the entries come in the same order as
-// above (fluid by cell, then slot, from the front; walls likewise from the
-// back).  Cells of more than 32 particles take several rounds.  16 resident
-// blocks per SM (32 registers a thread): the build is issue- and
-// load-latency bound, and the extra warps outweigh a few spilled registers
-// (3-D duct: 2.37 -> 2.32 ms; 56-register pair loops, by contrast, ran
-// slower than at 64).
+// The same rows built per cell, one lane per particle of the cell: each lane
+// appends to its own row, so the entries come in the same order as above
+// (fluid by cell, then slot, from the front; walls likewise from the back).
+// The rows of the targets [t0, t1) of one non-empty cell, G lanes of a
+// group per round (this thread is lane `lane` of its group): every
+// candidate of the 3^d neighbour cells is loaded once for the group and each
+// lane tests its own target against it.  No warp-wide operation, so the two
+// half-warps of a warp may run two cells side by side.
 template <int D>
-__global__ void __launch_bounds__(128, 16) k_pairlist_cells(Batch bt, Fluid f, Walls w, Solid s)
+__device__ __forceinline__ void cell_rows(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int cell,
+                                          int t0, int t1, int lane, int G)
 {
-    pdl_enter();
-    if (step_failed(bt)) return;   // the step's cell starts are not valid
-    if (!rebuild_step(bt, f)) return;
-    const int cell = blockIdx.x * 4 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (cell >= bt.ncell) return;
-    const int t0 = f.cstart[cell], t1 = f.cstart[cell + 1];
-    if (t0 >= t1) return;
     const Inst &In = bt.I[f.inst[t0]];
     const Grid &g = In.g;
     const float rc2 = In.P.rc2F;
     const int cap = f.list_cap;
     int cx, cy, cz;
     cell_xyz(cell, In, cx, cy, cz);
-    for (int tb = t0; tb < t1; tb += 32) {
+    for (int tb = t0; tb < t1; tb += G) {
         const int i = tb + lane;
         const bool act = i < t1;
         const float4 Pi = f.P4[act ? i : t0];
@@ -280,6 +272,40 @@ __global__ void __launch_bounds__(128, 16) k_pairlist_cells(Batch bt, Fluid f, W
     }
 }
 
+// One warp per two consecutive cells.  When they hold at most 32 targets
+// together, one round builds both: the first cell's targets take the first
+// lanes, the second cell's the next ones (in the 3-D duct, cells of 8, 12
+// and 18 particles come in rows where such pairs are common, and the two
+// groups then walk neighbour cells of nearly equal size); otherwise the
+// whole warp builds one cell after the other.  Either way each target's row
+// is built by one lane in candidate order, so the rows do not depend on the
+// grouping.
+// 16 resident blocks per SM (32 registers a thread): the build is issue- and
+// load-latency bound, and the extra warps outweigh a few spilled registers
+// (3-D duct: 2.37 -> 2.32 ms; 56-register pair loops, by contrast, ran
+// slower than at 64).
+template <int D>
+__global__ void __launch_bounds__(128, 16) k_pairlist_cells(Batch bt, Fluid f, Walls w, Solid s)
+{
+    pdl_enter();
+    if (step_failed(bt)) return;   // the step's cell starts are not valid
+    if (!rebuild_step(bt, f)) return;
+    const int c0 = 2 * (blockIdx.x * 4 + (int)(threadIdx.x >> 5)), lane = threadIdx.x & 31;
+    if (c0 >= bt.ncell) return;
+    const bool two = c0 + 1 < bt.ncell;
+    const int a0 = f.cstart[c0], a1 = f.cstart[c0 + 1];   // the second cell starts where the first ends
+    const int b1 = two ? f.cstart[c0 + 2] : a1;
+    const int na = a1 - a0;
+    if (b1 - a0 <= 32) {
+        const bool second = lane >= na;
+        const int t0 = second ? a1 : a0, t1 = second ? b1 : a1, ll = second ? lane - na : lane;
+        if (ll < t1 - t0) cell_rows<D>(bt, f, w, s, second ? c0 + 1 : c0, t0, t1, ll, 32);
+    } else {
+        if (a0 < a1) cell_rows<D>(bt, f, w, s, c0, a0, a1, lane, 32);
+        if (a1 < b1) cell_rows<D>(bt, f, w, s, c0 + 1, a1, b1, lane, 32);
+    }
+}
+
 int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid &s, int dim, cudaStream_t st)
 {
     if (f.n == 0 || !f.list) return 0;
@@ -291,7 +317,7 @@ int launch_pairlist(const Batch &bt, const Fluid &f, const Walls &w, const Solid
     };
     auto by_lanes = [&](auto Dc) {
         constexpr int D_ = decltype(Dc)::value;
-        if (f.list_lanes == 1) launch_k(k_pairlist_cells<D_>, (bt.ncell + 3) / 4, 128, 0, st, bt, f, w, s);
+        if (f.list_lanes == 1) launch_k(k_pairlist_cells<D_>, (bt.ncell + 7) / 8, 128, 0, st, bt, f, w, s);
         else if (f.list_lanes == 8) go(Dc, std::integral_constant<int, 8>{});
         else if (f.list_lanes == 16) go(Dc, std::integral_constant<int, 16>{});
         else if (f.list_lanes == 32) go(Dc, std::integral_constant<int, 32>{});
